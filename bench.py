@@ -1,0 +1,382 @@
+#!/usr/bin/env python
+"""Benchmark of hyperedge effective-resistance estimation (Algorithm 1) on GB300.
+
+One step = the whole hot path on one synthetic netlist: incidence build,
+Krylov basis (k steps of both expansions), CholQR2, scoring (two passes).
+Default workload: 500x420 grid (n = 210,000), 200,000 nets (80 % 2-3 pins,
+Pareto(2.2) tail capped at 400, 2 % long-range pins), k = 20 per expansion,
+S = 4 starts, K = 160 basis vectors, FP32 form (FP64 Cholesky and Q_H); the
+plain FP64 form is timed beside it for the speedup.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+instead, on a bounded window of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from netlists import start_block, window_subhypergraph, workload  # noqa: E402
+
+METRIC = "pins/s of Krylov resistance scoring; HBM GB/s; speedup vs FP64 plain at tol"
+L2_FLUSH_BYTES = 512 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="grid500x420_m200k")
+    ap.add_argument("--form", default="f32", choices=["f32", "f64"])
+    ap.add_argument("--fp64-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- helpers
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def instance(name, rank):
+    """The rank's netlist: the named workload, seed shifted per rank (each
+    rank scores its own netlist: weak scaling)."""
+    from netlists.synth import WORKLOADS, grid_netlist
+    cfg = dict(WORKLOADS[name])
+    k, S = cfg.pop("k"), cfg.pop("S")
+    cfg["seed"] = cfg["seed"] + 1000 * rank
+    H = grid_netlist(name=name, **cfg)
+    return H, k, S
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                pass
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured", d.get("sm_max_mhz", 2070.0)
+    return 6800.0, "fallback", 2070.0
+
+
+def kernel_model(name, H, K, S, k, esz):
+    """Algorithmic (compulsory, cache-perfect) bytes or flops of one launch of
+    `name`: ('hbm', bytes) or ('alu', flops)."""
+    n, m, P = H.n, H.m, H.P
+    if name == "k_gram":
+        return "alu", float(n) * K * (K + 1)          # K(K+1)/2 dots of length n
+    if name == "k_apply":
+        return "alu", float(n) * K * (K + 1)          # triangular V R^-1
+    if name == "k_score_pass1":
+        return "hbm", n * K * esz + 4.0 * P + 4.0 * (m + 1) + 8.0 * m
+    if name == "k_score_pass2":
+        return "hbm", n * K * esz + 4.0 * P + 4.0 * (m + 1) + 8.0 * m + 4.0 * m + 20.0 * m
+    if name == "k_edge_pass":   # reads node rows of 2 chains, writes s_e and star edge rows
+        return "hbm", 4.0 * P + 4.0 * (m + 1) + 8.0 * m + esz * S * (2 * n + 3 * m)
+    if name == "k_node_pass":
+        return "hbm", 4.0 * P + 4.0 * (n + 1) + 8.0 * (2 * m + 6 * n) + esz * S * (2 * m + 6 * n)
+    if name == "k_update":
+        return "hbm", esz * S * (2 * n + m) * 4.0 + 8.0 * (2 * n + m)
+    return "hbm", float("nan")
+
+
+# ---------------------------------------------------------------- reference arm (oracle)
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    from oracle import hef_oracle as O
+    H, k, S = instance(args.workload, 0)
+    Hs = window_subhypergraph(H, 0, min(H.nx, 250), 0, min(H.ny, 210)) if H.nx else H
+    x0c, x0b = start_block(Hs.n, Hs.m, S, 0)
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        O.hyperedge_resistance(Hs.n, Hs.eptr, Hs.pins, Hs.w, x0c, x0b, k)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    t = sum(times) / len(times)
+    v = Hs.P / t
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "pins/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "sample": f"{Hs.nx}x{Hs.ny} window",
+                   "n": Hs.n, "m": Hs.m, "P": Hs.P, "k": k, "S": S, "K": 2 * k * S},
+        "cpu_baseline": {"value": v, "unit": "pins/s", "cores": os.cpu_count(),
+                         "kind": "oracle",
+                         "sample": f"{Hs.nx}x{Hs.ny} window of the workload "
+                                   f"(n={Hs.n}, m={Hs.m}, P={Hs.P}); numpy/scipy FP64, "
+                                   "BLAS calls on all cores"},
+        "e2e": {"value": v, "unit": "pins/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(name):
+    from oracle import hef_oracle as O
+    H, k, S = instance(name, 0)
+    Hs = window_subhypergraph(H, 0, H.nx, 0, max(1, H.ny // 2)) if H.nx else H
+    x0c, x0b = start_block(Hs.n, Hs.m, S, 0)
+    t0 = time.perf_counter()
+    O.hyperedge_resistance(Hs.n, Hs.eptr, Hs.pins, Hs.w, x0c, x0b, k)
+    t = time.perf_counter() - t0
+    return {"value": Hs.P / t, "unit": "pins/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{Hs.nx}x{Hs.ny} window (n={Hs.n}, m={Hs.m}, P={Hs.P}), one run, "
+                      f"{t:.1f} s; numpy/scipy FP64, BLAS calls on all cores"}
+
+
+# ---------------------------------------------------------------- our arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    import paper_2511_06600_gb300 as hef
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    H, k, S = instance(args.workload, rank)
+    K = 2 * k * S
+    x0c, x0b = start_block(H.n, H.m, S, rank)
+    t_in = dict(eptr=torch.from_numpy(H.eptr).to(dev), pins=torch.from_numpy(H.pins).to(dev),
+                w=torch.from_numpy(H.w).to(dev), x0c=torch.from_numpy(x0c).to(dev),
+                x0b=torch.from_numpy(x0b).to(dev))
+    dtype = torch.float32 if args.form == "f32" else torch.float64
+    esz = 4 if args.form == "f32" else 8
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x):
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def timed(fn, steps, warmup, trace=None):
+        """Per-step CUDA-event times (ms) with an L2 flush before each step."""
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        if trace:
+            hef.trace_read()
+            hef.trace_kernels(trace)
+        barrier()
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        l0 = hef.launch_count()
+        wall0 = time.perf_counter()
+        for i in range(steps):
+            flush.fill_(float(i))
+            ev[i][0].record(st)
+            fn()
+            ev[i][1].record(st)
+        torch.cuda.synchronize()
+        barrier()
+        wall = time.perf_counter() - wall0
+        launches = hef.launch_count() - l0
+        tr = None
+        if trace:
+            hef.trace_kernels(None)
+            tr = hef.trace_read()
+        ms = [a.elapsed_time(b) for a, b in ev]
+        return ms, launches, wall, tr
+
+    # ---- main form: device-resident inputs
+    pipe = hef.Pipeline(H.n, H.m, H.P, k, S, dtype, device=dev)
+    step = lambda: pipe.run(t_in["eptr"], t_in["pins"], t_in["w"], t_in["x0c"], t_in["x0b"])  # noqa
+    # which kernel dominates: trace all library kernels over the warm-up steps
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    pipe.check()
+    hef.trace_read()
+    hef.trace_kernels("k_")
+    step()
+    torch.cuda.synchronize()
+    hef.trace_kernels(None)
+    per_kernel = hef.trace_read()
+    dominant = max(per_kernel.items(), key=lambda kv: kv[1][1])[0]
+
+    clocks = Clocks(local)
+    clocks.start()
+    ms, launches, wall, tr = timed(step, args.steps, args.warmup, trace=dominant)
+    clk = clocks.stop()
+    pipe.check()
+    R32 = pipe.out["R"].double().cpu().numpy()
+    t_step = max_over_ranks(sum(ms) / len(ms))
+    value = world * H.P / (t_step * 1e-3)
+
+    # ---- roofline of the dominant kernel (live, same timed region)
+    hbm_peak, peak_kind, sm_max = peaks()
+    nl, tot = tr.get(dominant, (0, float("nan")))
+    bound, units = kernel_model(dominant, H, K, S, k, esz)
+    avg_s = (tot / max(nl, 1)) * 1e-3
+    if bound == "hbm":
+        achieved = units / avg_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "kernel": dominant,
+                "peak_kind": peak_kind}
+    else:
+        alu_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12  # FP32 FMA lanes x 2 flops x max clock
+        achieved = units / avg_s / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                "frac": achieved / alu_peak, "traffic": None, "kernel": dominant,
+                "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
+    roof["launches"] = nl
+    roof["avg_ms"] = tot / max(nl, 1)
+
+    # ---- plain FP64 form (speedup reference) and its agreement with the FP32 form
+    pipe64 = hef.Pipeline(H.n, H.m, H.P, k, S, torch.float64, device=dev)
+    step64 = lambda: pipe64.run(t_in["eptr"], t_in["pins"], t_in["w"], t_in["x0c"], t_in["x0b"])  # noqa
+    ms64, _, _, _ = timed(step64, args.fp64_steps, 1)
+    pipe64.check()
+    R64 = pipe64.out["R"].cpu().numpy()
+    t64 = max_over_ranks(sum(ms64) / len(ms64))
+    big = R64 >= 1e-3 * R64.max()
+    rel = np.abs(R32 - R64) / np.maximum(R64, 1e-300)
+    err = {"max_rel": float(rel[big].max()), "p99_rel": float(np.percentile(rel[R64 > 0], 99)),
+           "normwise": float(np.abs(R32 - R64).max() / R64.max())}
+    del pipe64
+
+    # ---- end to end through the public API: pinned host inputs in, scores out
+    e2e = None
+    if not args.no_e2e:
+        host = {key: t.cpu().pin_memory() for key, t in t_in.items()}
+        dbuf = {key: torch.empty_like(t) for key, t in t_in.items()}
+        R_host = torch.empty(H.m, dtype=torch.float64).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in host.values())
+        d2h = R_host.numel() * R_host.element_size()
+
+        def e2e_step():
+            for key in host:
+                dbuf[key].copy_(host[key], non_blocking=True)
+            o = pipe.run(dbuf["eptr"], dbuf["pins"], dbuf["w"], dbuf["x0c"], dbuf["x0b"])
+            R_host.copy_(o["R"], non_blocking=True)
+            torch.cuda.current_stream().synchronize()
+
+        ms_e, _, _, _ = timed(e2e_step, args.steps, 1)
+        te = max_over_ranks(sum(ms_e) / len(ms_e))
+        e2e = {"value": world * H.P / (te * 1e-3), "unit": "pins/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "ms_per_step": te}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.workload)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "pins/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": args.form, "data": "synthetic",
+            "config": {"workload": args.workload, "n": H.n, "m": H.m, "P": H.P, "k": k, "S": S,
+                       "K": K, "form": args.form + " storage/accumulation, FP64 Cholesky and Q_H",
+                       "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write)",
+                       "parallelism": f"{world} independent netlists (one per GPU)"},
+            "scores_per_s": world * H.m / (t_step * 1e-3),
+            "fp64_plain": {"value": world * H.P / (t64 * 1e-3), "unit": "pins/s",
+                           "ms_per_step": t64},
+            "speedup_vs_fp64": t64 / t_step,
+            "error_vs_fp64": err,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "launches_per_step": launches / max(args.steps, 1),
+            "per_kernel_ms_one_step": {k_: round(v[1], 4) for k_, v in
+                                       sorted(per_kernel.items(), key=lambda kv: -kv[1][1])},
+            "clocks": clk,
+            "wall_s_timed_region": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

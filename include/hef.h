@@ -1,0 +1,224 @@
+/*
+ * hef.h -- C ABI of the GB300 hyperedge effective-resistance library.
+ *
+ * The library computes the hyperedge effective-resistance estimates of
+ * HyperEF 2.0 (arXiv 2511.06600, Algorithm 1, Section III-A.4) on one
+ * NVIDIA GB300 (sm_103a):
+ *
+ *   1. hef_build_incidence   Algorithm 1 steps 1-2: the star expansion G_b
+ *                            and clique expansion G_c of H = (V, E, w), kept
+ *                            implicit as edge-major and vertex-major incidence.
+ *   2. hef_krylov_basis      Algorithm 1 step 3, Eq. krylov: Krylov vectors
+ *                            A x ... A^k x of both expansions' random-walk
+ *                            operators from S random starts each.
+ *   3. hef_orthonormalize    Algorithm 1 step 4: orthonormal basis of the
+ *                            vertex parts (CholQR2, FP64 Cholesky).
+ *   4. hef_edge_resistance   Algorithm 1 steps 5 and 7, Eqs. non-linerQ,
+ *                            ratios and R: R_e = max_i spread_e(chi_i)^2 /
+ *                            Q_H(chi_i).
+ *
+ * Conventions shared by every call
+ *  - All array arguments are DEVICE pointers unless stated otherwise; the
+ *    caller owns them and keeps them alive until the work on `stream` is done.
+ *    `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *    asynchronous on `stream` and performs no host<->device synchronisation,
+ *    except hef_incidence_check, which synchronises `stream`.
+ *  - The library never allocates device memory.  Each call that needs
+ *    scratch takes a caller-provided `workspace` of at least the size that
+ *    its *_workspace_bytes query returns (256-byte aligned base).
+ *  - Matrices are row-major: row r of an n x K matrix starts at r * ld
+ *    elements; ld >= K.  Rows must start 16-byte aligned (ld * element size
+ *    a multiple of 16 bytes).
+ *  - Element types: HEF_F64 (double), HEF_F32 (float).
+ *  - Return value: HEF_OK or a negative hef_status; hef_last_error() gives a
+ *    thread-local message for the last failing call.  Errors found by device
+ *    code (malformed incidence, non-positive weights) are recorded in the
+ *    incidence's device status word: later kernels that use that incidence
+ *    do no work, and hef_incidence_check returns HEF_ERR_INVALID_INPUT.
+ */
+#ifndef HEF_H_
+#define HEF_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int32_t hef_status;
+
+#define HEF_OK 0
+#define HEF_ERR_INVALID_ARG (-1)   /* host-side argument check failed */
+#define HEF_ERR_CUDA (-2)          /* a CUDA launch or runtime call failed */
+#define HEF_ERR_WORKSPACE (-3)     /* workspace missing, misaligned or too small */
+#define HEF_ERR_BREAKDOWN (-4)     /* orthonormalisation lost every column */
+#define HEF_ERR_TIMEOUT (-5)       /* a bounded device wait expired */
+#define HEF_ERR_UNSUPPORTED (-6)   /* valid request outside supported sizes */
+#define HEF_ERR_INVALID_INPUT (-7) /* device-side check of the hypergraph failed */
+
+#define HEF_F64 0
+#define HEF_F32 1
+
+/* Reductions over basis vectors in hef_edge_resistance. */
+#define HEF_REDUCE_MAX 0 /* Eq. R: R_e = max_i r_e(chi_i) */
+#define HEF_REDUCE_SUM 1 /* sum_i r_e(chi_i); with Laplacian eigenvectors of a
+                            2-pin graph as the basis this is Eq. eff_resist0 */
+
+/* Clique-expansion pair weight (Section III-A.4). */
+#define HEF_CLIQUE_HYPEREDGE 0 /* w(e)/(|e|-1): clique degree = hypergraph degree */
+#define HEF_CLIQUE_PAPER 1     /* w(e)/C(|e|,2): weight spread evenly over pairs */
+
+/* Bits of the device status word (hef_incidence_check's detail output). */
+#define HEF_BAD_EPTR 1u      /* eptr[0] != 0, eptr[m] != P or decreasing */
+#define HEF_BAD_PIN 2u       /* a pin outside [0, n) */
+#define HEF_DUP_PIN 4u       /* a vertex repeated within one hyperedge */
+#define HEF_BAD_WEIGHT 8u    /* a weight that is not finite and > 0 */
+
+const char* hef_last_error(void);
+const char* hef_status_string(hef_status s);
+int32_t hef_abi_version(void);
+
+/* ------------------------------------------------------------------------
+ * Launch accounting and kernel timing (no counterpart in the paper: this is
+ * the library's tracing facility).
+ *
+ * hef_launch_count: number of kernels this library has launched in the
+ * process so far (all threads).
+ * hef_trace_kernels: from now on, record a pair of CUDA events on the launch
+ * stream around every launch of a library kernel whose name contains
+ * `name_substring` (e.g. "k_score_pass"); NULL or "" stops recording.  At most
+ * 65536 launches are recorded between reads.
+ * hef_trace_read: synchronises the recorded events, writes per kernel name
+ * (up to `cap` names, 64 chars each, NUL-terminated) the number of launches
+ * and their summed duration in ms, forgets the records, and returns the number
+ * of distinct names recorded.
+ * ---------------------------------------------------------------------- */
+uint64_t hef_launch_count(void);
+hef_status hef_trace_kernels(const char* name_substring);
+int32_t hef_trace_read(int32_t cap, char* names, int64_t* launches,
+                       double* total_ms);
+
+/* ------------------------------------------------------------------------
+ * Incidence (Algorithm 1 steps 1-2; expansions of Section III-A.4).
+ *
+ * Input H = (V, E, w) in edge-major (CSC) form: hyperedge e has the pins
+ * pins[eptr[e] .. eptr[e+1]) (vertex ids in [0, n), distinct within e) and
+ * weight w[e] > 0.  0 <= n, m; 0 <= P = eptr[m] < 2^31.
+ *
+ * The build copies what it needs into `workspace` (CSC in a locality order of
+ * the hyperedges, the vertex-major transpose, per-edge weights w/(|e|-1) or
+ * w/C(|e|,2) and w/|e|, vertex degrees of both expansions), validates the
+ * input on the device and records problems in the device status word.
+ * Hyperedges with fewer than 2 pins join neither expansion and score 0.
+ * The returned handle is a small host object (malloc); it refers to the
+ * workspace, which must outlive it.  Free it with hef_free_incidence.
+ * ---------------------------------------------------------------------- */
+typedef struct hef_incidence hef_incidence;
+
+size_t hef_incidence_workspace_bytes(int64_t n, int64_t m, int64_t P);
+
+hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P,
+                               const int64_t* eptr, const int32_t* pins,
+                               const double* w, int32_t clique_mode,
+                               void* workspace, size_t workspace_bytes,
+                               void* stream, hef_incidence** out);
+
+/* Synchronises `stream` and returns HEF_ERR_INVALID_INPUT (with the status
+ * bits in *detail, the first offending hyperedge in *where; either may be
+ * NULL) if the device-side validation failed, else HEF_OK. */
+hef_status hef_incidence_check(const hef_incidence* inc, void* stream,
+                               uint32_t* detail, int64_t* where);
+
+hef_status hef_incidence_sizes(const hef_incidence* inc, int64_t* n,
+                               int64_t* m, int64_t* P);
+
+/* Copies of the built incidence, for callers that consume the expansions
+ * (e.g. a downstream clustering): perm[m] internal -> caller hyperedge id
+ * (the locality order: ascending smallest pin, ties by caller id);
+ * vptr[n+1] and vedge[P] the vertex-major incidence (caller hyperedge ids,
+ * in locality order within each vertex); dc[n], db[n] the vertex degrees of
+ * the clique and star expansions.  Any output may be NULL.  Asynchronous. */
+hef_status hef_incidence_export(const hef_incidence* inc, int32_t* perm,
+                                int32_t* vptr, int32_t* vedge, double* dc,
+                                double* db, void* stream);
+
+void hef_free_incidence(hef_incidence* inc);
+
+/* ------------------------------------------------------------------------
+ * Krylov basis (Algorithm 1 step 3, Eq. krylov; Section III-A.4).
+ *
+ * For each expansion op (0 = clique on n vertices, 1 = star on n + m
+ * vertices) and start s < S, the chain x, M x, ..., M^k x of the random-walk
+ * operator M = D^-1 W, started from the given random vector with the
+ * trivial eigenvectors of M (the constant on non-isolated vertices, and for
+ * the bipartite star expansion the vertex-side and star-side constants)
+ * projected out in the degree-weighted inner product.  The raw start is not
+ * part of the basis.  Vertex rows of the j-th chain vector (j = 1..k) go to
+ * column c = (j-1)*2S + op*S + s of V (n x ldv, dtype), scaled arbitrarily
+ * per column and not mean-free: hef_orthonormalize removes the mean and the
+ * scale.  A chain whose Krylov space is exhausted yields zero columns.
+ *
+ * x0_clique: n x S row-major double.  x0_star: (n + m) x S row-major double,
+ * vertex rows first, then one row per hyperedge in the caller's order.
+ * K = 2 k S <= 512; S in {1, 2, 4, 8, 16}; ldv >= K.
+ * ---------------------------------------------------------------------- */
+size_t hef_krylov_workspace_bytes(const hef_incidence* inc, int32_t k,
+                                  int32_t S, int32_t dtype);
+
+hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int32_t S,
+                            int32_t dtype, const double* x0_clique,
+                            const double* x0_star, void* V, int64_t ldv,
+                            void* workspace, size_t workspace_bytes,
+                            void* stream);
+
+/* ------------------------------------------------------------------------
+ * Orthonormalisation (Algorithm 1 step 4): in place, V (n x K, ldv, dtype)
+ * becomes Q with orthonormal, mean-free columns spanning the mean-free parts
+ * of V's columns, in column order (Q = (I - 11^T/n) V R^-1 with R upper
+ * triangular, positive diagonal).  CholQR2: Gram matrix, FP64 Cholesky,
+ * triangular apply, twice.  A column whose squared norm after removing the
+ * mean and the earlier columns is <= tol * its squared norm as given (tol
+ * 1e-12 for HEF_F64, 1e-5 for HEF_F32; a Cholesky pivot resolves relative
+ * residual norms only down to about sqrt(machine epsilon)) is dropped: its Q
+ * column is zero and scoring ignores it.
+ * R_out (K x K double, row-major, nullable) receives R.  rank_out (one int32,
+ * nullable) receives the number of kept columns.  K <= 512, n >= 1.
+ * ---------------------------------------------------------------------- */
+size_t hef_orthonormalize_workspace_bytes(int64_t n, int32_t K, int32_t dtype);
+
+hef_status hef_orthonormalize(int64_t n, int32_t K, int32_t dtype, void* V,
+                              int64_t ldv, double* R_out, int32_t* rank_out,
+                              void* workspace, size_t workspace_bytes,
+                              void* stream);
+
+/* ------------------------------------------------------------------------
+ * Edge resistance (Algorithm 1 steps 5 and 7; Eqs. non-linerQ, ratios, R).
+ *
+ * For basis column i of Q (n x K, ldq, dtype) and hyperedge e with >= 2
+ * pins: spread_{e,i} = max_{p in e} Q[p,i] - min_{p in e} Q[p,i];
+ * Q_H[i] = sum_e w_e spread_{e,i}^2 (FP64, fixed summation order);
+ * r_{e,i} = spread_{e,i}^2 / Q_H[i] for columns with Q_H[i] > 1e-300;
+ * R_e = max_i r_{e,i} (HEF_REDUCE_MAX) or sum_i r_{e,i} (HEF_REDUCE_SUM).
+ * Outputs are indexed by the caller's hyperedge ids:
+ *   R_out[m] double; QH_out[K] double (nullable);
+ *   argvec[m] (nullable): the i attaining the max (lowest i on ties, -1 if
+ *   none); pmax[m], pmin[m] (nullable): the vertices attaining the max and
+ *   min of column argvec on e (lowest position within e on ties, -1 if none).
+ * K <= 512.
+ * ---------------------------------------------------------------------- */
+size_t hef_edge_resistance_workspace_bytes(const hef_incidence* inc,
+                                           int32_t K);
+
+hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q,
+                               int64_t ldq, int32_t K, int32_t dtype,
+                               int32_t reduce, double* R_out, double* QH_out,
+                               int32_t* argvec, int32_t* pmax, int32_t* pmin,
+                               void* workspace, size_t workspace_bytes,
+                               void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEF_H_ */

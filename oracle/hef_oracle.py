@@ -182,13 +182,13 @@ def krylov_chain(M, d, trivial, x0, k):
     for j in range(k):
         y = M @ prev
         y = deflate(y, d, trivial)
-        before = np.linalg.norm(y)
         B = X[:, :j]
         for _ in range(2):  # Gram-Schmidt twice against the chain so far
             y -= B @ (B.T @ y)
         after = np.linalg.norm(y)
-        if before == 0.0 or after <= DROP_TOL * before:
-            # exhausted: later powers lie in the span already
+        if after <= DROP_TOL * np.linalg.norm(prev):
+            # exhausted: M maps the chain into its own span (up to rounding),
+            # so no later power adds a direction
             break
         y /= after
         X[:, j] = y

@@ -1,0 +1,351 @@
+"""ctypes binding of libhef.so (argument marshalling only).
+
+Every function here forwards device pointers of torch CUDA tensors and the
+current CUDA stream to the C ABI declared in include/hef.h; all arithmetic
+runs in the library's kernels.  Device memory (outputs and workspaces) is
+allocated with torch.  If the library is missing, loading fails loudly: there
+is no other implementation.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhef.so")
+
+HEF_F64, HEF_F32 = 0, 1
+HEF_REDUCE_MAX, HEF_REDUCE_SUM = 0, 1
+HEF_CLIQUE_HYPEREDGE, HEF_CLIQUE_PAPER = 0, 1
+HEF_ERR_INVALID_INPUT = -7
+
+_DTYPES = {HEF_F64: torch.float64, HEF_F32: torch.float32}
+_CODES = {torch.float64: HEF_F64, torch.float32: HEF_F32, "f64": HEF_F64, "f32": HEF_F32}
+
+c_i32, c_i64, c_sz, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
+
+_SIGS = {
+    "hef_last_error": (ctypes.c_char_p, []),
+    "hef_status_string": (ctypes.c_char_p, [c_i32]),
+    "hef_abi_version": (c_i32, []),
+    "hef_launch_count": (ctypes.c_uint64, []),
+    "hef_trace_kernels": (c_i32, [ctypes.c_char_p]),
+    "hef_trace_read": (c_i32, [c_i32, ctypes.c_char_p, ctypes.POINTER(c_i64),
+                               ctypes.POINTER(ctypes.c_double)]),
+    "hef_incidence_workspace_bytes": (c_sz, [c_i64, c_i64, c_i64]),
+    "hef_build_incidence": (c_i32, [c_i64, c_i64, c_i64, c_p, c_p, c_p, c_i32, c_p, c_sz, c_p,
+                                    ctypes.POINTER(c_p)]),
+    "hef_incidence_check": (c_i32, [c_p, c_p, ctypes.POINTER(ctypes.c_uint32),
+                                    ctypes.POINTER(c_i64)]),
+    "hef_incidence_sizes": (c_i32, [c_p, ctypes.POINTER(c_i64), ctypes.POINTER(c_i64),
+                                    ctypes.POINTER(c_i64)]),
+    "hef_incidence_export": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p]),
+    "hef_free_incidence": (None, [c_p]),
+    "hef_krylov_workspace_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32]),
+    "hef_krylov_basis": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p, c_sz, c_p]),
+    "hef_orthonormalize_workspace_bytes": (c_sz, [c_i64, c_i32, c_i32]),
+    "hef_orthonormalize": (c_i32, [c_i64, c_i32, c_i32, c_p, c_i64, c_p, c_p, c_p, c_sz, c_p]),
+    "hef_edge_resistance_workspace_bytes": (c_sz, [c_p, c_i32]),
+    "hef_edge_resistance": (c_i32, [c_p, c_p, c_i64, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_p, c_p,
+                                    c_p, c_sz, c_p]),
+}
+
+_lib = None
+
+
+class HefError(RuntimeError):
+    def __init__(self, fn, status, msg):
+        super().__init__(f"{fn}: {status_string(status)}: {msg}")
+        self.status = status
+
+
+def lib():
+    """Load libhef.so (built in-tree by paper_2511_06600_gb300.build)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with `python -m paper_2511_06600_gb300.build` "
+                "(there is no fallback implementation)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGS.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def status_string(s):
+    return lib().hef_status_string(s).decode()
+
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(lib().hef_launch_count())
+
+
+def trace_kernels(substring):
+    """Time every launch of library kernels whose name contains `substring`
+    with CUDA events (None stops)."""
+    lib().hef_trace_kernels(substring.encode() if substring else None)
+
+
+def trace_read(cap=64):
+    """{kernel name: (launches, total ms)} of the traced launches so far."""
+    names = ctypes.create_string_buffer(64 * cap)
+    launches = (c_i64 * cap)()
+    ms = (ctypes.c_double * cap)()
+    k = lib().hef_trace_read(cap, names, launches, ms)
+    out = {}
+    for i in range(min(k, cap)):
+        nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]))
+    return out
+
+
+def _check(fn, status):
+    if status != 0:
+        raise HefError(fn, status, lib().hef_last_error().decode())
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dtype_code(dtype):
+    if isinstance(dtype, int):
+        return dtype
+    return _CODES[dtype]
+
+
+def _workspace(nbytes, device):
+    # 256-byte aligned: the caching allocator returns 512-byte aligned blocks
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def padded_ld(K, dtype):
+    """Row stride of an n x K basis: K rounded up to 16 bytes."""
+    per = 16 // torch.empty((), dtype=_DTYPES[_dtype_code(dtype)]).element_size()
+    return (K + per - 1) // per * per
+
+
+class Incidence:
+    """A built incidence (hef_build_incidence) and the workspace it lives in."""
+
+    def __init__(self, n, eptr, pins, w, clique_mode=HEF_CLIQUE_HYPEREDGE, stream=None):
+        L = lib()
+        dev = eptr.device
+        assert eptr.dtype == torch.int64 and pins.dtype == torch.int32 and w.dtype == torch.float64
+        assert eptr.is_cuda and pins.is_cuda and w.is_cuda
+        self.n = int(n)
+        self.m = int(eptr.numel() - 1)
+        self.P = int(pins.numel())
+        self.device = dev
+        ws = L.hef_incidence_workspace_bytes(self.n, self.m, self.P)
+        self.workspace = _workspace(ws, dev)
+        # keep the inputs alive until the build has run
+        self._inputs = (eptr, pins, w)
+        h = c_p()
+        _check("hef_build_incidence",
+               L.hef_build_incidence(self.n, self.m, self.P, _ptr(eptr), _ptr(pins), _ptr(w),
+                                     int(clique_mode), _ptr(self.workspace), ws, _stream(stream),
+                                     ctypes.byref(h)))
+        self.handle = h
+
+    def check(self, stream=None):
+        """Synchronise and raise HefError if device validation failed."""
+        detail = ctypes.c_uint32(0)
+        where = c_i64(-1)
+        st = lib().hef_incidence_check(self.handle, _stream(stream), ctypes.byref(detail),
+                                       ctypes.byref(where))
+        if st != 0:
+            err = HefError("hef_incidence_check", st, lib().hef_last_error().decode())
+            err.detail = detail.value
+            err.where = where.value
+            raise err
+
+    def export(self, stream=None):
+        dev = self.device
+        out = dict(perm=torch.empty(max(self.m, 1), dtype=torch.int32, device=dev)[:self.m],
+                   vptr=torch.empty(self.n + 1, dtype=torch.int32, device=dev),
+                   vedge=torch.empty(max(self.P, 1), dtype=torch.int32, device=dev)[:self.P],
+                   dc=torch.empty(self.n, dtype=torch.float64, device=dev),
+                   db=torch.empty(self.n, dtype=torch.float64, device=dev))
+        _check("hef_incidence_export",
+               lib().hef_incidence_export(self.handle, _ptr(out["perm"]), _ptr(out["vptr"]),
+                                          _ptr(out["vedge"]), _ptr(out["dc"]), _ptr(out["db"]),
+                                          _stream(stream)))
+        return out
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and _lib is not None:
+            _lib.hef_free_incidence(h)
+            self.handle = None
+
+
+def build_incidence(n, eptr, pins, w, clique_mode=HEF_CLIQUE_HYPEREDGE, stream=None):
+    return Incidence(n, eptr, pins, w, clique_mode, stream)
+
+
+def krylov_basis(inc, x0_clique, x0_star, k, dtype=torch.float64, V=None, workspace=None,
+                 stream=None):
+    """V (n x ldv, dtype): vertex rows of the k Krylov vectors of every chain
+    (hef_krylov_basis).  Returns V; its first K = 2kS columns are the basis."""
+    L = lib()
+    code = _dtype_code(dtype)
+    S = int(x0_clique.shape[1])
+    K = 2 * k * S
+    if V is None:
+        V = torch.empty(inc.n, padded_ld(K, code), dtype=_DTYPES[code], device=inc.device)
+    ws = L.hef_krylov_workspace_bytes(inc.handle, k, S, code)
+    if ws == 0:
+        raise HefError("hef_krylov_workspace_bytes", -6, "unsupported k/S/dtype")
+    if workspace is None:
+        workspace = _workspace(ws, inc.device)
+    _check("hef_krylov_basis",
+           L.hef_krylov_basis(inc.handle, k, S, code, _ptr(x0_clique), _ptr(x0_star), _ptr(V),
+                              V.stride(0), _ptr(workspace), workspace.numel(), _stream(stream)))
+    return V
+
+
+def orthonormalize(V, K, want_R=False, workspace=None, stream=None):
+    """In place: the first K columns of V become Q (hef_orthonormalize).
+    Returns (V, R or None, rank tensor)."""
+    L = lib()
+    code = _dtype_code(V.dtype)
+    n = V.shape[0]
+    ws = L.hef_orthonormalize_workspace_bytes(n, K, code)
+    if workspace is None:
+        workspace = _workspace(ws, V.device)
+    R = torch.empty(K, K, dtype=torch.float64, device=V.device) if want_R else None
+    rank = torch.empty(1, dtype=torch.int32, device=V.device)
+    _check("hef_orthonormalize",
+           L.hef_orthonormalize(n, K, code, _ptr(V), V.stride(0), _ptr(R), _ptr(rank),
+                                _ptr(workspace), workspace.numel(), _stream(stream)))
+    return V, R, rank
+
+
+def edge_resistance(inc, Q, K, reduce=HEF_REDUCE_MAX, routing=True, workspace=None, out=None,
+                    stream=None):
+    """Scores of every hyperedge (hef_edge_resistance); a dict of tensors."""
+    L = lib()
+    code = _dtype_code(Q.dtype)
+    dev = Q.device
+    m = inc.m
+    if out is None:
+        out = dict(R=torch.empty(max(m, 1), dtype=torch.float64, device=dev)[:m],
+                   QH=torch.empty(K, dtype=torch.float64, device=dev))
+        if routing:
+            for key in ("argvec", "pmax", "pmin"):
+                out[key] = torch.empty(max(m, 1), dtype=torch.int32, device=dev)[:m]
+    ws = L.hef_edge_resistance_workspace_bytes(inc.handle, K)
+    if workspace is None:
+        workspace = _workspace(ws, dev)
+    _check("hef_edge_resistance",
+           L.hef_edge_resistance(inc.handle, _ptr(Q), Q.stride(0), K, code, int(reduce),
+                                 _ptr(out["R"]), _ptr(out.get("QH")), _ptr(out.get("argvec")),
+                                 _ptr(out.get("pmax")), _ptr(out.get("pmin")), _ptr(workspace),
+                                 workspace.numel(), _stream(stream)))
+    return out
+
+
+def hyperedge_resistance(n, eptr, pins, w, x0_clique, x0_star, k, dtype=torch.float64,
+                         clique_mode=HEF_CLIQUE_HYPEREDGE, reduce=HEF_REDUCE_MAX, check=True):
+    """Algorithm 1 end to end on the GPU: incidence, Krylov basis, CholQR2,
+    scores.  All inputs are CUDA tensors."""
+    inc = build_incidence(n, eptr, pins, w, clique_mode)
+    S = int(x0_clique.shape[1])
+    K = 2 * k * S
+    V = krylov_basis(inc, x0_clique, x0_star, k, dtype)
+    Q, _, rank = orthonormalize(V, K)
+    out = edge_resistance(inc, Q, K, reduce)
+    if check:
+        inc.check()
+    out.update(Q=Q[:, :K], rank=rank, incidence=inc)
+    return out
+
+
+class Pipeline:
+    """Algorithm 1 on the GPU with every buffer allocated once (the first
+    run), so that repeated runs on hypergraphs of one shape allocate nothing:
+    hef_build_incidence -> hef_krylov_basis -> hef_orthonormalize ->
+    hef_edge_resistance, all on the current stream."""
+
+    def __init__(self, n, m, P, k, S, dtype=torch.float64, clique_mode=HEF_CLIQUE_HYPEREDGE,
+                 reduce=HEF_REDUCE_MAX, device=None, routing=True):
+        self.n, self.m, self.P, self.k, self.S = int(n), int(m), int(P), int(k), int(S)
+        self.K = 2 * self.k * self.S
+        self.code = _dtype_code(dtype)
+        self.clique_mode = int(clique_mode)
+        self.reduce = int(reduce)
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        L = lib()
+        dev = self.device
+        self.ws_inc = _workspace(L.hef_incidence_workspace_bytes(self.n, self.m, self.P), dev)
+        self.V = torch.empty(self.n, padded_ld(self.K, self.code), dtype=_DTYPES[self.code],
+                             device=dev)
+        self.ws_ortho = _workspace(L.hef_orthonormalize_workspace_bytes(self.n, self.K, self.code),
+                                   dev)
+        self.rank = torch.empty(1, dtype=torch.int32, device=dev)
+        self.out = dict(R=torch.empty(max(self.m, 1), dtype=torch.float64, device=dev)[:self.m],
+                        QH=torch.empty(self.K, dtype=torch.float64, device=dev))
+        if routing:
+            for key in ("argvec", "pmax", "pmin"):
+                self.out[key] = torch.empty(max(self.m, 1), dtype=torch.int32, device=dev)[:self.m]
+        self.ws_kry = None
+        self.ws_score = None
+        self.handle = None
+
+    def run(self, eptr, pins, w, x0_clique, x0_star, stream=None):
+        L = lib()
+        st = _stream(stream)
+        h = c_p()
+        _check("hef_build_incidence",
+               L.hef_build_incidence(self.n, self.m, self.P, _ptr(eptr), _ptr(pins), _ptr(w),
+                                     self.clique_mode, _ptr(self.ws_inc), self.ws_inc.numel(), st,
+                                     ctypes.byref(h)))
+        if self.handle is not None:
+            L.hef_free_incidence(self.handle)
+        self.handle = h
+        if self.ws_kry is None:
+            self.ws_kry = _workspace(L.hef_krylov_workspace_bytes(h, self.k, self.S, self.code),
+                                     self.device)
+            self.ws_score = _workspace(L.hef_edge_resistance_workspace_bytes(h, self.K),
+                                       self.device)
+        _check("hef_krylov_basis",
+               L.hef_krylov_basis(h, self.k, self.S, self.code, _ptr(x0_clique), _ptr(x0_star),
+                                  _ptr(self.V), self.V.stride(0), _ptr(self.ws_kry),
+                                  self.ws_kry.numel(), st))
+        _check("hef_orthonormalize",
+               L.hef_orthonormalize(self.n, self.K, self.code, _ptr(self.V), self.V.stride(0),
+                                    None, _ptr(self.rank), _ptr(self.ws_ortho),
+                                    self.ws_ortho.numel(), st))
+        o = self.out
+        _check("hef_edge_resistance",
+               L.hef_edge_resistance(h, _ptr(self.V), self.V.stride(0), self.K, self.code,
+                                     self.reduce, _ptr(o["R"]), _ptr(o["QH"]),
+                                     _ptr(o.get("argvec")), _ptr(o.get("pmax")),
+                                     _ptr(o.get("pmin")), _ptr(self.ws_score),
+                                     self.ws_score.numel(), st))
+        return o
+
+    def check(self, stream=None):
+        detail = ctypes.c_uint32(0)
+        where = c_i64(-1)
+        _check("hef_incidence_check",
+               lib().hef_incidence_check(self.handle, _stream(stream), ctypes.byref(detail),
+                                         ctypes.byref(where)))
+
+    def __del__(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.hef_free_incidence(self.handle)
+            self.handle = None

@@ -1,0 +1,595 @@
+// Incidence build: Algorithm 1 steps 1-2 (star and clique expansions of
+// Section III-A.4, kept implicit).  Validates H on the device, orders the
+// hyperedges for locality (ascending smallest pin, stable), builds the
+// vertex-major transpose with a stable radix sort (so every later sum runs in
+// a fixed order) and the per-edge / per-vertex scalars of both expansions.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "internal.h"
+
+namespace hef {
+
+namespace {
+
+constexpr int kItems = 8;                      // items per thread (scan/sort)
+constexpr int kTile = kThreads * kItems;        // 2048 items per tile
+
+// ----------------------------------------------------------------- scan
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int wsum[kThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int s = lane < kThreads / 32 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kThreads / 32) wsum[lane] = s;
+  }
+  __syncthreads();
+  int incl = x + (wid ? wsum[wid - 1] : 0);
+  *total = wsum[kThreads / 32 - 1];
+  __syncthreads();
+  return incl - v;
+}
+
+__global__ void k_scan_tiles(const int* __restrict__ in, int N, int* __restrict__ bsum) {
+  const long long base = (long long)blockIdx.x * kTile;
+  int s = 0;
+  for (int j = 0; j < kItems; ++j) {
+    long long i = base + (long long)threadIdx.x * kItems + j;
+    if (i < N) s += in[i];
+  }
+  int total;
+  block_exclusive_scan(s, &total);
+  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
+}
+
+// One CTA of 1024 threads scans the nb tile sums in place (exclusive) and
+// writes the grand total to bsum[nb].
+__global__ void k_scan_bsums(int* bsum, int nb) {
+  __shared__ int part[1024];
+  const int per = (nb + 1023) / 1024;
+  const int b0 = threadIdx.x * per;
+  int s = 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) s += bsum[b0 + i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    int y = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += y;
+    __syncthreads();
+  }
+  int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int i = 0; i < per; ++i)
+    if (b0 + i < nb) {
+      int t = bsum[b0 + i];
+      bsum[b0 + i] = run;
+      run += t;
+    }
+  if (threadIdx.x == 1023) bsum[nb] = part[1023];
+}
+
+__global__ void k_scan_apply(const int* __restrict__ in, int N, const int* __restrict__ bsum,
+                             int* __restrict__ out) {
+  const long long base = (long long)blockIdx.x * kTile + (long long)threadIdx.x * kItems;
+  int v[kItems];
+  int s = 0;
+  for (int j = 0; j < kItems; ++j) {
+    long long i = base + j;
+    v[j] = i < N ? in[i] : 0;
+    s += v[j];
+  }
+  int total;
+  int run = block_exclusive_scan(s, &total) + bsum[blockIdx.x];
+  for (int j = 0; j < kItems; ++j) {
+    long long i = base + j;
+    if (i < N) out[i] = run;
+    run += v[j];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[N] = bsum[gridDim.x];
+}
+
+inline int scan_tiles(long long N) { return (int)((N + kTile - 1) / kTile); }
+
+// out[0..N] = exclusive scan of in[0..N); out[N] = total.  bsum needs
+// scan_tiles(N) + 1 ints.  `in` and `out` may alias.
+hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, cudaStream_t st) {
+  int nb = scan_tiles(N);
+  if (nb == 0) {
+    HEF_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(int), st));
+    return HEF_OK;
+  }
+  HEF_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<nb, kThreads, 0, st>>>(in, (int)N, bsum));
+  HEF_LAUNCH("k_scan_bsums", st, k_scan_bsums<<<1, 1024, 0, st>>>(bsum, nb));
+  HEF_LAUNCH("k_scan_apply", st, k_scan_apply<<<nb, kThreads, 0, st>>>(in, (int)N, bsum, out));
+  HEF_CHECK_LAUNCH();
+  return HEF_OK;
+}
+
+// ----------------------------------------------------------------- stable LSD radix sort
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int N, int shift,
+                             int* __restrict__ counts, int ntiles) {
+  __shared__ int hist[256];
+  hist[threadIdx.x] = 0;
+  __syncthreads();
+  const long long base = (long long)blockIdx.x * kTile;
+  for (int j = 0; j < kItems; ++j) {
+    long long i = base + (long long)j * kThreads + threadIdx.x;
+    if (i < N) atomicAdd(&hist[(keys[i] >> shift) & 255u], 1);
+  }
+  __syncthreads();
+  counts[threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
+}
+
+// Stable scatter: items are visited in index order (striped over threads),
+// and each item's rank counts the earlier items of its tile with the same
+// digit (warp match + per-warp digit counts).
+__global__ void k_radix_scatter(const uint32_t* __restrict__ keys, const int32_t* __restrict__ vals,
+                                int N, int shift, const int* __restrict__ offs, int ntiles,
+                                uint32_t* __restrict__ okeys, int32_t* __restrict__ ovals) {
+  __shared__ int base[256];
+  __shared__ int wcnt[kThreads / 32][256];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  base[threadIdx.x] = offs[threadIdx.x * ntiles + blockIdx.x];
+  const long long tile0 = (long long)blockIdx.x * kTile;
+  for (int j = 0; j < kItems; ++j) {
+    for (int w = 0; w < kThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
+    __syncthreads();
+    long long i = tile0 + (long long)j * kThreads + threadIdx.x;
+    bool valid = i < N;
+    uint32_t key = valid ? keys[i] : 0u;
+    int digit = valid ? (int)((key >> shift) & 255u) : 256;
+    unsigned peers = __match_any_sync(0xffffffffu, digit);
+    int rank = __popc(peers & ((1u << lane) - 1u));
+    if (valid && rank == 0) wcnt[wid][digit] = __popc(peers);
+    __syncthreads();
+    // per digit: exclusive prefix over warps, then advance the running base
+    {
+      int d = threadIdx.x;
+      int run = base[d];
+      for (int w = 0; w < kThreads / 32; ++w) {
+        int c = wcnt[w][d];
+        wcnt[w][d] = run;
+        run += c;
+      }
+      base[d] = run;
+    }
+    __syncthreads();
+    if (valid) {
+      int pos = wcnt[wid][digit] + rank;
+      okeys[pos] = key;
+      ovals[pos] = vals[i];
+    }
+    __syncthreads();
+  }
+}
+
+struct SortBufs {
+  uint32_t* k_alt;
+  int32_t* v_alt;
+  int* counts;  // 256 * ntiles + 1
+  int* bsum;    // scan_tiles(256 * ntiles) + 1
+};
+
+inline int bits_for(long long maxkey) {
+  int b = 1;
+  while (b < 32 && (1ll << b) <= maxkey) ++b;
+  return b;
+}
+
+// Sorts (keys, vals) by key, stable; keys < 2^bits.  Result in keys/vals.
+hef_status radix_sort(uint32_t* keys, int32_t* vals, long long N, int bits, SortBufs b,
+                      cudaStream_t st) {
+  if (N <= 1) return HEF_OK;
+  const int ntiles = scan_tiles(N);
+  uint32_t* kin = keys;
+  int32_t* vin = vals;
+  uint32_t* kout = b.k_alt;
+  int32_t* vout = b.v_alt;
+  int passes = 0;
+  for (int shift = 0; shift < bits; shift += 8, ++passes) {
+    HEF_LAUNCH("k_radix_hist", st, k_radix_hist<<<ntiles, kThreads, 0, st>>>(kin, (int)N, shift, b.counts, ntiles));
+    HEF_CHECK_LAUNCH();
+    hef_status s = exclusive_scan(b.counts, b.counts, 256ll * ntiles, b.bsum, st);
+    if (s) return s;
+    HEF_LAUNCH("k_radix_scatter", st, k_radix_scatter<<<ntiles, kThreads, 0, st>>>(kin, vin, (int)N, shift, b.counts, ntiles, kout,
+                                                 vout));
+    HEF_CHECK_LAUNCH();
+    uint32_t* tk = kin; kin = kout; kout = tk;
+    int32_t* tv = vin; vin = vout; vout = tv;
+  }
+  if (passes & 1) {
+    HEF_CHECK_CUDA(cudaMemcpyAsync(keys, kin, N * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    HEF_CHECK_CUDA(cudaMemcpyAsync(vals, vin, N * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  }
+  return HEF_OK;
+}
+
+// ----------------------------------------------------------------- build kernels
+
+__device__ __forceinline__ void flag(unsigned int* status, unsigned bits, int e) {
+  atomicOr(&status[0], bits);
+  atomicMin(&status[1], (unsigned)e);
+}
+
+// One warp per hyperedge: offsets, weight, pin range, duplicate pins.
+__global__ void k_validate(int n, int m, long long P, const int64_t* __restrict__ eptr,
+                           const int32_t* __restrict__ pins, const double* __restrict__ w,
+                           unsigned int* status) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  if (warp == 0 && lane == 0) {
+    if (eptr[0] != 0 || eptr[m] != P) flag(status, HEF_BAD_EPTR, 0);
+  }
+  for (long long e = warp; e < m; e += nwarps) {
+    const long long a = eptr[e], b = eptr[e + 1];
+    if (a < 0 || b < a || b > P) {
+      if (lane == 0) flag(status, HEF_BAD_EPTR, (int)e);
+      continue;
+    }
+    const double we = w[e];
+    if (lane == 0 && !(we > 0.0 && we <= 1.7976931348623157e308)) flag(status, HEF_BAD_WEIGHT, (int)e);
+    const int k = (int)(b - a);
+    bool bad_pin = false, dup = false;
+    for (int i = lane; i < k; i += 32) {
+      const int p = pins[a + i];
+      if (p < 0 || p >= n) bad_pin = true;
+      for (int j = i + 1; j < k; ++j)
+        if (pins[a + j] == p) dup = true;
+    }
+    if (bad_pin) flag(status, HEF_BAD_PIN, (int)e);
+    if (dup) flag(status, HEF_DUP_PIN, (int)e);
+  }
+}
+
+// key = smallest pin (locality order), val = caller id.
+__global__ void k_edge_keys(int m, const int64_t* __restrict__ eptr, const int32_t* __restrict__ pins,
+                            const unsigned int* status, uint32_t* keys, int32_t* vals) {
+  if (status[0]) return;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
+       e += (long long)gridDim.x * blockDim.x) {
+    int mn = 0x7fffffff;
+    for (long long t = eptr[e]; t < eptr[e + 1]; ++t) mn = min(mn, (int)pins[t]);
+    keys[e] = (eptr[e + 1] > eptr[e]) ? (uint32_t)mn : 0u;
+    vals[e] = (int32_t)e;
+  }
+}
+
+__global__ void k_edge_sizes(int m, const int64_t* __restrict__ eptr, const int32_t* __restrict__ sched,
+                             const unsigned int* status, int* sizes) {
+  if (status[0]) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    int e = sched[i];
+    sizes[i] = (int)(eptr[e + 1] - eptr[e]);
+  }
+}
+
+// Per internal hyperedge: pins in internal order, weights of both expansions,
+// slot -> edge map, vertex incidence counts, and sum of w over |e| >= 2.
+__global__ void k_edge_fill(int m, int clique_mode, const int64_t* __restrict__ eptr,
+                            const int32_t* __restrict__ pins, const double* __restrict__ w,
+                            const int32_t* __restrict__ sched, const int32_t* __restrict__ ceptr,
+                            unsigned int* status, unsigned int* counter, int32_t* perm,
+                            int32_t* cpins, int32_t* slot_edge, double* ew, double* ewh, double* ez,
+                            int* deg, double* part, double* totals) {
+  if (status[0]) return;
+  double wsum = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int e = sched[i];
+    const long long a = eptr[e];
+    const int c0 = ceptr[i];
+    const int k = ceptr[i + 1] - c0;
+    perm[i] = e;
+    for (int t = 0; t < k; ++t) {
+      const int p = pins[a + t];
+      cpins[c0 + t] = p;
+      slot_edge[c0 + t] = (int32_t)i;
+      atomicAdd(&deg[p], 1);
+    }
+    const double we = w[e];
+    if (k >= 2) {
+      ew[i] = we;
+      ewh[i] = clique_mode == HEF_CLIQUE_PAPER ? we / (0.5 * (double)k * (double)(k - 1))
+                                               : we / (double)(k - 1);
+      ez[i] = we / (double)k;
+      wsum += we;
+    } else {
+      ew[i] = 0.0;
+      ewh[i] = 0.0;
+      ez[i] = 0.0;
+    }
+  }
+  double v[1] = {wsum};
+  block_partials<1>(v, part);
+  if (last_block_done(counter)) {
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) s += part[b];
+      totals[2] = s;
+    }
+  }
+}
+
+__global__ void k_csr_edges(long long P, const int32_t* __restrict__ vslot,
+                            const int32_t* __restrict__ slot_edge, const unsigned int* status,
+                            int32_t* vedge) {
+  if (status[0]) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x)
+    vedge[i] = slot_edge[vslot[i]];
+}
+
+__global__ void k_slot_keys(long long P, const int32_t* __restrict__ cpins, const unsigned int* status,
+                            uint32_t* keys, int32_t* vals) {
+  if (status[0]) return;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < P;
+       t += (long long)gridDim.x * blockDim.x) {
+    keys[t] = (uint32_t)cpins[t];
+    vals[t] = (int32_t)t;
+  }
+}
+
+// Vertex degrees of both expansions, in CSR (ascending hyperedge) order:
+// d_c(v) = sum_e ewh_e (|e|-1), d_b(v) = sum_e w_e/|e|.
+__global__ void k_node_scalars(int n, const int32_t* __restrict__ vptr, const int32_t* __restrict__ vedge,
+                               const int32_t* __restrict__ ceptr, const double* __restrict__ ewh,
+                               const double* __restrict__ ez, unsigned int* status,
+                               unsigned int* counter, double* dc, double* db, double* inv_dc,
+                               double* inv_db, double* part, double* totals) {
+  if (status[0]) return;
+  double sc = 0.0, sb = 0.0;
+  for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
+       v += (long long)gridDim.x * blockDim.x) {
+    double c = 0.0, b = 0.0;
+    for (int t = vptr[v]; t < vptr[v + 1]; ++t) {
+      const int e = vedge[t];
+      const int k = ceptr[e + 1] - ceptr[e];
+      c += ewh[e] * (double)(k - 1);
+      b += ez[e];
+    }
+    dc[v] = c;
+    db[v] = b;
+    inv_dc[v] = c > 0.0 ? 1.0 / c : 0.0;
+    inv_db[v] = b > 0.0 ? 1.0 / b : 0.0;
+    sc += c;
+    sb += b;
+  }
+  double v2[2] = {sc, sb};
+  block_partials<2>(v2, part);
+  if (last_block_done(counter)) {
+    if (threadIdx.x < 2) {
+      double s = 0.0;
+      for (unsigned b = 0; b < gridDim.x; ++b) s += part[(size_t)b * 2 + threadIdx.x];
+      totals[threadIdx.x] = s;
+    }
+  }
+}
+
+__global__ void k_export_vedge(long long P, const int32_t* __restrict__ vedge,
+                               const int32_t* __restrict__ perm, int32_t* out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = perm[vedge[i]];
+}
+
+// ----------------------------------------------------------------- workspace layout
+
+struct IncLayout {
+  hef_incidence h;
+  uint32_t* keys;
+  int32_t* vals;
+  SortBufs sb;
+  int* tmp;       // max(m, n) + 1 ints (sizes / degree counts, scanned in place)
+  int* scan_bsum;
+  double* part;
+};
+
+size_t carve_incidence(void* base, long long n, long long m, long long P, IncLayout* L) {
+  Carver c(base);
+  const long long NS = (m > P ? m : P);
+  const long long NT = (m > n ? m : n) + 1;
+  const int ntiles = scan_tiles(NS > 0 ? NS : 1);
+  L->h.status = c.take<unsigned int>(64);
+  L->h.counter = L->h.status + 32;
+  L->h.perm = c.take<int32_t>(m > 0 ? m : 1);
+  L->h.ceptr = c.take<int32_t>(m + 1);
+  L->h.cpins = c.take<int32_t>(P > 0 ? P : 1);
+  L->h.slot_edge = c.take<int32_t>(P > 0 ? P : 1);
+  L->h.ew = c.take<double>(m > 0 ? m : 1);
+  L->h.ewh = c.take<double>(m > 0 ? m : 1);
+  L->h.ez = c.take<double>(m > 0 ? m : 1);
+  L->h.vptr = c.take<int32_t>(n + 1);
+  L->h.vedge = c.take<int32_t>(P > 0 ? P : 1);
+  L->h.vslot = c.take<int32_t>(P > 0 ? P : 1);
+  L->h.dc = c.take<double>(n > 0 ? n : 1);
+  L->h.db = c.take<double>(n > 0 ? n : 1);
+  L->h.inv_dc = c.take<double>(n > 0 ? n : 1);
+  L->h.inv_db = c.take<double>(n > 0 ? n : 1);
+  L->h.totals = c.take<double>(8);
+  L->keys = c.take<uint32_t>(NS > 0 ? NS : 1);
+  L->vals = c.take<int32_t>(NS > 0 ? NS : 1);
+  L->sb.k_alt = c.take<uint32_t>(NS > 0 ? NS : 1);
+  L->sb.v_alt = c.take<int32_t>(NS > 0 ? NS : 1);
+  L->sb.counts = c.take<int>(256ll * ntiles + 1);
+  L->sb.bsum = c.take<int>(scan_tiles(256ll * ntiles) + 1);
+  L->tmp = c.take<int>(NT);
+  L->scan_bsum = c.take<int>(scan_tiles(NT) + 1);
+  L->part = c.take<double>(2ll * 8 * 1024);
+  return c.bytes();
+}
+
+}  // namespace
+
+}  // namespace hef
+
+using namespace hef;
+
+extern "C" size_t hef_incidence_workspace_bytes(int64_t n, int64_t m, int64_t P) {
+  if (n < 0 || m < 0 || P < 0) return 0;
+  IncLayout L;
+  return carve_incidence(nullptr, n, m, P, &L);
+}
+
+extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const int64_t* eptr,
+                                          const int32_t* pins, const double* w,
+                                          int32_t clique_mode, void* workspace,
+                                          size_t workspace_bytes, void* stream,
+                                          hef_incidence** out) {
+  if (!out) return set_error(HEF_ERR_INVALID_ARG, "hef_build_incidence: out is NULL");
+  *out = nullptr;
+  if (n < 1 || m < 0 || P < 0)
+    return set_error(HEF_ERR_INVALID_ARG, "hef_build_incidence: need n >= 1, m >= 0, P >= 0");
+  if (n >= (1ll << 31) - 1 || m >= (1ll << 31) - 1 || P >= (1ll << 31) - 1)
+    return set_error(HEF_ERR_UNSUPPORTED, "hef_build_incidence: n, m and P must be < 2^31 - 1");
+  if (!eptr || (P > 0 && !pins) || (m > 0 && !w))
+    return set_error(HEF_ERR_INVALID_ARG, "hef_build_incidence: NULL input array");
+  if (clique_mode != HEF_CLIQUE_HYPEREDGE && clique_mode != HEF_CLIQUE_PAPER)
+    return set_error(HEF_ERR_INVALID_ARG, "hef_build_incidence: unknown clique_mode %d", clique_mode);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255))
+    return set_error(HEF_ERR_WORKSPACE, "hef_build_incidence: workspace NULL or not 256-byte aligned");
+  IncLayout L;
+  size_t need = carve_incidence(workspace, n, m, P, &L);
+  if (workspace_bytes < need)
+    return set_error(HEF_ERR_WORKSPACE, "hef_build_incidence: workspace %zu bytes < %zu needed",
+                     workspace_bytes, need);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  hef_incidence* h = static_cast<hef_incidence*>(malloc(sizeof(hef_incidence)));
+  if (!h) return set_error(HEF_ERR_INVALID_ARG, "hef_build_incidence: host malloc failed");
+  *h = L.h;
+  h->n = n;
+  h->m = m;
+  h->P = P;
+  h->clique_mode = clique_mode;
+
+  auto fail = [&](hef_status s) {
+    free(h);
+    return s;
+  };
+#define HEF_TRY(x)                 \
+  do {                             \
+    hef_status s_ = (x);           \
+    if (s_ != HEF_OK) return fail(s_); \
+  } while (0)
+#define HEF_TRY_CUDA(call)                                                              \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(set_error(HEF_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_))); \
+  } while (0)
+
+  HEF_TRY_CUDA(cudaMemsetAsync(h->status, 0, 64 * sizeof(unsigned int), st));
+  HEF_TRY_CUDA(cudaMemsetAsync(h->status + 1, 0xFF, sizeof(unsigned int), st));
+  HEF_TRY_CUDA(cudaMemsetAsync(L.tmp, 0, sizeof(int) * ((m > n ? m : n) + 1), st));
+
+  // 1. validation (one warp per hyperedge)
+  {
+    long long warps = m > 0 ? m : 1;
+    int grid = stride_grid(warps * 32, 8);
+    HEF_LAUNCH("k_validate", st, k_validate<<<grid, kThreads, 0, st>>>((int)n, (int)m, P, eptr, pins, w, h->status));
+    HEF_TRY_CUDA(cudaGetLastError());
+  }
+  // 2. locality schedule of hyperedges: stable sort by smallest pin
+  if (m > 0) {
+    int grid = stride_grid(m);
+    HEF_LAUNCH("k_edge_keys", st, k_edge_keys<<<grid, kThreads, 0, st>>>((int)m, eptr, pins, h->status, L.keys, L.vals));
+    HEF_TRY_CUDA(cudaGetLastError());
+    HEF_TRY(radix_sort(L.keys, L.vals, m, bits_for(n), L.sb, st));
+    // internal CSC offsets
+    HEF_LAUNCH("k_edge_sizes", st, k_edge_sizes<<<grid, kThreads, 0, st>>>((int)m, eptr, L.vals, h->status, L.tmp));
+    HEF_TRY_CUDA(cudaGetLastError());
+    HEF_TRY(exclusive_scan(L.tmp, h->ceptr, m, L.scan_bsum, st));
+    HEF_TRY_CUDA(cudaMemsetAsync(L.tmp, 0, sizeof(int) * (n + 1), st));
+    HEF_LAUNCH("k_edge_fill", st, k_edge_fill<<<grid, kThreads, 0, st>>>((int)m, clique_mode, eptr, pins, w, L.vals, h->ceptr,
+                                           h->status, h->counter, h->perm, h->cpins, h->slot_edge,
+                                           h->ew, h->ewh, h->ez, L.tmp, L.part, h->totals));
+    HEF_TRY_CUDA(cudaGetLastError());
+  } else {
+    HEF_TRY_CUDA(cudaMemsetAsync(h->ceptr, 0, sizeof(int32_t), st));
+    HEF_TRY_CUDA(cudaMemsetAsync(h->totals, 0, 8 * sizeof(double), st));
+  }
+  // 3. vertex-major transpose: stable sort of CSC slots by vertex
+  HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, st));
+  if (P > 0) {
+    int grid = stride_grid(P);
+    HEF_LAUNCH("k_slot_keys", st, k_slot_keys<<<grid, kThreads, 0, st>>>(P, h->cpins, h->status, L.keys, h->vslot));
+    HEF_TRY_CUDA(cudaGetLastError());
+    HEF_TRY(radix_sort(L.keys, h->vslot, P, bits_for(n), L.sb, st));
+    HEF_LAUNCH("k_csr_edges", st, k_csr_edges<<<grid, kThreads, 0, st>>>(P, h->vslot, h->slot_edge, h->status, h->vedge));
+    HEF_TRY_CUDA(cudaGetLastError());
+  }
+  // 4. vertex degrees of both expansions and their totals
+  {
+    int grid = stride_grid(n);
+    HEF_LAUNCH("k_node_scalars", st, k_node_scalars<<<grid, kThreads, 0, st>>>((int)n, h->vptr, h->vedge, h->ceptr, h->ewh, h->ez,
+                                              h->status, h->counter, h->dc, h->db, h->inv_dc,
+                                              h->inv_db, L.part, h->totals));
+    HEF_TRY_CUDA(cudaGetLastError());
+  }
+#undef HEF_TRY
+#undef HEF_TRY_CUDA
+  *out = h;
+  return HEF_OK;
+}
+
+extern "C" hef_status hef_incidence_check(const hef_incidence* inc, void* stream, uint32_t* detail,
+                                          int64_t* where) {
+  if (!inc) return set_error(HEF_ERR_INVALID_ARG, "hef_incidence_check: NULL handle");
+  unsigned int st_host[2] = {0, 0};
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HEF_CHECK_CUDA(cudaMemcpyAsync(st_host, inc->status, sizeof(st_host), cudaMemcpyDeviceToHost, st));
+  HEF_CHECK_CUDA(cudaStreamSynchronize(st));
+  if (detail) *detail = st_host[0];
+  if (where) *where = st_host[0] ? (int64_t)st_host[1] : -1;
+  if (st_host[0])
+    return set_error(HEF_ERR_INVALID_INPUT,
+                     "hypergraph rejected by device validation (bits 0x%x, hyperedge %u)",
+                     st_host[0], st_host[1]);
+  return HEF_OK;
+}
+
+extern "C" hef_status hef_incidence_sizes(const hef_incidence* inc, int64_t* n, int64_t* m,
+                                          int64_t* P) {
+  if (!inc) return set_error(HEF_ERR_INVALID_ARG, "hef_incidence_sizes: NULL handle");
+  if (n) *n = inc->n;
+  if (m) *m = inc->m;
+  if (P) *P = inc->P;
+  return HEF_OK;
+}
+
+extern "C" void hef_free_incidence(hef_incidence* inc) { free(inc); }
+
+extern "C" hef_status hef_incidence_export(const hef_incidence* inc, int32_t* perm, int32_t* vptr,
+                                           int32_t* vedge, double* dc, double* db, void* stream) {
+  if (!inc) return set_error(HEF_ERR_INVALID_ARG, "hef_incidence_export: NULL handle");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (perm && inc->m > 0)
+    HEF_CHECK_CUDA(cudaMemcpyAsync(perm, inc->perm, inc->m * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  if (vptr)
+    HEF_CHECK_CUDA(cudaMemcpyAsync(vptr, inc->vptr, (inc->n + 1) * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  if (vedge && inc->P > 0) {
+    HEF_LAUNCH("k_export_vedge", st, k_export_vedge<<<stride_grid(inc->P), kThreads, 0, st>>>(inc->P, inc->vedge, inc->perm, vedge));
+    HEF_CHECK_LAUNCH();
+  }
+  if (dc) HEF_CHECK_CUDA(cudaMemcpyAsync(dc, inc->dc, inc->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (db) HEF_CHECK_CUDA(cudaMemcpyAsync(db, inc->db, inc->n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return HEF_OK;
+}

@@ -1,0 +1,79 @@
+// Internal host-side declarations shared by the hef translation units.
+#pragma once
+
+#include "common.cuh"
+
+// Host handle of a built incidence.  Every pointer is device memory inside
+// the caller's incidence workspace.  "Internal" hyperedge order is the
+// locality schedule (ascending smallest pin, ties by caller id); perm maps it
+// back to the caller's ids.
+struct hef_incidence {
+  int64_t n = 0, m = 0, P = 0;
+  int32_t clique_mode = 0;
+  unsigned int* status = nullptr;   // [0] error bits, [1] first bad edge
+  unsigned int* counter = nullptr;  // last-CTA counter for build kernels
+  int32_t* perm = nullptr;          // m: internal -> caller hyperedge id
+  int32_t* ceptr = nullptr;         // m+1: CSC offsets (internal order)
+  int32_t* cpins = nullptr;         // P: pins (internal order)
+  int32_t* slot_edge = nullptr;     // P: internal hyperedge of each CSC slot
+  double* ew = nullptr;             // m: w_e, 0 when |e| < 2
+  double* ewh = nullptr;            // m: clique pair weight, 0 when |e| < 2
+  double* ez = nullptr;             // m: star weight w_e/|e|, 0 when |e| < 2
+  int32_t* vptr = nullptr;          // n+1: vertex-major offsets
+  int32_t* vedge = nullptr;         // P: internal hyperedge of each entry
+  int32_t* vslot = nullptr;         // P: CSC slot of each entry
+  double* dc = nullptr;             // n: clique degree
+  double* db = nullptr;             // n: star degree of vertices
+  double* inv_dc = nullptr;         // n: 1/dc (0 for isolated)
+  double* inv_db = nullptr;         // n: 1/db (0 for isolated)
+  double* totals = nullptr;         // [0] sum dc, [1] sum db, [2] sum w (|e|>=2)
+};
+
+namespace hef {
+
+// Kernel-side view of the incidence (passed by value to kernels).
+struct IncView {
+  int n, m, P;
+  const unsigned int* status;
+  const int32_t* perm;
+  const int32_t* ceptr;
+  const int32_t* cpins;
+  const double* ew;
+  const double* ewh;
+  const double* ez;
+  const int32_t* vptr;
+  const int32_t* vedge;
+  const int32_t* vslot;
+  const double* dc;
+  const double* db;
+  const double* inv_dc;
+  const double* inv_db;
+  const double* totals;
+};
+
+inline IncView view(const hef_incidence* h) {
+  IncView v;
+  v.n = (int)h->n;
+  v.m = (int)h->m;
+  v.P = (int)h->P;
+  v.status = h->status;
+  v.perm = h->perm;
+  v.ceptr = h->ceptr;
+  v.cpins = h->cpins;
+  v.ew = h->ew;
+  v.ewh = h->ewh;
+  v.ez = h->ez;
+  v.vptr = h->vptr;
+  v.vedge = h->vedge;
+  v.vslot = h->vslot;
+  v.dc = h->dc;
+  v.db = h->db;
+  v.inv_dc = h->inv_dc;
+  v.inv_db = h->inv_db;
+  v.totals = h->totals;
+  return v;
+}
+
+hef_status check_stream_ptrs(const void* p, const char* what);
+
+}  // namespace hef
