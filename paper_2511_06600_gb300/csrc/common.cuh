@@ -122,10 +122,8 @@ __device__ __forceinline__ bool last_block_done(unsigned int* counter) {
   return is_last;
 }
 
-// Deterministic reduction of `nq` quantities held per thread into per-CTA
-// partials part[blockIdx.x * nq + q].  Thread t contributes v[q] to slot
-// (q, t mod S) when `S` > 0 (strided layouts: nq counts slots per s) --
-// here the simple variant: every thread contributes to all nq slots.
+// Deterministic reduction of NQ per-thread quantities into per-CTA partials
+// part[blockIdx.x * NQ + q] (warp shuffles, then warps in a fixed order).
 template <int NQ>
 __device__ __forceinline__ void block_partials(const double (&v)[NQ],
                                                double* part) {
@@ -141,6 +139,30 @@ __device__ __forceinline__ void block_partials(const double (&v)[NQ],
     double s = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[threadIdx.x][w];
     part[(size_t)blockIdx.x * NQ + threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// In one CTA: out[slot] = sum over b < nblk of part[b * nslot + slot], for
+// every slot < nslot.  One warp per slot, lanes stride over the partials, then
+// a fixed shuffle tree: the result does not depend on scheduling.  Ends with
+// __syncthreads (out may be shared memory).
+__device__ __forceinline__ void reduce_slots(const double* __restrict__ part, int nblk,
+                                             int nslot, double* out) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nw = blockDim.x >> 5;
+  for (int slot = wid; slot < nslot; slot += nw) {
+    double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nblk; b += 128) {
+      a0 += part[(size_t)b * nslot + slot];
+      a1 += part[(size_t)(b + 32) * nslot + slot];
+      a2 += part[(size_t)(b + 64) * nslot + slot];
+      a3 += part[(size_t)(b + 96) * nslot + slot];
+    }
+    for (; b < nblk; b += 32) a0 += part[(size_t)b * nslot + slot];
+    double acc = warp_sum((a0 + a1) + (a2 + a3));
+    if (lane == 0) out[slot] = acc;
   }
   __syncthreads();
 }

@@ -321,11 +321,9 @@ __global__ void k_edge_fill(int m, int clique_mode, const int64_t* __restrict__ 
   double v[1] = {wsum};
   block_partials<1>(v, part);
   if (last_block_done(counter)) {
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) s += part[b];
-      totals[2] = s;
-    }
+    __shared__ double tot[1];
+    reduce_slots(part, gridDim.x, 1, tot);
+    if (threadIdx.x == 0) totals[2] = tot[0];
   }
 }
 
@@ -376,11 +374,9 @@ __global__ void k_node_scalars(int n, const int32_t* __restrict__ vptr, const in
   double v2[2] = {sc, sb};
   block_partials<2>(v2, part);
   if (last_block_done(counter)) {
-    if (threadIdx.x < 2) {
-      double s = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) s += part[(size_t)b * 2 + threadIdx.x];
-      totals[threadIdx.x] = s;
-    }
+    __shared__ double tot[2];
+    reduce_slots(part, gridDim.x, 2, tot);
+    if (threadIdx.x < 2) totals[threadIdx.x] = tot[threadIdx.x];
   }
 }
 

@@ -71,13 +71,6 @@ __device__ __forceinline__ void partials_per_s(const A (&v)[NQ], int S, double* 
   __syncthreads();
 }
 
-// Fixed-order sum over CTAs of part[b][slot] for slot in [0, nslot).
-__device__ __forceinline__ double sum_parts(const double* part, int nblk, int nslot, int slot) {
-  double acc = 0.0;
-  for (int b = 0; b < nblk; ++b) acc += part[(size_t)b * nslot + slot];
-  return acc;
-}
-
 // ----------------------------------------------------------------- start vectors
 
 // D-weighted dots of the raw starts with the trivial vectors.
@@ -107,16 +100,15 @@ __global__ void k_start_dots(IncView g, KView<T> kv, const double* __restrict__ 
   }
   partials_per_s<3, double>(acc, S, kv.part_s);
   if (last_block_done(kv.counter)) {
+    __shared__ double tot[3 * kMaxS];
+    reduce_slots(kv.part_s, gridDim.x, 3 * S, tot);
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
-      const double tc = sum_parts(kv.part_s, gridDim.x, 3 * S, s * 3 + 0);
-      const double tv = sum_parts(kv.part_s, gridDim.x, 3 * S, s * 3 + 1);
-      const double te = sum_parts(kv.part_s, gridDim.x, 3 * S, s * 3 + 2);
       double* cc = kv.coef + (size_t)(0 * 2 * S + s) * 4;
       double* cb = kv.coef + (size_t)(0 * 2 * S + S + s) * 4;
-      cc[0] = g.totals[0] > 0 ? tc / g.totals[0] : 0.0;
+      cc[0] = g.totals[0] > 0 ? tot[s * 3 + 0] / g.totals[0] : 0.0;
       cc[1] = 0.0;
-      cb[0] = g.totals[1] > 0 ? tv / g.totals[1] : 0.0;
-      cb[1] = g.totals[2] > 0 ? te / g.totals[2] : 0.0;
+      cb[0] = g.totals[1] > 0 ? tot[s * 3 + 1] / g.totals[1] : 0.0;
+      cb[1] = g.totals[2] > 0 ? tot[s * 3 + 2] / g.totals[2] : 0.0;
     }
   }
 }
@@ -157,9 +149,11 @@ __global__ void k_start_write(IncView g, KView<T> kv, const double* __restrict__
   }
   partials_per_s<2, double>(acc, S, kv.part_s);
   if (last_block_done(kv.counter)) {
+    __shared__ double tot[2 * kMaxS];
+    reduce_slots(kv.part_s, gridDim.x, 2 * S, tot);
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
       const int op = c / S, s = c % S;
-      const double nu2 = sum_parts(kv.part_s, gridDim.x, 2 * S, s * 2 + op);
+      const double nu2 = tot[s * 2 + op];
       kv.inv_nu[c] = nu2 > 0.0 ? 1.0 / sqrt(nu2) : 0.0;
     }
   }
@@ -185,7 +179,18 @@ __global__ void k_edge_pass(IncView g, KView<T> kv, int j) {
     const int i = (int)(idx >> lgS), s = (int)(idx & (S - 1));
     const int a = g.ceptr[i], b = g.ceptr[i + 1];
     T sc = 0, sb = 0;
-    for (int t = a; t < b; ++t) {
+    int t = a;
+    for (; t + 4 <= b; t += 4) {  // four independent gathers in flight
+      const long long p0 = g.cpins[t], p1 = g.cpins[t + 1], p2 = g.cpins[t + 2],
+                      p3 = g.cpins[t + 3];
+      const T c0 = curc[(p0 << lgS) + s], c1 = curc[(p1 << lgS) + s];
+      const T c2 = curc[(p2 << lgS) + s], c3 = curc[(p3 << lgS) + s];
+      const T b0 = curb[(p0 << lgS) + s], b1 = curb[(p1 << lgS) + s];
+      const T b2 = curb[(p2 << lgS) + s], b3 = curb[(p3 << lgS) + s];
+      sc += (c0 + c1) + (c2 + c3);
+      sb += (b0 + b1) + (b2 + b3);
+    }
+    for (; t < b; ++t) {
       const long long p = g.cpins[t];
       sc += curc[(p << lgS) + s];
       sb += curb[(p << lgS) + s];
@@ -262,28 +267,23 @@ __global__ void k_node_pass(IncView g, KView<T> kv, int j, int grid_e, T* __rest
   }
   partials_per_s<8, T>(acc, S, kv.part_n);
   if (last_block_done(kv.counter)) {
+    __shared__ double tn[8 * kMaxS];
+    __shared__ double te[4 * kMaxS];
+    reduce_slots(kv.part_n, gridDim.x, 8 * S, tn);
+    reduce_slots(kv.part_e, grid_e, 4 * S, te);
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
       const int op = c / S, s = c % S;
       double* cf = kv.coef + ((size_t)j * 2 * S + c) * 4;
       if (op == 0) {
-        const double dt = sum_parts(kv.part_n, gridDim.x, 8 * S, s * 8 + 0);
-        const double dx = sum_parts(kv.part_n, gridDim.x, 8 * S, s * 8 + 1);
-        const double dp = sum_parts(kv.part_n, gridDim.x, 8 * S, s * 8 + 2);
-        cf[0] = g.totals[0] > 0 ? dt / g.totals[0] : 0.0;
+        cf[0] = g.totals[0] > 0 ? tn[s * 8 + 0] / g.totals[0] : 0.0;
         cf[1] = 0.0;
-        cf[2] = j >= 2 ? dx : 0.0;
-        cf[3] = j >= 3 ? dp : 0.0;
+        cf[2] = j >= 2 ? tn[s * 8 + 1] : 0.0;
+        cf[3] = j >= 3 ? tn[s * 8 + 2] : 0.0;
       } else {
-        const double dtv = sum_parts(kv.part_n, gridDim.x, 8 * S, s * 8 + 4);
-        const double dx = sum_parts(kv.part_n, gridDim.x, 8 * S, s * 8 + 5) +
-                          sum_parts(kv.part_e, grid_e, 4 * S, s * 4 + 1);
-        const double dp = sum_parts(kv.part_n, gridDim.x, 8 * S, s * 8 + 6) +
-                          sum_parts(kv.part_e, grid_e, 4 * S, s * 4 + 2);
-        const double dte = sum_parts(kv.part_e, grid_e, 4 * S, s * 4 + 0);
-        cf[0] = g.totals[1] > 0 ? dtv / g.totals[1] : 0.0;
-        cf[1] = g.totals[2] > 0 ? dte / g.totals[2] : 0.0;
-        cf[2] = j >= 2 ? dx : 0.0;
-        cf[3] = j >= 3 ? dp : 0.0;
+        cf[0] = g.totals[1] > 0 ? tn[s * 8 + 4] / g.totals[1] : 0.0;
+        cf[1] = g.totals[2] > 0 ? te[s * 4 + 0] / g.totals[2] : 0.0;
+        cf[2] = j >= 2 ? tn[s * 8 + 5] + te[s * 4 + 1] : 0.0;
+        cf[3] = j >= 3 ? tn[s * 8 + 6] + te[s * 4 + 2] : 0.0;
       }
     }
   }
@@ -338,9 +338,11 @@ __global__ void k_update(IncView g, KView<T> kv, int j) {
   }
   partials_per_s<2, T>(acc, S, kv.part_u);
   if (last_block_done(kv.counter)) {
+    __shared__ double tot[2 * kMaxS];
+    reduce_slots(kv.part_u, gridDim.x, 2 * S, tot);
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
       const int op = c / S, s = c % S;
-      const double nu2 = sum_parts(kv.part_u, gridDim.x, 2 * S, s * 2 + op);
+      const double nu2 = tot[s * 2 + op];
       const bool alive = nu0[c] > 0.0 && nu2 > kv.tol * kv.tol;
       kv.inv_nu[(size_t)j * 2 * S + c] = alive ? 1.0 / sqrt(nu2) : 0.0;
     }

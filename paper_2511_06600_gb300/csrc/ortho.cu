@@ -1,207 +1,284 @@
 // Orthonormalisation: Algorithm 1 step 4 ("Gram-Schmidt"), done as CholQR2
-// on the mean-free basis: G = V^T V - c c^T / n (c = V^T 1), R1 = chol(G)
-// in FP64, Q1 = (V - 1 mu^T) R1^-1; the same again on Q1 (which removes the
-// rounding left by the first pass); Q = Q1 R2^-1, R = R2 R1.  Q spans the
-// same nested column spaces as Gram-Schmidt in column order would, with a
-// positive diagonal, so it equals the Gram-Schmidt Q up to rounding.
+// on the mean-free basis.  Pass 1: G = V^T V - c c^T / n (c = V^T 1),
+// G = R1^T R1, Q1 = (V - 1 mu^T) R1^-1.  Pass 2: the same on Q1, whose Gram
+// matrix is I + E with E at rounding level, so R2 = I + X with X the
+// first-order Cholesky correction of E (FP64), Q = Q1 R2^-1, R = R2 R1.  R1
+// and R2 are upper triangular with positive diagonals, so Q spans the same
+// nested column spaces as V: it is the Gram-Schmidt Q up to rounding.
 //
-// Kernels: k_gram (tiled, split over rows, per-chunk partials), k_gram_reduce
-// (fixed-order sum), k_chol (one CTA, FP64: pivoted-out rank-deficient
-// columns, triangular inverse), k_apply (in place, row blocks in shared
-// memory, column blocks last to first so each column is overwritten only
-// after every later column has used it).
+// Kernels
+//  k_gram         partial Gram of a row chunk: thread = 8x8 block of the
+//                 upper triangle, FP32 (or FP64) accumulation per chunk, FP64
+//                 partials; k_gram_reduce sums chunks in a fixed order.
+//  k_chol_aug     one CTA: Gauss elimination of [G | I] -> [R | R^-T] (the
+//                 inverse comes out of the same K pivot steps).  FP32 in
+//                 shared memory for the FP32 form's first pass; FP64 (global
+//                 scratch) as the exact path: the FP64 form's first pass, and
+//                 the fallback when a fast pass reports near rank deficiency.
+//  k_chol_series  second pass: R2 = I + X1, R2^-1 = I - X1 (X1 = upper part of
+//                 E with halved diagonal); exact to O(|E|^2); falls back to the
+//                 exact path when |E| is not small.
+//  k_apply        in place Q = (V - 1 mu^T) Rinv: row blocks in shared memory,
+//                 column blocks last to first (a column is overwritten only
+//                 after every later column has used it), 4 x 8 outputs per
+//                 thread.
 #include "internal.h"
 
 namespace hef {
 
 namespace {
 
-constexpr int kTileG = 32;  // Gram output tile
-constexpr int kPanel = 32;  // rows per Gram panel
+constexpr int kGB = 8;       // Gram: rows/cols of the block a thread owns
+constexpr int kPR = 32;      // Gram: rows per shared-memory panel
+constexpr int kPairs = 256;  // Gram: block pairs (threads) per CTA
+constexpr int kACB = 64;     // apply: output columns per block
+
+inline int round8(int K) { return (K + 7) & ~7; }
 
 template <typename T>
-struct Acc;  // per-panel accumulator type of the Gram kernel
+struct Acc;
 template <>
 struct Acc<double> {
   using type = double;
-  static constexpr int flush = 1;  // panels between flushes to the FP64 sum
 };
 template <>
 struct Acc<float> {
   using type = float;
-  static constexpr int flush = 8;
 };
 
-// Partial Gram tile (bi, bj) over one chunk of rows, plus column sums when
-// bi == bj.  Thread (ty, tx) of a 16 x 16 layout owns a 2 x 2 output block.
-template <typename T>
-__global__ void __launch_bounds__(256) k_gram(const T* __restrict__ V, long long ldv, int n, int K,
-                                              int nb, int rows_per_chunk, double* part,
-                                              double* colpart) {
-  using A = typename Acc<T>::type;
-  __shared__ T As[kPanel][kTileG + 1];
-  __shared__ T Bs[kPanel][kTileG + 1];
-  // tile pair index -> (bi, bj), bi <= bj
-  int t = blockIdx.x, bi = 0;
-  while (t >= nb - bi) {
-    t -= nb - bi;
-    ++bi;
+// Block pair index -> (bi, bj), bi <= bj, row-major over the upper triangle.
+__device__ __forceinline__ void pair_of(int p, int nb, int& bi, int& bj) {
+  int i = 0;
+  while (p >= nb - i) {
+    p -= nb - i;
+    ++i;
   }
-  const int bj = bi + t;
-  const int chunk = blockIdx.y;
-  const long long r0 = (long long)chunk * rows_per_chunk;
-  const long long r1 = min((long long)n, r0 + rows_per_chunk);
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-  const int ci = bi * kTileG, cj = bj * kTileG;
-  double acc[2][2] = {{0, 0}, {0, 0}};
-  double csum = 0.0;
-  A pacc[2][2] = {{0, 0}, {0, 0}};
-  A pcs = 0;
-  int npanel = 0;
-  for (long long r = r0; r < r1; r += kPanel) {
-    for (int e = threadIdx.x; e < kPanel * kTileG; e += blockDim.x) {
-      const int rr = e / kTileG, cc = e % kTileG;
-      const long long row = r + rr;
-      const bool ok = row < r1;
-      As[rr][cc] = (ok && ci + cc < K) ? V[row * ldv + ci + cc] : (T)0;
-      Bs[rr][cc] = (ok && cj + cc < K) ? V[row * ldv + cj + cc] : (T)0;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int rr = 0; rr < kPanel; ++rr) {
-      const A a0 = As[rr][ty * 2], a1 = As[rr][ty * 2 + 1];
-      const A b0 = Bs[rr][tx * 2], b1 = Bs[rr][tx * 2 + 1];
-      pacc[0][0] += a0 * b0;
-      pacc[0][1] += a0 * b1;
-      pacc[1][0] += a1 * b0;
-      pacc[1][1] += a1 * b1;
-    }
-    if (bi == bj && threadIdx.x < kTileG) {
-      for (int rr = 0; rr < kPanel; ++rr) pcs += As[rr][threadIdx.x];
-    }
-    __syncthreads();
-    if (++npanel == Acc<T>::flush) {
-      npanel = 0;
-      for (int a = 0; a < 2; ++a)
-        for (int b = 0; b < 2; ++b) {
-          acc[a][b] += (double)pacc[a][b];
-          pacc[a][b] = 0;
-        }
-      csum += (double)pcs;
-      pcs = 0;
-    }
-  }
-  for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) acc[a][b] += (double)pacc[a][b];
-  csum += (double)pcs;
-  double* P = part + (size_t)chunk * K * K;
-  for (int a = 0; a < 2; ++a)
-    for (int b = 0; b < 2; ++b) {
-      const int i = ci + ty * 2 + a, j = cj + tx * 2 + b;
-      if (i < K && j < K) P[(size_t)i * K + j] = acc[a][b];
-    }
-  if (bi == bj && threadIdx.x < kTileG && ci + threadIdx.x < K)
-    colpart[(size_t)chunk * K + ci + threadIdx.x] = csum;
+  bi = i;
+  bj = i + p;
 }
 
-// G[i][j] (i <= j, mirrored) and c[i]: fixed-order sums over chunks.
-__global__ void k_gram_reduce(const double* part, const double* colpart, int K, int nchunk,
-                              double* G, double* c) {
-  const long long KK = (long long)K * K;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < KK + K;
+template <typename T>
+__global__ void __launch_bounds__(kPairs) k_gram(const T* __restrict__ V, long long ldv, int n,
+                                                 int K, int Kp, int rows_per_chunk, double* part,
+                                                 double* colpart) {
+  using A = typename Acc<T>::type;
+  extern __shared__ unsigned char sm_raw[];
+  T* Ps = reinterpret_cast<T*>(sm_raw);  // kPR x Kp
+  const int nb = Kp / kGB;
+  const int npairs = nb * (nb + 1) / 2;
+  const int pair = blockIdx.y * kPairs + threadIdx.x;
+  const bool active = pair < npairs;
+  int bi = 0, bj = 0;
+  if (active) pair_of(pair, nb, bi, bj);
+  const int chunk = blockIdx.x;
+  const long long r0 = (long long)chunk * rows_per_chunk;
+  const long long r1 = min((long long)n, r0 + rows_per_chunk);
+  A acc[kGB][kGB];
+  A cs[kGB];
+#pragma unroll
+  for (int a = 0; a < kGB; ++a) {
+    cs[a] = 0;
+#pragma unroll
+    for (int b = 0; b < kGB; ++b) acc[a][b] = 0;
+  }
+  for (long long r = r0; r < r1; r += kPR) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < kPR * Kp; e += blockDim.x) {
+      const int rr = e / Kp, cc = e % Kp;
+      const long long row = r + rr;
+      Ps[e] = (row < r1 && cc < K) ? V[row * ldv + cc] : (T)0;
+    }
+    __syncthreads();
+    if (active) {
+      const int nr = (int)min((long long)kPR, r1 - r);
+      for (int rr = 0; rr < nr; ++rr) {
+        const T* prow = Ps + rr * Kp;
+        A a[kGB], b[kGB];
+#pragma unroll
+        for (int q = 0; q < kGB; ++q) {
+          a[q] = prow[bi * kGB + q];
+          b[q] = prow[bj * kGB + q];
+        }
+#pragma unroll
+        for (int x = 0; x < kGB; ++x)
+#pragma unroll
+          for (int y = 0; y < kGB; ++y) acc[x][y] += a[x] * b[y];
+        if (bi == bj) {
+#pragma unroll
+          for (int q = 0; q < kGB; ++q) cs[q] += a[q];
+        }
+      }
+    }
+  }
+  if (active) {
+    double* P = part + ((size_t)chunk * npairs + pair) * (kGB * kGB);
+#pragma unroll
+    for (int x = 0; x < kGB; ++x)
+#pragma unroll
+      for (int y = 0; y < kGB; ++y) P[x * kGB + y] = (double)acc[x][y];
+    if (bi == bj) {
+#pragma unroll
+      for (int q = 0; q < kGB; ++q) colpart[(size_t)chunk * Kp + bi * kGB + q] = (double)cs[q];
+    }
+  }
+}
+
+// G (K x K, symmetric, FP64) and c (K): fixed-order sums over chunks.
+__global__ void k_gram_reduce(const double* __restrict__ part, const double* __restrict__ colpart,
+                              int K, int Kp, int nchunk, double* G, double* c) {
+  const int nb = Kp / kGB;
+  const int npairs = nb * (nb + 1) / 2;
+  const long long nel = (long long)npairs * kGB * kGB;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nel + Kp;
        idx += (long long)gridDim.x * blockDim.x) {
-    if (idx < KK) {
-      const int i = (int)(idx / K), j = (int)(idx % K);
-      if (i > j) continue;
+    if (idx < nel) {
+      const int pair = (int)(idx / (kGB * kGB)), xy = (int)(idx % (kGB * kGB));
+      int bi, bj;
+      pair_of(pair, nb, bi, bj);
+      const int i = bi * kGB + xy / kGB, j = bj * kGB + xy % kGB;
+      if (i >= K || j >= K || (bi == bj && i > j)) continue;
       double s = 0.0;
-      for (int q = 0; q < nchunk; ++q) s += part[(size_t)q * KK + idx];
+      for (int q = 0; q < nchunk; ++q) s += part[(size_t)q * nel + idx];
       G[(size_t)i * K + j] = s;
       G[(size_t)j * K + i] = s;
     } else {
-      const int i = (int)(idx - KK);
+      const int i = (int)(idx - nel);
+      if (i >= K) continue;
       double s = 0.0;
-      for (int q = 0; q < nchunk; ++q) s += colpart[(size_t)q * K + i];
+      for (int q = 0; q < nchunk; ++q) s += colpart[(size_t)q * Kp + i];
       c[i] = s;
     }
   }
 }
 
-// One CTA: A = G - c c^T / n (upper triangle), right-looking Cholesky with
-// rank-deficient columns dropped (pivot <= tol * G_ii, the column's squared
-// norm before projection; tol 1e-12 in FP64, 1e-5 in FP32: a Cholesky pivot
-// only resolves relative residuals above about sqrt(eps)), then
-// R^-1 by back substitution (one warp per column).  A lives in shared memory
-// when it fits, else in the global scratch `Ag`.
-template <typename T>
-__global__ void __launch_bounds__(1024) k_chol(const double* __restrict__ G,
-                                               const double* __restrict__ c, int K, double n,
-                                               double tol, double* Ag, double* R, double* Rinv,
-                                               T* RinvT, T* muT, int* kept, int* rank,
-                                               int use_smem) {
-  extern __shared__ double dsm[];
-  __shared__ double rrow[512];
-  __shared__ double diag0[512];
-  __shared__ double piv;
+struct CholOut {
+  void* Rinv;      // Kp x Kp, element type T, upper triangular, zero padded
+  void* mu;        // Kp, element type T
+  double* R;       // K x K upper (FP64), for R_out
+  int* kept;       // K
+  int* rank;       // 1
+  int* flag;       // [0] exact pass needed
+};
+
+// Gauss elimination of [A | I] with A = G - c c^T / n: after pivot j, row j
+// holds R[j][j..K) on the left and (R^-T)[j][0..j] on the right.  Columns
+// whose pivot is <= tol * G_jj are dropped (their rows stay zero).
+// C: arithmetic type; W: the K x 2K work matrix (shared or global memory).
+// fast = 1: report (flag) any kept pivot <= 1e-4 G_jj instead of trusting
+// it.  fast = 0: exact path; runs only when `flag` is set unless `always`.
+template <typename C, typename T>
+__global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
+                                                   const double* __restrict__ c, int K, int Kp,
+                                                   double n, double tol, C* Wg, int use_smem,
+                                                   int fast, int always, CholOut o) {
+  extern __shared__ unsigned char sm_raw[];
+  __shared__ double ref[512];
+  __shared__ C piv_inv;
   __shared__ int keep_j;
-  double* A = use_smem ? dsm : Ag;
-  const long long KK = (long long)K * K;
-  for (long long idx = threadIdx.x; idx < KK; idx += blockDim.x) {
-    const int i = (int)(idx / K), j = (int)(idx % K);
-    A[idx] = G[idx] - c[i] * c[j] / n;
-    R[idx] = 0.0;
-    Rinv[idx] = 0.0;
+  __shared__ int near_def;
+  if (!fast && !always && o.flag[0] == 0) return;
+  C* W = use_smem ? reinterpret_cast<C*>(sm_raw) : Wg;
+  const int W2 = 2 * K;
+  for (long long idx = threadIdx.x; idx < (long long)K * W2; idx += blockDim.x) {
+    const int i = (int)(idx / W2), j = (int)(idx % W2);
+    double v;
+    if (j < K) v = G[(size_t)i * K + j] - c[i] * c[j] / n;
+    else v = (j - K == i) ? 1.0 : 0.0;
+    W[idx] = (C)v;
   }
-  __syncthreads();
-  for (int i = threadIdx.x; i < K; i += blockDim.x) {
-    // reference for rank detection: the squared norm before any projection
-    // (the projected pivot carries rounding of order eps * this)
-    diag0[i] = G[(size_t)i * K + i];
-    muT[i] = (T)(c[i] / n);
-  }
+  for (int i = threadIdx.x; i < K; i += blockDim.x) ref[i] = G[(size_t)i * K + i];
+  if (threadIdx.x == 0) near_def = 0;
   __syncthreads();
   for (int j = 0; j < K; ++j) {
     if (threadIdx.x == 0) {
-      const double d = A[(size_t)j * K + j];
-      keep_j = (diag0[j] > 0.0 && d > tol * diag0[j]) ? 1 : 0;
-      piv = keep_j ? sqrt(d) : 0.0;
-      kept[j] = keep_j;
+      const double d = (double)W[(size_t)j * W2 + j];
+      int kj = (ref[j] > 0.0 && d > tol * ref[j]) ? 1 : 0;
+      if (fast && kj && d <= 1e-4 * ref[j]) near_def = 1;
+      keep_j = kj;
+      piv_inv = kj ? (C)(1.0 / sqrt(d)) : (C)0;
+      o.kept[j] = kj;
     }
     __syncthreads();
     const int kj = keep_j;
-    const double pv = piv;
-    __syncthreads();  // all have read before thread 0 writes the next pivot
-    if (!kj) continue;  // uniform across the CTA
-    for (int i = j + threadIdx.x; i < K; i += blockDim.x) {
-      const double r = (i == j) ? pv : A[(size_t)j * K + i] / pv;
-      rrow[i] = r;
-      R[(size_t)j * K + i] = r;
-    }
+    const C pinv = piv_inv;
     __syncthreads();
-    const int w = K - j - 1;
-    for (long long idx = threadIdx.x; idx < (long long)w * w; idx += blockDim.x) {
-      const int i = j + 1 + (int)(idx / w), l = j + 1 + (int)(idx % w);
-      if (l >= i) A[(size_t)i * K + l] -= rrow[i] * rrow[l];
+    C* rowj = W + (size_t)j * W2;
+    if (!kj) {  // dropped column: zero its row
+      for (int q = threadIdx.x; q < W2; q += blockDim.x) rowj[q] = (C)0;
+      __syncthreads();
+      continue;
+    }
+    // scale row j: left part j..K-1, right part 0..j
+    for (int q = threadIdx.x; q < W2; q += blockDim.x)
+      if ((q >= j && q < K) || (q >= K && q <= K + j)) rowj[q] *= pinv;
+    __syncthreads();
+    // eliminate column j from rows i > j: row_i -= R[j][i] * row_j
+    const int rows = K - j - 1;
+    const int cols = (K - j - 1) + (j + 1);  // left j+1..K-1, right 0..j
+    for (long long idx = threadIdx.x; idx < (long long)rows * cols; idx += blockDim.x) {
+      const int i = j + 1 + (int)(idx / cols);
+      const int q0 = (int)(idx % cols);
+      const int q = q0 < K - j - 1 ? j + 1 + q0 : K + (q0 - (K - j - 1));
+      W[(size_t)i * W2 + q] -= rowj[i] * rowj[q];
     }
     __syncthreads();
   }
-  // R^-1: column j solves R x = e_j over the kept indices (back substitution).
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = wid; j < K; j += nw) {
-    if (!kept[j]) continue;
-    const double xj = 1.0 / R[(size_t)j * K + j];
-    if (lane == 0) Rinv[(size_t)j * K + j] = xj;
-    __syncwarp();
-    for (int i = j - 1; i >= 0; --i) {
-      if (!kept[i]) continue;
-      double s = 0.0;
-      for (int l = i + 1 + lane; l <= j; l += 32) s += R[(size_t)i * K + l] * Rinv[(size_t)l * K + j];
-      s = warp_sum(s);
-      if (lane == 0) Rinv[(size_t)i * K + j] = -s / R[(size_t)i * K + i];
-      __syncwarp();
-    }
+  // outputs: R (FP64), Rinv = (R^-T)^T (type T), mu, rank, flag
+  T* Rinv = static_cast<T*>(o.Rinv);
+  T* mu = static_cast<T*>(o.mu);
+  for (long long idx = threadIdx.x; idx < (long long)Kp * Kp; idx += blockDim.x) {
+    const int i = (int)(idx / Kp), j = (int)(idx % Kp);
+    C v = 0;
+    if (i < K && j < K && i <= j) v = W[(size_t)j * W2 + K + i];
+    Rinv[idx] = (T)v;
+    if (i < K && j < K) o.R[(size_t)i * K + j] = (i <= j) ? (double)W[(size_t)i * W2 + j] : 0.0;
   }
+  for (int i = threadIdx.x; i < Kp; i += blockDim.x) mu[i] = i < K ? (T)(c[i] / n) : (T)0;
   __syncthreads();
-  for (long long idx = threadIdx.x; idx < KK; idx += blockDim.x) RinvT[idx] = (T)Rinv[idx];
+  if (threadIdx.x == 0) {
+    int r = 0;
+    for (int j = 0; j < K; ++j) r += o.kept[j];
+    *o.rank = r;
+    if (fast) o.flag[0] = near_def;
+  }
+}
+
+// Second pass from the Gram of Q1 (= I + E up to rounding): R2 = I + X1 and
+// R2^-1 = I - X1, X1 = strict upper part of E plus half its diagonal.  Sets
+// flag[0] when max|E| > gtol (the exact path then recomputes; flag must be
+// zero on entry).  Columns with G_jj == 0 (dropped in pass 1) stay dropped.
+template <typename T>
+__global__ void k_chol_series(const double* __restrict__ G, const double* __restrict__ c, int K,
+                              int Kp, double n, double gtol, CholOut o) {
+  T* Rinv = static_cast<T*>(o.Rinv);
+  T* mu = static_cast<T*>(o.mu);
+  bool bad = false;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)Kp * Kp;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / Kp), j = (int)(idx % Kp);
+    double rv = 0.0, riv = 0.0;
+    if (i < K && j < K && i <= j) {
+      const bool ki = G[(size_t)i * K + i] > 0.0, kj = G[(size_t)j * K + j] > 0.0;
+      if (ki && kj) {
+        const double e = G[(size_t)i * K + j] - c[i] * c[j] / n - (i == j ? 1.0 : 0.0);
+        if (!(fabs(e) <= gtol)) bad = true;
+        const double x = (i == j) ? 0.5 * e : e;
+        rv = (i == j ? 1.0 : 0.0) + x;
+        riv = (i == j ? 1.0 : 0.0) - x;
+      }
+    }
+    Rinv[idx] = (T)riv;
+    if (i < K && j < K) o.R[(size_t)i * K + j] = rv;
+  }
+  if (bad) atomicOr(o.flag, 1);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < Kp;
+       i += (long long)gridDim.x * blockDim.x) {
+    mu[i] = i < K ? (T)(c[i] / n) : (T)0;
+    if (i < K) o.kept[i] = G[(size_t)i * K + i] > 0.0 ? 1 : 0;
+  }
+}
+
+__global__ void k_rank(const int* kept, int K, int* rank) {
   if (threadIdx.x == 0) {
     int r = 0;
     for (int j = 0; j < K; ++j) r += kept[j];
@@ -209,56 +286,82 @@ __global__ void __launch_bounds__(1024) k_chol(const double* __restrict__ G,
   }
 }
 
-// Q = (V - 1 mu^T) Rinv in place.  One CTA per RB-row block.
+// Q = (V - 1 mu^T) Rinv in place.  CTA: RB rows x all Kp columns in shared
+// memory (row stride Kp + 1), output blocks of kACB columns from the last;
+// thread: 4 rows x 8 columns.
+// stage_r = 0 (large K in FP64): Rinv is read from global memory (L1/L2)
+// instead of being staged per column block.
 template <typename T>
-__global__ void __launch_bounds__(256) k_apply(T* V, long long ldv, int n, int K,
-                                               const T* __restrict__ Rinv, const T* __restrict__ mu,
-                                               int RB, int CB) {
+__global__ void __launch_bounds__(256) k_apply(T* V, long long ldv, int n, int K, int Kp,
+                                               const T* __restrict__ Rinv,
+                                               const T* __restrict__ mu, int RB, int stage_r) {
   extern __shared__ unsigned char sm_raw[];
-  T* Vs = reinterpret_cast<T*>(sm_raw);        // RB x K
-  T* Rs = Vs + (size_t)RB * K;                  // K x CB
+  const int ldv_s = Kp + 1;
+  T* Vs = reinterpret_cast<T*>(sm_raw);     // RB x (Kp + 1)
+  T* Rs = Vs + (size_t)RB * ldv_s;          // Kp x kACB
+  Rs = reinterpret_cast<T*>((reinterpret_cast<uintptr_t>(Rs) + 15) & ~uintptr_t(15));
   const long long r0 = (long long)blockIdx.x * RB;
   const int nrow = (int)min((long long)RB, (long long)n - r0);
-  for (int e = threadIdx.x; e < RB * K; e += blockDim.x) {
-    const int rr = e / K, cc = e % K;
-    Vs[e] = rr < nrow ? V[(r0 + rr) * ldv + cc] - mu[cc] : (T)0;
+  for (int e = threadIdx.x; e < RB * Kp; e += blockDim.x) {
+    const int rr = e / Kp, cc = e % Kp;
+    Vs[rr * ldv_s + cc] = (rr < nrow && cc < K) ? V[(r0 + rr) * ldv + cc] - mu[cc] : (T)0;
   }
-  const int tx = threadIdx.x % CB, ty = threadIdx.x / CB, nty = blockDim.x / CB;
-  const int nblk = (K + CB - 1) / CB;
+  const int tx = threadIdx.x & 7, ty = threadIdx.x >> 3;  // 8 column groups x RB/4 row groups
+  const int nblk = (Kp + kACB - 1) / kACB;
   for (int J = nblk - 1; J >= 0; --J) {
-    const int c0 = J * CB;
-    const int iend = min(K, c0 + CB);  // Rinv upper triangular: rows < iend
+    const int c0 = J * kACB;
+    const int cw = min(kACB, Kp - c0);
+    const int iend = c0 + cw;  // Rinv upper triangular: rows < iend
     __syncthreads();
-    for (int e = threadIdx.x; e < iend * CB; e += blockDim.x) {
-      const int i = e / CB, jj = e % CB;
-      Rs[e] = (c0 + jj < K) ? Rinv[(size_t)i * K + c0 + jj] : (T)0;
-    }
-    __syncthreads();
-    T acc[16];
-    const int nr = (RB + nty - 1) / nty;
-    for (int q = 0; q < nr; ++q) acc[q] = 0;
-    for (int i = 0; i < iend; ++i) {
-      const T rv = Rs[i * CB + tx];
-      for (int q = 0; q < nr; ++q) {
-        const int rr = ty + q * nty;
-        if (rr < RB) acc[q] += Vs[rr * K + i] * rv;
+    if (stage_r) {
+      for (int e = threadIdx.x; e < iend * kACB; e += blockDim.x) {
+        const int i = e / kACB, jj = e % kACB;
+        Rs[e] = (jj < cw) ? Rinv[(size_t)i * Kp + c0 + jj] : (T)0;
       }
     }
     __syncthreads();
-    if (c0 + tx < K)
-      for (int q = 0; q < nr; ++q) {
-        const int rr = ty + q * nty;
-        if (rr < RB) Vs[rr * K + c0 + tx] = acc[q];
+    T acc[4][8];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 8; ++b) acc[a][b] = 0;
+    const T* vrow = Vs + (ty * 4) * ldv_s;
+#pragma unroll 4
+    for (int i = 0; i < iend; ++i) {
+      T a[4], b[8];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = vrow[r * ldv_s + i];
+      if (stage_r) {
+        const T* rrow = Rs + i * kACB + tx * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = rrow[q];
+      } else {
+        const T* rrow = Rinv + (size_t)i * Kp + c0 + tx * 8;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) b[q] = (tx * 8 + q < cw) ? __ldg(rrow + q) : (T)0;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[r][q] += a[r] * b[q];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int col = c0 + tx * 8 + q;
+        if (tx * 8 + q < cw) Vs[(ty * 4 + r) * ldv_s + col] = acc[r][q];
       }
   }
   __syncthreads();
   for (int e = threadIdx.x; e < nrow * K; e += blockDim.x) {
     const int rr = e / K, cc = e % K;
-    V[(r0 + rr) * ldv + cc] = Vs[e];
+    V[(r0 + rr) * ldv + cc] = Vs[rr * ldv_s + cc];
   }
 }
 
-// R_out = R2 * R1 (both upper triangular).
+// R_out = R2 * R1 (both upper triangular, FP64).
 __global__ void k_trmm_upper(const double* R2, const double* R1, int K, double* Rout) {
   const long long KK = (long long)K * K;
   for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < KK;
@@ -275,89 +378,123 @@ struct OrthoWs {
   double* colpart;
   double* G;
   double* c;
-  double* Ag;
+  double* Wg;  // K x 2K FP64 scratch of the exact path
   double* R1;
   double* R2;
-  double* Rinv;
-  void* RinvT;
-  void* muT;
+  void* Rinv;
+  void* mu;
   int* kept;
   int* rank;
+  int* flag;
   int nchunk;
   int rows_per_chunk;
+  int ngroups;
 };
 
-inline int ntiles_of(int K) {
-  const int nb = (K + kTileG - 1) / kTileG;
-  return nb * (nb + 1) / 2;
-}
-
 size_t carve_ortho(void* base, long long n, int K, int dtype, OrthoWs* w) {
-  Carver c(base);
-  const int tiles = ntiles_of(K);
-  int nchunk = (num_sms() * 4 + tiles - 1) / tiles;
-  const long long max_chunks = (n + 63) / 64;
+  Carver cv(base);
+  const int Kp = round8(K);
+  const int nb = Kp / kGB;
+  const int npairs = nb * (nb + 1) / 2;
+  w->ngroups = (npairs + kPairs - 1) / kPairs;
+  int nchunk = (num_sms() * 2 + w->ngroups - 1) / w->ngroups;
+  const long long max_chunks = (n + kPR - 1) / kPR;
   if (nchunk > max_chunks) nchunk = (int)(max_chunks > 0 ? max_chunks : 1);
   w->nchunk = nchunk;
-  w->rows_per_chunk = (int)(((n + nchunk - 1) / nchunk + kPanel - 1) / kPanel * kPanel);
+  w->rows_per_chunk = (int)(((n + nchunk - 1) / nchunk + kPR - 1) / kPR * kPR);
   const size_t KK = (size_t)K * K;
   const size_t esz = dtype == HEF_F64 ? 8 : 4;
-  w->part = c.take<double>(KK * nchunk);
-  w->colpart = c.take<double>((size_t)K * nchunk);
-  w->G = c.take<double>(KK);
-  w->c = c.take<double>(K);
-  w->Ag = c.take<double>(KK);
-  w->R1 = c.take<double>(KK);
-  w->R2 = c.take<double>(KK);
-  w->Rinv = c.take<double>(KK);
-  w->RinvT = c.take<char>(KK * esz);
-  w->muT = c.take<char>(K * esz);
-  w->kept = c.take<int>(K);
-  w->rank = c.take<int>(4);
-  return c.bytes();
+  w->part = cv.take<double>((size_t)nchunk * npairs * kGB * kGB);
+  w->colpart = cv.take<double>((size_t)nchunk * Kp);
+  w->G = cv.take<double>(KK);
+  w->c = cv.take<double>(K);
+  w->Wg = cv.take<double>(2 * KK);
+  w->R1 = cv.take<double>(KK);
+  w->R2 = cv.take<double>(KK);
+  w->Rinv = cv.take<char>((size_t)Kp * Kp * esz);
+  w->mu = cv.take<char>((size_t)Kp * esz);
+  w->kept = cv.take<int>(K);
+  w->rank = cv.take<int>(4);
+  w->flag = cv.take<int>(4);
+  return cv.bytes();
 }
 
 template <typename T>
 hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int* rank_out,
                      const OrthoWs& w, cudaStream_t st) {
-  const int nb = (K + kTileG - 1) / kTileG;
-  const int tiles = ntiles_of(K);
-  const size_t chol_smem = (size_t)K * K * sizeof(double);
-  const int use_smem = chol_smem <= 200 * 1024 ? 1 : 0;
-  if (use_smem) {
-    HEF_CHECK_CUDA(cudaFuncSetAttribute(k_chol<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)chol_smem));
+  const int Kp = round8(K);
+  const size_t gram_smem = (size_t)kPR * Kp * sizeof(T);
+  HEF_CHECK_CUDA(cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)gram_smem));
+  const dim3 ggrid(w.nchunk, w.ngroups);
+  const int nb = Kp / kGB;
+  const long long nel = (long long)nb * (nb + 1) / 2 * kGB * kGB;
+  const int rgrid = stride_grid(nel + Kp, 4);
+  int stage_r = 1;
+  auto apply_smem = [&](int rb) {
+    return ((size_t)rb * (Kp + 1) + (stage_r ? (size_t)Kp * kACB : 0)) * sizeof(T) + 16;
+  };
+  int RB = 128;
+  while (RB > 32 && apply_smem(RB) > 200 * 1024) RB /= 2;
+  if (apply_smem(RB) > 200 * 1024) {
+    stage_r = 0;
+    RB = 128;
+    while (RB > 32 && apply_smem(RB) > 200 * 1024) RB /= 2;
   }
-  // apply tiling: largest (RB, CB) whose shared memory fits in 200 KB
-  int RB = 64, CB = 32;
-  auto smem_of = [&](int rb, int cb) { return ((size_t)rb * K + (size_t)K * cb) * sizeof(T); };
-  while (smem_of(RB, CB) > 200 * 1024 && RB > 16) RB /= 2;
-  while (smem_of(RB, CB) > 200 * 1024 && CB > 8) CB /= 2;
-  if (smem_of(RB, CB) > 200 * 1024 || (RB + (256 / CB) - 1) / (256 / CB) > 16)
+  if (apply_smem(RB) > 200 * 1024)
     return set_error(HEF_ERR_UNSUPPORTED, "hef_orthonormalize: K = %d too large", K);
-  const size_t apply_smem = smem_of(RB, CB);
   HEF_CHECK_CUDA(cudaFuncSetAttribute(k_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)apply_smem));
-  const double tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
-  const dim3 ggrid(tiles, w.nchunk);
-  const int rgrid = stride_grid((long long)K * K + K, 4);
+                                      (int)apply_smem(RB)));
   const int agrid = (int)((n + RB - 1) / RB);
+  const int athreads = RB * 2;  // (RB / 4) row groups x 8 column groups
+  const size_t fast_smem = (size_t)K * 2 * K * sizeof(float);
+  const bool fast_ok = sizeof(T) == 4 && fast_smem <= 200 * 1024;
+  if (fast_ok)
+    HEF_CHECK_CUDA(cudaFuncSetAttribute(k_chol_aug<float, T>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)fast_smem));
+  const double tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
+  const double gtol = sizeof(T) == 8 ? 1e-8 : 1e-4;
   double* Rs[2] = {w.R1, w.R2};
+
   for (int pass = 0; pass < 2; ++pass) {
-    HEF_LAUNCH("k_gram", st, k_gram<T><<<ggrid, 256, 0, st>>>(V, ldv, (int)n, K, nb, w.rows_per_chunk, w.part, w.colpart));
-    HEF_LAUNCH("k_gram_reduce", st, k_gram_reduce<<<rgrid, kThreads, 0, st>>>(w.part, w.colpart, K, w.nchunk, w.G, w.c));
-    HEF_LAUNCH("k_chol", st, k_chol<T><<<1, 1024, use_smem ? chol_smem : 0, st>>>(
-        w.G, w.c, K, (double)n, tol, w.Ag, Rs[pass], w.Rinv, static_cast<T*>(w.RinvT),
-        static_cast<T*>(w.muT), w.kept, w.rank, use_smem));
-    HEF_LAUNCH("k_apply", st, k_apply<T><<<agrid, 256, apply_smem, st>>>(V, ldv, (int)n, K, static_cast<const T*>(w.RinvT),
-                                               static_cast<const T*>(w.muT), RB, CB));
+    CholOut o{w.Rinv, w.mu, Rs[pass], w.kept, w.rank, w.flag};
+    HEF_LAUNCH("k_gram", st, k_gram<T><<<ggrid, kPairs, gram_smem, st>>>(
+                                 V, ldv, (int)n, K, Kp, w.rows_per_chunk, w.part, w.colpart));
+    HEF_LAUNCH("k_gram_reduce", st, k_gram_reduce<<<rgrid, kThreads, 0, st>>>(
+                                        w.part, w.colpart, K, Kp, w.nchunk, w.G, w.c));
+    HEF_CHECK_LAUNCH();
+    if (pass == 0) {
+      if (fast_ok) {
+        HEF_LAUNCH("k_chol_aug", st, k_chol_aug<float, T><<<1, 1024, fast_smem, st>>>(
+                                         w.G, w.c, K, Kp, (double)n, tol, nullptr, 1, 1, 0, o));
+      }
+      // exact FP64 path: always for the FP64 form, on demand for the FP32 form
+      HEF_LAUNCH("k_chol_aug", st, k_chol_aug<double, T><<<1, 1024, 0, st>>>(
+                                       w.G, w.c, K, Kp, (double)n, tol, w.Wg, 0, 0,
+                                       fast_ok ? 0 : 1, o));
+    } else {
+      HEF_CHECK_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
+      HEF_LAUNCH("k_chol_series", st, k_chol_series<T><<<stride_grid((long long)Kp * Kp, 2),
+                                                        kThreads, 0, st>>>(
+                                          w.G, w.c, K, Kp, (double)n, gtol, o));
+      HEF_LAUNCH("k_chol_aug", st, k_chol_aug<double, T><<<1, 1024, 0, st>>>(
+                                       w.G, w.c, K, Kp, (double)n, tol, w.Wg, 0, 0, 0, o));
+      HEF_LAUNCH("k_rank", st, k_rank<<<1, 32, 0, st>>>(w.kept, K, w.rank));
+    }
+    HEF_CHECK_LAUNCH();
+    HEF_LAUNCH("k_apply", st, k_apply<T><<<agrid, athreads, apply_smem(RB), st>>>(
+                                  V, ldv, (int)n, K, Kp, static_cast<const T*>(w.Rinv),
+                                  static_cast<const T*>(w.mu), RB, stage_r));
     HEF_CHECK_LAUNCH();
   }
   if (R_out) {
-    HEF_LAUNCH("k_trmm_upper", st, k_trmm_upper<<<rgrid, kThreads, 0, st>>>(w.R2, w.R1, K, R_out));
+    HEF_LAUNCH("k_trmm_upper", st, k_trmm_upper<<<stride_grid((long long)K * K, 4), kThreads, 0,
+                                                  st>>>(w.R2, w.R1, K, R_out));
     HEF_CHECK_LAUNCH();
   }
-  if (rank_out) HEF_CHECK_CUDA(cudaMemcpyAsync(rank_out, w.rank, sizeof(int), cudaMemcpyDeviceToDevice, st));
+  if (rank_out)
+    HEF_CHECK_CUDA(cudaMemcpyAsync(rank_out, w.rank, sizeof(int), cudaMemcpyDeviceToDevice, st));
   return HEF_OK;
 }
 
@@ -384,11 +521,13 @@ extern "C" hef_status hef_orthonormalize(int64_t n, int32_t K, int32_t dtype, vo
     return set_error(HEF_ERR_INVALID_ARG, "hef_orthonormalize: dtype must be HEF_F64 or HEF_F32");
   const size_t esz = dtype == HEF_F64 ? 8 : 4;
   if (!V || ldv < K || (ldv * esz) % 16 || (reinterpret_cast<uintptr_t>(V) & 15))
-    return set_error(HEF_ERR_INVALID_ARG, "hef_orthonormalize: V NULL, ldv < K or rows not 16-byte aligned");
+    return set_error(HEF_ERR_INVALID_ARG,
+                     "hef_orthonormalize: V NULL, ldv < K or rows not 16-byte aligned");
   OrthoWs w;
   const size_t need = carve_ortho(workspace, n, K, dtype, &w);
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
-    return set_error(HEF_ERR_WORKSPACE, "hef_orthonormalize: workspace needs %zu bytes (256-aligned)", need);
+    return set_error(HEF_ERR_WORKSPACE,
+                     "hef_orthonormalize: workspace needs %zu bytes (256-aligned)", need);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (dtype == HEF_F64)
     return run_ortho<double>(n, K, static_cast<double*>(V), ldv, R_out, rank_out, w, st);

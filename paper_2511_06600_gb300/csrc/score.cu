@@ -33,6 +33,45 @@ __device__ __forceinline__ float lowest<float>() {
   return -FLT_MAX;
 }
 
+// Max and min of each lane's columns over the pins of one hyperedge; four
+// pin rows are loaded before any is reduced, so long hyperedges keep several
+// row reads in flight.
+template <typename T, int NC>
+__device__ __forceinline__ void edge_extrema(const T* __restrict__ Q, long long ldq, int K,
+                                             const int32_t* __restrict__ cpins, int a, int b,
+                                             int lane, T (&mx)[NC], T (&mn)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
+  int t = a;
+  for (; t + 4 <= b; t += 4) {
+    const T* r0 = Q + (long long)cpins[t] * ldq;
+    const T* r1 = Q + (long long)cpins[t + 1] * ldq;
+    const T* r2 = Q + (long long)cpins[t + 2] * ldq;
+    const T* r3 = Q + (long long)cpins[t + 3] * ldq;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int col = lane + 32 * c;
+      if (col < K) {
+        const T v0 = r0[col], v1 = r1[col], v2 = r2[col], v3 = r3[col];
+        mx[c] = fmax(fmax(mx[c], fmax(v0, v1)), fmax(v2, v3));
+        mn[c] = fmin(fmin(mn[c], fmin(v0, v1)), fmin(v2, v3));
+      }
+    }
+  }
+  for (; t < b; ++t) {
+    const T* r0 = Q + (long long)cpins[t] * ldq;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int col = lane + 32 * c;
+      if (col < K) {
+        const T v = r0[col];
+        mx[c] = fmax(mx[c], v);
+        mn[c] = fmin(mn[c], v);
+      }
+    }
+  }
+}
+
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restrict__ Q, long long ldq,
                                                      int K, double* part, unsigned int* counter,
@@ -51,20 +90,7 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
     const int a = g.ceptr[e], b = g.ceptr[e + 1];
     if (b - a < 2) continue;
     T mx[NC], mn[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
-    for (int t = a; t < b; ++t) {
-      const T* row = Q + (long long)g.cpins[t] * ldq;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int col = lane + 32 * c;
-        if (col < K) {
-          const T v = row[col];
-          mx[c] = v > mx[c] ? v : mx[c];
-          mn[c] = v < mn[c] ? v : mn[c];
-        }
-      }
-    }
+    edge_extrema<T, NC>(Q, ldq, K, g.cpins, a, b, lane, mx, mn);
     const T we = (T)g.ew[e];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -126,21 +152,7 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
       continue;
     }
     T mx[NC], mn[NC];
-    int imx[NC], imn[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>(), imx[c] = a, imn[c] = a;
-    for (int t = a; t < b; ++t) {
-      const T* row = Q + (long long)g.cpins[t] * ldq;
-#pragma unroll
-      for (int c = 0; c < NC; ++c) {
-        const int col = lane + 32 * c;
-        if (col < K) {
-          const T v = row[col];
-          if (v > mx[c]) mx[c] = v, imx[c] = t;  // strict: first position wins ties
-          if (v < mn[c]) mn[c] = v, imn[c] = t;
-        }
-      }
-    }
+    edge_extrema<T, NC>(Q, ldq, K, g.cpins, a, b, lane, mx, mn);
     // lane-local best (lowest column on ties), then warp arg-max
     T best = (T)-1;
     int bcol = 0x7fffffff;
@@ -167,22 +179,32 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     }
-    int tmax = a, tmin = a;
-    double sp_win = 0.0;
     const bool any = bcol != 0x7fffffff;
+    // value extremes of the winning column, from the lane that owns it
+    T vmax = 0, vmin = 0;
     if (any && lane == (bcol & 31)) {
 #pragma unroll
       for (int c = 0; c < NC; ++c)
-        if (c == (bcol >> 5)) {
-          tmax = imx[c];
-          tmin = imn[c];
-          sp_win = (double)(mx[c] - mn[c]);
-        }
+        if (c == (bcol >> 5)) vmax = mx[c], vmin = mn[c];
     }
     const int owner = any ? (bcol & 31) : 0;
-    tmax = __shfl_sync(0xffffffffu, tmax, owner);
-    tmin = __shfl_sync(0xffffffffu, tmin, owner);
-    sp_win = __shfl_sync(0xffffffffu, sp_win, owner);
+    vmax = __shfl_sync(0xffffffffu, vmax, owner);
+    vmin = __shfl_sync(0xffffffffu, vmin, owner);
+    // first pin positions attaining them (lanes over the pins of e)
+    int tmax = 0x7fffffff, tmin = 0x7fffffff;
+    if (any) {
+      for (int t = a + lane; t < b; t += 32) {
+        const T v = Q[(long long)g.cpins[t] * ldq + bcol];
+        if (v == vmax && t < tmax) tmax = t;
+        if (v == vmin && t < tmin) tmin = t;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        tmax = min(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+        tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+      }
+    }
+    const double sp_win = (double)(vmax - vmin);
     if (lane == 0) {
       double Re = 0.0;
       if (reduce == HEF_REDUCE_SUM) Re = sum;
