@@ -1,0 +1,41 @@
+"""The C ABI library builds, loads and exports every function include/hef.h
+declares (CPU only: no kernel is launched)."""
+import ctypes
+import os
+import re
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hef.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"\b(hef_[a-z0-9_]+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_function():
+    from paper_2511_06600_gb300 import build
+    path = build.build()
+    lib = ctypes.CDLL(path)
+    names = declared_functions()
+    assert len(names) >= 15
+    missing = [nm for nm in names if not hasattr(lib, nm)]
+    assert not missing, missing
+
+
+def test_status_strings_and_version():
+    import paper_2511_06600_gb300 as hef
+    L = hef.lib()
+    assert L.hef_abi_version() >= 1
+    assert L.hef_status_string(-7).decode() == "HEF_ERR_INVALID_INPUT"
+    assert L.hef_status_string(0).decode() == "HEF_OK"
+
+
+def test_workspace_queries_reject_bad_sizes():
+    import paper_2511_06600_gb300 as hef
+    L = hef.lib()
+    assert L.hef_incidence_workspace_bytes(-1, 3, 4) == 0
+    assert L.hef_incidence_workspace_bytes(10, 3, 4) > 0
+    assert L.hef_orthonormalize_workspace_bytes(100, 513, 0) == 0
+    assert L.hef_orthonormalize_workspace_bytes(100, 20, 1) > 0
