@@ -217,6 +217,35 @@ hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q,
                                void* workspace, size_t workspace_bytes,
                                void* stream);
 
+/* ------------------------------------------------------------------------
+ * Edge resistance without caller-provided device memory.  The paper has no
+ * counterpart: this is a service of the library.
+ *
+ * Some callers cannot give the library a workspace: plain C code that only
+ * holds the pointers it was handed and has no device allocator of its own, or
+ * a host application whose memory pool already owns all of the GPU's free
+ * memory (cudaMalloc would fail, and it also synchronises the device, which a
+ * latency-critical caller must not do in mid-stream).  This call computes
+ * exactly what hef_edge_resistance computes and allocates nothing: its
+ * scratch (per-CTA partial sums of Q_H, Q_H and 1/Q_H, a completion counter)
+ * is a fixed 2 MiB array compiled into the library, which every GPU that
+ * loads the library reserves until the process exits.
+ *  - The caller still provides Q and the outputs (same meaning as
+ *    hef_edge_resistance); K must be <= 512 (HEF_ERR_UNSUPPORTED otherwise).
+ *  - The first call on a device looks up the array's device address (with
+ *    that device current) and caches it; make that first call before any
+ *    stream capture.
+ *  - Every call on a device shares the one array and leaves its contents
+ *    behind.  Calls ordered on one stream are safe; calls that overlap on the
+ *    GPU (different streams or host threads without ordering) race on it.
+ * ---------------------------------------------------------------------- */
+hef_status hef_edge_resistance_noalloc(const hef_incidence* inc,
+                                       const void* Q, int64_t ldq, int32_t K,
+                                       int32_t dtype, int32_t reduce,
+                                       double* R_out, double* QH_out,
+                                       int32_t* argvec, int32_t* pmax,
+                                       int32_t* pmin, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -50,6 +50,8 @@ _SIGS = {
     "hef_edge_resistance_workspace_bytes": (c_sz, [c_p, c_i32]),
     "hef_edge_resistance": (c_i32, [c_p, c_p, c_i64, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_p, c_p,
                                     c_p, c_sz, c_p]),
+    "hef_edge_resistance_noalloc": (c_i32, [c_p, c_p, c_i64, c_i32, c_i32, c_i32, c_p, c_p, c_p,
+                                            c_p, c_p, c_p]),
 }
 
 _lib = None
@@ -255,6 +257,25 @@ def edge_resistance(inc, Q, K, reduce=HEF_REDUCE_MAX, routing=True, workspace=No
                                  _ptr(out["R"]), _ptr(out.get("QH")), _ptr(out.get("argvec")),
                                  _ptr(out.get("pmax")), _ptr(out.get("pmin")), _ptr(workspace),
                                  workspace.numel(), _stream(stream)))
+    return out
+
+
+def edge_resistance_noalloc(inc, Q, K, reduce=HEF_REDUCE_MAX, out=None, stream=None):
+    """hef_edge_resistance_noalloc: the scores of edge_resistance, with the
+    library's fixed scratch instead of a workspace (outputs still needed)."""
+    code = _dtype_code(Q.dtype)
+    dev = Q.device
+    m = inc.m
+    if out is None:
+        out = dict(R=torch.empty(max(m, 1), dtype=torch.float64, device=dev)[:m],
+                   QH=torch.empty(K, dtype=torch.float64, device=dev))
+        for key in ("argvec", "pmax", "pmin"):
+            out[key] = torch.empty(max(m, 1), dtype=torch.int32, device=dev)[:m]
+    _check("hef_edge_resistance_noalloc",
+           lib().hef_edge_resistance_noalloc(inc.handle, _ptr(Q), Q.stride(0), K, code, int(reduce),
+                                             _ptr(out["R"]), _ptr(out.get("QH")),
+                                             _ptr(out.get("argvec")), _ptr(out.get("pmax")),
+                                             _ptr(out.get("pmin")), _stream(stream)))
     return out
 
 

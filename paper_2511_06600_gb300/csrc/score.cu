@@ -12,6 +12,7 @@
 // across warps and CTAs in a fixed order); pass 2 recomputes the spreads and
 // takes the max with its arg-max column and the pins that realise it.
 #include <cfloat>
+#include <mutex>
 
 #include "internal.h"
 
@@ -266,11 +267,95 @@ hef_status dispatch_score(const hef_incidence* inc, const T* Q, long long ldq, i
   return set_error(HEF_ERR_UNSUPPORTED, "hef_edge_resistance: K must be <= 512");
 }
 
+// ---------------------------------------------------------------------------
+// Scoring for callers that cannot hand the library any device memory of
+// their own (see hef_edge_resistance_noalloc): its scratch lives in one
+// fixed array that is part of the loaded library on every device.
+
+constexpr size_t kNoallocScratchBytes = size_t(2) << 20;  // 2 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[kMaxDevices] = {};
+
+// Device address of g_noalloc_scratch on the current device.  In host code
+// the symbol name is only a host-side stand-in, so the address is looked up
+// once per device (with that device current) and cached.
+hef_status noalloc_scratch(void** out) {
+  int dev = 0;
+  HEF_CHECK_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= kMaxDevices)
+    return set_error(HEF_ERR_UNSUPPORTED, "hef_edge_resistance_noalloc: device %d >= %d", dev,
+                     kMaxDevices);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p)
+      return set_error(HEF_ERR_CUDA, "hef_edge_resistance_noalloc: cudaGetSymbolAddress failed: %s",
+                       cudaGetErrorString(e));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return HEF_OK;
+}
+
+// Same layout as carve_score, with the CTA count capped so that the per-CTA
+// partial sums fit the fixed scratch.
+size_t carve_score_capped(void* base, int K, size_t cap, ScoreWs* w) {
+  const size_t fixed = 3 * 256 + 2 * (size_t)K * sizeof(double) + 64 * sizeof(unsigned int);
+  long long g = (long long)num_sms() * 4;
+  const long long fit = (long long)((cap - fixed) / ((size_t)K * sizeof(double)));
+  if (g > fit) g = fit;
+  Carver c(base);
+  w->grid = (int)(g > 0 ? g : 1);
+  w->part = c.take<double>((size_t)w->grid * K);
+  w->QH = c.take<double>(K);
+  w->invQH = c.take<double>(K);
+  w->counter = c.take<unsigned int>(64);
+  return c.bytes();
+}
+
 }  // namespace
 
 }  // namespace hef
 
 using namespace hef;
+
+extern "C" hef_status hef_edge_resistance_noalloc(const hef_incidence* inc, const void* Q,
+                                                  int64_t ldq, int32_t K, int32_t dtype,
+                                                  int32_t reduce, double* R_out, double* QH_out,
+                                                  int32_t* argvec, int32_t* pmax, int32_t* pmin,
+                                                  void* stream) {
+  if (!inc) return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: NULL incidence");
+  if (K < 1 || K > 512)
+    return set_error(HEF_ERR_UNSUPPORTED,
+                     "hef_edge_resistance_noalloc: K = %d outside 1..512 (the fixed %zu-byte "
+                     "scratch is sized for K <= 512)",
+                     K, kNoallocScratchBytes);
+  if (dtype != HEF_F64 && dtype != HEF_F32)
+    return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: dtype must be HEF_F64 or HEF_F32");
+  if (reduce != HEF_REDUCE_MAX && reduce != HEF_REDUCE_SUM)
+    return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: unknown reduce %d", reduce);
+  if (!Q || ldq < K || (inc->m > 0 && !R_out))
+    return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: Q or R_out NULL, or ldq < K");
+  void* scratch = nullptr;
+  hef_status s = noalloc_scratch(&scratch);
+  if (s) return s;
+  ScoreWs w;
+  if (carve_score_capped(nullptr, K, kNoallocScratchBytes, &w) > kNoallocScratchBytes)
+    return set_error(HEF_ERR_UNSUPPORTED, "hef_edge_resistance_noalloc: K = %d does not fit the scratch", K);
+  carve_score_capped(scratch, K, kNoallocScratchBytes, &w);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the completion counter must start at zero; partial sums are overwritten
+  HEF_CHECK_CUDA(cudaMemsetAsync(w.counter, 0, 64 * sizeof(unsigned int), st));
+  if (dtype == HEF_F64)
+    return dispatch_score<double>(inc, static_cast<const double*>(Q), ldq, K, reduce, R_out, QH_out,
+                                  argvec, pmax, pmin, w, st);
+  return dispatch_score<float>(inc, static_cast<const float*>(Q), ldq, K, reduce, R_out, QH_out,
+                               argvec, pmax, pmin, w, st);
+}
 
 extern "C" size_t hef_edge_resistance_workspace_bytes(const hef_incidence* inc, int32_t K) {
   if (!inc || K < 1 || K > 512) return 0;
