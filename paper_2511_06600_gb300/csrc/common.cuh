@@ -143,6 +143,94 @@ __device__ __forceinline__ void block_partials(const double (&v)[NQ],
   __syncthreads();
 }
 
+// Two-level deterministic grid reduction.  Each CTA has written its nslot
+// partial sums to part[blockIdx.x * nslot + slot] (all threads done); the last
+// CTA of each group of kRedGroup consecutive CTAs sums its group in CTA order
+// into gpart, and the last group leader sums the groups in order into `out`
+// (nslot doubles, shared memory).  Returns true in exactly that final CTA.
+// Counters must be zero on entry; they are zero again on exit.
+constexpr int kRedGroup = 32;
+
+struct GridRed {
+  double* part;        // nblk x nslot
+  double* gpart;       // ceil(nblk / kRedGroup) x nslot
+  unsigned int* gcnt;  // ceil(nblk / kRedGroup) counters
+  unsigned int* tcnt;  // 1 counter
+};
+
+// In one CTA of kThreads threads: out[slot] = sum over q < nq of
+// src[q * nslot + slot] for every slot < nslot.  P threads share a slot (each
+// sums a fixed strided subset of q in order), then a fixed shared-memory tree
+// combines them: the result does not depend on scheduling.  Ends synced.
+__device__ __forceinline__ void block_sum_columns(const double* __restrict__ src, int nq, int nslot,
+                                                  double* out) {
+  __shared__ double buf[kThreads];
+  const int T = kThreads, t = threadIdx.x;
+  int P = 1;
+  if (nslot > 32) {
+    P = 8;
+  } else {
+    while (P * 2 * nslot <= T) P *= 2;
+  }
+  const int C = T / P;  // slots per round
+  for (int c0 = 0; c0 < nslot; c0 += C) {
+    const int slot = c0 + t % C, p = t / C;
+    double acc = 0.0;
+    if (slot < nslot) {
+      int q = p;
+      for (; q + 3 * P < nq; q += 4 * P) {
+        const double v0 = __ldcg(src + (size_t)q * nslot + slot);
+        const double v1 = __ldcg(src + (size_t)(q + P) * nslot + slot);
+        const double v2 = __ldcg(src + (size_t)(q + 2 * P) * nslot + slot);
+        const double v3 = __ldcg(src + (size_t)(q + 3 * P) * nslot + slot);
+        acc += v0;
+        acc += v1;
+        acc += v2;
+        acc += v3;
+      }
+      for (; q < nq; q += P) acc += __ldcg(src + (size_t)q * nslot + slot);
+    }
+    buf[t] = acc;
+    __syncthreads();
+    for (int h = P / 2; h >= 1; h >>= 1) {
+      if (p < h) buf[t] += buf[t + h * C];
+      __syncthreads();
+    }
+    if (p == 0 && slot < nslot) out[slot] = buf[t];
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ bool grid_reduce(const GridRed& r, int nslot, double* out) {
+  __shared__ int role;
+  const int nblk = gridDim.x, b = blockIdx.x;
+  const int g = b / kRedGroup, g0 = g * kRedGroup;
+  const int gs = min(kRedGroup, nblk - g0);
+  const int ngroups = (nblk + kRedGroup - 1) / kRedGroup;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) role = (atomicAdd(&r.gcnt[g], 1u) == (unsigned)gs - 1) ? 1 : 0;
+  __syncthreads();
+  if (!role) return false;
+  __threadfence();
+  block_sum_columns(r.part + (size_t)g0 * nslot, gs, nslot, r.gpart + (size_t)g * nslot);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    r.gcnt[g] = 0u;
+    role = (atomicAdd(r.tcnt, 1u) == (unsigned)ngroups - 1) ? 2 : 0;
+  }
+  __syncthreads();
+  if (role != 2) return false;
+  __threadfence();
+  block_sum_columns(r.gpart, ngroups, nslot, out);
+  if (threadIdx.x == 0) *r.tcnt = 0u;
+  __syncthreads();
+  return true;
+}
+
+inline int red_groups(int nblk) { return (nblk + kRedGroup - 1) / kRedGroup; }
+
 // In one CTA: out[slot] = sum over b < nblk of part[b * nslot + slot], for
 // every slot < nslot.  One warp per slot, lanes stride over the partials, then
 // a fixed shuffle tree: the result does not depend on scheduling.  Ends with
@@ -155,12 +243,12 @@ __device__ __forceinline__ void reduce_slots(const double* __restrict__ part, in
     double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
     int b = lane;
     for (; b + 96 < nblk; b += 128) {
-      a0 += part[(size_t)b * nslot + slot];
-      a1 += part[(size_t)(b + 32) * nslot + slot];
-      a2 += part[(size_t)(b + 64) * nslot + slot];
-      a3 += part[(size_t)(b + 96) * nslot + slot];
+      a0 += __ldcg(part + (size_t)b * nslot + slot);
+      a1 += __ldcg(part + (size_t)(b + 32) * nslot + slot);
+      a2 += __ldcg(part + (size_t)(b + 64) * nslot + slot);
+      a3 += __ldcg(part + (size_t)(b + 96) * nslot + slot);
     }
-    for (; b < nblk; b += 32) a0 += part[(size_t)b * nslot + slot];
+    for (; b < nblk; b += 32) a0 += __ldcg(part + (size_t)b * nslot + slot);
     double acc = warp_sum((a0 + a1) + (a2 + a3));
     if (lane == 0) out[slot] = acc;
   }

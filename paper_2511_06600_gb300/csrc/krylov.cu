@@ -17,11 +17,13 @@
 // Krylov spaces of the definition.  Chain vectors are stored unnormalised
 // (u_j) with their inverse D-norms in `inv_nu`; kernels scale on the fly.
 //
-// Per step: an edge pass (segmented sums over each hyperedge's pins), a
-// vertex pass (segmented sums over each vertex's hyperedges, which also
-// archives x_{j-1} into V and reduces the Lanczos dot products), and an update
-// pass (x_j = y - projections, with its D-norm).  Every reduction is a
-// per-CTA partial followed by a fixed-order sum in the last CTA.
+// Layout: a chain block is row-major with the S starts of a row contiguous;
+// one thread owns a whole row (S values, vector loads).  Per step: an edge
+// pass (thread per hyperedge; hyperedges with more than kBig pins are summed
+// by their whole warp), a vertex pass (thread per vertex, same split), which
+// also archives x_{j-1} into V and reduces the Lanczos dots, and an update
+// pass (thread per row) forming x_j and its D-norm.  Every reduction is a
+// per-CTA partial followed by a two-level fixed-order sum (grid_reduce).
 #include "internal.h"
 
 namespace hef {
@@ -29,11 +31,11 @@ namespace hef {
 namespace {
 
 constexpr int kMaxS = 16;
-constexpr int kGridPerSm = 4;
+constexpr int kBig = 16;  // segments longer than this are summed by a warp
 
 template <typename T>
 struct KView {
-  int n, m, S, lgS;
+  int n, m;
   T* Yc;  // n x S
   T* Bc[2];
   T* Yb;  // (n+m) x S
@@ -41,339 +43,466 @@ struct KView {
   T* se;  // m x S
   double* inv_nu;  // (k+1) x 2S
   double* coef;    // (k+1) x 2S x 4: [ct, ct2, alpha, beta]
-  double* part_e;  // grid x S x 4
-  double* part_n;  // grid x S x 8
-  double* part_u;  // grid x 2S
-  double* part_s;  // grid x 3S (start)
-  unsigned int* counter;
-  double tol;  // breakdown threshold on the D-norm of a new vector
+  double* te;      // 3S: star edge-row dots of the current step
+  GridRed red;     // reduction scratch shared by all kernels (serialised)
+  double tol;      // breakdown threshold on the D-norm of a new vector
 };
 
-// Per-CTA partials of NQ quantities per column s (thread layout: s = idx mod S).
-// part[block][s][q].
-template <int NQ, typename A>
-__device__ __forceinline__ void partials_per_s(const A (&v)[NQ], int S, double* part) {
-  __shared__ double red[NQ][kThreads / 32][kMaxS];
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    A x = v[q];
-    for (int o = 16; o >= S; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if (lane < S) red[q][wid][lane] = (double)x;
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < NQ * S; t += blockDim.x) {
-    const int s = t / NQ, q = t % NQ;
-    double acc = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[q][w][s];
-    part[(size_t)blockIdx.x * NQ * S + t] = acc;
-  }
-  __syncthreads();
+// ---------------------------------------------------------------- row I/O
+
+// a[i] for i in {0, 1} without indexing the array at run time (which would
+// copy the kernel argument to local memory)
+template <typename P>
+__device__ __forceinline__ P pick2(P const (&a)[2], int i) {
+  return i ? a[1] : a[0];
 }
 
-// ----------------------------------------------------------------- start vectors
+template <typename T, int S>
+__device__ __forceinline__ void ldrow(const T* __restrict__ p, T (&v)[S]) {
+  if constexpr (sizeof(T) == 4 && S % 4 == 0) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int i = 0; i < S / 4; ++i) {
+      const float4 f = __ldg(q + i);
+      v[4 * i] = f.x, v[4 * i + 1] = f.y, v[4 * i + 2] = f.z, v[4 * i + 3] = f.w;
+    }
+  } else if constexpr (sizeof(T) == 8 && S % 2 == 0) {
+    const double2* q = reinterpret_cast<const double2*>(p);
+#pragma unroll
+    for (int i = 0; i < S / 2; ++i) {
+      const double2 f = __ldg(q + i);
+      v[2 * i] = f.x, v[2 * i + 1] = f.y;
+    }
+  } else {
+#pragma unroll
+    for (int s = 0; s < S; ++s) v[s] = __ldg(p + s);
+  }
+}
 
-// D-weighted dots of the raw starts with the trivial vectors.
-template <typename T>
-__global__ void k_start_dots(IncView g, KView<T> kv, const double* __restrict__ x0c,
-                             const double* __restrict__ x0b) {
-  if (g.status[0]) return;
-  const int S = kv.S, lgS = kv.lgS;
-  double acc[3] = {0.0, 0.0, 0.0};  // clique t, star vertex t, star edge t
-  const long long nc = (long long)g.n << lgS;
-  const long long nb = (long long)(g.n + g.m) << lgS;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nc + nb;
-       idx += (long long)gridDim.x * blockDim.x) {
-    if (idx < nc) {
-      const int v = (int)(idx >> lgS);
-      acc[0] += g.dc[v] * x0c[idx];
-    } else {
-      const long long j = idx - nc;
-      const int r = (int)(j >> lgS), s = (int)(j & (S - 1));
-      if (r < g.n) {
-        acc[1] += g.db[r] * x0b[j];
-      } else {
-        const int i = r - g.n;
-        acc[2] += g.ew[i] * x0b[((long long)(g.n + g.perm[i]) << lgS) + s];
-      }
+template <typename T, int S>
+__device__ __forceinline__ void strow(T* __restrict__ p, const T (&v)[S]) {
+  if constexpr (sizeof(T) == 4 && S % 4 == 0) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < S / 4; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else if constexpr (sizeof(T) == 8 && S % 2 == 0) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int i = 0; i < S / 2; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int s = 0; s < S; ++s) p[s] = v[s];
+  }
+}
+
+// Per-CTA partials of NQ*S values (slot q*S + s) written to part[block].
+template <int NQ, int S, typename A>
+__device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* part) {
+  __shared__ double red[kThreads / 32][NQ * S];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      A x = v[q][s];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0) red[wid][q * S + s] = (double)x;
+    }
+  __syncthreads();
+  for (int t = threadIdx.x; t < NQ * S; t += blockDim.x) {
+    double acc = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][t];
+    part[(size_t)blockIdx.x * NQ * S + t] = acc;
+  }
+}
+
+// Sum of the S-rows of `X` over the entries [a, b) of an index list `idx`
+// (X row = base + idx[t] * S) with weights, split between one thread (short
+// lists) and its whole warp (lists longer than kBig, handled one at a time).
+// W(t) gives the weight of entry t.  Result in acc (the owner thread).
+template <typename T, int S, typename RowOf, typename WeightOf>
+__device__ __forceinline__ void seg_sum(bool valid, int a, int b, RowOf row_of, WeightOf w_of,
+                                        T (&acc)[S]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < S; ++s) acc[s] = 0;
+  const bool big = valid && (b - a) > kBig;
+  if (valid && !big) {
+    int t = a;
+    for (; t + 2 <= b; t += 2) {
+      T v0[S], v1[S];
+      ldrow<T, S>(row_of(t), v0);
+      ldrow<T, S>(row_of(t + 1), v1);
+      const T w0 = w_of(t), w1 = w_of(t + 1);
+#pragma unroll
+      for (int s = 0; s < S; ++s) acc[s] += w0 * v0[s] + w1 * v1[s];
+    }
+    if (t < b) {
+      T v0[S];
+      ldrow<T, S>(row_of(t), v0);
+      const T w0 = w_of(t);
+#pragma unroll
+      for (int s = 0; s < S; ++s) acc[s] += w0 * v0[s];
     }
   }
-  partials_per_s<3, double>(acc, S, kv.part_s);
-  if (last_block_done(kv.counter)) {
-    __shared__ double tot[3 * kMaxS];
-    reduce_slots(kv.part_s, gridDim.x, 3 * S, tot);
+  unsigned bigmask = __ballot_sync(0xffffffffu, big);
+  while (bigmask) {
+    const int src = __ffs(bigmask) - 1;
+    bigmask &= bigmask - 1;
+    const int ba = __shfl_sync(0xffffffffu, a, src), bb = __shfl_sync(0xffffffffu, b, src);
+    T part[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) part[s] = 0;
+    for (int t = ba + lane; t < bb; t += 32) {
+      T v0[S];
+      ldrow<T, S>(row_of(t), v0);
+      const T w0 = w_of(t);
+#pragma unroll
+      for (int s = 0; s < S; ++s) part[s] += w0 * v0[s];
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) part[s] += __shfl_xor_sync(0xffffffffu, part[s], o);
+    }
+    if (lane == src) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) acc[s] = part[s];
+    }
+  }
+}
+
+// ---------------------------------------------------------------- start vectors
+
+// D-weighted dots of the raw starts with the trivial vectors -> coef[0].
+// Rows: [0, n) clique, [n, 2n) star vertices, [2n, 2n+m) star hyperedges.
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, KView<T> kv,
+                                                         const double* __restrict__ x0c,
+                                                         const double* __restrict__ x0b) {
+  if (g.status[0]) return;
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[3][S];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[q][s] = 0.0;
+  if (r < g.n) {
+    const double d = g.dc[r];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[0][s] = d * x0c[r * S + s];
+  } else if (r < 2ll * g.n) {
+    const long long v = r - g.n;
+    const double d = g.db[v];
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[1][s] = d * x0b[v * S + s];
+  } else if (r < 2ll * g.n + g.m) {
+    const int i = (int)(r - 2ll * g.n);
+    const double d = g.ew[i];
+    const long long src = (long long)(g.n + g.perm[i]) * S;
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[2][s] = d * x0b[src + s];
+  }
+  block_partials_qs<3, S, double>(acc, kv.red.part);
+  __shared__ double tot[3 * kMaxS];
+  if (grid_reduce(kv.red, 3 * S, tot)) {
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
-      double* cc = kv.coef + (size_t)(0 * 2 * S + s) * 4;
-      double* cb = kv.coef + (size_t)(0 * 2 * S + S + s) * 4;
-      cc[0] = g.totals[0] > 0 ? tot[s * 3 + 0] / g.totals[0] : 0.0;
+      double* cc = kv.coef + (size_t)s * 4;
+      double* cb = kv.coef + (size_t)(S + s) * 4;
+      cc[0] = g.totals[0] > 0 ? tot[0 * S + s] / g.totals[0] : 0.0;
       cc[1] = 0.0;
-      cb[0] = g.totals[1] > 0 ? tot[s * 3 + 1] / g.totals[1] : 0.0;
-      cb[1] = g.totals[2] > 0 ? tot[s * 3 + 2] / g.totals[2] : 0.0;
+      cb[0] = g.totals[1] > 0 ? tot[1 * S + s] / g.totals[1] : 0.0;
+      cb[1] = g.totals[2] > 0 ? tot[2 * S + s] / g.totals[2] : 0.0;
     }
   }
 }
 
 // x_0 = start minus its trivial components; D-norm -> inv_nu[0].
-template <typename T>
-__global__ void k_start_write(IncView g, KView<T> kv, const double* __restrict__ x0c,
-                              const double* __restrict__ x0b) {
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_start_write(IncView g, KView<T> kv,
+                                                          const double* __restrict__ x0c,
+                                                          const double* __restrict__ x0b) {
   if (g.status[0]) return;
-  const int S = kv.S, lgS = kv.lgS;
-  double acc[2] = {0.0, 0.0};
-  const long long nc = (long long)g.n << lgS;
-  const long long nb = (long long)(g.n + g.m) << lgS;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nc + nb;
-       idx += (long long)gridDim.x * blockDim.x) {
-    if (idx < nc) {
-      const int v = (int)(idx >> lgS), s = (int)(idx & (S - 1));
-      const double d = g.dc[v];
-      const double u = x0c[idx] - (d > 0 ? kv.coef[(size_t)s * 4 + 0] : 0.0);
-      kv.Bc[0][idx] = (T)u;
-      acc[0] += d * u * u;
-    } else {
-      const long long j = idx - nc;
-      const int r = (int)(j >> lgS), s = (int)(j & (S - 1));
-      const double* cb = kv.coef + (size_t)(S + s) * 4;
-      double d, u;
-      if (r < g.n) {
-        d = g.db[r];
-        u = x0b[j] - (d > 0 ? cb[0] : 0.0);
-      } else {
-        const int i = r - g.n;
-        d = g.ew[i];
-        u = x0b[((long long)(g.n + g.perm[i]) << lgS) + s] - (d > 0 ? cb[1] : 0.0);
-      }
-      kv.Bb[0][j] = (T)u;
-      acc[1] += d * u * u;
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  double acc[2][S];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[q][s] = 0.0;
+  if (r < g.n) {
+    const double d = g.dc[r];
+    T u[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const double x = x0c[r * S + s] - (d > 0 ? kv.coef[(size_t)s * 4] : 0.0);
+      u[s] = (T)x;
+      acc[0][s] = d * x * x;
     }
+    strow<T, S>(kv.Bc[0] + r * S, u);
+  } else if (r < 2ll * g.n + g.m) {
+    const long long rb = r - g.n;  // star row
+    double d, t;
+    long long src;
+    if (rb < g.n) {
+      d = g.db[rb];
+      src = rb * S;
+      t = 0;
+    } else {
+      const int i = (int)(rb - g.n);
+      d = g.ew[i];
+      src = (long long)(g.n + g.perm[i]) * S;
+      t = 1;
+    }
+    T u[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const double* cb = kv.coef + (size_t)(S + s) * 4;
+      const double x = x0b[src + s] - (d > 0 ? (t == 0 ? cb[0] : cb[1]) : 0.0);
+      u[s] = (T)x;
+      acc[1][s] = d * x * x;
+    }
+    strow<T, S>(kv.Bb[0] + rb * S, u);
   }
-  partials_per_s<2, double>(acc, S, kv.part_s);
-  if (last_block_done(kv.counter)) {
-    __shared__ double tot[2 * kMaxS];
-    reduce_slots(kv.part_s, gridDim.x, 2 * S, tot);
+  block_partials_qs<2, S, double>(acc, kv.red.part);
+  __shared__ double tot[2 * kMaxS];
+  if (grid_reduce(kv.red, 2 * S, tot)) {
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
-      const int op = c / S, s = c % S;
-      const double nu2 = tot[s * 2 + op];
+      const double nu2 = tot[c];  // slot op * S + s == chain c
       kv.inv_nu[c] = nu2 > 0.0 ? 1.0 / sqrt(nu2) : 0.0;
     }
   }
 }
 
-// ----------------------------------------------------------------- one Krylov step
+// ---------------------------------------------------------------- one Krylov step
 
-// Edge pass of step j: clique pin sums s_e, star rows (M_b x)_e and the
-// D-weighted dots of the star edge rows.
-template <typename T>
-__global__ void k_edge_pass(IncView g, KView<T> kv, int j) {
+// Edge pass of step j (thread per hyperedge): clique pin sums s_e, star rows
+// (M_b x)_e, and the D-weighted dots of the star hyperedge rows -> te.
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, KView<T> kv, int j) {
   if (g.status[0]) return;
-  const int S = kv.S, lgS = kv.lgS;
-  const T* __restrict__ curc = kv.Bc[(j - 1) & 1];
-  const T* __restrict__ curb = kv.Bb[(j - 1) & 1];
-  const T* __restrict__ prvb = j >= 3 ? kv.Bb[j & 1] : nullptr;
+  const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
+  const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
+  const T* __restrict__ prvb = j >= 3 ? pick2(kv.Bb, j & 1) : nullptr;
   const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
   const double* nup = j >= 2 ? kv.inv_nu + (size_t)(j - 2) * 2 * S : nullptr;
-  T acc[4] = {0, 0, 0, 0};  // sum w y, sum w y x_cur, sum w y x_prv, sum w y^2
-  const long long work = (long long)g.m << lgS;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < work;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(idx >> lgS), s = (int)(idx & (S - 1));
-    const int a = g.ceptr[i], b = g.ceptr[i + 1];
-    T sc = 0, sb = 0;
-    int t = a;
-    for (; t + 4 <= b; t += 4) {  // four independent gathers in flight
-      const long long p0 = g.cpins[t], p1 = g.cpins[t + 1], p2 = g.cpins[t + 2],
-                      p3 = g.cpins[t + 3];
-      const T c0 = curc[(p0 << lgS) + s], c1 = curc[(p1 << lgS) + s];
-      const T c2 = curc[(p2 << lgS) + s], c3 = curc[(p3 << lgS) + s];
-      const T b0 = curb[(p0 << lgS) + s], b1 = curb[(p1 << lgS) + s];
-      const T b2 = curb[(p2 << lgS) + s], b3 = curb[(p3 << lgS) + s];
-      sc += (c0 + c1) + (c2 + c3);
-      sb += (b0 + b1) + (b2 + b3);
-    }
-    for (; t < b; ++t) {
-      const long long p = g.cpins[t];
-      sc += curc[(p << lgS) + s];
-      sb += curb[(p << lgS) + s];
-    }
-    const T ic = (T)nu0[s], ib = (T)nu0[S + s];
-    kv.se[idx] = sc * ic;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = e < g.m;
+  int a = 0, b = 0;
+  if (valid) a = g.ceptr[e], b = g.ceptr[e + 1];
+  const int32_t* __restrict__ pins = g.cpins;
+  T sc[S], sb[S];
+  seg_sum<T, S>(valid, a, b, [&](int t) { return curc + (long long)pins[t] * S; },
+                [&](int) { return (T)1; }, sc);
+  seg_sum<T, S>(valid, a, b, [&](int t) { return curb + (long long)pins[t] * S; },
+                [&](int) { return (T)1; }, sb);
+  T acc[3][S];
+#pragma unroll
+  for (int q = 0; q < 3; ++q)
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[q][s] = 0;
+  if (valid) {
     const int k = b - a;
-    const long long row = ((long long)(g.n + i) << lgS) + s;
-    T ye = 0;
-    if (k >= 2) {
-      ye = sb * ib / (T)k;
-      const T we = (T)g.ew[i];
-      const T xc = curb[row] * ib;
-      const T xp = prvb ? prvb[row] * (T)nup[S + s] : (T)0;
-      acc[0] += we * ye;
-      acc[1] += we * ye * xc;
-      acc[2] += we * ye * xp;
-      acc[3] += we * ye * ye;
+    T ye[S], sev[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      sev[s] = sc[s] * (T)nu0[s];
+      ye[s] = k >= 2 ? sb[s] * (T)nu0[S + s] / (T)k : (T)0;
     }
-    kv.Yb[row] = ye;
+    strow<T, S>(kv.se + (long long)e * S, sev);
+    const long long row = (long long)(g.n + e) * S;
+    strow<T, S>(kv.Yb + row, ye);
+    if (k >= 2) {
+      const T we = (T)g.ew[e];
+      T xc[S], xp[S];
+      ldrow<T, S>(curb + row, xc);
+      if (prvb) ldrow<T, S>(prvb + row, xp);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const T wy = we * ye[s];
+        acc[0][s] = wy;
+        acc[1][s] = wy * xc[s] * (T)nu0[S + s];
+        acc[2][s] = prvb ? wy * xp[s] * (T)nup[S + s] : (T)0;
+      }
+    }
   }
-  partials_per_s<4, T>(acc, S, kv.part_e);
+  block_partials_qs<3, S, T>(acc, kv.red.part);
+  __shared__ double tot[3 * kMaxS];
+  if (grid_reduce(kv.red, 3 * S, tot)) {
+    for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) kv.te[t] = tot[t];
+  }
 }
 
-// Vertex pass of step j: (M_c x)_v and (M_b x)_v, archive of x_{j-1} into V,
-// and the Lanczos coefficients (last CTA, with the edge pass partials).
-template <typename T>
-__global__ void k_node_pass(IncView g, KView<T> kv, int j, int grid_e, T* __restrict__ V,
-                            long long ldv) {
+// Vertex pass of step j (thread per vertex): (M_c x)_v and (M_b x)_v, archive
+// of x_{j-1} into V, and the Lanczos coefficients of step j (final CTA, with
+// the star hyperedge-row dots of the edge pass).
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, KView<T> kv, int j,
+                                                        T* __restrict__ V, long long ldv) {
   if (g.status[0]) return;
-  const int S = kv.S, lgS = kv.lgS;
-  const T* __restrict__ curc = kv.Bc[(j - 1) & 1];
-  const T* __restrict__ curb = kv.Bb[(j - 1) & 1];
-  const T* __restrict__ prvc = j >= 3 ? kv.Bc[j & 1] : nullptr;
-  const T* __restrict__ prvb = j >= 3 ? kv.Bb[j & 1] : nullptr;
+  const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
+  const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
+  const T* __restrict__ prvc = j >= 3 ? pick2(kv.Bc, j & 1) : nullptr;
+  const T* __restrict__ prvb = j >= 3 ? pick2(kv.Bb, j & 1) : nullptr;
   const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
   const double* nup = j >= 2 ? kv.inv_nu + (size_t)(j - 2) * 2 * S : nullptr;
-  T acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-  const long long work = (long long)g.n << lgS;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < work;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(idx >> lgS), s = (int)(idx & (S - 1));
-    T accc = 0, wsum = 0, accb = 0;
-    for (int t = g.vptr[v]; t < g.vptr[v + 1]; ++t) {
-      const int e = g.vedge[t];
-      const T wh = (T)g.ewh[e];
-      accc += wh * kv.se[((long long)e << lgS) + s];
-      wsum += wh;
-      accb += (T)g.ez[e] * curb[((long long)(g.n + e) << lgS) + s];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = v < g.n;
+  int a = 0, b = 0;
+  if (valid) a = g.vptr[v], b = g.vptr[v + 1];
+  const int32_t* __restrict__ ve = g.vedge;
+  const T* __restrict__ se = kv.se;
+  T accc[S], accb[S];
+  seg_sum<T, S>(valid, a, b, [&](int t) { return se + (long long)ve[t] * S; },
+                [&](int t) { return (T)g.ewh[ve[t]]; }, accc);
+  seg_sum<T, S>(valid, a, b, [&](int t) { return curb + (long long)(g.n + ve[t]) * S; },
+                [&](int t) { return (T)g.ez[ve[t]]; }, accb);
+  T acc[6][S];
+#pragma unroll
+  for (int q = 0; q < 6; ++q)
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[q][s] = 0;
+  if (valid) {
+    T wsum = 0;
+    for (int t = a; t < b; ++t) wsum += (T)g.ewh[ve[t]];
+    T xv[S], xb[S], yc[S], yb[S], xpc[S], xpb[S];
+    ldrow<T, S>(curc + (long long)v * S, xv);
+    ldrow<T, S>(curb + (long long)v * S, xb);
+    if (prvc) {
+      ldrow<T, S>(prvc + (long long)v * S, xpc);
+      ldrow<T, S>(prvb + (long long)v * S, xpb);
     }
-    const T ic = (T)nu0[s], ib = (T)nu0[S + s];
-    const T xv = curc[idx] * ic;
-    const T xb = curb[idx] * ib;
-    const T yc = (T)g.inv_dc[v] * (accc - wsum * xv);
-    const T yb = (T)g.inv_db[v] * accb * ib;
-    kv.Yc[idx] = yc;
-    kv.Yb[idx] = yb;
+    const T idc = (T)g.inv_dc[v], idb = (T)g.inv_db[v];
+    const T dcv = (T)g.dc[v], dbv = (T)g.db[v];
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      xv[s] *= (T)nu0[s];
+      xb[s] *= (T)nu0[S + s];
+      yc[s] = idc * (accc[s] - wsum * xv[s]);
+      yb[s] = idb * accb[s] * (T)nu0[S + s];
+      const T pc = prvc ? xpc[s] * (T)nup[s] : (T)0;
+      const T pb = prvb ? xpb[s] * (T)nup[S + s] : (T)0;
+      acc[0][s] = dcv * yc[s];
+      acc[1][s] = dcv * yc[s] * xv[s];
+      acc[2][s] = dcv * yc[s] * pc;
+      acc[3][s] = dbv * yb[s];
+      acc[4][s] = dbv * yb[s] * xb[s];
+      acc[5][s] = dbv * yb[s] * pb;
+    }
+    strow<T, S>(kv.Yc + (long long)v * S, yc);
+    strow<T, S>(kv.Yb + (long long)v * S, yb);
     if (j >= 2) {  // x_{j-1} is basis vector j-1 -> column block j-2
       T* row = V + (long long)v * ldv + (long long)(j - 2) * 2 * S;
-      row[s] = xv;
-      row[S + s] = xb;
+      strow<T, S>(row, xv);
+      strow<T, S>(row + S, xb);
     }
-    const T dcv = (T)g.dc[v], dbv = (T)g.db[v];
-    const T xpc = prvc ? prvc[idx] * (T)nup[s] : (T)0;
-    const T xpb = prvb ? prvb[idx] * (T)nup[S + s] : (T)0;
-    acc[0] += dcv * yc;
-    acc[1] += dcv * yc * xv;
-    acc[2] += dcv * yc * xpc;
-    acc[3] += dcv * yc * yc;
-    acc[4] += dbv * yb;
-    acc[5] += dbv * yb * xb;
-    acc[6] += dbv * yb * xpb;
-    acc[7] += dbv * yb * yb;
   }
-  partials_per_s<8, T>(acc, S, kv.part_n);
-  if (last_block_done(kv.counter)) {
-    __shared__ double tn[8 * kMaxS];
-    __shared__ double te[4 * kMaxS];
-    reduce_slots(kv.part_n, gridDim.x, 8 * S, tn);
-    reduce_slots(kv.part_e, grid_e, 4 * S, te);
+  block_partials_qs<6, S, T>(acc, kv.red.part);
+  __shared__ double tn[6 * kMaxS];
+  if (grid_reduce(kv.red, 6 * S, tn)) {
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
       const int op = c / S, s = c % S;
       double* cf = kv.coef + ((size_t)j * 2 * S + c) * 4;
       if (op == 0) {
-        cf[0] = g.totals[0] > 0 ? tn[s * 8 + 0] / g.totals[0] : 0.0;
+        cf[0] = g.totals[0] > 0 ? tn[0 * S + s] / g.totals[0] : 0.0;
         cf[1] = 0.0;
-        cf[2] = j >= 2 ? tn[s * 8 + 1] : 0.0;
-        cf[3] = j >= 3 ? tn[s * 8 + 2] : 0.0;
+        cf[2] = j >= 2 ? tn[1 * S + s] : 0.0;
+        cf[3] = j >= 3 ? tn[2 * S + s] : 0.0;
       } else {
-        cf[0] = g.totals[1] > 0 ? tn[s * 8 + 4] / g.totals[1] : 0.0;
-        cf[1] = g.totals[2] > 0 ? te[s * 4 + 0] / g.totals[2] : 0.0;
-        cf[2] = j >= 2 ? tn[s * 8 + 5] + te[s * 4 + 1] : 0.0;
-        cf[3] = j >= 3 ? tn[s * 8 + 6] + te[s * 4 + 2] : 0.0;
+        cf[0] = g.totals[1] > 0 ? tn[3 * S + s] / g.totals[1] : 0.0;
+        cf[1] = g.totals[2] > 0 ? kv.te[0 * S + s] / g.totals[2] : 0.0;
+        cf[2] = j >= 2 ? tn[4 * S + s] + kv.te[1 * S + s] : 0.0;
+        cf[3] = j >= 3 ? tn[5 * S + s] + kv.te[2 * S + s] : 0.0;
       }
     }
   }
 }
 
-// Update pass of step j: u_j = y - trivial part - alpha x_{j-1} - beta x_{j-2}
-// (written over x_{j-2}'s buffer) and its D-norm -> inv_nu[j].
-template <typename T>
-__global__ void k_update(IncView g, KView<T> kv, int j) {
+// Update pass of step j (thread per row): u_j = y - trivial part
+// - alpha x_{j-1} - beta x_{j-2} (written over x_{j-2}'s buffer) and its
+// D-norm -> inv_nu[j].  Rows: [0, n) clique, [n, 2n + m) star.
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_update(IncView g, KView<T> kv, int j) {
   if (g.status[0]) return;
-  const int S = kv.S, lgS = kv.lgS;
-  const T* __restrict__ curc = kv.Bc[(j - 1) & 1];
-  const T* __restrict__ curb = kv.Bb[(j - 1) & 1];
-  T* newc = kv.Bc[j & 1];  // holds x_{j-2} (read first when j >= 3)
-  T* newb = kv.Bb[j & 1];
   const bool has_prv = j >= 3;
   const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
   const double* nup = has_prv ? kv.inv_nu + (size_t)(j - 2) * 2 * S : nullptr;
   const double* cf = kv.coef + (size_t)j * 2 * S * 4;
-  T acc[2] = {0, 0};
-  const long long nc = (long long)g.n << lgS;
-  const long long nb = (long long)(g.n + g.m) << lgS;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nc + nb;
-       idx += (long long)gridDim.x * blockDim.x) {
-    if (idx < nc) {
-      const int v = (int)(idx >> lgS), s = (int)(idx & (S - 1));
-      const double* c = cf + (size_t)s * 4;
-      const T d = (T)g.dc[v];
-      const T xc = curc[idx] * (T)nu0[s];
-      const T xp = has_prv ? newc[idx] * (T)nup[s] : (T)0;
-      const T u = kv.Yc[idx] - (d > 0 ? (T)c[0] : (T)0) - (T)c[2] * xc - (T)c[3] * xp;
-      newc[idx] = u;
-      acc[0] += d * u * u;
-    } else {
-      const long long jj = idx - nc;
-      const int r = (int)(jj >> lgS), s = (int)(jj & (S - 1));
-      const double* c = cf + (size_t)(S + s) * 4;
-      T d, t;
-      if (r < g.n) {
-        d = (T)g.db[r];
-        t = d > 0 ? (T)c[0] : (T)0;
-      } else {
-        d = (T)g.ew[r - g.n];
-        t = d > 0 ? (T)c[1] : (T)0;
-      }
-      const T xc = curb[jj] * (T)nu0[S + s];
-      const T xp = has_prv ? newb[jj] * (T)nup[S + s] : (T)0;
-      const T u = kv.Yb[jj] - t - (T)c[2] * xc - (T)c[3] * xp;
-      newb[jj] = u;
-      acc[1] += d * u * u;
+  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  T acc[2][S];
+#pragma unroll
+  for (int q = 0; q < 2; ++q)
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[q][s] = 0;
+  if (r < 2ll * g.n + g.m) {
+    const bool clique = r < g.n;
+    const int op = clique ? 0 : 1;
+    T dsq[S];
+    const long long rr = clique ? r : r - g.n;
+    const T* cur = clique ? pick2(kv.Bc, (j - 1) & 1) : pick2(kv.Bb, (j - 1) & 1);
+    T* nw = clique ? pick2(kv.Bc, j & 1) : pick2(kv.Bb, j & 1);
+    const T* Y = clique ? kv.Yc : kv.Yb;
+    T d;
+    int tsel;
+    if (clique) d = (T)g.dc[rr], tsel = 0;
+    else if (rr < g.n) d = (T)g.db[rr], tsel = 0;
+    else d = (T)g.ew[rr - g.n], tsel = 1;
+    T y[S], xc[S], xp[S], u[S];
+    ldrow<T, S>(Y + rr * S, y);
+    ldrow<T, S>(cur + rr * S, xc);
+    if (has_prv) ldrow<T, S>(nw + rr * S, xp);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const double* c = cf + (size_t)(op * S + s) * 4;
+      const T t = d > 0 ? (T)c[tsel] : (T)0;
+      const T p = has_prv ? xp[s] * (T)nup[op * S + s] : (T)0;
+      u[s] = y[s] - t - (T)c[2] * (xc[s] * (T)nu0[op * S + s]) - (T)c[3] * p;
+      dsq[s] = d * u[s] * u[s];
+    }
+    strow<T, S>(nw + rr * S, u);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      if (clique) acc[0][s] = dsq[s];
+      else acc[1][s] = dsq[s];
     }
   }
-  partials_per_s<2, T>(acc, S, kv.part_u);
-  if (last_block_done(kv.counter)) {
-    __shared__ double tot[2 * kMaxS];
-    reduce_slots(kv.part_u, gridDim.x, 2 * S, tot);
+  block_partials_qs<2, S, T>(acc, kv.red.part);
+  __shared__ double tot[2 * kMaxS];
+  if (grid_reduce(kv.red, 2 * S, tot)) {
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
-      const int op = c / S, s = c % S;
-      const double nu2 = tot[s * 2 + op];
+      const double nu2 = tot[c];
       const bool alive = nu0[c] > 0.0 && nu2 > kv.tol * kv.tol;
       kv.inv_nu[(size_t)j * 2 * S + c] = alive ? 1.0 / sqrt(nu2) : 0.0;
     }
   }
 }
 
-// Archive of the last chain vectors x_k into V.
-template <typename T>
-__global__ void k_archive_last(IncView g, KView<T> kv, int k, T* __restrict__ V, long long ldv) {
+// Archive of the last chain vectors x_k into V (thread per vertex).
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_archive_last(IncView g, KView<T> kv, int k,
+                                                           T* __restrict__ V, long long ldv) {
   if (g.status[0]) return;
-  const int S = kv.S, lgS = kv.lgS;
-  const T* curc = kv.Bc[k & 1];
-  const T* curb = kv.Bb[k & 1];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= g.n) return;
   const double* nu = kv.inv_nu + (size_t)k * 2 * S;
-  const long long work = (long long)g.n << lgS;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < work;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int v = (int)(idx >> lgS), s = (int)(idx & (S - 1));
-    T* row = V + (long long)v * ldv + (long long)(k - 1) * 2 * S;
-    row[s] = curc[idx] * (T)nu[s];
-    row[S + s] = curb[idx] * (T)nu[S + s];
-  }
+  T xc[S], xb[S];
+  ldrow<T, S>(pick2(kv.Bc, k & 1) + (long long)v * S, xc);
+  ldrow<T, S>(pick2(kv.Bb, k & 1) + (long long)v * S, xb);
+#pragma unroll
+  for (int s = 0; s < S; ++s) xc[s] *= (T)nu[s], xb[s] *= (T)nu[S + s];
+  T* row = V + (long long)v * ldv + (long long)(k - 1) * 2 * S;
+  strow<T, S>(row, xc);
+  strow<T, S>(row + S, xb);
 }
+
+inline int blocks_for(long long rows) { return (int)((rows + kThreads - 1) / kThreads); }
 
 template <typename T>
 size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>* kv) {
   Carver c(base);
-  const int grid = num_sms() * kGridPerSm;
+  const long long maxblk = blocks_for(2 * n + m);
   kv->n = (int)n;
   kv->m = (int)m;
-  kv->S = S;
   kv->Yc = c.take<T>(n * S);
   kv->Bc[0] = c.take<T>(n * S);
   kv->Bc[1] = c.take<T>(n * S);
@@ -383,12 +512,34 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->se = c.take<T>((m > 0 ? m : 1) * S);
   kv->inv_nu = c.take<double>((size_t)(k + 1) * 2 * S);
   kv->coef = c.take<double>((size_t)(k + 1) * 2 * S * 4);
-  kv->part_e = c.take<double>((size_t)grid * S * 4);
-  kv->part_n = c.take<double>((size_t)grid * S * 8);
-  kv->part_u = c.take<double>((size_t)grid * S * 2);
-  kv->part_s = c.take<double>((size_t)grid * S * 3);
-  kv->counter = c.take<unsigned int>(64);
+  kv->te = c.take<double>((size_t)3 * S);
+  kv->red.part = c.take<double>((size_t)maxblk * 6 * S);
+  kv->red.gpart = c.take<double>((size_t)red_groups((int)maxblk) * 6 * S);
+  kv->red.gcnt = c.take<unsigned int>(red_groups((int)maxblk) + 1);
+  kv->red.tcnt = c.take<unsigned int>(1);
   return c.bytes();
+}
+
+template <typename T, int S>
+hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, const double* x0b,
+                        T* V, long long ldv, KView<T>& kv, cudaStream_t st) {
+  IncView g = view(inc);
+  const long long n = inc->n, m = inc->m;
+  const int grid_all = blocks_for(2 * n + m);
+  const int grid_e = blocks_for(m > 0 ? m : 1);
+  const int grid_n = blocks_for(n);
+  HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, kv, x0c, x0b));
+  HEF_LAUNCH("k_start_write", st, k_start_write<T, S><<<grid_all, kThreads, 0, st>>>(g, kv, x0c, x0b));
+  HEF_CHECK_LAUNCH();
+  for (int j = 1; j <= k; ++j) {
+    HEF_LAUNCH("k_edge_pass", st, k_edge_pass<T, S><<<grid_e, kThreads, 0, st>>>(g, kv, j));
+    HEF_LAUNCH("k_node_pass", st, k_node_pass<T, S><<<grid_n, kThreads, 0, st>>>(g, kv, j, V, ldv));
+    HEF_LAUNCH("k_update", st, k_update<T, S><<<grid_all, kThreads, 0, st>>>(g, kv, j));
+    HEF_CHECK_LAUNCH();
+  }
+  HEF_LAUNCH("k_archive_last", st, k_archive_last<T, S><<<grid_n, kThreads, 0, st>>>(g, kv, k, V, ldv));
+  HEF_CHECK_LAUNCH();
+  return HEF_OK;
 }
 
 template <typename T>
@@ -396,30 +547,19 @@ hef_status run_krylov(const hef_incidence* inc, int k, int S, const double* x0c,
                       void* Vv, long long ldv, void* ws, cudaStream_t st) {
   KView<T> kv;
   carve_krylov<T>(ws, inc->n, inc->m, k, S, &kv);
-  int lgS = 0;
-  while ((1 << lgS) < S) ++lgS;
-  kv.lgS = lgS;
   kv.tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
+  const int ngr = red_groups(blocks_for(2 * inc->n + inc->m));
+  HEF_CHECK_CUDA(cudaMemsetAsync(kv.red.gcnt, 0, (ngr + 1) * sizeof(unsigned int), st));
+  HEF_CHECK_CUDA(cudaMemsetAsync(kv.red.tcnt, 0, sizeof(unsigned int), st));
   T* V = static_cast<T*>(Vv);
-  IncView g = view(inc);
-  const long long n = inc->n, m = inc->m;
-  HEF_CHECK_CUDA(cudaMemsetAsync(kv.counter, 0, 64 * sizeof(unsigned int), st));
-  const int grid_s = stride_grid((2 * n + m) * S, kGridPerSm);
-  HEF_LAUNCH("k_start_dots", st, k_start_dots<T><<<grid_s, kThreads, 0, st>>>(g, kv, x0c, x0b));
-  HEF_LAUNCH("k_start_write", st, k_start_write<T><<<grid_s, kThreads, 0, st>>>(g, kv, x0c, x0b));
-  HEF_CHECK_LAUNCH();
-  const int grid_e = stride_grid((m > 0 ? m : 1) * S, kGridPerSm);
-  const int grid_n = stride_grid(n * S, kGridPerSm);
-  const int grid_u = stride_grid((2 * n + m) * S, kGridPerSm);
-  for (int j = 1; j <= k; ++j) {
-    HEF_LAUNCH("k_edge_pass", st, k_edge_pass<T><<<grid_e, kThreads, 0, st>>>(g, kv, j));
-    HEF_LAUNCH("k_node_pass", st, k_node_pass<T><<<grid_n, kThreads, 0, st>>>(g, kv, j, grid_e, V, ldv));
-    HEF_LAUNCH("k_update", st, k_update<T><<<grid_u, kThreads, 0, st>>>(g, kv, j));
-    HEF_CHECK_LAUNCH();
+  switch (S) {
+    case 1: return run_krylov_s<T, 1>(inc, k, x0c, x0b, V, ldv, kv, st);
+    case 2: return run_krylov_s<T, 2>(inc, k, x0c, x0b, V, ldv, kv, st);
+    case 4: return run_krylov_s<T, 4>(inc, k, x0c, x0b, V, ldv, kv, st);
+    case 8: return run_krylov_s<T, 8>(inc, k, x0c, x0b, V, ldv, kv, st);
+    case 16: return run_krylov_s<T, 16>(inc, k, x0c, x0b, V, ldv, kv, st);
+    default: return set_error(HEF_ERR_UNSUPPORTED, "hef_krylov_basis: S must be 1, 2, 4, 8 or 16");
   }
-  HEF_LAUNCH("k_archive_last", st, k_archive_last<T><<<grid_n, kThreads, 0, st>>>(g, kv, k, V, ldv));
-  HEF_CHECK_LAUNCH();
-  return HEF_OK;
 }
 
 hef_status check_krylov_args(const hef_incidence* inc, int k, int S, int dtype, const char* fn) {

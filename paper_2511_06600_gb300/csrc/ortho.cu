@@ -212,14 +212,17 @@ __global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
     for (int q = threadIdx.x; q < W2; q += blockDim.x)
       if ((q >= j && q < K) || (q >= K && q <= K + j)) rowj[q] *= pinv;
     __syncthreads();
-    // eliminate column j from rows i > j: row_i -= R[j][i] * row_j
-    const int rows = K - j - 1;
-    const int cols = (K - j - 1) + (j + 1);  // left j+1..K-1, right 0..j
-    for (long long idx = threadIdx.x; idx < (long long)rows * cols; idx += blockDim.x) {
-      const int i = j + 1 + (int)(idx / cols);
-      const int q0 = (int)(idx % cols);
-      const int q = q0 < K - j - 1 ? j + 1 + q0 : K + (q0 - (K - j - 1));
-      W[(size_t)i * W2 + q] -= rowj[i] * rowj[q];
+    // eliminate column j from rows i > j: row_i -= R[j][i] * row_j over the
+    // K live columns (left j+1..K-1, right 0..j); warps over rows, lanes
+    // over columns
+    const int nleft = K - j - 1;
+    for (int i = j + 1 + (int)(threadIdx.x >> 5); i < K; i += (int)(blockDim.x >> 5)) {
+      const C r = rowj[i];
+      C* rowi = W + (size_t)i * W2;
+      for (int q0 = threadIdx.x & 31; q0 < K; q0 += 32) {
+        const int q = q0 < nleft ? j + 1 + q0 : K + (q0 - nleft);
+        rowi[q] -= r * rowj[q];
+      }
     }
     __syncthreads();
   }
@@ -278,11 +281,13 @@ __global__ void k_chol_series(const double* __restrict__ G, const double* __rest
   }
 }
 
-__global__ void k_rank(const int* kept, int K, int* rank) {
+// rank = number of kept columns, or -1 when a tensor-core wait timed out
+// (flag[1]).
+__global__ void k_rank(const int* kept, int K, const int* flag, int* rank) {
   if (threadIdx.x == 0) {
     int r = 0;
     for (int j = 0; j < K; ++j) r += kept[j];
-    *rank = r;
+    *rank = flag[1] ? -1 : r;
   }
 }
 
@@ -386,6 +391,7 @@ struct OrthoWs {
   int* kept;
   int* rank;
   int* flag;
+  float* tcs;  // tensor-core apply scratch (FP32 form)
   int nchunk;
   int rows_per_chunk;
   int ngroups;
@@ -404,7 +410,12 @@ size_t carve_ortho(void* base, long long n, int K, int dtype, OrthoWs* w) {
   w->rows_per_chunk = (int)(((n + nchunk - 1) / nchunk + kPR - 1) / kPR * kPR);
   const size_t KK = (size_t)K * K;
   const size_t esz = dtype == HEF_F64 ? 8 : 4;
-  w->part = cv.take<double>((size_t)nchunk * npairs * kGB * kGB);
+  size_t npart = (size_t)nchunk * npairs * kGB * kGB;
+  if (dtype == HEF_F32 && gram_tc_supported(K)) {
+    const size_t tc = gram_tc_part_doubles(n, K);
+    if (tc > npart) npart = tc;
+  }
+  w->part = cv.take<double>(npart);
   w->colpart = cv.take<double>((size_t)nchunk * Kp);
   w->G = cv.take<double>(KK);
   w->c = cv.take<double>(K);
@@ -416,6 +427,7 @@ size_t carve_ortho(void* base, long long n, int K, int dtype, OrthoWs* w) {
   w->kept = cv.take<int>(K);
   w->rank = cv.take<int>(4);
   w->flag = cv.take<int>(4);
+  w->tcs = cv.take<float>(dtype == HEF_F32 && apply_tc_supported(K) ? apply_tc_scratch_floats(K) : 1);
   return cv.bytes();
 }
 
@@ -457,13 +469,21 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
   const double gtol = sizeof(T) == 8 ? 1e-8 : 1e-4;
   double* Rs[2] = {w.R1, w.R2};
 
+  const bool use_tc = sizeof(T) == 4 && gram_tc_supported(K);
+  HEF_CHECK_CUDA(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), st));
   for (int pass = 0; pass < 2; ++pass) {
     CholOut o{w.Rinv, w.mu, Rs[pass], w.kept, w.rank, w.flag};
-    HEF_LAUNCH("k_gram", st, k_gram<T><<<ggrid, kPairs, gram_smem, st>>>(
-                                 V, ldv, (int)n, K, Kp, w.rows_per_chunk, w.part, w.colpart));
-    HEF_LAUNCH("k_gram_reduce", st, k_gram_reduce<<<rgrid, kThreads, 0, st>>>(
-                                        w.part, w.colpart, K, Kp, w.nchunk, w.G, w.c));
-    HEF_CHECK_LAUNCH();
+    if (use_tc) {
+      hef_status s = gram_tc(reinterpret_cast<const float*>(V), ldv, n, K, w.part, w.G, w.c,
+                             w.flag + 1, st);
+      if (s) return s;
+    } else {
+      HEF_LAUNCH("k_gram", st, k_gram<T><<<ggrid, kPairs, gram_smem, st>>>(
+                                   V, ldv, (int)n, K, Kp, w.rows_per_chunk, w.part, w.colpart));
+      HEF_LAUNCH("k_gram_reduce", st, k_gram_reduce<<<rgrid, kThreads, 0, st>>>(
+                                          w.part, w.colpart, K, Kp, w.nchunk, w.G, w.c));
+      HEF_CHECK_LAUNCH();
+    }
     if (pass == 0) {
       if (fast_ok) {
         HEF_LAUNCH("k_chol_aug", st, k_chol_aug<float, T><<<1, 1024, fast_smem, st>>>(
@@ -474,19 +494,26 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
                                        w.G, w.c, K, Kp, (double)n, tol, w.Wg, 0, 0,
                                        fast_ok ? 0 : 1, o));
     } else {
-      HEF_CHECK_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));
+      HEF_CHECK_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));  // flag[0] only
       HEF_LAUNCH("k_chol_series", st, k_chol_series<T><<<stride_grid((long long)Kp * Kp, 2),
                                                         kThreads, 0, st>>>(
                                           w.G, w.c, K, Kp, (double)n, gtol, o));
       HEF_LAUNCH("k_chol_aug", st, k_chol_aug<double, T><<<1, 1024, 0, st>>>(
                                        w.G, w.c, K, Kp, (double)n, tol, w.Wg, 0, 0, 0, o));
-      HEF_LAUNCH("k_rank", st, k_rank<<<1, 32, 0, st>>>(w.kept, K, w.rank));
+      HEF_LAUNCH("k_rank", st, k_rank<<<1, 32, 0, st>>>(w.kept, K, w.flag, w.rank));
     }
     HEF_CHECK_LAUNCH();
-    HEF_LAUNCH("k_apply", st, k_apply<T><<<agrid, athreads, apply_smem(RB), st>>>(
-                                  V, ldv, (int)n, K, Kp, static_cast<const T*>(w.Rinv),
-                                  static_cast<const T*>(w.mu), RB, stage_r));
-    HEF_CHECK_LAUNCH();
+    if (sizeof(T) == 4 && apply_tc_supported(K)) {
+      hef_status s = apply_tc(reinterpret_cast<float*>(V), ldv, n, K,
+                              static_cast<const float*>(w.Rinv), Kp,
+                              static_cast<const float*>(w.mu), w.tcs, w.flag + 1, st);
+      if (s) return s;
+    } else {
+      HEF_LAUNCH("k_apply", st, k_apply<T><<<agrid, athreads, apply_smem(RB), st>>>(
+                                    V, ldv, (int)n, K, Kp, static_cast<const T*>(w.Rinv),
+                                    static_cast<const T*>(w.mu), RB, stage_r));
+      HEF_CHECK_LAUNCH();
+    }
   }
   if (R_out) {
     HEF_LAUNCH("k_trmm_upper", st, k_trmm_upper<<<stride_grid((long long)K * K, 4), kThreads, 0,

@@ -1,0 +1,480 @@
+// Tensor-core Gram matrix for the FP32 form of CholQR2 (Algorithm 1 step 4):
+// G_aug = [V 1]^T [V 1] on the 5th-generation tensor cores (tcgen05, TMEM
+// accumulators).  FP32 accuracy from TF32 inputs by the 3-product split
+// x = hi + lo (hi = tf32(x), lo = x - hi): x y ~ hi hi' + hi lo' + lo hi'.
+// The all-ones column gives the column sums (and n) for free.
+//
+// One CTA per SM-sized chunk of rows.  Per 32-row slab the CTA writes the
+// transposed slab (basis index x 32 rows, K-major, 128-byte swizzle) as hi and
+// lo tiles into shared memory (double-buffered), and one thread issues the
+// MMAs of the upper block rows: block b covers basis rows [128b, 128b+128)
+// against basis columns [128b, Kq).  Completion is tracked by tcgen05.commit
+// on an mbarrier per stage; every wait is bounded and a timeout sets *err.
+// The epilogue moves the FP32 accumulators from TMEM to FP64 per-CTA partials.
+#include "internal.h"
+#include "umma.cuh"
+
+namespace hef {
+
+namespace {
+
+using namespace umma;
+
+constexpr int kTcThreads = 256;
+constexpr int kSlab = 32;                    // V rows per stage (128 B of fp32)
+constexpr uint32_t kWaitIters = 1u << 20;    // bounded mbarrier waits
+
+struct GramTcArgs {
+  const float* V;
+  long long ldv;
+  int n, K, Kq, nb;
+  int rows_per_cta;
+  double* part;  // gridDim.x x Kq x Kq
+  int* err;
+};
+
+// Slab loader: thread tid owns the float4 slots f = tid + 256 k of a slab
+// (slab row f % 32, basis columns 4 (f / 32) .. + 3); values past K are the
+// ones column (index K) or zero, rows past the chunk are zero.
+template <int PER>
+__device__ __forceinline__ void gram_load_slab(const GramTcArgs& a, long long rowbase, long long r1,
+                                               float4 (&buf)[PER]) {
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
+    const int f = threadIdx.x + kTcThreads * k;
+    const int r = f & (kSlab - 1), c0 = 4 * (f >> 5);
+    const long long row = rowbase + r;
+    const bool valid = row < r1;
+    if (valid && c0 + 3 < a.K) {
+      buf[k] = __ldg(reinterpret_cast<const float4*>(a.V + row * a.ldv + c0));
+    } else {
+      float x[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int c = c0 + u;
+        x[u] = !valid ? 0.f : (c < a.K ? a.V[row * a.ldv + c] : (c == a.K ? 1.f : 0.f));
+      }
+      buf[k] = make_float4(x[0], x[1], x[2], x[3]);
+    }
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int Mpad = NB * 128;
+  constexpr int PER = kSlab * (Mpad / 4) / kTcThreads;  // float4 slots per thread
+  const uint32_t tile_bytes = (uint32_t)Mpad * 128u;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 4 * tile_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int N0 = a.Kq, N1 = a.Kq - 128;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(N0 + (NB > 1 ? N1 : 0))) ncols <<= 1;
+
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  const long long r0 = (long long)blockIdx.x * a.rows_per_cta;
+  const long long r1 = min((long long)a.n, r0 + a.rows_per_cta);
+  const int nslab = r1 > r0 ? (int)((r1 - r0 + kSlab - 1) / kSlab) : 0;
+  const uint32_t id0 = idesc_tf32(128, N0);
+  const uint32_t id1 = idesc_tf32(128, NB > 1 ? N1 : 16);
+  bool ok = true;
+  int committed = 0;  // slabs whose MMAs were issued
+  float4 cur[PER], nxt[PER];
+  if (nslab > 0) gram_load_slab<PER>(a, r0, r1, cur);
+
+  for (int t = 0; t < nslab; ++t) {
+    const int s = t & 1;
+    // next slab's loads are in flight while this one is converted and issued
+    if (t + 1 < nslab) gram_load_slab<PER>(a, r0 + (long long)(t + 1) * kSlab, r1, nxt);
+    if (t >= 2) ok = ok && mbar_wait(&bars[s], ((t - 2) >> 1) & 1, kWaitIters);
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    unsigned char* hi = base + (size_t)s * 2 * tile_bytes;
+    unsigned char* lo = hi + tile_bytes;
+    // transposed slab: element (basis i, slab row r) at sw128_offset(i, r)
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int f = tid + kTcThreads * k;
+      const int r = f & (kSlab - 1), c0 = 4 * (f >> 5);
+      const float x[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const float h = tf32_round(x[u]);
+        const uint32_t off = sw128_offset(c0 + u, r);
+        *reinterpret_cast<float*>(hi + off) = h;
+        *reinterpret_cast<float*>(lo + off) = x[u] - h;
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < PER; ++k) cur[k] = nxt[k];
+    fence_async_smem();
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t shi = smem_u32(hi), slo = smem_u32(lo);
+#pragma unroll
+      for (int ks = 0; ks < kSlab / 8; ++ks) {
+        for (int b = 0; b < NB; ++b) {
+          const uint32_t aoff = (uint32_t)b * 128u * 128u + (uint32_t)ks * 32u;
+          const uint32_t d = tmem + (b ? (uint32_t)N0 : 0u);
+          const uint32_t id = b ? id1 : id0;
+          const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
+          mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(shi + aoff), id, acc);
+          mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(slo + aoff), id, 1u);
+          mma_tf32(d, desc_k_sw128(slo + aoff), desc_k_sw128(shi + aoff), id, 1u);
+        }
+      }
+      mma_commit(&bars[s]);
+    }
+    committed = t + 1;
+  }
+  // the last commit covers every MMA issued before it
+  if (committed > 0) {
+    const int t = committed - 1;
+    const bool done = mbar_wait(&bars[t & 1], (t >> 1) & 1, kWaitIters);
+    ok = ok && done;
+  }
+  ok = __syncthreads_and(ok);
+  tc_fence_after();
+  double* P = a.part + (size_t)blockIdx.x * a.Kq * a.Kq;
+  if (ok && committed > 0) {
+    const int q = warp & 3, half = warp >> 2;
+    for (int b = 0; b < NB; ++b) {
+      const int ncol = b ? N1 : N0;
+      const int i = b * 128 + q * 32 + lane;
+      for (int c8 = half; c8 < ncol / 8; c8 += 2) {
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (b ? (uint32_t)N0 : 0u) + (uint32_t)c8 * 8u, v);
+        tmem_wait_ld();
+        const int j0 = b * 128 + c8 * 8;
+        if (i < a.Kq && j0 + 7 >= i) {  // upper triangle only (the reducer reads i <= j)
+#pragma unroll
+          for (int u = 0; u < 8; ++u) P[(size_t)i * a.Kq + j0 + u] = (double)v[u];
+        }
+      }
+    }
+  } else {
+    for (int e = tid; e < a.Kq * a.Kq; e += kTcThreads) P[e] = 0.0;
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+    if (!ok && committed > 0) {  // let MMAs in flight finish before TMEM is released
+      const int t = committed - 1;
+      mbar_wait(&bars[t & 1], (t >> 1) & 1, kWaitIters);
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+// G (K x K, FP64) and c (K): fixed-order sums of the per-CTA partials of
+// G_aug; column K of G_aug holds the column sums.
+__global__ void k_gram_tc_reduce(const double* __restrict__ part, int K, int Kq, int nchunk,
+                                 double* G, double* c) {
+  const long long KK = (long long)K * K;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < KK + K;
+       idx += (long long)gridDim.x * blockDim.x) {
+    int i, j;
+    if (idx < KK) {
+      i = (int)(idx / K), j = (int)(idx % K);
+      if (i > j) continue;
+    } else {
+      i = (int)(idx - KK), j = K;
+    }
+    const double* p = part + (size_t)i * Kq + j;
+    const size_t stride = (size_t)Kq * Kq;
+    double s = 0.0;
+    int q = 0;
+    for (; q + 8 <= nchunk; q += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (size_t)(q + u) * stride);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; q < nchunk; ++q) s += __ldcg(p + (size_t)q * stride);
+    if (j < K) {
+      G[(size_t)i * K + j] = s;
+      G[(size_t)j * K + i] = s;
+    } else {
+      c[i] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- apply
+
+// B operand and mean correction of the apply: RinvT_hi/lo[j][i] (Kq x Kd,
+// row-major) = hi/lo split of Rinv[i][j]; muR[j] = sum_i mu_i Rinv[i][j].
+__global__ void k_rinv_split(const float* __restrict__ Rinv, const float* __restrict__ mu, int K,
+                             int Kp, int Kq, int Kd, float* RtH, float* RtL, float* muR) {
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < (long long)Kq * Kd;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(idx / Kd), i = (int)(idx % Kd);
+    const float x = (i < K && j < K) ? Rinv[(size_t)i * Kp + j] : 0.f;
+    const float h = tf32_round(x);
+    RtH[idx] = h;
+    RtL[idx] = x - h;
+  }
+  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < Kq;
+       j += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    if (j < K)
+      for (int i = 0; i <= j; ++i) s += (double)mu[i] * (double)Rinv[(size_t)i * Kp + j];
+    muR[j] = (float)s;
+  }
+}
+
+struct ApplyTcArgs {
+  float* V;
+  long long ldv;
+  int n, K, Kq, Kd;
+  const float* RtH;
+  const float* RtL;
+  const float* muR;
+  int* err;
+};
+
+// Q = (V - 1 mu^T) Rinv = V Rinv - 1 (mu^T Rinv), in place, 128-row tiles.
+// Stage ka holds the 32 basis values [32 ka, 32 ka + 32) of the tile's rows
+// (A, hi and lo) and rows j >= 32 ka of Rinv^T for those basis values (B): Rinv
+// is upper triangular, so block ka only feeds output columns j >= 32 ka.
+__global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t a_bytes = 128u * 128u;                // one A tile (hi or lo)
+  const uint32_t b_bytes = (uint32_t)a.Kq * 128u;      // one B tile (hi or lo), max
+  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * stage_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)a.Kq) ncols <<= 1;
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int nka = a.Kd / 32;
+  const int ntiles = (a.n + 127) / 128;
+  bool ok = true;
+  uint32_t uses[2] = {0u, 0u};  // commits per stage so far
+  int g = 0;                    // global stage counter (alternates buffers)
+  int last_stage = -1;
+  // A slots of a stage: f = tid + 256 k -> tile row f / 8, basis values
+  // c0 + 4 (f % 8) .. + 3; the next stage's are loaded while this one is used
+  auto load_a = [&](int tile, int ka, float4 (&buf)[4]) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int f = tid + kTcThreads * k;
+      const int r = f >> 3, q = f & 7;
+      const long long row = (long long)tile * 128 + r;
+      const int col = ka * 32 + 4 * q;
+      if (tile < ntiles && row < a.n && col + 3 < a.K) {
+        buf[k] = __ldg(reinterpret_cast<const float4*>(a.V + row * a.ldv + col));
+      } else {
+        float x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+          x[u] = (tile < ntiles && row < a.n && col + u < a.K) ? a.V[row * a.ldv + col + u] : 0.f;
+        buf[k] = make_float4(x[0], x[1], x[2], x[3]);
+      }
+    }
+  };
+  float4 cur[4], nxt[4];
+  load_a(blockIdx.x, 0, cur);
+  for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
+    const long long row0 = (long long)tile * 128;
+    for (int ka = 0; ka < nka; ++ka, ++g) {
+      const int s = g & 1;
+      if (ka + 1 < nka) load_a(tile, ka + 1, nxt);
+      else load_a(tile + gridDim.x, 0, nxt);
+      if (uses[s] > 0) ok = ok && mbar_wait(&bars[s], (uses[s] - 1) & 1, kWaitIters);
+      if (!__syncthreads_and(ok)) {
+        ok = false;
+        break;
+      }
+      unsigned char* ahi = base + (size_t)s * stage_bytes;
+      unsigned char* alo = ahi + a_bytes;
+      unsigned char* bhi = alo + a_bytes;
+      unsigned char* blo = bhi + b_bytes;
+      const int c0 = ka * 32;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int f = tid + kTcThreads * k;
+        const int r = f >> 3, q = f & 7;
+        const float x[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
+        float h[4], l[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) h[u] = tf32_round(x[u]), l[u] = x[u] - h[u];
+        const uint32_t off = sw128_offset(r, 4 * q);
+        *reinterpret_cast<float4*>(ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<float4*>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+      // B: rows j in [c0, Kq) of Rinv^T, basis values [c0, c0 + 32)
+      const int nb_rows = a.Kq - c0;
+      for (int f = tid; f < nb_rows * 8; f += kTcThreads) {
+        const int jr = f >> 3, q = f & 7;
+        const size_t src = (size_t)(c0 + jr) * a.Kd + c0 + 4 * q;
+        const uint32_t off = sw128_offset(jr, 4 * q);
+        *reinterpret_cast<float4*>(bhi + off) = __ldg(reinterpret_cast<const float4*>(a.RtH + src));
+        *reinterpret_cast<float4*>(blo + off) = __ldg(reinterpret_cast<const float4*>(a.RtL + src));
+      }
+      fence_async_smem();
+      __syncthreads();
+      if (tid == 0) {
+        tc_fence_after();
+        const uint32_t id = idesc_tf32(128, nb_rows);
+        const uint32_t d = tmem + (uint32_t)c0;
+        const uint32_t sah = smem_u32(ahi), sal = smem_u32(alo);
+        const uint32_t sbh = smem_u32(bhi), sbl = smem_u32(blo);
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 32u;
+          mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbh + ko), id, (ka > 0 || ks > 0) ? 1u : 0u);
+          mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbl + ko), id, 1u);
+          mma_tf32(d, desc_k_sw128(sal + ko), desc_k_sw128(sbh + ko), id, 1u);
+        }
+        mma_commit(&bars[s]);
+      }
+      uses[s] += 1;
+      last_stage = s;
+    }
+    if (!ok) break;
+    // tile done: wait for its last commit, then TMEM -> registers -> V
+    ok = ok && mbar_wait(&bars[last_stage], (uses[last_stage] - 1) & 1, kWaitIters);
+    if (!__syncthreads_and(ok)) {
+      ok = false;
+      break;
+    }
+    tc_fence_after();
+    const int q4 = warp & 3, half = warp >> 2;
+    const long long row = row0 + q4 * 32 + lane;
+    for (int c8 = half; c8 < a.Kq / 8; c8 += 2) {
+      float v[8];
+      tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c8 * 8u, v);
+      tmem_wait_ld();
+      const int j0 = c8 * 8;
+      if (row < a.n) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (j0 + u < a.K) a.V[row * a.ldv + j0 + u] = v[u] - a.muR[j0 + u];
+      }
+    }
+    tc_fence_before();
+    __syncthreads();  // TMEM reads done before the next tile's MMAs overwrite it
+  }
+  if (!ok) {
+    // let any MMA still in flight finish before releasing TMEM
+    if (last_stage >= 0) mbar_wait(&bars[last_stage], (uses[last_stage] - 1) & 1, kWaitIters);
+    if (tid == 0) atomicExch(a.err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+}  // namespace
+
+int apply_tc_supported(int K) { return K >= 1 && K <= 256; }
+
+size_t apply_tc_scratch_floats(int K) {
+  const int Kq = (K + 15) & ~15, Kd = (K + 31) & ~31;
+  return 2 * (size_t)Kq * Kd + Kq + 64;
+}
+
+hef_status apply_tc(float* V, long long ldv, long long n, int K, const float* Rinv, int Kp,
+                    const float* mu, float* scratch, int* err, cudaStream_t st) {
+  const int Kq = (K + 15) & ~15, Kd = (K + 31) & ~31;
+  float* RtH = scratch;
+  float* RtL = RtH + (size_t)Kq * Kd;
+  float* muR = RtL + (size_t)Kq * Kd;
+  HEF_LAUNCH("k_rinv_split", st, k_rinv_split<<<stride_grid((long long)Kq * Kd, 2), kThreads, 0, st>>>(
+                                     Rinv, mu, K, Kp, Kq, Kd, RtH, RtL, muR));
+  ApplyTcArgs a;
+  a.V = V;
+  a.ldv = ldv;
+  a.n = (int)n;
+  a.K = K;
+  a.Kq = Kq;
+  a.Kd = Kd;
+  a.RtH = RtH;
+  a.RtL = RtL;
+  a.muR = muR;
+  a.err = err;
+  const size_t stage = 2 * 128 * 128 + 2 * (size_t)Kq * 128;
+  const size_t smem = 1024 + 2 * stage + 64;
+  HEF_CHECK_CUDA(cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const long long ntiles = (n + 127) / 128;
+  const int ctas = (int)(ntiles < num_sms() ? ntiles : num_sms());
+  HEF_LAUNCH("k_apply_tc", st, k_apply_tc<<<ctas, kTcThreads, smem, st>>>(a));
+  HEF_CHECK_LAUNCH();
+  return HEF_OK;
+}
+
+int gram_tc_supported(int K) { return K >= 1 && K + 1 <= 256; }
+
+int gram_tc_ctas(long long n) {
+  long long want = (n + kSlab - 1) / kSlab;
+  long long g = num_sms();
+  return (int)(want < g ? (want > 0 ? want : 1) : g);
+}
+
+size_t gram_tc_part_doubles(long long n, int K) {
+  const int Kq = (K + 1 + 15) & ~15;
+  return (size_t)gram_tc_ctas(n) * Kq * Kq;
+}
+
+hef_status gram_tc(const float* V, long long ldv, long long n, int K, double* part, double* G,
+                   double* c, int* err, cudaStream_t st) {
+  const int Kq = (K + 1 + 15) & ~15;
+  const int nb = Kq > 128 ? 2 : 1;
+  const int ctas = gram_tc_ctas(n);
+  GramTcArgs a;
+  a.V = V;
+  a.ldv = ldv;
+  a.n = (int)n;
+  a.K = K;
+  a.Kq = Kq;
+  a.nb = nb;
+  a.rows_per_cta = (int)(((n + ctas - 1) / ctas + kSlab - 1) / kSlab * kSlab);
+  a.part = part;
+  a.err = err;
+  const size_t smem = 1024 + 4 * (size_t)nb * 128 * 128 + 64;
+  if (nb == 1) {
+    HEF_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HEF_LAUNCH("k_gram_tc", st, k_gram_tc<1><<<ctas, kTcThreads, smem, st>>>(a));
+  } else {
+    HEF_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HEF_LAUNCH("k_gram_tc", st, k_gram_tc<2><<<ctas, kTcThreads, smem, st>>>(a));
+  }
+  HEF_LAUNCH("k_gram_tc_reduce", st,
+             k_gram_tc_reduce<<<stride_grid((long long)K * K + K, 4), kThreads, 0, st>>>(
+                 part, K, Kq, ctas, G, c));
+  HEF_CHECK_LAUNCH();
+  return HEF_OK;
+}
+
+}  // namespace hef

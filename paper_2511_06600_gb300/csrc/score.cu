@@ -75,10 +75,10 @@ __device__ __forceinline__ void edge_extrema(const T* __restrict__ Q, long long 
 
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restrict__ Q, long long ldq,
-                                                     int K, double* part, unsigned int* counter,
-                                                     double* QH, double* invQH, double* QH_out) {
+                                                     int K, GridRed red, double* QH, double* invQH,
+                                                     double* QH_out) {
   if (g.status[0]) return;
-  __shared__ double red[kThreads / 32][32 * NC];
+  __shared__ double wred[kThreads / 32][32 * NC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -105,17 +105,17 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
     }
   }
 #pragma unroll
-  for (int c = 0; c < NC; ++c) red[wid][lane + 32 * c] = acc[c] + (double)pacc[c];
+  for (int c = 0; c < NC; ++c) wred[wid][lane + 32 * c] = acc[c] + (double)pacc[c];
   __syncthreads();
   for (int col = threadIdx.x; col < K; col += blockDim.x) {
     double s = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w][col];
-    part[(size_t)blockIdx.x * K + col] = s;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wred[w][col];
+    red.part[(size_t)blockIdx.x * K + col] = s;
   }
-  if (last_block_done(counter)) {
+  __shared__ double tot[32 * NC];
+  if (grid_reduce(red, K, tot)) {
     for (int col = threadIdx.x; col < K; col += blockDim.x) {
-      double s = 0.0;
-      for (unsigned b = 0; b < gridDim.x; ++b) s += part[(size_t)b * K + col];
+      const double s = tot[col];
       QH[col] = s;
       invQH[col] = s > kQhTiny ? 1.0 / s : 0.0;
       if (QH_out) QH_out[col] = s;
@@ -222,7 +222,8 @@ struct ScoreWs {
   double* part;
   double* QH;
   double* invQH;
-  unsigned int* counter;
+  unsigned int* counter;  // reduction counters (zero between calls)
+  double* gpart;
   int grid;
 };
 
@@ -233,6 +234,7 @@ size_t carve_score(void* base, int K, ScoreWs* w) {
   w->QH = c.take<double>(K);
   w->invQH = c.take<double>(K);
   w->counter = c.take<unsigned int>(64);
+  w->gpart = c.take<double>((size_t)red_groups(w->grid) * K);
   return c.bytes();
 }
 
@@ -241,7 +243,12 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
                         double* R_out, double* QH_out, int32_t* argvec, int32_t* pmax,
                         int32_t* pmin, const ScoreWs& w, cudaStream_t st) {
   IncView g = view(inc);
-  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<w.grid, kThreads, 0, st>>>(g, Q, ldq, K, w.part, w.counter, w.QH, w.invQH,
+  GridRed red;
+  red.part = w.part;
+  red.gpart = w.gpart;
+  red.gcnt = w.counter;                 // red_groups(grid) <= 63 counters
+  red.tcnt = w.counter + 63;
+  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<w.grid, kThreads, 0, st>>>(g, Q, ldq, K, red, w.QH, w.invQH,
                                                     QH_out));
   HEF_LAUNCH("k_score_pass2", st, k_score_pass2<T, NC><<<w.grid, kThreads, 0, st>>>(g, Q, ldq, K, reduce, w.QH, w.invQH, R_out,
                                                     argvec, pmax, pmin));
@@ -304,9 +311,11 @@ hef_status noalloc_scratch(void** out) {
 // Same layout as carve_score, with the CTA count capped so that the per-CTA
 // partial sums fit the fixed scratch.
 size_t carve_score_capped(void* base, int K, size_t cap, ScoreWs* w) {
-  const size_t fixed = 3 * 256 + 2 * (size_t)K * sizeof(double) + 64 * sizeof(unsigned int);
+  // per-CTA partials plus group partials (1/32 as many), Q_H, 1/Q_H, counters
+  const size_t fixed = 5 * 256 + 2 * (size_t)K * sizeof(double) + 64 * sizeof(unsigned int) +
+                       (size_t)K * sizeof(double);
   long long g = (long long)num_sms() * 4;
-  const long long fit = (long long)((cap - fixed) / ((size_t)K * sizeof(double)));
+  const long long fit = (long long)((cap - fixed) / ((size_t)K * sizeof(double) * 33 / 32 + 1));
   if (g > fit) g = fit;
   Carver c(base);
   w->grid = (int)(g > 0 ? g : 1);
@@ -314,6 +323,7 @@ size_t carve_score_capped(void* base, int K, size_t cap, ScoreWs* w) {
   w->QH = c.take<double>(K);
   w->invQH = c.take<double>(K);
   w->counter = c.take<unsigned int>(64);
+  w->gpart = c.take<double>((size_t)red_groups(w->grid) * K);
   return c.bytes();
 }
 
