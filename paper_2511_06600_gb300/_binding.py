@@ -365,6 +365,27 @@ class Pipeline:
         _check("hef_incidence_check",
                lib().hef_incidence_check(self.handle, _stream(stream), ctypes.byref(detail),
                                          ctypes.byref(where)))
+        if int(self.rank.item()) < 0:
+            raise HefError("hef_orthonormalize", -5, "a tensor-core wait timed out")
+
+    def capture(self, eptr, pins, w, x0_clique, x0_star):
+        """Record one run on these input tensors as a CUDA graph; `replay()`
+        then reruns the whole path with one launch (inputs may be refilled in
+        place between replays)."""
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.run(eptr, pins, w, x0_clique, x0_star)
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run(eptr, pins, w, x0_clique, x0_star)
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+        return self.out
 
     def __del__(self):
         if getattr(self, "handle", None) is not None and _lib is not None:

@@ -70,6 +70,31 @@ LaunchTrace::~LaunchTrace() {
 
 }  // namespace hef
 
+// cudaFuncAttributeMaxDynamicSharedMemorySize is set at most once per kernel,
+// device and size (so launches can also be recorded into CUDA graphs).
+namespace hef {
+namespace {
+std::mutex g_attr_mu;
+struct AttrRec {
+  const void* f;
+  int dev;
+  int bytes;
+};
+std::vector<AttrRec> g_attr;
+}  // namespace
+
+hef_status ensure_smem(const void* func, int bytes) {
+  int dev = 0;
+  HEF_CHECK_CUDA(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_attr_mu);
+  for (auto& r : g_attr)
+    if (r.f == func && r.dev == dev && r.bytes >= bytes) return HEF_OK;
+  HEF_CHECK_CUDA(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+  g_attr.push_back({func, dev, bytes});
+  return HEF_OK;
+}
+}  // namespace hef
+
 extern "C" uint64_t hef_launch_count(void) { return hef::g_launches.load(); }
 
 extern "C" hef_status hef_trace_kernels(const char* name_substring) {

@@ -25,6 +25,15 @@ hef_status set_error(hef_status s, const char* fmt, ...);
 
 #define HEF_CHECK_LAUNCH() HEF_CHECK_CUDA(cudaGetLastError())
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` (once per kernel,
+// device and size).
+hef_status ensure_smem(const void* func, int bytes);
+#define HEF_ENSURE_SMEM(func, bytes)                                              \
+  do {                                                                            \
+    hef_status s_ = ::hef::ensure_smem(reinterpret_cast<const void*>(func), (int)(bytes)); \
+    if (s_ != HEF_OK) return s_;                                                  \
+  } while (0)
+
 // Launch accounting and optional CUDA-event timing of selected kernels (see
 // hef_launch_count / hef_trace_kernels in hef.h).  Every kernel launch of the
 // library goes through HEF_LAUNCH(name, stream, kernel<<<...>>>(...)).

@@ -352,18 +352,20 @@ __global__ void k_node_scalars(int n, const int32_t* __restrict__ vptr, const in
                                const int32_t* __restrict__ ceptr, const double* __restrict__ ewh,
                                const double* __restrict__ ez, unsigned int* status,
                                unsigned int* counter, double* dc, double* db, double* inv_dc,
-                               double* inv_db, double* part, double* totals) {
+                               double* inv_db, double* wsc, double* part, double* totals) {
   if (status[0]) return;
   double sc = 0.0, sb = 0.0;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
-    double c = 0.0, b = 0.0;
+    double c = 0.0, b = 0.0, ws = 0.0;
     for (int t = vptr[v]; t < vptr[v + 1]; ++t) {
       const int e = vedge[t];
       const int k = ceptr[e + 1] - ceptr[e];
       c += ewh[e] * (double)(k - 1);
       b += ez[e];
+      ws += ewh[e];
     }
+    wsc[v] = ws;
     dc[v] = c;
     db[v] = b;
     inv_dc[v] = c > 0.0 ? 1.0 / c : 0.0;
@@ -420,6 +422,7 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   L->h.db = c.take<double>(n > 0 ? n : 1);
   L->h.inv_dc = c.take<double>(n > 0 ? n : 1);
   L->h.inv_db = c.take<double>(n > 0 ? n : 1);
+  L->h.wsc = c.take<double>(n > 0 ? n : 1);
   L->h.totals = c.take<double>(8);
   L->keys = c.take<uint32_t>(NS > 0 ? NS : 1);
   L->vals = c.take<int32_t>(NS > 0 ? NS : 1);
@@ -537,7 +540,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     int grid = stride_grid(n);
     HEF_LAUNCH("k_node_scalars", st, k_node_scalars<<<grid, kThreads, 0, st>>>((int)n, h->vptr, h->vedge, h->ceptr, h->ewh, h->ez,
                                               h->status, h->counter, h->dc, h->db, h->inv_dc,
-                                              h->inv_db, L.part, h->totals));
+                                              h->inv_db, h->wsc, L.part, h->totals));
     HEF_TRY_CUDA(cudaGetLastError());
   }
 #undef HEF_TRY

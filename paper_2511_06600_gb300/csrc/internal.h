@@ -26,6 +26,7 @@ struct hef_incidence {
   double* db = nullptr;             // n: star degree of vertices
   double* inv_dc = nullptr;         // n: 1/dc (0 for isolated)
   double* inv_db = nullptr;         // n: 1/db (0 for isolated)
+  double* wsc = nullptr;            // n: sum of clique pair weights over e ∋ v
   double* totals = nullptr;         // [0] sum dc, [1] sum db, [2] sum w (|e|>=2)
 };
 
@@ -48,6 +49,7 @@ struct IncView {
   const double* db;
   const double* inv_dc;
   const double* inv_db;
+  const double* wsc;
   const double* totals;
 };
 
@@ -70,6 +72,7 @@ inline IncView view(const hef_incidence* h) {
   v.db = h->db;
   v.inv_dc = h->inv_dc;
   v.inv_db = h->inv_db;
+  v.wsc = h->wsc;
   v.totals = h->totals;
   return v;
 }

@@ -31,7 +31,8 @@ namespace hef {
 namespace {
 
 constexpr int kMaxS = 16;
-constexpr int kBig = 16;  // segments longer than this are summed by a warp
+constexpr int kBig = 16;     // segments longer than this are summed by a warp
+constexpr int kUpdRows = 4;  // rows per thread in the update pass
 
 template <typename T>
 struct KView {
@@ -173,6 +174,75 @@ __device__ __forceinline__ void seg_sum(bool valid, int a, int b, RowOf row_of, 
   }
 }
 
+// Two weighted row sums over one index list at once (the index is loaded
+// once and both rows are in flight together): accA = sum_t wA(i) rowA(i),
+// accB = sum_t wB(i) rowB(i) with i = idx(t), t in [a, b).  Lists longer than
+// kBig are summed by the whole warp.
+template <typename T, int S, typename Idx, typename RowA, typename RowB, typename WA, typename WB>
+__device__ __forceinline__ void seg_sum2(bool valid, int a, int b, Idx idx, RowA rowA, RowB rowB,
+                                         WA wA, WB wB, T (&accA)[S], T (&accB)[S]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int s = 0; s < S; ++s) accA[s] = 0, accB[s] = 0;
+  const bool big = valid && (b - a) > kBig;
+  if (valid && !big) {
+    int t = a;
+    for (; t + 2 <= b; t += 2) {
+      const int i0 = idx(t), i1 = idx(t + 1);
+      T a0[S], a1[S], b0[S], b1[S];
+      ldrow<T, S>(rowA(i0), a0);
+      ldrow<T, S>(rowA(i1), a1);
+      ldrow<T, S>(rowB(i0), b0);
+      ldrow<T, S>(rowB(i1), b1);
+      const T wa0 = wA(i0), wa1 = wA(i1), wb0 = wB(i0), wb1 = wB(i1);
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        accA[s] += wa0 * a0[s] + wa1 * a1[s];
+        accB[s] += wb0 * b0[s] + wb1 * b1[s];
+      }
+    }
+    if (t < b) {
+      const int i0 = idx(t);
+      T a0[S], b0[S];
+      ldrow<T, S>(rowA(i0), a0);
+      ldrow<T, S>(rowB(i0), b0);
+      const T wa0 = wA(i0), wb0 = wB(i0);
+#pragma unroll
+      for (int s = 0; s < S; ++s) accA[s] += wa0 * a0[s], accB[s] += wb0 * b0[s];
+    }
+  }
+  unsigned bigmask = __ballot_sync(0xffffffffu, big);
+  while (bigmask) {
+    const int src = __ffs(bigmask) - 1;
+    bigmask &= bigmask - 1;
+    const int ba = __shfl_sync(0xffffffffu, a, src), bb = __shfl_sync(0xffffffffu, b, src);
+    T pa[S], pb[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) pa[s] = 0, pb[s] = 0;
+    for (int t = ba + lane; t < bb; t += 32) {
+      const int i0 = idx(t);
+      T a0[S], b0[S];
+      ldrow<T, S>(rowA(i0), a0);
+      ldrow<T, S>(rowB(i0), b0);
+      const T wa0 = wA(i0), wb0 = wB(i0);
+#pragma unroll
+      for (int s = 0; s < S; ++s) pa[s] += wa0 * a0[s], pb[s] += wb0 * b0[s];
+    }
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        pa[s] += __shfl_xor_sync(0xffffffffu, pa[s], o);
+        pb[s] += __shfl_xor_sync(0xffffffffu, pb[s], o);
+      }
+    }
+    if (lane == src) {
+#pragma unroll
+      for (int s = 0; s < S; ++s) accA[s] = pa[s], accB[s] = pb[s];
+    }
+  }
+}
+
 // ---------------------------------------------------------------- start vectors
 
 // D-weighted dots of the raw starts with the trivial vectors -> coef[0].
@@ -292,10 +362,10 @@ __global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, KView<T> kv, 
   if (valid) a = g.ceptr[e], b = g.ceptr[e + 1];
   const int32_t* __restrict__ pins = g.cpins;
   T sc[S], sb[S];
-  seg_sum<T, S>(valid, a, b, [&](int t) { return curc + (long long)pins[t] * S; },
-                [&](int) { return (T)1; }, sc);
-  seg_sum<T, S>(valid, a, b, [&](int t) { return curb + (long long)pins[t] * S; },
-                [&](int) { return (T)1; }, sb);
+  seg_sum2<T, S>(valid, a, b, [&](int t) { return __ldg(pins + t); },
+                 [&](int p) { return curc + (long long)p * S; },
+                 [&](int p) { return curb + (long long)p * S; }, [&](int) { return (T)1; },
+                 [&](int) { return (T)1; }, sc, sb);
   T acc[3][S];
 #pragma unroll
   for (int q = 0; q < 3; ++q)
@@ -353,18 +423,18 @@ __global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, KView<T> kv, 
   const int32_t* __restrict__ ve = g.vedge;
   const T* __restrict__ se = kv.se;
   T accc[S], accb[S];
-  seg_sum<T, S>(valid, a, b, [&](int t) { return se + (long long)ve[t] * S; },
-                [&](int t) { return (T)g.ewh[ve[t]]; }, accc);
-  seg_sum<T, S>(valid, a, b, [&](int t) { return curb + (long long)(g.n + ve[t]) * S; },
-                [&](int t) { return (T)g.ez[ve[t]]; }, accb);
+  seg_sum2<T, S>(valid, a, b, [&](int t) { return __ldg(ve + t); },
+                 [&](int e) { return se + (long long)e * S; },
+                 [&](int e) { return curb + (long long)(g.n + e) * S; },
+                 [&](int e) { return (T)__ldg(g.ewh + e); }, [&](int e) { return (T)__ldg(g.ez + e); },
+                 accc, accb);
   T acc[6][S];
 #pragma unroll
   for (int q = 0; q < 6; ++q)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (valid) {
-    T wsum = 0;
-    for (int t = a; t < b; ++t) wsum += (T)g.ewh[ve[t]];
+    const T wsum = (T)g.wsc[v];
     T xv[S], xb[S], yc[S], yb[S], xpc[S], xpb[S];
     ldrow<T, S>(curc + (long long)v * S, xv);
     ldrow<T, S>(curb + (long long)v * S, xb);
@@ -428,16 +498,19 @@ __global__ void __launch_bounds__(kThreads) k_update(IncView g, KView<T> kv, int
   const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
   const double* nup = has_prv ? kv.inv_nu + (size_t)(j - 2) * 2 * S : nullptr;
   const double* cf = kv.coef + (size_t)j * 2 * S * 4;
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   T acc[2][S];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
-  if (r < 2ll * g.n + g.m) {
+  const long long nrows = 2ll * g.n + g.m;
+  const long long r0 = (long long)blockIdx.x * blockDim.x * kUpdRows + threadIdx.x;
+#pragma unroll
+  for (int it = 0; it < kUpdRows; ++it) {
+    const long long r = r0 + (long long)it * blockDim.x;
+    if (r >= nrows) break;
     const bool clique = r < g.n;
     const int op = clique ? 0 : 1;
-    T dsq[S];
     const long long rr = clique ? r : r - g.n;
     const T* cur = clique ? pick2(kv.Bc, (j - 1) & 1) : pick2(kv.Bb, (j - 1) & 1);
     T* nw = clique ? pick2(kv.Bc, j & 1) : pick2(kv.Bb, j & 1);
@@ -447,7 +520,7 @@ __global__ void __launch_bounds__(kThreads) k_update(IncView g, KView<T> kv, int
     if (clique) d = (T)g.dc[rr], tsel = 0;
     else if (rr < g.n) d = (T)g.db[rr], tsel = 0;
     else d = (T)g.ew[rr - g.n], tsel = 1;
-    T y[S], xc[S], xp[S], u[S];
+    T y[S], xc[S], xp[S], u[S], dsq[S];
     ldrow<T, S>(Y + rr * S, y);
     ldrow<T, S>(cur + rr * S, xc);
     if (has_prv) ldrow<T, S>(nw + rr * S, xp);
@@ -462,8 +535,8 @@ __global__ void __launch_bounds__(kThreads) k_update(IncView g, KView<T> kv, int
     strow<T, S>(nw + rr * S, u);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      if (clique) acc[0][s] = dsq[s];
-      else acc[1][s] = dsq[s];
+      if (clique) acc[0][s] += dsq[s];
+      else acc[1][s] += dsq[s];
     }
   }
   block_partials_qs<2, S, T>(acc, kv.red.part);
@@ -528,13 +601,14 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   const int grid_all = blocks_for(2 * n + m);
   const int grid_e = blocks_for(m > 0 ? m : 1);
   const int grid_n = blocks_for(n);
+  const int grid_upd = blocks_for((2 * n + m + kUpdRows - 1) / kUpdRows);
   HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, kv, x0c, x0b));
   HEF_LAUNCH("k_start_write", st, k_start_write<T, S><<<grid_all, kThreads, 0, st>>>(g, kv, x0c, x0b));
   HEF_CHECK_LAUNCH();
   for (int j = 1; j <= k; ++j) {
     HEF_LAUNCH("k_edge_pass", st, k_edge_pass<T, S><<<grid_e, kThreads, 0, st>>>(g, kv, j));
     HEF_LAUNCH("k_node_pass", st, k_node_pass<T, S><<<grid_n, kThreads, 0, st>>>(g, kv, j, V, ldv));
-    HEF_LAUNCH("k_update", st, k_update<T, S><<<grid_all, kThreads, 0, st>>>(g, kv, j));
+    HEF_LAUNCH("k_update", st, k_update<T, S><<<grid_upd, kThreads, 0, st>>>(g, kv, j));
     HEF_CHECK_LAUNCH();
   }
   HEF_LAUNCH("k_archive_last", st, k_archive_last<T, S><<<grid_n, kThreads, 0, st>>>(g, kv, k, V, ldv));

@@ -436,8 +436,7 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
                      const OrthoWs& w, cudaStream_t st) {
   const int Kp = round8(K);
   const size_t gram_smem = (size_t)kPR * Kp * sizeof(T);
-  HEF_CHECK_CUDA(cudaFuncSetAttribute(k_gram<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)gram_smem));
+  HEF_ENSURE_SMEM(k_gram<T>, (int)gram_smem);
   const dim3 ggrid(w.nchunk, w.ngroups);
   const int nb = Kp / kGB;
   const long long nel = (long long)nb * (nb + 1) / 2 * kGB * kGB;
@@ -455,16 +454,13 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
   }
   if (apply_smem(RB) > 200 * 1024)
     return set_error(HEF_ERR_UNSUPPORTED, "hef_orthonormalize: K = %d too large", K);
-  HEF_CHECK_CUDA(cudaFuncSetAttribute(k_apply<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)apply_smem(RB)));
+  HEF_ENSURE_SMEM(k_apply<T>, (int)apply_smem(RB));
   const int agrid = (int)((n + RB - 1) / RB);
   const int athreads = RB * 2;  // (RB / 4) row groups x 8 column groups
   const size_t fast_smem = (size_t)K * 2 * K * sizeof(float);
   const bool fast_ok = sizeof(T) == 4 && fast_smem <= 200 * 1024;
   if (fast_ok)
-    HEF_CHECK_CUDA(cudaFuncSetAttribute(k_chol_aug<float, T>,
-                                        cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)fast_smem));
+    HEF_ENSURE_SMEM((k_chol_aug<float, T>), fast_smem);
   const double tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
   const double gtol = sizeof(T) == 8 ? 1e-8 : 1e-4;
   double* Rs[2] = {w.R1, w.R2};

@@ -250,17 +250,28 @@ struct ApplyTcArgs {
 };
 
 // Q = (V - 1 mu^T) Rinv = V Rinv - 1 (mu^T Rinv), in place, 128-row tiles.
-// Stage ka holds the 32 basis values [32 ka, 32 ka + 32) of the tile's rows
-// (A, hi and lo) and rows j >= 32 ka of Rinv^T for those basis values (B): Rinv
-// is upper triangular, so block ka only feeds output columns j >= 32 ka.
+// K block ka covers basis values [32 ka, 32 ka + 32): its A tile holds those
+// values of the tile's rows (hi and lo), its B tile the rows j >= 32 ka of
+// Rinv^T (Rinv is upper triangular, so block ka feeds output columns
+// j >= 32 ka only).  RESB: every B tile stays resident in shared memory
+// (staged once per CTA); otherwise B is staged with A for every block.
+template <bool RESB>
 __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  const uint32_t a_bytes = 128u * 128u;                // one A tile (hi or lo)
-  const uint32_t b_bytes = (uint32_t)a.Kq * 128u;      // one B tile (hi or lo), max
-  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * stage_bytes);
+  const int nka = a.Kd / 32;
+  const uint32_t a_bytes = 128u * 128u;  // one A tile (hi or lo)
+  // B region: tile ka (hi, then lo) at boff(ka); rows Kq - 32 ka
+  auto brows = [&](int ka) { return a.Kq - 32 * ka; };
+  auto boff = [&](int ka) {  // bytes before B tile pair ka
+    return RESB ? (uint32_t)(ka * a.Kq - 16 * ka * (ka - 1)) * 256u : 0u;
+  };
+  const uint32_t b_region = RESB ? boff(nka) : 2u * (uint32_t)a.Kq * 128u;
+  const uint32_t stage_bytes = 2 * a_bytes + (RESB ? 0u : b_region);
+  unsigned char* bbase = base;
+  unsigned char* sbase = base + (RESB ? b_region : 0u);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 2 * stage_bytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint32_t ncols = 32;
@@ -271,18 +282,34 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
     mbar_init(&bars[1], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // B tile ka: row jr = Rinv^T row 32 ka + jr, basis values [32 ka, 32 ka + 32)
+  auto stage_b = [&](int ka, unsigned char* bhi, unsigned char* blo) {
+    const int c0 = ka * 32, nr = brows(ka);
+    for (int f = tid; f < nr * 8; f += kTcThreads) {
+      const int jr = f >> 3, q = f & 7;
+      const size_t src = (size_t)(c0 + jr) * a.Kd + c0 + 4 * q;
+      const uint32_t off = sw128_offset(jr, 4 * q);
+      *reinterpret_cast<float4*>(bhi + off) = __ldg(reinterpret_cast<const float4*>(a.RtH + src));
+      *reinterpret_cast<float4*>(blo + off) = __ldg(reinterpret_cast<const float4*>(a.RtL + src));
+    }
+  };
+  if (RESB) {
+    for (int ka = 0; ka < nka; ++ka) {
+      unsigned char* bhi = bbase + boff(ka);
+      stage_b(ka, bhi, bhi + (uint32_t)brows(ka) * 128u);
+    }
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
-  const int nka = a.Kd / 32;
   const int ntiles = (a.n + 127) / 128;
   bool ok = true;
-  uint32_t uses[2] = {0u, 0u};  // commits per stage so far
-  int g = 0;                    // global stage counter (alternates buffers)
+  uint32_t uses0 = 0u, uses1 = 0u;  // commits per stage so far
+  int g = 0;                        // global stage counter (alternates buffers)
   int last_stage = -1;
   // A slots of a stage: f = tid + 256 k -> tile row f / 8, basis values
-  // c0 + 4 (f % 8) .. + 3; the next stage's are loaded while this one is used
+  // 32 ka + 4 (f % 8) .. + 3; the next stage's are loaded while this one is used
   auto load_a = [&](int tile, int ka, float4 (&buf)[4]) {
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -307,18 +334,26 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
     const long long row0 = (long long)tile * 128;
     for (int ka = 0; ka < nka; ++ka, ++g) {
       const int s = g & 1;
+      const uint32_t uses_s = s ? uses1 : uses0;
       if (ka + 1 < nka) load_a(tile, ka + 1, nxt);
       else load_a(tile + gridDim.x, 0, nxt);
-      if (uses[s] > 0) ok = ok && mbar_wait(&bars[s], (uses[s] - 1) & 1, kWaitIters);
+      if (uses_s > 0) ok = ok && mbar_wait(&bars[s], (uses_s - 1) & 1, kWaitIters);
       if (!__syncthreads_and(ok)) {
         ok = false;
         break;
       }
-      unsigned char* ahi = base + (size_t)s * stage_bytes;
+      unsigned char* ahi = sbase + (size_t)s * stage_bytes;
       unsigned char* alo = ahi + a_bytes;
-      unsigned char* bhi = alo + a_bytes;
-      unsigned char* blo = bhi + b_bytes;
-      const int c0 = ka * 32;
+      unsigned char* bhi;
+      unsigned char* blo;
+      if (RESB) {
+        bhi = bbase + boff(ka);
+        blo = bhi + (uint32_t)brows(ka) * 128u;
+      } else {
+        bhi = alo + a_bytes;
+        blo = bhi + (uint32_t)a.Kq * 128u;
+        stage_b(ka, bhi, blo);
+      }
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int f = tid + kTcThreads * k;
@@ -333,20 +368,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
       }
 #pragma unroll
       for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
-      // B: rows j in [c0, Kq) of Rinv^T, basis values [c0, c0 + 32)
-      const int nb_rows = a.Kq - c0;
-      for (int f = tid; f < nb_rows * 8; f += kTcThreads) {
-        const int jr = f >> 3, q = f & 7;
-        const size_t src = (size_t)(c0 + jr) * a.Kd + c0 + 4 * q;
-        const uint32_t off = sw128_offset(jr, 4 * q);
-        *reinterpret_cast<float4*>(bhi + off) = __ldg(reinterpret_cast<const float4*>(a.RtH + src));
-        *reinterpret_cast<float4*>(blo + off) = __ldg(reinterpret_cast<const float4*>(a.RtL + src));
-      }
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
         tc_fence_after();
-        const uint32_t id = idesc_tf32(128, nb_rows);
+        const int c0 = ka * 32;
+        const uint32_t id = idesc_tf32(128, brows(ka));
         const uint32_t d = tmem + (uint32_t)c0;
         const uint32_t sah = smem_u32(ahi), sal = smem_u32(alo);
         const uint32_t sbh = smem_u32(bhi), sbl = smem_u32(blo);
@@ -359,12 +386,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
         }
         mma_commit(&bars[s]);
       }
-      uses[s] += 1;
+      if (s) ++uses1;
+      else ++uses0;
       last_stage = s;
     }
     if (!ok) break;
     // tile done: wait for its last commit, then TMEM -> registers -> V
-    ok = ok && mbar_wait(&bars[last_stage], (uses[last_stage] - 1) & 1, kWaitIters);
+    {
+      const uint32_t ul = last_stage ? uses1 : uses0;
+      ok = ok && mbar_wait(&bars[last_stage], (ul - 1) & 1, kWaitIters);
+    }
     if (!__syncthreads_and(ok)) {
       ok = false;
       break;
@@ -378,9 +409,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
       tmem_wait_ld();
       const int j0 = c8 * 8;
       if (row < a.n) {
+        if (j0 + 7 < a.K) {
+          float* dst = a.V + row * a.ldv + j0;
+          const float4 m0 = __ldg(reinterpret_cast<const float4*>(a.muR + j0));
+          const float4 m1 = __ldg(reinterpret_cast<const float4*>(a.muR + j0 + 4));
+          reinterpret_cast<float4*>(dst)[0] = make_float4(v[0] - m0.x, v[1] - m0.y, v[2] - m0.z, v[3] - m0.w);
+          reinterpret_cast<float4*>(dst)[1] = make_float4(v[4] - m1.x, v[5] - m1.y, v[6] - m1.z, v[7] - m1.w);
+        } else {
 #pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (j0 + u < a.K) a.V[row * a.ldv + j0 + u] = v[u] - a.muR[j0 + u];
+          for (int u = 0; u < 8; ++u)
+            if (j0 + u < a.K) a.V[row * a.ldv + j0 + u] = v[u] - a.muR[j0 + u];
+        }
       }
     }
     tc_fence_before();
@@ -388,7 +427,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
   }
   if (!ok) {
     // let any MMA still in flight finish before releasing TMEM
-    if (last_stage >= 0) mbar_wait(&bars[last_stage], (uses[last_stage] - 1) & 1, kWaitIters);
+    if (last_stage >= 0) {
+      const uint32_t ul = last_stage ? uses1 : uses0;
+      mbar_wait(&bars[last_stage], (ul - 1) & 1, kWaitIters);
+    }
     if (tid == 0) atomicExch(a.err, 1);
   }
   tc_fence_before();
@@ -424,12 +466,20 @@ hef_status apply_tc(float* V, long long ldv, long long n, int K, const float* Ri
   a.RtL = RtL;
   a.muR = muR;
   a.err = err;
-  const size_t stage = 2 * 128 * 128 + 2 * (size_t)Kq * 128;
-  const size_t smem = 1024 + 2 * stage + 64;
-  HEF_CHECK_CUDA(cudaFuncSetAttribute(k_apply_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   const long long ntiles = (n + 127) / 128;
   const int ctas = (int)(ntiles < num_sms() ? ntiles : num_sms());
-  HEF_LAUNCH("k_apply_tc", st, k_apply_tc<<<ctas, kTcThreads, smem, st>>>(a));
+  const int nka = Kd / 32;
+  const size_t bres = (size_t)(nka * Kq - 16 * nka * (nka - 1)) * 256;  // resident B, hi + lo
+  const size_t smem_res = 1024 + bres + 2 * (2 * 128 * 128) + 64;
+  if (smem_res <= 220 * 1024) {
+    HEF_ENSURE_SMEM(k_apply_tc<true>, (int)smem_res);
+    HEF_LAUNCH("k_apply_tc", st, k_apply_tc<true><<<ctas, kTcThreads, smem_res, st>>>(a));
+  } else {
+    const size_t stage = 2 * 128 * 128 + 2 * (size_t)Kq * 128;
+    const size_t smem = 1024 + 2 * stage + 64;
+    HEF_ENSURE_SMEM(k_apply_tc<false>, (int)smem);
+    HEF_LAUNCH("k_apply_tc", st, k_apply_tc<false><<<ctas, kTcThreads, smem, st>>>(a));
+  }
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
@@ -464,10 +514,10 @@ hef_status gram_tc(const float* V, long long ldv, long long n, int K, double* pa
   a.err = err;
   const size_t smem = 1024 + 4 * (size_t)nb * 128 * 128 + 64;
   if (nb == 1) {
-    HEF_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HEF_ENSURE_SMEM(k_gram_tc<1>, (int)smem);
     HEF_LAUNCH("k_gram_tc", st, k_gram_tc<1><<<ctas, kTcThreads, smem, st>>>(a));
   } else {
-    HEF_CHECK_CUDA(cudaFuncSetAttribute(k_gram_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    HEF_ENSURE_SMEM(k_gram_tc<2>, (int)smem);
     HEF_LAUNCH("k_gram_tc", st, k_gram_tc<2><<<ctas, kTcThreads, smem, st>>>(a));
   }
   HEF_LAUNCH("k_gram_tc_reduce", st,

@@ -34,21 +34,22 @@ __device__ __forceinline__ float lowest<float>() {
   return -FLT_MAX;
 }
 
-// Max and min of each lane's columns over the pins of one hyperedge; four
-// pin rows are loaded before any is reduced, so long hyperedges keep several
-// row reads in flight.
+// Max and min of each lane's columns over the pins of one hyperedge.  Pins
+// are taken four at a time with the indices past the end clamped to the last
+// pin (a repeated pin changes neither max nor min), so even a 2- or 3-pin
+// hyperedge has all its rows in flight at once.
 template <typename T, int NC>
 __device__ __forceinline__ void edge_extrema(const T* __restrict__ Q, long long ldq, int K,
                                              const int32_t* __restrict__ cpins, int a, int b,
                                              int lane, T (&mx)[NC], T (&mn)[NC]) {
 #pragma unroll
   for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
-  int t = a;
-  for (; t + 4 <= b; t += 4) {
+  for (int t = a; t < b; t += 4) {
+    const int last = b - 1;
     const T* r0 = Q + (long long)cpins[t] * ldq;
-    const T* r1 = Q + (long long)cpins[t + 1] * ldq;
-    const T* r2 = Q + (long long)cpins[t + 2] * ldq;
-    const T* r3 = Q + (long long)cpins[t + 3] * ldq;
+    const T* r1 = Q + (long long)cpins[min(t + 1, last)] * ldq;
+    const T* r2 = Q + (long long)cpins[min(t + 2, last)] * ldq;
+    const T* r3 = Q + (long long)cpins[min(t + 3, last)] * ldq;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int col = lane + 32 * c;
@@ -56,18 +57,6 @@ __device__ __forceinline__ void edge_extrema(const T* __restrict__ Q, long long 
         const T v0 = r0[col], v1 = r1[col], v2 = r2[col], v3 = r3[col];
         mx[c] = fmax(fmax(mx[c], fmax(v0, v1)), fmax(v2, v3));
         mn[c] = fmin(fmin(mn[c], fmin(v0, v1)), fmin(v2, v3));
-      }
-    }
-  }
-  for (; t < b; ++t) {
-    const T* r0 = Q + (long long)cpins[t] * ldq;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const int col = lane + 32 * c;
-      if (col < K) {
-        const T v = r0[col];
-        mx[c] = fmax(mx[c], v);
-        mn[c] = fmin(mn[c], v);
       }
     }
   }
