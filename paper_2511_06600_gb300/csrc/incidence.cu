@@ -228,34 +228,60 @@ __device__ __forceinline__ void flag(unsigned int* status, unsigned bits, int e)
   atomicMin(&status[1], (unsigned)e);
 }
 
-// One warp per hyperedge: offsets, weight, pin range, duplicate pins.
+// Offsets, weight, pin range and duplicate pins of every hyperedge: one
+// thread per hyperedge, its warp together for hyperedges with > 32 pins.
 __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict__ eptr,
                            const int32_t* __restrict__ pins, const double* __restrict__ w,
                            unsigned int* status) {
   const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  if (warp == 0 && lane == 0) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (eptr[0] != 0 || eptr[m] != P) flag(status, HEF_BAD_EPTR, 0);
   }
-  for (long long e = warp; e < m; e += nwarps) {
-    const long long a = eptr[e], b = eptr[e + 1];
-    if (a < 0 || b < a || b > P) {
-      if (lane == 0) flag(status, HEF_BAD_EPTR, (int)e);
-      continue;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < m;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long e = base + threadIdx.x;
+    long long a = 0, b = 0;
+    bool big = false;
+    if (e < m) {
+      a = eptr[e], b = eptr[e + 1];
+      if (a < 0 || b < a || b > P) {
+        flag(status, HEF_BAD_EPTR, (int)e);
+        a = b = 0;
+      }
+      const double we = w[e];
+      if (!(we > 0.0 && we <= 1.7976931348623157e308)) flag(status, HEF_BAD_WEIGHT, (int)e);
+      const int k = (int)(b - a);
+      if (k > 32) {
+        big = true;
+      } else {
+        bool bad_pin = false, dup = false;
+        for (int i = 0; i < k; ++i) {
+          const int p = pins[a + i];
+          if (p < 0 || p >= n) bad_pin = true;
+          for (int j = i + 1; j < k; ++j)
+            if (pins[a + j] == p) dup = true;
+        }
+        if (bad_pin) flag(status, HEF_BAD_PIN, (int)e);
+        if (dup) flag(status, HEF_DUP_PIN, (int)e);
+      }
     }
-    const double we = w[e];
-    if (lane == 0 && !(we > 0.0 && we <= 1.7976931348623157e308)) flag(status, HEF_BAD_WEIGHT, (int)e);
-    const int k = (int)(b - a);
-    bool bad_pin = false, dup = false;
-    for (int i = lane; i < k; i += 32) {
-      const int p = pins[a + i];
-      if (p < 0 || p >= n) bad_pin = true;
-      for (int j = i + 1; j < k; ++j)
-        if (pins[a + j] == p) dup = true;
+    unsigned mask = __ballot_sync(0xffffffffu, big);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const long long ba = __shfl_sync(0xffffffffu, a, src), bb = __shfl_sync(0xffffffffu, b, src);
+      const int k = (int)(bb - ba);
+      bool bad_pin = false, dup = false;
+      for (int i = lane; i < k; i += 32) {
+        const int p = pins[ba + i];
+        if (p < 0 || p >= n) bad_pin = true;
+        for (int j = i + 1; j < k; ++j)
+          if (pins[ba + j] == p) dup = true;
+      }
+      const long long ee = base + (threadIdx.x & ~31u) + src;
+      if (__any_sync(0xffffffffu, bad_pin) && lane == 0) flag(status, HEF_BAD_PIN, (int)ee);
+      if (__any_sync(0xffffffffu, dup) && lane == 0) flag(status, HEF_DUP_PIN, (int)ee);
     }
-    if (bad_pin) flag(status, HEF_BAD_PIN, (int)e);
-    if (dup) flag(status, HEF_DUP_PIN, (int)e);
   }
 }
 
@@ -289,34 +315,57 @@ __global__ void k_edge_fill(int m, int clique_mode, const int64_t* __restrict__ 
                             const int32_t* __restrict__ sched, const int32_t* __restrict__ ceptr,
                             unsigned int* status, unsigned int* counter, int32_t* perm,
                             int32_t* cpins, int32_t* slot_edge, double* ew, double* ewh, double* ez,
-                            int* deg, double* part, double* totals) {
+                            float* f_ew, float* f_ewh, float* f_ez, int* deg, double* part,
+                            double* totals) {
   if (status[0]) return;
   double wsum = 0.0;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int e = sched[i];
-    const long long a = eptr[e];
-    const int c0 = ceptr[i];
-    const int k = ceptr[i + 1] - c0;
-    perm[i] = e;
-    for (int t = 0; t < k; ++t) {
-      const int p = pins[a + t];
-      cpins[c0 + t] = p;
-      slot_edge[c0 + t] = (int32_t)i;
-      atomicAdd(&deg[p], 1);
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < m;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    const bool valid = i < m;
+    int e = 0, c0 = 0, k = 0;
+    long long a = 0;
+    if (valid) {
+      e = sched[i];
+      a = eptr[e];
+      c0 = ceptr[i];
+      k = ceptr[i + 1] - c0;
+      perm[i] = e;
+      if (k <= 32) {
+        for (int t = 0; t < k; ++t) {
+          const int p = pins[a + t];
+          cpins[c0 + t] = p;
+          slot_edge[c0 + t] = (int32_t)i;
+          atomicAdd(&deg[p], 1);
+        }
+      }
     }
+    unsigned mask = __ballot_sync(0xffffffffu, valid && k > 32);
+    while (mask) {  // long hyperedges: the warp copies their pins
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const long long sa = __shfl_sync(0xffffffffu, a, src);
+      const int sc0 = __shfl_sync(0xffffffffu, c0, src), sk = __shfl_sync(0xffffffffu, k, src);
+      for (int t = lane; t < sk; t += 32) {
+        const int p = pins[sa + t];
+        cpins[sc0 + t] = p;
+        slot_edge[sc0 + t] = (int32_t)(base + (threadIdx.x & ~31u) + src);
+        atomicAdd(&deg[p], 1);
+      }
+    }
+    if (!valid) continue;
     const double we = w[e];
+    double wa = 0.0, bh = 0.0, z = 0.0;
     if (k >= 2) {
-      ew[i] = we;
-      ewh[i] = clique_mode == HEF_CLIQUE_PAPER ? we / (0.5 * (double)k * (double)(k - 1))
-                                               : we / (double)(k - 1);
-      ez[i] = we / (double)k;
+      wa = we;
+      bh = clique_mode == HEF_CLIQUE_PAPER ? we / (0.5 * (double)k * (double)(k - 1))
+                                           : we / (double)(k - 1);
+      z = we / (double)k;
       wsum += we;
-    } else {
-      ew[i] = 0.0;
-      ewh[i] = 0.0;
-      ez[i] = 0.0;
     }
+    ew[i] = wa, ewh[i] = bh, ez[i] = z;
+    f_ew[i] = (float)wa, f_ewh[i] = (float)bh, f_ez[i] = (float)z;
   }
   double v[1] = {wsum};
   block_partials<1>(v, part);
@@ -325,6 +374,24 @@ __global__ void k_edge_fill(int m, int clique_mode, const int64_t* __restrict__ 
     reduce_slots(part, gridDim.x, 1, tot);
     if (threadIdx.x == 0) totals[2] = tot[0];
   }
+}
+
+// flags of hyperedges with more than kBigEdge pins (internal order)
+__global__ void k_big_flags(int m, const int32_t* __restrict__ ceptr, const unsigned int* status,
+                            int* flags) {
+  if (status[0]) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x)
+    flags[i] = (ceptr[i + 1] - ceptr[i]) > kBigEdge ? 1 : 0;
+}
+
+__global__ void k_big_scatter(int m, const int32_t* __restrict__ ceptr,
+                              const int32_t* __restrict__ pos, const unsigned int* status,
+                              int32_t* idx) {
+  if (status[0]) return;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < m;
+       i += (long long)gridDim.x * blockDim.x)
+    if ((ceptr[i + 1] - ceptr[i]) > kBigEdge) idx[pos[i]] = (int32_t)i;
 }
 
 __global__ void k_csr_edges(long long P, const int32_t* __restrict__ vslot,
@@ -352,7 +419,9 @@ __global__ void k_node_scalars(int n, const int32_t* __restrict__ vptr, const in
                                const int32_t* __restrict__ ceptr, const double* __restrict__ ewh,
                                const double* __restrict__ ez, unsigned int* status,
                                unsigned int* counter, double* dc, double* db, double* inv_dc,
-                               double* inv_db, double* wsc, double* part, double* totals) {
+                               double* inv_db, double* wsc, float* f_dc, float* f_db,
+                               float* f_inv_dc, float* f_inv_db, float* f_wsc, double* part,
+                               double* totals) {
   if (status[0]) return;
   double sc = 0.0, sb = 0.0;
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
@@ -370,6 +439,8 @@ __global__ void k_node_scalars(int n, const int32_t* __restrict__ vptr, const in
     db[v] = b;
     inv_dc[v] = c > 0.0 ? 1.0 / c : 0.0;
     inv_db[v] = b > 0.0 ? 1.0 / b : 0.0;
+    f_wsc[v] = (float)ws, f_dc[v] = (float)c, f_db[v] = (float)b;
+    f_inv_dc[v] = (float)inv_dc[v], f_inv_db[v] = (float)inv_db[v];
     sc += c;
     sb += b;
   }
@@ -412,6 +483,8 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   L->h.ceptr = c.take<int32_t>(m + 1);
   L->h.cpins = c.take<int32_t>(P > 0 ? P : 1);
   L->h.slot_edge = c.take<int32_t>(P > 0 ? P : 1);
+  L->h.big_idx = c.take<int32_t>(m > 0 ? m : 1);
+  L->h.big_pos = c.take<int32_t>(m + 1);
   L->h.ew = c.take<double>(m > 0 ? m : 1);
   L->h.ewh = c.take<double>(m > 0 ? m : 1);
   L->h.ez = c.take<double>(m > 0 ? m : 1);
@@ -423,6 +496,14 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   L->h.inv_dc = c.take<double>(n > 0 ? n : 1);
   L->h.inv_db = c.take<double>(n > 0 ? n : 1);
   L->h.wsc = c.take<double>(n > 0 ? n : 1);
+  L->h.f_ew = c.take<float>(m > 0 ? m : 1);
+  L->h.f_ewh = c.take<float>(m > 0 ? m : 1);
+  L->h.f_ez = c.take<float>(m > 0 ? m : 1);
+  L->h.f_dc = c.take<float>(n > 0 ? n : 1);
+  L->h.f_db = c.take<float>(n > 0 ? n : 1);
+  L->h.f_inv_dc = c.take<float>(n > 0 ? n : 1);
+  L->h.f_inv_db = c.take<float>(n > 0 ? n : 1);
+  L->h.f_wsc = c.take<float>(n > 0 ? n : 1);
   L->h.totals = c.take<double>(8);
   L->keys = c.take<uint32_t>(NS > 0 ? NS : 1);
   L->vals = c.take<int32_t>(NS > 0 ? NS : 1);
@@ -501,8 +582,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
 
   // 1. validation (one warp per hyperedge)
   {
-    long long warps = m > 0 ? m : 1;
-    int grid = stride_grid(warps * 32, 8);
+    int grid = stride_grid(m > 0 ? m : 1, 8);
     HEF_LAUNCH("k_validate", st, k_validate<<<grid, kThreads, 0, st>>>((int)n, (int)m, P, eptr, pins, w, h->status));
     HEF_TRY_CUDA(cudaGetLastError());
   }
@@ -519,10 +599,20 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     HEF_TRY_CUDA(cudaMemsetAsync(L.tmp, 0, sizeof(int) * (n + 1), st));
     HEF_LAUNCH("k_edge_fill", st, k_edge_fill<<<grid, kThreads, 0, st>>>((int)m, clique_mode, eptr, pins, w, L.vals, h->ceptr,
                                            h->status, h->counter, h->perm, h->cpins, h->slot_edge,
-                                           h->ew, h->ewh, h->ez, L.tmp, L.part, h->totals));
+                                           h->ew, h->ewh, h->ez, h->f_ew, h->f_ewh, h->f_ez, L.tmp,
+                                           L.part, h->totals));
+    HEF_TRY_CUDA(cudaGetLastError());
+    // list of large hyperedges (scored by whole CTAs)
+    HEF_LAUNCH("k_big_flags", st, k_big_flags<<<grid, kThreads, 0, st>>>((int)m, h->ceptr, h->status,
+                                                                        h->big_pos));
+    HEF_TRY_CUDA(cudaGetLastError());
+    HEF_TRY(exclusive_scan(h->big_pos, h->big_pos, m, L.scan_bsum, st));
+    HEF_LAUNCH("k_big_scatter", st, k_big_scatter<<<grid, kThreads, 0, st>>>(
+                                        (int)m, h->ceptr, h->big_pos, h->status, h->big_idx));
     HEF_TRY_CUDA(cudaGetLastError());
   } else {
     HEF_TRY_CUDA(cudaMemsetAsync(h->ceptr, 0, sizeof(int32_t), st));
+    HEF_TRY_CUDA(cudaMemsetAsync(h->big_pos, 0, sizeof(int32_t), st));
     HEF_TRY_CUDA(cudaMemsetAsync(h->totals, 0, 8 * sizeof(double), st));
   }
   // 3. vertex-major transpose: stable sort of CSC slots by vertex
@@ -540,7 +630,8 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     int grid = stride_grid(n);
     HEF_LAUNCH("k_node_scalars", st, k_node_scalars<<<grid, kThreads, 0, st>>>((int)n, h->vptr, h->vedge, h->ceptr, h->ewh, h->ez,
                                               h->status, h->counter, h->dc, h->db, h->inv_dc,
-                                              h->inv_db, h->wsc, L.part, h->totals));
+                                              h->inv_db, h->wsc, h->f_dc, h->f_db, h->f_inv_dc,
+                                              h->f_inv_db, h->f_wsc, L.part, h->totals));
     HEF_TRY_CUDA(cudaGetLastError());
   }
 #undef HEF_TRY

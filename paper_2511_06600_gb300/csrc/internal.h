@@ -16,6 +16,8 @@ struct hef_incidence {
   int32_t* ceptr = nullptr;         // m+1: CSC offsets (internal order)
   int32_t* cpins = nullptr;         // P: pins (internal order)
   int32_t* slot_edge = nullptr;     // P: internal hyperedge of each CSC slot
+  int32_t* big_idx = nullptr;       // m: internal ids of hyperedges with > 64 pins
+  int32_t* big_pos = nullptr;       // m+1: exclusive scan of the big flags; [m] = count
   double* ew = nullptr;             // m: w_e, 0 when |e| < 2
   double* ewh = nullptr;            // m: clique pair weight, 0 when |e| < 2
   double* ez = nullptr;             // m: star weight w_e/|e|, 0 when |e| < 2
@@ -28,15 +30,28 @@ struct hef_incidence {
   double* inv_db = nullptr;         // n: 1/db (0 for isolated)
   double* wsc = nullptr;            // n: sum of clique pair weights over e ∋ v
   double* totals = nullptr;         // [0] sum dc, [1] sum db, [2] sum w (|e|>=2)
+  // FP32 copies of the scalars above, read by the FP32 form's kernels
+  float* f_ew = nullptr;
+  float* f_ewh = nullptr;
+  float* f_ez = nullptr;
+  float* f_dc = nullptr;
+  float* f_db = nullptr;
+  float* f_inv_dc = nullptr;
+  float* f_inv_db = nullptr;
+  float* f_wsc = nullptr;
 };
 
 namespace hef {
+
+constexpr int kBigEdge = 64;  // hyperedges with more pins are scored by a whole CTA
 
 // Kernel-side view of the incidence (passed by value to kernels).
 struct IncView {
   int n, m, P;
   const unsigned int* status;
   const int32_t* perm;
+  const int32_t* big_idx;
+  const int32_t* big_pos;
   const int32_t* ceptr;
   const int32_t* cpins;
   const double* ew;
@@ -60,6 +75,8 @@ inline IncView view(const hef_incidence* h) {
   v.P = (int)h->P;
   v.status = h->status;
   v.perm = h->perm;
+  v.big_idx = h->big_idx;
+  v.big_pos = h->big_pos;
   v.ceptr = h->ceptr;
   v.cpins = h->cpins;
   v.ew = h->ew;
@@ -78,6 +95,58 @@ inline IncView view(const hef_incidence* h) {
 }
 
 hef_status check_stream_ptrs(const void* p, const char* what);
+
+// The expansion scalars in the arithmetic type of a form (FP64 arrays for
+// double, their FP32 copies for float).
+template <typename T>
+struct ScalView {
+  const T* ew;
+  const T* ewh;
+  const T* ez;
+  const T* dc;
+  const T* db;
+  const T* inv_dc;
+  const T* inv_db;
+  const T* wsc;
+};
+
+inline ScalView<double> scal_view_d(const hef_incidence* h) {
+  return {h->ew, h->ewh, h->ez, h->dc, h->db, h->inv_dc, h->inv_db, h->wsc};
+}
+inline ScalView<float> scal_view_f(const hef_incidence* h) {
+  return {h->f_ew, h->f_ewh, h->f_ez, h->f_dc, h->f_db, h->f_inv_dc, h->f_inv_db, h->f_wsc};
+}
+template <typename T>
+inline ScalView<T> scal_view(const hef_incidence* h);
+template <>
+inline ScalView<double> scal_view<double>(const hef_incidence* h) {
+  return scal_view_d(h);
+}
+template <>
+inline ScalView<float> scal_view<float>(const hef_incidence* h) {
+  return scal_view_f(h);
+}
+
+// Forward tape of the Krylov chains (hef_krylov_basis_tape), read by the
+// backward: coefficients as used by the forward, then the unnormalised chain
+// vectors u_j (x_j = u_j * inv_nu[j]) for j = 0..k.
+struct TapeLayout {
+  double* coef;    // (k+1) x 2S x 4: [deflation, deflation (star edges), alpha, beta]
+  double* inv_nu;  // (k+1) x 2S
+  void* uc;        // (k+1) x n x S
+  void* ub;        // (k+1) x (n+m) x S
+};
+
+inline size_t carve_tape(void* base, long long n, long long m, int k, int S, size_t esz,
+                         TapeLayout* t) {
+  Carver c(base);
+  t->coef = c.take<double>((size_t)(k + 1) * 2 * S * 4);
+  t->inv_nu = c.take<double>((size_t)(k + 1) * 2 * S);
+  t->uc = c.take<char>((size_t)(k + 1) * n * S * esz);
+  t->ub = c.take<char>((size_t)(k + 1) * (n + m) * S * esz);
+  if (!base) t->uc = t->ub = nullptr, t->coef = t->inv_nu = nullptr;
+  return c.bytes();
+}
 
 // Tensor-core (tcgen05, 3xTF32) Gram matrix of an FP32 basis with K + 1 <= 256
 // (ortho_tc.cu): G = V^T V (K x K), c = V^T 1; part is per-CTA scratch.

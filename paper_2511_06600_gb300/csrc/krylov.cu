@@ -44,8 +44,12 @@ struct KView {
   T* se;  // m x S
   double* inv_nu;  // (k+1) x 2S
   double* coef;    // (k+1) x 2S x 4: [ct, ct2, alpha, beta]
+  T* nuT;          // inv_nu in the working type
+  T* cfT;          // (k+1) x 2S x 4: [ct, ct2, alpha * nu_{j-1}, beta * nu_{j-2}]
   double* te;      // 3S: star edge-row dots of the current step
   GridRed red;     // reduction scratch shared by all kernels (serialised)
+  T* tape_c;       // nullable: u_j of the clique chains, (k+1) x n x S
+  T* tape_b;       // nullable: u_j of the star chains, (k+1) x (n+m) x S
   double tol;      // breakdown threshold on the D-norm of a new vector
 };
 
@@ -248,33 +252,33 @@ __device__ __forceinline__ void seg_sum2(bool valid, int a, int b, Idx idx, RowA
 // D-weighted dots of the raw starts with the trivial vectors -> coef[0].
 // Rows: [0, n) clique, [n, 2n) star vertices, [2n, 2n+m) star hyperedges.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, KView<T> kv,
+__global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, ScalView<T> sv, KView<T> kv,
                                                          const double* __restrict__ x0c,
                                                          const double* __restrict__ x0b) {
   if (g.status[0]) return;
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[3][S];
+  T acc[3][S];
 #pragma unroll
   for (int q = 0; q < 3; ++q)
 #pragma unroll
-    for (int s = 0; s < S; ++s) acc[q][s] = 0.0;
+    for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (r < g.n) {
-    const double d = g.dc[r];
+    const T d = sv.dc[r];
 #pragma unroll
-    for (int s = 0; s < S; ++s) acc[0][s] = d * x0c[r * S + s];
+    for (int s = 0; s < S; ++s) acc[0][s] = d * (T)x0c[r * S + s];
   } else if (r < 2ll * g.n) {
     const long long v = r - g.n;
-    const double d = g.db[v];
+    const T d = sv.db[v];
 #pragma unroll
-    for (int s = 0; s < S; ++s) acc[1][s] = d * x0b[v * S + s];
+    for (int s = 0; s < S; ++s) acc[1][s] = d * (T)x0b[v * S + s];
   } else if (r < 2ll * g.n + g.m) {
     const int i = (int)(r - 2ll * g.n);
-    const double d = g.ew[i];
+    const T d = sv.ew[i];
     const long long src = (long long)(g.n + g.perm[i]) * S;
 #pragma unroll
-    for (int s = 0; s < S; ++s) acc[2][s] = d * x0b[src + s];
+    for (int s = 0; s < S; ++s) acc[2][s] = d * (T)x0b[src + s];
   }
-  block_partials_qs<3, S, double>(acc, kv.red.part);
+  block_partials_qs<3, S, T>(acc, kv.red.part);
   __shared__ double tot[3 * kMaxS];
   if (grid_reduce(kv.red, 3 * S, tot)) {
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
@@ -284,62 +288,63 @@ __global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, KView<T> kv,
       cc[1] = 0.0;
       cb[0] = g.totals[1] > 0 ? tot[1 * S + s] / g.totals[1] : 0.0;
       cb[1] = g.totals[2] > 0 ? tot[2 * S + s] / g.totals[2] : 0.0;
+      T* tc = kv.cfT + (size_t)s * 4;
+      T* tb = kv.cfT + (size_t)(S + s) * 4;
+      tc[0] = (T)cc[0], tc[1] = (T)0, tb[0] = (T)cb[0], tb[1] = (T)cb[1];
     }
   }
 }
 
 // x_0 = start minus its trivial components; D-norm -> inv_nu[0].
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_start_write(IncView g, KView<T> kv,
+__global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T> sv, KView<T> kv,
                                                           const double* __restrict__ x0c,
                                                           const double* __restrict__ x0b) {
   if (g.status[0]) return;
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  double acc[2][S];
+  T acc[2][S];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
-    for (int s = 0; s < S; ++s) acc[q][s] = 0.0;
+    for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (r < g.n) {
-    const double d = g.dc[r];
+    const T d = sv.dc[r];
     T u[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      const double x = x0c[r * S + s] - (d > 0 ? kv.coef[(size_t)s * 4] : 0.0);
-      u[s] = (T)x;
-      acc[0][s] = d * x * x;
+      u[s] = (T)x0c[r * S + s] - (d > 0 ? kv.cfT[(size_t)s * 4] : (T)0);
+      acc[0][s] = d * u[s] * u[s];
     }
     strow<T, S>(kv.Bc[0] + r * S, u);
+    if (kv.tape_c) strow<T, S>(kv.tape_c + r * S, u);
   } else if (r < 2ll * g.n + g.m) {
     const long long rb = r - g.n;  // star row
-    double d, t;
+    T d;
     long long src;
+    int t;
     if (rb < g.n) {
-      d = g.db[rb];
-      src = rb * S;
-      t = 0;
+      d = sv.db[rb], src = rb * S, t = 0;
     } else {
       const int i = (int)(rb - g.n);
-      d = g.ew[i];
-      src = (long long)(g.n + g.perm[i]) * S;
-      t = 1;
+      d = sv.ew[i], src = (long long)(g.n + g.perm[i]) * S, t = 1;
     }
     T u[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      const double* cb = kv.coef + (size_t)(S + s) * 4;
-      const double x = x0b[src + s] - (d > 0 ? (t == 0 ? cb[0] : cb[1]) : 0.0);
-      u[s] = (T)x;
-      acc[1][s] = d * x * x;
+      const T c = kv.cfT[(size_t)(S + s) * 4 + t];
+      u[s] = (T)x0b[src + s] - (d > 0 ? c : (T)0);
+      acc[1][s] = d * u[s] * u[s];
     }
     strow<T, S>(kv.Bb[0] + rb * S, u);
+    if (kv.tape_b) strow<T, S>(kv.tape_b + rb * S, u);
   }
-  block_partials_qs<2, S, double>(acc, kv.red.part);
+  block_partials_qs<2, S, T>(acc, kv.red.part);
   __shared__ double tot[2 * kMaxS];
   if (grid_reduce(kv.red, 2 * S, tot)) {
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
       const double nu2 = tot[c];  // slot op * S + s == chain c
       kv.inv_nu[c] = nu2 > 0.0 ? 1.0 / sqrt(nu2) : 0.0;
+      kv.nuT[c] = (T)kv.inv_nu[c];
     }
   }
 }
@@ -349,13 +354,18 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, KView<T> kv
 // Edge pass of step j (thread per hyperedge): clique pin sums s_e, star rows
 // (M_b x)_e, and the D-weighted dots of the star hyperedge rows -> te.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, KView<T> kv, int j) {
+__global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, ScalView<T> sv, KView<T> kv, int j) {
   if (g.status[0]) return;
   const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
   const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
   const T* __restrict__ prvb = j >= 3 ? pick2(kv.Bb, j & 1) : nullptr;
-  const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
-  const double* nup = j >= 2 ? kv.inv_nu + (size_t)(j - 2) * 2 * S : nullptr;
+  T ncc[S], ncb[S], npb[S];  // inverse norms of x_{j-1} (clique, star) and x_{j-2} (star)
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    ncc[s] = kv.nuT[(size_t)(j - 1) * 2 * S + s];
+    ncb[s] = kv.nuT[(size_t)(j - 1) * 2 * S + S + s];
+    npb[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + S + s] : (T)0;
+  }
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = e < g.m;
   int a = 0, b = 0;
@@ -373,17 +383,18 @@ __global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, KView<T> kv, 
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (valid) {
     const int k = b - a;
+    const T invk = k >= 2 ? (T)1 / (T)k : (T)0;
     T ye[S], sev[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      sev[s] = sc[s] * (T)nu0[s];
-      ye[s] = k >= 2 ? sb[s] * (T)nu0[S + s] / (T)k : (T)0;
+      sev[s] = sc[s] * ncc[s];
+      ye[s] = sb[s] * ncb[s] * invk;
     }
     strow<T, S>(kv.se + (long long)e * S, sev);
     const long long row = (long long)(g.n + e) * S;
     strow<T, S>(kv.Yb + row, ye);
     if (k >= 2) {
-      const T we = (T)g.ew[e];
+      const T we = sv.ew[e];
       T xc[S], xp[S];
       ldrow<T, S>(curb + row, xc);
       if (prvb) ldrow<T, S>(prvb + row, xp);
@@ -391,8 +402,8 @@ __global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, KView<T> kv, 
       for (int s = 0; s < S; ++s) {
         const T wy = we * ye[s];
         acc[0][s] = wy;
-        acc[1][s] = wy * xc[s] * (T)nu0[S + s];
-        acc[2][s] = prvb ? wy * xp[s] * (T)nup[S + s] : (T)0;
+        acc[1][s] = wy * xc[s] * ncb[s];
+        acc[2][s] = prvb ? wy * xp[s] * npb[s] : (T)0;
       }
     }
   }
@@ -407,34 +418,42 @@ __global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, KView<T> kv, 
 // of x_{j-1} into V, and the Lanczos coefficients of step j (final CTA, with
 // the star hyperedge-row dots of the edge pass).
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, KView<T> kv, int j,
+__global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, ScalView<T> sv, KView<T> kv, int j,
                                                         T* __restrict__ V, long long ldv) {
   if (g.status[0]) return;
   const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
   const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
   const T* __restrict__ prvc = j >= 3 ? pick2(kv.Bc, j & 1) : nullptr;
   const T* __restrict__ prvb = j >= 3 ? pick2(kv.Bb, j & 1) : nullptr;
-  const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
-  const double* nup = j >= 2 ? kv.inv_nu + (size_t)(j - 2) * 2 * S : nullptr;
+  T ncc[S], ncb[S], npc[S], npb[S];
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    ncc[s] = kv.nuT[(size_t)(j - 1) * 2 * S + s];
+    ncb[s] = kv.nuT[(size_t)(j - 1) * 2 * S + S + s];
+    npc[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + s] : (T)0;
+    npb[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + S + s] : (T)0;
+  }
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = v < g.n;
   int a = 0, b = 0;
   if (valid) a = g.vptr[v], b = g.vptr[v + 1];
   const int32_t* __restrict__ ve = g.vedge;
   const T* __restrict__ se = kv.se;
+  const T* __restrict__ ewh = sv.ewh;
+  const T* __restrict__ ez = sv.ez;
   T accc[S], accb[S];
   seg_sum2<T, S>(valid, a, b, [&](int t) { return __ldg(ve + t); },
                  [&](int e) { return se + (long long)e * S; },
                  [&](int e) { return curb + (long long)(g.n + e) * S; },
-                 [&](int e) { return (T)__ldg(g.ewh + e); }, [&](int e) { return (T)__ldg(g.ez + e); },
-                 accc, accb);
+                 [&](int e) { return __ldg(ewh + e); }, [&](int e) { return __ldg(ez + e); }, accc,
+                 accb);
   T acc[6][S];
 #pragma unroll
   for (int q = 0; q < 6; ++q)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (valid) {
-    const T wsum = (T)g.wsc[v];
+    const T wsum = sv.wsc[v];
     T xv[S], xb[S], yc[S], yb[S], xpc[S], xpb[S];
     ldrow<T, S>(curc + (long long)v * S, xv);
     ldrow<T, S>(curb + (long long)v * S, xb);
@@ -442,16 +461,16 @@ __global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, KView<T> kv, 
       ldrow<T, S>(prvc + (long long)v * S, xpc);
       ldrow<T, S>(prvb + (long long)v * S, xpb);
     }
-    const T idc = (T)g.inv_dc[v], idb = (T)g.inv_db[v];
-    const T dcv = (T)g.dc[v], dbv = (T)g.db[v];
+    const T idc = sv.inv_dc[v], idb = sv.inv_db[v];
+    const T dcv = sv.dc[v], dbv = sv.db[v];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      xv[s] *= (T)nu0[s];
-      xb[s] *= (T)nu0[S + s];
+      xv[s] *= ncc[s];
+      xb[s] *= ncb[s];
       yc[s] = idc * (accc[s] - wsum * xv[s]);
-      yb[s] = idb * accb[s] * (T)nu0[S + s];
-      const T pc = prvc ? xpc[s] * (T)nup[s] : (T)0;
-      const T pb = prvb ? xpb[s] * (T)nup[S + s] : (T)0;
+      yb[s] = idb * accb[s] * ncb[s];
+      const T pc = prvc ? xpc[s] * npc[s] : (T)0;
+      const T pb = prvb ? xpb[s] * npb[s] : (T)0;
       acc[0][s] = dcv * yc[s];
       acc[1][s] = dcv * yc[s] * xv[s];
       acc[2][s] = dcv * yc[s] * pc;
@@ -484,20 +503,31 @@ __global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, KView<T> kv, 
         cf[2] = j >= 2 ? tn[4 * S + s] + kv.te[1 * S + s] : 0.0;
         cf[3] = j >= 3 ? tn[5 * S + s] + kv.te[2 * S + s] : 0.0;
       }
+      // working-type copies with the inverse norms folded in
+      T* ct = kv.cfT + ((size_t)j * 2 * S + c) * 4;
+      ct[0] = (T)cf[0];
+      ct[1] = (T)cf[1];
+      ct[2] = (T)(cf[2] * kv.inv_nu[(size_t)(j - 1) * 2 * S + c]);
+      ct[3] = j >= 3 ? (T)(cf[3] * kv.inv_nu[(size_t)(j - 2) * 2 * S + c]) : (T)0;
     }
   }
 }
 
-// Update pass of step j (thread per row): u_j = y - trivial part
+// Update pass of step j (kUpdRows rows per thread): u_j = y - trivial part
 // - alpha x_{j-1} - beta x_{j-2} (written over x_{j-2}'s buffer) and its
 // D-norm -> inv_nu[j].  Rows: [0, n) clique, [n, 2n + m) star.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_update(IncView g, KView<T> kv, int j) {
+__global__ void __launch_bounds__(kThreads) k_update(IncView g, ScalView<T> sv, KView<T> kv, int j) {
   if (g.status[0]) return;
   const bool has_prv = j >= 3;
-  const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
-  const double* nup = has_prv ? kv.inv_nu + (size_t)(j - 2) * 2 * S : nullptr;
-  const double* cf = kv.coef + (size_t)j * 2 * S * 4;
+  // coefficients of both expansions in registers: [op][s][ct, ct2, a, b]
+  T cf[2][S][4];
+#pragma unroll
+  for (int op = 0; op < 2; ++op)
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) cf[op][s][q] = kv.cfT[((size_t)j * 2 * S + op * S + s) * 4 + q];
   T acc[2][S];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
@@ -510,29 +540,31 @@ __global__ void __launch_bounds__(kThreads) k_update(IncView g, KView<T> kv, int
     const long long r = r0 + (long long)it * blockDim.x;
     if (r >= nrows) break;
     const bool clique = r < g.n;
-    const int op = clique ? 0 : 1;
     const long long rr = clique ? r : r - g.n;
     const T* cur = clique ? pick2(kv.Bc, (j - 1) & 1) : pick2(kv.Bb, (j - 1) & 1);
     T* nw = clique ? pick2(kv.Bc, j & 1) : pick2(kv.Bb, j & 1);
     const T* Y = clique ? kv.Yc : kv.Yb;
     T d;
     int tsel;
-    if (clique) d = (T)g.dc[rr], tsel = 0;
-    else if (rr < g.n) d = (T)g.db[rr], tsel = 0;
-    else d = (T)g.ew[rr - g.n], tsel = 1;
+    if (clique) d = sv.dc[rr], tsel = 0;
+    else if (rr < g.n) d = sv.db[rr], tsel = 0;
+    else d = sv.ew[rr - g.n], tsel = 1;
     T y[S], xc[S], xp[S], u[S], dsq[S];
     ldrow<T, S>(Y + rr * S, y);
     ldrow<T, S>(cur + rr * S, xc);
     if (has_prv) ldrow<T, S>(nw + rr * S, xp);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      const double* c = cf + (size_t)(op * S + s) * 4;
-      const T t = d > 0 ? (T)c[tsel] : (T)0;
-      const T p = has_prv ? xp[s] * (T)nup[op * S + s] : (T)0;
-      u[s] = y[s] - t - (T)c[2] * (xc[s] * (T)nu0[op * S + s]) - (T)c[3] * p;
+      const T c0 = clique ? cf[0][s][0] : (tsel ? cf[1][s][1] : cf[1][s][0]);
+      const T ca = clique ? cf[0][s][2] : cf[1][s][2];
+      const T cb = clique ? cf[0][s][3] : cf[1][s][3];
+      const T t = d > 0 ? c0 : (T)0;
+      u[s] = y[s] - t - ca * xc[s] - (has_prv ? cb * xp[s] : (T)0);
       dsq[s] = d * u[s] * u[s];
     }
     strow<T, S>(nw + rr * S, u);
+    if (clique && kv.tape_c) strow<T, S>(kv.tape_c + ((long long)j * g.n + rr) * S, u);
+    if (!clique && kv.tape_b) strow<T, S>(kv.tape_b + ((long long)j * (g.n + g.m) + rr) * S, u);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       if (clique) acc[0][s] += dsq[s];
@@ -542,10 +574,12 @@ __global__ void __launch_bounds__(kThreads) k_update(IncView g, KView<T> kv, int
   block_partials_qs<2, S, T>(acc, kv.red.part);
   __shared__ double tot[2 * kMaxS];
   if (grid_reduce(kv.red, 2 * S, tot)) {
+    const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
       const double nu2 = tot[c];
       const bool alive = nu0[c] > 0.0 && nu2 > kv.tol * kv.tol;
       kv.inv_nu[(size_t)j * 2 * S + c] = alive ? 1.0 / sqrt(nu2) : 0.0;
+      kv.nuT[(size_t)j * 2 * S + c] = (T)kv.inv_nu[(size_t)j * 2 * S + c];
     }
   }
 }
@@ -557,12 +591,14 @@ __global__ void __launch_bounds__(kThreads) k_archive_last(IncView g, KView<T> k
   if (g.status[0]) return;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= g.n) return;
-  const double* nu = kv.inv_nu + (size_t)k * 2 * S;
   T xc[S], xb[S];
   ldrow<T, S>(pick2(kv.Bc, k & 1) + (long long)v * S, xc);
   ldrow<T, S>(pick2(kv.Bb, k & 1) + (long long)v * S, xb);
 #pragma unroll
-  for (int s = 0; s < S; ++s) xc[s] *= (T)nu[s], xb[s] *= (T)nu[S + s];
+  for (int s = 0; s < S; ++s) {
+    xc[s] *= kv.nuT[(size_t)k * 2 * S + s];
+    xb[s] *= kv.nuT[(size_t)k * 2 * S + S + s];
+  }
   T* row = V + (long long)v * ldv + (long long)(k - 1) * 2 * S;
   strow<T, S>(row, xc);
   strow<T, S>(row + S, xb);
@@ -585,6 +621,8 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->se = c.take<T>((m > 0 ? m : 1) * S);
   kv->inv_nu = c.take<double>((size_t)(k + 1) * 2 * S);
   kv->coef = c.take<double>((size_t)(k + 1) * 2 * S * 4);
+  kv->nuT = c.take<T>((size_t)(k + 1) * 2 * S);
+  kv->cfT = c.take<T>((size_t)(k + 1) * 2 * S * 4);
   kv->te = c.take<double>((size_t)3 * S);
   kv->red.part = c.take<double>((size_t)maxblk * 6 * S);
   kv->red.gpart = c.take<double>((size_t)red_groups((int)maxblk) * 6 * S);
@@ -597,18 +635,19 @@ template <typename T, int S>
 hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, const double* x0b,
                         T* V, long long ldv, KView<T>& kv, cudaStream_t st) {
   IncView g = view(inc);
+  const ScalView<T> sv = scal_view<T>(inc);
   const long long n = inc->n, m = inc->m;
   const int grid_all = blocks_for(2 * n + m);
   const int grid_e = blocks_for(m > 0 ? m : 1);
   const int grid_n = blocks_for(n);
   const int grid_upd = blocks_for((2 * n + m + kUpdRows - 1) / kUpdRows);
-  HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, kv, x0c, x0b));
-  HEF_LAUNCH("k_start_write", st, k_start_write<T, S><<<grid_all, kThreads, 0, st>>>(g, kv, x0c, x0b));
+  HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
+  HEF_LAUNCH("k_start_write", st, k_start_write<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
   HEF_CHECK_LAUNCH();
   for (int j = 1; j <= k; ++j) {
-    HEF_LAUNCH("k_edge_pass", st, k_edge_pass<T, S><<<grid_e, kThreads, 0, st>>>(g, kv, j));
-    HEF_LAUNCH("k_node_pass", st, k_node_pass<T, S><<<grid_n, kThreads, 0, st>>>(g, kv, j, V, ldv));
-    HEF_LAUNCH("k_update", st, k_update<T, S><<<grid_upd, kThreads, 0, st>>>(g, kv, j));
+    HEF_LAUNCH("k_edge_pass", st, k_edge_pass<T, S><<<grid_e, kThreads, 0, st>>>(g, sv, kv, j));
+    HEF_LAUNCH("k_node_pass", st, k_node_pass<T, S><<<grid_n, kThreads, 0, st>>>(g, sv, kv, j, V, ldv));
+    HEF_LAUNCH("k_update", st, k_update<T, S><<<grid_upd, kThreads, 0, st>>>(g, sv, kv, j));
     HEF_CHECK_LAUNCH();
   }
   HEF_LAUNCH("k_archive_last", st, k_archive_last<T, S><<<grid_n, kThreads, 0, st>>>(g, kv, k, V, ldv));
@@ -618,22 +657,33 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
 
 template <typename T>
 hef_status run_krylov(const hef_incidence* inc, int k, int S, const double* x0c, const double* x0b,
-                      void* Vv, long long ldv, void* ws, cudaStream_t st) {
+                      void* Vv, long long ldv, void* ws, cudaStream_t st, void* tape = nullptr) {
   KView<T> kv;
   carve_krylov<T>(ws, inc->n, inc->m, k, S, &kv);
+  TapeLayout tl;
+  carve_tape(tape, inc->n, inc->m, k, S, sizeof(T), &tl);
+  kv.tape_c = static_cast<T*>(tl.uc);
+  kv.tape_b = static_cast<T*>(tl.ub);
   kv.tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
   const int ngr = red_groups(blocks_for(2 * inc->n + inc->m));
   HEF_CHECK_CUDA(cudaMemsetAsync(kv.red.gcnt, 0, (ngr + 1) * sizeof(unsigned int), st));
   HEF_CHECK_CUDA(cudaMemsetAsync(kv.red.tcnt, 0, sizeof(unsigned int), st));
   T* V = static_cast<T*>(Vv);
+  hef_status s;
   switch (S) {
-    case 1: return run_krylov_s<T, 1>(inc, k, x0c, x0b, V, ldv, kv, st);
-    case 2: return run_krylov_s<T, 2>(inc, k, x0c, x0b, V, ldv, kv, st);
-    case 4: return run_krylov_s<T, 4>(inc, k, x0c, x0b, V, ldv, kv, st);
-    case 8: return run_krylov_s<T, 8>(inc, k, x0c, x0b, V, ldv, kv, st);
-    case 16: return run_krylov_s<T, 16>(inc, k, x0c, x0b, V, ldv, kv, st);
+    case 1: s = run_krylov_s<T, 1>(inc, k, x0c, x0b, V, ldv, kv, st); break;
+    case 2: s = run_krylov_s<T, 2>(inc, k, x0c, x0b, V, ldv, kv, st); break;
+    case 4: s = run_krylov_s<T, 4>(inc, k, x0c, x0b, V, ldv, kv, st); break;
+    case 8: s = run_krylov_s<T, 8>(inc, k, x0c, x0b, V, ldv, kv, st); break;
+    case 16: s = run_krylov_s<T, 16>(inc, k, x0c, x0b, V, ldv, kv, st); break;
     default: return set_error(HEF_ERR_UNSUPPORTED, "hef_krylov_basis: S must be 1, 2, 4, 8 or 16");
   }
+  if (s || !tape) return s;
+  HEF_CHECK_CUDA(cudaMemcpyAsync(tl.coef, kv.coef, (size_t)(k + 1) * 2 * S * 4 * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+  HEF_CHECK_CUDA(cudaMemcpyAsync(tl.inv_nu, kv.inv_nu, (size_t)(k + 1) * 2 * S * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+  return HEF_OK;
 }
 
 hef_status check_krylov_args(const hef_incidence* inc, int k, int S, int dtype, const char* fn) {
@@ -684,4 +734,36 @@ extern "C" hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int3
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (dtype == HEF_F64) return run_krylov<double>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st);
   return run_krylov<float>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st);
+}
+
+extern "C" size_t hef_krylov_tape_bytes(const hef_incidence* inc, int32_t k, int32_t S, int32_t dtype) {
+  if (check_krylov_args(inc, k, S, dtype, "hef_krylov_tape_bytes")) return 0;
+  TapeLayout tl;
+  return carve_tape(nullptr, inc->n, inc->m, k, S, dtype == HEF_F64 ? 8 : 4, &tl);
+}
+
+extern "C" hef_status hef_krylov_basis_tape(const hef_incidence* inc, int32_t k, int32_t S,
+                                            int32_t dtype, const double* x0_clique,
+                                            const double* x0_star, void* V, int64_t ldv,
+                                            void* tape, size_t tape_bytes, void* workspace,
+                                            size_t workspace_bytes, void* stream) {
+  hef_status s = check_krylov_args(inc, k, S, dtype, "hef_krylov_basis_tape");
+  if (s) return s;
+  const long long K = 2ll * k * S;
+  if (!x0_clique || !x0_star || !V || !tape)
+    return set_error(HEF_ERR_INVALID_ARG, "hef_krylov_basis_tape: NULL array");
+  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  if (ldv < K || (ldv * esz) % 16 || (reinterpret_cast<uintptr_t>(V) & 15))
+    return set_error(HEF_ERR_INVALID_ARG,
+                     "hef_krylov_basis_tape: ldv must be >= K = %lld with 16-byte aligned rows", K);
+  const size_t need = hef_krylov_workspace_bytes(inc, k, S, dtype);
+  const size_t tneed = hef_krylov_tape_bytes(inc, k, S, dtype);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
+    return set_error(HEF_ERR_WORKSPACE, "hef_krylov_basis_tape: workspace needs %zu bytes", need);
+  if ((reinterpret_cast<uintptr_t>(tape) & 255) || tape_bytes < tneed)
+    return set_error(HEF_ERR_WORKSPACE, "hef_krylov_basis_tape: tape needs %zu bytes", tneed);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (dtype == HEF_F64)
+    return run_krylov<double>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st, tape);
+  return run_krylov<float>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st, tape);
 }

@@ -32,6 +32,7 @@ constexpr int kGB = 8;       // Gram: rows/cols of the block a thread owns
 constexpr int kPR = 32;      // Gram: rows per shared-memory panel
 constexpr int kPairs = 256;  // Gram: block pairs (threads) per CTA
 constexpr int kACB = 64;     // apply: output columns per block
+constexpr int kPB = 8;       // elimination: pivots per panel
 
 inline int round8(int K) { return (K + 7) & ~7; }
 
@@ -151,6 +152,21 @@ __global__ void k_gram_reduce(const double* __restrict__ part, const double* __r
   }
 }
 
+// A = G - c c^T / n (FP64, and an FP32 copy for the fast factorisation),
+// over the whole grid so the one-CTA factorisation does no FP64 set-up work.
+__global__ void k_gram_project(const double* __restrict__ G, const double* __restrict__ c, int K,
+                               double n, double* A64, float* A32) {
+  const long long KK = (long long)K * K;
+  const double inv_n = 1.0 / n;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < KK;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(idx / K), j = (int)(idx % K);
+    const double v = G[idx] - c[i] * (c[j] * inv_n);
+    A64[idx] = v;
+    A32[idx] = (float)v;
+  }
+}
+
 struct CholOut {
   void* Rinv;      // Kp x Kp, element type T, upper triangular, zero padded
   void* mu;        // Kp, element type T
@@ -168,60 +184,83 @@ struct CholOut {
 // it.  fast = 0: exact path; runs only when `flag` is set unless `always`.
 template <typename C, typename T>
 __global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
-                                                   const double* __restrict__ c, int K, int Kp,
+                                                   const double* __restrict__ c,
+                                                   const C* __restrict__ Aproj, int K, int Kp,
                                                    double n, double tol, C* Wg, int use_smem,
                                                    int fast, int always, CholOut o) {
   extern __shared__ unsigned char sm_raw[];
   __shared__ double ref[512];
-  __shared__ C piv_inv;
-  __shared__ int keep_j;
+  __shared__ int pk[kPB];  // kept flags of the current panel
   __shared__ int near_def;
   if (!fast && !always && o.flag[0] == 0) return;
   C* W = use_smem ? reinterpret_cast<C*>(sm_raw) : Wg;
   const int W2 = 2 * K;
-  for (long long idx = threadIdx.x; idx < (long long)K * W2; idx += blockDim.x) {
-    const int i = (int)(idx / W2), j = (int)(idx % W2);
-    double v;
-    if (j < K) v = G[(size_t)i * K + j] - c[i] * c[j] / n;
-    else v = (j - K == i) ? 1.0 : 0.0;
-    W[idx] = (C)v;
+  for (int i = (int)(threadIdx.x >> 5); i < K; i += (int)(blockDim.x >> 5)) {
+    C* row = W + (size_t)i * W2;
+    for (int j = (int)(threadIdx.x & 31); j < W2; j += 32)
+      row[j] = j < K ? Aproj[(size_t)i * K + j] : (j - K == i ? (C)1 : (C)0);
   }
   for (int i = threadIdx.x; i < K; i += blockDim.x) ref[i] = G[(size_t)i * K + i];
   if (threadIdx.x == 0) near_def = 0;
   __syncthreads();
-  for (int j = 0; j < K; ++j) {
-    if (threadIdx.x == 0) {
-      const double d = (double)W[(size_t)j * W2 + j];
-      int kj = (ref[j] > 0.0 && d > tol * ref[j]) ? 1 : 0;
-      if (fast && kj && d <= 1e-4 * ref[j]) near_def = 1;
-      keep_j = kj;
-      piv_inv = kj ? (C)(1.0 / sqrt(d)) : (C)0;
-      o.kept[j] = kj;
+  // Blocked: a panel of kPB pivots is eliminated among its own rows by warp 0
+  // (warp-synchronous), then every later row takes the panel's rank-kPB
+  // update in one sweep.  Row j's live columns after its pivot: left j..K-1,
+  // right 0..j (K + 1 values).
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j0 = 0; j0 < K; j0 += kPB) {
+    const int jend = min(K, j0 + kPB);
+    if (wid == 0) {
+      for (int j = j0; j < jend; ++j) {
+        C* rowj = W + (size_t)j * W2;
+        int kj = 0;
+        C pinv = 0;
+        if (lane == 0) {
+          const double d = (double)rowj[j];
+          kj = (ref[j] > 0.0 && d > tol * ref[j]) ? 1 : 0;
+          if (fast && kj && d <= 1e-4 * ref[j]) near_def = 1;
+          pinv = kj ? (C)(1.0 / sqrt(d)) : (C)0;
+          o.kept[j] = kj;
+        }
+        kj = __shfl_sync(0xffffffffu, kj, 0);
+        pinv = __shfl_sync(0xffffffffu, pinv, 0);
+        pk[j - j0] = kj;
+        // scale (or zero) row j over its live columns
+        for (int q0 = lane; q0 <= K; q0 += 32) {
+          const int q = q0 < K - j ? j + q0 : K + (q0 - (K - j));
+          rowj[q] = kj ? rowj[q] * pinv : (C)0;
+        }
+        __syncwarp();
+        if (kj) {  // eliminate column j from the panel's later rows
+          for (int i = j + 1; i < jend; ++i) {
+            C* rowi = W + (size_t)i * W2;
+            const C r = rowj[i];
+            for (int q0 = lane; q0 < K; q0 += 32) {
+              const int nleft = K - j - 1;
+              const int q = q0 < nleft ? j + 1 + q0 : K + (q0 - nleft);
+              rowi[q] -= r * rowj[q];
+            }
+          }
+        }
+        __syncwarp();
+      }
     }
     __syncthreads();
-    const int kj = keep_j;
-    const C pinv = piv_inv;
-    __syncthreads();
-    C* rowj = W + (size_t)j * W2;
-    if (!kj) {  // dropped column: zero its row
-      for (int q = threadIdx.x; q < W2; q += blockDim.x) rowj[q] = (C)0;
-      __syncthreads();
-      continue;
-    }
-    // scale row j: left part j..K-1, right part 0..j
-    for (int q = threadIdx.x; q < W2; q += blockDim.x)
-      if ((q >= j && q < K) || (q >= K && q <= K + j)) rowj[q] *= pinv;
-    __syncthreads();
-    // eliminate column j from rows i > j: row_i -= R[j][i] * row_j over the
-    // K live columns (left j+1..K-1, right 0..j); warps over rows, lanes
-    // over columns
-    const int nleft = K - j - 1;
-    for (int i = j + 1 + (int)(threadIdx.x >> 5); i < K; i += (int)(blockDim.x >> 5)) {
-      const C r = rowj[i];
+    // rank-kPB update of rows i >= jend: live columns left jend..K-1, right 0..jend-1
+    const int nleft = K - jend;
+    for (int i = jend + wid; i < K; i += nw) {
       C* rowi = W + (size_t)i * W2;
-      for (int q0 = threadIdx.x & 31; q0 < K; q0 += 32) {
-        const int q = q0 < nleft ? j + 1 + q0 : K + (q0 - nleft);
-        rowi[q] -= r * rowj[q];
+      C rj[kPB];
+#pragma unroll
+      for (int p = 0; p < kPB; ++p)
+        rj[p] = (j0 + p < jend && pk[p]) ? W[(size_t)(j0 + p) * W2 + i] : (C)0;
+      for (int q0 = lane; q0 < K; q0 += 32) {
+        const int q = q0 < nleft ? jend + q0 : K + (q0 - nleft);
+        C acc = rowi[q];
+#pragma unroll
+        for (int p = 0; p < kPB; ++p)
+          if (j0 + p < jend) acc -= rj[p] * W[(size_t)(j0 + p) * W2 + q];
+        rowi[q] = acc;
       }
     }
     __syncthreads();
@@ -229,12 +268,13 @@ __global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
   // outputs: R (FP64), Rinv = (R^-T)^T (type T), mu, rank, flag
   T* Rinv = static_cast<T*>(o.Rinv);
   T* mu = static_cast<T*>(o.mu);
-  for (long long idx = threadIdx.x; idx < (long long)Kp * Kp; idx += blockDim.x) {
-    const int i = (int)(idx / Kp), j = (int)(idx % Kp);
-    C v = 0;
-    if (i < K && j < K && i <= j) v = W[(size_t)j * W2 + K + i];
-    Rinv[idx] = (T)v;
-    if (i < K && j < K) o.R[(size_t)i * K + j] = (i <= j) ? (double)W[(size_t)i * W2 + j] : 0.0;
+  for (int i = (int)(threadIdx.x >> 5); i < Kp; i += (int)(blockDim.x >> 5)) {
+    for (int j = (int)(threadIdx.x & 31); j < Kp; j += 32) {
+      C v = 0;
+      if (i < K && j < K && i <= j) v = W[(size_t)j * W2 + K + i];
+      Rinv[(size_t)i * Kp + j] = (T)v;
+      if (o.R && i < K && j < K) o.R[(size_t)i * K + j] = (i <= j) ? (double)W[(size_t)i * W2 + j] : 0.0;
+    }
   }
   for (int i = threadIdx.x; i < Kp; i += blockDim.x) mu[i] = i < K ? (T)(c[i] / n) : (T)0;
   __syncthreads();
@@ -384,6 +424,8 @@ struct OrthoWs {
   double* G;
   double* c;
   double* Wg;  // K x 2K FP64 scratch of the exact path
+  double* A64; // projected Gram (FP64)
+  float* A32;  // projected Gram (FP32 copy)
   double* R1;
   double* R2;
   void* Rinv;
@@ -420,6 +462,8 @@ size_t carve_ortho(void* base, long long n, int K, int dtype, OrthoWs* w) {
   w->G = cv.take<double>(KK);
   w->c = cv.take<double>(K);
   w->Wg = cv.take<double>(2 * KK);
+  w->A64 = cv.take<double>(KK);
+  w->A32 = cv.take<float>(KK);
   w->R1 = cv.take<double>(KK);
   w->R2 = cv.take<double>(KK);
   w->Rinv = cv.take<char>((size_t)Kp * Kp * esz);
@@ -466,6 +510,7 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
   double* Rs[2] = {w.R1, w.R2};
 
   const bool use_tc = sizeof(T) == 4 && gram_tc_supported(K);
+  const bool want_R = R_out != nullptr;
   HEF_CHECK_CUDA(cudaMemsetAsync(w.flag, 0, 4 * sizeof(int), st));
   for (int pass = 0; pass < 2; ++pass) {
     CholOut o{w.Rinv, w.mu, Rs[pass], w.kept, w.rank, w.flag};
@@ -481,21 +526,27 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
       HEF_CHECK_LAUNCH();
     }
     if (pass == 0) {
+      if (!want_R) o.R = nullptr;
+      HEF_LAUNCH("k_gram_project", st, k_gram_project<<<stride_grid((long long)K * K, 2), kThreads, 0,
+                                                         st>>>(w.G, w.c, K, (double)n, w.A64, w.A32));
       if (fast_ok) {
         HEF_LAUNCH("k_chol_aug", st, k_chol_aug<float, T><<<1, 1024, fast_smem, st>>>(
-                                         w.G, w.c, K, Kp, (double)n, tol, nullptr, 1, 1, 0, o));
+                                         w.G, w.c, w.A32, K, Kp, (double)n, tol, nullptr, 1, 1, 0, o));
       }
       // exact FP64 path: always for the FP64 form, on demand for the FP32 form
       HEF_LAUNCH("k_chol_aug", st, k_chol_aug<double, T><<<1, 1024, 0, st>>>(
-                                       w.G, w.c, K, Kp, (double)n, tol, w.Wg, 0, 0,
+                                       w.G, w.c, w.A64, K, Kp, (double)n, tol, w.Wg, 0, 0,
                                        fast_ok ? 0 : 1, o));
     } else {
       HEF_CHECK_CUDA(cudaMemsetAsync(w.flag, 0, sizeof(int), st));  // flag[0] only
       HEF_LAUNCH("k_chol_series", st, k_chol_series<T><<<stride_grid((long long)Kp * Kp, 2),
                                                         kThreads, 0, st>>>(
                                           w.G, w.c, K, Kp, (double)n, gtol, o));
+      HEF_LAUNCH("k_gram_project_exact", st,
+                 k_gram_project<<<stride_grid((long long)K * K, 2), kThreads, 0, st>>>(
+                     w.G, w.c, K, (double)n, w.A64, w.A32));
       HEF_LAUNCH("k_chol_aug", st, k_chol_aug<double, T><<<1, 1024, 0, st>>>(
-                                       w.G, w.c, K, Kp, (double)n, tol, w.Wg, 0, 0, 0, o));
+                                       w.G, w.c, w.A64, K, Kp, (double)n, tol, w.Wg, 0, 0, 0, o));
       HEF_LAUNCH("k_rank", st, k_rank<<<1, 32, 0, st>>>(w.kept, K, w.flag, w.rank));
     }
     HEF_CHECK_LAUNCH();

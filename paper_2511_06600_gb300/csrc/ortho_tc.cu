@@ -232,10 +232,16 @@ __global__ void k_rinv_split(const float* __restrict__ Rinv, const float* __rest
   }
   for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < Kq;
        j += (long long)gridDim.x * blockDim.x) {
-    double s = 0.0;
-    if (j < K)
-      for (int i = 0; i <= j; ++i) s += (double)mu[i] * (double)Rinv[(size_t)i * Kp + j];
-    muR[j] = (float)s;
+    float s0 = 0.f, s1 = 0.f;
+    if (j < K) {
+      int i = 0;
+      for (; i + 1 <= (int)j; i += 2) {
+        s0 += mu[i] * Rinv[(size_t)i * Kp + j];
+        s1 += mu[i + 1] * Rinv[(size_t)(i + 1) * Kp + j];
+      }
+      if (i <= (int)j) s0 += mu[i] * Rinv[(size_t)i * Kp + j];
+    }
+    muR[j] = s0 + s1;
   }
 }
 

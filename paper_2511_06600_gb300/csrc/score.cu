@@ -34,17 +34,65 @@ __device__ __forceinline__ float lowest<float>() {
   return -FLT_MAX;
 }
 
-// Max and min of each lane's columns over the pins of one hyperedge.  Pins
-// are taken four at a time with the indices past the end clamped to the last
-// pin (a repeated pin changes neither max nor min), so even a 2- or 3-pin
-// hyperedge has all its rows in flight at once.
+// Extrema of two hyperedges at once (pins [a0, b0) and [a1, b1), warp-uniform):
+// four clamped pin rows of each are in flight together.
 template <typename T, int NC>
-__device__ __forceinline__ void edge_extrema(const T* __restrict__ Q, long long ldq, int K,
-                                             const int32_t* __restrict__ cpins, int a, int b,
-                                             int lane, T (&mx)[NC], T (&mn)[NC]) {
+__device__ __forceinline__ void two_edge_extrema(const T* __restrict__ Q, long long ldq, int K,
+                                                 const int32_t* __restrict__ cpins, int a0, int b0,
+                                                 int a1, int b1, int lane, T (&mx0)[NC],
+                                                 T (&mn0)[NC], T (&mx1)[NC], T (&mn1)[NC]) {
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    mx0[c] = lowest<T>(), mn0[c] = -lowest<T>();
+    mx1[c] = lowest<T>(), mn1[c] = -lowest<T>();
+  }
+  int t0 = a0, t1 = a1;
+  while (t0 < b0 || t1 < b1) {
+    const bool u0 = t0 < b0, u1 = t1 < b1;
+    const int l0 = b0 - 1, l1 = b1 - 1;
+    const T* r[8];
+    r[0] = Q + (long long)(u0 ? cpins[t0] : 0) * ldq;
+    r[1] = Q + (long long)(u0 ? cpins[min(t0 + 1, l0)] : 0) * ldq;
+    r[2] = Q + (long long)(u0 ? cpins[min(t0 + 2, l0)] : 0) * ldq;
+    r[3] = Q + (long long)(u0 ? cpins[min(t0 + 3, l0)] : 0) * ldq;
+    r[4] = Q + (long long)(u1 ? cpins[t1] : 0) * ldq;
+    r[5] = Q + (long long)(u1 ? cpins[min(t1 + 1, l1)] : 0) * ldq;
+    r[6] = Q + (long long)(u1 ? cpins[min(t1 + 2, l1)] : 0) * ldq;
+    r[7] = Q + (long long)(u1 ? cpins[min(t1 + 3, l1)] : 0) * ldq;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const int col = lane + 32 * c;
+      if (col < K) {
+        T v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = r[q][col];
+        if (u0) {
+          mx0[c] = fmax(fmax(mx0[c], fmax(v[0], v[1])), fmax(v[2], v[3]));
+          mn0[c] = fmin(fmin(mn0[c], fmin(v[0], v[1])), fmin(v[2], v[3]));
+        }
+        if (u1) {
+          mx1[c] = fmax(fmax(mx1[c], fmax(v[4], v[5])), fmax(v[6], v[7]));
+          mn1[c] = fmin(fmin(mn1[c], fmin(v[4], v[5])), fmin(v[6], v[7]));
+        }
+      }
+    }
+    t0 += 4;
+    t1 += 4;
+  }
+}
+
+// Column extrema of one large hyperedge by a whole CTA: warp w takes pin
+// batches w, w + 8, ...; partial extrema meet in shared memory (smx/smn,
+// [warp][32 NC]).  On return every thread's columns (lane + 32 c) hold the
+// hyperedge's extrema in mx/mn.
+template <typename T, int NC>
+__device__ __forceinline__ void cta_edge_extrema(const T* __restrict__ Q, long long ldq, int K,
+                                                 const int32_t* __restrict__ cpins, int a, int b,
+                                                 T* smx, T* smn, T (&mx)[NC], T (&mn)[NC]) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
-  for (int t = a; t < b; t += 4) {
+  for (int t = a + 4 * wid; t < b; t += 4 * nw) {
     const int last = b - 1;
     const T* r0 = Q + (long long)cpins[t] * ldq;
     const T* r1 = Q + (long long)cpins[min(t + 1, last)] * ldq;
@@ -60,11 +108,61 @@ __device__ __forceinline__ void edge_extrema(const T* __restrict__ Q, long long 
       }
     }
   }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    smx[wid * 32 * NC + lane + 32 * c] = mx[c];
+    smn[wid * 32 * NC + lane + 32 * c] = mn[c];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    T a_ = lowest<T>(), b_ = -lowest<T>();
+    for (int w = 0; w < nw; ++w) {
+      a_ = fmax(a_, smx[w * 32 * NC + lane + 32 * c]);
+      b_ = fmin(b_, smn[w * 32 * NC + lane + 32 * c]);
+    }
+    mx[c] = a_, mn[c] = b_;
+  }
+  __syncthreads();
 }
 
+// Pass 1, large hyperedges: CTA b handles list entries b, b + grid, ...; its
+// sum of w_e spread^2 per column goes to bpart[b][col] (FP64).
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restrict__ Q, long long ldq,
+                                                    int K, double* bpart) {
+  if (g.status[0]) return;
+  __shared__ T smx[8 * 32 * NC], smn[8 * 32 * NC];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int nbig = g.big_pos[g.m];
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  for (int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+    const int e = g.big_idx[bi];
+    T mx[NC], mn[NC];
+    cta_edge_extrema<T, NC>(Q, ldq, K, g.cpins, g.ceptr[e], g.ceptr[e + 1], smx, smn, mx, mn);
+    const double we = g.ew[e];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      const double sp = (double)(mx[c] - mn[c]);
+      acc[c] += we * sp * sp;
+    }
+  }
+  if (wid == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (lane + 32 * c < K) bpart[(size_t)blockIdx.x * K + lane + 32 * c] = acc[c];
+  }
+}
+
+// Pass 1, hyperedges with 2..kBigEdge pins: warp per group of 32 consecutive
+// hyperedges (two at a time); Q_H[i] = sum of per-CTA partials, then the
+// large hyperedges' partials bpart, in a fixed order.
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restrict__ Q, long long ldq,
-                                                     int K, GridRed red, double* QH, double* invQH,
+                                                     int K, GridRed red, const double* __restrict__ bpart,
+                                                     int nbpart, double* QH, double* invQH,
                                                      double* QH_out) {
   if (g.status[0]) return;
   __shared__ double wred[kThreads / 32][32 * NC];
@@ -75,26 +173,38 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
   T pacc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = 0.0, pacc[c] = 0;
-  int nflush = 0;
-  for (long long e = warp; e < g.m; e += nwarps) {
-    const int a = g.ceptr[e], b = g.ceptr[e + 1];
-    if (b - a < 2) continue;
-    T mx[NC], mn[NC];
-    edge_extrema<T, NC>(Q, ldq, K, g.cpins, a, b, lane, mx, mn);
-    const T we = (T)g.ew[e];
+  const long long ngroups = ((long long)g.m + 31) / 32;
+  for (long long grp = warp; grp < ngroups; grp += nwarps) {
+    const long long e = grp * 32 + lane;
+    int a = 0, b = 0;
+    if (e < g.m) a = g.ceptr[e], b = g.ceptr[e + 1];
+    if (b - a < 2 || b - a > kBigEdge) b = a;  // not scored here
+    const T wl = e < g.m ? (T)g.ew[e] : (T)0;
+    for (int i = 0; i < 32; i += 2) {
+      const int a0 = __shfl_sync(0xffffffffu, a, i), b0 = __shfl_sync(0xffffffffu, b, i);
+      const int a1 = __shfl_sync(0xffffffffu, a, i + 1), b1 = __shfl_sync(0xffffffffu, b, i + 1);
+      const T w0 = __shfl_sync(0xffffffffu, wl, i), w1 = __shfl_sync(0xffffffffu, wl, i + 1);
+      if (a0 == b0 && a1 == b1) continue;
+      T mx0[NC], mn0[NC], mx1[NC], mn1[NC];
+      two_edge_extrema<T, NC>(Q, ldq, K, g.cpins, a0, b0, a1, b1, lane, mx0, mn0, mx1, mn1);
 #pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      const T sp = mx[c] - mn[c];
-      pacc[c] += we * sp * sp;
+      for (int c = 0; c < NC; ++c) {
+        if (b0 > a0) {
+          const T sp = mx0[c] - mn0[c];
+          pacc[c] += w0 * sp * sp;
+        }
+        if (b1 > a1) {
+          const T sp = mx1[c] - mn1[c];
+          pacc[c] += w1 * sp * sp;
+        }
+      }
     }
-    if (sizeof(T) == 8 || ++nflush == kFlushEdges) {
-      nflush = 0;
+    // FP32 partial sums span one group (<= 32 hyperedges); FP64 beyond
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] += (double)pacc[c], pacc[c] = 0;
-    }
+    for (int c = 0; c < NC; ++c) acc[c] += (double)pacc[c], pacc[c] = 0;
   }
 #pragma unroll
-  for (int c = 0; c < NC; ++c) wred[wid][lane + 32 * c] = acc[c] + (double)pacc[c];
+  for (int c = 0; c < NC; ++c) wred[wid][lane + 32 * c] = acc[c];
   __syncthreads();
   for (int col = threadIdx.x; col < K; col += blockDim.x) {
     double s = 0.0;
@@ -104,7 +214,8 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
   __shared__ double tot[32 * NC];
   if (grid_reduce(red, K, tot)) {
     for (int col = threadIdx.x; col < K; col += blockDim.x) {
-      const double s = tot[col];
+      double s = tot[col];
+      for (int q = 0; q < nbpart; ++q) s += bpart[(size_t)q * K + col];
       QH[col] = s;
       invQH[col] = s > kQhTiny ? 1.0 / s : 0.0;
       if (QH_out) QH_out[col] = s;
@@ -112,6 +223,116 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
   }
 }
 
+// Pass 2 for one hyperedge whose extrema a warp holds (lanes over columns):
+// arg-max column (lowest on ties), its pins (lowest position on ties), R_e.
+template <typename T, int NC>
+__device__ __forceinline__ void score_edge_out(IncView g, const T* __restrict__ Q, long long ldq,
+                                               int K, int reduce, const double* __restrict__ QH,
+                                               const T (&iq)[NC], const bool (&use)[NC], int e,
+                                               int a, int b, const T (&mx)[NC], const T (&mn)[NC],
+                                               double* R_out, int32_t* argvec, int32_t* pmax,
+                                               int32_t* pmin) {
+  const int lane = threadIdx.x & 31;
+  T best = (T)-1;
+  int bcol = 0x7fffffff;
+  double sum = 0.0;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    if (use[c]) {
+      const T sp = mx[c] - mn[c];
+      const T r = sp * sp * iq[c];
+      if (reduce == HEF_REDUCE_SUM) {
+        const double spd = (double)sp;
+        sum += spd * spd / QH[lane + 32 * c];
+      }
+      if (r > best) best = r, bcol = lane + 32 * c;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oc = __shfl_xor_sync(0xffffffffu, bcol, o);
+    if (ob > best || (ob == best && oc < bcol)) best = ob, bcol = oc;
+  }
+  if (reduce == HEF_REDUCE_SUM) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  }
+  const bool any = bcol != 0x7fffffff;
+  T vmax = 0, vmin = 0;
+  if (any && lane == (bcol & 31)) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c == (bcol >> 5)) vmax = mx[c], vmin = mn[c];
+  }
+  const int owner = any ? (bcol & 31) : 0;
+  vmax = __shfl_sync(0xffffffffu, vmax, owner);
+  vmin = __shfl_sync(0xffffffffu, vmin, owner);
+  int tmax = 0x7fffffff, tmin = 0x7fffffff;
+  if (any) {
+    for (int t = a + lane; t < b; t += 32) {
+      const T v = Q[(long long)g.cpins[t] * ldq + bcol];
+      if (v == vmax && t < tmax) tmax = t;
+      if (v == vmin && t < tmin) tmin = t;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      tmax = min(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
+      tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
+    }
+  }
+  if (lane == 0) {
+    const int oe = g.perm[e];
+    double Re = 0.0;
+    if (reduce == HEF_REDUCE_SUM) Re = sum;
+    else if (any) {
+      const double spw = (double)(vmax - vmin);
+      Re = spw * spw / QH[bcol];
+    }
+    R_out[oe] = Re;
+    if (argvec) argvec[oe] = any ? bcol : -1;
+    if (pmax) pmax[oe] = any ? g.cpins[tmax] : -1;
+    if (pmin) pmin[oe] = any ? g.cpins[tmin] : -1;
+  }
+}
+
+template <typename T, int NC>
+__device__ __forceinline__ void load_use(const double* __restrict__ QH, const double* __restrict__ invQH,
+                                         int K, T (&iq)[NC], bool (&use)[NC]) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+    const int col = lane + 32 * c;
+    use[c] = col < K && QH[col] > kQhTiny;
+    iq[c] = use[c] ? (T)invQH[col] : (T)0;
+  }
+}
+
+// Pass 2, large hyperedges (one CTA each; warp 0 writes the outputs).
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_score_big2(IncView g, const T* __restrict__ Q, long long ldq,
+                                                    int K, int reduce, const double* __restrict__ QH,
+                                                    const double* __restrict__ invQH, double* R_out,
+                                                    int32_t* argvec, int32_t* pmax, int32_t* pmin) {
+  if (g.status[0]) return;
+  __shared__ T smx[8 * 32 * NC], smn[8 * 32 * NC];
+  T iq[NC];
+  bool use[NC];
+  load_use<T, NC>(QH, invQH, K, iq, use);
+  const int nbig = g.big_pos[g.m];
+  for (int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
+    const int e = g.big_idx[bi];
+    const int a = g.ceptr[e], b = g.ceptr[e + 1];
+    T mx[NC], mn[NC];
+    cta_edge_extrema<T, NC>(Q, ldq, K, g.cpins, a, b, smx, smn, mx, mn);
+    if ((threadIdx.x >> 5) == 0)
+      score_edge_out<T, NC>(g, Q, ldq, K, reduce, QH, iq, use, e, a, b, mx, mn, R_out, argvec, pmax,
+                            pmin);
+  }
+}
+
+// Pass 2, the other hyperedges: warp per group of 32, two at a time; those
+// with < 2 pins get 0 / -1.
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restrict__ Q, long long ldq,
                                                      int K, int reduce, const double* __restrict__ QH,
@@ -123,86 +344,32 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   T iq[NC];
   bool use[NC];
-#pragma unroll
-  for (int c = 0; c < NC; ++c) {
-    const int col = lane + 32 * c;
-    use[c] = col < K && QH[col] > kQhTiny;
-    iq[c] = use[c] ? (T)invQH[col] : (T)0;
-  }
-  for (long long e = warp; e < g.m; e += nwarps) {
-    const int a = g.ceptr[e], b = g.ceptr[e + 1];
-    const int oe = g.perm[e];
-    if (b - a < 2) {
-      if (lane == 0) {
-        R_out[oe] = 0.0;
-        if (argvec) argvec[oe] = -1;
-        if (pmax) pmax[oe] = -1;
-        if (pmin) pmin[oe] = -1;
-      }
-      continue;
+  load_use<T, NC>(QH, invQH, K, iq, use);
+  const long long ngroups = ((long long)g.m + 31) / 32;
+  for (long long grp = warp; grp < ngroups; grp += nwarps) {
+    const long long e = grp * 32 + lane;
+    int a = 0, b = 0;
+    if (e < g.m) a = g.ceptr[e], b = g.ceptr[e + 1];
+    if (e < g.m && b - a < 2) {  // degenerate: no score, no routing
+      const int oe = g.perm[e];
+      R_out[oe] = 0.0;
+      if (argvec) argvec[oe] = -1;
+      if (pmax) pmax[oe] = -1;
+      if (pmin) pmin[oe] = -1;
     }
-    T mx[NC], mn[NC];
-    edge_extrema<T, NC>(Q, ldq, K, g.cpins, a, b, lane, mx, mn);
-    // lane-local best (lowest column on ties), then warp arg-max
-    T best = (T)-1;
-    int bcol = 0x7fffffff;
-    double sum = 0.0;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (use[c]) {
-        const T sp = mx[c] - mn[c];
-        const T r = sp * sp * iq[c];
-        if (reduce == HEF_REDUCE_SUM) {
-          const double spd = (double)sp;
-          sum += spd * spd / QH[lane + 32 * c];
-        }
-        if (r > best) best = r, bcol = lane + 32 * c;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oc = __shfl_xor_sync(0xffffffffu, bcol, o);
-      if (ob > best || (ob == best && oc < bcol)) best = ob, bcol = oc;
-    }
-    if (reduce == HEF_REDUCE_SUM) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    }
-    const bool any = bcol != 0x7fffffff;
-    // value extremes of the winning column, from the lane that owns it
-    T vmax = 0, vmin = 0;
-    if (any && lane == (bcol & 31)) {
-#pragma unroll
-      for (int c = 0; c < NC; ++c)
-        if (c == (bcol >> 5)) vmax = mx[c], vmin = mn[c];
-    }
-    const int owner = any ? (bcol & 31) : 0;
-    vmax = __shfl_sync(0xffffffffu, vmax, owner);
-    vmin = __shfl_sync(0xffffffffu, vmin, owner);
-    // first pin positions attaining them (lanes over the pins of e)
-    int tmax = 0x7fffffff, tmin = 0x7fffffff;
-    if (any) {
-      for (int t = a + lane; t < b; t += 32) {
-        const T v = Q[(long long)g.cpins[t] * ldq + bcol];
-        if (v == vmax && t < tmax) tmax = t;
-        if (v == vmin && t < tmin) tmin = t;
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        tmax = min(tmax, __shfl_xor_sync(0xffffffffu, tmax, o));
-        tmin = min(tmin, __shfl_xor_sync(0xffffffffu, tmin, o));
-      }
-    }
-    const double sp_win = (double)(vmax - vmin);
-    if (lane == 0) {
-      double Re = 0.0;
-      if (reduce == HEF_REDUCE_SUM) Re = sum;
-      else if (any) Re = sp_win * sp_win / QH[bcol];
-      R_out[oe] = Re;
-      if (argvec) argvec[oe] = any ? bcol : -1;
-      if (pmax) pmax[oe] = any ? g.cpins[tmax] : -1;
-      if (pmin) pmin[oe] = any ? g.cpins[tmin] : -1;
+    if (b - a < 2 || b - a > kBigEdge) b = a;
+    for (int i = 0; i < 32; i += 2) {
+      const int a0 = __shfl_sync(0xffffffffu, a, i), b0 = __shfl_sync(0xffffffffu, b, i);
+      const int a1 = __shfl_sync(0xffffffffu, a, i + 1), b1 = __shfl_sync(0xffffffffu, b, i + 1);
+      if (a0 == b0 && a1 == b1) continue;
+      T mx0[NC], mn0[NC], mx1[NC], mn1[NC];
+      two_edge_extrema<T, NC>(Q, ldq, K, g.cpins, a0, b0, a1, b1, lane, mx0, mn0, mx1, mn1);
+      if (b0 > a0)
+        score_edge_out<T, NC>(g, Q, ldq, K, reduce, QH, iq, use, (int)(grp * 32 + i), a0, b0, mx0, mn0,
+                              R_out, argvec, pmax, pmin);
+      if (b1 > a1)
+        score_edge_out<T, NC>(g, Q, ldq, K, reduce, QH, iq, use, (int)(grp * 32 + i + 1), a1, b1, mx1,
+                              mn1, R_out, argvec, pmax, pmin);
     }
   }
 }
@@ -213,7 +380,9 @@ struct ScoreWs {
   double* invQH;
   unsigned int* counter;  // reduction counters (zero between calls)
   double* gpart;
+  double* bpart;          // large hyperedges: per-CTA partial Q_H sums
   int grid;
+  int bgrid;
 };
 
 size_t carve_score(void* base, int K, ScoreWs* w) {
@@ -224,6 +393,8 @@ size_t carve_score(void* base, int K, ScoreWs* w) {
   w->invQH = c.take<double>(K);
   w->counter = c.take<unsigned int>(64);
   w->gpart = c.take<double>((size_t)red_groups(w->grid) * K);
+  w->bgrid = num_sms();
+  w->bpart = c.take<double>((size_t)w->bgrid * K);
   return c.bytes();
 }
 
@@ -237,10 +408,13 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
   red.gpart = w.gpart;
   red.gcnt = w.counter;                 // red_groups(grid) <= 63 counters
   red.tcnt = w.counter + 63;
-  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<w.grid, kThreads, 0, st>>>(g, Q, ldq, K, red, w.QH, w.invQH,
-                                                    QH_out));
-  HEF_LAUNCH("k_score_pass2", st, k_score_pass2<T, NC><<<w.grid, kThreads, 0, st>>>(g, Q, ldq, K, reduce, w.QH, w.invQH, R_out,
-                                                    argvec, pmax, pmin));
+  HEF_LAUNCH("k_score_big1", st, k_score_big1<T, NC><<<w.bgrid, kThreads, 0, st>>>(g, Q, ldq, K, w.bpart));
+  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<w.grid, kThreads, 0, st>>>(
+                                      g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out));
+  HEF_LAUNCH("k_score_big2", st, k_score_big2<T, NC><<<w.bgrid, kThreads, 0, st>>>(
+                                     g, Q, ldq, K, reduce, w.QH, w.invQH, R_out, argvec, pmax, pmin));
+  HEF_LAUNCH("k_score_pass2", st, k_score_pass2<T, NC><<<w.grid, kThreads, 0, st>>>(
+                                      g, Q, ldq, K, reduce, w.QH, w.invQH, R_out, argvec, pmax, pmin));
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
@@ -301,8 +475,8 @@ hef_status noalloc_scratch(void** out) {
 // partial sums fit the fixed scratch.
 size_t carve_score_capped(void* base, int K, size_t cap, ScoreWs* w) {
   // per-CTA partials plus group partials (1/32 as many), Q_H, 1/Q_H, counters
-  const size_t fixed = 5 * 256 + 2 * (size_t)K * sizeof(double) + 64 * sizeof(unsigned int) +
-                       (size_t)K * sizeof(double);
+  const size_t fixed = 6 * 256 + 2 * (size_t)K * sizeof(double) + 64 * sizeof(unsigned int) +
+                       (size_t)K * sizeof(double) + 64 * (size_t)K * sizeof(double);
   long long g = (long long)num_sms() * 4;
   const long long fit = (long long)((cap - fixed) / ((size_t)K * sizeof(double) * 33 / 32 + 1));
   if (g > fit) g = fit;
@@ -313,6 +487,8 @@ size_t carve_score_capped(void* base, int K, size_t cap, ScoreWs* w) {
   w->invQH = c.take<double>(K);
   w->counter = c.take<unsigned int>(64);
   w->gpart = c.take<double>((size_t)red_groups(w->grid) * K);
+  w->bgrid = num_sms();
+  w->bpart = c.take<double>((size_t)w->bgrid * K);
   return c.bytes();
 }
 
