@@ -172,6 +172,21 @@ hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int32_t S,
                             void* workspace, size_t workspace_bytes,
                             void* stream);
 
+/* Krylov basis with a tape for the backward: computes exactly what
+ * hef_krylov_basis computes and also stores in `tape` (device, 256-byte
+ * aligned, hef_krylov_tape_bytes bytes, caller-owned) what
+ * hef_edge_resistance_backward reads: the recurrence coefficients and norms
+ * of every chain and the chain vectors x_0 .. x_k of both expansions (in the
+ * basis dtype).  The tape is (k + 1) * (2n + m) * S elements plus a few KB. */
+size_t hef_krylov_tape_bytes(const hef_incidence* inc, int32_t k, int32_t S,
+                             int32_t dtype);
+hef_status hef_krylov_basis_tape(const hef_incidence* inc, int32_t k,
+                                 int32_t S, int32_t dtype,
+                                 const double* x0_clique,
+                                 const double* x0_star, void* V, int64_t ldv,
+                                 void* tape, size_t tape_bytes,
+                                 void* workspace, size_t workspace_bytes,
+                                 void* stream);
 /* ------------------------------------------------------------------------
  * Orthonormalisation (Algorithm 1 step 4): in place, V (n x K, ldv, dtype)
  * becomes Q with orthonormal, mean-free columns spanning the mean-free parts
@@ -217,6 +232,42 @@ hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q,
                                void* workspace, size_t workspace_bytes,
                                void* stream);
 
+/* ------------------------------------------------------------------------
+ * Backward of the whole path (Algorithm 1 steps 3-7).  The paper defines
+ * only the forward; this is its derivative: given g = dL/dR (R as returned
+ * by hef_edge_resistance with HEF_REDUCE_MAX), it writes
+ *   dw[m]              dL/dw_e (caller's hyperedge order), through Q_H, the
+ *                      expansion weights w/(|e|-1) (or w/C(|e|,2)) and w/|e|,
+ *                      the degrees, and the degree-weighted deflation of the
+ *                      starts;
+ *   dx0_clique[n x S]  dL/d x0_clique (nullable);
+ *   dx0_star[(n+m) x S] dL/d x0_star, same layout as x0_star (nullable).
+ * The routing of the forward is held: the column argvec[e] and the pins
+ * attaining the max and min of each column on e (lowest position on ties) do
+ * not move under a small change of the inputs, so R is piecewise smooth and
+ * this is the derivative of the smooth piece.  The Krylov recurrence
+ * coefficients only change V by an upper-triangular factor, which Q does
+ * not see, so they carry no gradient.
+ * Inputs are the forward's, unchanged: x0_clique / x0_star as given to the
+ * Krylov call; tape from hef_krylov_basis_tape with the same arguments, or
+ * NULL to recompute it inside the workspace (query with recompute = 1); Q
+ * (n x ldq, dtype) and R_fac (K x K, FP64) from hef_orthonormalize; QH,
+ * argvec and R from hef_edge_resistance.  Columns dropped by the
+ * orthonormalisation carry no gradient.  dR is device FP64 (m, caller
+ * order).  All adjoint arithmetic is FP64; scatter-adds use FP64 atomics, so
+ * two runs agree to rounding, not bit for bit.
+ * ---------------------------------------------------------------------- */
+size_t hef_edge_resistance_backward_workspace_bytes(const hef_incidence* inc,
+                                                    int32_t k, int32_t S,
+                                                    int32_t dtype,
+                                                    int32_t recompute);
+hef_status hef_edge_resistance_backward(
+    const hef_incidence* inc, int32_t k, int32_t S, int32_t dtype,
+    const double* x0_clique, const double* x0_star, const void* tape,
+    size_t tape_bytes, const void* Q, int64_t ldq, const double* R_fac,
+    const double* QH, const int32_t* argvec, const double* R, const double* dR,
+    double* dw, double* dx0_clique, double* dx0_star, void* workspace,
+    size_t workspace_bytes, void* stream);
 /* ------------------------------------------------------------------------
  * Edge resistance without caller-provided device memory.  The paper has no
  * counterpart: this is a service of the library.

@@ -52,6 +52,13 @@ _SIGS = {
                                     c_p, c_sz, c_p]),
     "hef_edge_resistance_noalloc": (c_i32, [c_p, c_p, c_i64, c_i32, c_i32, c_i32, c_p, c_p, c_p,
                                             c_p, c_p, c_p]),
+    "hef_krylov_tape_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32]),
+    "hef_krylov_basis_tape": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p, c_sz,
+                                      c_p, c_sz, c_p]),
+    "hef_edge_resistance_backward_workspace_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32, c_i32]),
+    "hef_edge_resistance_backward": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_sz, c_p,
+                                             c_i64, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p,
+                                             c_sz, c_p]),
 }
 
 _lib = None
@@ -217,6 +224,81 @@ def krylov_basis(inc, x0_clique, x0_star, k, dtype=torch.float64, V=None, worksp
            L.hef_krylov_basis(inc.handle, k, S, code, _ptr(x0_clique), _ptr(x0_star), _ptr(V),
                               V.stride(0), _ptr(workspace), workspace.numel(), _stream(stream)))
     return V
+
+
+def krylov_basis_tape(inc, x0_clique, x0_star, k, dtype=torch.float64, stream=None):
+    """hef_krylov_basis_tape: the basis V of krylov_basis plus the tape the
+    backward reads.  Returns (V, tape)."""
+    L = lib()
+    code = _dtype_code(dtype)
+    S = int(x0_clique.shape[1])
+    K = 2 * k * S
+    V = torch.empty(inc.n, padded_ld(K, code), dtype=_DTYPES[code], device=inc.device)
+    ws = _workspace(L.hef_krylov_workspace_bytes(inc.handle, k, S, code), inc.device)
+    tape = _workspace(L.hef_krylov_tape_bytes(inc.handle, k, S, code), inc.device)
+    _check("hef_krylov_basis_tape",
+           L.hef_krylov_basis_tape(inc.handle, k, S, code, _ptr(x0_clique), _ptr(x0_star), _ptr(V),
+                                   V.stride(0), _ptr(tape), tape.numel(), _ptr(ws), ws.numel(),
+                                   _stream(stream)))
+    return V, tape
+
+
+def edge_resistance_backward(inc, k, x0_clique, x0_star, Q, R_fac, scores, dR, tape=None,
+                             want_dx0=True, stream=None):
+    """hef_edge_resistance_backward: (dw, dx0_clique, dx0_star) from
+    dR = dL/dR.  `scores` is the dict of edge_resistance (R, QH, argvec);
+    `tape` from krylov_basis_tape, or None to recompute it."""
+    L = lib()
+    code = _dtype_code(Q.dtype)
+    S = int(x0_clique.shape[1])
+    dev = Q.device
+    ws = _workspace(L.hef_edge_resistance_backward_workspace_bytes(inc.handle, k, S, code,
+                                                                   int(tape is None)), dev)
+    dw = torch.empty(max(inc.m, 1), dtype=torch.float64, device=dev)[:inc.m]
+    dxc = torch.empty_like(x0_clique) if want_dx0 else None
+    dxb = torch.empty_like(x0_star) if want_dx0 else None
+    dR = dR.to(device=dev, dtype=torch.float64).contiguous()
+    _check("hef_edge_resistance_backward",
+           L.hef_edge_resistance_backward(
+               inc.handle, k, S, code, _ptr(x0_clique), _ptr(x0_star), _ptr(tape),
+               0 if tape is None else tape.numel(), _ptr(Q), Q.stride(0), _ptr(R_fac),
+               _ptr(scores["QH"]), _ptr(scores["argvec"]), _ptr(scores["R"]), _ptr(dR), _ptr(dw),
+               _ptr(dxc), _ptr(dxb), _ptr(ws), ws.numel(), _stream(stream)))
+    return dw, dxc, dxb
+
+
+class HefResistance(torch.autograd.Function):
+    """R = HyperEF resistance scores (Algorithm 1, HEF_REDUCE_MAX) as a
+    differentiable function of the hyperedge weights w and the random starts
+    (x0_clique, x0_star); the structure (n, eptr, pins) and k are fixed.
+    Forward keeps the Krylov tape; backward calls hef_edge_resistance_backward."""
+
+    @staticmethod
+    def forward(ctx, w, x0_clique, x0_star, n, eptr, pins, k, dtype, clique_mode):
+        w64 = w.detach().to(torch.float64).contiguous()
+        xc = x0_clique.detach().to(torch.float64).contiguous()
+        xb = x0_star.detach().to(torch.float64).contiguous()
+        inc = build_incidence(n, eptr, pins, w64, clique_mode)
+        S = int(xc.shape[1])
+        K = 2 * k * S
+        V, tape = krylov_basis_tape(inc, xc, xb, k, dtype)
+        Q, Rf, rank = orthonormalize(V, K, want_R=True)
+        scores = edge_resistance(inc, Q, K)
+        ctx.state = (inc, k, xc, xb, Q, Rf, scores, tape, w.dtype)
+        return scores["R"].clone().to(w.dtype)
+
+    @staticmethod
+    def backward(ctx, gR):
+        inc, k, xc, xb, Q, Rf, scores, tape, wdt = ctx.state
+        dw, dxc, dxb = edge_resistance_backward(inc, k, xc, xb, Q, Rf, scores, gR, tape=tape)
+        ctx.state = None
+        return dw.to(wdt), dxc, dxb, None, None, None, None, None, None
+
+
+def resistance(w, x0_clique, x0_star, n, eptr, pins, k, dtype=torch.float64,
+               clique_mode=HEF_CLIQUE_HYPEREDGE):
+    """Differentiable scores: HefResistance.apply with keyword defaults."""
+    return HefResistance.apply(w, x0_clique, x0_star, n, eptr, pins, k, dtype, clique_mode)
 
 
 def orthonormalize(V, K, want_R=False, workspace=None, stream=None):
