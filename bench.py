@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 512 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="grid500x420_m200k")
@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--backward-workload", default="grid500x400_m210k_logw")
     return ap.parse_args()
 
 
@@ -86,10 +88,17 @@ class Clocks:
             self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "20"],
                 stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return
+        # start timing only once the sampler is producing rows
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < 5.0:
+            if os.path.getsize(self.f.name) > 0:
+                break
+            time.sleep(0.02)
 
     def stop(self):
         if self.proc is None:
@@ -162,7 +171,18 @@ def run_reference(args):
         return
     from oracle import hef_oracle as O
     H, k, S = instance(args.workload, 0)
-    Hs = window_subhypergraph(H, 0, min(H.nx, 250), 0, min(H.ny, 210)) if H.nx else H
+    # each step is the oracle on a window of the workload, sized so that the
+    # whole run takes about 100 s (at most 3 s per step): a probe on a
+    # 125 x 105 window gives the cost per pin
+    Hp = window_subhypergraph(H, 0, min(H.nx, 125), 0, min(H.ny, 105)) if H.nx else H
+    xp, xq = start_block(Hp.n, Hp.m, S, 0)
+    t0 = time.perf_counter()
+    O.hyperedge_resistance(Hp.n, Hp.eptr, Hp.pins, Hp.w, xp, xq, k)
+    per_pin = (time.perf_counter() - t0) / max(Hp.P, 1)
+    budget = min(3.0, 100.0 / max(args.steps + args.warmup, 1))
+    frac = min(1.0, budget / (per_pin * H.P))
+    rows = max(20, int(H.ny * frac)) if H.nx else 0
+    Hs = window_subhypergraph(H, 0, H.nx, 0, min(H.ny, rows)) if H.nx else H
     x0c, x0b = start_block(Hs.n, Hs.m, S, 0)
     times = []
     for i in range(args.warmup + args.steps):
@@ -190,19 +210,71 @@ def run_reference(args):
 
 
 def cpu_baseline(name):
+    """The oracle on the whole workload (one run, about 10 s on 16 cores)."""
     from oracle import hef_oracle as O
     H, k, S = instance(name, 0)
-    Hs = window_subhypergraph(H, 0, H.nx, 0, max(1, H.ny // 2)) if H.nx else H
-    x0c, x0b = start_block(Hs.n, Hs.m, S, 0)
+    x0c, x0b = start_block(H.n, H.m, S, 0)
     t0 = time.perf_counter()
-    O.hyperedge_resistance(Hs.n, Hs.eptr, Hs.pins, Hs.w, x0c, x0b, k)
+    O.hyperedge_resistance(H.n, H.eptr, H.pins, H.w, x0c, x0b, k)
     t = time.perf_counter() - t0
-    return {"value": Hs.P / t, "unit": "pins/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": f"{Hs.nx}x{Hs.ny} window (n={Hs.n}, m={Hs.m}, P={Hs.P}), one run, "
+    return {"value": H.P / t, "unit": "pins/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the whole workload (n={H.n}, m={H.m}, P={H.P}), one run, "
                       f"{t:.1f} s; numpy/scipy FP64, BLAS calls on all cores"}
 
 
 # ---------------------------------------------------------------- our arm
+
+def backward_leg(hef, args, dev, rank, timed, max_over_ranks, world):
+    """FP32 forward (keeping the Krylov tape) and backward of
+    L = sum over a seeded 10 % subset of w_e R_e, on the log-uniform-weight
+    netlist; dL/dR = w_e on the subset.  Times forward and backward with CUDA
+    events (L2 flushed before each step) and reports the Euler identity
+    sum_e w_e dL/dw_e = -L of the score term as a live check."""
+    import torch
+    H, k, S = instance(args.backward_workload, rank)
+    K = 2 * k * S
+    x0c, x0b = start_block(H.n, H.m, S, 5 + rank)
+    t = dict(eptr=torch.from_numpy(H.eptr).to(dev), pins=torch.from_numpy(H.pins).to(dev),
+             w=torch.from_numpy(H.w).to(dev), x0c=torch.from_numpy(x0c).to(dev),
+             x0b=torch.from_numpy(x0b).to(dev))
+    sel = np.random.default_rng(5).random(H.m) < 0.1
+    g = torch.from_numpy(np.where(sel, H.w, 0.0)).to(dev)
+    state = {}
+
+    def fwd():
+        inc = hef.build_incidence(H.n, t["eptr"], t["pins"], t["w"])
+        V, tape = hef.krylov_basis_tape(inc, t["x0c"], t["x0b"], k, torch.float32)
+        Q, Rf, _ = hef.orthonormalize(V, K, want_R=True)
+        sc = hef.edge_resistance(inc, Q, K)
+        state.update(inc=inc, Q=Q, Rf=Rf, sc=sc, tape=tape)
+
+    def bwd():
+        s_ = state
+        s_["grad"] = hef.edge_resistance_backward(s_["inc"], k, t["x0c"], t["x0b"], s_["Q"],
+                                                  s_["Rf"], s_["sc"], g, tape=s_["tape"])
+
+    def step():
+        fwd()
+        bwd()
+
+    ms_f, _, _, _ = timed(fwd, args.steps, args.warmup)
+    ms_s, _, _, _ = timed(step, args.steps, 1)
+    tf = max_over_ranks(sum(ms_f) / len(ms_f))
+    ts = max_over_ranks(sum(ms_s) / len(ms_s))
+    torch.cuda.synchronize()
+    state["inc"].check()
+    dw = state["grad"][0].cpu().numpy()
+    R = state["sc"]["R"].cpu().numpy()
+    gn = g.cpu().numpy()
+    L = float(gn @ R)
+    euler = abs(float(H.w @ dw) + L) / L
+    tape_mb = state["tape"].numel() / 2**20
+    return {"workload": args.backward_workload, "n": H.n, "m": H.m, "P": H.P, "k": k, "S": S,
+            "dtype": "f32 basis, FP64 adjoints", "loss": "sum over a seeded 10% subset of w_e R_e",
+            "ms_forward": tf, "ms_forward_backward": ts, "ms_backward": ts - tf,
+            "pins_per_s_forward_backward": world * H.P / (ts * 1e-3),
+            "tape_mib": tape_mb, "euler_residual": euler}
+
 
 def main():
     args = parse()
@@ -367,6 +439,11 @@ def main():
         e2e = {"value": world * H.P / (te * 1e-3), "unit": "pins/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te}
 
+    # ---- differentiation form: forward + backward of a score-based loss
+    bwd = None
+    if not args.no_backward:
+        bwd = backward_leg(hef, args, dev, rank, timed, max_over_ranks, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -389,6 +466,7 @@ def main():
             "roofline": roof,
             "cpu_baseline": cpu,
             "e2e": e2e,
+            "backward": bwd,
             "gpu_launches": launches,
             "cuda_graph": graph,
             "launches_per_step": launches / max(args.steps, 1),
