@@ -5,6 +5,8 @@
 #include <stdint.h>
 
 #include <cstddef>
+#include <mutex>
+#include <unordered_map>
 
 #include "../../include/hef.h"
 
@@ -65,6 +67,23 @@ inline int num_sms() {
 
 // Grid for a grid-stride loop over `work` items: at most `per_sm` CTAs of
 // kThreads per SM (a fixed size, so per-CTA partial sums are reproducible).
+// CTAs of `kernel` (with `threads` threads and `smem` dynamic shared memory)
+// that fit on one SM at once, looked up once per kernel.
+template <typename F>
+inline int resident_ctas(F* kernel, int threads, size_t smem = 0) {
+  static std::mutex mu;
+  static std::unordered_map<const void*, int> cache;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = cache.find(reinterpret_cast<const void*>(kernel));
+  if (it != cache.end()) return it->second;
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, smem) != cudaSuccess ||
+      n < 1)
+    n = 1;
+  cache[reinterpret_cast<const void*>(kernel)] = n;
+  return n;
+}
+
 inline int stride_grid(long long work, int per_sm = 4) {
   long long want = (work + kThreads - 1) / kThreads;
   long long cap = (long long)num_sms() * per_sm;

@@ -34,6 +34,14 @@ constexpr int kMaxS = 16;
 constexpr int kBig = 16;     // segments longer than this are summed by a warp
 constexpr int kUpdRows = 4;  // rows per thread in the update pass
 
+// Minimum resident CTAs per SM asked of the compiler for the step kernels:
+// the FP32 form with S <= 4 fits one wave of the 200k-row workloads in its
+// register budget; wider rows keep the compiler's choice (no spills).
+template <typename T, int S>
+constexpr int kMinBlocks(int want) {
+  return (sizeof(T) == 4 && S <= 4) ? want : (S * sizeof(T) <= 32 ? 2 : 1);
+}
+
 template <typename T>
 struct KView {
   int n, m;
@@ -101,24 +109,45 @@ __device__ __forceinline__ void strow(T* __restrict__ p, const T (&v)[S]) {
 }
 
 // Per-CTA partials of NQ*S values (slot q*S + s) written to part[block].
+// Within a warp the values are summed by a transposing butterfly: at each
+// level a lane keeps half of its values and adds its partner's copy of that
+// half, so N values cost about N shuffles instead of 5 N; a lane ends with
+// the warp sum of one slot.  Warps then meet in a fixed order.
 template <int NQ, int S, typename A>
 __device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* part) {
-  __shared__ double red[kThreads / 32][NQ * S];
+  constexpr int N = NQ * S;
+  constexpr int P = N > 16 ? 32 : (N > 8 ? 16 : (N > 4 ? 8 : (N > 2 ? 4 : (N > 1 ? 2 : 1))));
+  constexpr int R = 32 / P;  // lanes that end up holding the same slot
+  constexpr int NCH = (N + P - 1) / P;
+  __shared__ double red[kThreads / 32][NCH * P];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-  for (int q = 0; q < NQ; ++q)
+  for (int ch = 0; ch < NCH; ++ch) {
+    A x[P];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      A x = v[q][s];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-      if (lane == 0) red[wid][q * S + s] = (double)x;
+    for (int i = 0; i < P; ++i) {
+      const int idx = ch * P + i;
+      x[i] = idx < N ? v[idx / S][idx % S] : (A)0;
     }
+#pragma unroll
+    for (int h = P / 2; h >= 1; h >>= 1) {
+      const bool up = (lane & (h * R)) != 0;
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const A send = up ? x[i] : x[i + h];
+        const A keep = up ? x[i + h] : x[i];
+        x[i] = keep + __shfl_xor_sync(0xffffffffu, send, h * R);
+      }
+    }
+#pragma unroll
+    for (int o = R / 2; o >= 1; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
+    if (lane % R == 0) red[wid][ch * P + lane / R] = (double)x[0];
+  }
   __syncthreads();
-  for (int t = threadIdx.x; t < NQ * S; t += blockDim.x) {
+  for (int t = threadIdx.x; t < N; t += blockDim.x) {
     double acc = 0.0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][t];
-    part[(size_t)blockIdx.x * NQ * S + t] = acc;
+    part[(size_t)blockIdx.x * N + t] = acc;
   }
 }
 
@@ -354,7 +383,7 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T>
 // Edge pass of step j (thread per hyperedge): clique pin sums s_e, star rows
 // (M_b x)_e, and the D-weighted dots of the star hyperedge rows -> te.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, ScalView<T> sv, KView<T> kv, int j) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5)) k_edge_pass(IncView g, ScalView<T> sv, KView<T> kv, int j) {
   if (g.status[0]) return;
   const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
   const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
@@ -418,7 +447,7 @@ __global__ void __launch_bounds__(kThreads) k_edge_pass(IncView g, ScalView<T> s
 // of x_{j-1} into V, and the Lanczos coefficients of step j (final CTA, with
 // the star hyperedge-row dots of the edge pass).
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, ScalView<T> sv, KView<T> kv, int j,
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_node_pass(IncView g, ScalView<T> sv, KView<T> kv, int j,
                                                         T* __restrict__ V, long long ldv) {
   if (g.status[0]) return;
   const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
@@ -441,6 +470,18 @@ __global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, ScalView<T> s
   const T* __restrict__ se = kv.se;
   const T* __restrict__ ewh = sv.ewh;
   const T* __restrict__ ez = sv.ez;
+  // the vertex's own rows and scalars first: their loads overlap the gathers
+  T xv[S], xb[S], xpc[S], xpb[S];
+  T wsum = 0, idc = 0, idb = 0, dcv = 0, dbv = 0;
+  if (valid) {
+    ldrow<T, S>(curc + (long long)v * S, xv);
+    ldrow<T, S>(curb + (long long)v * S, xb);
+    if (prvc) {
+      ldrow<T, S>(prvc + (long long)v * S, xpc);
+      ldrow<T, S>(prvb + (long long)v * S, xpb);
+    }
+    wsum = sv.wsc[v], idc = sv.inv_dc[v], idb = sv.inv_db[v], dcv = sv.dc[v], dbv = sv.db[v];
+  }
   T accc[S], accb[S];
   seg_sum2<T, S>(valid, a, b, [&](int t) { return __ldg(ve + t); },
                  [&](int e) { return se + (long long)e * S; },
@@ -453,16 +494,7 @@ __global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, ScalView<T> s
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (valid) {
-    const T wsum = sv.wsc[v];
-    T xv[S], xb[S], yc[S], yb[S], xpc[S], xpb[S];
-    ldrow<T, S>(curc + (long long)v * S, xv);
-    ldrow<T, S>(curb + (long long)v * S, xb);
-    if (prvc) {
-      ldrow<T, S>(prvc + (long long)v * S, xpc);
-      ldrow<T, S>(prvb + (long long)v * S, xpb);
-    }
-    const T idc = sv.inv_dc[v], idb = sv.inv_db[v];
-    const T dcv = sv.dc[v], dbv = sv.db[v];
+    T yc[S], yb[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       xv[s] *= ncc[s];
@@ -517,7 +549,7 @@ __global__ void __launch_bounds__(kThreads) k_node_pass(IncView g, ScalView<T> s
 // - alpha x_{j-1} - beta x_{j-2} (written over x_{j-2}'s buffer) and its
 // D-norm -> inv_nu[j].  Rows: [0, n) clique, [n, 2n + m) star.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_update(IncView g, ScalView<T> sv, KView<T> kv, int j) {
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_update(IncView g, ScalView<T> sv, KView<T> kv, int j) {
   if (g.status[0]) return;
   const bool has_prv = j >= 3;
   // coefficients of both expansions in registers: [op][s][ct, ct2, a, b]

@@ -22,6 +22,8 @@ namespace {
 
 constexpr double kQhTiny = 1e-300;
 constexpr int kFlushEdges = 32;  // FP32 form: edges per FP32 partial sum
+constexpr int kGroup1 = 8;      // hyperedges per warp task in pass 1
+constexpr int kWorkSlot = 60;    // counters [60], [61]: work distribution of the passes
 
 template <typename T>
 __device__ __forceinline__ T lowest();
@@ -32,6 +34,14 @@ __device__ __forceinline__ double lowest<double>() {
 template <>
 __device__ __forceinline__ float lowest<float>() {
   return -FLT_MAX;
+}
+
+// Next group of 32 hyperedges for the calling warp (dynamic distribution:
+// one atomic per group on a counter that starts each call at zero).
+__device__ __forceinline__ long long next_group(unsigned int* work) {
+  unsigned int grp = 0;
+  if ((threadIdx.x & 31) == 0) grp = atomicAdd(work, 1u);
+  return (long long)__shfl_sync(0xffffffffu, grp, 0);
 }
 
 // Extrema of two hyperedges at once (pins [a0, b0) and [a1, b1), warp-uniform):
@@ -163,24 +173,27 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restrict__ Q, long long ldq,
                                                      int K, GridRed red, const double* __restrict__ bpart,
                                                      int nbpart, double* QH, double* invQH,
-                                                     double* QH_out) {
+                                                     double* QH_out, unsigned int* work) {
   if (g.status[0]) return;
   __shared__ double wred[kThreads / 32][32 * NC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   double acc[NC];
   T pacc[NC];
 #pragma unroll
   for (int c = 0; c < NC; ++c) acc[c] = 0.0, pacc[c] = 0;
-  const long long ngroups = ((long long)g.m + 31) / 32;
+  // static assignment (the FP64 partials must not depend on scheduling):
+  // warp w takes groups of kGroup1 hyperedges w, w + nwarps, ...
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long ngroups = ((long long)g.m + kGroup1 - 1) / kGroup1;
+  (void)work;
   for (long long grp = warp; grp < ngroups; grp += nwarps) {
-    const long long e = grp * 32 + lane;
+    const long long e = grp * kGroup1 + lane;
     int a = 0, b = 0;
-    if (e < g.m) a = g.ceptr[e], b = g.ceptr[e + 1];
+    if (lane < kGroup1 && e < g.m) a = g.ceptr[e], b = g.ceptr[e + 1];
     if (b - a < 2 || b - a > kBigEdge) b = a;  // not scored here
-    const T wl = e < g.m ? (T)g.ew[e] : (T)0;
-    for (int i = 0; i < 32; i += 2) {
+    const T wl = (lane < kGroup1 && e < g.m) ? (T)g.ew[e] : (T)0;
+    for (int i = 0; i < kGroup1; i += 2) {
       const int a0 = __shfl_sync(0xffffffffu, a, i), b0 = __shfl_sync(0xffffffffu, b, i);
       const int a1 = __shfl_sync(0xffffffffu, a, i + 1), b1 = __shfl_sync(0xffffffffu, b, i + 1);
       const T w0 = __shfl_sync(0xffffffffu, wl, i), w1 = __shfl_sync(0xffffffffu, wl, i + 1);
@@ -199,7 +212,7 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
         }
       }
     }
-    // FP32 partial sums span one group (<= 32 hyperedges); FP64 beyond
+    // FP32 partial sums span one group (kGroup1 hyperedges); FP64 beyond
 #pragma unroll
     for (int c = 0; c < NC; ++c) acc[c] += (double)pacc[c], pacc[c] = 0;
   }
@@ -337,16 +350,17 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restrict__ Q, long long ldq,
                                                      int K, int reduce, const double* __restrict__ QH,
                                                      const double* __restrict__ invQH, double* R_out,
-                                                     int32_t* argvec, int32_t* pmax, int32_t* pmin) {
+                                                     int32_t* argvec, int32_t* pmax, int32_t* pmin,
+                                                     unsigned int* work) {
   if (g.status[0]) return;
   const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   T iq[NC];
   bool use[NC];
   load_use<T, NC>(QH, invQH, K, iq, use);
   const long long ngroups = ((long long)g.m + 31) / 32;
-  for (long long grp = warp; grp < ngroups; grp += nwarps) {
+  for (;;) {
+    const long long grp = next_group(work);
+    if (grp >= ngroups) break;
     const long long e = grp * 32 + lane;
     int a = 0, b = 0;
     if (e < g.m) a = g.ceptr[e], b = g.ceptr[e + 1];
@@ -408,13 +422,18 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
   red.gpart = w.gpart;
   red.gcnt = w.counter;                 // red_groups(grid) <= 63 counters
   red.tcnt = w.counter + 63;
+  // grids of co-resident CTAs only (work is handed out dynamically)
+  const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
+  const int g2 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass2<T, NC>, kThreads));
   HEF_LAUNCH("k_score_big1", st, k_score_big1<T, NC><<<w.bgrid, kThreads, 0, st>>>(g, Q, ldq, K, w.bpart));
-  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<w.grid, kThreads, 0, st>>>(
-                                      g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out));
+  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<g1, kThreads, 0, st>>>(
+                                      g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out,
+                                      w.counter + kWorkSlot));
   HEF_LAUNCH("k_score_big2", st, k_score_big2<T, NC><<<w.bgrid, kThreads, 0, st>>>(
                                      g, Q, ldq, K, reduce, w.QH, w.invQH, R_out, argvec, pmax, pmin));
-  HEF_LAUNCH("k_score_pass2", st, k_score_pass2<T, NC><<<w.grid, kThreads, 0, st>>>(
-                                      g, Q, ldq, K, reduce, w.QH, w.invQH, R_out, argvec, pmax, pmin));
+  HEF_LAUNCH("k_score_pass2", st, k_score_pass2<T, NC><<<g2, kThreads, 0, st>>>(
+                                      g, Q, ldq, K, reduce, w.QH, w.invQH, R_out, argvec, pmax, pmin,
+                                      w.counter + kWorkSlot + 1));
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
