@@ -32,7 +32,7 @@ constexpr int kGB = 8;       // Gram: rows/cols of the block a thread owns
 constexpr int kPR = 32;      // Gram: rows per shared-memory panel
 constexpr int kPairs = 256;  // Gram: block pairs (threads) per CTA
 constexpr int kACB = 64;     // apply: output columns per block
-constexpr int kPB = 8;       // elimination: pivots per panel
+constexpr int kPB = 16;      // elimination: pivots per panel
 
 inline int round8(int K) { return (K + 7) & ~7; }
 
@@ -176,6 +176,23 @@ struct CholOut {
   int* flag;       // [0] exact pass needed
 };
 
+// Barrier among the first `count` threads of the CTA (named barrier `id`).
+__device__ __forceinline__ void named_sync(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+// 1 / sqrt(pivot) in the elimination's arithmetic type.
+template <typename C>
+__device__ __forceinline__ C pivot_rsqrt(C d);
+template <>
+__device__ __forceinline__ float pivot_rsqrt<float>(float d) {
+  return 1.0f / sqrtf(d);
+}
+template <>
+__device__ __forceinline__ double pivot_rsqrt<double>(double d) {
+  return 1.0 / sqrt(d);
+}
+
 // Gauss elimination of [A | I] with A = G - c c^T / n: after pivot j, row j
 // holds R[j][j..K) on the left and (R^-T)[j][0..j] on the right.  Columns
 // whose pivot is <= tol * G_jj are dropped (their rows stay zero).
@@ -189,7 +206,7 @@ __global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
                                                    double n, double tol, C* Wg, int use_smem,
                                                    int fast, int always, CholOut o) {
   extern __shared__ unsigned char sm_raw[];
-  __shared__ double ref[512];
+  __shared__ C ref[512], thr_keep[512], thr_near[512];
   __shared__ int pk[kPB];  // kept flags of the current panel
   __shared__ int near_def;
   if (!fast && !always && o.flag[0] == 0) return;
@@ -200,67 +217,97 @@ __global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
     for (int j = (int)(threadIdx.x & 31); j < W2; j += 32)
       row[j] = j < K ? Aproj[(size_t)i * K + j] : (j - K == i ? (C)1 : (C)0);
   }
-  for (int i = threadIdx.x; i < K; i += blockDim.x) ref[i] = G[(size_t)i * K + i];
+  for (int i = threadIdx.x; i < K; i += blockDim.x) {
+    // pivot thresholds in the elimination's own type (no FP64 on the pivot path)
+    const double gi = G[(size_t)i * K + i];
+    ref[i] = (C)gi;
+    thr_keep[i] = (C)(tol * gi);
+    thr_near[i] = (C)(1e-4 * gi);
+  }
   if (threadIdx.x == 0) near_def = 0;
   __syncthreads();
-  // Blocked: a panel of kPB pivots is eliminated among its own rows by warp 0
-  // (warp-synchronous), then every later row takes the panel's rank-kPB
-  // update in one sweep.  Row j's live columns after its pivot: left j..K-1,
-  // right 0..j (K + 1 values).
+  // Blocked: a panel of kPB pivots is eliminated among its own rows by kPB
+  // warps (warp w owns panel row j0 + w; two named-barrier steps per pivot:
+  // the owner of row j scales it, then the later panel rows eliminate column
+  // j), then every later row takes the panel's rank-kPB update in one sweep.
+  // Row j's live columns after its pivot: left j..K-1, right 0..j (K + 1
+  // values).
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j0 = 0; j0 < K; j0 += kPB) {
     const int jend = min(K, j0 + kPB);
-    if (wid == 0) {
+    if (wid < kPB) {
+      const int i = j0 + wid;
+      C* rowi = W + (size_t)i * W2;
       for (int j = j0; j < jend; ++j) {
         C* rowj = W + (size_t)j * W2;
-        int kj = 0;
-        C pinv = 0;
-        if (lane == 0) {
-          const double d = (double)rowj[j];
-          kj = (ref[j] > 0.0 && d > tol * ref[j]) ? 1 : 0;
-          if (fast && kj && d <= 1e-4 * ref[j]) near_def = 1;
-          pinv = kj ? (C)(1.0 / sqrt(d)) : (C)0;
-          o.kept[j] = kj;
-        }
-        kj = __shfl_sync(0xffffffffu, kj, 0);
-        pinv = __shfl_sync(0xffffffffu, pinv, 0);
-        pk[j - j0] = kj;
-        // scale (or zero) row j over its live columns
-        for (int q0 = lane; q0 <= K; q0 += 32) {
-          const int q = q0 < K - j ? j + q0 : K + (q0 - (K - j));
-          rowj[q] = kj ? rowj[q] * pinv : (C)0;
-        }
-        __syncwarp();
-        if (kj) {  // eliminate column j from the panel's later rows
-          for (int i = j + 1; i < jend; ++i) {
-            C* rowi = W + (size_t)i * W2;
-            const C r = rowj[i];
-            for (int q0 = lane; q0 < K; q0 += 32) {
-              const int nleft = K - j - 1;
-              const int q = q0 < nleft ? j + 1 + q0 : K + (q0 - nleft);
-              rowi[q] -= r * rowj[q];
-            }
+        if (i == j) {  // owner: pivot, kept flag, scale the live columns
+          int kj = 0;
+          C pinv = 0;
+          if (lane == 0) {
+            const C d = rowj[j];
+            kj = (ref[j] > (C)0 && d > thr_keep[j]) ? 1 : 0;
+            if (fast && kj && d <= thr_near[j]) near_def = 1;
+            if (kj) pinv = pivot_rsqrt<C>(d);
+            o.kept[j] = kj;
+            pk[j - j0] = kj;
+          }
+          kj = __shfl_sync(0xffffffffu, kj, 0);
+          pinv = __shfl_sync(0xffffffffu, pinv, 0);
+          for (int q0 = lane; q0 <= K; q0 += 32) {
+            const int q = q0 < K - j ? j + q0 : K + (q0 - (K - j));
+            rowj[q] = kj ? rowj[q] * pinv : (C)0;
           }
         }
-        __syncwarp();
+        named_sync(1, kPB * 32);
+        if (i > j && i < jend && pk[j - j0]) {  // eliminate column j from row i
+          const C r = rowj[i];
+          const int nleft = K - j - 1;
+          for (int q0 = lane; q0 < K; q0 += 32) {
+            const int q = q0 < nleft ? j + 1 + q0 : K + (q0 - nleft);
+            rowi[q] -= r * rowj[q];
+          }
+        }
+        named_sync(1, kPB * 32);
       }
     }
     __syncthreads();
-    // rank-kPB update of rows i >= jend: live columns left jend..K-1, right 0..jend-1
-    const int nleft = K - jend;
-    for (int i = jend + wid; i < K; i += nw) {
-      C* rowi = W + (size_t)i * W2;
-      C rj[kPB];
+    // rank-kPB update of rows i >= jend.  Their live columns (left jend..K-1,
+    // right 0..jend-1) are the contiguous range [jend, K + jend) of the row.
+    int npb = 0;
 #pragma unroll
-      for (int p = 0; p < kPB; ++p)
-        rj[p] = (j0 + p < jend && pk[p]) ? W[(size_t)(j0 + p) * W2 + i] : (C)0;
-      for (int q0 = lane; q0 < K; q0 += 32) {
-        const int q = q0 < nleft ? jend + q0 : K + (q0 - nleft);
-        C acc = rowi[q];
+    for (int p = 0; p < kPB; ++p) npb += (j0 + p < jend) ? 1 : 0;
+    if (sizeof(C) == 4 && (K & 3) == 0 && (jend & 3) == 0) {
+      // FP32: four columns per lane (16-byte shared-memory accesses)
+      for (int i = jend + wid; i < K; i += nw) {
+        float* rowi = reinterpret_cast<float*>(W + (size_t)i * W2) + jend;
+        float rj[kPB];
 #pragma unroll
         for (int p = 0; p < kPB; ++p)
-          if (j0 + p < jend) acc -= rj[p] * W[(size_t)(j0 + p) * W2 + q];
-        rowi[q] = acc;
+          rj[p] = (p < npb && pk[p]) ? (float)W[(size_t)(j0 + p) * W2 + i] : 0.0f;
+        for (int v = lane; v < K / 4; v += 32) {
+          float4 acc = reinterpret_cast<float4*>(rowi)[v];
+#pragma unroll
+          for (int p = 0; p < kPB; ++p) {
+            const float4 b =
+                reinterpret_cast<const float4*>(reinterpret_cast<float*>(W + (size_t)(j0 + p) * W2) + jend)[v];
+            acc.x -= rj[p] * b.x, acc.y -= rj[p] * b.y, acc.z -= rj[p] * b.z, acc.w -= rj[p] * b.w;
+          }
+          reinterpret_cast<float4*>(rowi)[v] = acc;
+        }
+      }
+    } else {
+      for (int i = jend + wid; i < K; i += nw) {
+        C* rowi = W + (size_t)i * W2 + jend;
+        C rj[kPB];
+#pragma unroll
+        for (int p = 0; p < kPB; ++p)
+          rj[p] = (p < npb && pk[p]) ? W[(size_t)(j0 + p) * W2 + i] : (C)0;
+        for (int q0 = lane; q0 < K; q0 += 32) {
+          C acc = rowi[q0];
+#pragma unroll
+          for (int p = 0; p < kPB; ++p) acc -= rj[p] * W[(size_t)(j0 + p) * W2 + jend + q0];
+          rowi[q0] = acc;
+        }
       }
     }
     __syncthreads();
@@ -268,12 +315,13 @@ __global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
   // outputs: R (FP64), Rinv = (R^-T)^T (type T), mu, rank, flag
   T* Rinv = static_cast<T*>(o.Rinv);
   T* mu = static_cast<T*>(o.mu);
-  for (int i = (int)(threadIdx.x >> 5); i < Kp; i += (int)(blockDim.x >> 5)) {
-    for (int j = (int)(threadIdx.x & 31); j < Kp; j += 32) {
+  // lanes run along W's rows (conflict-free shared-memory reads)
+  for (int j = (int)(threadIdx.x >> 5); j < Kp; j += (int)(blockDim.x >> 5)) {
+    for (int i = (int)(threadIdx.x & 31); i < Kp; i += 32) {
       C v = 0;
       if (i < K && j < K && i <= j) v = W[(size_t)j * W2 + K + i];
       Rinv[(size_t)i * Kp + j] = (T)v;
-      if (o.R && i < K && j < K) o.R[(size_t)i * K + j] = (i <= j) ? (double)W[(size_t)i * W2 + j] : 0.0;
+      if (o.R && i < K && j < K) o.R[(size_t)j * K + i] = (j <= i) ? (double)W[(size_t)j * W2 + i] : 0.0;
     }
   }
   for (int i = threadIdx.x; i < Kp; i += blockDim.x) mu[i] = i < K ? (T)(c[i] / n) : (T)0;
