@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
+    ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--batched-graphs", type=int, default=64)
     ap.add_argument("--backward-workload", default="grid500x400_m210k_logw")
     return ap.parse_args()
 
@@ -223,6 +225,59 @@ def cpu_baseline(name):
 
 
 # ---------------------------------------------------------------- our arm
+
+def batched_leg(hef, args, dev, rank, timed, max_over_ranks, world):
+    """The batched form: G netlists of uneven sizes (n log-uniform in
+    5k..150k, m = 1.05 n, 2 + Geometric(0.5) pins on radius-3 neighbourhoods,
+    unit weights; k = 20, S = 4), scored in one hef_resistance_batched call
+    captured as a CUDA graph with the autotuned stream count and schedule,
+    FP32.  Against it: the same batch in FP64 on one stream (the plain form,
+    one netlist after another), and the error of FP32 against FP64."""
+    import torch
+    from netlists.synth import batch_sizes, grid_netlist
+    k, S = 20, 4
+    graphs = []
+    P = 0
+    for g, (nx, ny, m, seed) in enumerate(batch_sizes(args.batched_graphs, 4000 + 1000 * rank)):
+        H = grid_netlist(nx, ny, m, seed)
+        x0c, x0b = start_block(H.n, H.m, S, seed)
+        graphs.append(dict(n=H.n, eptr=torch.from_numpy(H.eptr).to(dev),
+                           pins=torch.from_numpy(H.pins).to(dev), w=torch.from_numpy(H.w).to(dev),
+                           x0c=torch.from_numpy(x0c).to(dev), x0b=torch.from_numpy(x0b).to(dev)))
+        P += H.P
+    n_tot = sum(gr["n"] for gr in graphs)
+    b32 = hef.Batch(graphs, k, S, torch.float32)
+    b32.run()
+    torch.cuda.synchronize()
+    b32.check()
+    ns, _, tune_ms = b32.autotune()
+    b32.capture()
+    ms, _, _, _ = timed(b32.replay, args.steps, args.warmup)
+    t32 = max_over_ranks(sum(ms) / len(ms))
+    R32 = [o["R"].double().cpu().numpy() for o in b32.out]
+    del b32
+    b64 = hef.Batch(graphs, k, S, torch.float64, nstreams=1)
+    b64.run()
+    torch.cuda.synchronize()
+    b64.capture()
+    ms64, _, _, _ = timed(b64.replay, max(1, args.fp64_steps), 1)
+    t64 = max_over_ranks(sum(ms64) / len(ms64))
+    R64 = [o["R"].cpu().numpy() for o in b64.out]
+    del b64
+    a = np.concatenate(R32)
+    r = np.concatenate(R64)
+    big = r >= 1e-3 * r.max()
+    rel = np.abs(a - r) / np.maximum(r, 1e-300)
+    norm = max(float(np.abs(x - y).max() / y.max()) for x, y in zip(R32, R64))
+    return {"graphs": len(graphs), "n_total": n_tot, "P_total": P, "k": k, "S": S,
+            "dtype": "f32", "nstreams": ns, "autotune_ms": tune_ms, "ms_per_batch": t32,
+            "pins_per_s": world * P / (t32 * 1e-3),
+            "fp64_one_stream": {"ms_per_batch": t64, "pins_per_s": world * P / (t64 * 1e-3)},
+            "speedup_vs_fp64": t64 / t32,
+            "error_vs_fp64": {"max_rel": float(rel[big].max()),
+                              "p99_rel": float(np.percentile(rel[r > 0], 99)),
+                              "normwise_worst_graph": norm}}
+
 
 def backward_leg(hef, args, dev, rank, timed, max_over_ranks, world):
     """FP32 forward (keeping the Krylov tape) and backward of
@@ -444,6 +499,11 @@ def main():
     if not args.no_backward:
         bwd = backward_leg(hef, args, dev, rank, timed, max_over_ranks, world)
 
+    # ---- batched form: many uneven netlists in one captured call
+    batched = None
+    if not args.no_batched:
+        batched = batched_leg(hef, args, dev, rank, timed, max_over_ranks, world)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(args.workload)
@@ -467,6 +527,7 @@ def main():
             "cpu_baseline": cpu,
             "e2e": e2e,
             "backward": bwd,
+            "batched": batched,
             "gpu_launches": launches,
             "cuda_graph": graph,
             "launches_per_step": launches / max(args.steps, 1),

@@ -269,6 +269,67 @@ hef_status hef_edge_resistance_backward(
     double* dw, double* dx0_clique, double* dx0_star, void* workspace,
     size_t workspace_bytes, void* stream);
 /* ------------------------------------------------------------------------
+ * Batched form: Algorithm 1 on G independent hypergraphs of uneven sizes
+ * (e.g. the levels of a multilevel hierarchy) in one call.  The paper scores
+ * one hypergraph at a time; batching is a service of the library.
+ *
+ * `items` is a HOST array of G descriptors; every pointer inside is device
+ * memory with the meaning of hef_build_incidence (eptr, pins, w), of
+ * hef_krylov_basis (x0_clique, x0_star) and of hef_edge_resistance (R_out,
+ * QH_out, argvec, pmax, pmin; all but R_out nullable).  status_out
+ * (nullable, 2 words) receives the item's device status word and first bad
+ * hyperedge (hef_incidence_check's detail and where), so a caller can check
+ * every item after the stream has run.
+ *
+ * Each item runs the whole path (HEF_REDUCE_MAX) as one chain of launches on
+ * one stream of a per-device pool of 16 streams; chains of different items
+ * overlap.  The call forks from `stream` with an event and joins back, so it
+ * can be captured in a CUDA graph; the pool is created by the first call on
+ * a device, which must happen outside stream capture.  schedule[g] (HOST,
+ * nullable) is the pool stream of item g in [0, nstreams); NULL assigns items
+ * longest first to the least loaded stream (hef_batch_schedule).  Results are
+ * identical, bit for bit, to one hef_build_incidence / hef_krylov_basis /
+ * hef_orthonormalize / hef_edge_resistance sequence per item.
+ * The pool and its fork/join events are shared by every batched call on a
+ * device: make batched calls from one host thread at a time.
+ * hef_batch_autotune waits for `stream`, then for nstreams = 1, 2, 4, 8, 16
+ * (each with its longest-first schedule) captures the batch as a CUDA graph
+ * on a private stream and times three replays; it returns the fastest:
+ * nstreams_out, schedule_out[G] (HOST), ms_out (nullable, ms per batch).  It
+ * writes the items' outputs while timing and must not be called inside a
+ * stream capture.
+ * ---------------------------------------------------------------------- */
+typedef struct hef_batch_item {
+  int64_t n, m, P;
+  const int64_t* eptr;
+  const int32_t* pins;
+  const double* w;
+  const double* x0_clique;
+  const double* x0_star;
+  double* R_out;
+  double* QH_out;
+  int32_t* argvec;
+  int32_t* pmax;
+  int32_t* pmin;
+  uint32_t* status_out;
+} hef_batch_item;
+size_t hef_batch_workspace_bytes(const hef_batch_item* items, int32_t G,
+                                 int32_t k, int32_t S, int32_t dtype);
+hef_status hef_batch_schedule(const hef_batch_item* items, int32_t G,
+                              int32_t k, int32_t S, int32_t nstreams,
+                              int32_t* schedule);
+hef_status hef_resistance_batched(const hef_batch_item* items, int32_t G,
+                                  int32_t k, int32_t S, int32_t dtype,
+                                  int32_t clique_mode, const int32_t* schedule,
+                                  int32_t nstreams, void* workspace,
+                                  size_t workspace_bytes, void* stream);
+hef_status hef_batch_autotune(const hef_batch_item* items, int32_t G,
+                              int32_t k, int32_t S, int32_t dtype,
+                              int32_t clique_mode, void* workspace,
+                              size_t workspace_bytes, void* stream,
+                              int32_t* nstreams_out, int32_t* schedule_out,
+                              float* ms_out);
+/* ------------------------------------------------------------------------
  * Edge resistance without caller-provided device memory.  The paper has no
  * counterpart: this is a service of the library.
  *

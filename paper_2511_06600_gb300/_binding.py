@@ -52,6 +52,12 @@ _SIGS = {
                                     c_p, c_sz, c_p]),
     "hef_edge_resistance_noalloc": (c_i32, [c_p, c_p, c_i64, c_i32, c_i32, c_i32, c_p, c_p, c_p,
                                             c_p, c_p, c_p]),
+    "hef_batch_workspace_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32, c_i32]),
+    "hef_batch_schedule": (c_i32, [c_p, c_i32, c_i32, c_i32, c_i32, c_p]),
+    "hef_resistance_batched": (c_i32, [c_p, c_i32, c_i32, c_i32, c_i32, c_i32, c_p, c_i32, c_p,
+                                       c_sz, c_p]),
+    "hef_batch_autotune": (c_i32, [c_p, c_i32, c_i32, c_i32, c_i32, c_i32, c_p, c_sz, c_p, c_p,
+                                   c_p, c_p]),
     "hef_krylov_tape_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32]),
     "hef_krylov_basis_tape": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p, c_sz,
                                       c_p, c_sz, c_p]),
@@ -473,3 +479,104 @@ class Pipeline:
         if getattr(self, "handle", None) is not None and _lib is not None:
             _lib.hef_free_incidence(self.handle)
             self.handle = None
+
+
+class _BatchItem(ctypes.Structure):
+    """hef_batch_item (include/hef.h)."""
+    _fields_ = [("n", c_i64), ("m", c_i64), ("P", c_i64), ("eptr", c_p), ("pins", c_p), ("w", c_p),
+                ("x0_clique", c_p), ("x0_star", c_p), ("R_out", c_p), ("QH_out", c_p),
+                ("argvec", c_p), ("pmax", c_p), ("pmin", c_p), ("status_out", c_p)]
+
+
+class Batch:
+    """Batched form: Algorithm 1 on G hypergraphs in one call
+    (hef_resistance_batched).  `graphs` is a list of dicts of CUDA tensors
+    with keys n, eptr, pins, w, x0c, x0b; outputs (R, QH, argvec, pmax, pmin,
+    status per item) are allocated once."""
+
+    def __init__(self, graphs, k, S, dtype=torch.float32, clique_mode=HEF_CLIQUE_HYPEREDGE,
+                 nstreams=8, device=None):
+        self.k, self.S, self.K = int(k), int(S), 2 * int(k) * int(S)
+        self.code = _dtype_code(dtype)
+        self.clique_mode = int(clique_mode)
+        self.device = device or torch.device("cuda", torch.cuda.current_device())
+        dev = self.device
+        self.graphs = graphs
+        self.out = []
+        items = (_BatchItem * len(graphs))()
+        for g, gr in enumerate(graphs):
+            m = int(gr["eptr"].numel() - 1)
+            o = dict(R=torch.empty(max(m, 1), dtype=torch.float64, device=dev)[:m],
+                     QH=torch.empty(self.K, dtype=torch.float64, device=dev),
+                     argvec=torch.empty(max(m, 1), dtype=torch.int32, device=dev)[:m],
+                     pmax=torch.empty(max(m, 1), dtype=torch.int32, device=dev)[:m],
+                     pmin=torch.empty(max(m, 1), dtype=torch.int32, device=dev)[:m],
+                     status=torch.zeros(2, dtype=torch.int32, device=dev))
+            self.out.append(o)
+            it = items[g]
+            it.n, it.m, it.P = int(gr["n"]), m, int(gr["pins"].numel())
+            it.eptr, it.pins, it.w = (gr["eptr"].data_ptr(), gr["pins"].data_ptr(),
+                                      gr["w"].data_ptr())
+            it.x0_clique, it.x0_star = gr["x0c"].data_ptr(), gr["x0b"].data_ptr()
+            it.R_out, it.QH_out = o["R"].data_ptr(), o["QH"].data_ptr()
+            it.argvec, it.pmax, it.pmin = (o["argvec"].data_ptr(), o["pmax"].data_ptr(),
+                                           o["pmin"].data_ptr())
+            it.status_out = o["status"].data_ptr()
+        self.items = items
+        self.G = len(graphs)
+        L = lib()
+        nb = L.hef_batch_workspace_bytes(items, self.G, self.k, self.S, self.code)
+        if nb == 0:
+            raise HefError("hef_batch_workspace_bytes", -1, lib().hef_last_error().decode())
+        self.workspace = _workspace(nb, dev)
+        self.nstreams = int(nstreams)
+        self.schedule = None
+        self.graph = None
+
+    def run(self, stream=None):
+        sched = None if self.schedule is None else self.schedule
+        _check("hef_resistance_batched",
+               lib().hef_resistance_batched(self.items, self.G, self.k, self.S, self.code,
+                                            self.clique_mode, sched, self.nstreams,
+                                            _ptr(self.workspace), self.workspace.numel(),
+                                            _stream(stream)))
+        return self.out
+
+    def autotune(self, stream=None):
+        """hef_batch_autotune: keep the fastest stream count and schedule."""
+        ns = c_i32(0)
+        sched = (c_i32 * self.G)()
+        ms = ctypes.c_float(0.0)
+        _check("hef_batch_autotune",
+               lib().hef_batch_autotune(self.items, self.G, self.k, self.S, self.code,
+                                        self.clique_mode, _ptr(self.workspace),
+                                        self.workspace.numel(), _stream(stream),
+                                        ctypes.byref(ns), sched, ctypes.byref(ms)))
+        self.nstreams = ns.value
+        self.schedule = sched
+        return ns.value, list(sched), ms.value
+
+    def check(self):
+        """Raise HefError if any item failed device validation."""
+        st = torch.stack([o["status"] for o in self.out]).cpu()
+        bad = (st[:, 0] != 0).nonzero().flatten().tolist()
+        if bad:
+            raise HefError("hef_resistance_batched", HEF_ERR_INVALID_INPUT,
+                           f"items {bad} rejected by device validation")
+
+    def capture(self):
+        """Record one batched run as a CUDA graph; replay() reruns it."""
+        side = torch.cuda.Stream(device=self.device)
+        side.wait_stream(torch.cuda.current_stream(self.device))
+        with torch.cuda.stream(side):
+            self.run()
+        torch.cuda.current_stream(self.device).wait_stream(side)
+        torch.cuda.synchronize(self.device)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph):
+            self.run()
+        return self.graph
+
+    def replay(self):
+        self.graph.replay()
+        return self.out

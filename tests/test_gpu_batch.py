@@ -1,0 +1,132 @@
+"""Batched form (hef_resistance_batched through the C ABI): every item's
+outputs equal, bit for bit, those of the one-hypergraph path on the same
+inputs; the FP64 items match the oracle; graph replay and the autotuner
+leave the results unchanged; a malformed item is flagged alone."""
+import numpy as np
+import pytest
+import torch
+
+from netlists import start_block
+from netlists.synth import grid_netlist
+from oracle import hef_oracle as O
+from tests._gpu import DEV, rel_errors, run_pipeline, to_dev
+from tests._hypergraphs import from_lists, random_hypergraph
+
+pytestmark = pytest.mark.gpu
+
+
+def hef():
+    import paper_2511_06600_gb300 as m
+    return m
+
+
+def batch_inputs(Hs, S, seed0=0):
+    graphs, host = [], []
+    for g, H in enumerate(Hs):
+        x0c, x0b = start_block(H.n, H.m, S, seed0 + g)
+        t = to_dev(H, x0c, x0b)
+        t["n"] = H.n
+        graphs.append(t)
+        host.append((H, x0c, x0b))
+    return graphs, host
+
+
+def uneven_netlists():
+    Hs = [grid_netlist(nx, ny, int(1.05 * nx * ny), 100 + i)
+          for i, (nx, ny) in enumerate([(40, 30), (12, 10), (64, 50), (25, 25), (90, 70)])]
+    Hs.append(from_lists(12, [[0, 1, 2], [2, 3], [4], [], [5, 6, 7], [6, 8], [1, 3], [11, 0]],
+                         [1.0, 2.0, 1.0, 1.0, 0.5, 1.5, 1.0, 3.0]))
+    Hs.append(random_hypergraph(300, 320, 20, 9, weights=True))
+    return Hs
+
+
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("nstreams", [1, 3, 16])
+def test_batched_equals_single_path_bitwise(dtype, nstreams):
+    k, S = 5, 2
+    Hs = uneven_netlists()
+    graphs, host = batch_inputs(Hs, S)
+    b = hef().Batch(graphs, k, S, dtype, nstreams=nstreams)
+    out = b.run()
+    torch.cuda.synchronize()
+    b.check()
+    for g, (H, x0c, x0b) in enumerate(host):
+        ref = run_pipeline(H, x0c, x0b, k, dtype)
+        got = {key: v.cpu().numpy() for key, v in out[g].items()}
+        assert np.array_equal(got["R"], ref["R"]), g
+        for key in ("argvec", "pmax", "pmin"):
+            assert np.array_equal(got[key], ref[key]), (g, key)
+        assert np.array_equal(got["QH"], ref["QH"]), g
+
+
+def test_batched_fp64_matches_oracle():
+    k, S = 5, 2
+    Hs = uneven_netlists()
+    graphs, host = batch_inputs(Hs, S)
+    b = hef().Batch(graphs, k, S, torch.float64, nstreams=4)
+    out = b.run()
+    torch.cuda.synchronize()
+    for g, (H, x0c, x0b) in enumerate(host):
+        ref = O.hyperedge_resistance(H.n, H.eptr, H.pins, H.w, x0c, x0b, k)["R"]
+        err = rel_errors(out[g]["R"].cpu().numpy(), ref)
+        assert err["max"] <= 1e-9, (g, err)
+
+
+def test_batched_graph_replay_and_autotune():
+    k, S = 5, 2
+    Hs = uneven_netlists()
+    graphs, _ = batch_inputs(Hs, S)
+    b = hef().Batch(graphs, k, S, torch.float32, nstreams=2)
+    first = [o["R"].clone() for o in b.run()]
+    ns, sched, ms = b.autotune()
+    assert ns in (1, 2, 4, 8, 16) and len(sched) == len(Hs) and ms > 0
+    assert all(0 <= s < ns for s in sched)
+    for o in b.out:
+        o["R"].zero_()
+    b.capture()
+    for _ in range(2):
+        out = b.replay()
+    torch.cuda.synchronize()
+    for g in range(len(Hs)):
+        assert torch.equal(out[g]["R"], first[g]), g
+
+
+def test_batched_flags_a_malformed_item_alone():
+    k, S = 3, 1
+    Hs = uneven_netlists()[:3]
+    bad = from_lists(6, [[0, 1], [2, 2, 3], [4, 5]])  # repeated pin in hyperedge 1
+    Hs.insert(1, bad)
+    graphs, _ = batch_inputs(Hs, S)
+    b = hef().Batch(graphs, k, S, torch.float64, nstreams=2)
+    b.run()
+    torch.cuda.synchronize()
+    st = [int(o["status"][0].item()) for o in b.out]
+    assert st[1] != 0 and st[0] == 0 and st[2] == 0 and st[3] == 0
+    with pytest.raises(hef().HefError):
+        b.check()
+
+
+def test_batched_fp32_error_against_fp64():
+    """Sixteen uneven netlists with the 2 + Geometric(0.5) pin law on
+    radius-3 neighbourhoods (k = 20, S = 4, n from 5,000 as in the batched
+    workload, so that n >> K): the FP32 batch within 2e-3 of the FP64 batch
+    (normwise and p99), ranking tau >= 0.999.  (On much smaller netlists the
+    basis of K = 160 columns becomes ill-conditioned and the FP32 rank
+    threshold drops directions that FP64 keeps.)"""
+    from tests._gpu import kendall_tau
+    rng = np.random.default_rng(4)
+    Hs = []
+    for g in range(16):
+        n = int(np.exp(rng.uniform(np.log(5e3), np.log(3e4))))
+        nx = int(np.ceil(np.sqrt(n)))
+        ny = int(np.ceil(n / nx))
+        Hs.append(grid_netlist(nx, ny, int(round(1.05 * nx * ny)), 4000 + g))
+    graphs, _ = batch_inputs(Hs, 4)
+    o32 = hef().Batch(graphs, 20, 4, torch.float32, nstreams=8).run()
+    o64 = hef().Batch(graphs, 20, 4, torch.float64, nstreams=8).run()
+    torch.cuda.synchronize()
+    for g in range(len(Hs)):
+        a, r = o32[g]["R"].cpu().numpy(), o64[g]["R"].cpu().numpy()
+        err = rel_errors(a, r)
+        assert err["normwise"] <= 2e-3 and err["p99"] <= 2e-3, (g, err)
+        assert kendall_tau(a, r) >= 0.999
