@@ -2,7 +2,7 @@
  * hef.h -- C ABI of the GB300 hyperedge effective-resistance library.
  *
  * The library computes the hyperedge effective-resistance estimates of
- * HyperEF 2.0 (arXiv 2511.06600, Algorithm 1, Section III-A.4) on one
+ * HyperEF 2.0 (arXiv 2511.06600, Algorithm 1, Section III-A.3) on one
  * NVIDIA GB300 (sm_103a):
  *
  *   1. hef_build_incidence   Algorithm 1 steps 1-2: the star expansion G_b
@@ -65,7 +65,7 @@ typedef int32_t hef_status;
 #define HEF_REDUCE_SUM 1 /* sum_i r_e(chi_i); with Laplacian eigenvectors of a
                             2-pin graph as the basis this is Eq. eff_resist0 */
 
-/* Clique-expansion pair weight (Section III-A.4). */
+/* Clique-expansion pair weight (Section III-A.3). */
 #define HEF_CLIQUE_HYPEREDGE 0 /* w(e)/(|e|-1): clique degree = hypergraph degree */
 #define HEF_CLIQUE_PAPER 1     /* w(e)/C(|e|,2): weight spread evenly over pairs */
 
@@ -100,7 +100,7 @@ int32_t hef_trace_read(int32_t cap, char* names, int64_t* launches,
                        double* total_ms);
 
 /* ------------------------------------------------------------------------
- * Incidence (Algorithm 1 steps 1-2; expansions of Section III-A.4).
+ * Incidence (Algorithm 1 steps 1-2; expansions of Section III-A.3).
  *
  * Input H = (V, E, w) in edge-major (CSC) form: hyperedge e has the pins
  * pins[eptr[e] .. eptr[e+1]) (vertex ids in [0, n), distinct within e) and
@@ -146,7 +146,7 @@ hef_status hef_incidence_export(const hef_incidence* inc, int32_t* perm,
 void hef_free_incidence(hef_incidence* inc);
 
 /* ------------------------------------------------------------------------
- * Krylov basis (Algorithm 1 step 3, Eq. krylov; Section III-A.4).
+ * Krylov basis (Algorithm 1 step 3, Eq. krylov; Section III-A.3).
  *
  * For each expansion op (0 = clique on n vertices, 1 = star on n + m
  * vertices) and start s < S, the chain x, M x, ..., M^k x of the random-walk

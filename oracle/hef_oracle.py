@@ -1,5 +1,5 @@
 """Plain FP64 CPU oracle of the hyperedge effective-resistance estimator of
-HyperEF 2.0 (Algorithm 1, Section III-A.4).
+HyperEF 2.0 (Algorithm 1, Section III-A.3).
 
 TEST INFRASTRUCTURE ONLY: imported by the tests, the smoke check and the
 benchmark's CPU-baseline leg; the GPU path never imports it and the two share
@@ -49,7 +49,7 @@ QH_TINY = 1e-300
 
 
 # ----------------------------------------------------------------------------
-# Section II / III-A.4: expansions and their random-walk operators
+# Section II / III-A.3: expansions and their random-walk operators
 
 
 def edge_sizes(eptr):
@@ -57,7 +57,7 @@ def edge_sizes(eptr):
 
 
 def clique_expansion(n, eptr, pins, w, clique="hyperedge"):
-    """Adjacency W_c of the clique expansion G_c (Section III-A.4).
+    """Adjacency W_c of the clique expansion G_c (Section III-A.3).
 
     Every unordered pin pair {u, v} of a hyperedge e with |e| >= 2 receives
     weight w(e)/(|e|-1) (``clique="hyperedge"``) or w(e)/C(|e|,2)
@@ -94,7 +94,7 @@ def clique_expansion(n, eptr, pins, w, clique="hyperedge"):
 
 def star_expansion(n, eptr, pins, w):
     """Adjacency W_b of the star (bipartite) expansion G_b on n + m vertices
-    (Section III-A.4): vertex p and star node n+e are joined with weight
+    (Section III-A.3): vertex p and star node n+e are joined with weight
     z_b(e, p) = w(e)/|e| for each pin p of hyperedge e with |e| >= 2."""
     sizes = edge_sizes(eptr)
     m = sizes.size
@@ -202,7 +202,7 @@ def krylov_basis(H_n, eptr, pins, w, x0_c, x0_b, k, clique="hyperedge"):
     Column c = (j-1)*2S + op*S + s holds the vertex entries of the j-th chain
     vector of start s of expansion op (0 = clique, 1 = star), with its mean
     removed (vectors are taken modulo the all-ones vector: scores only see
-    differences).  Star-node entries are dropped (Section III-A.4)."""
+    differences).  Star-node entries are dropped (Section III-A.3)."""
     n = H_n
     S = x0_c.shape[1]
     Mc, dc = random_walk(clique_expansion(n, eptr, pins, w, clique))

@@ -1,5 +1,5 @@
 // Incidence build: Algorithm 1 steps 1-2 (star and clique expansions of
-// Section III-A.4, kept implicit).  Validates H on the device, orders the
+// Section III-A.3, kept implicit).  Validates H on the device, orders the
 // hyperedges for locality (ascending smallest pin, stable), builds the
 // vertex-major transpose with a stable radix sort (so every later sum runs in
 // a fixed order) and the per-edge / per-vertex scalars of both expansions.

@@ -1,4 +1,4 @@
-// Krylov basis: Algorithm 1 step 3 (Eq. krylov, Section III-A.4).
+// Krylov basis: Algorithm 1 step 3 (Eq. krylov, Section III-A.3).
 //
 // For each expansion (clique G_c on n vertices, star G_b on n + m vertices)
 // and each of S starts, the chain x_1 .. x_k spans M x, ..., M^k x of the

@@ -79,7 +79,7 @@ def test_clique_and_star_match_signed_incidence():
 def test_expansion_degrees_match_hypergraph_degree():
     """Section II defines d_v = sum_{e ∋ v} w(e).  With weight w/(|e|-1) each
     pin has |e|-1 clique neighbours, so the clique degree is d_v; the
-    C(|e|,2) weighting spreads w(e) evenly over the pairs (Section III-A.4),
+    C(|e|,2) weighting spreads w(e) evenly over the pairs (Section III-A.3),
     so the clique weights of e sum to w(e); the star node of e has degree
     |e| * w(e)/|e| = w(e)."""
     H = random_hypergraph(40, 30, 9, 5, weights=True)
