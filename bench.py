@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-backward", action="store_true")
     ap.add_argument("--no-batched", action="store_true")
+    ap.add_argument("--no-precision", action="store_true")
+    ap.add_argument("--no-precision-oracle", action="store_true")
     ap.add_argument("--batched-graphs", type=int, default=64)
     ap.add_argument("--backward-workload", default="grid500x400_m210k_logw")
     return ap.parse_args()
@@ -225,6 +227,69 @@ def cpu_baseline(name):
 
 
 # ---------------------------------------------------------------- our arm
+
+def score_errors(R, ref):
+    big = ref >= 1e-3 * ref.max()
+    rel = np.abs(R - ref) / np.maximum(ref, 1e-300)
+    from scipy.stats import kendalltau
+    return {"max_rel": float(rel[big].max()), "p99_rel": float(np.percentile(rel[ref > 0], 99)),
+            "normwise": float(np.abs(R - ref).max() / ref.max()),
+            "kendall_tau": float(kendalltau(R, ref).statistic)}
+
+
+def precision_leg(hef, args, dev, rank, timed, max_over_ranks, world):
+    """The precision form at its own scale: the 1200 x 1000 grid with 1.3M
+    nets (2 + Geometric(0.5) pins, radius 3), k = 24, S = 8 (K = 384), FP32
+    basis with tensor-core or FP32 Gram, FP64 Cholesky and Q_H; one CUDA
+    graph per step.  Against it: the FP64 form on the same instance (one
+    step), and the FP64 oracle on the induced 400 x 250 window (100k cells)
+    scored by the same FP32 path."""
+    import torch
+    name = "grid1200x1000_m1300k"
+    H, k, S = instance(name, rank)
+    K = 2 * k * S
+    x0c, x0b = start_block(H.n, H.m, S, 3 + rank)
+    t = dict(eptr=torch.from_numpy(H.eptr).to(dev), pins=torch.from_numpy(H.pins).to(dev),
+             w=torch.from_numpy(H.w).to(dev), x0c=torch.from_numpy(x0c).to(dev),
+             x0b=torch.from_numpy(x0b).to(dev))
+    pipe = hef.Pipeline(H.n, H.m, H.P, k, S, torch.float32, device=dev)
+    pipe.run(t["eptr"], t["pins"], t["w"], t["x0c"], t["x0b"])
+    torch.cuda.synchronize()
+    pipe.check()
+    pipe.capture(t["eptr"], t["pins"], t["w"], t["x0c"], t["x0b"])
+    ms, _, _, _ = timed(pipe.replay, args.steps, args.warmup)
+    t32 = max_over_ranks(sum(ms) / len(ms))
+    R32 = pipe.out["R"].cpu().numpy()
+    rank32 = int(pipe.rank.item())
+    del pipe
+    p64 = hef.Pipeline(H.n, H.m, H.P, k, S, torch.float64, device=dev)
+    step64 = lambda: p64.run(t["eptr"], t["pins"], t["w"], t["x0c"], t["x0b"])  # noqa
+    ms64, _, _, _ = timed(step64, 1, 1)
+    t64 = max_over_ranks(sum(ms64) / len(ms64))
+    R64 = p64.out["R"].cpu().numpy()
+    del p64
+    out = {"workload": name, "n": H.n, "m": H.m, "P": H.P, "k": k, "S": S, "K": K,
+           "dtype": "f32 basis, FP64 Cholesky and Q_H", "rank": rank32, "ms_per_step": t32,
+           "pins_per_s": world * H.P / (t32 * 1e-3),
+           "fp64_plain": {"ms_per_step": t64, "pins_per_s": world * H.P / (t64 * 1e-3)},
+           "speedup_vs_fp64": t64 / t32, "error_vs_fp64_gpu": score_errors(R32, R64)}
+    if rank == 0 and not args.no_precision_oracle:
+        from oracle import hef_oracle as O
+        Hs = window_subhypergraph(H, 0, 400, 0, 250)
+        xs, xb = start_block(Hs.n, Hs.m, S, 3)
+        tw = dict(eptr=torch.from_numpy(Hs.eptr).to(dev), pins=torch.from_numpy(Hs.pins).to(dev),
+                  w=torch.from_numpy(Hs.w).to(dev), x0c=torch.from_numpy(xs).to(dev),
+                  x0b=torch.from_numpy(xb).to(dev))
+        o = hef.hyperedge_resistance(Hs.n, tw["eptr"], tw["pins"], tw["w"], tw["x0c"], tw["x0b"], k,
+                                     torch.float32)
+        Rw = o["R"].cpu().numpy()
+        t0 = time.perf_counter()
+        ref = O.hyperedge_resistance(Hs.n, Hs.eptr, Hs.pins, Hs.w, xs, xb, k)["R"]
+        out["error_vs_oracle_window"] = dict(score_errors(Rw, ref), n=Hs.n, m=Hs.m,
+                                             window="400x250",
+                                             oracle_s=time.perf_counter() - t0)
+    return out
+
 
 def batched_leg(hef, args, dev, rank, timed, max_over_ranks, world):
     """The batched form: G netlists of uneven sizes (n log-uniform in
@@ -499,6 +564,11 @@ def main():
     if not args.no_backward:
         bwd = backward_leg(hef, args, dev, rank, timed, max_over_ranks, world)
 
+    # ---- precision form at its own scale (1.2M cells, K = 384)
+    precision = None
+    if not args.no_precision:
+        precision = precision_leg(hef, args, dev, rank, timed, max_over_ranks, world)
+
     # ---- batched form: many uneven netlists in one captured call
     batched = None
     if not args.no_batched:
@@ -528,6 +598,7 @@ def main():
             "e2e": e2e,
             "backward": bwd,
             "batched": batched,
+            "precision": precision,
             "gpu_launches": launches,
             "cuda_graph": graph,
             "launches_per_step": launches / max(args.steps, 1),
