@@ -256,6 +256,13 @@ def precision_leg(hef, args, dev, rank, timed, max_over_ranks, world):
     pipe.run(t["eptr"], t["pins"], t["w"], t["x0c"], t["x0b"])
     torch.cuda.synchronize()
     pipe.check()
+    hef.trace_read()
+    hef.trace_kernels("k_")
+    pipe.run(t["eptr"], t["pins"], t["w"], t["x0c"], t["x0b"])
+    torch.cuda.synchronize()
+    hef.trace_kernels(None)
+    per_kernel = {k_: round(v[1], 3) for k_, v in
+                  sorted(hef.trace_read().items(), key=lambda kv: -kv[1][1])[:8]}
     pipe.capture(t["eptr"], t["pins"], t["w"], t["x0c"], t["x0b"])
     ms, _, _, _ = timed(pipe.replay, args.steps, args.warmup)
     t32 = max_over_ranks(sum(ms) / len(ms))
@@ -272,7 +279,8 @@ def precision_leg(hef, args, dev, rank, timed, max_over_ranks, world):
            "dtype": "f32 basis, FP64 Cholesky and Q_H", "rank": rank32, "ms_per_step": t32,
            "pins_per_s": world * H.P / (t32 * 1e-3),
            "fp64_plain": {"ms_per_step": t64, "pins_per_s": world * H.P / (t64 * 1e-3)},
-           "speedup_vs_fp64": t64 / t32, "error_vs_fp64_gpu": score_errors(R32, R64)}
+           "speedup_vs_fp64": t64 / t32, "error_vs_fp64_gpu": score_errors(R32, R64),
+           "top_kernels_ms_one_step": per_kernel}
     if rank == 0 and not args.no_precision_oracle:
         from oracle import hef_oracle as O
         Hs = window_subhypergraph(H, 0, 400, 0, 250)

@@ -549,9 +549,12 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
   HEF_ENSURE_SMEM(k_apply<T>, (int)apply_smem(RB));
   const int agrid = (int)((n + RB - 1) / RB);
   const int athreads = RB * 2;  // (RB / 4) row groups x 8 column groups
+  // FP32 form: the FP32 elimination works in shared memory when [A | I]
+  // fits (K <= 160), else in the (L2-resident) FP64 scratch reused as FP32
   const size_t fast_smem = (size_t)K * 2 * K * sizeof(float);
-  const bool fast_ok = sizeof(T) == 4 && fast_smem <= 200 * 1024;
-  if (fast_ok)
+  const bool fast_ok = sizeof(T) == 4;
+  const bool fast_in_smem = fast_ok && fast_smem <= 200 * 1024;
+  if (fast_in_smem)
     HEF_ENSURE_SMEM((k_chol_aug<float, T>), fast_smem);
   const double tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
   const double gtol = sizeof(T) == 8 ? 1e-8 : 1e-4;
@@ -578,8 +581,10 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
       HEF_LAUNCH("k_gram_project", st, k_gram_project<<<stride_grid((long long)K * K, 2), kThreads, 0,
                                                          st>>>(w.G, w.c, K, (double)n, w.A64, w.A32));
       if (fast_ok) {
-        HEF_LAUNCH("k_chol_aug", st, k_chol_aug<float, T><<<1, 1024, fast_smem, st>>>(
-                                         w.G, w.c, w.A32, K, Kp, (double)n, tol, nullptr, 1, 1, 0, o));
+        HEF_LAUNCH("k_chol_aug", st, k_chol_aug<float, T><<<1, 1024, fast_in_smem ? fast_smem : 0, st>>>(
+                                         w.G, w.c, w.A32, K, Kp, (double)n, tol,
+                                         fast_in_smem ? nullptr : reinterpret_cast<float*>(w.Wg),
+                                         fast_in_smem ? 1 : 0, 1, 0, o));
       }
       // exact FP64 path: always for the FP64 form, on demand for the FP32 form
       HEF_LAUNCH("k_chol_aug", st, k_chol_aug<double, T><<<1, 1024, 0, st>>>(

@@ -29,6 +29,7 @@ struct GramTcArgs {
   long long ldv;
   int n, K, Kq, nb;
   int rows_per_cta;
+  int gmask[4];  // block rows of G_aug computed by CTA group blockIdx.y (bit b: rows 128b..)
   double* part;  // gridDim.x x Kq x Kq
   int* err;
 };
@@ -59,7 +60,12 @@ __device__ __forceinline__ void gram_load_slab(const GramTcArgs& a, long long ro
   }
 }
 
-template <int NB>
+// G_aug block rows of this CTA's group: block b covers basis rows
+// [128b, 128b+128) against basis columns [128b, Kq) (N_b = Kq - 128b, issued
+// as MMAs of N <= 256); its accumulator occupies TMEM columns from the sum of
+// the earlier blocks' N in the group.  NB blocks of 128 rows pad the
+// transposed slab; STAGES shared-memory stages (2, or 1 when two do not fit).
+template <int NB, int STAGES>
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -67,17 +73,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   constexpr int Mpad = NB * 128;
   constexpr int PER = kSlab * (Mpad / 4) / kTcThreads;  // float4 slots per thread
   const uint32_t tile_bytes = (uint32_t)Mpad * 128u;
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 4 * tile_bytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGES * tile_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int N0 = a.Kq, N1 = a.Kq - 128;
+  const int gmask = a.gmask[blockIdx.y];
+  int toff[NB];  // TMEM column of each block of the group
+  int used = 0;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    toff[b] = used;
+    if ((gmask >> b) & 1) used += a.Kq - 128 * b;
+  }
   uint32_t ncols = 32;
-  while (ncols < (uint32_t)(N0 + (NB > 1 ? N1 : 0))) ncols <<= 1;
+  while (ncols < (uint32_t)used) ncols <<= 1;
 
   if (warp == 0) tmem_alloc(tmem_slot, ncols);
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+#pragma unroll
+    for (int q = 0; q < STAGES; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   tc_fence_before();
@@ -88,18 +101,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   const long long r0 = (long long)blockIdx.x * a.rows_per_cta;
   const long long r1 = min((long long)a.n, r0 + a.rows_per_cta);
   const int nslab = r1 > r0 ? (int)((r1 - r0 + kSlab - 1) / kSlab) : 0;
-  const uint32_t id0 = idesc_tf32(128, N0);
-  const uint32_t id1 = idesc_tf32(128, NB > 1 ? N1 : 16);
   bool ok = true;
   int committed = 0;  // slabs whose MMAs were issued
   float4 cur[PER], nxt[PER];
   if (nslab > 0) gram_load_slab<PER>(a, r0, r1, cur);
 
   for (int t = 0; t < nslab; ++t) {
-    const int s = t & 1;
+    const int s = t % STAGES;
     // next slab's loads are in flight while this one is converted and issued
     if (t + 1 < nslab) gram_load_slab<PER>(a, r0 + (long long)(t + 1) * kSlab, r1, nxt);
-    if (t >= 2) ok = ok && mbar_wait(&bars[s], ((t - 2) >> 1) & 1, kWaitIters);
+    if (t >= STAGES) ok = ok && mbar_wait(&bars[s], ((t - STAGES) / STAGES) & 1, kWaitIters);
     if (!__syncthreads_and(ok)) {
       ok = false;
       break;
@@ -129,14 +140,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
       const uint32_t shi = smem_u32(hi), slo = smem_u32(lo);
 #pragma unroll
       for (int ks = 0; ks < kSlab / 8; ++ks) {
+#pragma unroll
         for (int b = 0; b < NB; ++b) {
+          if (!((gmask >> b) & 1)) continue;
+          const int Nb = a.Kq - 128 * b;
           const uint32_t aoff = (uint32_t)b * 128u * 128u + (uint32_t)ks * 32u;
-          const uint32_t d = tmem + (b ? (uint32_t)N0 : 0u);
-          const uint32_t id = b ? id1 : id0;
           const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
-          mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(shi + aoff), id, acc);
-          mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(slo + aoff), id, 1u);
-          mma_tf32(d, desc_k_sw128(slo + aoff), desc_k_sw128(shi + aoff), id, 1u);
+          for (int h0 = 0; h0 < Nb; h0 += 256) {
+            const int Nh = min(256, Nb - h0);
+            const uint32_t boff = aoff + (uint32_t)h0 * 128u;
+            const uint32_t d = tmem + (uint32_t)(toff[b] + h0);
+            const uint32_t id = idesc_tf32(128, Nh);
+            mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(shi + boff), id, acc);
+            mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(slo + boff), id, 1u);
+            mma_tf32(d, desc_k_sw128(slo + aoff), desc_k_sw128(shi + boff), id, 1u);
+          }
         }
       }
       mma_commit(&bars[s]);
@@ -146,7 +164,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   // the last commit covers every MMA issued before it
   if (committed > 0) {
     const int t = committed - 1;
-    const bool done = mbar_wait(&bars[t & 1], (t >> 1) & 1, kWaitIters);
+    const bool done = mbar_wait(&bars[t % STAGES], (t / STAGES) & 1, kWaitIters);
     ok = ok && done;
   }
   ok = __syncthreads_and(ok);
@@ -154,12 +172,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   double* P = a.part + (size_t)blockIdx.x * a.Kq * a.Kq;
   if (ok && committed > 0) {
     const int q = warp & 3, half = warp >> 2;
+#pragma unroll
     for (int b = 0; b < NB; ++b) {
-      const int ncol = b ? N1 : N0;
+      if (!((gmask >> b) & 1)) continue;
+      const int ncol = a.Kq - 128 * b;
       const int i = b * 128 + q * 32 + lane;
       for (int c8 = half; c8 < ncol / 8; c8 += 2) {
         float v[8];
-        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (b ? (uint32_t)N0 : 0u) + (uint32_t)c8 * 8u, v);
+        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)toff[b] + (uint32_t)c8 * 8u, v);
         tmem_wait_ld();
         const int j0 = b * 128 + c8 * 8;
         if (i < a.Kq && j0 + 7 >= i) {  // upper triangle only (the reducer reads i <= j)
@@ -169,11 +189,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
       }
     }
   } else {
-    for (int e = tid; e < a.Kq * a.Kq; e += kTcThreads) P[e] = 0.0;
+    // zero this group's block rows
+    for (int e = tid; e < a.Kq * a.Kq; e += kTcThreads)
+      if ((gmask >> ((e / a.Kq) / 128)) & 1) P[e] = 0.0;
     if (!ok && tid == 0) atomicExch(a.err, 1);
     if (!ok && committed > 0) {  // let MMAs in flight finish before TMEM is released
       const int t = committed - 1;
-      mbar_wait(&bars[t & 1], (t >> 1) & 1, kWaitIters);
+      mbar_wait(&bars[t % STAGES], (t / STAGES) & 1, kWaitIters);
     }
   }
   tc_fence_before();
@@ -261,7 +283,7 @@ struct ApplyTcArgs {
 // Rinv^T (Rinv is upper triangular, so block ka feeds output columns
 // j >= 32 ka only).  RESB: every B tile stays resident in shared memory
 // (staged once per CTA); otherwise B is staged with A for every block.
-template <bool RESB>
+template <bool RESB, int STAGES>
 __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -277,15 +299,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
   const uint32_t stage_bytes = 2 * a_bytes + (RESB ? 0u : b_region);
   unsigned char* bbase = base;
   unsigned char* sbase = base + (RESB ? b_region : 0u);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + 2 * stage_bytes);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sbase + STAGES * stage_bytes);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint32_t ncols = 32;
   while (ncols < (uint32_t)a.Kq) ncols <<= 1;
   if (warp == 0) tmem_alloc(tmem_slot, ncols);
   if (tid == 0) {
-    mbar_init(&bars[0], 1);
-    mbar_init(&bars[1], 1);
+#pragma unroll
+    for (int q = 0; q < STAGES; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // B tile ka: row jr = Rinv^T row 32 ka + jr, basis values [32 ka, 32 ka + 32)
@@ -339,7 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long row0 = (long long)tile * 128;
     for (int ka = 0; ka < nka; ++ka, ++g) {
-      const int s = g & 1;
+      const int s = STAGES == 1 ? 0 : (g & 1);
       const uint32_t uses_s = s ? uses1 : uses0;
       if (ka + 1 < nka) load_a(tile, ka + 1, nxt);
       else load_a(tile + gridDim.x, 0, nxt);
@@ -379,16 +401,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
       if (tid == 0) {
         tc_fence_after();
         const int c0 = ka * 32;
-        const uint32_t id = idesc_tf32(128, brows(ka));
-        const uint32_t d = tmem + (uint32_t)c0;
+        const int nr = brows(ka);
         const uint32_t sah = smem_u32(ahi), sal = smem_u32(alo);
         const uint32_t sbh = smem_u32(bhi), sbl = smem_u32(blo);
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks) {
           const uint32_t ko = (uint32_t)ks * 32u;
-          mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbh + ko), id, (ka > 0 || ks > 0) ? 1u : 0u);
-          mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbl + ko), id, 1u);
-          mma_tf32(d, desc_k_sw128(sal + ko), desc_k_sw128(sbh + ko), id, 1u);
+          // output columns c0 .. c0 + nr - 1, in MMAs of N <= 256
+          for (int h0 = 0; h0 < nr; h0 += 256) {
+            const int Nh = min(256, nr - h0);
+            const uint32_t id = idesc_tf32(128, Nh);
+            const uint32_t d = tmem + (uint32_t)(c0 + h0);
+            const uint32_t bo = ko + (uint32_t)h0 * 128u;
+            // block 0 covers every output column: its first K step starts them
+            const uint32_t acc = (ka > 0 || ks > 0) ? 1u : 0u;
+            mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbh + bo), id, acc);
+            mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbl + bo), id, 1u);
+            mma_tf32(d, desc_k_sw128(sal + ko), desc_k_sw128(sbh + bo), id, 1u);
+          }
         }
         mma_commit(&bars[s]);
       }
@@ -446,7 +476,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
 
 }  // namespace
 
-int apply_tc_supported(int K) { return K >= 1 && K <= 256; }
+int apply_tc_supported(int K) { return K >= 1 && K <= 511; }
 
 size_t apply_tc_scratch_floats(int K) {
   const int Kq = (K + 15) & ~15, Kd = (K + 31) & ~31;
@@ -477,20 +507,23 @@ hef_status apply_tc(float* V, long long ldv, long long n, int K, const float* Ri
   const int nka = Kd / 32;
   const size_t bres = (size_t)(nka * Kq - 16 * nka * (nka - 1)) * 256;  // resident B, hi + lo
   const size_t smem_res = 1024 + bres + 2 * (2 * 128 * 128) + 64;
+  const size_t stage = 2 * 128 * 128 + 2 * (size_t)Kq * 128;  // A and B of one K block
+  const size_t smem2 = 1024 + 2 * stage + 64, smem1 = 1024 + stage + 64;
   if (smem_res <= 220 * 1024) {
-    HEF_ENSURE_SMEM(k_apply_tc<true>, (int)smem_res);
-    HEF_LAUNCH("k_apply_tc", st, k_apply_tc<true><<<ctas, kTcThreads, smem_res, st>>>(a));
+    HEF_ENSURE_SMEM((k_apply_tc<true, 2>), (int)smem_res);
+    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<true, 2><<<ctas, kTcThreads, smem_res, st>>>(a)));
+  } else if (smem2 <= 220 * 1024) {
+    HEF_ENSURE_SMEM((k_apply_tc<false, 2>), (int)smem2);
+    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<false, 2><<<ctas, kTcThreads, smem2, st>>>(a)));
   } else {
-    const size_t stage = 2 * 128 * 128 + 2 * (size_t)Kq * 128;
-    const size_t smem = 1024 + 2 * stage + 64;
-    HEF_ENSURE_SMEM(k_apply_tc<false>, (int)smem);
-    HEF_LAUNCH("k_apply_tc", st, k_apply_tc<false><<<ctas, kTcThreads, smem, st>>>(a));
+    HEF_ENSURE_SMEM((k_apply_tc<false, 1>), (int)smem1);
+    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<false, 1><<<ctas, kTcThreads, smem1, st>>>(a)));
   }
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
 
-int gram_tc_supported(int K) { return K >= 1 && K + 1 <= 256; }
+int gram_tc_supported(int K) { return K >= 1 && K + 1 <= 512; }
 
 int gram_tc_ctas(long long n) {
   long long want = (n + kSlab - 1) / kSlab;
@@ -503,10 +536,34 @@ size_t gram_tc_part_doubles(long long n, int K) {
   return (size_t)gram_tc_ctas(n) * Kq * Kq;
 }
 
+// Block rows of G_aug packed into CTA groups whose accumulators fit the 512
+// TMEM columns (largest first, first fit).  Returns the number of groups.
+static int gram_groups(int Kq, int nb, int (&gmask)[4]) {
+  int load[4] = {0, 0, 0, 0};
+  int ng = 0;
+  for (int b = 0; b < nb; ++b) {
+    const int N = Kq - 128 * b;
+    int g = 0;
+    while (g < ng && load[g] + N > 512) ++g;
+    if (g == ng) gmask[ng++] = 0;
+    gmask[g] |= 1 << b;
+    load[g] += N;
+  }
+  return ng;
+}
+
+template <int NB, int STAGES>
+static hef_status launch_gram_tc(const GramTcArgs& a, int ctas, int ng, cudaStream_t st) {
+  const size_t smem = 1024 + 2 * (size_t)STAGES * NB * 128 * 128 + 64;
+  HEF_ENSURE_SMEM((k_gram_tc<NB, STAGES>), (int)smem);
+  HEF_LAUNCH("k_gram_tc", st, (k_gram_tc<NB, STAGES><<<dim3(ctas, ng), kTcThreads, smem, st>>>(a)));
+  return HEF_OK;
+}
+
 hef_status gram_tc(const float* V, long long ldv, long long n, int K, double* part, double* G,
                    double* c, int* err, cudaStream_t st) {
   const int Kq = (K + 1 + 15) & ~15;
-  const int nb = Kq > 128 ? 2 : 1;
+  const int nb = (Kq + 127) / 128;
   const int ctas = gram_tc_ctas(n);
   GramTcArgs a;
   a.V = V;
@@ -518,14 +575,16 @@ hef_status gram_tc(const float* V, long long ldv, long long n, int K, double* pa
   a.rows_per_cta = (int)(((n + ctas - 1) / ctas + kSlab - 1) / kSlab * kSlab);
   a.part = part;
   a.err = err;
-  const size_t smem = 1024 + 4 * (size_t)nb * 128 * 128 + 64;
-  if (nb == 1) {
-    HEF_ENSURE_SMEM(k_gram_tc<1>, (int)smem);
-    HEF_LAUNCH("k_gram_tc", st, k_gram_tc<1><<<ctas, kTcThreads, smem, st>>>(a));
-  } else {
-    HEF_ENSURE_SMEM(k_gram_tc<2>, (int)smem);
-    HEF_LAUNCH("k_gram_tc", st, k_gram_tc<2><<<ctas, kTcThreads, smem, st>>>(a));
+  for (int g = 0; g < 4; ++g) a.gmask[g] = 0;
+  const int ng = gram_groups(Kq, nb, a.gmask);
+  hef_status s;
+  switch (nb) {
+    case 1: s = launch_gram_tc<1, 2>(a, ctas, ng, st); break;
+    case 2: s = launch_gram_tc<2, 2>(a, ctas, ng, st); break;
+    case 3: s = launch_gram_tc<3, 2>(a, ctas, ng, st); break;
+    default: s = launch_gram_tc<4, 1>(a, ctas, ng, st); break;
   }
+  if (s) return s;
   HEF_LAUNCH("k_gram_tc_reduce", st,
              k_gram_tc_reduce<<<stride_grid((long long)K * K + K, 4), kThreads, 0, st>>>(
                  part, K, Kq, ctas, G, c));
