@@ -164,6 +164,10 @@ def kernel_model(name, H, K, S, k, esz):
         return "hbm", 4.0 * P + 4.0 * (n + 1) + 8.0 * (2 * m + 6 * n) + esz * S * (2 * m + 6 * n)
     if name == "k_update":
         return "hbm", esz * S * (2 * n + m) * 4.0 + 8.0 * (2 * n + m)
+    if name == "k_krylov_steps":  # all k steps in one launch, plus the last archive
+        step = sum(kernel_model(x, H, K, S, k, esz)[1]
+                   for x in ("k_edge_pass", "k_node_pass", "k_update"))
+        return "hbm", k * step + 2.0 * n * S * esz * 2
     return "hbm", float("nan")
 
 
@@ -532,6 +536,27 @@ def main():
     roof["launches"] = nl
     roof["avg_ms"] = tot / max(nl, 1)
 
+    # ---- latency of the small FP64 case (64 x 32 grid, 2,300 nets, k = 10,
+    # S = 1), one CUDA graph per step, with the Krylov steps as one
+    # persistent launch and as three launches per step
+    small = {}
+    Hs, ks, Ss = instance("grid64x32_m2300", rank)
+    xs0, xs1 = start_block(Hs.n, Hs.m, Ss, rank)
+    ts = dict(eptr=torch.from_numpy(Hs.eptr).to(dev), pins=torch.from_numpy(Hs.pins).to(dev),
+              w=torch.from_numpy(Hs.w).to(dev), x0c=torch.from_numpy(xs0).to(dev),
+              x0b=torch.from_numpy(xs1).to(dev))
+    for label, mode in (("persistent", 1), ("per_step_launches", 0)):
+        hef.set_krylov_persistent(mode)
+        ps = hef.Pipeline(Hs.n, Hs.m, Hs.P, ks, Ss, torch.float64, device=dev)
+        ps.run(ts["eptr"], ts["pins"], ts["w"], ts["x0c"], ts["x0b"])
+        ps.capture(ts["eptr"], ts["pins"], ts["w"], ts["x0c"], ts["x0b"])
+        ms_s, _, _, _ = timed(ps.replay, args.steps, args.warmup)
+        ps.check()
+        small[label + "_ms"] = max_over_ranks(statistics.median(ms_s))
+        del ps
+    hef.set_krylov_persistent(1)
+    small.update(workload="grid64x32_m2300", dtype="f64", n=Hs.n, m=Hs.m, P=Hs.P, k=ks, S=Ss)
+
     # ---- plain FP64 form (speedup reference) and its agreement with the FP32 form
     pipe64 = hef.Pipeline(H.n, H.m, H.P, k, S, torch.float64, device=dev)
     step64 = lambda: pipe64.run(t_in["eptr"], t_in["pins"], t_in["w"], t_in["x0c"], t_in["x0b"])  # noqa
@@ -600,6 +625,7 @@ def main():
             "fp64_plain": {"value": world * H.P / (t64 * 1e-3), "unit": "pins/s",
                            "ms_per_step": t64},
             "speedup_vs_fp64": t64 / t_step,
+            "small_fp64_latency": small,
             "error_vs_fp64": err,
             "roofline": roof,
             "cpu_baseline": cpu,

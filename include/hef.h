@@ -74,6 +74,9 @@ typedef int32_t hef_status;
 #define HEF_BAD_PIN 2u       /* a pin outside [0, n) */
 #define HEF_DUP_PIN 4u       /* a vertex repeated within one hyperedge */
 #define HEF_BAD_WEIGHT 8u    /* a weight that is not finite and > 0 */
+#define HEF_WAIT_TIMEOUT 16u /* a bounded grid-wide wait of the one-launch
+                                Krylov form expired (hef_incidence_check then
+                                returns HEF_ERR_TIMEOUT) */
 
 const char* hef_last_error(void);
 const char* hef_status_string(hef_status s);
@@ -126,7 +129,9 @@ hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P,
 
 /* Synchronises `stream` and returns HEF_ERR_INVALID_INPUT (with the status
  * bits in *detail, the first offending hyperedge in *where; either may be
- * NULL) if the device-side validation failed, else HEF_OK. */
+ * NULL) if the device-side validation failed, HEF_ERR_TIMEOUT if a bounded
+ * device wait of a later call on this incidence expired (HEF_WAIT_TIMEOUT),
+ * else HEF_OK. */
 hef_status hef_incidence_check(const hef_incidence* inc, void* stream,
                                uint32_t* detail, int64_t* where);
 
@@ -172,6 +177,22 @@ hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int32_t S,
                             void* workspace, size_t workspace_bytes,
                             void* stream);
 
+/* Launch form of the Krylov calls made from the calling host thread
+ * (a library setting; the paper has no counterpart).  on = 1 (default): a
+ * hypergraph small enough that every row of a pass gets a resident thread
+ * (2n + m up to about 1e5 rows) runs all k steps as one persistent launch
+ * whose CTAs are all resident at once and meet at bounded grid-wide
+ * barriers (a barrier that waits too long sets HEF_WAIT_TIMEOUT in the
+ * incidence's status word instead of hanging); larger ones, and every call
+ * with on = 0, use three launches per step.  Both forms give the same
+ * results up to the order of floating-point sums.  The persistent form
+ * assumes the kernel has the GPU to itself; hef_resistance_batched always
+ * uses the per-step form.  on = 2 exercises the timeout path: the persistent
+ * form (when it applies) is launched with twice the CTAs that can be
+ * resident, so its first barrier cannot complete; the launch ends after the
+ * wait limit with HEF_WAIT_TIMEOUT set and later calls on that incidence do
+ * no work until it is rebuilt. */
+hef_status hef_set_krylov_persistent(int32_t on);
 /* Krylov basis with a tape for the backward: computes exactly what
  * hef_krylov_basis computes and also stores in `tape` (device, 256-byte
  * aligned, hef_krylov_tape_bytes bytes, caller-owned) what

@@ -59,6 +59,7 @@ _SIGS = {
     "hef_batch_autotune": (c_i32, [c_p, c_i32, c_i32, c_i32, c_i32, c_i32, c_p, c_sz, c_p, c_p,
                                    c_p, c_p]),
     "hef_krylov_tape_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32]),
+    "hef_set_krylov_persistent": (c_i32, [c_i32]),
     "hef_krylov_basis_tape": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p, c_sz,
                                       c_p, c_sz, c_p]),
     "hef_edge_resistance_backward_workspace_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32, c_i32]),
@@ -230,6 +231,11 @@ def krylov_basis(inc, x0_clique, x0_star, k, dtype=torch.float64, V=None, worksp
            L.hef_krylov_basis(inc.handle, k, S, code, _ptr(x0_clique), _ptr(x0_star), _ptr(V),
                               V.stride(0), _ptr(workspace), workspace.numel(), _stream(stream)))
     return V
+
+
+def set_krylov_persistent(on):
+    """hef_set_krylov_persistent for calls from this thread (0, 1 or 2)."""
+    _check("hef_set_krylov_persistent", lib().hef_set_krylov_persistent(int(on)))
 
 
 def krylov_basis_tape(inc, x0_clique, x0_star, k, dtype=torch.float64, stream=None):

@@ -168,11 +168,14 @@ hef_status run_batch(const hef_batch_item* items, int G, int k, int S, int dtype
     off[g + 1] = off[g] + item_bytes(zs[g]);
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  // items overlap on the GPU: one-launch Krylov grids could not all be resident
+  krylov_allow_persistent(false);
   for (int g : order) {
     const int si = sched[g];
     hef_status r = run_item(items[g], k, S, dtype, clique_mode, zs[g], base + off[g], pool->s[si]);
     if (r && !first) first = r;
   }
+  krylov_allow_persistent(true);
   // join every stream that took part, also after an error (a capture must
   // end with all forked streams joined)
   for (int i = 0; i < ns; ++i) {

@@ -649,6 +649,8 @@ extern "C" hef_status hef_incidence_check(const hef_incidence* inc, void* stream
   HEF_CHECK_CUDA(cudaStreamSynchronize(st));
   if (detail) *detail = st_host[0];
   if (where) *where = st_host[0] ? (int64_t)st_host[1] : -1;
+  if (st_host[0] & HEF_WAIT_TIMEOUT)
+    return set_error(HEF_ERR_TIMEOUT, "a bounded grid-wide wait of the Krylov launch expired");
   if (st_host[0])
     return set_error(HEF_ERR_INVALID_INPUT,
                      "hypergraph rejected by device validation (bits 0x%x, hyperedge %u)",

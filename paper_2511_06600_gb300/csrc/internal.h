@@ -148,6 +148,13 @@ inline size_t carve_tape(void* base, long long n, long long m, int k, int S, siz
   return c.bytes();
 }
 
+// Whether hef_krylov_basis(_tape) calls from this thread may run all Krylov
+// steps as one persistent launch (default on).  The persistent grid needs
+// every CTA resident at once, so callers that overlap other work on the GPU
+// turn it off.
+void krylov_allow_persistent(bool on);
+void krylov_force_oversized(bool on);
+
 // Tensor-core (tcgen05, 3xTF32) Gram matrix of an FP32 basis with K + 1 <= 256
 // (ortho_tc.cu): G = V^T V (K x K), c = V^T 1; part is per-CTA scratch.
 int gram_tc_supported(int K);

@@ -24,6 +24,8 @@
 // also archives x_{j-1} into V and reduces the Lanczos dots, and an update
 // pass (thread per row) forming x_j and its D-norm.  Every reduction is a
 // per-CTA partial followed by a two-level fixed-order sum (grid_reduce).
+#include <algorithm>
+
 #include "internal.h"
 
 namespace hef {
@@ -59,6 +61,7 @@ struct KView {
   T* tape_c;       // nullable: u_j of the clique chains, (k+1) x n x S
   T* tape_b;       // nullable: u_j of the star chains, (k+1) x (n+m) x S
   double tol;      // breakdown threshold on the D-norm of a new vector
+  unsigned int* gen;  // barrier generation of the persistent launch
 };
 
 // ---------------------------------------------------------------- row I/O
@@ -379,12 +382,20 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T>
 }
 
 // ---------------------------------------------------------------- one Krylov step
+//
+// Each pass is a per-item device function (one hyperedge, vertex or group of
+// rows per thread, adding to the caller's partial dots) plus a final step
+// run by the CTA that completes the grid-wide reduction.  The kernels
+// k_edge_pass, k_node_pass and k_update run one item per thread;
+// k_krylov_steps runs all k steps in one persistent launch over the same
+// functions (grid-stride loops, bounded grid barriers).
 
-// Edge pass of step j (thread per hyperedge): clique pin sums s_e, star rows
-// (M_b x)_e, and the D-weighted dots of the star hyperedge rows -> te.
+// Edge pass item (hyperedge e; past the end it still takes part in its
+// warp's collective sums): clique pin sums s_e, star rows (M_b x)_e, and the
+// D-weighted dots of the star hyperedge rows, added to acc.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5)) k_edge_pass(IncView g, ScalView<T> sv, KView<T> kv, int j) {
-  if (g.status[0]) return;
+__device__ __forceinline__ void edge_item(const IncView& g, const ScalView<T>& sv,
+                                          const KView<T>& kv, int j, int e, T (&acc)[3][S]) {
   const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
   const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
   const T* __restrict__ prvb = j >= 3 ? pick2(kv.Bb, j & 1) : nullptr;
@@ -395,7 +406,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5)) k_edge_pass(Inc
     ncb[s] = kv.nuT[(size_t)(j - 1) * 2 * S + S + s];
     npb[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + S + s] : (T)0;
   }
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = e < g.m;
   int a = 0, b = 0;
   if (valid) a = g.ceptr[e], b = g.ceptr[e + 1];
@@ -405,11 +415,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5)) k_edge_pass(Inc
                  [&](int p) { return curc + (long long)p * S; },
                  [&](int p) { return curb + (long long)p * S; }, [&](int) { return (T)1; },
                  [&](int) { return (T)1; }, sc, sb);
-  T acc[3][S];
-#pragma unroll
-  for (int q = 0; q < 3; ++q)
-#pragma unroll
-    for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (valid) {
     const int k = b - a;
     const T invk = k >= 2 ? (T)1 / (T)k : (T)0;
@@ -430,26 +435,25 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5)) k_edge_pass(Inc
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         const T wy = we * ye[s];
-        acc[0][s] = wy;
-        acc[1][s] = wy * xc[s] * ncb[s];
-        acc[2][s] = prvb ? wy * xp[s] * npb[s] : (T)0;
+        acc[0][s] += wy;
+        acc[1][s] += wy * xc[s] * ncb[s];
+        acc[2][s] += prvb ? wy * xp[s] * npb[s] : (T)0;
       }
     }
   }
-  block_partials_qs<3, S, T>(acc, kv.red.part);
-  __shared__ double tot[3 * kMaxS];
-  if (grid_reduce(kv.red, 3 * S, tot)) {
-    for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) kv.te[t] = tot[t];
-  }
 }
 
-// Vertex pass of step j (thread per vertex): (M_c x)_v and (M_b x)_v, archive
-// of x_{j-1} into V, and the Lanczos coefficients of step j (final CTA, with
-// the star hyperedge-row dots of the edge pass).
+template <typename T>
+__device__ __forceinline__ void edge_final(const KView<T>& kv, int S, const double* tot) {
+  for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) kv.te[t] = tot[t];
+}
+
+// Vertex pass item (vertex v): (M_c x)_v and (M_b x)_v, archive of x_{j-1}
+// into V, and the dots of the Lanczos coefficients, added to acc.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_node_pass(IncView g, ScalView<T> sv, KView<T> kv, int j,
-                                                        T* __restrict__ V, long long ldv) {
-  if (g.status[0]) return;
+__device__ __forceinline__ void node_item(const IncView& g, const ScalView<T>& sv,
+                                          const KView<T>& kv, int j, int v, T (&acc)[6][S],
+                                          T* __restrict__ V, long long ldv) {
   const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
   const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
   const T* __restrict__ prvc = j >= 3 ? pick2(kv.Bc, j & 1) : nullptr;
@@ -462,7 +466,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_node_pass(Inc
     npc[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + s] : (T)0;
     npb[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + S + s] : (T)0;
   }
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = v < g.n;
   int a = 0, b = 0;
   if (valid) a = g.vptr[v], b = g.vptr[v + 1];
@@ -488,11 +491,6 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_node_pass(Inc
                  [&](int e) { return curb + (long long)(g.n + e) * S; },
                  [&](int e) { return __ldg(ewh + e); }, [&](int e) { return __ldg(ez + e); }, accc,
                  accb);
-  T acc[6][S];
-#pragma unroll
-  for (int q = 0; q < 6; ++q)
-#pragma unroll
-    for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (valid) {
     T yc[S], yb[S];
 #pragma unroll
@@ -503,12 +501,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_node_pass(Inc
       yb[s] = idb * accb[s] * ncb[s];
       const T pc = prvc ? xpc[s] * npc[s] : (T)0;
       const T pb = prvb ? xpb[s] * npb[s] : (T)0;
-      acc[0][s] = dcv * yc[s];
-      acc[1][s] = dcv * yc[s] * xv[s];
-      acc[2][s] = dcv * yc[s] * pc;
-      acc[3][s] = dbv * yb[s];
-      acc[4][s] = dbv * yb[s] * xb[s];
-      acc[5][s] = dbv * yb[s] * pb;
+      acc[0][s] += dcv * yc[s];
+      acc[1][s] += dcv * yc[s] * xv[s];
+      acc[2][s] += dcv * yc[s] * pc;
+      acc[3][s] += dbv * yb[s];
+      acc[4][s] += dbv * yb[s] * xb[s];
+      acc[5][s] += dbv * yb[s] * pb;
     }
     strow<T, S>(kv.Yc + (long long)v * S, yc);
     strow<T, S>(kv.Yb + (long long)v * S, yb);
@@ -518,39 +516,43 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_node_pass(Inc
       strow<T, S>(row + S, xb);
     }
   }
-  block_partials_qs<6, S, T>(acc, kv.red.part);
-  __shared__ double tn[6 * kMaxS];
-  if (grid_reduce(kv.red, 6 * S, tn)) {
-    for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
-      const int op = c / S, s = c % S;
-      double* cf = kv.coef + ((size_t)j * 2 * S + c) * 4;
-      if (op == 0) {
-        cf[0] = g.totals[0] > 0 ? tn[0 * S + s] / g.totals[0] : 0.0;
-        cf[1] = 0.0;
-        cf[2] = j >= 2 ? tn[1 * S + s] : 0.0;
-        cf[3] = j >= 3 ? tn[2 * S + s] : 0.0;
-      } else {
-        cf[0] = g.totals[1] > 0 ? tn[3 * S + s] / g.totals[1] : 0.0;
-        cf[1] = g.totals[2] > 0 ? kv.te[0 * S + s] / g.totals[2] : 0.0;
-        cf[2] = j >= 2 ? tn[4 * S + s] + kv.te[1 * S + s] : 0.0;
-        cf[3] = j >= 3 ? tn[5 * S + s] + kv.te[2 * S + s] : 0.0;
-      }
-      // working-type copies with the inverse norms folded in
-      T* ct = kv.cfT + ((size_t)j * 2 * S + c) * 4;
-      ct[0] = (T)cf[0];
-      ct[1] = (T)cf[1];
-      ct[2] = (T)(cf[2] * kv.inv_nu[(size_t)(j - 1) * 2 * S + c]);
-      ct[3] = j >= 3 ? (T)(cf[3] * kv.inv_nu[(size_t)(j - 2) * 2 * S + c]) : (T)0;
+}
+
+// Lanczos coefficients of step j from the vertex dots tn (6S) and the star
+// hyperedge-row dots te (3S).
+template <typename T>
+__device__ __forceinline__ void node_final(const IncView& g, const KView<T>& kv, int S, int j,
+                                           const double* tn) {
+  for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
+    const int op = c / S, s = c % S;
+    double* cf = kv.coef + ((size_t)j * 2 * S + c) * 4;
+    if (op == 0) {
+      cf[0] = g.totals[0] > 0 ? tn[0 * S + s] / g.totals[0] : 0.0;
+      cf[1] = 0.0;
+      cf[2] = j >= 2 ? tn[1 * S + s] : 0.0;
+      cf[3] = j >= 3 ? tn[2 * S + s] : 0.0;
+    } else {
+      cf[0] = g.totals[1] > 0 ? tn[3 * S + s] / g.totals[1] : 0.0;
+      cf[1] = g.totals[2] > 0 ? kv.te[0 * S + s] / g.totals[2] : 0.0;
+      cf[2] = j >= 2 ? tn[4 * S + s] + kv.te[1 * S + s] : 0.0;
+      cf[3] = j >= 3 ? tn[5 * S + s] + kv.te[2 * S + s] : 0.0;
     }
+    // working-type copies with the inverse norms folded in
+    T* ct = kv.cfT + ((size_t)j * 2 * S + c) * 4;
+    ct[0] = (T)cf[0];
+    ct[1] = (T)cf[1];
+    ct[2] = (T)(cf[2] * kv.inv_nu[(size_t)(j - 1) * 2 * S + c]);
+    ct[3] = j >= 3 ? (T)(cf[3] * kv.inv_nu[(size_t)(j - 2) * 2 * S + c]) : (T)0;
   }
 }
 
-// Update pass of step j (kUpdRows rows per thread): u_j = y - trivial part
-// - alpha x_{j-1} - beta x_{j-2} (written over x_{j-2}'s buffer) and its
-// D-norm -> inv_nu[j].  Rows: [0, n) clique, [n, 2n + m) star.
+// Update pass item (rows r0 + it * blockDim.x, it < kUpdRows): u_j = y -
+// trivial part - alpha x_{j-1} - beta x_{j-2} (written over x_{j-2}'s
+// buffer) and its D-norm, added to acc.  Rows: [0, n) clique, [n, 2n + m) star.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_update(IncView g, ScalView<T> sv, KView<T> kv, int j) {
-  if (g.status[0]) return;
+__device__ __forceinline__ void update_item(const IncView& g, const ScalView<T>& sv,
+                                            const KView<T>& kv, int j, long long r0,
+                                            T (&acc)[2][S]) {
   const bool has_prv = j >= 3;
   // coefficients of both expansions in registers: [op][s][ct, ct2, a, b]
   T cf[2][S][4];
@@ -560,13 +562,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_update(IncVie
     for (int s = 0; s < S; ++s)
 #pragma unroll
       for (int q = 0; q < 4; ++q) cf[op][s][q] = kv.cfT[((size_t)j * 2 * S + op * S + s) * 4 + q];
-  T acc[2][S];
-#pragma unroll
-  for (int q = 0; q < 2; ++q)
-#pragma unroll
-    for (int s = 0; s < S; ++s) acc[q][s] = 0;
   const long long nrows = 2ll * g.n + g.m;
-  const long long r0 = (long long)blockIdx.x * blockDim.x * kUpdRows + threadIdx.x;
 #pragma unroll
   for (int it = 0; it < kUpdRows; ++it) {
     const long long r = r0 + (long long)it * blockDim.x;
@@ -603,25 +599,24 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4)) k_update(IncVie
       else acc[1][s] += dsq[s];
     }
   }
-  block_partials_qs<2, S, T>(acc, kv.red.part);
-  __shared__ double tot[2 * kMaxS];
-  if (grid_reduce(kv.red, 2 * S, tot)) {
-    const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
-    for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
-      const double nu2 = tot[c];
-      const bool alive = nu0[c] > 0.0 && nu2 > kv.tol * kv.tol;
-      kv.inv_nu[(size_t)j * 2 * S + c] = alive ? 1.0 / sqrt(nu2) : 0.0;
-      kv.nuT[(size_t)j * 2 * S + c] = (T)kv.inv_nu[(size_t)j * 2 * S + c];
-    }
+}
+
+// Inverse D-norms of step j from the squared norms tot (2S).
+template <typename T>
+__device__ __forceinline__ void update_final(const KView<T>& kv, int S, int j, const double* tot) {
+  const double* nu0 = kv.inv_nu + (size_t)(j - 1) * 2 * S;
+  for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
+    const double nu2 = tot[c];
+    const bool alive = nu0[c] > 0.0 && nu2 > kv.tol * kv.tol;
+    kv.inv_nu[(size_t)j * 2 * S + c] = alive ? 1.0 / sqrt(nu2) : 0.0;
+    kv.nuT[(size_t)j * 2 * S + c] = (T)kv.inv_nu[(size_t)j * 2 * S + c];
   }
 }
 
-// Archive of the last chain vectors x_k into V (thread per vertex).
+// Archive of the last chain vector x_k of vertex v into V.
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_archive_last(IncView g, KView<T> kv, int k,
-                                                           T* __restrict__ V, long long ldv) {
-  if (g.status[0]) return;
-  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void archive_item(const IncView& g, const KView<T>& kv, int k, int v,
+                                             T* __restrict__ V, long long ldv) {
   if (v >= g.n) return;
   T xc[S], xb[S];
   ldrow<T, S>(pick2(kv.Bc, k & 1) + (long long)v * S, xc);
@@ -634,6 +629,147 @@ __global__ void __launch_bounds__(kThreads) k_archive_last(IncView g, KView<T> k
   T* row = V + (long long)v * ldv + (long long)(k - 1) * 2 * S;
   strow<T, S>(row, xc);
   strow<T, S>(row + S, xb);
+}
+
+template <int NQ, int S, typename T>
+__device__ __forceinline__ void zero_acc(T (&acc)[NQ][S]) {
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int s = 0; s < S; ++s) acc[q][s] = 0;
+}
+
+// Edge pass of step j (thread per hyperedge).
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5))
+    k_edge_pass(IncView g, ScalView<T> sv, KView<T> kv, int j) {
+  if (g.status[0]) return;
+  T acc[3][S];
+  zero_acc(acc);
+  edge_item<T, S>(g, sv, kv, j, blockIdx.x * blockDim.x + threadIdx.x, acc);
+  block_partials_qs<3, S, T>(acc, kv.red.part);
+  __shared__ double tot[3 * kMaxS];
+  if (grid_reduce(kv.red, 3 * S, tot)) edge_final(kv, S, tot);
+}
+
+// Vertex pass of step j (thread per vertex); the final CTA forms the
+// Lanczos coefficients.
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
+    k_node_pass(IncView g, ScalView<T> sv, KView<T> kv, int j, T* __restrict__ V, long long ldv) {
+  if (g.status[0]) return;
+  T acc[6][S];
+  zero_acc(acc);
+  node_item<T, S>(g, sv, kv, j, blockIdx.x * blockDim.x + threadIdx.x, acc, V, ldv);
+  block_partials_qs<6, S, T>(acc, kv.red.part);
+  __shared__ double tn[6 * kMaxS];
+  if (grid_reduce(kv.red, 6 * S, tn)) node_final(g, kv, S, j, tn);
+}
+
+// Update pass of step j (kUpdRows rows per thread); the final CTA forms the
+// inverse norms.
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
+    k_update(IncView g, ScalView<T> sv, KView<T> kv, int j) {
+  if (g.status[0]) return;
+  T acc[2][S];
+  zero_acc(acc);
+  update_item<T, S>(g, sv, kv, j, (long long)blockIdx.x * blockDim.x * kUpdRows + threadIdx.x, acc);
+  block_partials_qs<2, S, T>(acc, kv.red.part);
+  __shared__ double tot[2 * kMaxS];
+  if (grid_reduce(kv.red, 2 * S, tot)) update_final(kv, S, j, tot);
+}
+
+// Archive of the last chain vectors x_k into V (thread per vertex).
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads) k_archive_last(IncView g, KView<T> kv, int k,
+                                                           T* __restrict__ V, long long ldv) {
+  if (g.status[0]) return;
+  archive_item<T, S>(g, kv, k, blockIdx.x * blockDim.x + threadIdx.x, V, ldv);
+}
+
+// ---------------------------------------------------------------- persistent form
+
+constexpr unsigned int kBarIters = 1u << 20;  // bounded barrier wait (about 0.25 s)
+
+// Grid barrier with the pass's reduction: per-CTA partials, the two-level
+// reduction of grid_reduce, the final step fin(tot) in the CTA that completes
+// it, then a generation counter releases the others.  A wait that runs out
+// sets HEF_WAIT_TIMEOUT in the status word; every later pass then stops.
+template <int NQ, int S, typename T, typename Fin>
+__device__ __forceinline__ void reduce_barrier(const KView<T>& kv, const T (&acc)[NQ][S],
+                                               unsigned int* gen, unsigned int* status, Fin fin) {
+  __shared__ unsigned int g0;
+  __shared__ double tot[6 * kMaxS];
+  if (threadIdx.x == 0) g0 = *reinterpret_cast<volatile unsigned int*>(gen);
+  // (block_partials_qs begins and grid_reduce ends with a CTA barrier)
+  block_partials_qs<NQ, S, T>(acc, kv.red.part);
+  if (grid_reduce(kv.red, NQ * S, tot)) {
+    fin(tot);
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) atomicAdd(gen, 1u);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    unsigned int it = 0;
+    while (*reinterpret_cast<volatile unsigned int*>(gen) == g0) {
+      if (++it > kBarIters) {
+        atomicOr(status, HEF_WAIT_TIMEOUT);
+        break;
+      }
+      __nanosleep(64);
+    }
+    __threadfence();
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ bool stopped(const unsigned int* status) {
+  return *reinterpret_cast<const volatile unsigned int*>(status) != 0u;
+}
+
+// All k steps in one launch.  Every CTA must be resident at once (the grid is
+// sized from the occupancy of this kernel); passes walk their items in
+// grid-stride tiles of blockDim.x.
+template <typename T, int S>
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(3))
+    k_krylov_steps(IncView g, ScalView<T> sv, KView<T> kv, int k, T* __restrict__ V,
+                   long long ldv, unsigned int* gen, unsigned int* status) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long base = (long long)blockIdx.x * blockDim.x;
+  const long long nrows = 2ll * g.n + g.m;
+  for (int j = 1; j <= k; ++j) {
+    if (stopped(status)) return;
+    {
+      T acc[3][S];
+      zero_acc(acc);
+      for (long long e0 = base; e0 < g.m; e0 += stride)
+        edge_item<T, S>(g, sv, kv, j, (int)(e0 + threadIdx.x), acc);
+      reduce_barrier<3, S>(kv, acc, gen, status, [&](const double* tot) { edge_final(kv, S, tot); });
+    }
+    if (stopped(status)) return;
+    {
+      T acc[6][S];
+      zero_acc(acc);
+      for (long long v0 = base; v0 < g.n; v0 += stride)
+        node_item<T, S>(g, sv, kv, j, (int)(v0 + threadIdx.x), acc, V, ldv);
+      reduce_barrier<6, S>(kv, acc, gen, status,
+                           [&](const double* tn) { node_final(g, kv, S, j, tn); });
+    }
+    if (stopped(status)) return;
+    {
+      T acc[2][S];
+      zero_acc(acc);
+      for (long long r0 = base * kUpdRows; r0 < nrows; r0 += stride * kUpdRows)
+        update_item<T, S>(g, sv, kv, j, r0 + threadIdx.x, acc);
+      reduce_barrier<2, S>(kv, acc, gen, status,
+                           [&](const double* tot) { update_final(kv, S, j, tot); });
+    }
+  }
+  if (stopped(status)) return;
+  for (long long v0 = base; v0 < g.n; v0 += stride)
+    archive_item<T, S>(g, kv, k, (int)(v0 + threadIdx.x), V, ldv);
 }
 
 inline int blocks_for(long long rows) { return (int)((rows + kThreads - 1) / kThreads); }
@@ -660,12 +796,20 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->red.gpart = c.take<double>((size_t)red_groups((int)maxblk) * 6 * S);
   kv->red.gcnt = c.take<unsigned int>(red_groups((int)maxblk) + 1);
   kv->red.tcnt = c.take<unsigned int>(1);
+  kv->gen = c.take<unsigned int>(1);
   return c.bytes();
 }
 
+// Whether the one-launch form may be used by calls from this thread (the
+// batched form, whose hypergraphs share the GPU, turns it off).
+thread_local bool t_persistent = true;
+// Test of the timeout path: launch the persistent form with twice the
+// resident grid, so that its first barrier cannot complete.
+thread_local bool t_force_oversized = false;
+
 template <typename T, int S>
 hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, const double* x0b,
-                        T* V, long long ldv, KView<T>& kv, cudaStream_t st) {
+                        T* V, long long ldv, KView<T>& kv, bool persistent, cudaStream_t st) {
   IncView g = view(inc);
   const ScalView<T> sv = scal_view<T>(inc);
   const long long n = inc->n, m = inc->m;
@@ -676,6 +820,19 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
   HEF_LAUNCH("k_start_write", st, k_start_write<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
   HEF_CHECK_LAUNCH();
+  // one launch for all steps when every row of a pass has a resident thread
+  // of its own (small hypergraphs, where per-step launches cost more than the
+  // work); larger ones run faster as three launches per step, whose CTAs each
+  // take one item per thread
+  const int res = persistent ? num_sms() * resident_ctas(k_krylov_steps<T, S>, kThreads) : 0;
+  if (persistent && (t_force_oversized || (long long)res * kThreads >= 2 * n + m)) {
+    int grid = std::max(1, std::min(res, grid_all));
+    if (t_force_oversized) grid = std::min(2 * res, grid_all);
+    HEF_LAUNCH("k_krylov_steps", st, k_krylov_steps<T, S><<<grid, kThreads, 0, st>>>(
+                                         g, sv, kv, k, V, ldv, kv.gen, inc->status));
+    HEF_CHECK_LAUNCH();
+    return HEF_OK;
+  }
   for (int j = 1; j <= k; ++j) {
     HEF_LAUNCH("k_edge_pass", st, k_edge_pass<T, S><<<grid_e, kThreads, 0, st>>>(g, sv, kv, j));
     HEF_LAUNCH("k_node_pass", st, k_node_pass<T, S><<<grid_n, kThreads, 0, st>>>(g, sv, kv, j, V, ldv));
@@ -703,11 +860,11 @@ hef_status run_krylov(const hef_incidence* inc, int k, int S, const double* x0c,
   T* V = static_cast<T*>(Vv);
   hef_status s;
   switch (S) {
-    case 1: s = run_krylov_s<T, 1>(inc, k, x0c, x0b, V, ldv, kv, st); break;
-    case 2: s = run_krylov_s<T, 2>(inc, k, x0c, x0b, V, ldv, kv, st); break;
-    case 4: s = run_krylov_s<T, 4>(inc, k, x0c, x0b, V, ldv, kv, st); break;
-    case 8: s = run_krylov_s<T, 8>(inc, k, x0c, x0b, V, ldv, kv, st); break;
-    case 16: s = run_krylov_s<T, 16>(inc, k, x0c, x0b, V, ldv, kv, st); break;
+    case 1: s = run_krylov_s<T, 1>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 2: s = run_krylov_s<T, 2>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 4: s = run_krylov_s<T, 4>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 8: s = run_krylov_s<T, 8>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 16: s = run_krylov_s<T, 16>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
     default: return set_error(HEF_ERR_UNSUPPORTED, "hef_krylov_basis: S must be 1, 2, 4, 8 or 16");
   }
   if (s || !tape) return s;
@@ -730,6 +887,9 @@ hef_status check_krylov_args(const hef_incidence* inc, int k, int S, int dtype, 
 }
 
 }  // namespace
+
+void krylov_allow_persistent(bool on) { t_persistent = on; }
+void krylov_force_oversized(bool on) { t_force_oversized = on; }
 
 }  // namespace hef
 
@@ -766,6 +926,13 @@ extern "C" hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int3
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (dtype == HEF_F64) return run_krylov<double>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st);
   return run_krylov<float>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st);
+}
+
+extern "C" hef_status hef_set_krylov_persistent(int32_t on) {
+  if (on < 0 || on > 2) return set_error(HEF_ERR_INVALID_ARG, "hef_set_krylov_persistent: on must be 0, 1 or 2");
+  krylov_allow_persistent(on != 0);
+  krylov_force_oversized(on == 2);
+  return HEF_OK;
 }
 
 extern "C" size_t hef_krylov_tape_bytes(const hef_incidence* inc, int32_t k, int32_t S, int32_t dtype) {
