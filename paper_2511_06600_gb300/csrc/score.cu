@@ -140,7 +140,7 @@ __device__ __forceinline__ void cta_edge_extrema(const T* __restrict__ Q, long l
 // sum of w_e spread^2 per column goes to bpart[b][col] (FP64).
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restrict__ Q, long long ldq,
-                                                    int K, double* bpart) {
+                                                    int K, double* bpart, T* spread) {
   if (g.status[0]) return;
   __shared__ T smx[8 * 32 * NC], smn[8 * 32 * NC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -157,6 +157,8 @@ __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restri
     for (int c = 0; c < NC; ++c) {
       const double sp = (double)(mx[c] - mn[c]);
       acc[c] += we * sp * sp;
+      if (spread && wid == 0 && lane + 32 * c < K)
+        spread[(long long)e * K + lane + 32 * c] = mx[c] - mn[c];
     }
   }
   if (wid == 0) {
@@ -173,7 +175,8 @@ template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restrict__ Q, long long ldq,
                                                      int K, GridRed red, const double* __restrict__ bpart,
                                                      int nbpart, double* QH, double* invQH,
-                                                     double* QH_out, unsigned int* work) {
+                                                     double* QH_out, unsigned int* work,
+                                                     T* spread) {
   if (g.status[0]) return;
   __shared__ double wred[kThreads / 32][32 * NC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -200,15 +203,19 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
       if (a0 == b0 && a1 == b1) continue;
       T mx0[NC], mn0[NC], mx1[NC], mn1[NC];
       two_edge_extrema<T, NC>(Q, ldq, K, g.cpins, a0, b0, a1, b1, lane, mx0, mn0, mx1, mn1);
+      const long long e0 = grp * kGroup1 + i;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
+        const int col = lane + 32 * c;
         if (b0 > a0) {
           const T sp = mx0[c] - mn0[c];
           pacc[c] += w0 * sp * sp;
+          if (spread && col < K) spread[e0 * K + col] = sp;
         }
         if (b1 > a1) {
           const T sp = mx1[c] - mn1[c];
           pacc[c] += w1 * sp * sp;
+          if (spread && col < K) spread[(e0 + 1) * K + col] = sp;
         }
       }
     }
@@ -388,6 +395,99 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
   }
 }
 
+// Pass 2 from the spreads that pass 1 stored (spread[e][i], K per row; every
+// hyperedge with >= 2 pins has its row): warp per hyperedge, lanes over
+// columns.  Ratios and the arg-max column in the working type as in Eq.
+// ratios; R_e from the spread in FP64; the routing pins by one gather of the
+// arg-max column over the hyperedge's pins (lowest position on ties).  Gives
+// exactly what k_score_pass2 / k_score_big2 give, without gathering every
+// column of Q again.
+template <typename T, int NC>
+__global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restrict__ Q, long long ldq,
+                                                     int K, int reduce, const double* __restrict__ QH,
+                                                     const double* __restrict__ invQH,
+                                                     const T* __restrict__ spread, double* R_out,
+                                                     int32_t* argvec, int32_t* pmax, int32_t* pmin) {
+  if (g.status[0]) return;
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  T iq[NC];
+  bool use[NC];
+  load_use<T, NC>(QH, invQH, K, iq, use);
+  for (long long e = warp; e < g.m; e += nwarps) {
+    const int a = g.ceptr[e], b = g.ceptr[e + 1];
+    const int oe = g.perm[e];
+    if (b - a < 2) {  // degenerate: no score, no routing
+      if (lane == 0) {
+        R_out[oe] = 0.0;
+        if (argvec) argvec[oe] = -1;
+        if (pmax) pmax[oe] = -1;
+        if (pmin) pmin[oe] = -1;
+      }
+      continue;
+    }
+    T best = (T)-1, spb = 0;
+    int bcol = 0x7fffffff;
+    double sum = 0.0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (use[c]) {
+        const T sp = spread[e * K + lane + 32 * c];
+        const T r = sp * sp * iq[c];
+        if (reduce == HEF_REDUCE_SUM) {
+          const double spd = (double)sp;
+          sum += spd * spd / QH[lane + 32 * c];
+        }
+        if (r > best) best = r, bcol = lane + 32 * c, spb = sp;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bcol, o);
+      const T os = __shfl_xor_sync(0xffffffffu, spb, o);
+      if (ob > best || (ob == best && oc < bcol)) best = ob, bcol = oc, spb = os;
+    }
+    if (reduce == HEF_REDUCE_SUM) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    }
+    const bool any = bcol != 0x7fffffff;
+    int tmax = 0x7fffffff, tmin = 0x7fffffff;
+    if (any && (pmax || pmin)) {
+      // extrema of column bcol over the pins, lowest position on ties
+      T vmax = lowest<T>(), vmin = -lowest<T>();
+      for (int t = a + lane; t < b; t += 32) {
+        const T v = Q[(long long)g.cpins[t] * ldq + bcol];
+        if (v > vmax) vmax = v, tmax = t;
+        if (v < vmin) vmin = v, tmin = t;
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ov = __shfl_xor_sync(0xffffffffu, vmax, o);
+        const int ot = __shfl_xor_sync(0xffffffffu, tmax, o);
+        if (ov > vmax || (ov == vmax && ot < tmax)) vmax = ov, tmax = ot;
+        const T pv = __shfl_xor_sync(0xffffffffu, vmin, o);
+        const int pt = __shfl_xor_sync(0xffffffffu, tmin, o);
+        if (pv < vmin || (pv == vmin && pt < tmin)) vmin = pv, tmin = pt;
+      }
+    }
+    if (lane == 0) {
+      double Re = 0.0;
+      if (reduce == HEF_REDUCE_SUM) Re = sum;
+      else if (any) {
+        const double spw = (double)spb;
+        Re = spw * spw / QH[bcol];
+      }
+      R_out[oe] = Re;
+      if (argvec) argvec[oe] = any ? bcol : -1;
+      if (pmax) pmax[oe] = any ? g.cpins[tmax] : -1;
+      if (pmin) pmin[oe] = any ? g.cpins[tmin] : -1;
+    }
+  }
+}
+
 struct ScoreWs {
   double* part;
   double* QH;
@@ -395,11 +495,14 @@ struct ScoreWs {
   unsigned int* counter;  // reduction counters (zero between calls)
   double* gpart;
   double* bpart;          // large hyperedges: per-CTA partial Q_H sums
+  void* spread;           // m x K spreads of pass 1 (NULL: pass 2 gathers Q again)
   int grid;
   int bgrid;
 };
 
-size_t carve_score(void* base, int K, ScoreWs* w) {
+// Workspace of hef_edge_resistance; the spreads take 8-byte slots whatever
+// the dtype (the size query does not know it).
+size_t carve_score(void* base, int K, long long m, ScoreWs* w) {
   Carver c(base);
   w->grid = num_sms() * 4;
   w->part = c.take<double>((size_t)w->grid * K);
@@ -409,6 +512,7 @@ size_t carve_score(void* base, int K, ScoreWs* w) {
   w->gpart = c.take<double>((size_t)red_groups(w->grid) * K);
   w->bgrid = num_sms();
   w->bpart = c.take<double>((size_t)w->bgrid * K);
+  w->spread = c.take<double>((size_t)(m > 0 ? m : 1) * K);
   return c.bytes();
 }
 
@@ -425,10 +529,20 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
   // grids of co-resident CTAs only (work is handed out dynamically)
   const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
   const int g2 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass2<T, NC>, kThreads));
-  HEF_LAUNCH("k_score_big1", st, k_score_big1<T, NC><<<w.bgrid, kThreads, 0, st>>>(g, Q, ldq, K, w.bpart));
+  T* spread = static_cast<T*>(w.spread);
+  HEF_LAUNCH("k_score_big1", st, k_score_big1<T, NC><<<w.bgrid, kThreads, 0, st>>>(g, Q, ldq, K, w.bpart,
+                                                                                   spread));
   HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<g1, kThreads, 0, st>>>(
                                       g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out,
-                                      w.counter + kWorkSlot));
+                                      w.counter + kWorkSlot, spread));
+  if (spread) {
+    const int g3 = num_sms() * resident_ctas(k_score_ratio<T, NC>, kThreads);
+    HEF_LAUNCH("k_score_ratio", st, k_score_ratio<T, NC><<<g3, kThreads, 0, st>>>(
+                                        g, Q, ldq, K, reduce, w.QH, w.invQH, spread, R_out, argvec,
+                                        pmax, pmin));
+    HEF_CHECK_LAUNCH();
+    return HEF_OK;
+  }
   HEF_LAUNCH("k_score_big2", st, k_score_big2<T, NC><<<w.bgrid, kThreads, 0, st>>>(
                                      g, Q, ldq, K, reduce, w.QH, w.invQH, R_out, argvec, pmax, pmin));
   HEF_LAUNCH("k_score_pass2", st, k_score_pass2<T, NC><<<g2, kThreads, 0, st>>>(
@@ -508,6 +622,7 @@ size_t carve_score_capped(void* base, int K, size_t cap, ScoreWs* w) {
   w->gpart = c.take<double>((size_t)red_groups(w->grid) * K);
   w->bgrid = num_sms();
   w->bpart = c.take<double>((size_t)w->bgrid * K);
+  w->spread = nullptr;  // no room: pass 2 gathers Q again
   return c.bytes();
 }
 
@@ -554,7 +669,7 @@ extern "C" hef_status hef_edge_resistance_noalloc(const hef_incidence* inc, cons
 extern "C" size_t hef_edge_resistance_workspace_bytes(const hef_incidence* inc, int32_t K) {
   if (!inc || K < 1 || K > 512) return 0;
   ScoreWs w;
-  return carve_score(nullptr, K, &w);
+  return carve_score(nullptr, K, inc->m, &w);
 }
 
 extern "C" hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q, int64_t ldq,
@@ -571,7 +686,7 @@ extern "C" hef_status hef_edge_resistance(const hef_incidence* inc, const void* 
   if (!Q || ldq < K || (inc->m > 0 && !R_out))
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance: Q or R_out NULL, or ldq < K");
   ScoreWs w;
-  const size_t need = carve_score(workspace, K, &w);
+  const size_t need = carve_score(workspace, K, inc->m, &w);
   if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
     return set_error(HEF_ERR_WORKSPACE, "hef_edge_resistance: workspace needs %zu bytes (256-aligned)", need);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
