@@ -35,6 +35,12 @@ namespace {
 constexpr int kMaxS = 16;
 constexpr int kBig = 16;     // segments longer than this are summed by a warp
 constexpr int kUpdRows = 4;  // rows per thread in the update pass
+// entries gathered per round by one thread in the segment sums (wider rows
+// keep two, for registers)
+template <typename T, int S>
+__host__ __device__ constexpr int seg_round() {
+  return S * sizeof(T) <= 16 ? 4 : 2;
+}
 
 // Minimum resident CTAs per SM asked of the compiler for the step kernels:
 // the FP32 form with S <= 4 fits one wave of the 200k-row workloads in its
@@ -218,33 +224,30 @@ template <typename T, int S, typename Idx, typename RowA, typename RowB, typenam
 __device__ __forceinline__ void seg_sum2(bool valid, int a, int b, Idx idx, RowA rowA, RowB rowB,
                                          WA wA, WB wB, T (&accA)[S], T (&accB)[S]) {
   const int lane = threadIdx.x & 31;
+  constexpr int kSeg = seg_round<T, S>();
 #pragma unroll
   for (int s = 0; s < S; ++s) accA[s] = 0, accB[s] = 0;
   const bool big = valid && (b - a) > kBig;
   if (valid && !big) {
-    int t = a;
-    for (; t + 2 <= b; t += 2) {
-      const int i0 = idx(t), i1 = idx(t + 1);
-      T a0[S], a1[S], b0[S], b1[S];
-      ldrow<T, S>(rowA(i0), a0);
-      ldrow<T, S>(rowA(i1), a1);
-      ldrow<T, S>(rowB(i0), b0);
-      ldrow<T, S>(rowB(i1), b1);
-      const T wa0 = wA(i0), wa1 = wA(i1), wb0 = wB(i0), wb1 = wB(i1);
+    // kSeg entries per round, all index loads then all row loads in flight
+    // (indices past the end repeat the last entry and are weighted out)
+    for (int t = a; t < b; t += kSeg) {
+      int ii[kSeg];
 #pragma unroll
-      for (int s = 0; s < S; ++s) {
-        accA[s] += wa0 * a0[s] + wa1 * a1[s];
-        accB[s] += wb0 * b0[s] + wb1 * b1[s];
+      for (int q = 0; q < kSeg; ++q) ii[q] = idx(min(t + q, b - 1));
+      T ra[kSeg][S], rb[kSeg][S];
+#pragma unroll
+      for (int q = 0; q < kSeg; ++q) {
+        ldrow<T, S>(rowA(ii[q]), ra[q]);
+        ldrow<T, S>(rowB(ii[q]), rb[q]);
       }
-    }
-    if (t < b) {
-      const int i0 = idx(t);
-      T a0[S], b0[S];
-      ldrow<T, S>(rowA(i0), a0);
-      ldrow<T, S>(rowB(i0), b0);
-      const T wa0 = wA(i0), wb0 = wB(i0);
 #pragma unroll
-      for (int s = 0; s < S; ++s) accA[s] += wa0 * a0[s], accB[s] += wb0 * b0[s];
+      for (int q = 0; q < kSeg; ++q) {
+        const bool in = t + q < b;
+        const T wa = in ? wA(ii[q]) : (T)0, wb = in ? wB(ii[q]) : (T)0;
+#pragma unroll
+        for (int s = 0; s < S; ++s) accA[s] += wa * ra[q][s], accB[s] += wb * rb[q][s];
+      }
     }
   }
   unsigned bigmask = __ballot_sync(0xffffffffu, big);
