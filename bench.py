@@ -391,6 +391,15 @@ def backward_leg(hef, args, dev, rank, timed, max_over_ranks, world):
 
     ms_f, _, _, _ = timed(fwd, args.steps, args.warmup)
     ms_s, _, _, _ = timed(step, args.steps, 1)
+    fwd()
+    torch.cuda.synchronize()
+    hef.trace_read()
+    hef.trace_kernels("k_bwd")
+    bwd()
+    torch.cuda.synchronize()
+    hef.trace_kernels(None)
+    top_bwd = {k_: round(v[1], 3) for k_, v in
+               sorted(hef.trace_read().items(), key=lambda kv: -kv[1][1])[:8]}
     tf = max_over_ranks(sum(ms_f) / len(ms_f))
     ts = max_over_ranks(sum(ms_s) / len(ms_s))
     torch.cuda.synchronize()
@@ -405,7 +414,7 @@ def backward_leg(hef, args, dev, rank, timed, max_over_ranks, world):
             "dtype": "f32 basis, FP64 adjoints", "loss": "sum over a seeded 10% subset of w_e R_e",
             "ms_forward": tf, "ms_forward_backward": ts, "ms_backward": ts - tf,
             "pins_per_s_forward_backward": world * H.P / (ts * 1e-3),
-            "tape_mib": tape_mb, "euler_residual": euler}
+            "tape_mib": tape_mb, "euler_residual": euler, "top_backward_kernels_ms": top_bwd}
 
 
 def main():

@@ -28,6 +28,8 @@
 // Scatter-adds into Qbar and Qbar_H use FP64 atomics: gradients agree across
 // runs to rounding, not bit for bit.  Every adjoint buffer is FP64; the FP32
 // form reads its FP32 tape and Q.
+#include <algorithm>
+
 #include "internal.h"
 
 namespace hef {
@@ -122,7 +124,9 @@ __global__ void __launch_bounds__(256) k_bwd_scores(IncView g, const T* __restri
 
 // ---------------------------------------------------------------- QR adjoint
 
-// part[chunk][i][j] = sum over the chunk's rows r of Qbar[r][i] * Q[r][j].
+// part[chunk][i][j] = sum over the chunk's rows r of Qbar[r][i] * Q[r][j],
+// in the storage type within a chunk (FP32 products and sums for the FP32
+// form: FP64 runs at 1/64 of the rate) and FP64 across chunks.
 template <typename T>
 __global__ void k_bwd_xgram(const double* __restrict__ Qbar, const T* __restrict__ Q, long long ldq,
                             long long n, int K, long long rows_per_chunk, double* part) {
@@ -131,9 +135,9 @@ __global__ void k_bwd_xgram(const double* __restrict__ Qbar, const T* __restrict
   const long long r1 = min(n, r0 + rows_per_chunk);
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < K * K; idx += gridDim.x * blockDim.x) {
     const int i = idx / K, j = idx % K;
-    double s = 0.0;
-    for (long long r = r0; r < r1; ++r) s += Qbar[r * K + i] * (double)Q[r * ldq + j];
-    part[(size_t)chunk * K * K + idx] = s;
+    T s = 0;
+    for (long long r = r0; r < r1; ++r) s += (T)Qbar[r * K + i] * Q[r * ldq + j];
+    part[(size_t)chunk * K * K + idx] = (double)s;
   }
 }
 
@@ -171,7 +175,7 @@ __global__ void k_bwd_rinv(const double* __restrict__ R, int K, double* Rinv) {
   }
 }
 
-// Z = Qbar + Q C (thread per element).
+// Z = Qbar + Q C (thread per element; products in the storage type).
 template <typename T>
 __global__ void k_bwd_qr_z(const T* __restrict__ Q, long long ldq, const double* __restrict__ Qbar,
                            const double* __restrict__ C, long long n, int K, double* Z) {
@@ -181,9 +185,9 @@ __global__ void k_bwd_qr_z(const T* __restrict__ Q, long long ldq, const double*
     const long long r = idx / K;
     const int j = (int)(idx % K);
     const T* q = Q + r * ldq;
-    double s = Qbar[idx];
-    for (int i = 0; i < K; ++i) s += (double)q[i] * C[(size_t)i * K + j];
-    Z[idx] = s;
+    T s = 0;
+    for (int i = 0; i < K; ++i) s += q[i] * (T)C[(size_t)i * K + j];
+    Z[idx] = Qbar[idx] + (double)s;
   }
 }
 
@@ -389,28 +393,46 @@ __global__ void k_bwd_edge2(IncView g, ChainBwd c) {
 
 // Deflation of the start (j = 0): ubar_0 = nu_0 xbar_0 and its sums over the
 // rows of each trivial vector t (clique; star vertices; star hyperedges)
-// with d > 0: tdot[slot][s] = t^T ubar_0.
+// with d > 0: tdot[slot][s] = t^T ubar_0.  Sums per thread, then per CTA in
+// shared memory, then one atomic per CTA and slot.
 __global__ void k_bwd_defl_dots(IncView g, ChainBwd c, double* tdot) {
   if (g.status[0]) return;
+  __shared__ double sacc[3 * 16];
   const int S = c.S;
+  for (int q = threadIdx.x; q < 3 * S; q += blockDim.x) sacc[q] = 0.0;
+  __syncthreads();
   const long long nrows = 2ll * c.n + c.m;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < nrows * S;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const long long r = idx / S;
-    const int s = (int)(idx % S);
-    double d, u;
+  double acc[3][16];
+  for (int q = 0; q < 3; ++q)
+    for (int s = 0; s < S; ++s) acc[q][s] = 0.0;
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+       r += (long long)gridDim.x * blockDim.x) {
+    double d;
     int slot;
+    const double* xa;
+    long long arow;
     if (r < c.n) {
-      d = g.dc[r], u = c.inv_nu[s] * c.xbc0[r * S + s], slot = 0;
+      d = g.dc[r], slot = 0, xa = c.xbc0, arow = r;
     } else {
       const long long rb = r - c.n;
       const bool vrow = rb < c.n;
       d = vrow ? g.db[rb] : g.ew[rb - c.n];
-      u = c.inv_nu[S + s] * c.xbb0[rb * S + s];
-      slot = vrow ? 1 : 2;
+      slot = vrow ? 1 : 2, xa = c.xbb0, arow = rb;
     }
-    if (d > 0.0 && u != 0.0) atomicAdd(&tdot[slot * S + s], u);
+    if (d > 0.0)
+      for (int s = 0; s < S; ++s)
+        acc[slot][s] += c.inv_nu[(slot ? S : 0) + s] * xa[arow * S + s];
   }
+  for (int q = 0; q < 3; ++q)
+    for (int s = 0; s < S; ++s) {
+      double v = acc[q][s];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(&sacc[q * S + s], v);
+    }
+  __syncthreads();
+  for (int q = threadIdx.x; q < 3 * S; q += blockDim.x)
+    if (sacc[q] != 0.0) atomicAdd(&tdot[q], sacc[q]);
 }
 
 // x0 = Pi x0_raw with Pi x = x - sum_t t c_t(x), c_t = (t^T D x) / (t^T D t):
@@ -523,8 +545,12 @@ size_t carve_bwd(void* base, const hef_incidence* inc, int k, int S, int dtype, 
   const long long m1 = m > 0 ? m : 1;
   const int K = 2 * k * S;
   const size_t esz = dtype == HEF_F64 ? 8 : 4;
-  const long long chunks = (n + 4095) / 4096;
-  w->nchunk = (int)(chunks < 1 ? 1 : (chunks > 64 ? 64 : chunks));
+  // row chunks of the Qbar^T Q partials: about 256 rows each, at most 1024
+  // chunks and 32 M partial values
+  long long chunks = (n + 255) / 256;
+  const long long cap = std::max(1ll, (1ll << 25) / ((long long)K * K));
+  chunks = std::min(chunks, std::min(1024ll, cap));
+  w->nchunk = (int)(chunks < 1 ? 1 : chunks);
   w->QHbar = c.take<double>(K);
   w->wbar = c.take<double>(m1);
   w->Qbar = c.take<double>((size_t)n * K);

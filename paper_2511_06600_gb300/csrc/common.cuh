@@ -136,9 +136,11 @@ __device__ __forceinline__ double warp_sum_strided(double v, int S) {
 // kernel can be replayed (CUDA graphs).
 __device__ __forceinline__ bool last_block_done(unsigned int* counter) {
   __shared__ bool is_last;
-  __threadfence();
+  // the CTA barrier orders every thread's writes before thread 0's fence,
+  // which publishes them (cumulatively) ahead of its arrival
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     unsigned int prev = atomicAdd(counter, 1u);
     is_last = (prev == gridDim.x * gridDim.y * gridDim.z - 1);
   }
@@ -235,18 +237,24 @@ __device__ __forceinline__ bool grid_reduce(const GridRed& r, int nslot, double*
   const int g = b / kRedGroup, g0 = g * kRedGroup;
   const int gs = min(kRedGroup, nblk - g0);
   const int ngroups = (nblk + kRedGroup - 1) / kRedGroup;
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) role = (atomicAdd(&r.gcnt[g], 1u) == (unsigned)gs - 1) ? 1 : 0;
-  __syncthreads();
-  if (!role) return false;
-  __threadfence();
-  block_sum_columns(r.part + (size_t)g0 * nslot, gs, nslot, r.gpart + (size_t)g * nslot);
-  __threadfence();
+  // arrival: the CTA barrier orders the partial writes of every thread before
+  // thread 0's fence, which publishes them ahead of the atomic (only the
+  // arriving thread fences: the other threads' unrelated stores need not wait)
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
+    role = (atomicAdd(&r.gcnt[g], 1u) == (unsigned)gs - 1) ? 1 : 0;
+    if (role) __threadfence();
+  }
+  __syncthreads();
+  if (!role) return false;
+  block_sum_columns(r.part + (size_t)g0 * nslot, gs, nslot, r.gpart + (size_t)g * nslot);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
     r.gcnt[g] = 0u;
     role = (atomicAdd(r.tcnt, 1u) == (unsigned)ngroups - 1) ? 2 : 0;
+    if (role) __threadfence();
   }
   __syncthreads();
   if (role != 2) return false;

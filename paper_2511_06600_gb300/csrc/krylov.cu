@@ -34,7 +34,11 @@ namespace {
 
 constexpr int kMaxS = 16;
 constexpr int kBig = 16;     // segments longer than this are summed by a warp
-constexpr int kUpdRows = 4;  // rows per thread in the update pass
+// rows per thread in the update pass
+template <typename T, int S>
+__host__ __device__ constexpr int upd_rows() {
+  return 4;
+}
 // entries gathered per round by one thread in the segment sums (wider rows
 // keep two, for registers)
 template <typename T, int S>
@@ -549,7 +553,7 @@ __device__ __forceinline__ void node_final(const IncView& g, const KView<T>& kv,
   }
 }
 
-// Update pass item (rows r0 + it * blockDim.x, it < kUpdRows): u_j = y -
+// Update pass item (rows r0 + it * blockDim.x, it < upd_rows): u_j = y -
 // trivial part - alpha x_{j-1} - beta x_{j-2} (written over x_{j-2}'s
 // buffer) and its D-norm, added to acc.  Rows: [0, n) clique, [n, 2n + m) star.
 template <typename T, int S>
@@ -566,6 +570,7 @@ __device__ __forceinline__ void update_item(const IncView& g, const ScalView<T>&
 #pragma unroll
       for (int q = 0; q < 4; ++q) cf[op][s][q] = kv.cfT[((size_t)j * 2 * S + op * S + s) * 4 + q];
   const long long nrows = 2ll * g.n + g.m;
+  constexpr int kUpdRows = upd_rows<T, S>();
 #pragma unroll
   for (int it = 0; it < kUpdRows; ++it) {
     const long long r = r0 + (long long)it * blockDim.x;
@@ -669,7 +674,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
   if (grid_reduce(kv.red, 6 * S, tn)) node_final(g, kv, S, j, tn);
 }
 
-// Update pass of step j (kUpdRows rows per thread); the final CTA forms the
+// Update pass of step j (upd_rows rows per thread); the final CTA forms the
 // inverse norms.
 template <typename T, int S>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
@@ -677,7 +682,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
   if (g.status[0]) return;
   T acc[2][S];
   zero_acc(acc);
-  update_item<T, S>(g, sv, kv, j, (long long)blockIdx.x * blockDim.x * kUpdRows + threadIdx.x, acc);
+  update_item<T, S>(g, sv, kv, j,
+                    (long long)blockIdx.x * blockDim.x * upd_rows<T, S>() + threadIdx.x, acc);
   block_partials_qs<2, S, T>(acc, kv.red.part);
   __shared__ double tot[2 * kMaxS];
   if (grid_reduce(kv.red, 2 * S, tot)) update_final(kv, S, j, tot);
@@ -764,7 +770,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(3))
     {
       T acc[2][S];
       zero_acc(acc);
-      for (long long r0 = base * kUpdRows; r0 < nrows; r0 += stride * kUpdRows)
+      for (long long r0 = base * upd_rows<T, S>(); r0 < nrows; r0 += stride * upd_rows<T, S>())
         update_item<T, S>(g, sv, kv, j, r0 + threadIdx.x, acc);
       reduce_barrier<2, S>(kv, acc, gen, status,
                            [&](const double* tot) { update_final(kv, S, j, tot); });
@@ -819,7 +825,7 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   const int grid_all = blocks_for(2 * n + m);
   const int grid_e = blocks_for(m > 0 ? m : 1);
   const int grid_n = blocks_for(n);
-  const int grid_upd = blocks_for((2 * n + m + kUpdRows - 1) / kUpdRows);
+  const int grid_upd = blocks_for((2 * n + m + upd_rows<T, S>() - 1) / upd_rows<T, S>());
   HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
   HEF_LAUNCH("k_start_write", st, k_start_write<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
   HEF_CHECK_LAUNCH();
