@@ -23,6 +23,7 @@ namespace {
 constexpr double kQhTiny = 1e-300;
 constexpr int kFlushEdges = 32;  // FP32 form: edges per FP32 partial sum
 constexpr int kGroup1 = 8;      // hyperedges per warp task in pass 1
+constexpr int kPinStage = 96;   // pins of a pass-1 task staged in shared memory
 constexpr int kWorkSlot = 60;    // counters [60], [61]: work distribution of the passes
 
 template <typename T>
@@ -46,9 +47,9 @@ __device__ __forceinline__ long long next_group(unsigned int* work) {
 
 // Extrema of two hyperedges at once (pins [a0, b0) and [a1, b1), warp-uniform):
 // four clamped pin rows of each are in flight together.
-template <typename T, int NC>
+template <typename T, int NC, typename PinAt>
 __device__ __forceinline__ void two_edge_extrema(const T* __restrict__ Q, long long ldq, int K,
-                                                 const int32_t* __restrict__ cpins, int a0, int b0,
+                                                 PinAt cpins, int a0, int b0,
                                                  int a1, int b1, int lane, T (&mx0)[NC],
                                                  T (&mn0)[NC], T (&mx1)[NC], T (&mn1)[NC]) {
 #pragma unroll
@@ -61,14 +62,14 @@ __device__ __forceinline__ void two_edge_extrema(const T* __restrict__ Q, long l
     const bool u0 = t0 < b0, u1 = t1 < b1;
     const int l0 = b0 - 1, l1 = b1 - 1;
     const T* r[8];
-    r[0] = Q + (long long)(u0 ? cpins[t0] : 0) * ldq;
-    r[1] = Q + (long long)(u0 ? cpins[min(t0 + 1, l0)] : 0) * ldq;
-    r[2] = Q + (long long)(u0 ? cpins[min(t0 + 2, l0)] : 0) * ldq;
-    r[3] = Q + (long long)(u0 ? cpins[min(t0 + 3, l0)] : 0) * ldq;
-    r[4] = Q + (long long)(u1 ? cpins[t1] : 0) * ldq;
-    r[5] = Q + (long long)(u1 ? cpins[min(t1 + 1, l1)] : 0) * ldq;
-    r[6] = Q + (long long)(u1 ? cpins[min(t1 + 2, l1)] : 0) * ldq;
-    r[7] = Q + (long long)(u1 ? cpins[min(t1 + 3, l1)] : 0) * ldq;
+    r[0] = Q + (long long)(u0 ? cpins(t0) : 0) * ldq;
+    r[1] = Q + (long long)(u0 ? cpins(min(t0 + 1, l0)) : 0) * ldq;
+    r[2] = Q + (long long)(u0 ? cpins(min(t0 + 2, l0)) : 0) * ldq;
+    r[3] = Q + (long long)(u0 ? cpins(min(t0 + 3, l0)) : 0) * ldq;
+    r[4] = Q + (long long)(u1 ? cpins(t1) : 0) * ldq;
+    r[5] = Q + (long long)(u1 ? cpins(min(t1 + 1, l1)) : 0) * ldq;
+    r[6] = Q + (long long)(u1 ? cpins(min(t1 + 2, l1)) : 0) * ldq;
+    r[7] = Q + (long long)(u1 ? cpins(min(t1 + 3, l1)) : 0) * ldq;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int col = lane + 32 * c;
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restri
       const double sp = (double)(mx[c] - mn[c]);
       acc[c] += we * sp * sp;
       if (spread && wid == 0 && lane + 32 * c < K)
-        spread[(long long)e * K + lane + 32 * c] = mx[c] - mn[c];
+        spread[(long long)(lane + 32 * c) * g.m + e] = mx[c] - mn[c];
     }
   }
   if (wid == 0) {
@@ -179,7 +180,9 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
                                                      T* spread) {
   if (g.status[0]) return;
   __shared__ double wred[kThreads / 32][32 * NC];
+  extern __shared__ unsigned char sp_raw[];  // spreads of the warp's group: kGroup1 x K
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  T* tile = reinterpret_cast<T*>(sp_raw) + (size_t)wid * kGroup1 * K;
   double acc[NC];
   T pacc[NC];
 #pragma unroll
@@ -190,34 +193,57 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const long long ngroups = ((long long)g.m + kGroup1 - 1) / kGroup1;
   (void)work;
+  __shared__ int spins[kThreads / 32][kPinStage];  // the group's first pins
   for (long long grp = warp; grp < ngroups; grp += nwarps) {
     const long long e = grp * kGroup1 + lane;
     int a = 0, b = 0;
     if (lane < kGroup1 && e < g.m) a = g.ceptr[e], b = g.ceptr[e + 1];
+    // the group's pin ids in one coalesced read (the extrema then wait on one
+    // round trip, Q, instead of two)
+    const int gp0 = __shfl_sync(0xffffffffu, a, 0);
+    const int gp1 = __shfl_sync(0xffffffffu, b, min(kGroup1, (int)(g.m - grp * kGroup1)) - 1);
+    const int npin = min(gp1 - gp0, kPinStage);
+    __syncwarp();  // the previous group's reads of spins are done
+    for (int q = lane; q < npin; q += 32) spins[wid][q] = g.cpins[gp0 + q];
+    __syncwarp();
+    auto pin_at = [&](int t) { return t - gp0 < npin ? spins[wid][t - gp0] : g.cpins[t]; };
     if (b - a < 2 || b - a > kBigEdge) b = a;  // not scored here
     const T wl = (lane < kGroup1 && e < g.m) ? (T)g.ew[e] : (T)0;
+    unsigned scored = 0u;  // hyperedges of the group whose spreads are in the tile
     for (int i = 0; i < kGroup1; i += 2) {
       const int a0 = __shfl_sync(0xffffffffu, a, i), b0 = __shfl_sync(0xffffffffu, b, i);
       const int a1 = __shfl_sync(0xffffffffu, a, i + 1), b1 = __shfl_sync(0xffffffffu, b, i + 1);
       const T w0 = __shfl_sync(0xffffffffu, wl, i), w1 = __shfl_sync(0xffffffffu, wl, i + 1);
       if (a0 == b0 && a1 == b1) continue;
       T mx0[NC], mn0[NC], mx1[NC], mn1[NC];
-      two_edge_extrema<T, NC>(Q, ldq, K, g.cpins, a0, b0, a1, b1, lane, mx0, mn0, mx1, mn1);
-      const long long e0 = grp * kGroup1 + i;
+      two_edge_extrema<T, NC>(Q, ldq, K, pin_at, a0, b0, a1, b1, lane, mx0, mn0, mx1, mn1);
+      if (b0 > a0) scored |= 1u << i;
+      if (b1 > a1) scored |= 2u << i;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int col = lane + 32 * c;
         if (b0 > a0) {
           const T sp = mx0[c] - mn0[c];
           pacc[c] += w0 * sp * sp;
-          if (spread && col < K) spread[e0 * K + col] = sp;
+          if (spread && col < K) tile[i * K + col] = sp;
         }
         if (b1 > a1) {
           const T sp = mx1[c] - mn1[c];
           pacc[c] += w1 * sp * sp;
-          if (spread && col < K) spread[(e0 + 1) * K + col] = sp;
+          if (spread && col < K) tile[(i + 1) * K + col] = sp;
         }
       }
+    }
+    // the group's spreads, column-major (spread[col][e]): each store of the
+    // warp covers kGroup1 consecutive hyperedges of 32 / kGroup1 columns
+    if (spread && scored) {
+      __syncwarp();
+      const long long eb = grp * kGroup1;
+      for (int idx = lane; idx < kGroup1 * K; idx += 32) {
+        const int col = idx / kGroup1, ee = idx % kGroup1;
+        if ((scored >> ee) & 1u) spread[(long long)col * g.m + eb + ee] = tile[ee * K + col];
+      }
+      __syncwarp();
     }
     // FP32 partial sums span one group (kGroup1 hyperedges); FP64 beyond
 #pragma unroll
@@ -384,7 +410,8 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
       const int a1 = __shfl_sync(0xffffffffu, a, i + 1), b1 = __shfl_sync(0xffffffffu, b, i + 1);
       if (a0 == b0 && a1 == b1) continue;
       T mx0[NC], mn0[NC], mx1[NC], mn1[NC];
-      two_edge_extrema<T, NC>(Q, ldq, K, g.cpins, a0, b0, a1, b1, lane, mx0, mn0, mx1, mn1);
+      two_edge_extrema<T, NC>(Q, ldq, K, [&](int t) { return g.cpins[t]; }, a0, b0, a1, b1, lane,
+                              mx0, mn0, mx1, mn1);
       if (b0 > a0)
         score_edge_out<T, NC>(g, Q, ldq, K, reduce, QH, iq, use, (int)(grp * 32 + i), a0, b0, mx0, mn0,
                               R_out, argvec, pmax, pmin);
@@ -395,96 +422,71 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
   }
 }
 
-// Pass 2 from the spreads that pass 1 stored (spread[e][i], K per row; every
-// hyperedge with >= 2 pins has its row): warp per hyperedge, lanes over
-// columns.  Ratios and the arg-max column in the working type as in Eq.
-// ratios; R_e from the spread in FP64; the routing pins by one gather of the
+// Pass 2 from the spreads that pass 1 stored column-major (spread[i][e]; every
+// hyperedge with >= 2 pins has them): thread per hyperedge, so that each load
+// of a warp reads 32 consecutive hyperedges of one column.  Ratios and the
+// arg-max column in the working type as in Eq. ratios (lowest column on
+// ties); R_e from the spread in FP64; the routing pins by one gather of the
 // arg-max column over the hyperedge's pins (lowest position on ties).  Gives
 // exactly what k_score_pass2 / k_score_big2 give, without gathering every
 // column of Q again.
-template <typename T, int NC>
+template <typename T>
 __global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restrict__ Q, long long ldq,
                                                      int K, int reduce, const double* __restrict__ QH,
                                                      const double* __restrict__ invQH,
                                                      const T* __restrict__ spread, double* R_out,
                                                      int32_t* argvec, int32_t* pmax, int32_t* pmin) {
   if (g.status[0]) return;
-  const int lane = threadIdx.x & 31;
-  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
-  T iq[NC];
-  bool use[NC];
-  load_use<T, NC>(QH, invQH, K, iq, use);
-  for (long long e = warp; e < g.m; e += nwarps) {
+  extern __shared__ unsigned char iq_raw[];
+  T* iq = reinterpret_cast<T*>(iq_raw);  // K: 1 / Q_H in the working type, 0 when unused
+  for (int i = threadIdx.x; i < K; i += blockDim.x) iq[i] = QH[i] > kQhTiny ? (T)invQH[i] : (T)0;
+  __syncthreads();
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < g.m;
+       e += (long long)gridDim.x * blockDim.x) {
     const int a = g.ceptr[e], b = g.ceptr[e + 1];
     const int oe = g.perm[e];
     if (b - a < 2) {  // degenerate: no score, no routing
-      if (lane == 0) {
-        R_out[oe] = 0.0;
-        if (argvec) argvec[oe] = -1;
-        if (pmax) pmax[oe] = -1;
-        if (pmin) pmin[oe] = -1;
-      }
+      R_out[oe] = 0.0;
+      if (argvec) argvec[oe] = -1;
+      if (pmax) pmax[oe] = -1;
+      if (pmin) pmin[oe] = -1;
       continue;
     }
     T best = (T)-1, spb = 0;
-    int bcol = 0x7fffffff;
+    int bcol = -1;
     double sum = 0.0;
-#pragma unroll
-    for (int c = 0; c < NC; ++c) {
-      if (use[c]) {
-        const T sp = spread[e * K + lane + 32 * c];
-        const T r = sp * sp * iq[c];
-        if (reduce == HEF_REDUCE_SUM) {
-          const double spd = (double)sp;
-          sum += spd * spd / QH[lane + 32 * c];
-        }
-        if (r > best) best = r, bcol = lane + 32 * c, spb = sp;
+    const T* col = spread + e;
+    for (int i = 0; i < K; ++i, col += g.m) {
+      if (iq[i] == (T)0) continue;
+      const T sp = *col;
+      const T r = sp * sp * iq[i];
+      if (reduce == HEF_REDUCE_SUM) {
+        const double spd = (double)sp;
+        sum += spd * spd / QH[i];
       }
+      if (r > best) best = r, bcol = i, spb = sp;
     }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oc = __shfl_xor_sync(0xffffffffu, bcol, o);
-      const T os = __shfl_xor_sync(0xffffffffu, spb, o);
-      if (ob > best || (ob == best && oc < bcol)) best = ob, bcol = oc, spb = os;
-    }
-    if (reduce == HEF_REDUCE_SUM) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    }
-    const bool any = bcol != 0x7fffffff;
-    int tmax = 0x7fffffff, tmin = 0x7fffffff;
+    const bool any = bcol >= 0;
+    int tmax = a, tmin = a;
     if (any && (pmax || pmin)) {
       // extrema of column bcol over the pins, lowest position on ties
-      T vmax = lowest<T>(), vmin = -lowest<T>();
-      for (int t = a + lane; t < b; t += 32) {
+      T vmax = Q[(long long)g.cpins[a] * ldq + bcol], vmin = vmax;
+      for (int t = a + 1; t < b; ++t) {
         const T v = Q[(long long)g.cpins[t] * ldq + bcol];
         if (v > vmax) vmax = v, tmax = t;
         if (v < vmin) vmin = v, tmin = t;
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ov = __shfl_xor_sync(0xffffffffu, vmax, o);
-        const int ot = __shfl_xor_sync(0xffffffffu, tmax, o);
-        if (ov > vmax || (ov == vmax && ot < tmax)) vmax = ov, tmax = ot;
-        const T pv = __shfl_xor_sync(0xffffffffu, vmin, o);
-        const int pt = __shfl_xor_sync(0xffffffffu, tmin, o);
-        if (pv < vmin || (pv == vmin && pt < tmin)) vmin = pv, tmin = pt;
-      }
     }
-    if (lane == 0) {
-      double Re = 0.0;
-      if (reduce == HEF_REDUCE_SUM) Re = sum;
-      else if (any) {
-        const double spw = (double)spb;
-        Re = spw * spw / QH[bcol];
-      }
-      R_out[oe] = Re;
-      if (argvec) argvec[oe] = any ? bcol : -1;
-      if (pmax) pmax[oe] = any ? g.cpins[tmax] : -1;
-      if (pmin) pmin[oe] = any ? g.cpins[tmin] : -1;
+    double Re = 0.0;
+    if (reduce == HEF_REDUCE_SUM) Re = sum;
+    else if (any) {
+      const double spw = (double)spb;
+      Re = spw * spw / QH[bcol];
     }
+    R_out[oe] = Re;
+    if (argvec) argvec[oe] = any ? bcol : -1;
+    if (pmax) pmax[oe] = any ? g.cpins[tmax] : -1;
+    if (pmin) pmin[oe] = any ? g.cpins[tmin] : -1;
   }
 }
 
@@ -529,15 +531,20 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
   // grids of co-resident CTAs only (work is handed out dynamically)
   const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
   const int g2 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass2<T, NC>, kThreads));
-  T* spread = static_cast<T*>(w.spread);
+  // spreads kept for pass 2 when the workspace has them and the staging tile
+  // of pass 1 (kGroup1 x K per warp) fits
+  const size_t tile_bytes = (size_t)(kThreads / 32) * kGroup1 * K * sizeof(T);
+  T* spread = (w.spread && tile_bytes <= 96 * 1024) ? static_cast<T*>(w.spread) : nullptr;
+  const size_t smem1 = spread ? tile_bytes : 0;
+  if (spread) HEF_ENSURE_SMEM((k_score_pass1<T, NC>), (int)smem1);
   HEF_LAUNCH("k_score_big1", st, k_score_big1<T, NC><<<w.bgrid, kThreads, 0, st>>>(g, Q, ldq, K, w.bpart,
                                                                                    spread));
-  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<g1, kThreads, 0, st>>>(
+  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<g1, kThreads, smem1, st>>>(
                                       g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out,
                                       w.counter + kWorkSlot, spread));
   if (spread) {
-    const int g3 = num_sms() * resident_ctas(k_score_ratio<T, NC>, kThreads);
-    HEF_LAUNCH("k_score_ratio", st, k_score_ratio<T, NC><<<g3, kThreads, 0, st>>>(
+    const int g3 = stride_grid(inc->m > 0 ? inc->m : 1, 8);
+    HEF_LAUNCH("k_score_ratio", st, k_score_ratio<T><<<g3, kThreads, K * sizeof(T), st>>>(
                                         g, Q, ldq, K, reduce, w.QH, w.invQH, spread, R_out, argvec,
                                         pmax, pmin));
     HEF_CHECK_LAUNCH();
