@@ -133,6 +133,28 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def recorded_traffic(kernel, workload, form):
+    """DRAM bytes per launch of `kernel` from the committed ncu record for this
+    workload and form, or None when there is none or the kernel's sources
+    changed after the capture (their sha256 no longer matches)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"dram_traffic_{workload}_{form}.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) != 4 or f[0] != kernel:
+            continue
+        h = hashlib.sha256()
+        for src in f[3].split(","):
+            p = os.path.join(ROOT, src)
+            if not os.path.exists(p):
+                return None
+            h.update(open(p, "rb").read())
+        return int(f[1]) if h.hexdigest() == f[2] else None
+    return None
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -544,6 +566,8 @@ def main():
                 "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 x max SM clock"}
     roof["launches"] = nl
     roof["avg_ms"] = tot / max(nl, 1)
+    roof["traffic"] = recorded_traffic(dominant, args.workload, args.form)
+    roof["algorithmic_bytes"] = units if bound == "hbm" else None
 
     # ---- latency of the small FP64 case (64 x 32 grid, 2,300 nets, k = 10,
     # S = 1), one CUDA graph per step, with the Krylov steps as one

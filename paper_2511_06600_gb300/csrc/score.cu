@@ -532,9 +532,10 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
   const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
   const int g2 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass2<T, NC>, kThreads));
   // spreads kept for pass 2 when the workspace has them and the staging tile
-  // of pass 1 (kGroup1 x K per warp) fits
+  // of pass 1 (kGroup1 x K per warp) is small enough not to cut the pass's
+  // occupancy (K <= 192 in FP32); larger K gather Q again in pass 2
   const size_t tile_bytes = (size_t)(kThreads / 32) * kGroup1 * K * sizeof(T);
-  T* spread = (w.spread && tile_bytes <= 96 * 1024) ? static_cast<T*>(w.spread) : nullptr;
+  T* spread = (w.spread && tile_bytes <= 48 * 1024) ? static_cast<T*>(w.spread) : nullptr;
   const size_t smem1 = spread ? tile_bytes : 0;
   if (spread) HEF_ENSURE_SMEM((k_score_pass1<T, NC>), (int)smem1);
   HEF_LAUNCH("k_score_big1", st, k_score_big1<T, NC><<<w.bgrid, kThreads, 0, st>>>(g, Q, ldq, K, w.bpart,
