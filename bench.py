@@ -64,6 +64,28 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x, world, device):
+    """Largest x over the ranks (all-reduce MAX: NCCL on GPUs, gloo on CPU)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x, world, device):
+    """Sum of x over the ranks (all-reduce SUM)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def instance(name, rank):
     """The rank's netlist: the named workload, seed shifted per rank (each
     rank scores its own netlist: weak scaling)."""
@@ -263,7 +285,7 @@ def score_errors(R, ref):
             "kendall_tau": float(kendalltau(R, ref).statistic)}
 
 
-def precision_leg(hef, args, dev, rank, timed, max_over_ranks, world):
+def precision_leg(hef, args, dev, rank, timed, max_ranks, world):
     """The precision form at its own scale: the 1200 x 1000 grid with 1.3M
     nets (2 + Geometric(0.5) pins, radius 3), k = 24, S = 8 (K = 384), FP32
     basis with tensor-core or FP32 Gram, FP64 Cholesky and Q_H; one CUDA
@@ -291,14 +313,14 @@ def precision_leg(hef, args, dev, rank, timed, max_over_ranks, world):
                   sorted(hef.trace_read().items(), key=lambda kv: -kv[1][1])[:8]}
     pipe.capture(t["eptr"], t["pins"], t["w"], t["x0c"], t["x0b"])
     ms, _, _, _ = timed(pipe.replay, args.steps, args.warmup)
-    t32 = max_over_ranks(sum(ms) / len(ms))
+    t32 = max_ranks(sum(ms) / len(ms))
     R32 = pipe.out["R"].cpu().numpy()
     rank32 = int(pipe.rank.item())
     del pipe
     p64 = hef.Pipeline(H.n, H.m, H.P, k, S, torch.float64, device=dev)
     step64 = lambda: p64.run(t["eptr"], t["pins"], t["w"], t["x0c"], t["x0b"])  # noqa
     ms64, _, _, _ = timed(step64, 1, 1)
-    t64 = max_over_ranks(sum(ms64) / len(ms64))
+    t64 = max_ranks(sum(ms64) / len(ms64))
     R64 = p64.out["R"].cpu().numpy()
     del p64
     out = {"workload": name, "n": H.n, "m": H.m, "P": H.P, "k": k, "S": S, "K": K,
@@ -325,7 +347,7 @@ def precision_leg(hef, args, dev, rank, timed, max_over_ranks, world):
     return out
 
 
-def batched_leg(hef, args, dev, rank, timed, max_over_ranks, world):
+def batched_leg(hef, args, dev, rank, timed, max_ranks, world):
     """The batched form: G netlists of uneven sizes (n log-uniform in
     5k..150k, m = 1.05 n, 2 + Geometric(0.5) pins on radius-3 neighbourhoods,
     unit weights; k = 20, S = 4), scored in one hef_resistance_batched call
@@ -352,7 +374,7 @@ def batched_leg(hef, args, dev, rank, timed, max_over_ranks, world):
     ns, _, tune_ms = b32.autotune()
     b32.capture()
     ms, _, _, _ = timed(b32.replay, args.steps, args.warmup)
-    t32 = max_over_ranks(sum(ms) / len(ms))
+    t32 = max_ranks(sum(ms) / len(ms))
     R32 = [o["R"].double().cpu().numpy() for o in b32.out]
     del b32
     b64 = hef.Batch(graphs, k, S, torch.float64, nstreams=1)
@@ -360,7 +382,7 @@ def batched_leg(hef, args, dev, rank, timed, max_over_ranks, world):
     torch.cuda.synchronize()
     b64.capture()
     ms64, _, _, _ = timed(b64.replay, max(1, args.fp64_steps), 1)
-    t64 = max_over_ranks(sum(ms64) / len(ms64))
+    t64 = max_ranks(sum(ms64) / len(ms64))
     R64 = [o["R"].cpu().numpy() for o in b64.out]
     del b64
     a = np.concatenate(R32)
@@ -378,7 +400,7 @@ def batched_leg(hef, args, dev, rank, timed, max_over_ranks, world):
                               "normwise_worst_graph": norm}}
 
 
-def backward_leg(hef, args, dev, rank, timed, max_over_ranks, world):
+def backward_leg(hef, args, dev, rank, timed, max_ranks, world):
     """FP32 forward (keeping the Krylov tape) and backward of
     L = sum over a seeded 10 % subset of w_e R_e, on the log-uniform-weight
     netlist; dL/dR = w_e on the subset.  Times forward and backward with CUDA
@@ -422,8 +444,8 @@ def backward_leg(hef, args, dev, rank, timed, max_over_ranks, world):
     hef.trace_kernels(None)
     top_bwd = {k_: round(v[1], 3) for k_, v in
                sorted(hef.trace_read().items(), key=lambda kv: -kv[1][1])[:8]}
-    tf = max_over_ranks(sum(ms_f) / len(ms_f))
-    ts = max_over_ranks(sum(ms_s) / len(ms_s))
+    tf = max_ranks(sum(ms_f) / len(ms_f))
+    ts = max_ranks(sum(ms_s) / len(ms_s))
     torch.cuda.synchronize()
     state["inc"].check()
     dw = state["grad"][0].cpu().numpy()
@@ -469,12 +491,8 @@ def main():
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x):
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_ranks = lambda x: max_over_ranks(x, world, dev)  # noqa: E731
+    P_all = sum_over_ranks(H.P, world, dev)  # pins scored by all ranks in one step
 
     def timed(fn, steps, warmup, trace=None):
         """Per-step CUDA-event times (ms) with an L2 flush before each step."""
@@ -541,8 +559,8 @@ def main():
     clk = clocks.stop()
     pipe.check()
     R32 = pipe.out["R"].double().cpu().numpy()
-    t_step = max_over_ranks(sum(ms) / len(ms))
-    value = world * H.P / (t_step * 1e-3)
+    t_step = max_ranks(sum(ms) / len(ms))
+    value = P_all / (t_step * 1e-3)
     if graph:  # kernels inside a replayed graph are not counted by the library
         launches = int(round(per_kernel_launches)) * args.steps
     # dominant kernel's launch durations: eager steps with CUDA events around it
@@ -585,7 +603,7 @@ def main():
         ps.capture(ts["eptr"], ts["pins"], ts["w"], ts["x0c"], ts["x0b"])
         ms_s, _, _, _ = timed(ps.replay, args.steps, args.warmup)
         ps.check()
-        small[label + "_ms"] = max_over_ranks(statistics.median(ms_s))
+        small[label + "_ms"] = max_ranks(statistics.median(ms_s))
         del ps
     hef.set_krylov_persistent(1)
     small.update(workload="grid64x32_m2300", dtype="f64", n=Hs.n, m=Hs.m, P=Hs.P, k=ks, S=Ss)
@@ -596,7 +614,7 @@ def main():
     ms64, _, _, _ = timed(step64, args.fp64_steps, 1)
     pipe64.check()
     R64 = pipe64.out["R"].cpu().numpy()
-    t64 = max_over_ranks(sum(ms64) / len(ms64))
+    t64 = max_ranks(sum(ms64) / len(ms64))
     big = R64 >= 1e-3 * R64.max()
     rel = np.abs(R32 - R64) / np.maximum(R64, 1e-300)
     err = {"max_rel": float(rel[big].max()), "p99_rel": float(np.percentile(rel[R64 > 0], 99)),
@@ -621,24 +639,24 @@ def main():
             torch.cuda.current_stream().synchronize()
 
         ms_e, _, _, _ = timed(e2e_step, args.steps, 1)
-        te = max_over_ranks(sum(ms_e) / len(ms_e))
-        e2e = {"value": world * H.P / (te * 1e-3), "unit": "pins/s", "h2d_bytes_per_step": h2d,
+        te = max_ranks(sum(ms_e) / len(ms_e))
+        e2e = {"value": P_all / (te * 1e-3), "unit": "pins/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": te}
 
     # ---- differentiation form: forward + backward of a score-based loss
     bwd = None
     if not args.no_backward:
-        bwd = backward_leg(hef, args, dev, rank, timed, max_over_ranks, world)
+        bwd = backward_leg(hef, args, dev, rank, timed, max_ranks, world)
 
     # ---- precision form at its own scale (1.2M cells, K = 384)
     precision = None
     if not args.no_precision:
-        precision = precision_leg(hef, args, dev, rank, timed, max_over_ranks, world)
+        precision = precision_leg(hef, args, dev, rank, timed, max_ranks, world)
 
     # ---- batched form: many uneven netlists in one captured call
     batched = None
     if not args.no_batched:
-        batched = batched_leg(hef, args, dev, rank, timed, max_over_ranks, world)
+        batched = batched_leg(hef, args, dev, rank, timed, max_ranks, world)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -655,7 +673,7 @@ def main():
                        "l2": f"flushed before every step ({L2_FLUSH_BYTES >> 20} MiB write)",
                        "parallelism": f"{world} independent netlists (one per GPU)"},
             "scores_per_s": world * H.m / (t_step * 1e-3),
-            "fp64_plain": {"value": world * H.P / (t64 * 1e-3), "unit": "pins/s",
+            "fp64_plain": {"value": P_all / (t64 * 1e-3), "unit": "pins/s",
                            "ms_per_step": t64},
             "speedup_vs_fp64": t64 / t_step,
             "small_fp64_latency": small,
