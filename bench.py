@@ -455,7 +455,7 @@ def backward_leg(hef, args, dev, rank, timed, max_ranks, world):
     euler = abs(float(H.w @ dw) + L) / L
     tape_mb = state["tape"].numel() / 2**20
     return {"workload": args.backward_workload, "n": H.n, "m": H.m, "P": H.P, "k": k, "S": S,
-            "dtype": "f32 basis, FP64 adjoints", "loss": "sum over a seeded 10% subset of w_e R_e",
+            "dtype": "f32 basis, QR and chain adjoints; FP64 scoring adjoint", "loss": "sum over a seeded 10% subset of w_e R_e",
             "ms_forward": tf, "ms_forward_backward": ts, "ms_backward": ts - tf,
             "pins_per_s_forward_backward": world * H.P / (ts * 1e-3),
             "tape_mib": tape_mb, "euler_residual": euler, "top_backward_kernels_ms": top_bwd}

@@ -275,8 +275,10 @@ hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q,
  * (n x ldq, dtype) and R_fac (K x K, FP64) from hef_orthonormalize; QH,
  * argvec and R from hef_edge_resistance.  Columns dropped by the
  * orthonormalisation carry no gradient.  dR is device FP64 (m, caller
- * order).  All adjoint arithmetic is FP64; scatter-adds use FP64 atomics, so
- * two runs agree to rounding, not bit for bit.
+ * order).  The scoring adjoint is FP64; the orthonormalisation and
+ * Krylov-chain adjoints run in the basis dtype (FP32 for HEF_F32) with FP64
+ * partial sums and weight-gradient sums; the Q_H adjoint is summed with FP64
+ * atomics, so two runs agree to rounding, not bit for bit.
  * ---------------------------------------------------------------------- */
 size_t hef_edge_resistance_backward_workspace_bytes(const hef_incidence* inc,
                                                     int32_t k, int32_t S,
