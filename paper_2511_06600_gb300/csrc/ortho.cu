@@ -199,8 +199,15 @@ __device__ __forceinline__ double pivot_rsqrt<double>(double d) {
 // C: arithmetic type; W: the K x 2K work matrix (shared or global memory).
 // fast = 1: report (flag) any kept pivot <= 1e-4 G_jj instead of trusting
 // it.  fast = 0: exact path; runs only when `flag` is set unless `always`.
-template <typename C, typename T>
-__global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
+// REGP (FP32, K <= kRegK, 512 threads): each panel is eliminated by warp 0 in
+// registers (lane l holds columns j0 + l + 32 q of the panel's rows; the
+// pivot rows' entries travel by shuffles), so a panel costs two CTA barriers
+// instead of two named barriers per pivot.
+constexpr int kRegK = 176;   // columns j0 .. j0 + K + 15 fit 6 per lane
+constexpr int kRegQ = 6;
+
+template <typename C, typename T, int THREADS = 1024, bool REGP = false>
+__global__ void __launch_bounds__(THREADS) k_chol_aug(const double* __restrict__ G,
                                                    const double* __restrict__ c,
                                                    const C* __restrict__ Aproj, int K, int Kp,
                                                    double n, double tol, C* Wg, int use_smem,
@@ -235,7 +242,49 @@ __global__ void __launch_bounds__(1024) k_chol_aug(const double* __restrict__ G,
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j0 = 0; j0 < K; j0 += kPB) {
     const int jend = min(K, j0 + kPB);
-    if (wid < kPB) {
+    if (REGP) {
+      if (wid == 0) {
+        float rw[kPB][kRegQ];
+#pragma unroll
+        for (int p = 0; p < kPB; ++p)
+#pragma unroll
+          for (int q = 0; q < kRegQ; ++q) {
+            const int col = j0 + lane + 32 * q;
+            rw[p][q] = (j0 + p < K && col < W2) ? (float)W[(size_t)(j0 + p) * W2 + col] : 0.0f;
+          }
+#pragma unroll
+        for (int p = 0; p < kPB; ++p) {
+          const int j = j0 + p;
+          if (j < K) {  // warp-uniform
+            const float d = __shfl_sync(0xffffffffu, rw[p][0], p);  // (j, j): lane p
+            const int kj = (ref[j] > (C)0 && d > (float)thr_keep[j]) ? 1 : 0;
+            const float pinv = kj ? pivot_rsqrt<float>(d) : 0.0f;
+            if (lane == 0) {
+              if (fast && kj && d <= (float)thr_near[j]) near_def = 1;
+              o.kept[j] = kj;
+              pk[p] = kj;
+            }
+#pragma unroll
+            for (int q = 0; q < kRegQ; ++q) rw[p][q] *= pinv;  // dropped rows become zero
+            if (kj) {
+#pragma unroll
+              for (int i = p + 1; i < kPB; ++i) {
+                const float r = __shfl_sync(0xffffffffu, rw[p][0], i);  // scaled (j, j0 + i)
+#pragma unroll
+                for (int q = 0; q < kRegQ; ++q) rw[i][q] -= r * rw[p][q];
+              }
+            }
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < kPB; ++p)
+#pragma unroll
+          for (int q = 0; q < kRegQ; ++q) {
+            const int col = j0 + lane + 32 * q;
+            if (j0 + p < K && col < W2) W[(size_t)(j0 + p) * W2 + col] = (C)rw[p][q];
+          }
+      }
+    } else if (wid < kPB) {
       const int i = j0 + wid;
       C* rowi = W + (size_t)i * W2;
       for (int j = j0; j < jend; ++j) {
@@ -554,8 +603,10 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
   const size_t fast_smem = (size_t)K * 2 * K * sizeof(float);
   const bool fast_ok = sizeof(T) == 4;
   const bool fast_in_smem = fast_ok && fast_smem <= 200 * 1024;
-  if (fast_in_smem)
+  if (fast_in_smem) {
     HEF_ENSURE_SMEM((k_chol_aug<float, T>), fast_smem);
+    HEF_ENSURE_SMEM((k_chol_aug<float, T, 512, true>), fast_smem);
+  }
   const double tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
   const double gtol = sizeof(T) == 8 ? 1e-8 : 1e-4;
   double* Rs[2] = {w.R1, w.R2};
@@ -581,10 +632,16 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
       HEF_LAUNCH("k_gram_project", st, k_gram_project<<<stride_grid((long long)K * K, 2), kThreads, 0,
                                                          st>>>(w.G, w.c, K, (double)n, w.A64, w.A32));
       if (fast_ok) {
-        HEF_LAUNCH("k_chol_aug", st, k_chol_aug<float, T><<<1, 1024, fast_in_smem ? fast_smem : 0, st>>>(
-                                         w.G, w.c, w.A32, K, Kp, (double)n, tol,
-                                         fast_in_smem ? nullptr : reinterpret_cast<float*>(w.Wg),
-                                         fast_in_smem ? 1 : 0, 1, 0, o));
+        if (fast_in_smem && K <= kRegK) {
+          HEF_LAUNCH("k_chol_aug", st, (k_chol_aug<float, T, 512, true><<<1, 512, fast_smem, st>>>(
+                                           w.G, w.c, w.A32, K, Kp, (double)n, tol, nullptr, 1, 1, 0,
+                                           o)));
+        } else {
+          HEF_LAUNCH("k_chol_aug", st, k_chol_aug<float, T><<<1, 1024, fast_in_smem ? fast_smem : 0, st>>>(
+                                           w.G, w.c, w.A32, K, Kp, (double)n, tol,
+                                           fast_in_smem ? nullptr : reinterpret_cast<float*>(w.Wg),
+                                           fast_in_smem ? 1 : 0, 1, 0, o));
+        }
       }
       // exact FP64 path: always for the FP64 form, on demand for the FP32 form
       HEF_LAUNCH("k_chol_aug", st, k_chol_aug<double, T><<<1, 1024, 0, st>>>(
