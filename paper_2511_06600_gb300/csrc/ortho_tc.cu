@@ -44,6 +44,7 @@ __device__ __forceinline__ void gram_load_slab(const GramTcArgs& a, long long ro
   for (int k = 0; k < PER; ++k) {
     const int f = threadIdx.x + kTcThreads * k;
     const int r = f & (kSlab - 1), c0 = 4 * (f >> 5);
+    if (c0 >= a.Kq) continue;  // padding rows of the tile: zero, written once
     const long long row = rowbase + r;
     const bool valid = row < r1;
     if (valid && c0 + 3 < a.K) {
@@ -93,6 +94,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
     for (int q = 0; q < STAGES; ++q) mbar_init(&bars[q], 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
+  // basis rows [Kq, Mpad) of the transposed tiles are zero for every slab
+  for (int q = 0; q < 2 * STAGES; ++q) {
+    unsigned char* tile = base + (size_t)q * tile_bytes;
+    for (int e = tid; e < (Mpad - a.Kq) * 32; e += kTcThreads)
+      *reinterpret_cast<float*>(tile + sw128_offset(a.Kq + e / 32, e % 32)) = 0.f;
+  }
+  fence_async_smem();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
@@ -122,6 +130,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
     for (int k = 0; k < PER; ++k) {
       const int f = tid + kTcThreads * k;
       const int r = f & (kSlab - 1), c0 = 4 * (f >> 5);
+      if (c0 >= a.Kq) continue;  // warp-uniform
       const float x[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
