@@ -54,6 +54,33 @@ struct LaunchTrace {
 
 constexpr int kThreads = 256;
 
+// Programmatic dependent launch (sm_90 and later).  A kernel launched by
+// launch_dependent() may be scheduled while the previous kernel of its stream
+// drains; it calls pdl_wait() before its first access to memory that an
+// earlier kernel writes or reads (the wait returns once the previous grid has
+// completed and its writes are visible; it is a no-op for a kernel launched
+// without the attribute), and pdl_trigger() after that wait, which lets the
+// next such kernel be scheduled.  Triggering only after the wait keeps the
+// order transitive: when kernel i+1 starts, kernel i-1 has completed.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                                    cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 inline int num_sms() {
   static int sms = 0;
   if (!sms) {

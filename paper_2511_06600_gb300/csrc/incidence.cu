@@ -376,6 +376,21 @@ __global__ void k_edge_fill(int m, int clique_mode, const int64_t* __restrict__ 
   }
 }
 
+// Window table: hyperedge e (thread, e in [0, m], ceptr[m] = P) is the first
+// of the windows w with ceptr[e-1] < w kWinSlots <= ceptr[e]; the windows
+// past ceptr[m] (only the last one when P is not a multiple) get m.
+__global__ void k_windows(int m, long long P, const int32_t* __restrict__ ceptr,
+                          const unsigned int* status, int32_t* win_edge) {
+  if (status[0]) return;
+  const long long nwin = num_windows(P);
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e <= m;
+       e += (long long)gridDim.x * blockDim.x) {
+    const long long lo = e == 0 ? 0 : (long long)ceptr[e - 1] / kWinSlots + 1;
+    const long long hi = e == m ? nwin : (long long)ceptr[e] / kWinSlots;
+    for (long long w = lo; w <= hi && w <= nwin; ++w) win_edge[w] = (int32_t)e;
+  }
+}
+
 // flags of hyperedges with more than kBigEdge pins (internal order)
 __global__ void k_big_flags(int m, const int32_t* __restrict__ ceptr, const unsigned int* status,
                             int* flags) {
@@ -485,6 +500,7 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   L->h.slot_edge = c.take<int32_t>(P > 0 ? P : 1);
   L->h.big_idx = c.take<int32_t>(m > 0 ? m : 1);
   L->h.big_pos = c.take<int32_t>(m + 1);
+  L->h.win_edge = c.take<int32_t>(num_windows(P) + 1);
   L->h.ew = c.take<double>(m > 0 ? m : 1);
   L->h.ewh = c.take<double>(m > 0 ? m : 1);
   L->h.ez = c.take<double>(m > 0 ? m : 1);
@@ -607,12 +623,16 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
                                                                         h->big_pos));
     HEF_TRY_CUDA(cudaGetLastError());
     HEF_TRY(exclusive_scan(h->big_pos, h->big_pos, m, L.scan_bsum, st));
+    HEF_LAUNCH("k_windows", st, k_windows<<<stride_grid(m + 1), kThreads, 0, st>>>(
+                                    (int)m, P, h->ceptr, h->status, h->win_edge));
+    HEF_TRY_CUDA(cudaGetLastError());
     HEF_LAUNCH("k_big_scatter", st, k_big_scatter<<<grid, kThreads, 0, st>>>(
                                         (int)m, h->ceptr, h->big_pos, h->status, h->big_idx));
     HEF_TRY_CUDA(cudaGetLastError());
   } else {
     HEF_TRY_CUDA(cudaMemsetAsync(h->ceptr, 0, sizeof(int32_t), st));
     HEF_TRY_CUDA(cudaMemsetAsync(h->big_pos, 0, sizeof(int32_t), st));
+    HEF_TRY_CUDA(cudaMemsetAsync(h->win_edge, 0, sizeof(int32_t) * (num_windows(P) + 1), st));
     HEF_TRY_CUDA(cudaMemsetAsync(h->totals, 0, 8 * sizeof(double), st));
   }
   // 3. vertex-major transpose: stable sort of CSC slots by vertex

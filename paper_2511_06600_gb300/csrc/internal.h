@@ -18,6 +18,7 @@ struct hef_incidence {
   int32_t* slot_edge = nullptr;     // P: internal hyperedge of each CSC slot
   int32_t* big_idx = nullptr;       // m: internal ids of hyperedges with > 64 pins
   int32_t* big_pos = nullptr;       // m+1: exclusive scan of the big flags; [m] = count
+  int32_t* win_edge = nullptr;      // nwin+1: first hyperedge of each window of CSC slots
   double* ew = nullptr;             // m: w_e, 0 when |e| < 2
   double* ewh = nullptr;            // m: clique pair weight, 0 when |e| < 2
   double* ez = nullptr;             // m: star weight w_e/|e|, 0 when |e| < 2
@@ -45,6 +46,15 @@ namespace hef {
 
 constexpr int kBigEdge = 64;  // hyperedges with more pins are scored by a whole CTA
 
+// Windows of CSC slots for the staged scoring pass: window w covers slots
+// [w kWinSlots, (w+1) kWinSlots) and owns the hyperedges whose first slot lies
+// in it; win_edge[w] = min{e : ceptr[e] >= w kWinSlots} (internal order, m
+// past the end), for w = 0..nwin with nwin = ceil(P / kWinSlots).  The pins of
+// a window's hyperedges with at most kBigEdge pins lie in fewer than
+// kWinSlots + kBigEdge consecutive slots from its first hyperedge's.
+constexpr int kWinSlots = 96;
+__host__ __device__ inline long long num_windows(long long P) { return (P + kWinSlots - 1) / kWinSlots; }
+
 // Kernel-side view of the incidence (passed by value to kernels).
 struct IncView {
   int n, m, P;
@@ -52,6 +62,7 @@ struct IncView {
   const int32_t* perm;
   const int32_t* big_idx;
   const int32_t* big_pos;
+  const int32_t* win_edge;
   const int32_t* ceptr;
   const int32_t* cpins;
   const double* ew;
@@ -77,6 +88,7 @@ inline IncView view(const hef_incidence* h) {
   v.perm = h->perm;
   v.big_idx = h->big_idx;
   v.big_pos = h->big_pos;
+  v.win_edge = h->win_edge;
   v.ceptr = h->ceptr;
   v.cpins = h->cpins;
   v.ew = h->ew;

@@ -339,6 +339,8 @@ template <typename T, int S>
 __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T> sv, KView<T> kv,
                                                           const double* __restrict__ x0c,
                                                           const double* __restrict__ x0b) {
+  pdl_wait();
+  pdl_trigger();
   if (g.status[0]) return;
   const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   T acc[2][S];
@@ -651,6 +653,8 @@ __device__ __forceinline__ void zero_acc(T (&acc)[NQ][S]) {
 template <typename T, int S>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5))
     k_edge_pass(IncView g, ScalView<T> sv, KView<T> kv, int j) {
+  pdl_wait();
+  pdl_trigger();
   if (g.status[0]) return;
   T acc[3][S];
   zero_acc(acc);
@@ -665,6 +669,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5))
 template <typename T, int S>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
     k_node_pass(IncView g, ScalView<T> sv, KView<T> kv, int j, T* __restrict__ V, long long ldv) {
+  pdl_wait();
+  pdl_trigger();
   if (g.status[0]) return;
   T acc[6][S];
   zero_acc(acc);
@@ -679,6 +685,8 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
 template <typename T, int S>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
     k_update(IncView g, ScalView<T> sv, KView<T> kv, int j) {
+  pdl_wait();
+  pdl_trigger();
   if (g.status[0]) return;
   T acc[2][S];
   zero_acc(acc);
@@ -693,6 +701,7 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
 template <typename T, int S>
 __global__ void __launch_bounds__(kThreads) k_archive_last(IncView g, KView<T> kv, int k,
                                                            T* __restrict__ V, long long ldv) {
+  pdl_wait();
   if (g.status[0]) return;
   archive_item<T, S>(g, kv, k, blockIdx.x * blockDim.x + threadIdx.x, V, ldv);
 }
@@ -827,7 +836,11 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   const int grid_n = blocks_for(n);
   const int grid_upd = blocks_for((2 * n + m + upd_rows<T, S>() - 1) / upd_rows<T, S>());
   HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
-  HEF_LAUNCH("k_start_write", st, k_start_write<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
+  // the launches after the first are programmatically dependent on their
+  // predecessor (each kernel waits for it before touching shared buffers)
+  HEF_LAUNCH("k_start_write", st,
+             HEF_CHECK_CUDA(launch_dependent(k_start_write<T, S>, grid_all, kThreads, st, g, sv,
+                                             kv, x0c, x0b)));
   HEF_CHECK_LAUNCH();
   // one launch for all steps when every row of a pass has a resident thread
   // of its own (small hypergraphs, where per-step launches cost more than the
@@ -843,12 +856,18 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
     return HEF_OK;
   }
   for (int j = 1; j <= k; ++j) {
-    HEF_LAUNCH("k_edge_pass", st, k_edge_pass<T, S><<<grid_e, kThreads, 0, st>>>(g, sv, kv, j));
-    HEF_LAUNCH("k_node_pass", st, k_node_pass<T, S><<<grid_n, kThreads, 0, st>>>(g, sv, kv, j, V, ldv));
-    HEF_LAUNCH("k_update", st, k_update<T, S><<<grid_upd, kThreads, 0, st>>>(g, sv, kv, j));
+    HEF_LAUNCH("k_edge_pass", st,
+               HEF_CHECK_CUDA(launch_dependent(k_edge_pass<T, S>, grid_e, kThreads, st, g, sv, kv, j)));
+    HEF_LAUNCH("k_node_pass", st,
+               HEF_CHECK_CUDA(launch_dependent(k_node_pass<T, S>, grid_n, kThreads, st, g, sv, kv,
+                                               j, V, ldv)));
+    HEF_LAUNCH("k_update", st,
+               HEF_CHECK_CUDA(launch_dependent(k_update<T, S>, grid_upd, kThreads, st, g, sv, kv, j)));
     HEF_CHECK_LAUNCH();
   }
-  HEF_LAUNCH("k_archive_last", st, k_archive_last<T, S><<<grid_n, kThreads, 0, st>>>(g, kv, k, V, ldv));
+  HEF_LAUNCH("k_archive_last", st,
+             HEF_CHECK_CUDA(launch_dependent(k_archive_last<T, S>, grid_n, kThreads, st, g, kv, k,
+                                             V, ldv)));
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }

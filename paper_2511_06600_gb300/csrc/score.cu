@@ -12,17 +12,20 @@
 // across warps and CTAs in a fixed order); pass 2 recomputes the spreads and
 // takes the max with its arg-max column and the pins that realise it.
 #include <cfloat>
+#include <cstring>
 #include <mutex>
 
 #include "internal.h"
+#include "umma.cuh"
 
 namespace hef {
 
 namespace {
 
 constexpr double kQhTiny = 1e-300;
-constexpr int kFlushEdges = 32;  // FP32 form: edges per FP32 partial sum
 constexpr int kGroup1 = 8;      // hyperedges per warp task in pass 1
+constexpr int kMaxStages = 4;    // stages of the staged pass 1
+constexpr size_t kStageSmem = 200 * 1024;  // shared memory for its stages
 constexpr int kPinStage = 96;   // pins of a pass-1 task staged in shared memory
 constexpr int kWorkSlot = 60;    // counters [60], [61]: work distribution of the passes
 
@@ -141,7 +144,7 @@ __device__ __forceinline__ void cta_edge_extrema(const T* __restrict__ Q, long l
 // sum of w_e spread^2 per column goes to bpart[b][col] (FP64).
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restrict__ Q, long long ldq,
-                                                    int K, double* bpart, T* spread) {
+                                                    int K, double* bpart, T* spread, int ldsp) {
   if (g.status[0]) return;
   __shared__ T smx[8 * 32 * NC], smn[8 * 32 * NC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -159,7 +162,7 @@ __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restri
       const double sp = (double)(mx[c] - mn[c]);
       acc[c] += we * sp * sp;
       if (spread && wid == 0 && lane + 32 * c < K)
-        spread[(long long)(lane + 32 * c) * g.m + e] = mx[c] - mn[c];
+        spread[(long long)e * ldsp + lane + 32 * c] = mx[c] - mn[c];
     }
   }
   if (wid == 0) {
@@ -169,20 +172,38 @@ __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restri
   }
 }
 
-// Pass 1, hyperedges with 2..kBigEdge pins: warp per group of 32 consecutive
-// hyperedges (two at a time); Q_H[i] = sum of per-CTA partials, then the
-// large hyperedges' partials bpart, in a fixed order.
+// Q_H from the per-CTA partials (K per CTA, already in red.part) and the large
+// hyperedges' partials, in a fixed order; run by the CTA that completes the
+// grid reduction.
+template <int NC>
+__device__ __forceinline__ void finish_qh(const GridRed& red, int K, const double* __restrict__ bpart,
+                                          int nbpart, double* QH, double* invQH, double* QH_out) {
+  __shared__ double tot[32 * NC];
+  if (grid_reduce(red, K, tot)) {
+    for (int col = threadIdx.x; col < K; col += blockDim.x) {
+      double s = tot[col];
+      for (int q = 0; q < nbpart; ++q) s += bpart[(size_t)q * K + col];
+      QH[col] = s;
+      invQH[col] = s > kQhTiny ? 1.0 / s : 0.0;
+      if (QH_out) QH_out[col] = s;
+    }
+  }
+}
+
+// Pass 1, hyperedges with 2..kBigEdge pins, rows of Q gathered by the warps:
+// warp per group of kGroup1 consecutive hyperedges (two at a time), their
+// spreads stored row-major (spread[e K + i]) when `spread` is given; Q_H[i] =
+// sum of per-CTA partials, then the large hyperedges' partials bpart, in a
+// fixed order.
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restrict__ Q, long long ldq,
                                                      int K, GridRed red, const double* __restrict__ bpart,
                                                      int nbpart, double* QH, double* invQH,
                                                      double* QH_out, unsigned int* work,
-                                                     T* spread) {
+                                                     T* spread, int ldsp) {
   if (g.status[0]) return;
   __shared__ double wred[kThreads / 32][32 * NC];
-  extern __shared__ unsigned char sp_raw[];  // spreads of the warp's group: kGroup1 x K
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  T* tile = reinterpret_cast<T*>(sp_raw) + (size_t)wid * kGroup1 * K;
   double acc[NC];
   T pacc[NC];
 #pragma unroll
@@ -209,7 +230,7 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
     auto pin_at = [&](int t) { return t - gp0 < npin ? spins[wid][t - gp0] : g.cpins[t]; };
     if (b - a < 2 || b - a > kBigEdge) b = a;  // not scored here
     const T wl = (lane < kGroup1 && e < g.m) ? (T)g.ew[e] : (T)0;
-    unsigned scored = 0u;  // hyperedges of the group whose spreads are in the tile
+    T* sprow = spread ? spread + grp * kGroup1 * ldsp : nullptr;  // row-major spreads of the group
     for (int i = 0; i < kGroup1; i += 2) {
       const int a0 = __shfl_sync(0xffffffffu, a, i), b0 = __shfl_sync(0xffffffffu, b, i);
       const int a1 = __shfl_sync(0xffffffffu, a, i + 1), b1 = __shfl_sync(0xffffffffu, b, i + 1);
@@ -217,33 +238,20 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
       if (a0 == b0 && a1 == b1) continue;
       T mx0[NC], mn0[NC], mx1[NC], mn1[NC];
       two_edge_extrema<T, NC>(Q, ldq, K, pin_at, a0, b0, a1, b1, lane, mx0, mn0, mx1, mn1);
-      if (b0 > a0) scored |= 1u << i;
-      if (b1 > a1) scored |= 2u << i;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int col = lane + 32 * c;
         if (b0 > a0) {
           const T sp = mx0[c] - mn0[c];
           pacc[c] += w0 * sp * sp;
-          if (spread && col < K) tile[i * K + col] = sp;
+          if (sprow && col < K) sprow[(long long)i * ldsp + col] = sp;
         }
         if (b1 > a1) {
           const T sp = mx1[c] - mn1[c];
           pacc[c] += w1 * sp * sp;
-          if (spread && col < K) tile[(i + 1) * K + col] = sp;
+          if (sprow && col < K) sprow[(long long)(i + 1) * ldsp + col] = sp;
         }
       }
-    }
-    // the group's spreads, column-major (spread[col][e]): each store of the
-    // warp covers kGroup1 consecutive hyperedges of 32 / kGroup1 columns
-    if (spread && scored) {
-      __syncwarp();
-      const long long eb = grp * kGroup1;
-      for (int idx = lane; idx < kGroup1 * K; idx += 32) {
-        const int col = idx / kGroup1, ee = idx % kGroup1;
-        if ((scored >> ee) & 1u) spread[(long long)col * g.m + eb + ee] = tile[ee * K + col];
-      }
-      __syncwarp();
     }
     // FP32 partial sums span one group (kGroup1 hyperedges); FP64 beyond
 #pragma unroll
@@ -257,16 +265,226 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += wred[w][col];
     red.part[(size_t)blockIdx.x * K + col] = s;
   }
-  __shared__ double tot[32 * NC];
-  if (grid_reduce(red, K, tot)) {
-    for (int col = threadIdx.x; col < K; col += blockDim.x) {
-      double s = tot[col];
-      for (int q = 0; q < nbpart; ++q) s += bpart[(size_t)q * K + col];
-      QH[col] = s;
-      invQH[col] = s > kQhTiny ? 1.0 / s : 0.0;
-      if (QH_out) QH_out[col] = s;
+  finish_qh<NC>(red, K, bpart, nbpart, QH, invQH, QH_out);
+}
+
+
+// Pass 1 with the pin rows staged in shared memory by bulk asynchronous
+// copies (the same sums as k_score_pass1).  CTA b takes the windows of CSC
+// slots b, b + grid, ... (see kWinSlots).  Warp 0 produces: for window i it
+// copies the Q rows of the slots from the window's first hyperedge to the end
+// of its last one (a trailing hyperedge with more than kBigEdge pins is left
+// to k_score_big1) into stage i mod nst (kStageRows rows of `pitch` elements,
+// `row_bytes` a multiple of 16), once the consumers have released that stage;
+// the window table, offsets and pin ids it needs are loaded three, two and
+// one windows ahead.  Warps 1..7 consume: each scores the window's
+// hyperedges w, w + 7, ... from shared memory, lanes over columns, its
+// hyperedges' offsets loaded before it waits for the stage.  Waits are
+// bounded: on expiry the kernel sets HEF_WAIT_TIMEOUT in `status`, stops,
+// waits (bounded) for the copies it issued and still takes part in the
+// reduction.
+constexpr int kStageRows = kWinSlots + kBigEdge;
+constexpr int kPinRegs = (kStageRows + 31) / 32;
+constexpr int kConsumers = kThreads / 32 - 1;
+constexpr uint32_t kCopyWaitIters = 1u << 20;
+
+template <typename T, int NC>
+__global__ void __launch_bounds__(256, 1)
+    k_score_pass1_bulk(IncView g, const T* __restrict__ Q, long long ldq, int K, int pitch,
+                       uint32_t row_bytes, int nst, GridRed red, const double* __restrict__ bpart,
+                       int nbpart, double* QH, double* invQH, double* QH_out, T* spread,
+                       int ldsp, unsigned int* status) {
+  using namespace umma;
+  if (g.status[0]) return;
+  extern __shared__ __align__(128) unsigned char stage_raw[];
+  T* stages = reinterpret_cast<T*>(stage_raw);
+  __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
+  __shared__ int meta[kMaxStages][2];  // first slot and row count of the staged window
+  __shared__ int abort_flag;
+  __shared__ long long issued;
+  __shared__ double wred[kThreads / 32][32 * NC];
+  volatile int* abort_v = &abort_flag;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const long long nwin = num_windows(g.P);
+  const long long G = gridDim.x;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < nst; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kConsumers);
+    }
+    abort_flag = 0;
+    issued = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  double acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = 0.0;
+  auto fail = [&]() {
+    if (lane == 0) {
+      *abort_v = 1;
+      atomicOr(&status[0], HEF_WAIT_TIMEOUT);
+    }
+  };
+  if (wid == 0) {
+    // ---- producer: window table (i + 3) -> slots (i + 2) -> pins (i + 1) -> copies (i)
+    struct Edges { int ef, el; };
+    struct Slots { int s0, rows; };
+    auto edges_of = [&](long long i) {
+      const long long w = blockIdx.x + i * G;
+      Edges x{0, 0};
+      if (w < nwin) x.ef = g.win_edge[w], x.el = g.win_edge[w + 1];
+      return x;
+    };
+    auto slots_of = [&](Edges x) {
+      Slots y{0, 0};
+      if (x.el > x.ef) {
+        y.s0 = g.ceptr[x.ef];
+        int s1 = g.ceptr[x.el];
+        const int sl = g.ceptr[x.el - 1];
+        if (s1 - sl > kBigEdge) s1 = sl;
+        y.rows = min(max(s1 - y.s0, 0), kStageRows);
+      }
+      return y;
+    };
+    auto pins_of = [&](Slots y, int (&pin)[kPinRegs]) {
+#pragma unroll
+      for (int j = 0; j < kPinRegs; ++j) {
+        const int r = lane + 32 * j;
+        pin[j] = r < y.rows ? g.cpins[y.s0 + r] : 0;
+      }
+    };
+    Edges a2 = edges_of(2);
+    Slots b1 = slots_of(edges_of(1));
+    Slots b0 = slots_of(edges_of(0));
+    int p0[kPinRegs];
+    pins_of(b0, p0);
+    long long i = 0;
+    for (; blockIdx.x + i * G < nwin; ++i) {
+      if (*abort_v) break;
+      const Edges a3 = edges_of(i + 3);
+      const Slots b2 = slots_of(a2);
+      int p1[kPinRegs];
+      pins_of(b1, p1);
+      const int q = (int)(i % nst);
+      if (i >= nst) {
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(&empty[q], (uint32_t)((i / nst - 1) & 1),
+                                                          kCopyWaitIters));
+        if (!ok) {
+          fail();
+          break;
+        }
+      }
+      if (lane == 0) {
+        meta[q][0] = b0.s0;
+        meta[q][1] = b0.rows;
+        mbar_arrive_expect_tx(&full[q], (uint32_t)b0.rows * row_bytes);
+      }
+      __syncwarp();
+      T* dst = stages + (size_t)q * kStageRows * pitch;
+#pragma unroll
+      for (int j = 0; j < kPinRegs; ++j) {
+        const int r = lane + 32 * j;
+        if (r < b0.rows) bulk_g2s(dst + (size_t)r * pitch, Q + (long long)p0[j] * ldq, row_bytes, &full[q]);
+      }
+      b0 = b1;
+      b1 = b2;
+      a2 = a3;
+#pragma unroll
+      for (int j = 0; j < kPinRegs; ++j) p0[j] = p1[j];
+    }
+    if (lane == 0) issued = i;
+  } else {
+    // ---- consumers
+    const int cw = wid - 1;
+    int nef = 0, nel = 0;  // hyperedges of the next window
+    if (blockIdx.x < nwin) nef = g.win_edge[blockIdx.x], nel = g.win_edge[blockIdx.x + 1];
+    for (long long i = 0; blockIdx.x + i * G < nwin; ++i) {
+      const int ef = nef, el = nel;
+      // offsets and weights of this warp's first 32 hyperedges of the window
+      int ea = 0, eb = 0;
+      T ewl = 0;
+      {
+        const int e = ef + cw + kConsumers * lane;
+        if (e < el) ea = g.ceptr[e], eb = g.ceptr[e + 1], ewl = (T)g.ew[e];
+      }
+      const long long wn = blockIdx.x + (i + 1) * G;
+      if (wn < nwin) nef = g.win_edge[wn], nel = g.win_edge[wn + 1];
+      const int q = (int)(i % nst);
+      const bool got =
+          __all_sync(0xffffffffu, mbar_wait(&full[q], (uint32_t)((i / nst) & 1), kCopyWaitIters));
+      if (!got || *abort_v) {
+        if (!got) fail();
+        break;
+      }
+      const int s0 = meta[q][0], rows = meta[q][1];
+      const T* st = stages + (size_t)q * kStageRows * pitch;
+      T pacc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) pacc[c] = 0;
+      for (int base = ef + cw; base < el; base += kConsumers * 32) {
+        if (base != ef + cw) {  // hyperedges past this warp's first 32 (long runs of empty ones)
+          const int e = base + kConsumers * lane;
+          ea = eb = 0;
+          ewl = 0;
+          if (e < el) ea = g.ceptr[e], eb = g.ceptr[e + 1], ewl = (T)g.ew[e];
+        }
+        const int cnt = min(32, (el - base + kConsumers - 1) / kConsumers);
+        for (int jj = 0; jj < cnt; ++jj) {
+          const int e = base + kConsumers * jj;
+          const int a = __shfl_sync(0xffffffffu, ea, jj) - s0;
+          const int b = __shfl_sync(0xffffffffu, eb, jj) - s0;
+          const T we = __shfl_sync(0xffffffffu, ewl, jj);
+          if (b - a < 2 || b - a > kBigEdge || a < 0 || b > rows) continue;
+          T mx[NC], mn[NC];
+#pragma unroll
+          for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
+          for (int r = a; r < b; r += 4) {
+            const int r1 = min(r + 1, b - 1), r2 = min(r + 2, b - 1), r3 = min(r + 3, b - 1);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) {
+              const int col = lane + 32 * c;
+              if (col < K) {
+                const T v0 = st[(size_t)r * pitch + col], v1 = st[(size_t)r1 * pitch + col];
+                const T v2 = st[(size_t)r2 * pitch + col], v3 = st[(size_t)r3 * pitch + col];
+                mx[c] = fmax(fmax(mx[c], fmax(v0, v1)), fmax(v2, v3));
+                mn[c] = fmin(fmin(mn[c], fmin(v0, v1)), fmin(v2, v3));
+              }
+            }
+          }
+#pragma unroll
+          for (int c = 0; c < NC; ++c) {
+            const int col = lane + 32 * c;
+            const T sp = mx[c] - mn[c];
+            if (col < K) {
+              pacc[c] += we * sp * sp;
+              if (spread) spread[(long long)e * ldsp + col] = sp;
+            }
+          }
+        }
+      }
+      // FP32 partial sums span one window; FP64 beyond
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] += (double)pacc[c];
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[q]);
     }
   }
+  __syncthreads();
+  if (abort_flag && threadIdx.x == 0) {
+    // copies of the last nst issued windows may still be in flight
+    for (long long j = issued > nst ? issued - nst : 0; j < issued; ++j)
+      mbar_wait(&full[j % nst], (uint32_t)((j / nst) & 1), kCopyWaitIters);
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) wred[wid][lane + 32 * c] = acc[c];
+  __syncthreads();
+  for (int col = threadIdx.x; col < K; col += blockDim.x) {
+    double sum = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += wred[w][col];
+    red.part[(size_t)blockIdx.x * K + col] = sum;
+  }
+  finish_qh<NC>(red, K, bpart, nbpart, QH, invQH, QH_out);
 }
 
 // Pass 2 for one hyperedge whose extrema a warp holds (lanes over columns):
@@ -422,21 +640,26 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
   }
 }
 
-// Pass 2 from the spreads that pass 1 stored column-major (spread[i][e]; every
-// hyperedge with >= 2 pins has them): thread per hyperedge, so that each load
-// of a warp reads 32 consecutive hyperedges of one column.  Ratios and the
-// arg-max column in the working type as in Eq. ratios (lowest column on
-// ties); R_e from the spread in FP64; the routing pins by one gather of the
-// arg-max column over the hyperedge's pins (lowest position on ties).  Gives
-// exactly what k_score_pass2 / k_score_big2 give, without gathering every
-// column of Q again.
+// Pass 2 from the spreads that pass 1 stored (row-major, spread[e ldsp + i],
+// rows 16-byte aligned; every hyperedge with >= 2 pins has them): thread per
+// hyperedge, its row read with 16-byte loads, kRatioVecs of them in flight.
+// Ratios and the arg-max column in the working type as in Eq. ratios (lowest
+// column on ties); R_e from the spread in FP64; the routing pins from one
+// gather of the arg-max column over the hyperedge's pins (lowest position on
+// ties).  Gives exactly what k_score_pass2 / k_score_big2 give without
+// gathering every column of Q again.
+constexpr int kRatioVecs = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restrict__ Q, long long ldq,
                                                      int K, int reduce, const double* __restrict__ QH,
                                                      const double* __restrict__ invQH,
-                                                     const T* __restrict__ spread, double* R_out,
-                                                     int32_t* argvec, int32_t* pmax, int32_t* pmin) {
+                                                     const T* __restrict__ spread, int ldsp,
+                                                     double* R_out, int32_t* argvec, int32_t* pmax,
+                                                     int32_t* pmin) {
   if (g.status[0]) return;
+  constexpr int V = 16 / sizeof(T);  // elements per 16-byte load
+  constexpr int B = V * kRatioVecs;  // columns per batch
   extern __shared__ unsigned char iq_raw[];
   T* iq = reinterpret_cast<T*>(iq_raw);  // K: 1 / Q_H in the working type, 0 when unused
   for (int i = threadIdx.x; i < K; i += blockDim.x) iq[i] = QH[i] > kQhTiny ? (T)invQH[i] : (T)0;
@@ -452,19 +675,29 @@ __global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restr
       if (pmin) pmin[oe] = -1;
       continue;
     }
+    const uint4* row = reinterpret_cast<const uint4*>(spread + e * ldsp);
     T best = (T)-1, spb = 0;
     int bcol = -1;
     double sum = 0.0;
-    const T* col = spread + e;
-    for (int i = 0; i < K; ++i, col += g.m) {
-      if (iq[i] == (T)0) continue;
-      const T sp = *col;
-      const T r = sp * sp * iq[i];
-      if (reduce == HEF_REDUCE_SUM) {
-        const double spd = (double)sp;
-        sum += spd * spd / QH[i];
+    for (int i0 = 0; i0 < K; i0 += B) {
+      T sp[B];
+#pragma unroll
+      for (int u = 0; u < kRatioVecs; ++u) {
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (i0 + u * V < K) v = __ldg(row + i0 / V + u);
+        memcpy(&sp[u * V], &v, 16);
       }
-      if (r > best) best = r, bcol = i, spb = sp;
+#pragma unroll
+      for (int q = 0; q < B; ++q) {
+        const int i = i0 + q;
+        if (i >= K || iq[i] == (T)0) continue;
+        const T r = sp[q] * sp[q] * iq[i];
+        if (reduce == HEF_REDUCE_SUM) {
+          const double spd = (double)sp[q];
+          sum += spd * spd / QH[i];
+        }
+        if (r > best) best = r, bcol = i, spb = sp[q];
+      }
     }
     const bool any = bcol >= 0;
     int tmax = a, tmin = a;
@@ -502,8 +735,14 @@ struct ScoreWs {
   int bgrid;
 };
 
-// Workspace of hef_edge_resistance; the spreads take 8-byte slots whatever
-// the dtype (the size query does not know it).
+// Row pitch (elements) of the stored spreads: K rounded up to 16 bytes.
+inline int spread_ld(int K, size_t esz) {
+  const int v = (int)(16 / esz);
+  return (K + v - 1) / v * v;
+}
+
+// Workspace of hef_edge_resistance; the spread rows take the FP32 pitch in
+// 8-byte slots, enough for either dtype (the size query does not know it).
 size_t carve_score(void* base, int K, long long m, ScoreWs* w) {
   Carver c(base);
   w->grid = num_sms() * 4;
@@ -514,7 +753,7 @@ size_t carve_score(void* base, int K, long long m, ScoreWs* w) {
   w->gpart = c.take<double>((size_t)red_groups(w->grid) * K);
   w->bgrid = num_sms();
   w->bpart = c.take<double>((size_t)w->bgrid * K);
-  w->spread = c.take<double>((size_t)(m > 0 ? m : 1) * K);
+  w->spread = c.take<double>((size_t)(m > 0 ? m : 1) * spread_ld(K, sizeof(float)));
   return c.bytes();
 }
 
@@ -528,26 +767,38 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
   red.gpart = w.gpart;
   red.gcnt = w.counter;                 // red_groups(grid) <= 63 counters
   red.tcnt = w.counter + 63;
-  // grids of co-resident CTAs only (work is handed out dynamically)
-  const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
+  // grids of co-resident CTAs only
   const int g2 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass2<T, NC>, kThreads));
-  // spreads kept for pass 2 when the workspace has them and the staging tile
-  // of pass 1 (kGroup1 x K per warp) is small enough not to cut the pass's
-  // occupancy (K <= 192 in FP32); larger K gather Q again in pass 2
-  const size_t tile_bytes = (size_t)(kThreads / 32) * kGroup1 * K * sizeof(T);
-  T* spread = (w.spread && tile_bytes <= 48 * 1024) ? static_cast<T*>(w.spread) : nullptr;
-  const size_t smem1 = spread ? tile_bytes : 0;
-  if (spread) HEF_ENSURE_SMEM((k_score_pass1<T, NC>), (int)smem1);
+  T* spread = static_cast<T*>(w.spread);
+  const int ldsp = spread_ld(K, sizeof(T));
   HEF_LAUNCH("k_score_big1", st, k_score_big1<T, NC><<<w.bgrid, kThreads, 0, st>>>(g, Q, ldq, K, w.bpart,
-                                                                                   spread));
-  HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<g1, kThreads, smem1, st>>>(
-                                      g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out,
-                                      w.counter + kWorkSlot, spread));
+                                                                                   spread, ldsp));
+  // pass 1 staged through shared memory when the rows can be bulk-copied
+  // (16-byte aligned rows; a row pitch of 16-byte multiples) and at least two
+  // stages fit; otherwise the warps gather the rows
+  const uint32_t row_bytes = (uint32_t)(((size_t)K * sizeof(T) + 15) / 16 * 16);
+  const size_t stage_bytes = (size_t)kStageRows * row_bytes;
+  const int nst = (int)std::min<size_t>(kMaxStages, kStageSmem / stage_bytes);
+  const bool bulk = (reinterpret_cast<uintptr_t>(Q) % 16 == 0) && ((size_t)ldq * sizeof(T)) % 16 == 0 &&
+                    nst >= 2 && num_sms() <= w.grid;
+  if (bulk) {
+    HEF_ENSURE_SMEM((k_score_pass1_bulk<T, NC>), (int)(nst * stage_bytes));
+    const size_t smem = nst * stage_bytes;
+    HEF_LAUNCH("k_score_pass1", st,
+               k_score_pass1_bulk<T, NC><<<num_sms(), kThreads, smem, st>>>(
+                   g, Q, ldq, K, (int)(row_bytes / sizeof(T)), row_bytes, nst, red, w.bpart,
+                   w.bgrid, w.QH, w.invQH, QH_out, spread, ldsp, inc->status));
+  } else {
+    const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
+    HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<g1, kThreads, 0, st>>>(
+                                        g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out,
+                                        w.counter + kWorkSlot, spread, ldsp));
+  }
   if (spread) {
     const int g3 = stride_grid(inc->m > 0 ? inc->m : 1, 8);
     HEF_LAUNCH("k_score_ratio", st, k_score_ratio<T><<<g3, kThreads, K * sizeof(T), st>>>(
-                                        g, Q, ldq, K, reduce, w.QH, w.invQH, spread, R_out, argvec,
-                                        pmax, pmin));
+                                        g, Q, ldq, K, reduce, w.QH, w.invQH, spread, ldsp, R_out,
+                                        argvec, pmax, pmin));
     HEF_CHECK_LAUNCH();
     return HEF_OK;
   }

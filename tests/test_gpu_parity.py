@@ -215,6 +215,47 @@ def test_edge_resistance_on_oracle_basis(K):
     assert np.all(got["R"][sizes < 2] == 0) and np.all(got["argvec"][sizes < 2] == -1)
 
 
+@pytest.mark.parametrize("dtype", [torch.float64, torch.float32])
+@pytest.mark.parametrize("K,pad", [(20, 0), (20, 1), (33, 0), (160, 0)])
+def test_edge_resistance_window_boundaries(dtype, K, pad):
+    """Hyperedges of 0 to 200 pins (runs of empty ones; sizes around the 64
+    pins a warp scores and the 96-slot windows the staged pass 1 copies),
+    scored from shared-memory stages (16-byte row pitch) and by the gathering
+    pass 1 (pad = 1: a pitch that is not a multiple of 16 bytes), against the
+    oracle on the same Q."""
+    rng = np.random.default_rng(100 * K + pad)
+    n = 1500
+    choices = np.array([0, 1, 2, 3, 5, 8, 40, 64, 65, 95, 96, 97, 200])
+    prob = np.array([8, 4, 30, 20, 12, 8, 5, 3, 3, 2, 2, 2, 1], float)
+    sizes = rng.choice(choices, size=700, p=prob / prob.sum())
+    edges = [list(rng.choice(n, size=int(k), replace=False)) for k in sizes]
+    H = from_lists(n, edges, rng.uniform(0.5, 2.0, size=len(edges)))
+    Q = rng.standard_normal((n, K))
+    if dtype == torch.float32:
+        Q = Q.astype(np.float32).astype(np.float64)
+    h = hef()
+    t = to_dev(H)
+    inc = h.build_incidence(H.n, t["eptr"], t["pins"], t["w"])
+    ld = h.padded_ld(K, dtype) + pad
+    Qd = torch.zeros(n, ld, dtype=dtype, device=DEV)
+    Qd[:, :K] = torch.from_numpy(Q).to(dtype).to(DEV)
+    out = h.edge_resistance(inc, Qd, K)
+    inc.check()
+    got = {k: v.cpu().numpy() for k, v in out.items()}
+    ref = O.edge_resistance(Q, H.eptr, H.pins, H.w)
+    # FP32: spreads are FP32 differences, Q_H partial sums FP32 per window
+    rtol, sep_tol = (1e-12, 1e-9) if dtype == torch.float64 else (1e-5, 1e-4)
+    assert np.allclose(got["QH"], ref["QH"], rtol=rtol, atol=0)
+    assert np.allclose(got["R"], ref["R"], rtol=rtol, atol=0)
+    r = np.where(ref["use"][None, :], ref["r"], -1)
+    srt = np.sort(r, axis=1)
+    sep = srt[:, -1] - srt[:, -2] > sep_tol * np.abs(srt[:, -1])
+    assert sep.sum() > 0.9 * (sizes >= 2).sum()
+    for key in ("argvec", "pmax", "pmin"):
+        assert np.array_equal(got[key][sep], ref[key][sep]), key
+    assert np.all(got["R"][sizes < 2] == 0) and np.all(got["argvec"][sizes < 2] == -1)
+
+
 def test_edge_resistance_eigenbasis_closed_form():
     """Eq. eff_resist0 through the GPU scorer: 2-pin graph, Laplacian
     eigenvectors as the basis, summed ratios = pseudo-inverse resistance and
