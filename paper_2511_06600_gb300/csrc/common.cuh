@@ -215,7 +215,8 @@ struct GridRed {
   unsigned int* tcnt;  // 1 counter
 };
 
-// In one CTA of kThreads threads: out[slot] = sum over q < nq of
+// In one CTA of at least kThreads threads (the first kThreads work, all
+// take part in the barriers): out[slot] = sum over q < nq of
 // src[q * nslot + slot] for every slot < nslot.  P threads share a slot (each
 // sums a fixed strided subset of q in order), then a fixed shared-memory tree
 // combines them: the result does not depend on scheduling.  Ends synced.
@@ -223,6 +224,7 @@ __device__ __forceinline__ void block_sum_columns(const double* __restrict__ src
                                                   double* out) {
   __shared__ double buf[kThreads];
   const int T = kThreads, t = threadIdx.x;
+  const bool act = t < T;
   int P = 1;
   if (nslot > 32) {
     P = 8;
@@ -233,7 +235,7 @@ __device__ __forceinline__ void block_sum_columns(const double* __restrict__ src
   for (int c0 = 0; c0 < nslot; c0 += C) {
     const int slot = c0 + t % C, p = t / C;
     double acc = 0.0;
-    if (slot < nslot) {
+    if (act && slot < nslot) {
       int q = p;
       for (; q + 3 * P < nq; q += 4 * P) {
         const double v0 = __ldcg(src + (size_t)q * nslot + slot);
@@ -247,13 +249,13 @@ __device__ __forceinline__ void block_sum_columns(const double* __restrict__ src
       }
       for (; q < nq; q += P) acc += __ldcg(src + (size_t)q * nslot + slot);
     }
-    buf[t] = acc;
+    if (act) buf[t] = acc;
     __syncthreads();
     for (int h = P / 2; h >= 1; h >>= 1) {
-      if (p < h) buf[t] += buf[t + h * C];
+      if (act && p < h) buf[t] += buf[t + h * C];
       __syncthreads();
     }
-    if (p == 0 && slot < nslot) out[slot] = buf[t];
+    if (act && p == 0 && slot < nslot) out[slot] = buf[t];
     __syncthreads();
   }
 }

@@ -49,10 +49,10 @@ constexpr int kBigEdge = 64;  // hyperedges with more pins are scored by a whole
 // Windows of CSC slots for the staged scoring pass: window w covers slots
 // [w kWinSlots, (w+1) kWinSlots) and owns the hyperedges whose first slot lies
 // in it; win_edge[w] = min{e : ceptr[e] >= w kWinSlots} (internal order, m
-// past the end), for w = 0..nwin with nwin = ceil(P / kWinSlots).  The pins of
-// a window's hyperedges with at most kBigEdge pins lie in fewer than
-// kWinSlots + kBigEdge consecutive slots from its first hyperedge's.
-constexpr int kWinSlots = 96;
+// past the end), for w = 0..nwin with nwin = ceil(P / kWinSlots).  A
+// hyperedge with at most kBigEdge <= kWinSlots pins ends within the window
+// after its own.
+constexpr int kWinSlots = 64;
 __host__ __device__ inline long long num_windows(long long P) { return (P + kWinSlots - 1) / kWinSlots; }
 
 // Kernel-side view of the incidence (passed by value to kernels).

@@ -11,6 +11,9 @@
 // Q is one coalesced read.  Pass 1 reduces Q_H (per-warp partials, FP64
 // across warps and CTAs in a fixed order); pass 2 recomputes the spreads and
 // takes the max with its arg-max column and the pins that realise it.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include <cfloat>
 #include <cstring>
 #include <mutex>
@@ -24,8 +27,9 @@ namespace {
 
 constexpr double kQhTiny = 1e-300;
 constexpr int kGroup1 = 8;      // hyperedges per warp task in pass 1
-constexpr int kMaxStages = 4;    // stages of the staged pass 1
-constexpr size_t kStageSmem = 200 * 1024;  // shared memory for its stages
+constexpr int kMaxStages = 8;    // stages of the staged pass 1
+constexpr size_t kStageSmem = 220 * 1024;  // shared memory per CTA for its stages and the rest
+constexpr size_t kMaxSmemOptin = 227 * 1024;  // per-CTA limit of the sm_100 family
 constexpr int kPinStage = 96;   // pins of a pass-1 task staged in shared memory
 constexpr int kWorkSlot = 60;    // counters [60], [61]: work distribution of the passes
 
@@ -270,50 +274,63 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
 
 
 // Pass 1 with the pin rows staged in shared memory by bulk asynchronous
-// copies (the same sums as k_score_pass1).  CTA b takes the windows of CSC
-// slots b, b + grid, ... (see kWinSlots).  Warp 0 produces: for window i it
-// copies the Q rows of the slots from the window's first hyperedge to the end
-// of its last one (a trailing hyperedge with more than kBigEdge pins is left
-// to k_score_big1) into stage i mod nst (kStageRows rows of `pitch` elements,
-// `row_bytes` a multiple of 16), once the consumers have released that stage;
-// the window table, offsets and pin ids it needs are loaded three, two and
-// one windows ahead.  Warps 1..7 consume: each scores the window's
-// hyperedges w, w + 7, ... from shared memory, lanes over columns, its
-// hyperedges' offsets loaded before it waits for the stage.  Waits are
-// bounded: on expiry the kernel sets HEF_WAIT_TIMEOUT in `status`, stops,
-// waits (bounded) for the copies it issued and still takes part in the
-// reduction.
-constexpr int kStageRows = kWinSlots + kBigEdge;
-constexpr int kPinRegs = (kStageRows + 31) / 32;
-constexpr int kConsumers = kThreads / 32 - 1;
+// copies (the same sums as k_score_pass1).  CTA b takes a contiguous range of
+// windows of CSC slots (see kWinSlots) and streams the Q rows of their slots,
+// in slot order, through a ring of `nst` stages of kWinSlots rows (row pitch
+// `pitch` elements, `row_bytes` a multiple of 16): slot t sits in ring row
+// (t - first slot of the range) mod (nst kWinSlots).  Warp 0 produces: it
+// copies window j's rows once the consumers have released window j - nst
+// (plus the window after the range, whose rows the range's last hyperedges
+// may reach), with the offsets and weights of the hyperedges the window owns
+// (aligned supersets of ceptr[ef..el] and ew[ef..el), when at most
+// kMetaEdges - 8 of them); the pin ids and the window table are loaded a
+// group of kGroupWin windows ahead.  Warps 1..15 consume: for window w, once
+// windows w and w + 1 have landed, each scores the window's hyperedges (first
+// slot in w; at most kBigEdge pins, so they end within w + 1) w, w + 15, ...
+// from shared memory, lanes over columns.  Waits are bounded: on expiry the
+// kernel sets HEF_WAIT_TIMEOUT in `status`, stops, waits (bounded) for the
+// copies it issued and still takes part in the reduction.
+static_assert(kBigEdge <= kWinSlots, "a scored hyperedge must end within the next window");
+constexpr int kPinRegs = (kWinSlots + 31) / 32;
+constexpr int kBulkThreads = 512;  // warp 0 produces, warps 1..15 consume
+constexpr int kConsumers = kBulkThreads / 32 - 1;
+constexpr int kGroupWin = 8;    // windows per prefetch group of the producer
+constexpr int kMetaEdges = 128;  // hyperedge offsets / weights staged per window
 constexpr uint32_t kCopyWaitIters = 1u << 20;
 
-template <typename T, int NC>
-__global__ void __launch_bounds__(256, 1)
+template <typename T, int NC, bool G4>
+__global__ void __launch_bounds__(kBulkThreads, 1)
     k_score_pass1_bulk(IncView g, const T* __restrict__ Q, long long ldq, int K, int pitch,
                        uint32_t row_bytes, int nst, GridRed red, const double* __restrict__ bpart,
                        int nbpart, double* QH, double* invQH, double* QH_out, T* spread,
-                       int ldsp, unsigned int* status) {
+                       int ldsp, unsigned int* status, const __grid_constant__ CUtensorMap tmap) {
   using namespace umma;
   if (g.status[0]) return;
   extern __shared__ __align__(128) unsigned char stage_raw[];
-  T* stages = reinterpret_cast<T*>(stage_raw);
+  // the ring from the first 128-byte boundary (the launch adds 128 bytes)
+  unsigned char* ring_raw = stage_raw + ((128u - (umma::smem_u32(stage_raw) & 127u)) & 127u);
+  T* ring = reinterpret_cast<T*>(ring_raw);
   __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
-  __shared__ int meta[kMaxStages][2];  // first slot and row count of the staged window
+  __shared__ __align__(16) int m_ceptr[kMaxStages][kMetaEdges];
+  __shared__ __align__(16) double m_ew[kMaxStages][kMetaEdges];
+  __shared__ int meta[kMaxStages][3];  // ef, el, offsets staged
   __shared__ int abort_flag;
   __shared__ long long issued;
-  __shared__ double wred[kThreads / 32][32 * NC];
   volatile int* abort_v = &abort_flag;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const long long nwin = num_windows(g.P);
-  const long long G = gridDim.x;
+  // this CTA's windows [wb, we) and the windows it copies [wb, wc): one
+  // more when it has any, whose first slots its last hyperedges may reach
+  const long long wb = nwin * blockIdx.x / gridDim.x, we = nwin * (blockIdx.x + 1) / gridDim.x;
+  const long long wc = (we > wb && we < nwin) ? we + 1 : we;
+  const int ring_rows = nst * kWinSlots;
   if (threadIdx.x == 0) {
     for (int q = 0; q < nst; ++q) {
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], kConsumers);
     }
     abort_flag = 0;
-    issued = 0;
+    issued = wb;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   __syncthreads();
@@ -327,139 +344,168 @@ __global__ void __launch_bounds__(256, 1)
     }
   };
   if (wid == 0) {
-    // ---- producer: window table (i + 3) -> slots (i + 2) -> pins (i + 1) -> copies (i)
-    struct Edges { int ef, el; };
-    struct Slots { int s0, rows; };
-    auto edges_of = [&](long long i) {
-      const long long w = blockIdx.x + i * G;
-      Edges x{0, 0};
-      if (w < nwin) x.ef = g.win_edge[w], x.el = g.win_edge[w + 1];
-      return x;
-    };
-    auto slots_of = [&](Edges x) {
-      Slots y{0, 0};
-      if (x.el > x.ef) {
-        y.s0 = g.ceptr[x.ef];
-        int s1 = g.ceptr[x.el];
-        const int sl = g.ceptr[x.el - 1];
-        if (s1 - sl > kBigEdge) s1 = sl;
-        y.rows = min(max(s1 - y.s0, 0), kStageRows);
-      }
-      return y;
-    };
-    auto pins_of = [&](Slots y, int (&pin)[kPinRegs]) {
+    // ---- producer
+    // group buffers of kGroupWin windows from g0: the pin ids (per-row copies:
+    // lane l holds slots l and l + 32 of window g0 + d in pc[d]; gather4: lane
+    // l holds slots 4 (l mod 16) .. + 3 of window g0 + 2 h + l / 16 in pc4[h])
+    // and win_edge[g0 + l] for l <= kGroupWin
+    constexpr int kRegs = G4 ? 1 : kPinRegs;
+    constexpr int kBufs = G4 ? kGroupWin / 2 : kGroupWin;
+    int pc[kBufs][kRegs], pn[kBufs][kRegs];
+    int4 pc4[kBufs], pn4[kBufs];
+    int wc_e = 0, wn_e = 0;
+    auto load_group = [&](long long g0, int (&pp)[kBufs][kRegs], int4 (&pp4)[kBufs], int& wl) {
+      if constexpr (G4) {
 #pragma unroll
-      for (int j = 0; j < kPinRegs; ++j) {
-        const int r = lane + 32 * j;
-        pin[j] = r < y.rows ? g.cpins[y.s0 + r] : 0;
+        for (int h = 0; h < kBufs; ++h) {
+          const long long jw = g0 + 2 * h + (lane >> 4);
+          const long long t = jw * kWinSlots + 4 * (lane & 15);
+          pp4[h] = (jw < wc && t < g.P) ? *reinterpret_cast<const int4*>(g.cpins + t)
+                                        : make_int4(0, 0, 0, 0);
+        }
+      } else {
+#pragma unroll
+        for (int d = 0; d < kBufs; ++d)
+#pragma unroll
+          for (int u = 0; u < kRegs; ++u) {
+            const long long t = (g0 + d) * kWinSlots + lane + 32 * u;
+            pp[d][u] = (g0 + d < wc && lane + 32 * u < kWinSlots && t < g.P) ? g.cpins[t] : 0;
+          }
       }
+      wl = (lane <= kGroupWin && g0 + lane <= nwin) ? g.win_edge[g0 + lane] : 0;
     };
-    Edges a2 = edges_of(2);
-    Slots b1 = slots_of(edges_of(1));
-    Slots b0 = slots_of(edges_of(0));
-    int p0[kPinRegs];
-    pins_of(b0, p0);
-    long long i = 0;
-    for (; blockIdx.x + i * G < nwin; ++i) {
-      if (*abort_v) break;
-      const Edges a3 = edges_of(i + 3);
-      const Slots b2 = slots_of(a2);
-      int p1[kPinRegs];
-      pins_of(b1, p1);
-      const int q = (int)(i % nst);
-      if (i >= nst) {
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(&empty[q], (uint32_t)((i / nst - 1) & 1),
-                                                          kCopyWaitIters));
-        if (!ok) {
-          fail();
+    load_group(wb, pc, pc4, wc_e);
+    long long j = wb;
+    bool stop = false;
+    for (long long g0 = wb; g0 < wc && !stop; g0 += kGroupWin) {
+      load_group(g0 + kGroupWin, pn, pn4, wn_e);
+#pragma unroll
+      for (int d = 0; d < kGroupWin; ++d) {
+        j = g0 + d;
+        if (j >= wc) break;
+        if (*abort_v) {
+          stop = true;
           break;
         }
-      }
-      if (lane == 0) {
-        meta[q][0] = b0.s0;
-        meta[q][1] = b0.rows;
-        mbar_arrive_expect_tx(&full[q], (uint32_t)b0.rows * row_bytes);
-      }
-      __syncwarp();
-      T* dst = stages + (size_t)q * kStageRows * pitch;
+        const int q = (int)((j - wb) % nst);
+        const long long use = (j - wb) / nst;
+        if (use > 0) {
+          const bool ok = __all_sync(0xffffffffu, mbar_wait(&empty[q], (uint32_t)((use - 1) & 1),
+                                                            kCopyWaitIters));
+          if (!ok) {
+            fail();
+            stop = true;
+            break;
+          }
+        }
+        const int ef = __shfl_sync(0xffffffffu, wc_e, d), el = __shfl_sync(0xffffffffu, wc_e, d + 1);
+        const int rows = (int)min((long long)kWinSlots, (long long)g.P - j * kWinSlots);
+        // offsets ceptr[c0, c0 + cn) and weights ew[w0, w0 + wn): 16-byte aligned
+        // supersets (within the arrays' 256-byte padded allocations)
+        const int c0 = ef & ~3, cn = ((el + 4) & ~3) - c0;
+        const int w0 = ef & ~1, wn = ((el + 1) & ~1) - w0;
+        const bool mok = el >= ef && el - ef + 8 <= kMetaEdges;
+        const int copied = G4 ? (rows + 3) / 4 * 4 : rows;  // gather4 moves whole groups of four
+        const uint32_t bytes = (uint32_t)copied * row_bytes + (mok ? (uint32_t)(cn * 4 + wn * 8) : 0u);
+        if (lane == 0) {
+          meta[q][0] = ef;
+          meta[q][1] = el;
+          meta[q][2] = mok;
+          mbar_arrive_expect_tx(&full[q], bytes);
+        }
+        __syncwarp();
+        T* dst = ring + (size_t)q * kWinSlots * pitch;
+        if constexpr (G4) {
+          const int r4 = 4 * (lane & 15);
+          if ((lane >> 4) == (d & 1) && r4 < rows) {
+            const int4 pv = pc4[d >> 1];
+            // rows past the window's end repeat its row r4
+            gather4_g2s(dst + (size_t)r4 * pitch, &tmap, pv.x, r4 + 1 < rows ? pv.y : pv.x,
+                        r4 + 2 < rows ? pv.z : pv.x, r4 + 3 < rows ? pv.w : pv.x, &full[q]);
+          }
+        } else {
 #pragma unroll
-      for (int j = 0; j < kPinRegs; ++j) {
-        const int r = lane + 32 * j;
-        if (r < b0.rows) bulk_g2s(dst + (size_t)r * pitch, Q + (long long)p0[j] * ldq, row_bytes, &full[q]);
+          for (int u = 0; u < kRegs; ++u) {
+            const int r = lane + 32 * u;
+            if (r < rows)
+              bulk_g2s(dst + (size_t)r * pitch, Q + (long long)pc[d][u] * ldq, row_bytes, &full[q]);
+          }
+        }
+        if (mok && lane == 0) {
+          bulk_g2s(&m_ceptr[q][0], g.ceptr + c0, (uint32_t)cn * 4u, &full[q]);
+          if (wn > 0) bulk_g2s(&m_ew[q][0], g.ew + w0, (uint32_t)wn * 8u, &full[q]);
+        }
+        j = j + 1;
       }
-      b0 = b1;
-      b1 = b2;
-      a2 = a3;
 #pragma unroll
-      for (int j = 0; j < kPinRegs; ++j) p0[j] = p1[j];
+      for (int d = 0; d < kBufs; ++d) {
+        pc4[d] = pn4[d];
+#pragma unroll
+        for (int u = 0; u < kRegs; ++u) pc[d][u] = pn[d][u];
+      }
+      wc_e = wn_e;
     }
-    if (lane == 0) issued = i;
+    if (lane == 0) issued = j;
   } else {
     // ---- consumers
     const int cw = wid - 1;
-    int nef = 0, nel = 0;  // hyperedges of the next window
-    if (blockIdx.x < nwin) nef = g.win_edge[blockIdx.x], nel = g.win_edge[blockIdx.x + 1];
-    for (long long i = 0; blockIdx.x + i * G < nwin; ++i) {
-      const int ef = nef, el = nel;
-      // offsets and weights of this warp's first 32 hyperedges of the window
-      int ea = 0, eb = 0;
-      T ewl = 0;
-      {
-        const int e = ef + cw + kConsumers * lane;
-        if (e < el) ea = g.ceptr[e], eb = g.ceptr[e + 1], ewl = (T)g.ew[e];
-      }
-      const long long wn = blockIdx.x + (i + 1) * G;
-      if (wn < nwin) nef = g.win_edge[wn], nel = g.win_edge[wn + 1];
-      const int q = (int)(i % nst);
-      const bool got =
-          __all_sync(0xffffffffu, mbar_wait(&full[q], (uint32_t)((i / nst) & 1), kCopyWaitIters));
+    for (long long w = wb; w < we; ++w) {
+      const int q = (int)((w - wb) % nst);
+      bool got = mbar_wait(&full[q], (uint32_t)(((w - wb) / nst) & 1), kCopyWaitIters);
+      if (w + 1 < wc)
+        got = got && mbar_wait(&full[(w + 1 - wb) % nst], (uint32_t)(((w + 1 - wb) / nst) & 1),
+                               kCopyWaitIters);
+      got = __all_sync(0xffffffffu, got);
       if (!got || *abort_v) {
         if (!got) fail();
         break;
       }
-      const int s0 = meta[q][0], rows = meta[q][1];
-      const T* st = stages + (size_t)q * kStageRows * pitch;
+      const int ef = meta[q][0], el = meta[q][1];
+      const bool mok = meta[q][2] != 0;
+      const int c0 = ef & ~3, w0 = ef & ~1;
+      const int row_w = q * kWinSlots;  // ring row of the window's first slot
+      const long long slot_w = w * kWinSlots;
+      const long long slot_end = min(wc * kWinSlots, (long long)g.P);
       T pacc[NC];
 #pragma unroll
       for (int c = 0; c < NC; ++c) pacc[c] = 0;
-      for (int base = ef + cw; base < el; base += kConsumers * 32) {
-        if (base != ef + cw) {  // hyperedges past this warp's first 32 (long runs of empty ones)
-          const int e = base + kConsumers * lane;
-          ea = eb = 0;
-          ewl = 0;
-          if (e < el) ea = g.ceptr[e], eb = g.ceptr[e + 1], ewl = (T)g.ew[e];
-        }
-        const int cnt = min(32, (el - base + kConsumers - 1) / kConsumers);
-        for (int jj = 0; jj < cnt; ++jj) {
-          const int e = base + kConsumers * jj;
-          const int a = __shfl_sync(0xffffffffu, ea, jj) - s0;
-          const int b = __shfl_sync(0xffffffffu, eb, jj) - s0;
-          const T we = __shfl_sync(0xffffffffu, ewl, jj);
-          if (b - a < 2 || b - a > kBigEdge || a < 0 || b > rows) continue;
-          T mx[NC], mn[NC];
+      for (int e = ef + cw; e < el; e += kConsumers) {
+        int a, b;
+        T we_;
+        if (mok) a = m_ceptr[q][e - c0], b = m_ceptr[q][e + 1 - c0], we_ = (T)m_ew[q][e - w0];
+        else a = g.ceptr[e], b = g.ceptr[e + 1], we_ = (T)g.ew[e];
+        const int k = b - a;
+        // staged: slots [w kWinSlots, min(wc kWinSlots, P)); a >= w kWinSlots
+        if (k < 2 || k > kBigEdge || (long long)b > slot_end) continue;
+        const int r0 = row_w + (int)(a - slot_w);  // ring row of the first pin
+        T mx[NC], mn[NC];
 #pragma unroll
-          for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
-          for (int r = a; r < b; r += 4) {
-            const int r1 = min(r + 1, b - 1), r2 = min(r + 2, b - 1), r3 = min(r + 3, b - 1);
+        for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
+        for (int t = 0; t < k; t += 4) {
+          const T* rp[4];
 #pragma unroll
-            for (int c = 0; c < NC; ++c) {
-              const int col = lane + 32 * c;
-              if (col < K) {
-                const T v0 = st[(size_t)r * pitch + col], v1 = st[(size_t)r1 * pitch + col];
-                const T v2 = st[(size_t)r2 * pitch + col], v3 = st[(size_t)r3 * pitch + col];
-                mx[c] = fmax(fmax(mx[c], fmax(v0, v1)), fmax(v2, v3));
-                mn[c] = fmin(fmin(mn[c], fmin(v0, v1)), fmin(v2, v3));
-              }
-            }
+          for (int u = 0; u < 4; ++u) {
+            int x = r0 + min(t + u, k - 1);
+            x = x >= ring_rows ? x - ring_rows : x;
+            rp[u] = ring + x * pitch + lane;
           }
 #pragma unroll
           for (int c = 0; c < NC; ++c) {
-            const int col = lane + 32 * c;
-            const T sp = mx[c] - mn[c];
-            if (col < K) {
-              pacc[c] += we * sp * sp;
-              if (spread) spread[(long long)e * ldsp + col] = sp;
+            if (lane + 32 * c < K) {
+              const T v0 = rp[0][32 * c], v1 = rp[1][32 * c];
+              const T v2 = rp[2][32 * c], v3 = rp[3][32 * c];
+              mx[c] = fmax(fmax(mx[c], fmax(v0, v1)), fmax(v2, v3));
+              mn[c] = fmin(fmin(mn[c], fmin(v0, v1)), fmin(v2, v3));
             }
+          }
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          const int col = lane + 32 * c;
+          const T sp = mx[c] - mn[c];
+          if (col < K) {
+            pacc[c] += we_ * sp * sp;
+            if (spread) spread[(long long)e * ldsp + col] = sp;
           }
         }
       }
@@ -471,17 +517,20 @@ __global__ void __launch_bounds__(256, 1)
     }
   }
   __syncthreads();
-  if (abort_flag && threadIdx.x == 0) {
-    // copies of the last nst issued windows may still be in flight
-    for (long long j = issued > nst ? issued - nst : 0; j < issued; ++j)
-      mbar_wait(&full[j % nst], (uint32_t)((j / nst) & 1), kCopyWaitIters);
-  }
+  // every copy has landed before the ring is reused or the CTA exits: the
+  // last use of each stage (a no-op unless a wait expired)
+  if (threadIdx.x == 0)
+    for (long long j = issued - nst > wb ? issued - nst : wb; j < issued; ++j)
+      mbar_wait(&full[(j - wb) % nst], (uint32_t)(((j - wb) / nst) & 1), kCopyWaitIters);
+  __syncthreads();
+  // per-warp sums in the (now idle) ring: [warp][32 NC]
+  double* wred = reinterpret_cast<double*>(ring_raw);
 #pragma unroll
-  for (int c = 0; c < NC; ++c) wred[wid][lane + 32 * c] = acc[c];
+  for (int c = 0; c < NC; ++c) wred[wid * 32 * NC + lane + 32 * c] = acc[c];
   __syncthreads();
   for (int col = threadIdx.x; col < K; col += blockDim.x) {
     double sum = 0.0;
-    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) sum += wred[w][col];
+    for (int w = 0; w < kBulkThreads / 32; ++w) sum += wred[w * 32 * NC + col];
     red.part[(size_t)blockIdx.x * K + col] = sum;
   }
   finish_qh<NC>(red, K, bpart, nbpart, QH, invQH, QH_out);
@@ -757,6 +806,38 @@ size_t carve_score(void* base, int K, long long m, ScoreWs* w) {
   return c.bytes();
 }
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when unavailable.
+PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// Tensor map of the row-major n x ldq matrix Q with a box of one row of bw
+// elements (for tile::gather4); false when it cannot be encoded.
+template <typename T>
+bool encode_rows_map(CUtensorMap* tm, const T* Q, long long ldq, long long n, int bw) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (!fn || n < 1 || n > 0x7fffffffll) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)ldq, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldq * sizeof(T)};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, 1u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  const CUresult r = fn(tm, sizeof(T) == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64,
+                        2, const_cast<T*>(Q), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 template <typename T, int NC>
 hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int K, int reduce,
                         double* R_out, double* QH_out, int32_t* argvec, int32_t* pmax,
@@ -775,19 +856,45 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
                                                                                    spread, ldsp));
   // pass 1 staged through shared memory when the rows can be bulk-copied
   // (16-byte aligned rows; a row pitch of 16-byte multiples) and at least two
-  // stages fit; otherwise the warps gather the rows
-  const uint32_t row_bytes = (uint32_t)(((size_t)K * sizeof(T) + 15) / 16 * 16);
-  const size_t stage_bytes = (size_t)kStageRows * row_bytes;
-  const int nst = (int)std::min<size_t>(kMaxStages, kStageSmem / stage_bytes);
-  const bool bulk = (reinterpret_cast<uintptr_t>(Q) % 16 == 0) && ((size_t)ldq * sizeof(T)) % 16 == 0 &&
-                    nst >= 2 && num_sms() <= w.grid;
+  // stages fit; by four-row tensor-map gathers when a box row (K rounded up
+  // to 32 bytes, at most 256 elements) fits in the pitch; otherwise the warps
+  // gather the rows
+  const bool aligned = (reinterpret_cast<uintptr_t>(Q) % 16 == 0) && ((size_t)ldq * sizeof(T)) % 16 == 0;
+  const int bw = (int)(((size_t)K * sizeof(T) + 31) / 32 * 32 / sizeof(T));
+  CUtensorMap tmap;
+  memset(&tmap, 0, sizeof(tmap));
+  bool g4 = aligned && bw <= 256 && bw <= ldq && encode_rows_map(&tmap, Q, ldq, inc->n, bw);
+  const uint32_t row_bytes = g4 ? (uint32_t)(bw * sizeof(T)) : (uint32_t)(((size_t)K * sizeof(T) + 15) / 16 * 16);
+  const size_t stage_bytes = (size_t)kWinSlots * row_bytes;
+  // stages: as many as fit next to the kernel's static shared memory (and
+  // 128 bytes to align the ring)
+  static thread_local int stat = -1;  // static bytes of this instantiation
+  if (stat < 0) {
+    cudaFuncAttributes fa;
+    HEF_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_score_pass1_bulk<T, NC, true>));
+    stat = (int)fa.sharedSizeBytes;
+  }
+  const size_t avail = kStageSmem > (size_t)stat + 128 ? kStageSmem - stat - 128 : 0;
+  const int nst = (int)std::min<size_t>(kMaxStages, avail / stage_bytes);
+  // the ring also holds the per-warp sums at the end
+  const size_t smem =
+      std::max(nst * stage_bytes, (size_t)(kBulkThreads / 32) * 32 * NC * sizeof(double)) + 128;
+  const bool bulk = aligned && nst >= 2 && smem + stat <= kMaxSmemOptin && num_sms() <= w.grid;
   if (bulk) {
-    HEF_ENSURE_SMEM((k_score_pass1_bulk<T, NC>), (int)(nst * stage_bytes));
-    const size_t smem = nst * stage_bytes;
-    HEF_LAUNCH("k_score_pass1", st,
-               k_score_pass1_bulk<T, NC><<<num_sms(), kThreads, smem, st>>>(
-                   g, Q, ldq, K, (int)(row_bytes / sizeof(T)), row_bytes, nst, red, w.bpart,
-                   w.bgrid, w.QH, w.invQH, QH_out, spread, ldsp, inc->status));
+    const int pitch = (int)(row_bytes / sizeof(T));
+    if (g4) {
+      HEF_ENSURE_SMEM((k_score_pass1_bulk<T, NC, true>), (int)smem);
+      HEF_LAUNCH("k_score_pass1", st,
+                 k_score_pass1_bulk<T, NC, true><<<num_sms(), kBulkThreads, smem, st>>>(
+                     g, Q, ldq, K, pitch, row_bytes, nst, red, w.bpart, w.bgrid, w.QH, w.invQH,
+                     QH_out, spread, ldsp, inc->status, tmap));
+    } else {
+      HEF_ENSURE_SMEM((k_score_pass1_bulk<T, NC, false>), (int)smem);
+      HEF_LAUNCH("k_score_pass1", st,
+                 k_score_pass1_bulk<T, NC, false><<<num_sms(), kBulkThreads, smem, st>>>(
+                     g, Q, ldq, K, pitch, row_bytes, nst, red, w.bpart, w.bgrid, w.QH, w.invQH,
+                     QH_out, spread, ldsp, inc->status, tmap));
+    }
   } else {
     const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
     HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<g1, kThreads, 0, st>>>(

@@ -67,6 +67,19 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Tensor-map gather of four rows (tile::gather4; the map's box is one row
+// high and `box_bytes` wide): rows y0..y3 from column 0, written as four
+// consecutive box rows at `dst` (128-byte aligned); completion counts the
+// 4 box_bytes against the phase of `bar`.
+__device__ __forceinline__ void gather4_g2s(void* dst, const void* tmap, int y0, int y1, int y2, int y3,
+                                            uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile::gather4.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(0), "r"(y0), "r"(y1), "r"(y2), "r"(y3), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // ---------------------------------------------------------------- fences
 
 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
