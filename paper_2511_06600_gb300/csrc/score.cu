@@ -296,6 +296,7 @@ constexpr int kBulkThreads = 512;  // warp 0 produces, warps 1..15 consume
 constexpr int kConsumers = kBulkThreads / 32 - 1;
 constexpr int kGroupWin = 8;    // windows per prefetch group of the producer
 constexpr int kMetaEdges = 128;  // hyperedge offsets / weights staged per window
+constexpr int kFlushWin = 8;     // windows per working-type partial sum of a consumer warp
 constexpr uint32_t kCopyWaitIters = 1u << 20;
 
 template <typename T, int NC, bool G4>
@@ -303,7 +304,8 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
     k_score_pass1_bulk(IncView g, const T* __restrict__ Q, long long ldq, int K, int pitch,
                        uint32_t row_bytes, int nst, GridRed red, const double* __restrict__ bpart,
                        int nbpart, double* QH, double* invQH, double* QH_out, T* spread,
-                       int ldsp, unsigned int* status, const __grid_constant__ CUtensorMap tmap) {
+                       int ldsp, const T* __restrict__ ewT, unsigned int* status,
+                       const __grid_constant__ CUtensorMap tmap) {
   using namespace umma;
   if (g.status[0]) return;
   extern __shared__ __align__(128) unsigned char stage_raw[];
@@ -312,7 +314,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
   T* ring = reinterpret_cast<T*>(ring_raw);
   __shared__ uint64_t full[kMaxStages], empty[kMaxStages];
   __shared__ __align__(16) int m_ceptr[kMaxStages][kMetaEdges];
-  __shared__ __align__(16) double m_ew[kMaxStages][kMetaEdges];
+  __shared__ __align__(16) T m_ew[kMaxStages][kMetaEdges];
   __shared__ int meta[kMaxStages][3];  // ef, el, offsets staged
   __shared__ int abort_flag;
   __shared__ long long issued;
@@ -400,13 +402,15 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
         }
         const int ef = __shfl_sync(0xffffffffu, wc_e, d), el = __shfl_sync(0xffffffffu, wc_e, d + 1);
         const int rows = (int)min((long long)kWinSlots, (long long)g.P - j * kWinSlots);
-        // offsets ceptr[c0, c0 + cn) and weights ew[w0, w0 + wn): 16-byte aligned
+        // offsets ceptr[c0, c0 + cn) and weights ewT[w0, w0 + wn): 16-byte aligned
         // supersets (within the arrays' 256-byte padded allocations)
+        constexpr int kWv = 16 / sizeof(T);
         const int c0 = ef & ~3, cn = ((el + 4) & ~3) - c0;
-        const int w0 = ef & ~1, wn = ((el + 1) & ~1) - w0;
+        const int w0 = ef & ~(kWv - 1), wn = ((el + kWv - 1) & ~(kWv - 1)) - w0;
         const bool mok = el >= ef && el - ef + 8 <= kMetaEdges;
         const int copied = G4 ? (rows + 3) / 4 * 4 : rows;  // gather4 moves whole groups of four
-        const uint32_t bytes = (uint32_t)copied * row_bytes + (mok ? (uint32_t)(cn * 4 + wn * 8) : 0u);
+        const uint32_t bytes =
+            (uint32_t)copied * row_bytes + (mok ? (uint32_t)(cn * 4 + wn * (int)sizeof(T)) : 0u);
         if (lane == 0) {
           meta[q][0] = ef;
           meta[q][1] = el;
@@ -433,7 +437,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
         }
         if (mok && lane == 0) {
           bulk_g2s(&m_ceptr[q][0], g.ceptr + c0, (uint32_t)cn * 4u, &full[q]);
-          if (wn > 0) bulk_g2s(&m_ew[q][0], g.ew + w0, (uint32_t)wn * 8u, &full[q]);
+          if (wn > 0) bulk_g2s(&m_ew[q][0], ewT + w0, (uint32_t)(wn * sizeof(T)), &full[q]);
         }
         j = j + 1;
       }
@@ -449,6 +453,9 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
   } else {
     // ---- consumers
     const int cw = wid - 1;
+    T pacc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) pacc[c] = 0;
     for (long long w = wb; w < we; ++w) {
       const int q = (int)((w - wb) % nst);
       bool got = mbar_wait(&full[q], (uint32_t)(((w - wb) / nst) & 1), kCopyWaitIters);
@@ -462,18 +469,15 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
       }
       const int ef = meta[q][0], el = meta[q][1];
       const bool mok = meta[q][2] != 0;
-      const int c0 = ef & ~3, w0 = ef & ~1;
+      const int c0 = ef & ~3, w0 = ef & ~(16 / (int)sizeof(T) - 1);
       const int row_w = q * kWinSlots;  // ring row of the window's first slot
       const long long slot_w = w * kWinSlots;
       const long long slot_end = min(wc * kWinSlots, (long long)g.P);
-      T pacc[NC];
-#pragma unroll
-      for (int c = 0; c < NC; ++c) pacc[c] = 0;
       for (int e = ef + cw; e < el; e += kConsumers) {
         int a, b;
         T we_;
-        if (mok) a = m_ceptr[q][e - c0], b = m_ceptr[q][e + 1 - c0], we_ = (T)m_ew[q][e - w0];
-        else a = g.ceptr[e], b = g.ceptr[e + 1], we_ = (T)g.ew[e];
+        if (mok) a = m_ceptr[q][e - c0], b = m_ceptr[q][e + 1 - c0], we_ = m_ew[q][e - w0];
+        else a = g.ceptr[e], b = g.ceptr[e + 1], we_ = ewT[e];
         const int k = b - a;
         // staged: slots [w kWinSlots, min(wc kWinSlots, P)); a >= w kWinSlots
         if (k < 2 || k > kBigEdge || (long long)b > slot_end) continue;
@@ -509,12 +513,16 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
           }
         }
       }
-      // FP32 partial sums span one window; FP64 beyond
+      // partial sums in the working type over kFlushWin windows; FP64 beyond
+      if ((w - wb) % kFlushWin == kFlushWin - 1) {
 #pragma unroll
-      for (int c = 0; c < NC; ++c) acc[c] += (double)pacc[c];
+        for (int c = 0; c < NC; ++c) acc[c] += (double)pacc[c], pacc[c] = 0;
+      }
       __syncwarp();
       if (lane == 0) mbar_arrive(&empty[q]);
     }
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] += (double)pacc[c];
   }
   __syncthreads();
   // every copy has landed before the ring is reused or the CTA exits: the
@@ -887,13 +895,13 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
       HEF_LAUNCH("k_score_pass1", st,
                  k_score_pass1_bulk<T, NC, true><<<num_sms(), kBulkThreads, smem, st>>>(
                      g, Q, ldq, K, pitch, row_bytes, nst, red, w.bpart, w.bgrid, w.QH, w.invQH,
-                     QH_out, spread, ldsp, inc->status, tmap));
+                     QH_out, spread, ldsp, scal_view<T>(inc).ew, inc->status, tmap));
     } else {
       HEF_ENSURE_SMEM((k_score_pass1_bulk<T, NC, false>), (int)smem);
       HEF_LAUNCH("k_score_pass1", st,
                  k_score_pass1_bulk<T, NC, false><<<num_sms(), kBulkThreads, smem, st>>>(
                      g, Q, ldq, K, pitch, row_bytes, nst, red, w.bpart, w.bgrid, w.QH, w.invQH,
-                     QH_out, spread, ldsp, inc->status, tmap));
+                     QH_out, spread, ldsp, scal_view<T>(inc).ew, inc->status, tmap));
     }
   } else {
     const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
