@@ -198,8 +198,10 @@ def kernel_model(name, H, K, S, k, esz):
         return "hbm", float(n) * K * esz + 152 * Kq * Kq * 8.0 / 2
     if name == "k_apply_tc":      # V read and written in place
         return "hbm", 2.0 * n * K * esz
-    if name == "k_score_pass1":
-        return "hbm", n * K * esz + 4.0 * P + 4.0 * (m + 1) + 8.0 * m
+    if name == "k_score_pass1":   # Q once, the pin lists, offsets, weights; spreads written
+        return "hbm", n * K * esz + 4.0 * P + 4.0 * (m + 1) + 8.0 * m + float(m) * K * esz
+    if name == "k_score_ratio":   # spreads read; one column of Q per hyperedge's pins; outputs
+        return "hbm", float(m) * K * esz + 4.0 * (m + 1) + 4.0 * m + 4.0 * P + esz * P + 20.0 * m
     if name == "k_score_pass2":
         return "hbm", n * K * esz + 4.0 * P + 4.0 * (m + 1) + 8.0 * m + 4.0 * m + 20.0 * m
     if name == "k_edge_pass":   # reads node rows of 2 chains, writes s_e and star edge rows
