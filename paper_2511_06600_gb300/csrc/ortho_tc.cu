@@ -10,7 +10,8 @@
 // MMAs of the upper block rows: block b covers basis rows [128b, 128b+128)
 // against basis columns [128b, Kq).  Completion is tracked by tcgen05.commit
 // on an mbarrier per stage; every wait is bounded and a timeout sets *err.
-// The epilogue moves the FP32 accumulators from TMEM to FP64 per-CTA partials.
+// The epilogue moves the FP32 accumulators from TMEM to per-CTA FP32 partials
+// (no FP64 work on the SM); k_gram_tc_reduce widens them and sums in FP64.
 #include "internal.h"
 #include "umma.cuh"
 
@@ -30,7 +31,7 @@ struct GramTcArgs {
   int n, K, Kq, nb;
   int rows_per_cta;
   int gmask[4];  // block rows of G_aug computed by CTA group blockIdx.y (bit b: rows 128b..)
-  double* part;  // gridDim.x x Kq x Kq
+  float* part;   // gridDim.x x Kq x Kq FP32 partials (the accumulators as they are)
   int* err;
 };
 
@@ -178,7 +179,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   }
   ok = __syncthreads_and(ok);
   tc_fence_after();
-  double* P = a.part + (size_t)blockIdx.x * a.Kq * a.Kq;
+  float* P = a.part + (size_t)blockIdx.x * a.Kq * a.Kq;
   if (ok && committed > 0) {
     const int q = warp & 3, half = warp >> 2;
 #pragma unroll
@@ -193,14 +194,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
         const int j0 = b * 128 + c8 * 8;
         if (i < a.Kq && j0 + 7 >= i) {  // upper triangle only (the reducer reads i <= j)
 #pragma unroll
-          for (int u = 0; u < 8; ++u) P[(size_t)i * a.Kq + j0 + u] = (double)v[u];
+          for (int u = 0; u < 8; ++u) P[(size_t)i * a.Kq + j0 + u] = v[u];
         }
       }
     }
   } else {
     // zero this group's block rows
     for (int e = tid; e < a.Kq * a.Kq; e += kTcThreads)
-      if ((gmask >> ((e / a.Kq) / 128)) & 1) P[e] = 0.0;
+      if ((gmask >> ((e / a.Kq) / 128)) & 1) P[e] = 0.f;
     if (!ok && tid == 0) atomicExch(a.err, 1);
     if (!ok && committed > 0) {  // let MMAs in flight finish before TMEM is released
       const int t = committed - 1;
@@ -212,37 +213,52 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-// G (K x K, FP64) and c (K): fixed-order sums of the per-CTA partials of
-// G_aug; column K of G_aug holds the column sums.
-__global__ void k_gram_tc_reduce(const double* __restrict__ part, int K, int Kq, int nchunk,
+// G (K x K, FP64) and c (K): fixed-order FP64 sums of the per-CTA FP32
+// partials of G_aug (column K holds the column sums).  Eight lanes per entry:
+// lane l of the eight sums partials l, l + 8, ... in order, then a fixed
+// shuffle tree; a warp takes four consecutive entries per round.
+__global__ void k_gram_tc_reduce(const float* __restrict__ part, int K, int Kq, int nchunk,
                                  double* G, double* c) {
-  const long long KK = (long long)K * K;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < KK + K;
-       idx += (long long)gridDim.x * blockDim.x) {
-    int i, j;
-    if (idx < KK) {
-      i = (int)(idx / K), j = (int)(idx % K);
-      if (i > j) continue;
-    } else {
-      i = (int)(idx - KK), j = K;
+  const long long KK = (long long)K * K, total = KK + K;
+  const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const size_t stride = (size_t)Kq * Kq;
+  for (long long wb = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; wb < total;
+       wb += nwarps * 4) {
+    const long long idx = wb + grp;
+    int i = 0, j = 0;
+    bool act = idx < total;
+    if (act) {
+      if (idx < KK) {
+        i = (int)(idx / K), j = (int)(idx % K);
+        act = i <= j;
+      } else {
+        i = (int)(idx - KK), j = K;
+      }
     }
-    const double* p = part + (size_t)i * Kq + j;
-    const size_t stride = (size_t)Kq * Kq;
     double s = 0.0;
-    int q = 0;
-    for (; q + 8 <= nchunk; q += 8) {
-      double v[8];
+    if (act) {
+      const float* p = part + (size_t)i * Kq + j;
+      int q = sub;
+      for (; q + 24 < nchunk; q += 32) {
+        float v[4];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (size_t)(q + u) * stride);
+        for (int u = 0; u < 4; ++u) v[u] = __ldcg(p + (size_t)(q + 8 * u) * stride);
 #pragma unroll
-      for (int u = 0; u < 8; ++u) s += v[u];
+        for (int u = 0; u < 4; ++u) s += (double)v[u];
+      }
+      for (; q < nchunk; q += 8) s += (double)__ldcg(p + (size_t)q * stride);
     }
-    for (; q < nchunk; ++q) s += __ldcg(p + (size_t)q * stride);
-    if (j < K) {
-      G[(size_t)i * K + j] = s;
-      G[(size_t)j * K + i] = s;
-    } else {
-      c[i] = s;
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    s += __shfl_xor_sync(0xffffffffu, s, 4);
+    if (act && sub == 0) {
+      if (j < K) {
+        G[(size_t)i * K + j] = s;
+        G[(size_t)j * K + i] = s;
+      } else {
+        c[i] = s;
+      }
     }
   }
 }
@@ -582,7 +598,7 @@ hef_status gram_tc(const float* V, long long ldv, long long n, int K, double* pa
   a.Kq = Kq;
   a.nb = nb;
   a.rows_per_cta = (int)(((n + ctas - 1) / ctas + kSlab - 1) / kSlab * kSlab);
-  a.part = part;
+  a.part = reinterpret_cast<float*>(part);  // FP32 partials in the FP64-sized buffer
   a.err = err;
   for (int g = 0; g < 4; ++g) a.gmask[g] = 0;
   const int ng = gram_groups(Kq, nb, a.gmask);
@@ -595,8 +611,8 @@ hef_status gram_tc(const float* V, long long ldv, long long n, int K, double* pa
   }
   if (s) return s;
   HEF_LAUNCH("k_gram_tc_reduce", st,
-             k_gram_tc_reduce<<<stride_grid((long long)K * K + K, 4), kThreads, 0, st>>>(
-                 part, K, Kq, ctas, G, c));
+             k_gram_tc_reduce<<<stride_grid(((long long)K * K + K) * 8, 8), kThreads, 0, st>>>(
+                 reinterpret_cast<const float*>(part), K, Kq, ctas, G, c));
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
