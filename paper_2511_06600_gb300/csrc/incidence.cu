@@ -228,11 +228,16 @@ __device__ __forceinline__ void flag(unsigned int* status, unsigned bits, int e)
   atomicMin(&status[1], (unsigned)e);
 }
 
-// Offsets, weight, pin range and duplicate pins of every hyperedge: one
-// thread per hyperedge, its warp together for hyperedges with > 32 pins.
+// Offsets, weight, pin range and duplicate pins of every hyperedge, and its
+// locality key (smallest pin; 0 for an empty hyperedge) with val = caller id:
+// one thread per hyperedge, the pins of a hyperedge with at most kRegPins
+// loaded at once into registers; its warp together for hyperedges with more
+// than 32 pins.
+constexpr int kRegPins = 8;
+
 __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict__ eptr,
                            const int32_t* __restrict__ pins, const double* __restrict__ w,
-                           unsigned int* status) {
+                           unsigned int* status, uint32_t* keys, int32_t* vals) {
   const int lane = threadIdx.x & 31;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (eptr[0] != 0 || eptr[m] != P) flag(status, HEF_BAD_EPTR, 0);
@@ -242,6 +247,7 @@ __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict_
     const long long e = base + threadIdx.x;
     long long a = 0, b = 0;
     bool big = false;
+    int mn = 0x7fffffff;
     if (e < m) {
       a = eptr[e], b = eptr[e + 1];
       if (a < 0 || b < a || b > P) {
@@ -251,19 +257,33 @@ __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict_
       const double we = w[e];
       if (!(we > 0.0 && we <= 1.7976931348623157e308)) flag(status, HEF_BAD_WEIGHT, (int)e);
       const int k = (int)(b - a);
+      bool bad_pin = false, dup = false;
       if (k > 32) {
         big = true;
+      } else if (k > 0 && k <= kRegPins) {
+        int q[kRegPins];
+#pragma unroll
+        for (int i = 0; i < kRegPins; ++i) q[i] = pins[a + min(i, k - 1)];
+#pragma unroll
+        for (int i = 0; i < kRegPins; ++i) {
+          if (i < k) {
+            bad_pin |= q[i] < 0 || q[i] >= n;
+            mn = min(mn, q[i]);
+#pragma unroll
+            for (int j = i + 1; j < kRegPins; ++j) dup |= j < k && q[j] == q[i];
+          }
+        }
       } else {
-        bool bad_pin = false, dup = false;
         for (int i = 0; i < k; ++i) {
           const int p = pins[a + i];
-          if (p < 0 || p >= n) bad_pin = true;
+          bad_pin |= p < 0 || p >= n;
+          mn = min(mn, p);
           for (int j = i + 1; j < k; ++j)
             if (pins[a + j] == p) dup = true;
         }
-        if (bad_pin) flag(status, HEF_BAD_PIN, (int)e);
-        if (dup) flag(status, HEF_DUP_PIN, (int)e);
       }
+      if (bad_pin) flag(status, HEF_BAD_PIN, (int)e);
+      if (dup) flag(status, HEF_DUP_PIN, (int)e);
     }
     unsigned mask = __ballot_sync(0xffffffffu, big);
     while (mask) {
@@ -272,29 +292,25 @@ __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict_
       const long long ba = __shfl_sync(0xffffffffu, a, src), bb = __shfl_sync(0xffffffffu, b, src);
       const int k = (int)(bb - ba);
       bool bad_pin = false, dup = false;
+      int wmn = 0x7fffffff;
       for (int i = lane; i < k; i += 32) {
         const int p = pins[ba + i];
         if (p < 0 || p >= n) bad_pin = true;
+        wmn = min(wmn, p);
         for (int j = i + 1; j < k; ++j)
           if (pins[ba + j] == p) dup = true;
       }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) wmn = min(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));
+      if (lane == src) mn = wmn;
       const long long ee = base + (threadIdx.x & ~31u) + src;
       if (__any_sync(0xffffffffu, bad_pin) && lane == 0) flag(status, HEF_BAD_PIN, (int)ee);
       if (__any_sync(0xffffffffu, dup) && lane == 0) flag(status, HEF_DUP_PIN, (int)ee);
     }
-  }
-}
-
-// key = smallest pin (locality order), val = caller id.
-__global__ void k_edge_keys(int m, const int64_t* __restrict__ eptr, const int32_t* __restrict__ pins,
-                            const unsigned int* status, uint32_t* keys, int32_t* vals) {
-  if (status[0]) return;
-  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < m;
-       e += (long long)gridDim.x * blockDim.x) {
-    int mn = 0x7fffffff;
-    for (long long t = eptr[e]; t < eptr[e + 1]; ++t) mn = min(mn, (int)pins[t]);
-    keys[e] = (eptr[e + 1] > eptr[e]) ? (uint32_t)mn : 0u;
-    vals[e] = (int32_t)e;
+    if (e < m) {
+      keys[e] = b > a ? (uint32_t)mn : 0u;
+      vals[e] = (int32_t)e;
+    }
   }
 }
 
@@ -332,7 +348,19 @@ __global__ void k_edge_fill(int m, int clique_mode, const int64_t* __restrict__ 
       c0 = ceptr[i];
       k = ceptr[i + 1] - c0;
       perm[i] = e;
-      if (k <= 32) {
+      if (k <= kRegPins) {  // pins loaded together, then stored
+        int q[kRegPins];
+#pragma unroll
+        for (int t = 0; t < kRegPins; ++t) q[t] = t < k ? pins[a + t] : 0;
+#pragma unroll
+        for (int t = 0; t < kRegPins; ++t) {
+          if (t < k) {
+            cpins[c0 + t] = q[t];
+            slot_edge[c0 + t] = (int32_t)i;
+            atomicAdd(&deg[q[t]], 1);
+          }
+        }
+      } else if (k <= 32) {
         for (int t = 0; t < k; ++t) {
           const int p = pins[a + t];
           cpins[c0 + t] = p;
@@ -442,12 +470,29 @@ __global__ void k_node_scalars(int n, const int32_t* __restrict__ vptr, const in
   for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < n;
        v += (long long)gridDim.x * blockDim.x) {
     double c = 0.0, b = 0.0, ws = 0.0;
-    for (int t = vptr[v]; t < vptr[v + 1]; ++t) {
-      const int e = vedge[t];
-      const int k = ceptr[e + 1] - ceptr[e];
-      c += ewh[e] * (double)(k - 1);
-      b += ez[e];
-      ws += ewh[e];
+    const int t0 = vptr[v], t1 = vptr[v + 1];
+    // four incidences per round: their hyperedge ids, then their offsets and
+    // weights, each set of loads in flight together (sums in incidence order)
+    for (int t = t0; t < t1; t += 4) {
+      int e[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) e[u] = vedge[min(t + u, t1 - 1)];
+      int k[4];
+      double wh[4], wz[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        k[u] = ceptr[e[u] + 1] - ceptr[e[u]];
+        wh[u] = ewh[e[u]];
+        wz[u] = ez[e[u]];
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (t + u < t1) {
+          c += wh[u] * (double)(k[u] - 1);
+          b += wz[u];
+          ws += wh[u];
+        }
+      }
     }
     wsc[v] = ws;
     dc[v] = c;
@@ -596,17 +641,16 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
   HEF_TRY_CUDA(cudaMemsetAsync(h->status + 1, 0xFF, sizeof(unsigned int), st));
   HEF_TRY_CUDA(cudaMemsetAsync(L.tmp, 0, sizeof(int) * ((m > n ? m : n) + 1), st));
 
-  // 1. validation (one warp per hyperedge)
+  // 1. validation and locality keys (one thread per hyperedge)
   {
     int grid = stride_grid(m > 0 ? m : 1, 8);
-    HEF_LAUNCH("k_validate", st, k_validate<<<grid, kThreads, 0, st>>>((int)n, (int)m, P, eptr, pins, w, h->status));
+    HEF_LAUNCH("k_validate", st, k_validate<<<grid, kThreads, 0, st>>>((int)n, (int)m, P, eptr, pins, w,
+                                                                       h->status, L.keys, L.vals));
     HEF_TRY_CUDA(cudaGetLastError());
   }
   // 2. locality schedule of hyperedges: stable sort by smallest pin
   if (m > 0) {
     int grid = stride_grid(m);
-    HEF_LAUNCH("k_edge_keys", st, k_edge_keys<<<grid, kThreads, 0, st>>>((int)m, eptr, pins, h->status, L.keys, L.vals));
-    HEF_TRY_CUDA(cudaGetLastError());
     HEF_TRY(radix_sort(L.keys, L.vals, m, bits_for(n), L.sb, st));
     // internal CSC offsets
     HEF_LAUNCH("k_edge_sizes", st, k_edge_sizes<<<grid, kThreads, 0, st>>>((int)m, eptr, L.vals, h->status, L.tmp));
