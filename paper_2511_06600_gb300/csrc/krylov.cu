@@ -651,7 +651,7 @@ __device__ __forceinline__ void zero_acc(T (&acc)[NQ][S]) {
 
 // Edge pass of step j (thread per hyperedge).
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(5))
+__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(6))
     k_edge_pass(IncView g, ScalView<T> sv, KView<T> kv, int j) {
   pdl_wait();
   pdl_trigger();
