@@ -125,14 +125,16 @@ __device__ __forceinline__ void strow(T* __restrict__ p, const T (&v)[S]) {
 // Within a warp the values are summed by a transposing butterfly: at each
 // level a lane keeps half of its values and adds its partner's copy of that
 // half, so N values cost about N shuffles instead of 5 N; a lane ends with
-// the warp sum of one slot.  Warps then meet in a fixed order.
+// the warp sum of one slot.  Warps then meet in a fixed order, in the
+// working type; only the CTA's sums are widened to FP64 (conversions and
+// FP64 adds run at 1/64 rate on GB300).
 template <int NQ, int S, typename A>
 __device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* part) {
   constexpr int N = NQ * S;
   constexpr int P = N > 16 ? 32 : (N > 8 ? 16 : (N > 4 ? 8 : (N > 2 ? 4 : (N > 1 ? 2 : 1))));
   constexpr int R = 32 / P;  // lanes that end up holding the same slot
   constexpr int NCH = (N + P - 1) / P;
-  __shared__ double red[kThreads / 32][NCH * P];
+  __shared__ A red[kThreads / 32][NCH * P];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int ch = 0; ch < NCH; ++ch) {
@@ -154,13 +156,13 @@ __device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* p
     }
 #pragma unroll
     for (int o = R / 2; o >= 1; o >>= 1) x[0] += __shfl_xor_sync(0xffffffffu, x[0], o);
-    if (lane % R == 0) red[wid][ch * P + lane / R] = (double)x[0];
+    if (lane % R == 0) red[wid][ch * P + lane / R] = x[0];
   }
   __syncthreads();
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
-    double acc = 0.0;
+    A acc = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][t];
-    part[(size_t)blockIdx.x * N + t] = acc;
+    part[(size_t)blockIdx.x * N + t] = (double)acc;
   }
 }
 
