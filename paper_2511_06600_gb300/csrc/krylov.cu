@@ -290,7 +290,9 @@ __device__ __forceinline__ void seg_sum2(bool valid, int a, int b, Idx idx, RowA
 
 // ---------------------------------------------------------------- start vectors
 
-// D-weighted dots of the raw starts with the trivial vectors -> coef[0].
+// D-weighted dots of the raw starts with the trivial vectors -> coef[0]; the
+// starts, in the working type (and the internal hyperedge order), go to the
+// first chain buffers for k_start_write (one FP64 -> working-type conversion).
 // Rows: [0, n) clique, [n, 2n) star vertices, [2n, 2n+m) star hyperedges.
 template <typename T, int S>
 __global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, ScalView<T> sv, KView<T> kv,
@@ -303,21 +305,25 @@ __global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, ScalView<T> 
   for (int q = 0; q < 3; ++q)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
+  T u[S];
   if (r < g.n) {
     const T d = sv.dc[r];
 #pragma unroll
-    for (int s = 0; s < S; ++s) acc[0][s] = d * (T)x0c[r * S + s];
+    for (int s = 0; s < S; ++s) u[s] = (T)x0c[r * S + s], acc[0][s] = d * u[s];
+    strow<T, S>(kv.Bc[0] + r * S, u);
   } else if (r < 2ll * g.n) {
     const long long v = r - g.n;
     const T d = sv.db[v];
 #pragma unroll
-    for (int s = 0; s < S; ++s) acc[1][s] = d * (T)x0b[v * S + s];
+    for (int s = 0; s < S; ++s) u[s] = (T)x0b[v * S + s], acc[1][s] = d * u[s];
+    strow<T, S>(kv.Bb[0] + v * S, u);
   } else if (r < 2ll * g.n + g.m) {
     const int i = (int)(r - 2ll * g.n);
     const T d = sv.ew[i];
     const long long src = (long long)(g.n + g.perm[i]) * S;
 #pragma unroll
-    for (int s = 0; s < S; ++s) acc[2][s] = d * (T)x0b[src + s];
+    for (int s = 0; s < S; ++s) u[s] = (T)x0b[src + s], acc[2][s] = d * u[s];
+    strow<T, S>(kv.Bb[0] + (long long)(g.n + i) * S, u);
   }
   block_partials_qs<3, S, T>(acc, kv.red.part);
   __shared__ double tot[3 * kMaxS];
@@ -336,11 +342,10 @@ __global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, ScalView<T> 
   }
 }
 
-// x_0 = start minus its trivial components; D-norm -> inv_nu[0].
+// x_0 = start minus its trivial components (in place over the starts that
+// k_start_dots stored); D-norm -> inv_nu[0].
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T> sv, KView<T> kv,
-                                                          const double* __restrict__ x0c,
-                                                          const double* __restrict__ x0b) {
+__global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T> sv, KView<T> kv) {
   pdl_wait();
   pdl_trigger();
   if (g.status[0]) return;
@@ -353,9 +358,10 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T>
   if (r < g.n) {
     const T d = sv.dc[r];
     T u[S];
+    ldrow<T, S>(kv.Bc[0] + r * S, u);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      u[s] = (T)x0c[r * S + s] - (d > 0 ? kv.cfT[(size_t)s * 4] : (T)0);
+      u[s] -= (d > 0 ? kv.cfT[(size_t)s * 4] : (T)0);
       acc[0][s] = d * u[s] * u[s];
     }
     strow<T, S>(kv.Bc[0] + r * S, u);
@@ -363,19 +369,18 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T>
   } else if (r < 2ll * g.n + g.m) {
     const long long rb = r - g.n;  // star row
     T d;
-    long long src;
     int t;
     if (rb < g.n) {
-      d = sv.db[rb], src = rb * S, t = 0;
+      d = sv.db[rb], t = 0;
     } else {
-      const int i = (int)(rb - g.n);
-      d = sv.ew[i], src = (long long)(g.n + g.perm[i]) * S, t = 1;
+      d = sv.ew[rb - g.n], t = 1;
     }
     T u[S];
+    ldrow<T, S>(kv.Bb[0] + rb * S, u);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       const T c = kv.cfT[(size_t)(S + s) * 4 + t];
-      u[s] = (T)x0b[src + s] - (d > 0 ? c : (T)0);
+      u[s] -= (d > 0 ? c : (T)0);
       acc[1][s] = d * u[s] * u[s];
     }
     strow<T, S>(kv.Bb[0] + rb * S, u);
@@ -841,8 +846,7 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   // the launches after the first are programmatically dependent on their
   // predecessor (each kernel waits for it before touching shared buffers)
   HEF_LAUNCH("k_start_write", st,
-             HEF_CHECK_CUDA(launch_dependent(k_start_write<T, S>, grid_all, kThreads, st, g, sv,
-                                             kv, x0c, x0b)));
+             HEF_CHECK_CUDA(launch_dependent(k_start_write<T, S>, grid_all, kThreads, st, g, sv, kv)));
   HEF_CHECK_LAUNCH();
   // one launch for all steps when every row of a pass has a resident thread
   // of its own (small hypergraphs, where per-step launches cost more than the

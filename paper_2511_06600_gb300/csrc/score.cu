@@ -701,7 +701,7 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
 // rows 16-byte aligned; every hyperedge with >= 2 pins has them): thread per
 // hyperedge, its row read with 16-byte loads, kRatioVecs of them in flight.
 // Ratios and the arg-max column in the working type as in Eq. ratios (lowest
-// column on ties); R_e from the spread in FP64; the routing pins from one
+// column on ties); R_e from the spread in FP64 (times 1/Q_H); the routing pins from one
 // gather of the arg-max column over the hyperedge's pins (lowest position on
 // ties).  Gives exactly what k_score_pass2 / k_score_big2 give without
 // gathering every column of Q again.
@@ -751,7 +751,7 @@ __global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restr
         const T r = sp[q] * sp[q] * iq[i];
         if (reduce == HEF_REDUCE_SUM) {
           const double spd = (double)sp[q];
-          sum += spd * spd / QH[i];
+          sum += spd * spd * invQH[i];
         }
         if (r > best) best = r, bcol = i, spb = sp[q];
       }
@@ -769,9 +769,9 @@ __global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restr
     }
     double Re = 0.0;
     if (reduce == HEF_REDUCE_SUM) Re = sum;
-    else if (any) {
+    else if (any) {  // times the FP64 1/Q_H (an FP64 division costs about ten FP64 operations)
       const double spw = (double)spb;
-      Re = spw * spw / QH[bcol];
+      Re = spw * spw * invQH[bcol];
     }
     R_out[oe] = Re;
     if (argvec) argvec[oe] = any ? bcol : -1;
