@@ -22,6 +22,7 @@ namespace {
 using namespace umma;
 
 constexpr int kTcThreads = 256;
+constexpr int kApThreads = 512;  // apply: 16 warps load and split the A tiles
 constexpr int kSlab = 32;                    // V rows per stage (128 B of fp32)
 constexpr uint32_t kWaitIters = 1u << 20;    // bounded mbarrier waits
 
@@ -309,7 +310,7 @@ struct ApplyTcArgs {
 // j >= 32 ka only).  RESB: every B tile stays resident in shared memory
 // (staged once per CTA); otherwise B is staged with A for every block.
 template <bool RESB, int STAGES>
-__global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
+__global__ void __launch_bounds__(kApThreads, 1) k_apply_tc(ApplyTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
   // B tile ka: row jr = Rinv^T row 32 ka + jr, basis values [32 ka, 32 ka + 32)
   auto stage_b = [&](int ka, unsigned char* bhi, unsigned char* blo) {
     const int c0 = ka * 32, nr = brows(ka);
-    for (int f = tid; f < nr * 8; f += kTcThreads) {
+    for (int f = tid; f < nr * 8; f += kApThreads) {
       const int jr = f >> 3, q = f & 7;
       const size_t src = (size_t)(c0 + jr) * a.Kd + c0 + 4 * q;
       const uint32_t off = sw128_offset(jr, 4 * q);
@@ -361,12 +362,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
   uint32_t uses0 = 0u, uses1 = 0u;  // commits per stage so far
   int g = 0;                        // global stage counter (alternates buffers)
   int last_stage = -1;
-  // A slots of a stage: f = tid + 256 k -> tile row f / 8, basis values
-  // 32 ka + 4 (f % 8) .. + 3; the next stage's are loaded while this one is used
-  auto load_a = [&](int tile, int ka, float4 (&buf)[4]) {
+  // A slots of a stage: f = tid + kApThreads k -> tile row f / 8, basis
+  // values 32 ka + 4 (f % 8) .. + 3; the next stage's are loaded while this
+  // one is used
+  constexpr int kAPer = 128 * 8 / kApThreads;
+  auto load_a = [&](int tile, int ka, float4 (&buf)[kAPer]) {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int f = tid + kTcThreads * k;
+    for (int k = 0; k < kAPer; ++k) {
+      const int f = tid + kApThreads * k;
       const int r = f >> 3, q = f & 7;
       const long long row = (long long)tile * 128 + r;
       const int col = ka * 32 + 4 * q;
@@ -381,7 +384,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
       }
     }
   };
-  float4 cur[4], nxt[4];
+  float4 cur[kAPer], nxt[kAPer];
   load_a(blockIdx.x, 0, cur);
   for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const long long row0 = (long long)tile * 128;
@@ -408,8 +411,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
         stage_b(ka, bhi, blo);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const int f = tid + kTcThreads * k;
+      for (int k = 0; k < kAPer; ++k) {
+        const int f = tid + kApThreads * k;
         const int r = f >> 3, q = f & 7;
         const float x[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
         float h[4], l[4];
@@ -420,7 +423,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
         *reinterpret_cast<float4*>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
       }
 #pragma unroll
-      for (int k = 0; k < 4; ++k) cur[k] = nxt[k];
+      for (int k = 0; k < kAPer; ++k) cur[k] = nxt[k];
       fence_async_smem();
       __syncthreads();
       if (tid == 0) {
@@ -462,9 +465,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_apply_tc(ApplyTcArgs a) {
       break;
     }
     tc_fence_after();
-    const int q4 = warp & 3, half = warp >> 2;
+    // warp w reads TMEM lanes 32 (w mod 4) ..; the kApThreads / 128 warps of
+    // a lane quarter take every (kApThreads / 128)-th group of 8 columns
+    const int q4 = warp & 3, part = warp >> 2;
     const long long row = row0 + q4 * 32 + lane;
-    for (int c8 = half; c8 < a.Kq / 8; c8 += 2) {
+    for (int c8 = part; c8 < a.Kq / 8; c8 += kApThreads / 128) {
       float v[8];
       tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c8 * 8u, v);
       tmem_wait_ld();
@@ -536,13 +541,13 @@ hef_status apply_tc(float* V, long long ldv, long long n, int K, const float* Ri
   const size_t smem2 = 1024 + 2 * stage + 64, smem1 = 1024 + stage + 64;
   if (smem_res <= 220 * 1024) {
     HEF_ENSURE_SMEM((k_apply_tc<true, 2>), (int)smem_res);
-    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<true, 2><<<ctas, kTcThreads, smem_res, st>>>(a)));
+    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<true, 2><<<ctas, kApThreads, smem_res, st>>>(a)));
   } else if (smem2 <= 220 * 1024) {
     HEF_ENSURE_SMEM((k_apply_tc<false, 2>), (int)smem2);
-    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<false, 2><<<ctas, kTcThreads, smem2, st>>>(a)));
+    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<false, 2><<<ctas, kApThreads, smem2, st>>>(a)));
   } else {
     HEF_ENSURE_SMEM((k_apply_tc<false, 1>), (int)smem1);
-    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<false, 1><<<ctas, kTcThreads, smem1, st>>>(a)));
+    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<false, 1><<<ctas, kApThreads, smem1, st>>>(a)));
   }
   HEF_CHECK_LAUNCH();
   return HEF_OK;
