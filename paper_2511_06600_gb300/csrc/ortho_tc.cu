@@ -21,8 +21,8 @@ namespace {
 
 using namespace umma;
 
-constexpr int kTcThreads = 256;
 constexpr int kApThreads = 512;  // apply: 16 warps load and split the A tiles
+constexpr int kGrThreads = 512;  // Gram: 16 warps load and split the slabs
 constexpr int kSlab = 32;                    // V rows per stage (128 B of fp32)
 constexpr uint32_t kWaitIters = 1u << 20;    // bounded mbarrier waits
 
@@ -44,7 +44,7 @@ __device__ __forceinline__ void gram_load_slab(const GramTcArgs& a, long long ro
                                                float4 (&buf)[PER]) {
 #pragma unroll
   for (int k = 0; k < PER; ++k) {
-    const int f = threadIdx.x + kTcThreads * k;
+    const int f = threadIdx.x + kGrThreads * k;
     const int r = f & (kSlab - 1), c0 = 4 * (f >> 5);
     if (c0 >= a.Kq) continue;  // padding rows of the tile: zero, written once
     const long long row = rowbase + r;
@@ -69,12 +69,12 @@ __device__ __forceinline__ void gram_load_slab(const GramTcArgs& a, long long ro
 // the earlier blocks' N in the group.  NB blocks of 128 rows pad the
 // transposed slab; STAGES shared-memory stages (2, or 1 when two do not fit).
 template <int NB, int STAGES>
-__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
+__global__ void __launch_bounds__(kGrThreads, 1) k_gram_tc(GramTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int Mpad = NB * 128;
-  constexpr int PER = kSlab * (Mpad / 4) / kTcThreads;  // float4 slots per thread
+  constexpr int PER = kSlab * (Mpad / 4) / kGrThreads;  // float4 slots per thread
   const uint32_t tile_bytes = (uint32_t)Mpad * 128u;
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + 2 * STAGES * tile_bytes);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + STAGES);
@@ -99,7 +99,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   // basis rows [Kq, Mpad) of the transposed tiles are zero for every slab
   for (int q = 0; q < 2 * STAGES; ++q) {
     unsigned char* tile = base + (size_t)q * tile_bytes;
-    for (int e = tid; e < (Mpad - a.Kq) * 32; e += kTcThreads)
+    for (int e = tid; e < (Mpad - a.Kq) * 32; e += kGrThreads)
       *reinterpret_cast<float*>(tile + sw128_offset(a.Kq + e / 32, e % 32)) = 0.f;
   }
   fence_async_smem();
@@ -130,7 +130,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
     // transposed slab: element (basis i, slab row r) at sw128_offset(i, r)
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
-      const int f = tid + kTcThreads * k;
+      const int f = tid + kGrThreads * k;
       const int r = f & (kSlab - 1), c0 = 4 * (f >> 5);
       if (c0 >= a.Kq) continue;  // warp-uniform
       const float x[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
@@ -182,13 +182,15 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
   tc_fence_after();
   float* P = a.part + (size_t)blockIdx.x * a.Kq * a.Kq;
   if (ok && committed > 0) {
-    const int q = warp & 3, half = warp >> 2;
+    // warp w reads TMEM lanes 32 (w mod 4) ..; the kGrThreads / 128 warps of a
+    // lane quarter take every (kGrThreads / 128)-th group of 8 columns
+    const int q = warp & 3, part = warp >> 2;
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
       if (!((gmask >> b) & 1)) continue;
       const int ncol = a.Kq - 128 * b;
       const int i = b * 128 + q * 32 + lane;
-      for (int c8 = half; c8 < ncol / 8; c8 += 2) {
+      for (int c8 = part; c8 < ncol / 8; c8 += kGrThreads / 128) {
         float v[8];
         tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)toff[b] + (uint32_t)c8 * 8u, v);
         tmem_wait_ld();
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(GramTcArgs a) {
     }
   } else {
     // zero this group's block rows
-    for (int e = tid; e < a.Kq * a.Kq; e += kTcThreads)
+    for (int e = tid; e < a.Kq * a.Kq; e += kGrThreads)
       if ((gmask >> ((e / a.Kq) / 128)) & 1) P[e] = 0.f;
     if (!ok && tid == 0) atomicExch(a.err, 1);
     if (!ok && committed > 0) {  // let MMAs in flight finish before TMEM is released
@@ -586,7 +588,7 @@ template <int NB, int STAGES>
 static hef_status launch_gram_tc(const GramTcArgs& a, int ctas, int ng, cudaStream_t st) {
   const size_t smem = 1024 + 2 * (size_t)STAGES * NB * 128 * 128 + 64;
   HEF_ENSURE_SMEM((k_gram_tc<NB, STAGES>), (int)smem);
-  HEF_LAUNCH("k_gram_tc", st, (k_gram_tc<NB, STAGES><<<dim3(ctas, ng), kTcThreads, smem, st>>>(a)));
+  HEF_LAUNCH("k_gram_tc", st, (k_gram_tc<NB, STAGES><<<dim3(ctas, ng), kGrThreads, smem, st>>>(a)));
   return HEF_OK;
 }
 
