@@ -123,45 +123,52 @@ hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, cudaS
 
 // ----------------------------------------------------------------- stable LSD radix sort
 
-__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int N, int shift,
+// Digits of up to kMaxDigitBits bits: keys of b bits take ceil(b / 10)
+// passes of equal width (an 18-bit vertex id: two passes of 9 bits).
+constexpr int kMaxDigitBits = 10;
+constexpr int kMaxBuckets = 1 << kMaxDigitBits;
+
+__global__ void k_radix_hist(const uint32_t* __restrict__ keys, int N, int shift, int nb,
                              int* __restrict__ counts, int ntiles) {
-  __shared__ int hist[256];
-  hist[threadIdx.x] = 0;
+  __shared__ int hist[kMaxBuckets];
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) hist[d] = 0;
   __syncthreads();
+  const uint32_t mask = (uint32_t)nb - 1u;
   const long long base = (long long)blockIdx.x * kTile;
   for (int j = 0; j < kItems; ++j) {
     long long i = base + (long long)j * kThreads + threadIdx.x;
-    if (i < N) atomicAdd(&hist[(keys[i] >> shift) & 255u], 1);
+    if (i < N) atomicAdd(&hist[(keys[i] >> shift) & mask], 1);
   }
   __syncthreads();
-  counts[threadIdx.x * ntiles + blockIdx.x] = hist[threadIdx.x];
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) counts[d * ntiles + blockIdx.x] = hist[d];
 }
 
 // Stable scatter: items are visited in index order (striped over threads),
 // and each item's rank counts the earlier items of its tile with the same
 // digit (warp match + per-warp digit counts).
 __global__ void k_radix_scatter(const uint32_t* __restrict__ keys, const int32_t* __restrict__ vals,
-                                int N, int shift, const int* __restrict__ offs, int ntiles,
+                                int N, int shift, int nb, const int* __restrict__ offs, int ntiles,
                                 uint32_t* __restrict__ okeys, int32_t* __restrict__ ovals) {
-  __shared__ int base[256];
-  __shared__ int wcnt[kThreads / 32][256];
+  __shared__ int base[kMaxBuckets];
+  __shared__ int wcnt[kThreads / 32][kMaxBuckets];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  base[threadIdx.x] = offs[threadIdx.x * ntiles + blockIdx.x];
+  const uint32_t mask = (uint32_t)nb - 1u;
+  for (int d = threadIdx.x; d < nb; d += blockDim.x) base[d] = offs[d * ntiles + blockIdx.x];
   const long long tile0 = (long long)blockIdx.x * kTile;
   for (int j = 0; j < kItems; ++j) {
-    for (int w = 0; w < kThreads / 32; ++w) wcnt[w][threadIdx.x] = 0;
+    for (int d = threadIdx.x; d < nb; d += blockDim.x)
+      for (int w = 0; w < kThreads / 32; ++w) wcnt[w][d] = 0;
     __syncthreads();
     long long i = tile0 + (long long)j * kThreads + threadIdx.x;
     bool valid = i < N;
     uint32_t key = valid ? keys[i] : 0u;
-    int digit = valid ? (int)((key >> shift) & 255u) : 256;
+    int digit = valid ? (int)((key >> shift) & mask) : nb;
     unsigned peers = __match_any_sync(0xffffffffu, digit);
     int rank = __popc(peers & ((1u << lane) - 1u));
     if (valid && rank == 0) wcnt[wid][digit] = __popc(peers);
     __syncthreads();
     // per digit: exclusive prefix over warps, then advance the running base
-    {
-      int d = threadIdx.x;
+    for (int d = threadIdx.x; d < nb; d += blockDim.x) {
       int run = base[d];
       for (int w = 0; w < kThreads / 32; ++w) {
         int c = wcnt[w][d];
@@ -183,8 +190,8 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ keys, const int32_t
 struct SortBufs {
   uint32_t* k_alt;
   int32_t* v_alt;
-  int* counts;  // 256 * ntiles + 1
-  int* bsum;    // scan_tiles(256 * ntiles) + 1
+  int* counts;  // kMaxBuckets * ntiles + 1
+  int* bsum;    // scan_tiles(kMaxBuckets * ntiles) + 1
 };
 
 inline int bits_for(long long maxkey) {
@@ -198,18 +205,22 @@ hef_status radix_sort(uint32_t* keys, int32_t* vals, long long N, int bits, Sort
                       cudaStream_t st) {
   if (N <= 1) return HEF_OK;
   const int ntiles = scan_tiles(N);
+  const int npass = (bits + kMaxDigitBits - 1) / kMaxDigitBits;
+  const int dbits = (bits + npass - 1) / npass;
+  const int nb = 1 << dbits;
   uint32_t* kin = keys;
   int32_t* vin = vals;
   uint32_t* kout = b.k_alt;
   int32_t* vout = b.v_alt;
   int passes = 0;
-  for (int shift = 0; shift < bits; shift += 8, ++passes) {
-    HEF_LAUNCH("k_radix_hist", st, k_radix_hist<<<ntiles, kThreads, 0, st>>>(kin, (int)N, shift, b.counts, ntiles));
+  for (int shift = 0; shift < bits; shift += dbits, ++passes) {
+    HEF_LAUNCH("k_radix_hist", st, k_radix_hist<<<ntiles, kThreads, 0, st>>>(kin, (int)N, shift, nb,
+                                                                           b.counts, ntiles));
     HEF_CHECK_LAUNCH();
-    hef_status s = exclusive_scan(b.counts, b.counts, 256ll * ntiles, b.bsum, st);
+    hef_status s = exclusive_scan(b.counts, b.counts, (long long)nb * ntiles, b.bsum, st);
     if (s) return s;
-    HEF_LAUNCH("k_radix_scatter", st, k_radix_scatter<<<ntiles, kThreads, 0, st>>>(kin, vin, (int)N, shift, b.counts, ntiles, kout,
-                                                 vout));
+    HEF_LAUNCH("k_radix_scatter", st, k_radix_scatter<<<ntiles, kThreads, 0, st>>>(kin, vin, (int)N, shift, nb,
+                                                                                 b.counts, ntiles, kout, vout));
     HEF_CHECK_LAUNCH();
     uint32_t* tk = kin; kin = kout; kout = tk;
     int32_t* tv = vin; vin = vout; vout = tv;
@@ -570,8 +581,8 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   L->vals = c.take<int32_t>(NS > 0 ? NS : 1);
   L->sb.k_alt = c.take<uint32_t>(NS > 0 ? NS : 1);
   L->sb.v_alt = c.take<int32_t>(NS > 0 ? NS : 1);
-  L->sb.counts = c.take<int>(256ll * ntiles + 1);
-  L->sb.bsum = c.take<int>(scan_tiles(256ll * ntiles) + 1);
+  L->sb.counts = c.take<int>((long long)kMaxBuckets * ntiles + 1);
+  L->sb.bsum = c.take<int>(scan_tiles((long long)kMaxBuckets * ntiles) + 1);
   L->tmp = c.take<int>(NT);
   L->scan_bsum = c.take<int>(scan_tiles(NT) + 1);
   L->part = c.take<double>(2ll * 8 * 1024);
