@@ -326,22 +326,38 @@ __global__ void __launch_bounds__(THREADS) k_chol_aug(const double* __restrict__
 #pragma unroll
     for (int p = 0; p < kPB; ++p) npb += (j0 + p < jend) ? 1 : 0;
     if (sizeof(C) == 4 && (K & 3) == 0 && (jend & 3) == 0) {
-      // FP32: four columns per lane (16-byte shared-memory accesses)
-      for (int i = jend + wid; i < K; i += nw) {
-        float* rowi = reinterpret_cast<float*>(W + (size_t)i * W2) + jend;
-        float rj[kPB];
+      // FP32: four columns per lane (16-byte shared-memory accesses), kUR rows
+      // per warp at a time, so that a lane has 4 kUR independent FMA chains
+      // (one row with 1024 threads, whose 64 registers hold no more)
+      constexpr int kUR = THREADS >= 1024 ? 1 : 4;
+      for (int i0 = jend + wid * kUR; i0 < K; i0 += nw * kUR) {
+        float rj[kUR][kPB];
 #pragma unroll
-        for (int p = 0; p < kPB; ++p)
-          rj[p] = (p < npb && pk[p]) ? (float)W[(size_t)(j0 + p) * W2 + i] : 0.0f;
+        for (int r = 0; r < kUR; ++r)
+#pragma unroll
+          for (int p = 0; p < kPB; ++p)
+            rj[r][p] = (i0 + r < K && p < npb && pk[p]) ? (float)W[(size_t)(j0 + p) * W2 + i0 + r] : 0.0f;
         for (int v = lane; v < K / 4; v += 32) {
-          float4 acc = reinterpret_cast<float4*>(rowi)[v];
+          float4 acc[kUR];
+#pragma unroll
+          for (int r = 0; r < kUR; ++r)
+            acc[r] = i0 + r < K ? reinterpret_cast<const float4*>(
+                                      reinterpret_cast<const float*>(W + (size_t)(i0 + r) * W2) + jend)[v]
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
           for (int p = 0; p < kPB; ++p) {
             const float4 b =
                 reinterpret_cast<const float4*>(reinterpret_cast<float*>(W + (size_t)(j0 + p) * W2) + jend)[v];
-            acc.x -= rj[p] * b.x, acc.y -= rj[p] * b.y, acc.z -= rj[p] * b.z, acc.w -= rj[p] * b.w;
+#pragma unroll
+            for (int r = 0; r < kUR; ++r) {
+              acc[r].x -= rj[r][p] * b.x, acc[r].y -= rj[r][p] * b.y;
+              acc[r].z -= rj[r][p] * b.z, acc[r].w -= rj[r][p] * b.w;
+            }
           }
-          reinterpret_cast<float4*>(rowi)[v] = acc;
+#pragma unroll
+          for (int r = 0; r < kUR; ++r)
+            if (i0 + r < K)
+              reinterpret_cast<float4*>(reinterpret_cast<float*>(W + (size_t)(i0 + r) * W2) + jend)[v] = acc[r];
         }
       }
     } else {
