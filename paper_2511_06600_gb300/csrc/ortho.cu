@@ -186,7 +186,7 @@ template <typename C>
 __device__ __forceinline__ C pivot_rsqrt(C d);
 template <>
 __device__ __forceinline__ float pivot_rsqrt<float>(float d) {
-  return 1.0f / sqrtf(d);
+  return rsqrtf(d);  // the fast path's R is refined by the second CholQR pass
 }
 template <>
 __device__ __forceinline__ double pivot_rsqrt<double>(double d) {
