@@ -66,12 +66,12 @@ __device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;"
 __device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
 
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block,
-                                    cudaStream_t st, Args... args) {
+inline cudaError_t launch_dependent_smem(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                                         size_t smem, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
-  cfg.dynamicSmemBytes = 0;
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -79,6 +79,12 @@ inline cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, uns
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                                    cudaStream_t st, Args... args) {
+  return launch_dependent_smem(kernel, grid, block, 0, st, args...);
 }
 
 inline int num_sms() {

@@ -45,7 +45,11 @@ __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
   return incl - v;
 }
 
-__global__ void k_scan_tiles(const int* __restrict__ in, int N, int* __restrict__ bsum) {
+// Tile sums bsum[b] of in; the last CTA to finish (counter, zero on entry and
+// on exit) then scans them in place (exclusive) and writes the grand total to
+// bsum[nb].
+__global__ void k_scan_tiles(const int* __restrict__ in, int N, int* __restrict__ bsum,
+                             unsigned int* counter) {
   const long long base = (long long)blockIdx.x * kTile;
   int s = 0;
   for (int j = 0; j < kItems; ++j) {
@@ -55,33 +59,22 @@ __global__ void k_scan_tiles(const int* __restrict__ in, int N, int* __restrict_
   int total;
   block_exclusive_scan(s, &total);
   if (threadIdx.x == 0) bsum[blockIdx.x] = total;
-}
-
-// One CTA of 1024 threads scans the nb tile sums in place (exclusive) and
-// writes the grand total to bsum[nb].
-__global__ void k_scan_bsums(int* bsum, int nb) {
-  __shared__ int part[1024];
-  const int per = (nb + 1023) / 1024;
+  if (!last_block_done(counter)) return;
+  const int nb = gridDim.x;
+  const int per = (nb + kThreads - 1) / kThreads;
   const int b0 = threadIdx.x * per;
-  int s = 0;
+  int t = 0;
   for (int i = 0; i < per; ++i)
-    if (b0 + i < nb) s += bsum[b0 + i];
-  part[threadIdx.x] = s;
-  __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    int y = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-    __syncthreads();
-    part[threadIdx.x] += y;
-    __syncthreads();
-  }
-  int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+    if (b0 + i < nb) t += __ldcg(bsum + b0 + i);
+  int grand;
+  int run = block_exclusive_scan(t, &grand);
   for (int i = 0; i < per; ++i)
     if (b0 + i < nb) {
-      int t = bsum[b0 + i];
+      const int v = __ldcg(bsum + b0 + i);
       bsum[b0 + i] = run;
-      run += t;
+      run += v;
     }
-  if (threadIdx.x == 1023) bsum[nb] = part[1023];
+  if (threadIdx.x == 0) bsum[nb] = grand;
 }
 
 __global__ void k_scan_apply(const int* __restrict__ in, int N, const int* __restrict__ bsum,
@@ -107,15 +100,16 @@ __global__ void k_scan_apply(const int* __restrict__ in, int N, const int* __res
 inline int scan_tiles(long long N) { return (int)((N + kTile - 1) / kTile); }
 
 // out[0..N] = exclusive scan of in[0..N); out[N] = total.  bsum needs
-// scan_tiles(N) + 1 ints.  `in` and `out` may alias.
-hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, cudaStream_t st) {
+// scan_tiles(N) + 1 ints; counter is zero on entry (and on exit).  `in` and
+// `out` may alias.
+hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, unsigned int* counter,
+                          cudaStream_t st) {
   int nb = scan_tiles(N);
   if (nb == 0) {
     HEF_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(int), st));
     return HEF_OK;
   }
-  HEF_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<nb, kThreads, 0, st>>>(in, (int)N, bsum));
-  HEF_LAUNCH("k_scan_bsums", st, k_scan_bsums<<<1, 1024, 0, st>>>(bsum, nb));
+  HEF_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<nb, kThreads, 0, st>>>(in, (int)N, bsum, counter));
   HEF_LAUNCH("k_scan_apply", st, k_scan_apply<<<nb, kThreads, 0, st>>>(in, (int)N, bsum, out));
   HEF_CHECK_LAUNCH();
   return HEF_OK;
@@ -190,6 +184,7 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ keys, const int32_t
 struct SortBufs {
   uint32_t* k_alt;
   int32_t* v_alt;
+  unsigned int* counter;  // of the scans (zero between calls)
   int* counts;  // kMaxBuckets * ntiles + 1
   int* bsum;    // scan_tiles(kMaxBuckets * ntiles) + 1
 };
@@ -217,7 +212,7 @@ hef_status radix_sort(uint32_t* keys, int32_t* vals, long long N, int bits, Sort
     HEF_LAUNCH("k_radix_hist", st, k_radix_hist<<<ntiles, kThreads, 0, st>>>(kin, (int)N, shift, nb,
                                                                            b.counts, ntiles));
     HEF_CHECK_LAUNCH();
-    hef_status s = exclusive_scan(b.counts, b.counts, (long long)nb * ntiles, b.bsum, st);
+    hef_status s = exclusive_scan(b.counts, b.counts, (long long)nb * ntiles, b.bsum, b.counter, st);
     if (s) return s;
     HEF_LAUNCH("k_radix_scatter", st, k_radix_scatter<<<ntiles, kThreads, 0, st>>>(kin, vin, (int)N, shift, nb,
                                                                                  b.counts, ntiles, kout, vout));
@@ -550,6 +545,7 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   const int ntiles = scan_tiles(NS > 0 ? NS : 1);
   L->h.status = c.take<unsigned int>(64);
   L->h.counter = L->h.status + 32;
+  L->sb.counter = L->h.status + 34;  // zeroed with the status word at the start of a build
   L->h.perm = c.take<int32_t>(m > 0 ? m : 1);
   L->h.ceptr = c.take<int32_t>(m + 1);
   L->h.cpins = c.take<int32_t>(P > 0 ? P : 1);
@@ -666,7 +662,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     // internal CSC offsets
     HEF_LAUNCH("k_edge_sizes", st, k_edge_sizes<<<grid, kThreads, 0, st>>>((int)m, eptr, L.vals, h->status, L.tmp));
     HEF_TRY_CUDA(cudaGetLastError());
-    HEF_TRY(exclusive_scan(L.tmp, h->ceptr, m, L.scan_bsum, st));
+    HEF_TRY(exclusive_scan(L.tmp, h->ceptr, m, L.scan_bsum, L.sb.counter, st));
     HEF_TRY_CUDA(cudaMemsetAsync(L.tmp, 0, sizeof(int) * (n + 1), st));
     HEF_LAUNCH("k_edge_fill", st, k_edge_fill<<<grid, kThreads, 0, st>>>((int)m, clique_mode, eptr, pins, w, L.vals, h->ceptr,
                                            h->status, h->counter, h->perm, h->cpins, h->slot_edge,
@@ -677,7 +673,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     HEF_LAUNCH("k_big_flags", st, k_big_flags<<<grid, kThreads, 0, st>>>((int)m, h->ceptr, h->status,
                                                                         h->big_pos));
     HEF_TRY_CUDA(cudaGetLastError());
-    HEF_TRY(exclusive_scan(h->big_pos, h->big_pos, m, L.scan_bsum, st));
+    HEF_TRY(exclusive_scan(h->big_pos, h->big_pos, m, L.scan_bsum, L.sb.counter, st));
     HEF_LAUNCH("k_windows", st, k_windows<<<stride_grid(m + 1), kThreads, 0, st>>>(
                                     (int)m, P, h->ceptr, h->status, h->win_edge));
     HEF_TRY_CUDA(cudaGetLastError());
@@ -691,7 +687,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     HEF_TRY_CUDA(cudaMemsetAsync(h->totals, 0, 8 * sizeof(double), st));
   }
   // 3. vertex-major transpose: stable sort of CSC slots by vertex
-  HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, st));
+  HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, L.sb.counter, st));
   if (P > 0) {
     int grid = stride_grid(P);
     HEF_LAUNCH("k_slot_keys", st, k_slot_keys<<<grid, kThreads, 0, st>>>(P, h->cpins, h->status, L.keys, h->vslot));

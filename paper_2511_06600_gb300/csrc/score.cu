@@ -149,6 +149,9 @@ __device__ __forceinline__ void cta_edge_extrema(const T* __restrict__ Q, long l
 template <typename T, int NC>
 __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restrict__ Q, long long ldq,
                                                     int K, double* bpart, T* spread, int ldsp) {
+  // the staged pass 1 may start beside this one: it reads bpart only after
+  // its dependency wait
+  pdl_trigger();
   if (g.status[0]) return;
   __shared__ T smx[8 * 32 * NC], smn[8 * 32 * NC];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -182,6 +185,9 @@ __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restri
 template <int NC>
 __device__ __forceinline__ void finish_qh(const GridRed& red, int K, const double* __restrict__ bpart,
                                           int nbpart, double* QH, double* invQH, double* QH_out) {
+  // k_score_big1 (bpart) complete: a no-op unless this pass was launched as
+  // its programmatic dependent
+  pdl_wait();
   __shared__ double tot[32 * NC];
   if (grid_reduce(red, K, tot)) {
     for (int col = threadIdx.x; col < K; col += blockDim.x) {
@@ -892,16 +898,20 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
     const int pitch = (int)(row_bytes / sizeof(T));
     if (g4) {
       HEF_ENSURE_SMEM((k_score_pass1_bulk<T, NC, true>), (int)smem);
+      // a programmatic dependent of k_score_big1: it runs beside it and waits
+      // for it only before the reduction that reads bpart
       HEF_LAUNCH("k_score_pass1", st,
-                 k_score_pass1_bulk<T, NC, true><<<num_sms(), kBulkThreads, smem, st>>>(
-                     g, Q, ldq, K, pitch, row_bytes, nst, red, w.bpart, w.bgrid, w.QH, w.invQH,
-                     QH_out, spread, ldsp, scal_view<T>(inc).ew, inc->status, tmap));
+                 HEF_CHECK_CUDA(launch_dependent_smem(
+                     k_score_pass1_bulk<T, NC, true>, num_sms(), kBulkThreads, smem, st, g, Q, ldq, K,
+                     pitch, row_bytes, nst, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out, spread, ldsp,
+                     scal_view<T>(inc).ew, inc->status, tmap)));
     } else {
       HEF_ENSURE_SMEM((k_score_pass1_bulk<T, NC, false>), (int)smem);
       HEF_LAUNCH("k_score_pass1", st,
-                 k_score_pass1_bulk<T, NC, false><<<num_sms(), kBulkThreads, smem, st>>>(
-                     g, Q, ldq, K, pitch, row_bytes, nst, red, w.bpart, w.bgrid, w.QH, w.invQH,
-                     QH_out, spread, ldsp, scal_view<T>(inc).ew, inc->status, tmap));
+                 HEF_CHECK_CUDA(launch_dependent_smem(
+                     k_score_pass1_bulk<T, NC, false>, num_sms(), kBulkThreads, smem, st, g, Q, ldq,
+                     K, pitch, row_bytes, nst, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out, spread,
+                     ldsp, scal_view<T>(inc).ew, inc->status, tmap)));
     }
   } else {
     const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<T, NC>, kThreads));
