@@ -236,6 +236,11 @@ hef_status hef_orthonormalize(int64_t n, int32_t K, int32_t dtype, void* V,
  * Q_H[i] = sum_e w_e spread_{e,i}^2 (FP64, fixed summation order);
  * r_{e,i} = spread_{e,i}^2 / Q_H[i] for columns with Q_H[i] > 1e-300;
  * R_e = max_i r_{e,i} (HEF_REDUCE_MAX) or sum_i r_{e,i} (HEF_REDUCE_SUM).
+ * Precision: spreads in the basis dtype; the arg-max column is chosen on the
+ * ratios in that dtype; R_e is formed in FP64 as spread^2 times the FP64
+ * 1/Q_H (within an ulp or two of the quotient).  The workspace call and the
+ * no-alloc call sum Q_H in the same order; the no-alloc call gathers Q again
+ * instead of storing the spreads.
  * Outputs are indexed by the caller's hyperedge ids:
  *   R_out[m] double; QH_out[K] double (nullable);
  *   argvec[m] (nullable): the i attaining the max (lowest i on ties, -1 if

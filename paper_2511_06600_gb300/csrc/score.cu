@@ -554,7 +554,7 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
 // arg-max column (lowest on ties), its pins (lowest position on ties), R_e.
 template <typename T, int NC>
 __device__ __forceinline__ void score_edge_out(IncView g, const T* __restrict__ Q, long long ldq,
-                                               int K, int reduce, const double* __restrict__ QH,
+                                               int K, int reduce, const double* __restrict__ invQH,
                                                const T (&iq)[NC], const bool (&use)[NC], int e,
                                                int a, int b, const T (&mx)[NC], const T (&mn)[NC],
                                                double* R_out, int32_t* argvec, int32_t* pmax,
@@ -570,7 +570,7 @@ __device__ __forceinline__ void score_edge_out(IncView g, const T* __restrict__ 
       const T r = sp * sp * iq[c];
       if (reduce == HEF_REDUCE_SUM) {
         const double spd = (double)sp;
-        sum += spd * spd / QH[lane + 32 * c];
+        sum += spd * spd * invQH[lane + 32 * c];
       }
       if (r > best) best = r, bcol = lane + 32 * c;
     }
@@ -614,7 +614,7 @@ __device__ __forceinline__ void score_edge_out(IncView g, const T* __restrict__ 
     if (reduce == HEF_REDUCE_SUM) Re = sum;
     else if (any) {
       const double spw = (double)(vmax - vmin);
-      Re = spw * spw / QH[bcol];
+      Re = spw * spw * invQH[bcol];  // as in k_score_ratio
     }
     R_out[oe] = Re;
     if (argvec) argvec[oe] = any ? bcol : -1;
@@ -653,7 +653,7 @@ __global__ void __launch_bounds__(256) k_score_big2(IncView g, const T* __restri
     T mx[NC], mn[NC];
     cta_edge_extrema<T, NC>(Q, ldq, K, g.cpins, a, b, smx, smn, mx, mn);
     if ((threadIdx.x >> 5) == 0)
-      score_edge_out<T, NC>(g, Q, ldq, K, reduce, QH, iq, use, e, a, b, mx, mn, R_out, argvec, pmax,
+      score_edge_out<T, NC>(g, Q, ldq, K, reduce, invQH, iq, use, e, a, b, mx, mn, R_out, argvec, pmax,
                             pmin);
   }
 }
@@ -694,10 +694,10 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
       two_edge_extrema<T, NC>(Q, ldq, K, [&](int t) { return g.cpins[t]; }, a0, b0, a1, b1, lane,
                               mx0, mn0, mx1, mn1);
       if (b0 > a0)
-        score_edge_out<T, NC>(g, Q, ldq, K, reduce, QH, iq, use, (int)(grp * 32 + i), a0, b0, mx0, mn0,
+        score_edge_out<T, NC>(g, Q, ldq, K, reduce, invQH, iq, use, (int)(grp * 32 + i), a0, b0, mx0, mn0,
                               R_out, argvec, pmax, pmin);
       if (b1 > a1)
-        score_edge_out<T, NC>(g, Q, ldq, K, reduce, QH, iq, use, (int)(grp * 32 + i + 1), a1, b1, mx1,
+        score_edge_out<T, NC>(g, Q, ldq, K, reduce, invQH, iq, use, (int)(grp * 32 + i + 1), a1, b1, mx1,
                               mn1, R_out, argvec, pmax, pmin);
     }
   }
