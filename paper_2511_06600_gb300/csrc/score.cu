@@ -285,7 +285,9 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restr
 // in slot order, through a ring of `nst` stages of kWinSlots rows (row pitch
 // `pitch` elements, `row_bytes` a multiple of 16): slot t sits in ring row
 // (t - first slot of the range) mod (nst kWinSlots).  Warp 0 produces: it
-// copies window j's rows once the consumers have released window j - nst
+// copies window j's rows (G4: four-row tensor-map gathers, tile::gather4 with
+// a box one row high; else one bulk copy per row) once the consumers have
+// released window j - nst
 // (plus the window after the range, whose rows the range's last hyperedges
 // may reach), with the offsets and weights of the hyperedges the window owns
 // (aligned supersets of ceptr[ef..el] and ew[ef..el), when at most
