@@ -67,6 +67,7 @@ struct KView {
   T* nuT;          // inv_nu in the working type
   T* cfT;          // (k+1) x 2S x 4: [ct, ct2, alpha * nu_{j-1}, beta * nu_{j-2}]
   double* te;      // 3S: star edge-row dots of the current step
+  double* itot;    // 3: 1 / the incidence's totals (0 where a total is 0), set by k_start_dots
   GridRed red;     // reduction scratch shared by all kernels (serialised)
   T* tape_c;       // nullable: u_j of the clique chains, (k+1) x n x S
   T* tape_b;       // nullable: u_j of the star chains, (k+1) x (n+m) x S
@@ -328,6 +329,8 @@ __global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, ScalView<T> 
   block_partials_qs<3, S, T>(acc, kv.red.part);
   __shared__ double tot[3 * kMaxS];
   if (grid_reduce(kv.red, 3 * S, tot)) {
+    if (threadIdx.x < 3)
+      kv.itot[threadIdx.x] = g.totals[threadIdx.x] > 0 ? 1.0 / g.totals[threadIdx.x] : 0.0;
     for (int s = threadIdx.x; s < S; s += blockDim.x) {
       double* cc = kv.coef + (size_t)s * 4;
       double* cb = kv.coef + (size_t)(S + s) * 4;
@@ -543,13 +546,13 @@ __device__ __forceinline__ void node_final(const IncView& g, const KView<T>& kv,
     const int op = c / S, s = c % S;
     double* cf = kv.coef + ((size_t)j * 2 * S + c) * 4;
     if (op == 0) {
-      cf[0] = g.totals[0] > 0 ? tn[0 * S + s] / g.totals[0] : 0.0;
+      cf[0] = tn[0 * S + s] * kv.itot[0];  // products: FP64 division is slow here
       cf[1] = 0.0;
       cf[2] = j >= 2 ? tn[1 * S + s] : 0.0;
       cf[3] = j >= 3 ? tn[2 * S + s] : 0.0;
     } else {
-      cf[0] = g.totals[1] > 0 ? tn[3 * S + s] / g.totals[1] : 0.0;
-      cf[1] = g.totals[2] > 0 ? kv.te[0 * S + s] / g.totals[2] : 0.0;
+      cf[0] = tn[3 * S + s] * kv.itot[1];
+      cf[1] = kv.te[0 * S + s] * kv.itot[2];
       cf[2] = j >= 2 ? tn[4 * S + s] + kv.te[1 * S + s] : 0.0;
       cf[3] = j >= 3 ? tn[5 * S + s] + kv.te[2 * S + s] : 0.0;
     }
@@ -817,6 +820,7 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->nuT = c.take<T>((size_t)(k + 1) * 2 * S);
   kv->cfT = c.take<T>((size_t)(k + 1) * 2 * S * 4);
   kv->te = c.take<double>((size_t)3 * S);
+  kv->itot = c.take<double>(4);
   kv->red.part = c.take<double>((size_t)maxblk * 6 * S);
   kv->red.gpart = c.take<double>((size_t)red_groups((int)maxblk) * 6 * S);
   kv->red.gcnt = c.take<unsigned int>(red_groups((int)maxblk) + 1);
