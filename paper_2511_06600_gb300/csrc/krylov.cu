@@ -394,7 +394,7 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T>
   if (grid_reduce(kv.red, 2 * S, tot)) {
     for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
       const double nu2 = tot[c];  // slot op * S + s == chain c
-      kv.inv_nu[c] = nu2 > 0.0 ? 1.0 / sqrt(nu2) : 0.0;
+      kv.inv_nu[c] = nu2 > 0.0 ? rsqrt(nu2) : 0.0;
       kv.nuT[c] = (T)kv.inv_nu[c];
     }
   }
@@ -628,7 +628,7 @@ __device__ __forceinline__ void update_final(const KView<T>& kv, int S, int j, c
   for (int c = threadIdx.x; c < 2 * S; c += blockDim.x) {
     const double nu2 = tot[c];
     const bool alive = nu0[c] > 0.0 && nu2 > kv.tol * kv.tol;
-    kv.inv_nu[(size_t)j * 2 * S + c] = alive ? 1.0 / sqrt(nu2) : 0.0;
+    kv.inv_nu[(size_t)j * 2 * S + c] = alive ? rsqrt(nu2) : 0.0;  // one FP64 rsqrt
     kv.nuT[(size_t)j * 2 * S + c] = (T)kv.inv_nu[(size_t)j * 2 * S + c];
   }
 }
