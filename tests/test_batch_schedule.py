@@ -78,3 +78,21 @@ def test_null_array_in_an_item_is_rejected():
     out = (ctypes.c_int32 * len(SIZES))()
     assert B.lib().hef_batch_schedule(arr, len(SIZES), 5, 2, 4, out) != HEF_OK
     assert B.lib().hef_batch_schedule(items(SIZES), len(SIZES), 5, 2, 4, None) != HEF_OK
+
+
+def test_incidence_workspace_size_query():
+    """hef_incidence_workspace_bytes (host arithmetic over the layout): 0 for
+    negative sizes, 256-byte multiples, never smaller for a larger hypergraph,
+    and room for at least the CSC, CSR and per-edge / per-vertex arrays."""
+    f = B.lib().hef_incidence_workspace_bytes
+    assert f(-1, 5, 5) == 0 and f(5, -1, 5) == 0 and f(5, 5, -1) == 0
+    base = f(210000, 200000, 716793)
+    assert base % 256 == 0
+    for n, m, P in [(210001, 200000, 716793), (210000, 200001, 716793), (210000, 200000, 716794),
+                    (420000, 400000, 1433586)]:
+        assert f(n, m, P) >= base
+    n, m, P = 210000, 200000, 716793
+    # ceptr, perm, 3 FP64 + 3 FP32 edge arrays; vptr, 5 FP64 + 5 FP32 vertex
+    # arrays; cpins, slot_edge, vedge, vslot
+    floor = 4 * (2 * m) + 8 * 3 * m + 4 * 3 * m + 4 * n + 8 * 5 * n + 4 * 5 * n + 4 * 4 * P
+    assert base >= floor
