@@ -185,9 +185,11 @@ hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int32_t S,
  * barriers (a barrier that waits too long sets HEF_WAIT_TIMEOUT in the
  * incidence's status word instead of hanging); larger ones, and every call
  * with on = 0, use three launches per step.  Both forms give the same
- * results up to the order of floating-point sums.  The persistent form
- * assumes the kernel has the GPU to itself; hef_resistance_batched always
- * uses the per-step form.  on = 2 exercises the timeout path: the persistent
+ * results up to the order of floating-point sums.  The persistent form is a
+ * cooperative launch: the runtime starts it only with all of its CTAs
+ * resident (work on other streams delays it rather than starving a barrier);
+ * if the runtime refuses the grid, the per-step form runs instead.
+ * hef_resistance_batched always uses the per-step form.  on = 2 exercises the timeout path: the persistent
  * form (when it applies) is launched with twice the CTAs that can be
  * resident, so its first barrier cannot complete; the launch ends after the
  * wait limit with HEF_WAIT_TIMEOUT set and later calls on that incidence do

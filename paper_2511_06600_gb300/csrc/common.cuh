@@ -81,6 +81,24 @@ inline cudaError_t launch_dependent_smem(void (*kernel)(KArgs...), unsigned grid
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
+// Cooperative launch: the runtime starts the grid only with every CTA
+// resident at once (or refuses a grid that can never be), which is what a
+// kernel with grid-wide barriers needs when other work shares the GPU.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_cooperative(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                                      cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(block);
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 template <typename... KArgs, typename... Args>
 inline cudaError_t launch_dependent(void (*kernel)(KArgs...), unsigned grid, unsigned block,
                                     cudaStream_t st, Args... args) {

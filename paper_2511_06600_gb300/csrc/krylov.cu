@@ -857,13 +857,28 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   // work); larger ones run faster as three launches per step, whose CTAs each
   // take one item per thread
   const int res = persistent ? num_sms() * resident_ctas(k_krylov_steps<T, S>, kThreads) : 0;
-  if (persistent && (t_force_oversized || (long long)res * kThreads >= 2 * n + m)) {
-    int grid = std::max(1, std::min(res, grid_all));
-    if (t_force_oversized) grid = std::min(2 * res, grid_all);
+  if (persistent && t_force_oversized) {
+    // the timeout test: a plain launch of twice the resident grid, so that
+    // the first barrier cannot complete and its bounded wait runs out
+    const int grid = std::max(1, std::min(2 * res, grid_all));
     HEF_LAUNCH("k_krylov_steps", st, k_krylov_steps<T, S><<<grid, kThreads, 0, st>>>(
                                          g, sv, kv, k, V, ldv, kv.gen, inc->status));
     HEF_CHECK_LAUNCH();
     return HEF_OK;
+  }
+  if (persistent && (long long)res * kThreads >= 2 * n + m) {
+    // cooperative: the runtime guarantees that all CTAs are resident at once
+    // (other work on the GPU delays the start instead of starving a barrier);
+    // if it refuses the grid, the per-step form below runs instead
+    const int grid = std::max(1, std::min(res, grid_all));
+    cudaError_t e = cudaSuccess;
+    HEF_LAUNCH("k_krylov_steps", st,
+               e = launch_cooperative(k_krylov_steps<T, S>, grid, kThreads, st, g, sv, kv, k, V,
+                                      ldv, kv.gen, inc->status));
+    if (e == cudaSuccess) return HEF_OK;
+    if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorNotSupported)
+      return set_error(HEF_ERR_CUDA, "k_krylov_steps: %s", cudaGetErrorString(e));
+    (void)cudaGetLastError();
   }
   for (int j = 1; j <= k; ++j) {
     HEF_LAUNCH("k_edge_pass", st,

@@ -993,9 +993,13 @@ hef_status noalloc_scratch(void** out) {
 // Same layout as carve_score, with the CTA count capped so that the per-CTA
 // partial sums fit the fixed scratch.
 size_t carve_score_capped(void* base, int K, size_t cap, ScoreWs* w) {
-  // per-CTA partials plus group partials (1/32 as many), Q_H, 1/Q_H, counters
+  // Q_H, 1/Q_H, counters, one partial row per SM for the large-hyperedge pass
+  // (bgrid = num_sms() rows, as taken below), a spare group-partial row and
+  // the alignment of the six takes; what is left holds the per-CTA partials
+  // and their group partials (1/32 as many)
   const size_t fixed = 6 * 256 + 2 * (size_t)K * sizeof(double) + 64 * sizeof(unsigned int) +
-                       (size_t)K * sizeof(double) + 64 * (size_t)K * sizeof(double);
+                       (size_t)K * sizeof(double) + (size_t)num_sms() * K * sizeof(double);
+  if (fixed >= cap) return cap + 1;
   long long g = (long long)num_sms() * 4;
   const long long fit = (long long)((cap - fixed) / ((size_t)K * sizeof(double) * 33 / 32 + 1));
   if (g > fit) g = fit;

@@ -46,3 +46,35 @@ def test_noalloc_rejects_oversized_K():
     with pytest.raises(hef.HefError) as ei:
         hef.edge_resistance_noalloc(inc, Q, 513)
     assert ei.value.status == -6
+
+
+@pytest.mark.parametrize("K,dtype", [(384, torch.float32), (512, torch.float32),
+                                     (512, torch.float64)])
+def test_noalloc_large_K_pareto_netlist_matches_workspace_call(K, dtype):
+    """Large K takes the capped per-CTA partials; the Pareto tail gives
+    hyperedges of more than 64 pins, which the large-hyperedge kernels score.
+    Any basis is a valid input to the scoring, so Q is a seeded random matrix."""
+    import paper_2511_06600_gb300 as hef
+    from netlists.synth import grid_netlist
+    H = grid_netlist(120, 80, 9000, seed=11, size_law="pareto400", radius_law="sqrt",
+                     long_range=0.02)
+    assert int(H.sizes().max()) > 64
+    t = to_dev(H)
+    inc = hef.build_incidence(H.n, t["eptr"], t["pins"], t["w"])
+    g = torch.Generator(device="cpu").manual_seed(K)
+    ld = hef.padded_ld(K, dtype)
+    Q = torch.zeros(H.n, ld, dtype=dtype)
+    Q[:, :K] = torch.randn(H.n, K, generator=g, dtype=torch.float64).to(dtype)
+    Q = Q.to("cuda:0")
+    ref = hef.edge_resistance(inc, Q, K)
+    inc.check()
+    ref = {key: v.cpu().numpy() for key, v in ref.items()}
+    for _ in range(2):
+        got = hef.edge_resistance_noalloc(inc, Q, K)
+        torch.cuda.synchronize()
+        got = {key: v.cpu().numpy() for key, v in got.items()}
+        assert np.allclose(got["QH"], ref["QH"], rtol=1e-12, atol=0)
+        assert np.allclose(got["R"], ref["R"], rtol=1e-12, atol=0)
+        assert np.array_equal(got["argvec"], ref["argvec"])
+        assert np.array_equal(got["pmax"], ref["pmax"])
+        assert np.array_equal(got["pmin"], ref["pmin"])
