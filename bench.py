@@ -204,12 +204,15 @@ def kernel_model(name, H, K, S, k, esz):
         return "hbm", float(m) * K * esz + 4.0 * (m + 1) + 4.0 * m + 4.0 * P + esz * P + 20.0 * m
     if name == "k_score_pass2":
         return "hbm", n * K * esz + 4.0 * P + 4.0 * (m + 1) + 8.0 * m + 4.0 * m + 20.0 * m
-    if name == "k_edge_pass":   # reads node rows of 2 chains, writes s_e and star edge rows
-        return "hbm", 4.0 * P + 4.0 * (m + 1) + 8.0 * m + esz * S * (2 * n + 3 * m)
-    if name == "k_node_pass":
-        return "hbm", 4.0 * P + 4.0 * (n + 1) + 8.0 * (2 * m + 6 * n) + esz * S * (2 * m + 6 * n)
-    if name == "k_update":
-        return "hbm", esz * S * (2 * n + m) * 4.0 + 8.0 * (2 * n + m)
+    # Krylov passes: vertex records [x_c | x_b] (2S values), star hyperedge
+    # rows (S values), edge records [wh s | z x_b] (2S values); the per-edge
+    # and per-vertex scalars are read in the basis type (esz bytes)
+    if name == "k_edge_pass":   # pin lists; vertex records once; own star rows (x_{j-1}, x_{j-2}); Ye, Er written
+        return "hbm", 4.0 * P + 4.0 * (m + 1) + 3.0 * esz * m + esz * S * (2 * n + 5 * m)
+    if name == "k_node_pass":   # incidence; own records (x_{j-1}, x_{j-2}); Er once; Yv and the V archive written
+        return "hbm", 4.0 * P + 4.0 * (n + 1) + 5.0 * esz * n + esz * S * (8 * n + 2 * m)
+    if name == "k_update":      # Y, x_{j-1}, x_{j-2} read and x_j written, vertex records and star rows
+        return "hbm", esz * S * (8 * n + 4 * m) + esz * (2 * n + m)
     if name == "k_krylov_steps":  # all k steps in one launch, plus the last archive
         step = sum(kernel_model(x, H, K, S, k, esz)[1]
                    for x in ("k_edge_pass", "k_node_pass", "k_update"))

@@ -178,22 +178,23 @@ hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int32_t S,
                             void* stream);
 
 /* Launch form of the Krylov calls made from the calling host thread
- * (a library setting; the paper has no counterpart).  on = 1 (default): a
- * hypergraph small enough that every row of a pass gets a resident thread
- * (2n + m up to about 1e5 rows) runs all k steps as one persistent launch
- * whose CTAs are all resident at once and meet at bounded grid-wide
- * barriers (a barrier that waits too long sets HEF_WAIT_TIMEOUT in the
- * incidence's status word instead of hanging); larger ones, and every call
- * with on = 0, use three launches per step.  Both forms give the same
- * results up to the order of floating-point sums.  The persistent form is a
- * cooperative launch: the runtime starts it only with all of its CTAs
- * resident (work on other streams delays it rather than starving a barrier);
- * if the runtime refuses the grid, the per-step form runs instead.
- * hef_resistance_batched always uses the per-step form.  on = 2 exercises the timeout path: the persistent
- * form (when it applies) is launched with twice the CTAs that can be
- * resident, so its first barrier cannot complete; the launch ends after the
- * wait limit with HEF_WAIT_TIMEOUT set and later calls on that incidence do
- * no work until it is rebuilt. */
+ * (a library setting; the paper has no counterpart).  on = 1 (default): for
+ * hypergraphs with n + m >= 32768 all k steps run as one cooperative launch
+ * of one CTA per SM (smaller ones use the per-step form, which is as fast
+ * there).  Each CTA owns a
+ * balanced range of vertices and hyperedges, keeps their index lists in
+ * shared memory across the steps, and meets the others at bounded grid-wide
+ * barriers that carry the Lanczos reductions (a barrier that waits too long
+ * sets HEF_WAIT_TIMEOUT in the incidence's status word instead of hanging).
+ * The runtime starts a cooperative launch only with all of its CTAs resident
+ * (work on other streams delays it rather than starving a barrier); if it
+ * refuses the grid, or with on = 0, three launches per step run instead.
+ * Both forms give the same results up to the order of floating-point sums.
+ * hef_resistance_batched always uses the per-step form.  on = 2 exercises
+ * the timeout path: the persistent form is launched (plainly) with twice the
+ * CTAs that can be resident, so its first barrier cannot complete; the
+ * launch ends after the wait limit with HEF_WAIT_TIMEOUT set and later calls
+ * on that incidence do no work until it is rebuilt. */
 hef_status hef_set_krylov_persistent(int32_t on);
 /* Krylov basis with a tape for the backward: computes exactly what
  * hef_krylov_basis computes and also stores in `tape` (device, 256-byte
@@ -319,7 +320,8 @@ hef_status hef_edge_resistance_backward(
  * nullable) is the pool stream of item g in [0, nstreams); NULL assigns items
  * longest first to the least loaded stream (hef_batch_schedule).  Results are
  * identical, bit for bit, to one hef_build_incidence / hef_krylov_basis /
- * hef_orthonormalize / hef_edge_resistance sequence per item.
+ * hef_orthonormalize / hef_edge_resistance sequence per item made with the
+ * per-step Krylov form (hef_set_krylov_persistent(0)).
  * The pool and its fork/join events are shared by every batched call on a
  * device: make batched calls from one host thread at a time.
  * hef_batch_autotune waits for `stream`, then for nstreams = 1, 2, 4, 8, 16

@@ -85,11 +85,12 @@ inline cudaError_t launch_dependent_smem(void (*kernel)(KArgs...), unsigned grid
 // resident at once (or refuses a grid that can never be), which is what a
 // kernel with grid-wide barriers needs when other work shares the GPU.
 template <typename... KArgs, typename... Args>
-inline cudaError_t launch_cooperative(void (*kernel)(KArgs...), unsigned grid, unsigned block,
-                                      cudaStream_t st, Args... args) {
+inline cudaError_t launch_cooperative_smem(void (*kernel)(KArgs...), unsigned grid, unsigned block,
+                                           size_t smem, cudaStream_t st, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(block);
+  cfg.dynamicSmemBytes = smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeCooperative;

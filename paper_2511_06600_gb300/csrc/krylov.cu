@@ -17,13 +17,18 @@
 // Krylov spaces of the definition.  Chain vectors are stored unnormalised
 // (u_j) with their inverse D-norms in `inv_nu`; kernels scale on the fly.
 //
-// Layout: a chain block is row-major with the S starts of a row contiguous;
-// one thread owns a whole row (S values, vector loads).  Per step: an edge
-// pass (thread per hyperedge; hyperedges with more than kBig pins are summed
-// by their whole warp), a vertex pass (thread per vertex, same split), which
-// also archives x_{j-1} into V and reduces the Lanczos dots, and an update
-// pass (thread per row) forming x_j and its D-norm.  Every reduction is a
-// per-CTA partial followed by a two-level fixed-order sum (grid_reduce).
+// Layout.  Both expansions' chain values of vertex v form one record
+// [x_c(v) | x_b(v)] of 2S values (S starts each), so one gather per pin in
+// the edge pass fetches the rows of both operators; the star rows of the
+// hyperedges are a separate m x S block.  The edge pass leaves per hyperedge
+// the record [wh_e s_e | z_e x_b(e)] (weighted and scaled), so the vertex pass
+// sums one record per incidence.  Per step: an edge pass (thread per
+// hyperedge; hyperedges with more than kBig pins are summed by their whole
+// warp), a vertex pass (thread per vertex, same split), which also archives
+// x_{j-1} into V (the vertex's record is the contiguous column block of the
+// step) and reduces the Lanczos dots, and an update pass (thread per vertex
+// record or star hyperedge row) forming x_j and its D-norm.  Every reduction
+// is a per-CTA partial followed by a two-level fixed-order sum (grid_reduce).
 #include <algorithm>
 
 #include "internal.h"
@@ -34,16 +39,17 @@ namespace {
 
 constexpr int kMaxS = 16;
 constexpr int kBig = 16;     // segments longer than this are summed by a warp
-// rows per thread in the update pass
+// rows per thread in the update pass (vertex records of 32 bytes or more
+// take two, for registers)
 template <typename T, int S>
 __host__ __device__ constexpr int upd_rows() {
-  return 4;
+  return 2 * S * sizeof(T) >= 32 ? 2 : 4;
 }
-// entries gathered per round by one thread in the segment sums (wider rows
-// keep two, for registers)
-template <typename T, int S>
-__host__ __device__ constexpr int seg_round() {
-  return S * sizeof(T) <= 16 ? 4 : 2;
+// records gathered per round by one thread in the segment sums (wider
+// records keep two, for registers)
+template <typename T, int N>
+__host__ __device__ constexpr int gather_round() {
+  return N * sizeof(T) <= 32 ? 4 : 2;
 }
 
 // Minimum resident CTAs per SM asked of the compiler for the step kernels:
@@ -57,11 +63,11 @@ constexpr int kMinBlocks(int want) {
 template <typename T>
 struct KView {
   int n, m;
-  T* Yc;  // n x S
-  T* Bc[2];
-  T* Yb;  // (n+m) x S
-  T* Bb[2];
-  T* se;  // m x S
+  T* Yv;     // n x 2S: [(M_c x)_v | (M_b x)_v]
+  T* Bv[2];  // n x 2S: [u_c(v) | u_b(v)] of alternate steps
+  T* Ye;     // m x S: (M_b x)_e
+  T* Be[2];  // m x S: u_b(e) of alternate steps
+  T* Er;     // m x 2S: [wh_e s_e | z_e x_b(e)] of the current step (scaled)
   double* inv_nu;  // (k+1) x 2S
   double* coef;    // (k+1) x 2S x 4: [ct, ct2, alpha, beta]
   T* nuT;          // inv_nu in the working type
@@ -72,7 +78,9 @@ struct KView {
   T* tape_c;       // nullable: u_j of the clique chains, (k+1) x n x S
   T* tape_b;       // nullable: u_j of the star chains, (k+1) x (n+m) x S
   double tol;      // breakdown threshold on the D-norm of a new vector
-  unsigned int* gen;  // barrier generation of the persistent launch
+  double* ppart;   // persistent launch: partial sums (2 x grid x 6S; the timeout
+                   // test's grid is 2 num_sms), then the published sums (2 x 6S)
+  unsigned int* pcount;  // persistent launch: barrier arrivals, barriers released
 };
 
 // ---------------------------------------------------------------- row I/O
@@ -84,42 +92,95 @@ __device__ __forceinline__ P pick2(P const (&a)[2], int i) {
   return i ? a[1] : a[0];
 }
 
-template <typename T, int S>
-__device__ __forceinline__ void ldrow(const T* __restrict__ p, T (&v)[S]) {
-  if constexpr (sizeof(T) == 4 && S % 4 == 0) {
+// Load through the read-only path (data written by earlier launches), or,
+// with CG, through L2 only: coherent with writes of other CTAs of the same
+// launch that a grid barrier has ordered before the load.
+template <bool CG, typename V>
+__device__ __forceinline__ V ld1(const V* p) {
+  if constexpr (CG) return __ldcg(p);
+  else return __ldg(p);
+}
+
+// N contiguous values with the widest vector access the row size allows
+// (rows and records start at multiples of their own size).
+template <typename T, int N, bool CG = false>
+__device__ __forceinline__ void ldrow(const T* __restrict__ p, T (&v)[N]) {
+  if constexpr (sizeof(T) == 4 && N % 4 == 0) {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
-    for (int i = 0; i < S / 4; ++i) {
-      const float4 f = __ldg(q + i);
+    for (int i = 0; i < N / 4; ++i) {
+      const float4 f = ld1<CG>(q + i);
       v[4 * i] = f.x, v[4 * i + 1] = f.y, v[4 * i + 2] = f.z, v[4 * i + 3] = f.w;
     }
-  } else if constexpr (sizeof(T) == 8 && S % 2 == 0) {
+  } else if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+    const float2* q = reinterpret_cast<const float2*>(p);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) {
+      const float2 f = ld1<CG>(q + i);
+      v[2 * i] = f.x, v[2 * i + 1] = f.y;
+    }
+  } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
     const double2* q = reinterpret_cast<const double2*>(p);
 #pragma unroll
-    for (int i = 0; i < S / 2; ++i) {
-      const double2 f = __ldg(q + i);
+    for (int i = 0; i < N / 2; ++i) {
+      const double2 f = ld1<CG>(q + i);
       v[2 * i] = f.x, v[2 * i + 1] = f.y;
     }
   } else {
 #pragma unroll
-    for (int s = 0; s < S; ++s) v[s] = __ldg(p + s);
+    for (int s = 0; s < N; ++s) v[s] = ld1<CG>(p + s);
   }
 }
 
-template <typename T, int S>
-__device__ __forceinline__ void strow(T* __restrict__ p, const T (&v)[S]) {
-  if constexpr (sizeof(T) == 4 && S % 4 == 0) {
+template <typename T, int N>
+__device__ __forceinline__ void strow(T* __restrict__ p, const T (&v)[N]) {
+  if constexpr (sizeof(T) == 4 && N % 4 == 0) {
     float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
-    for (int i = 0; i < S / 4; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
-  } else if constexpr (sizeof(T) == 8 && S % 2 == 0) {
+    for (int i = 0; i < N / 4; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
+  } else if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+    float2* q = reinterpret_cast<float2*>(p);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) q[i] = make_float2(v[2 * i], v[2 * i + 1]);
+  } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
     double2* q = reinterpret_cast<double2*>(p);
 #pragma unroll
-    for (int i = 0; i < S / 2; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
+    for (int i = 0; i < N / 2; ++i) q[i] = make_double2(v[2 * i], v[2 * i + 1]);
   } else {
 #pragma unroll
-    for (int s = 0; s < S; ++s) p[s] = v[s];
+    for (int s = 0; s < N; ++s) p[s] = v[s];
   }
+}
+
+// Store with the streaming (evict-first) hint: the basis archive is written
+// once per step and read only by the orthonormalisation, so it should not
+// push the chain blocks out of L2.
+template <typename T, int N>
+__device__ __forceinline__ void strow_cs(T* __restrict__ p, const T (&v)[N]) {
+  if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+    float4* q = reinterpret_cast<float4*>(p);
+#pragma unroll
+    for (int i = 0; i < N / 4; ++i)
+      __stcs(q + i, make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]));
+  } else if constexpr (sizeof(T) == 4 && N % 2 == 0) {
+    float2* q = reinterpret_cast<float2*>(p);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) __stcs(q + i, make_float2(v[2 * i], v[2 * i + 1]));
+  } else if constexpr (sizeof(T) == 8 && N % 2 == 0) {
+    double2* q = reinterpret_cast<double2*>(p);
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i) __stcs(q + i, make_double2(v[2 * i], v[2 * i + 1]));
+  } else {
+#pragma unroll
+    for (int s = 0; s < N; ++s) __stcs(p + s, v[s]);
+  }
+}
+
+// The halves of a record.
+template <typename T, int S>
+__device__ __forceinline__ void split2(const T (&r)[2 * S], T (&lo)[S], T (&hi)[S]) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) lo[s] = r[s], hi[s] = r[S + s];
 }
 
 // Per-CTA partials of NQ*S values (slot q*S + s) written to part[block].
@@ -129,13 +190,15 @@ __device__ __forceinline__ void strow(T* __restrict__ p, const T (&v)[S]) {
 // the warp sum of one slot.  Warps then meet in a fixed order, in the
 // working type; only the CTA's sums are widened to FP64 (conversions and
 // FP64 adds run at 1/64 rate on GB300).
-template <int NQ, int S, typename A>
+// PMAX caps the butterfly width (values held at once) for register-tight callers.
+template <int NQ, int S, typename A, int NT = kThreads, int PMAX = 32>
 __device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* part) {
   constexpr int N = NQ * S;
-  constexpr int P = N > 16 ? 32 : (N > 8 ? 16 : (N > 4 ? 8 : (N > 2 ? 4 : (N > 1 ? 2 : 1))));
+  constexpr int P0 = N > 16 ? 32 : (N > 8 ? 16 : (N > 4 ? 8 : (N > 2 ? 4 : (N > 1 ? 2 : 1))));
+  constexpr int P = P0 < PMAX ? P0 : PMAX;
   constexpr int R = 32 / P;  // lanes that end up holding the same slot
   constexpr int NCH = (N + P - 1) / P;
-  __shared__ A red[kThreads / 32][NCH * P];
+  __shared__ A red[NT / 32][NCH * P];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int ch = 0; ch < NCH; ++ch) {
@@ -167,93 +230,35 @@ __device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* p
   }
 }
 
-// Sum of the S-rows of `X` over the entries [a, b) of an index list `idx`
-// (X row = base + idx[t] * S) with weights, split between one thread (short
-// lists) and its whole warp (lists longer than kBig, handled one at a time).
-// W(t) gives the weight of entry t.  Result in acc (the owner thread).
-template <typename T, int S, typename RowOf, typename WeightOf>
-__device__ __forceinline__ void seg_sum(bool valid, int a, int b, RowOf row_of, WeightOf w_of,
-                                        T (&acc)[S]) {
-  const int lane = threadIdx.x & 31;
-#pragma unroll
-  for (int s = 0; s < S; ++s) acc[s] = 0;
-  const bool big = valid && (b - a) > kBig;
-  if (valid && !big) {
-    int t = a;
-    for (; t + 2 <= b; t += 2) {
-      T v0[S], v1[S];
-      ldrow<T, S>(row_of(t), v0);
-      ldrow<T, S>(row_of(t + 1), v1);
-      const T w0 = w_of(t), w1 = w_of(t + 1);
-#pragma unroll
-      for (int s = 0; s < S; ++s) acc[s] += w0 * v0[s] + w1 * v1[s];
-    }
-    if (t < b) {
-      T v0[S];
-      ldrow<T, S>(row_of(t), v0);
-      const T w0 = w_of(t);
-#pragma unroll
-      for (int s = 0; s < S; ++s) acc[s] += w0 * v0[s];
-    }
-  }
-  unsigned bigmask = __ballot_sync(0xffffffffu, big);
-  while (bigmask) {
-    const int src = __ffs(bigmask) - 1;
-    bigmask &= bigmask - 1;
-    const int ba = __shfl_sync(0xffffffffu, a, src), bb = __shfl_sync(0xffffffffu, b, src);
-    T part[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) part[s] = 0;
-    for (int t = ba + lane; t < bb; t += 32) {
-      T v0[S];
-      ldrow<T, S>(row_of(t), v0);
-      const T w0 = w_of(t);
-#pragma unroll
-      for (int s = 0; s < S; ++s) part[s] += w0 * v0[s];
-    }
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) part[s] += __shfl_xor_sync(0xffffffffu, part[s], o);
-    }
-    if (lane == src) {
-#pragma unroll
-      for (int s = 0; s < S; ++s) acc[s] = part[s];
-    }
-  }
-}
 
-// Two weighted row sums over one index list at once (the index is loaded
-// once and both rows are in flight together): accA = sum_t wA(i) rowA(i),
-// accB = sum_t wB(i) rowB(i) with i = idx(t), t in [a, b).  Lists longer than
-// kBig are summed by the whole warp.
-template <typename T, int S, typename Idx, typename RowA, typename RowB, typename WA, typename WB>
-__device__ __forceinline__ void seg_sum2(bool valid, int a, int b, Idx idx, RowA rowA, RowB rowB,
-                                         WA wA, WB wB, T (&accA)[S], T (&accB)[S]) {
+// Sum of the N-value records row(idx(t)) over the entries t in [a, b) of an
+// index list, split between one thread (short lists) and its whole warp
+// (lists longer than kBig, handled one at a time).  A short list is gathered
+// gather_round records per round, all index loads and then all record loads
+// in flight (entries past the end repeat the last one and are not added).
+// Each thread adds in entry order, so the sum does not depend on scheduling.
+// Result in acc (the owner thread).
+template <typename T, int N, bool CG, typename Idx, typename Row>
+__device__ __forceinline__ void seg_gather(bool valid, int a, int b, Idx idx, Row row,
+                                           T (&acc)[N]) {
   const int lane = threadIdx.x & 31;
-  constexpr int kSeg = seg_round<T, S>();
+  constexpr int kSeg = gather_round<T, N>();
 #pragma unroll
-  for (int s = 0; s < S; ++s) accA[s] = 0, accB[s] = 0;
+  for (int i = 0; i < N; ++i) acc[i] = 0;
   const bool big = valid && (b - a) > kBig;
   if (valid && !big) {
-    // kSeg entries per round, all index loads then all row loads in flight
-    // (indices past the end repeat the last entry and are weighted out)
     for (int t = a; t < b; t += kSeg) {
       int ii[kSeg];
 #pragma unroll
       for (int q = 0; q < kSeg; ++q) ii[q] = idx(min(t + q, b - 1));
-      T ra[kSeg][S], rb[kSeg][S];
+      T r[kSeg][N];
 #pragma unroll
-      for (int q = 0; q < kSeg; ++q) {
-        ldrow<T, S>(rowA(ii[q]), ra[q]);
-        ldrow<T, S>(rowB(ii[q]), rb[q]);
-      }
+      for (int q = 0; q < kSeg; ++q) ldrow<T, N, CG>(row(ii[q]), r[q]);
 #pragma unroll
       for (int q = 0; q < kSeg; ++q) {
         const bool in = t + q < b;
-        const T wa = in ? wA(ii[q]) : (T)0, wb = in ? wB(ii[q]) : (T)0;
 #pragma unroll
-        for (int s = 0; s < S; ++s) accA[s] += wa * ra[q][s], accB[s] += wb * rb[q][s];
+        for (int i = 0; i < N; ++i) acc[i] += in ? r[q][i] : (T)0;
       }
     }
   }
@@ -262,29 +267,23 @@ __device__ __forceinline__ void seg_sum2(bool valid, int a, int b, Idx idx, RowA
     const int src = __ffs(bigmask) - 1;
     bigmask &= bigmask - 1;
     const int ba = __shfl_sync(0xffffffffu, a, src), bb = __shfl_sync(0xffffffffu, b, src);
-    T pa[S], pb[S];
+    T part[N];
 #pragma unroll
-    for (int s = 0; s < S; ++s) pa[s] = 0, pb[s] = 0;
+    for (int i = 0; i < N; ++i) part[i] = 0;
     for (int t = ba + lane; t < bb; t += 32) {
-      const int i0 = idx(t);
-      T a0[S], b0[S];
-      ldrow<T, S>(rowA(i0), a0);
-      ldrow<T, S>(rowB(i0), b0);
-      const T wa0 = wA(i0), wb0 = wB(i0);
+      T r0[N];
+      ldrow<T, N, CG>(row(idx(t)), r0);
 #pragma unroll
-      for (int s = 0; s < S; ++s) pa[s] += wa0 * a0[s], pb[s] += wb0 * b0[s];
+      for (int i = 0; i < N; ++i) part[i] += r0[i];
     }
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
+    for (int i = 0; i < N; ++i) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        pa[s] += __shfl_xor_sync(0xffffffffu, pa[s], o);
-        pb[s] += __shfl_xor_sync(0xffffffffu, pb[s], o);
-      }
+      for (int o = 16; o > 0; o >>= 1) part[i] += __shfl_xor_sync(0xffffffffu, part[i], o);
     }
     if (lane == src) {
 #pragma unroll
-      for (int s = 0; s < S; ++s) accA[s] = pa[s], accB[s] = pb[s];
+      for (int i = 0; i < N; ++i) acc[i] = part[i];
     }
   }
 }
@@ -294,7 +293,7 @@ __device__ __forceinline__ void seg_sum2(bool valid, int a, int b, Idx idx, RowA
 // D-weighted dots of the raw starts with the trivial vectors -> coef[0]; the
 // starts, in the working type (and the internal hyperedge order), go to the
 // first chain buffers for k_start_write (one FP64 -> working-type conversion).
-// Rows: [0, n) clique, [n, 2n) star vertices, [2n, 2n+m) star hyperedges.
+// Rows: [0, n) vertex records (clique and star), [n, n+m) star hyperedges.
 template <typename T, int S>
 __global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, ScalView<T> sv, KView<T> kv,
                                                          const double* __restrict__ x0c,
@@ -306,25 +305,23 @@ __global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, ScalView<T> 
   for (int q = 0; q < 3; ++q)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
-  T u[S];
   if (r < g.n) {
-    const T d = sv.dc[r];
+    const T dc = sv.dc[r], db = sv.db[r];
+    T u[2 * S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) u[s] = (T)x0c[r * S + s], acc[0][s] = d * u[s];
-    strow<T, S>(kv.Bc[0] + r * S, u);
-  } else if (r < 2ll * g.n) {
-    const long long v = r - g.n;
-    const T d = sv.db[v];
-#pragma unroll
-    for (int s = 0; s < S; ++s) u[s] = (T)x0b[v * S + s], acc[1][s] = d * u[s];
-    strow<T, S>(kv.Bb[0] + v * S, u);
-  } else if (r < 2ll * g.n + g.m) {
-    const int i = (int)(r - 2ll * g.n);
+    for (int s = 0; s < S; ++s) {
+      u[s] = (T)x0c[r * S + s], acc[0][s] = dc * u[s];
+      u[S + s] = (T)x0b[r * S + s], acc[1][s] = db * u[S + s];
+    }
+    strow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
+  } else if (r < (long long)g.n + g.m) {
+    const int i = (int)(r - g.n);
     const T d = sv.ew[i];
     const long long src = (long long)(g.n + g.perm[i]) * S;
+    T u[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) u[s] = (T)x0b[src + s], acc[2][s] = d * u[s];
-    strow<T, S>(kv.Bb[0] + (long long)(g.n + i) * S, u);
+    strow<T, S>(kv.Be[0] + (long long)i * S, u);
   }
   block_partials_qs<3, S, T>(acc, kv.red.part);
   __shared__ double tot[3 * kMaxS];
@@ -359,35 +356,35 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T>
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
   if (r < g.n) {
-    const T d = sv.dc[r];
-    T u[S];
-    ldrow<T, S>(kv.Bc[0] + r * S, u);
+    const T dc = sv.dc[r], db = sv.db[r];
+    T u[2 * S];
+    ldrow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      u[s] -= (d > 0 ? kv.cfT[(size_t)s * 4] : (T)0);
-      acc[0][s] = d * u[s] * u[s];
+      u[s] -= (dc > 0 ? kv.cfT[(size_t)s * 4] : (T)0);
+      acc[0][s] = dc * u[s] * u[s];
+      u[S + s] -= (db > 0 ? kv.cfT[(size_t)(S + s) * 4] : (T)0);
+      acc[1][s] = db * u[S + s] * u[S + s];
     }
-    strow<T, S>(kv.Bc[0] + r * S, u);
-    if (kv.tape_c) strow<T, S>(kv.tape_c + r * S, u);
-  } else if (r < 2ll * g.n + g.m) {
-    const long long rb = r - g.n;  // star row
-    T d;
-    int t;
-    if (rb < g.n) {
-      d = sv.db[rb], t = 0;
-    } else {
-      d = sv.ew[rb - g.n], t = 1;
+    strow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
+    if (kv.tape_c) {
+      T uc[S], ub[S];
+      split2<T, S>(u, uc, ub);
+      strow<T, S>(kv.tape_c + r * S, uc);
+      strow<T, S>(kv.tape_b + r * S, ub);
     }
+  } else if (r < (long long)g.n + g.m) {
+    const long long i = r - g.n;  // star hyperedge row
+    const T d = sv.ew[i];
     T u[S];
-    ldrow<T, S>(kv.Bb[0] + rb * S, u);
+    ldrow<T, S>(kv.Be[0] + i * S, u);
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      const T c = kv.cfT[(size_t)(S + s) * 4 + t];
-      u[s] -= (d > 0 ? c : (T)0);
+      u[s] -= (d > 0 ? kv.cfT[(size_t)(S + s) * 4 + 1] : (T)0);
       acc[1][s] = d * u[s] * u[s];
     }
-    strow<T, S>(kv.Bb[0] + rb * S, u);
-    if (kv.tape_b) strow<T, S>(kv.tape_b + rb * S, u);
+    strow<T, S>(kv.Be[0] + i * S, u);
+    if (kv.tape_b) strow<T, S>(kv.tape_b + (g.n + i) * S, u);
   }
   block_partials_qs<2, S, T>(acc, kv.red.part);
   __shared__ double tot[2 * kMaxS];
@@ -410,55 +407,55 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T>
 // functions (grid-stride loops, bounded grid barriers).
 
 // Edge pass item (hyperedge e; past the end it still takes part in its
-// warp's collective sums): clique pin sums s_e, star rows (M_b x)_e, and the
-// D-weighted dots of the star hyperedge rows, added to acc.
-template <typename T, int S>
+// warp's collective sums): the clique pin sum s_e and star pin sum from one
+// record gather per pin, the star row (M_b x)_e, the record
+// [wh_e s_e | z_e x_b(e)] for the vertex pass, and the D-weighted dots of the
+// star hyperedge rows, added to acc.
+// ofs(e) gives the CSC offset of hyperedge e and pin(t) the vertex of CSC
+// slot t; CG selects coherent loads of the chain data (see ldrow).
+template <typename T, int S, bool CG, typename Ofs, typename Pin>
 __device__ __forceinline__ void edge_item(const IncView& g, const ScalView<T>& sv,
-                                          const KView<T>& kv, int j, int e, T (&acc)[3][S]) {
-  const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
-  const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
-  const T* __restrict__ prvb = j >= 3 ? pick2(kv.Bb, j & 1) : nullptr;
-  T ncc[S], ncb[S], npb[S];  // inverse norms of x_{j-1} (clique, star) and x_{j-2} (star)
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    ncc[s] = kv.nuT[(size_t)(j - 1) * 2 * S + s];
-    ncb[s] = kv.nuT[(size_t)(j - 1) * 2 * S + S + s];
-    npb[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + S + s] : (T)0;
-  }
+                                          const KView<T>& kv, const T* nuT, int j, int e,
+                                          T (&acc)[3][S], Ofs ofs, Pin pin) {
+  const T* __restrict__ curv = pick2(kv.Bv, (j - 1) & 1);
+  const T* __restrict__ cure = pick2(kv.Be, (j - 1) & 1);
+  const T* __restrict__ prve = j >= 3 ? pick2(kv.Be, j & 1) : nullptr;
   const bool valid = e < g.m;
   int a = 0, b = 0;
-  if (valid) a = g.ceptr[e], b = g.ceptr[e + 1];
-  const int32_t* __restrict__ pins = g.cpins;
-  T sc[S], sb[S];
-  seg_sum2<T, S>(valid, a, b, [&](int t) { return __ldg(pins + t); },
-                 [&](int p) { return curc + (long long)p * S; },
-                 [&](int p) { return curb + (long long)p * S; }, [&](int) { return (T)1; },
-                 [&](int) { return (T)1; }, sc, sb);
+  // the hyperedge's own rows and scalars first: their loads overlap the gathers
+  T xc[S], xp[S];
+  T we = 0, wh = 0, z = 0;
+  if (valid) {
+    a = ofs(e), b = ofs(e + 1);
+    ldrow<T, S, CG>(cure + (long long)e * S, xc);
+    if (prve) ldrow<T, S, CG>(prve + (long long)e * S, xp);
+    we = sv.ew[e], wh = sv.ewh[e], z = sv.ez[e];
+  }
+  T sum[2 * S];
+  seg_gather<T, 2 * S, CG>(valid, a, b, pin,
+                           [&](int p) { return curv + (long long)p * 2 * S; }, sum);
   if (valid) {
     const int k = b - a;
     const T invk = k >= 2 ? (T)1 / (T)k : (T)0;
-    T ye[S], sev[S];
+    // inverse norms of x_{j-1} (clique, star) and x_{j-2} (star)
+    const T* __restrict__ n1 = nuT + (size_t)(j - 1) * 2 * S;
+    const T* __restrict__ n2 = nuT + (size_t)(j >= 2 ? j - 2 : 0) * 2 * S;
+    T ye[S], er[2 * S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      sev[s] = sc[s] * ncc[s];
-      ye[s] = sb[s] * ncb[s] * invk;
-    }
-    strow<T, S>(kv.se + (long long)e * S, sev);
-    const long long row = (long long)(g.n + e) * S;
-    strow<T, S>(kv.Yb + row, ye);
-    if (k >= 2) {
-      const T we = sv.ew[e];
-      T xc[S], xp[S];
-      ldrow<T, S>(curb + row, xc);
-      if (prvb) ldrow<T, S>(prvb + row, xp);
-#pragma unroll
-      for (int s = 0; s < S; ++s) {
+      const T ncc = n1[s], ncb = n1[S + s];
+      ye[s] = sum[S + s] * ncb * invk;
+      er[s] = wh * (sum[s] * ncc);
+      er[S + s] = z * (xc[s] * ncb);
+      if (k >= 2) {
         const T wy = we * ye[s];
         acc[0][s] += wy;
-        acc[1][s] += wy * xc[s] * ncb[s];
-        acc[2][s] += prvb ? wy * xp[s] * npb[s] : (T)0;
+        acc[1][s] += wy * xc[s] * ncb;
+        acc[2][s] += prve ? wy * xp[s] * n2[S + s] : (T)0;
       }
     }
+    strow<T, S>(kv.Ye + (long long)e * S, ye);
+    strow<T, 2 * S>(kv.Er + (long long)e * 2 * S, er);
   }
 }
 
@@ -467,73 +464,58 @@ __device__ __forceinline__ void edge_final(const KView<T>& kv, int S, const doub
   for (int t = threadIdx.x; t < 3 * S; t += blockDim.x) kv.te[t] = tot[t];
 }
 
-// Vertex pass item (vertex v): (M_c x)_v and (M_b x)_v, archive of x_{j-1}
-// into V, and the dots of the Lanczos coefficients, added to acc.
-template <typename T, int S>
+// Vertex pass item (vertex v): (M_c x)_v and (M_b x)_v from one record per
+// incidence, archive of x_{j-1} into V (one contiguous record), and the dots
+// of the Lanczos coefficients, added to acc.
+// ofs(v) gives the offset of vertex v's incidences and edge(t) the hyperedge
+// of incidence t; CG as in edge_item.
+template <typename T, int S, bool CG, typename Ofs, typename Edge>
 __device__ __forceinline__ void node_item(const IncView& g, const ScalView<T>& sv,
-                                          const KView<T>& kv, int j, int v, T (&acc)[6][S],
-                                          T* __restrict__ V, long long ldv) {
-  const T* __restrict__ curc = pick2(kv.Bc, (j - 1) & 1);
-  const T* __restrict__ curb = pick2(kv.Bb, (j - 1) & 1);
-  const T* __restrict__ prvc = j >= 3 ? pick2(kv.Bc, j & 1) : nullptr;
-  const T* __restrict__ prvb = j >= 3 ? pick2(kv.Bb, j & 1) : nullptr;
-  T ncc[S], ncb[S], npc[S], npb[S];
-#pragma unroll
-  for (int s = 0; s < S; ++s) {
-    ncc[s] = kv.nuT[(size_t)(j - 1) * 2 * S + s];
-    ncb[s] = kv.nuT[(size_t)(j - 1) * 2 * S + S + s];
-    npc[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + s] : (T)0;
-    npb[s] = j >= 2 ? kv.nuT[(size_t)(j - 2) * 2 * S + S + s] : (T)0;
-  }
+                                          const KView<T>& kv, const T* nuT, int j, int v,
+                                          T (&acc)[6][S], T* __restrict__ V, long long ldv,
+                                          Ofs ofs, Edge edge) {
+  const T* __restrict__ curv = pick2(kv.Bv, (j - 1) & 1);
+  const T* __restrict__ prvv = j >= 3 ? pick2(kv.Bv, j & 1) : nullptr;
   const bool valid = v < g.n;
   int a = 0, b = 0;
-  if (valid) a = g.vptr[v], b = g.vptr[v + 1];
-  const int32_t* __restrict__ ve = g.vedge;
-  const T* __restrict__ se = kv.se;
-  const T* __restrict__ ewh = sv.ewh;
-  const T* __restrict__ ez = sv.ez;
-  // the vertex's own rows and scalars first: their loads overlap the gathers
-  T xv[S], xb[S], xpc[S], xpb[S];
+  if (valid) a = ofs(v), b = ofs(v + 1);
+  const T* __restrict__ er = kv.Er;
+  // the vertex's own records and scalars first: their loads overlap the gathers
+  T xr[2 * S], pr[2 * S];
   T wsum = 0, idc = 0, idb = 0, dcv = 0, dbv = 0;
   if (valid) {
-    ldrow<T, S>(curc + (long long)v * S, xv);
-    ldrow<T, S>(curb + (long long)v * S, xb);
-    if (prvc) {
-      ldrow<T, S>(prvc + (long long)v * S, xpc);
-      ldrow<T, S>(prvb + (long long)v * S, xpb);
-    }
+    ldrow<T, 2 * S, CG>(curv + (long long)v * 2 * S, xr);
+    if (prvv) ldrow<T, 2 * S, CG>(prvv + (long long)v * 2 * S, pr);
     wsum = sv.wsc[v], idc = sv.inv_dc[v], idb = sv.inv_db[v], dcv = sv.dc[v], dbv = sv.db[v];
   }
-  T accc[S], accb[S];
-  seg_sum2<T, S>(valid, a, b, [&](int t) { return __ldg(ve + t); },
-                 [&](int e) { return se + (long long)e * S; },
-                 [&](int e) { return curb + (long long)(g.n + e) * S; },
-                 [&](int e) { return __ldg(ewh + e); }, [&](int e) { return __ldg(ez + e); }, accc,
-                 accb);
+  T sum[2 * S];
+  seg_gather<T, 2 * S, CG>(valid, a, b, edge,
+                           [&](int e) { return er + (long long)e * 2 * S; }, sum);
   if (valid) {
-    T yc[S], yb[S];
+    // inverse norms of x_{j-1} and x_{j-2} (both expansions)
+    const T* __restrict__ n1 = nuT + (size_t)(j - 1) * 2 * S;
+    const T* __restrict__ n2 = nuT + (size_t)(j >= 2 ? j - 2 : 0) * 2 * S;
+    T y[2 * S], xo[2 * S];
 #pragma unroll
     for (int s = 0; s < S; ++s) {
-      xv[s] *= ncc[s];
-      xb[s] *= ncb[s];
-      yc[s] = idc * (accc[s] - wsum * xv[s]);
-      yb[s] = idb * accb[s] * ncb[s];
-      const T pc = prvc ? xpc[s] * npc[s] : (T)0;
-      const T pb = prvb ? xpb[s] * npb[s] : (T)0;
-      acc[0][s] += dcv * yc[s];
-      acc[1][s] += dcv * yc[s] * xv[s];
-      acc[2][s] += dcv * yc[s] * pc;
-      acc[3][s] += dbv * yb[s];
-      acc[4][s] += dbv * yb[s] * xb[s];
-      acc[5][s] += dbv * yb[s] * pb;
+      const T xv = xr[s] * n1[s];
+      const T xb = xr[S + s] * n1[S + s];
+      const T yc = idc * (sum[s] - wsum * xv);
+      const T yb = idb * sum[S + s];
+      const T pc = prvv ? pr[s] * n2[s] : (T)0;
+      const T pb = prvv ? pr[S + s] * n2[S + s] : (T)0;
+      acc[0][s] += dcv * yc;
+      acc[1][s] += dcv * yc * xv;
+      acc[2][s] += dcv * yc * pc;
+      acc[3][s] += dbv * yb;
+      acc[4][s] += dbv * yb * xb;
+      acc[5][s] += dbv * yb * pb;
+      y[s] = yc, y[S + s] = yb;
+      xo[s] = xv, xo[S + s] = xb;
     }
-    strow<T, S>(kv.Yc + (long long)v * S, yc);
-    strow<T, S>(kv.Yb + (long long)v * S, yb);
-    if (j >= 2) {  // x_{j-1} is basis vector j-1 -> column block j-2
-      T* row = V + (long long)v * ldv + (long long)(j - 2) * 2 * S;
-      strow<T, S>(row, xv);
-      strow<T, S>(row + S, xb);
-    }
+    strow<T, 2 * S>(kv.Yv + (long long)v * 2 * S, y);
+    if (j >= 2)  // x_{j-1} is basis vector j-1 -> column block j-2
+      strow_cs<T, 2 * S>(V + (long long)v * ldv + (long long)(j - 2) * 2 * S, xo);
   }
 }
 
@@ -565,59 +547,106 @@ __device__ __forceinline__ void node_final(const IncView& g, const KView<T>& kv,
   }
 }
 
-// Update pass item (rows r0 + it * blockDim.x, it < upd_rows): u_j = y -
-// trivial part - alpha x_{j-1} - beta x_{j-2} (written over x_{j-2}'s
-// buffer) and its D-norm, added to acc.  Rows: [0, n) clique, [n, 2n + m) star.
-template <typename T, int S>
-__device__ __forceinline__ void update_item(const IncView& g, const ScalView<T>& sv,
-                                            const KView<T>& kv, int j, long long r0,
-                                            T (&acc)[2][S]) {
+// Update of one vertex record (both expansions) and of one star hyperedge
+// row: u_j = y - trivial part - alpha x_{j-1} - beta x_{j-2} (written over
+// x_{j-2}'s buffer) and its D-norm, added to acc.  cf[op][s][q] = [ct, ct2,
+// alpha nu_{j-1}, beta nu_{j-2}] of step j (a register array, or a view of
+// shared memory).
+template <typename T, int S, bool CG, typename CF>
+__device__ __forceinline__ void update_vertex(const IncView& g, const ScalView<T>& sv,
+                                              const KView<T>& kv, int j, long long r,
+                                              const CF& cf, T (&acc)[2][S]) {
   const bool has_prv = j >= 3;
-  // coefficients of both expansions in registers: [op][s][ct, ct2, a, b]
-  T cf[2][S][4];
+  const T* cur = pick2(kv.Bv, (j - 1) & 1) + r * 2 * S;
+  T* nw = pick2(kv.Bv, j & 1) + r * 2 * S;
+  const T dc = sv.dc[r], db = sv.db[r];
+  T y[2 * S], xc[2 * S], xp[2 * S], u[2 * S];
+  ldrow<T, 2 * S, CG>(kv.Yv + r * 2 * S, y);
+  ldrow<T, 2 * S, CG>(cur, xc);
+  if (has_prv) ldrow<T, 2 * S, CG>(nw, xp);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const T tc = dc > 0 ? cf[0][s][0] : (T)0;
+    u[s] = y[s] - tc - cf[0][s][2] * xc[s] - (has_prv ? cf[0][s][3] * xp[s] : (T)0);
+    acc[0][s] += dc * u[s] * u[s];
+    const T tb = db > 0 ? cf[1][s][0] : (T)0;
+    u[S + s] = y[S + s] - tb - cf[1][s][2] * xc[S + s] -
+               (has_prv ? cf[1][s][3] * xp[S + s] : (T)0);
+    acc[1][s] += db * u[S + s] * u[S + s];
+  }
+  strow<T, 2 * S>(nw, u);
+  if (kv.tape_c) {
+    T uc[S], ub[S];
+    split2<T, S>(u, uc, ub);
+    strow<T, S>(kv.tape_c + ((long long)j * g.n + r) * S, uc);
+    strow<T, S>(kv.tape_b + ((long long)j * (g.n + g.m) + r) * S, ub);
+  }
+}
+
+template <typename T, int S, bool CG, typename CF>
+__device__ __forceinline__ void update_edge(const IncView& g, const ScalView<T>& sv,
+                                            const KView<T>& kv, int j, long long i,
+                                            const CF& cf, T (&acc)[2][S]) {
+  const bool has_prv = j >= 3;
+  const T* cur = pick2(kv.Be, (j - 1) & 1) + i * S;
+  T* nw = pick2(kv.Be, j & 1) + i * S;
+  const T d = sv.ew[i];
+  T y[S], xc[S], xp[S], u[S];
+  ldrow<T, S, CG>(kv.Ye + i * S, y);
+  ldrow<T, S, CG>(cur, xc);
+  if (has_prv) ldrow<T, S, CG>(nw, xp);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    const T t = d > 0 ? cf[1][s][1] : (T)0;
+    u[s] = y[s] - t - cf[1][s][2] * xc[s] - (has_prv ? cf[1][s][3] * xp[s] : (T)0);
+    acc[1][s] += d * u[s] * u[s];
+  }
+  strow<T, S>(nw, u);
+  if (kv.tape_b) strow<T, S>(kv.tape_b + ((long long)j * (g.n + g.m) + g.n + i) * S, u);
+}
+
+// cf[op][s][q] read from coefficients in (shared) memory, the same indexing
+// as a register array T[2][S][4].
+template <typename T, int S>
+struct CoefView {
+  const T* p;  // cfT + j * 2S * 4
+  struct Row {
+    const T* p;
+    __device__ T operator[](int q) const { return p[q]; }
+  };
+  struct Op {
+    const T* p;
+    __device__ Row operator[](int s) const { return Row{p + s * 4}; }
+  };
+  __device__ Op operator[](int op) const { return Op{p + op * S * 4}; }
+};
+
+template <typename T, int S>
+__device__ __forceinline__ void load_coefs(const T* cfT, int j, T (&cf)[2][S][4]) {
 #pragma unroll
   for (int op = 0; op < 2; ++op)
 #pragma unroll
     for (int s = 0; s < S; ++s)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) cf[op][s][q] = kv.cfT[((size_t)j * 2 * S + op * S + s) * 4 + q];
-  const long long nrows = 2ll * g.n + g.m;
+      for (int q = 0; q < 4; ++q) cf[op][s][q] = cfT[((size_t)j * 2 * S + op * S + s) * 4 + q];
+}
+
+// Update pass item (rows r0 + it * blockDim.x, it < upd_rows).  Rows: [0, n)
+// vertex records, [n, n + m) star hyperedge rows.
+template <typename T, int S>
+__device__ __forceinline__ void update_item(const IncView& g, const ScalView<T>& sv,
+                                            const KView<T>& kv, int j, long long r0,
+                                            T (&acc)[2][S]) {
+  T cf[2][S][4];
+  load_coefs<T, S>(kv.cfT, j, cf);
+  const long long nrows = (long long)g.n + g.m;
   constexpr int kUpdRows = upd_rows<T, S>();
 #pragma unroll
   for (int it = 0; it < kUpdRows; ++it) {
     const long long r = r0 + (long long)it * blockDim.x;
     if (r >= nrows) break;
-    const bool clique = r < g.n;
-    const long long rr = clique ? r : r - g.n;
-    const T* cur = clique ? pick2(kv.Bc, (j - 1) & 1) : pick2(kv.Bb, (j - 1) & 1);
-    T* nw = clique ? pick2(kv.Bc, j & 1) : pick2(kv.Bb, j & 1);
-    const T* Y = clique ? kv.Yc : kv.Yb;
-    T d;
-    int tsel;
-    if (clique) d = sv.dc[rr], tsel = 0;
-    else if (rr < g.n) d = sv.db[rr], tsel = 0;
-    else d = sv.ew[rr - g.n], tsel = 1;
-    T y[S], xc[S], xp[S], u[S], dsq[S];
-    ldrow<T, S>(Y + rr * S, y);
-    ldrow<T, S>(cur + rr * S, xc);
-    if (has_prv) ldrow<T, S>(nw + rr * S, xp);
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const T c0 = clique ? cf[0][s][0] : (tsel ? cf[1][s][1] : cf[1][s][0]);
-      const T ca = clique ? cf[0][s][2] : cf[1][s][2];
-      const T cb = clique ? cf[0][s][3] : cf[1][s][3];
-      const T t = d > 0 ? c0 : (T)0;
-      u[s] = y[s] - t - ca * xc[s] - (has_prv ? cb * xp[s] : (T)0);
-      dsq[s] = d * u[s] * u[s];
-    }
-    strow<T, S>(nw + rr * S, u);
-    if (clique && kv.tape_c) strow<T, S>(kv.tape_c + ((long long)j * g.n + rr) * S, u);
-    if (!clique && kv.tape_b) strow<T, S>(kv.tape_b + ((long long)j * (g.n + g.m) + rr) * S, u);
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      if (clique) acc[0][s] += dsq[s];
-      else acc[1][s] += dsq[s];
-    }
+    if (r < g.n) update_vertex<T, S, false>(g, sv, kv, j, r, cf, acc);
+    else update_edge<T, S, false>(g, sv, kv, j, r - g.n, cf, acc);
   }
 }
 
@@ -634,21 +663,18 @@ __device__ __forceinline__ void update_final(const KView<T>& kv, int S, int j, c
 }
 
 // Archive of the last chain vector x_k of vertex v into V.
-template <typename T, int S>
-__device__ __forceinline__ void archive_item(const IncView& g, const KView<T>& kv, int k, int v,
-                                             T* __restrict__ V, long long ldv) {
+template <typename T, int S, bool CG = false>
+__device__ __forceinline__ void archive_item(const IncView& g, const KView<T>& kv, const T* nuT,
+                                             int k, int v, T* __restrict__ V, long long ldv) {
   if (v >= g.n) return;
-  T xc[S], xb[S];
-  ldrow<T, S>(pick2(kv.Bc, k & 1) + (long long)v * S, xc);
-  ldrow<T, S>(pick2(kv.Bb, k & 1) + (long long)v * S, xb);
+  T x[2 * S];
+  ldrow<T, 2 * S, CG>(pick2(kv.Bv, k & 1) + (long long)v * 2 * S, x);
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    xc[s] *= kv.nuT[(size_t)k * 2 * S + s];
-    xb[s] *= kv.nuT[(size_t)k * 2 * S + S + s];
+    x[s] *= nuT[(size_t)k * 2 * S + s];
+    x[S + s] *= nuT[(size_t)k * 2 * S + S + s];
   }
-  T* row = V + (long long)v * ldv + (long long)(k - 1) * 2 * S;
-  strow<T, S>(row, xc);
-  strow<T, S>(row + S, xb);
+  strow_cs<T, 2 * S>(V + (long long)v * ldv + (long long)(k - 1) * 2 * S, x);
 }
 
 template <int NQ, int S, typename T>
@@ -668,7 +694,9 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(6))
   if (g.status[0]) return;
   T acc[3][S];
   zero_acc(acc);
-  edge_item<T, S>(g, sv, kv, j, blockIdx.x * blockDim.x + threadIdx.x, acc);
+  edge_item<T, S, false>(g, sv, kv, kv.nuT, j, blockIdx.x * blockDim.x + threadIdx.x, acc,
+                         [&](int e) { return g.ceptr[e]; },
+                         [&](int t) { return __ldg(g.cpins + t); });
   block_partials_qs<3, S, T>(acc, kv.red.part);
   __shared__ double tot[3 * kMaxS];
   if (grid_reduce(kv.red, 3 * S, tot)) edge_final(kv, S, tot);
@@ -684,7 +712,10 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
   if (g.status[0]) return;
   T acc[6][S];
   zero_acc(acc);
-  node_item<T, S>(g, sv, kv, j, blockIdx.x * blockDim.x + threadIdx.x, acc, V, ldv);
+  node_item<T, S, false>(g, sv, kv, kv.nuT, j, blockIdx.x * blockDim.x + threadIdx.x, acc, V,
+                         ldv,
+                         [&](int v) { return g.vptr[v]; },
+                         [&](int t) { return __ldg(g.vedge + t); });
   block_partials_qs<6, S, T>(acc, kv.red.part);
   __shared__ double tn[6 * kMaxS];
   if (grid_reduce(kv.red, 6 * S, tn)) node_final(g, kv, S, j, tn);
@@ -713,91 +744,294 @@ __global__ void __launch_bounds__(kThreads) k_archive_last(IncView g, KView<T> k
                                                            T* __restrict__ V, long long ldv) {
   pdl_wait();
   if (g.status[0]) return;
-  archive_item<T, S>(g, kv, k, blockIdx.x * blockDim.x + threadIdx.x, V, ldv);
+  archive_item<T, S>(g, kv, kv.nuT, k, blockIdx.x * blockDim.x + threadIdx.x, V, ldv);
 }
 
 // ---------------------------------------------------------------- persistent form
+//
+// All k steps in one cooperative launch of one CTA per SM.  CTA b owns a
+// contiguous range of vertices and one of hyperedges (internal order),
+// balanced on incidences plus items, and keeps their offsets and index lists
+// in shared memory for all k steps (entries past the capacity are read from
+// global memory): after the first step a gather costs one dependent load
+// instead of three.  The three phases of a step (edge, vertex, update) meet
+// at grid barriers, each carrying its phase's reduction: every CTA writes its
+// partial sums, and after the barrier every CTA sums all partials in the
+// same fixed order (reduce_slots), so every CTA holds the same coefficients
+// and no CTA runs a serial final step.  Chain data written during the launch
+// is read through L2 only (ldrow with CG), which the barriers order.
 
-constexpr unsigned int kBarIters = 1u << 20;  // bounded barrier wait (about 0.25 s)
+constexpr unsigned int kBarIters = 1u << 21;  // bounded barrier wait (polls of an L2 line: about 1 s)
+constexpr int kCapItems = 4096;               // vertices / hyperedges cached per CTA
+constexpr long long kPersistentMinRows = 32768;  // n + m from which the persistent form runs
+constexpr int kCapList = 12288;               // incidences / pins cached per CTA
 
-// Grid barrier with the pass's reduction: per-CTA partials, the two-level
-// reduction of grid_reduce, the final step fin(tot) in the CTA that completes
-// it, then a generation counter releases the others.  A wait that runs out
-// sets HEF_WAIT_TIMEOUT in the status word; every later pass then stops.
-template <int NQ, int S, typename T, typename Fin>
-__device__ __forceinline__ void reduce_barrier(const KView<T>& kv, const T (&acc)[NQ][S],
-                                               unsigned int* gen, unsigned int* status, Fin fin) {
-  __shared__ unsigned int g0;
-  __shared__ double tot[6 * kMaxS];
-  if (threadIdx.x == 0) g0 = *reinterpret_cast<volatile unsigned int*>(gen);
-  // (block_partials_qs begins and grid_reduce ends with a CTA barrier)
-  block_partials_qs<NQ, S, T>(acc, kv.red.part);
-  if (grid_reduce(kv.red, NQ * S, tot)) {
-    fin(tot);
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) atomicAdd(gen, 1u);
-    return;
-  }
-  if (threadIdx.x == 0) {
-    unsigned int it = 0;
-    while (*reinterpret_cast<volatile unsigned int*>(gen) == g0) {
-      if (++it > kBarIters) {
-        atomicOr(status, HEF_WAIT_TIMEOUT);
-        break;
+// Threads of the persistent CTA: 128 registers a thread (the fused phases
+// spill at 64) for records of up to 32 bytes, 255 for wider records.
+template <typename T, int S>
+__host__ __device__ constexpr int pers_threads() {
+  return 2 * S * sizeof(T) <= 32 ? 512 : 256;
+}
+
+// In one CTA of NT threads: out[slot] = sum over b < nb of part[b * N + slot]
+// for slot < N, with every load of a thread issued before its adds (one
+// round trip to L2 for up to 8 partials a thread), then the per-thread sums
+// of a slot added in thread order: a fixed order for given nb, N and NT.
+// Ends with __syncthreads (out may be shared memory).
+template <int NT>
+__device__ __forceinline__ void reduce_slots_wide(const double* part, int nb, int N,
+                                                  double* out) {
+  __shared__ double tmp[NT];
+  const int per = NT / N;  // threads per slot (N <= 6 * 16 <= NT)
+  const int t = threadIdx.x, slot = t % N, r = t / N;
+  double acc = 0.0;
+  if (r < per) {
+    for (int b0 = r; b0 < nb; b0 += 8 * per) {
+      double x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int b = b0 + q * per;
+        x[q] = b < nb ? __ldcg(part + (size_t)b * N + slot) : 0.0;
       }
-      __nanosleep(64);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) acc += x[q];
     }
-    __threadfence();
+  }
+  tmp[t] = acc;
+  __syncthreads();
+  if (t < N) {
+    double sacc = 0.0;
+    for (int q = 0; q < per; ++q) sacc += tmp[q * N + t];
+    out[t] = sacc;
   }
   __syncthreads();
+}
+
+// Dynamic shared memory of the persistent kernel.
+// Layout: the vertex and edge lists at fixed offsets (so that their addresses
+// take no registers), then inv_nu, te, the reduction results, itot (FP64),
+// cfT and nuT (working type).
+constexpr size_t kListBytes = (size_t)2 * (kCapItems + 1 + kCapList) * sizeof(int);
+template <typename T>
+__host__ __device__ inline size_t pers_smem(int k, int S) {
+  const size_t nc = (size_t)(k + 1) * 2 * S;
+  size_t b = kListBytes;
+  b += nc * sizeof(double);                                            // inv_nu
+  b += (size_t)(3 + 6 + 1) * S * sizeof(double) + 4 * sizeof(double);  // te, red, spare, itot
+  b += nc * 4 * sizeof(T) + nc * sizeof(T);                            // cfT, nuT
+  return (b + 15) / 16 * 16;
+}
+
+// Smallest x in [0, hi] with key(x) >= t (key non-decreasing, key(hi) >= t),
+// by one warp: 32 probes per round.
+template <typename Key>
+__device__ __forceinline__ int warp_lower_bound(int hi, long long t, Key key) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0;
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) / 32;
+    const int x = min(lo + step * (lane + 1), hi);
+    const unsigned mask = __ballot_sync(0xffffffffu, key(x) >= t);
+    const int f = __ffs(mask) - 1;  // lane 31 probes hi, so f >= 0
+    const int nhi = min(lo + step * (f + 1), hi);
+    lo = f == 0 ? lo : lo + step * f + 1;
+    hi = nhi;
+  }
+  const int x = lo + lane;
+  const unsigned mask = __ballot_sync(0xffffffffu, x <= hi && key(min(x, hi)) >= t);
+  return lo + __ffs(mask) - 1;
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
 }
 
 __device__ __forceinline__ bool stopped(const unsigned int* status) {
   return *reinterpret_cast<const volatile unsigned int*>(status) != 0u;
 }
 
-// All k steps in one launch.  Every CTA must be resident at once (the grid is
-// sized from the occupancy of this kernel); passes walk their items in
-// grid-stride tiles of blockDim.x.
+// Grid barrier number `ph` with its phase's reduction.  Every CTA writes its
+// partial sums to part[ph & 1] and arrives on cnt[0]; the last CTA to arrive
+// sums all partials in a fixed order (reduce_slots), publishes the N results
+// in pub[ph & 1] and releases the others through cnt[1]; each CTA then copies
+// the results to `out` (shared memory).  Double buffers suffice: a buffer is
+// written again only at barrier ph + 2, which no CTA reaches before every
+// CTA has finished reading barrier ph's results.  Every wait is bounded; on
+// expiry HEF_WAIT_TIMEOUT is set in the status word.  Returns false when
+// the launch must stop.
+template <int NQ, int S, int NT, typename T>
+__device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, double* pub, int ph,
+                                         unsigned int* cnt, unsigned int* status, double* out) {
+  constexpr int N = NQ * S;
+  double* buf = part + (size_t)(ph & 1) * gridDim.x * 6 * S;
+  double* res = pub + (size_t)(ph & 1) * 6 * S;
+  block_partials_qs<NQ, S, T, NT, 8>(acc, buf);
+  __shared__ int role;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int old = atomicAdd(cnt, 1u);
+    role = old == (unsigned int)(ph + 1) * gridDim.x - 1u;
+    if (role) __threadfence();
+  }
+  __syncthreads();
+  if (role) {
+    reduce_slots_wide<NT>(buf, gridDim.x, N, out);
+    for (int t = threadIdx.x; t < N; t += NT) res[t] = out[t];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      __threadfence();
+      atomicExch(cnt + 1, (unsigned int)(ph + 1));
+    }
+    return true;
+  }
+  if (threadIdx.x == 0) {
+    unsigned int it = 0;
+    int ok = 1;
+    while (ld_acquire(cnt + 1) < (unsigned int)(ph + 1)) {
+      if (++it > kBarIters) {
+        atomicOr(status, HEF_WAIT_TIMEOUT);
+        ok = 0;
+        break;
+      }
+      if ((it & 255u) == 0u && stopped(status)) {
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    role = ok ? 2 : 0;
+  }
+  __syncthreads();
+  if (role != 2) return false;
+  for (int t = threadIdx.x; t < N; t += NT) out[t] = __ldcg(res + t);
+  __syncthreads();
+  return true;
+}
+
 template <typename T, int S>
-__global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(3))
+__global__ void __launch_bounds__(pers_threads<T, S>(), 1)
     k_krylov_steps(IncView g, ScalView<T> sv, KView<T> kv, int k, T* __restrict__ V,
-                   long long ldv, unsigned int* gen, unsigned int* status) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  const long long base = (long long)blockIdx.x * blockDim.x;
-  const long long nrows = 2ll * g.n + g.m;
+                   long long ldv, double* part, unsigned int* cnt, unsigned int* status) {
+  constexpr int NT = pers_threads<T, S>();
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int nc = (k + 1) * 2 * S;
+  int* lv_ofs = reinterpret_cast<int*>(smem_raw);
+  int* lv_edge = lv_ofs + kCapItems + 1;
+  int* le_ofs = lv_edge + kCapList;
+  int* le_pin = le_ofs + kCapItems + 1;
+  double* s_inv_nu = reinterpret_cast<double*>(smem_raw + kListBytes);
+  double* s_te = s_inv_nu + nc;
+  double* s_red = s_te + 3 * S;
+  double* s_itot = s_red + 7 * S;
+  T* s_cfT = reinterpret_cast<T*>(s_itot + 4);
+  T* s_nuT = s_cfT + (size_t)nc * 4;
+  __shared__ int rng[4];
+  double* pub = part + (size_t)2 * gridDim.x * 6 * S;
+
+  if (stopped(status)) return;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int G = gridDim.x, b = blockIdx.x;
+  // this CTA's ranges: boundaries at b/G of the weights (incidences + items)
+  if (wid < 4) {
+    const bool vtx = wid < 2;
+    const int bb = b + (wid & 1);
+    const long long W = vtx ? (long long)g.vptr[g.n] + g.n : (long long)g.ceptr[g.m] + g.m;
+    const long long t = bb >= G ? W : W * bb / G;
+    const int x = vtx ? warp_lower_bound(g.n, t, [&](int v) { return (long long)__ldg(g.vptr + v) + v; })
+                      : warp_lower_bound(g.m, t, [&](int e) { return (long long)__ldg(g.ceptr + e) + e; });
+    if (lane == 0) rng[wid] = x;
+  }
+  for (int c = tid; c < nc; c += NT) {
+    s_inv_nu[c] = kv.inv_nu[c];
+    s_nuT[c] = kv.nuT[c];
+  }
+  if (tid < 3) s_itot[tid] = kv.itot[tid];
+  __syncthreads();
+  const int v0 = rng[0], v1 = rng[1], e0 = rng[2], e1 = rng[3];
+  const int i0 = g.vptr[v0], p0 = g.ceptr[e0];
+  const int nv = min(v1 - v0, kCapItems), ne = min(e1 - e0, kCapItems);
+  const int ni = min(g.vptr[v1] - i0, kCapList), np = min(g.ceptr[e1] - p0, kCapList);
+  for (int i = tid; i <= nv; i += NT) lv_ofs[i] = __ldg(g.vptr + v0 + i);
+  for (int i = tid; i < ni; i += NT) lv_edge[i] = __ldg(g.vedge + i0 + i);
+  for (int i = tid; i <= ne; i += NT) le_ofs[i] = __ldg(g.ceptr + e0 + i);
+  for (int i = tid; i < np; i += NT) le_pin[i] = __ldg(g.cpins + p0 + i);
+  __syncthreads();
+  auto vofs = [&](int v) { const int i = v - v0; return i <= nv ? lv_ofs[i] : __ldg(g.vptr + v); };
+  auto vedg = [&](int t) { const int i = t - i0; return i < ni ? lv_edge[i] : __ldg(g.vedge + t); };
+  auto eofs = [&](int e) { const int i = e - e0; return i <= ne ? le_ofs[i] : __ldg(g.ceptr + e); };
+  auto epin = [&](int t) { const int i = t - p0; return i < np ? le_pin[i] : __ldg(g.cpins + t); };
+
+  int ph = 0;
   for (int j = 1; j <= k; ++j) {
-    if (stopped(status)) return;
-    {
+    {  // edge phase
       T acc[3][S];
       zero_acc(acc);
-      for (long long e0 = base; e0 < g.m; e0 += stride)
-        edge_item<T, S>(g, sv, kv, j, (int)(e0 + threadIdx.x), acc);
-      reduce_barrier<3, S>(kv, acc, gen, status, [&](const double* tot) { edge_final(kv, S, tot); });
+      for (int base = e0 + wid * 32; base < e1; base += NT) {
+        const int e = base + lane;
+        edge_item<T, S, true>(g, sv, kv, s_nuT, j, e < e1 ? e : g.m, acc, eofs, epin);
+      }
+      if (!pbarrier<3, S, NT>(acc, part, pub, ph++, cnt, status, s_red)) return;
+      for (int t = tid; t < 3 * S; t += NT) s_te[t] = s_red[t];
+      __syncthreads();
     }
-    if (stopped(status)) return;
-    {
+    {  // vertex phase; then the Lanczos coefficients of step j
       T acc[6][S];
       zero_acc(acc);
-      for (long long v0 = base; v0 < g.n; v0 += stride)
-        node_item<T, S>(g, sv, kv, j, (int)(v0 + threadIdx.x), acc, V, ldv);
-      reduce_barrier<6, S>(kv, acc, gen, status,
-                           [&](const double* tn) { node_final(g, kv, S, j, tn); });
+      for (int base = v0 + wid * 32; base < v1; base += NT) {
+        const int v = base + lane;
+        node_item<T, S, true>(g, sv, kv, s_nuT, j, v < v1 ? v : g.n, acc, V, ldv, vofs, vedg);
+      }
+      if (!pbarrier<6, S, NT>(acc, part, pub, ph++, cnt, status, s_red)) return;
+      for (int c = tid; c < 2 * S; c += NT) {
+        const int op = c / S, q = c % S;
+        double cf[4];
+        if (op == 0) {
+          cf[0] = s_red[0 * S + q] * s_itot[0];
+          cf[1] = 0.0;
+          cf[2] = j >= 2 ? s_red[1 * S + q] : 0.0;
+          cf[3] = j >= 3 ? s_red[2 * S + q] : 0.0;
+        } else {
+          cf[0] = s_red[3 * S + q] * s_itot[1];
+          cf[1] = s_te[0 * S + q] * s_itot[2];
+          cf[2] = j >= 2 ? s_red[4 * S + q] + s_te[1 * S + q] : 0.0;
+          cf[3] = j >= 3 ? s_red[5 * S + q] + s_te[2 * S + q] : 0.0;
+        }
+        T* ct = s_cfT + ((size_t)j * 2 * S + c) * 4;
+        ct[0] = (T)cf[0];
+        ct[1] = (T)cf[1];
+        ct[2] = (T)(cf[2] * s_inv_nu[(size_t)(j - 1) * 2 * S + c]);
+        ct[3] = j >= 3 ? (T)(cf[3] * s_inv_nu[(size_t)(j - 2) * 2 * S + c]) : (T)0;
+        if (b == 0) {  // one copy in global memory for the tape and the backward
+          double* gc = kv.coef + ((size_t)j * 2 * S + c) * 4;
+          T* gt = kv.cfT + ((size_t)j * 2 * S + c) * 4;
+#pragma unroll
+          for (int q4 = 0; q4 < 4; ++q4) gc[q4] = cf[q4], gt[q4] = ct[q4];
+        }
+      }
+      __syncthreads();
     }
-    if (stopped(status)) return;
-    {
+    {  // update phase; then the inverse norms of step j
+      const CoefView<T, S> cf{s_cfT + (size_t)j * 2 * S * 4};
       T acc[2][S];
       zero_acc(acc);
-      for (long long r0 = base * upd_rows<T, S>(); r0 < nrows; r0 += stride * upd_rows<T, S>())
-        update_item<T, S>(g, sv, kv, j, r0 + threadIdx.x, acc);
-      reduce_barrier<2, S>(kv, acc, gen, status,
-                           [&](const double* tot) { update_final(kv, S, j, tot); });
+      for (int v = v0 + tid; v < v1; v += NT) update_vertex<T, S, true>(g, sv, kv, j, v, cf, acc);
+      for (int e = e0 + tid; e < e1; e += NT) update_edge<T, S, true>(g, sv, kv, j, e, cf, acc);
+      if (!pbarrier<2, S, NT>(acc, part, pub, ph++, cnt, status, s_red)) return;
+      for (int c = tid; c < 2 * S; c += NT) {
+        const double nu2 = s_red[c];
+        const bool alive = s_inv_nu[(size_t)(j - 1) * 2 * S + c] > 0.0 && nu2 > kv.tol * kv.tol;
+        const double inu = alive ? rsqrt(nu2) : 0.0;
+        s_inv_nu[(size_t)j * 2 * S + c] = inu;
+        s_nuT[(size_t)j * 2 * S + c] = (T)inu;
+        if (b == 0) kv.inv_nu[(size_t)j * 2 * S + c] = inu, kv.nuT[(size_t)j * 2 * S + c] = (T)inu;
+      }
+      __syncthreads();
     }
   }
-  if (stopped(status)) return;
-  for (long long v0 = base; v0 < g.n; v0 += stride)
-    archive_item<T, S>(g, kv, k, (int)(v0 + threadIdx.x), V, ldv);
+  for (int v = v0 + tid; v < v1; v += NT) archive_item<T, S, true>(g, kv, s_nuT, k, v, V, ldv);
 }
 
 inline int blocks_for(long long rows) { return (int)((rows + kThreads - 1) / kThreads); }
@@ -806,15 +1040,16 @@ template <typename T>
 size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>* kv) {
   Carver c(base);
   const long long maxblk = blocks_for(2 * n + m);
+  const long long me = m > 0 ? m : 1;
   kv->n = (int)n;
   kv->m = (int)m;
-  kv->Yc = c.take<T>(n * S);
-  kv->Bc[0] = c.take<T>(n * S);
-  kv->Bc[1] = c.take<T>(n * S);
-  kv->Yb = c.take<T>((n + m) * S);
-  kv->Bb[0] = c.take<T>((n + m) * S);
-  kv->Bb[1] = c.take<T>((n + m) * S);
-  kv->se = c.take<T>((m > 0 ? m : 1) * S);
+  kv->Yv = c.take<T>(n * 2 * S);
+  kv->Bv[0] = c.take<T>(n * 2 * S);
+  kv->Bv[1] = c.take<T>(n * 2 * S);
+  kv->Ye = c.take<T>(me * S);
+  kv->Be[0] = c.take<T>(me * S);
+  kv->Be[1] = c.take<T>(me * S);
+  kv->Er = c.take<T>(me * 2 * S);
   kv->inv_nu = c.take<double>((size_t)(k + 1) * 2 * S);
   kv->coef = c.take<double>((size_t)(k + 1) * 2 * S * 4);
   kv->nuT = c.take<T>((size_t)(k + 1) * 2 * S);
@@ -825,7 +1060,8 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->red.gpart = c.take<double>((size_t)red_groups((int)maxblk) * 6 * S);
   kv->red.gcnt = c.take<unsigned int>(red_groups((int)maxblk) + 1);
   kv->red.tcnt = c.take<unsigned int>(1);
-  kv->gen = c.take<unsigned int>(1);
+  kv->ppart = c.take<double>((size_t)2 * num_sms() * 2 * 6 * S + 2 * 6 * S);
+  kv->pcount = c.take<unsigned int>(2);
   return c.bytes();
 }
 
@@ -842,43 +1078,53 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   IncView g = view(inc);
   const ScalView<T> sv = scal_view<T>(inc);
   const long long n = inc->n, m = inc->m;
-  const int grid_all = blocks_for(2 * n + m);
+  const int grid_all = blocks_for(n + m);
   const int grid_e = blocks_for(m > 0 ? m : 1);
   const int grid_n = blocks_for(n);
-  const int grid_upd = blocks_for((2 * n + m + upd_rows<T, S>() - 1) / upd_rows<T, S>());
+  const int grid_upd = blocks_for((n + m + upd_rows<T, S>() - 1) / upd_rows<T, S>());
   HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
   // the launches after the first are programmatically dependent on their
   // predecessor (each kernel waits for it before touching shared buffers)
   HEF_LAUNCH("k_start_write", st,
              HEF_CHECK_CUDA(launch_dependent(k_start_write<T, S>, grid_all, kThreads, st, g, sv, kv)));
   HEF_CHECK_LAUNCH();
-  // one launch for all steps when every row of a pass has a resident thread
-  // of its own (small hypergraphs, where per-step launches cost more than the
-  // work); larger ones run faster as three launches per step, whose CTAs each
-  // take one item per thread
-  const int res = persistent ? num_sms() * resident_ctas(k_krylov_steps<T, S>, kThreads) : 0;
-  if (persistent && t_force_oversized) {
-    // the timeout test: a plain launch of twice the resident grid, so that
-    // the first barrier cannot complete and its bounded wait runs out
-    const int grid = std::max(1, std::min(2 * res, grid_all));
-    HEF_LAUNCH("k_krylov_steps", st, k_krylov_steps<T, S><<<grid, kThreads, 0, st>>>(
-                                         g, sv, kv, k, V, ldv, kv.gen, inc->status));
-    HEF_CHECK_LAUNCH();
-    return HEF_OK;
-  }
-  if (persistent && (long long)res * kThreads >= 2 * n + m) {
-    // cooperative: the runtime guarantees that all CTAs are resident at once
-    // (other work on the GPU delays the start instead of starving a barrier);
-    // if it refuses the grid, the per-step form below runs instead
-    const int grid = std::max(1, std::min(res, grid_all));
-    cudaError_t e = cudaSuccess;
-    HEF_LAUNCH("k_krylov_steps", st,
-               e = launch_cooperative(k_krylov_steps<T, S>, grid, kThreads, st, g, sv, kv, k, V,
-                                      ldv, kv.gen, inc->status));
-    if (e == cudaSuccess) return HEF_OK;
-    if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorNotSupported)
-      return set_error(HEF_ERR_CUDA, "k_krylov_steps: %s", cudaGetErrorString(e));
-    (void)cudaGetLastError();
+  // all steps as one cooperative launch of one CTA per SM (see
+  // k_krylov_steps) unless this thread's calls share the GPU with other work
+  // (the batched form); if the runtime refuses the grid, three launches per
+  // step run instead
+  // (small hypergraphs: the per-step launches are as fast as the barriers)
+  if (persistent && (n + m >= kPersistentMinRows || t_force_oversized)) {
+    constexpr int NT = pers_threads<T, S>();
+    const size_t smem = pers_smem<T>(k, S);
+    constexpr size_t kSmemLimit = 227 * 1024;  // per-CTA opt-in limit of the sm_100 family
+    if (smem <= kSmemLimit) HEF_ENSURE_SMEM((k_krylov_steps<T, S>), smem);
+    int occ = 0;
+    if (smem <= kSmemLimit &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_krylov_steps<T, S>, NT, smem) ==
+            cudaSuccess &&
+        occ >= 1) {
+      HEF_CHECK_CUDA(cudaMemsetAsync(kv.pcount, 0, 2 * sizeof(unsigned int), st));
+      // the timeout test launches twice the resident grid as a plain launch,
+      // so that the first barrier cannot complete and its bounded wait runs out
+      const int grid = num_sms() * (t_force_oversized ? 2 : 1);
+      cudaError_t e = cudaSuccess;
+      if (t_force_oversized) {
+        HEF_LAUNCH("k_krylov_steps", st,
+                   k_krylov_steps<T, S><<<grid, NT, smem, st>>>(g, sv, kv, k, V, ldv, kv.ppart,
+                                                               kv.pcount, inc->status));
+        e = cudaGetLastError();
+      } else {
+        HEF_LAUNCH("k_krylov_steps", st,
+                   e = launch_cooperative_smem(k_krylov_steps<T, S>, grid, NT, smem, st, g, sv,
+                                               kv, k, V, ldv, kv.ppart, kv.pcount, inc->status));
+      }
+      if (e == cudaSuccess) return HEF_OK;
+      if (e != cudaErrorCooperativeLaunchTooLarge && e != cudaErrorNotSupported)
+        return set_error(HEF_ERR_CUDA, "k_krylov_steps: %s", cudaGetErrorString(e));
+      (void)cudaGetLastError();
+    } else {
+      (void)cudaGetLastError();
+    }
   }
   for (int j = 1; j <= k; ++j) {
     HEF_LAUNCH("k_edge_pass", st,

@@ -30,7 +30,9 @@ def restore_default():
 
 @pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
 def test_persistent_and_per_step_forms_agree(dtype, tol):
-    H, k, S = workload("grid64x32_m2300")  # small: the persistent form applies
+    # n + m = 41,000 rows: above the size from which the persistent form runs
+    H = grid_netlist(200, 100, 21000, 7)
+    k = 10
     x0c, x0b = start_block(H.n, H.m, 2, 0)
     hef().set_krylov_persistent(1)
     a = run_pipeline(H, x0c, x0b, k, dtype)
