@@ -362,6 +362,96 @@ hef_status hef_batch_autotune(const hef_batch_item* items, int32_t G,
                               int32_t* nstreams_out, int32_t* schedule_out,
                               float* ms_out);
 /* ------------------------------------------------------------------------
+ * Consumers of the scores: Algorithm 1 step 6 and one coarsening level of
+ * Algorithm 2 (Section III-B, steps 4-10) with Eq. R_W_update (Section
+ * III-A.3, "Multilevel Effective Resistance Clustering").  The paper fixes
+ * neither the threshold nor any tie rule; these calls implement the
+ * following reading of it, and their results are a deterministic function
+ * of the inputs (integer atomics only; FP64 sums in the stated orders with
+ * round-to-nearest operations), equal bit for bit to a sequential CPU
+ * statement of the same rules.
+ *
+ * hef_sort_resistance (Algorithm 1 step 6): order[m] = the hyperedge ids in
+ * ascending R (finite), ties by ascending id.
+ *
+ * hef_coarsen_level, with the hyperedges as given to hef_build_incidence
+ * (eptr[m+1], pins[P], w[m], caller order; `inc` is that incidence):
+ *  1. Eq. R_W_update: R_upd[e] = (sum over e's pins, in pin order from 0.0,
+ *     of eta[v]) + R[e]; eta (n, nullable = zeros) are the vertices'
+ *     supernode weights from the previous level.
+ *  2. order = hyperedges by ascending R_upd, ties by id.
+ *  3. delta = the given delta (>= 0), or with delta < 0 the quantile-th
+ *     quantile of R_upd over the hyperedges with >= 2 pins: the value at
+ *     position floor(quantile (c - 1)) of their ascending order (c of them;
+ *     +inf if c = 0).  *out->delta receives it.
+ *  4. Greedy contraction in that order: a hyperedge with >= 2 pins and
+ *     R_upd < delta is contracted when none of its pins belongs to a
+ *     hyperedge contracted before it; owner[v] = the contracted hyperedge
+ *     that v joined, -1 for isolated vertices.
+ *  5. cluster[v]: a new id, in ascending vertex order, for every isolated
+ *     vertex and for the smallest pin of every contracted hyperedge; the
+ *     other pins take their supernode's id (nc ids).
+ *  6. Local clustering (Section III-B.2; only when Q is given: Q n x ldq of
+ *     dtype, K columns, QH[K] from hef_edge_resistance): every isolated
+ *     vertex p joins the supernode c, among those of its co-pins (in the
+ *     hyperedges containing p) formed by a contraction, that minimises
+ *     d = max over i with QH[i] > 1e-300 of (Q[p,i] - mu_c[i])^2 / QH[i],
+ *     mu_c = the mean Q row of c's members (summed in the forming
+ *     hyperedge's pin order); ties to the smallest c.  target[p] = c (an id
+ *     of step 5) or -1, dist[p] = d (0 if none).
+ *  7. Weights: a supernode's weight is the R_upd of its hyperedge, an
+ *     isolated vertex keeps eta[v]; each joining seed p adds (eta[p] +
+ *     dist[p]) to its supernode's weight, in ascending p.
+ *  8. final_cluster[v]: compact ids (nf of them) in the order of each
+ *     cluster's smallest vertex; eta_out[nf] their weights (the next level's
+ *     eta).
+ *  9. Coarse hypergraph (Algorithm 2 step 6): each hyperedge's pins mapped
+ *     to final ids, the first occurrence of each id kept in pin order;
+ *     hyperedges left with < 2 pins are dropped, the rest keep their weight
+ *     and relative order: ceptr[m'+1] (int64), cpins[P'], cw[m'], emap[m']
+ *     (the hyperedge it came from).
+ * counts[5] = {nc, nf, m', P', status}; status is nonzero when a bounded
+ * grid-wide wait of the contraction ran out (results then invalid).  The
+ * contraction is one cooperative launch (rounds of a fixed point that equals
+ * the sequential greedy rule).  All outputs are caller-owned device arrays
+ * sized for the fine hypergraph: R_upd, order, cw, emap [m]; ceptr [m+1];
+ * cpins [P]; owner, cluster, target, final_cluster [n]; dist, eta_out [n];
+ * delta [1]; counts [5].  Workspace: hef_level_workspace_bytes(n, m, K)
+ * (K = 0 without Q); hef_sort_resistance needs hef_level_workspace_bytes(0,
+ * m, 0).
+ * ---------------------------------------------------------------------- */
+typedef struct hef_level_out {
+  double* R_upd;
+  int32_t* order;
+  double* delta;
+  int32_t* owner;
+  int32_t* cluster;
+  int32_t* target;
+  double* dist;
+  int32_t* final_cluster;
+  double* eta_out;
+  int32_t* counts;
+  int64_t* ceptr;
+  int32_t* cpins;
+  double* cw;
+  int32_t* emap;
+} hef_level_out;
+
+size_t hef_level_workspace_bytes(int64_t n, int64_t m, int32_t K);
+hef_status hef_sort_resistance(int64_t m, const double* R, int32_t* order,
+                               void* workspace, size_t workspace_bytes,
+                               void* stream);
+/* `out` is a HOST struct of device pointers. */
+hef_status hef_coarsen_level(const hef_incidence* inc, const int64_t* eptr,
+                             const int32_t* pins, const double* w,
+                             const double* R, const double* eta,
+                             const void* Q, int64_t ldq, int32_t K,
+                             int32_t dtype, const double* QH, double delta,
+                             double quantile, const hef_level_out* out,
+                             void* workspace, size_t workspace_bytes,
+                             void* stream);
+
+/* ------------------------------------------------------------------------
  * Edge resistance without caller-provided device memory.  The paper has no
  * counterpart: this is a service of the library.
  *

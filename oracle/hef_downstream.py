@@ -147,22 +147,17 @@ def clusters(n, eptr, pins, owner, contracted, Ru, eta):
     return cluster, nc, eta_next, formed_by
 
 
-def centroids(eptr, pins, formed_by, Q):
-    """Reading D7: mean embedding row of every contracted supernode (rows of
-    isolated vertices' clusters stay zero)."""
-    nc = len(formed_by)
+def centroid(c, eptr, pins, formed_by, Q):
+    """Reading D7: mean embedding row of the contracted supernode c."""
     K = Q.shape[1]
-    mu = np.zeros((nc, K), dtype=np.float64)
-    for c in range(nc):
-        e = formed_by[c]
-        if e < 0:
-            continue
-        a, b = int(eptr[e]), int(eptr[e + 1])
-        for i in range(K):
-            acc = 0.0
-            for t in range(a, b):
-                acc += float(Q[pins[t], i])
-            mu[c, i] = acc / (b - a)
+    e = formed_by[c]
+    a, b = int(eptr[e]), int(eptr[e + 1])
+    mu = np.zeros(K, dtype=np.float64)
+    for i in range(K):
+        acc = 0.0
+        for t in range(a, b):
+            acc += float(Q[pins[t], i])
+        mu[i] = acc / (b - a)
     return mu
 
 
@@ -178,30 +173,38 @@ def seed_distance(qp, mu_c, QH):
     return d
 
 
+def seed_choice(p, eptr, pins, vptr, vedge, cluster, formed_by, Q, QH, mu_cache=None):
+    """Readings D6-D7 for one isolated vertex p: (supernode, distance), or
+    (-1, 0.0) without a candidate.  mu_cache (dict) keeps centroids."""
+    mu_cache = {} if mu_cache is None else mu_cache
+    best, bd = -1, math.inf
+    for t in range(int(vptr[p]), int(vptr[p + 1])):
+        e = int(vedge[t])
+        for s in range(int(eptr[e]), int(eptr[e + 1])):
+            u = int(pins[s])
+            c = int(cluster[u])
+            if u == p or formed_by[c] < 0:
+                continue
+            if c not in mu_cache:
+                mu_cache[c] = centroid(c, eptr, pins, formed_by, Q)
+            d = seed_distance(Q[p], mu_cache[c], QH)
+            if d < bd or (d == bd and c < best):
+                best, bd = c, d
+    return (best, bd) if best >= 0 else (-1, 0.0)
+
+
 def local_clustering(n, eptr, pins, vptr, vedge, cluster, owner, formed_by, eta, eta_next, Q, QH):
     """Algorithm 2 steps 7-10 with readings D6-D8.  vptr/vedge: the hyperedges
     containing each vertex.  Returns target[n] (the supernode each seed joins,
     -1 otherwise), dist[n] and the updated supernode weights."""
-    mu = centroids(eptr, pins, formed_by, Q)
     target = np.full(n, -1, dtype=np.int32)
     dist = np.zeros(n, dtype=np.float64)
+    mu_cache = {}
     for p in range(n):
         if owner[p] >= 0:
             continue
-        best, bd = -1, math.inf
-        for t in range(int(vptr[p]), int(vptr[p + 1])):
-            e = int(vedge[t])
-            for s in range(int(eptr[e]), int(eptr[e + 1])):
-                u = int(pins[s])
-                c = int(cluster[u])
-                if u == p or formed_by[c] < 0:
-                    continue
-                d = seed_distance(Q[p], mu[c], QH)
-                if d < bd or (d == bd and c < best):
-                    best, bd = c, d
-        if best >= 0:
-            target[p] = best
-            dist[p] = bd
+        target[p], dist[p] = seed_choice(p, eptr, pins, vptr, vedge, cluster, formed_by, Q, QH,
+                                         mu_cache)
     eta2 = eta_next.copy()
     for p in range(n):
         if target[p] >= 0:

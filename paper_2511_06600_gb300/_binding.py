@@ -62,6 +62,10 @@ _SIGS = {
     "hef_set_krylov_persistent": (c_i32, [c_i32]),
     "hef_krylov_basis_tape": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p, c_sz,
                                       c_p, c_sz, c_p]),
+    "hef_level_workspace_bytes": (c_sz, [c_i64, c_i64, c_i32]),
+    "hef_sort_resistance": (c_i32, [c_i64, c_p, c_p, c_p, c_sz, c_p]),
+    "hef_coarsen_level": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_i32, c_i32, c_p,
+                                  ctypes.c_double, ctypes.c_double, c_p, c_p, c_sz, c_p]),
     "hef_edge_resistance_backward_workspace_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32, c_i32]),
     "hef_edge_resistance_backward": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_sz, c_p,
                                              c_i64, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p,
@@ -586,3 +590,109 @@ class Batch:
     def replay(self):
         self.graph.replay()
         return self.out
+
+
+# ---------------------------------------------------------------- downstream
+
+
+class _LevelOut(ctypes.Structure):
+    """hef_level_out (include/hef.h)."""
+    _fields_ = [("R_upd", c_p), ("order", c_p), ("delta", c_p), ("owner", c_p), ("cluster", c_p),
+                ("target", c_p), ("dist", c_p), ("final_cluster", c_p), ("eta_out", c_p),
+                ("counts", c_p), ("ceptr", c_p), ("cpins", c_p), ("cw", c_p), ("emap", c_p)]
+
+
+def sort_resistance(R, stream=None):
+    """hef_sort_resistance (Algorithm 1 step 6): hyperedge ids by ascending R,
+    ties by id."""
+    L = lib()
+    m = int(R.numel())
+    R = R.to(torch.float64).contiguous()
+    order = torch.empty(max(m, 1), dtype=torch.int32, device=R.device)[:m]
+    ws = _workspace(L.hef_level_workspace_bytes(0, m, 0), R.device)
+    _check("hef_sort_resistance",
+           L.hef_sort_resistance(m, _ptr(R), _ptr(order), _ptr(ws), ws.numel(), _stream(stream)))
+    return order
+
+
+def coarsen_level(inc, eptr, pins, w, R, eta=None, Q=None, K=None, QH=None, delta=-1.0,
+                  quantile=0.5, stream=None):
+    """hef_coarsen_level: one coarsening level (Algorithm 2 steps 4-10) from
+    the scores R of the incidence `inc` (built from eptr, pins, w).  Returns
+    a dict of device tensors; `counts` holds nc, nf, m', P', status (the
+    coarse arrays are valid up to m' and P')."""
+    L = lib()
+    dev = R.device
+    n, m, P = inc.n, inc.m, inc.P
+    o = dict(R_upd=torch.empty(max(m, 1), dtype=torch.float64, device=dev),
+             order=torch.empty(max(m, 1), dtype=torch.int32, device=dev),
+             delta=torch.empty(1, dtype=torch.float64, device=dev),
+             owner=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+             cluster=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+             target=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+             dist=torch.empty(max(n, 1), dtype=torch.float64, device=dev),
+             final_cluster=torch.empty(max(n, 1), dtype=torch.int32, device=dev),
+             eta_out=torch.empty(max(n, 1), dtype=torch.float64, device=dev),
+             counts=torch.zeros(5, dtype=torch.int32, device=dev),
+             ceptr=torch.empty(m + 1, dtype=torch.int64, device=dev),
+             cpins=torch.empty(max(P, 1), dtype=torch.int32, device=dev),
+             cw=torch.empty(max(m, 1), dtype=torch.float64, device=dev),
+             emap=torch.empty(max(m, 1), dtype=torch.int32, device=dev))
+    st = _LevelOut(*[_ptr(o[f]) for f, _ in _LevelOut._fields_])
+    code = _dtype_code(Q.dtype) if Q is not None else HEF_F64
+    Kc = int(K) if Q is not None else 0
+    ws = _workspace(L.hef_level_workspace_bytes(n, m, Kc), dev)
+    _check("hef_coarsen_level",
+           L.hef_coarsen_level(inc.handle, _ptr(eptr), _ptr(pins), _ptr(w), _ptr(R), _ptr(eta),
+                               _ptr(Q), Q.stride(0) if Q is not None else 0, Kc, code, _ptr(QH),
+                               float(delta), float(quantile), ctypes.byref(st), _ptr(ws),
+                               ws.numel(), _stream(stream)))
+    o["_keep"] = (ws, R, eta, Q, QH)
+    return o
+
+
+def level_sizes(out):
+    """(nc, nf, m', P') of a coarsen_level result (synchronises); raises if
+    the contraction's bounded wait ran out."""
+    c = out["counts"].cpu().tolist()
+    if c[4]:
+        raise HefError("hef_coarsen_level", -5, f"contraction wait status {c[4]}")
+    return c[0], c[1], c[2], c[3]
+
+
+def multilevel(n, eptr, pins, w, starts, k, levels, dtype=torch.float32, quantile=0.5,
+               min_vertices=2, clique_mode=HEF_CLIQUE_HYPEREDGE):
+    """Algorithm 2's level loop (Section III-B): per level, Algorithm 1 on
+    the current hypergraph (hef_build_incidence, hef_krylov_basis,
+    hef_orthonormalize, hef_edge_resistance), then hef_coarsen_level with the
+    previous level's supernode weights, and the coarse hypergraph as the next
+    level's input.  `starts(level, n, m)` returns that level's random start
+    block (x0_clique n x S, x0_star (n+m) x S, CUDA float64).  Returns the
+    per-level records and the cluster of every original vertex."""
+    dev = eptr.device
+    eta = None
+    cur = (int(n), eptr, pins, w)
+    of_orig = torch.arange(int(n), dtype=torch.int32, device=dev)
+    out = []
+    for lv in range(int(levels)):
+        nl, ep, pi, wl = cur
+        ml = int(ep.numel() - 1)
+        if nl < min_vertices or ml < 1:
+            break
+        x0c, x0b = starts(lv, nl, ml)
+        S = int(x0c.shape[1])
+        K = 2 * int(k) * S
+        inc = build_incidence(nl, ep, pi, wl, clique_mode)
+        V = krylov_basis(inc, x0c, x0b, k, dtype)
+        Q, _, rank = orthonormalize(V, K)
+        sc = edge_resistance(inc, Q, K)
+        inc.check()
+        lo = coarsen_level(inc, ep, pi, wl, sc["R"], eta, Q, K, sc["QH"], quantile=quantile)
+        nc, nf, mc, pc = level_sizes(lo)
+        of_orig = lo["final_cluster"][of_orig.long()]
+        out.append(dict(n=nl, m=ml, P=int(pi.numel()), R=sc["R"], Q=Q, QH=sc["QH"], K=K,
+                        eptr=ep, pins=pi, w=wl, eta=eta, level=lo, nc=nc, nf=nf, m_next=mc,
+                        P_next=pc, incidence=inc))
+        eta = lo["eta_out"][:nf].clone()
+        cur = (nf, lo["ceptr"][:mc + 1].clone(), lo["cpins"][:pc].clone(), lo["cw"][:mc].clone())
+    return out, of_orig

@@ -97,7 +97,9 @@ __global__ void k_scan_apply(const int* __restrict__ in, int N, const int* __res
   if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[N] = bsum[gridDim.x];
 }
 
-inline int scan_tiles(long long N) { return (int)((N + kTile - 1) / kTile); }
+}  // namespace
+
+int scan_tiles(long long N) { return (int)((N + kTile - 1) / kTile); }
 
 // out[0..N] = exclusive scan of in[0..N); out[N] = total.  bsum needs
 // scan_tiles(N) + 1 ints; counter is zero on entry (and on exit).  `in` and
@@ -114,6 +116,8 @@ hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, unsig
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
+
+namespace {
 
 // ----------------------------------------------------------------- stable LSD radix sort
 
@@ -181,18 +185,14 @@ __global__ void k_radix_scatter(const uint32_t* __restrict__ keys, const int32_t
   }
 }
 
-struct SortBufs {
-  uint32_t* k_alt;
-  int32_t* v_alt;
-  unsigned int* counter;  // of the scans (zero between calls)
-  int* counts;  // kMaxBuckets * ntiles + 1
-  int* bsum;    // scan_tiles(kMaxBuckets * ntiles) + 1
-};
+}  // namespace
 
-inline int bits_for(long long maxkey) {
-  int b = 1;
-  while (b < 32 && (1ll << b) <= maxkey) ++b;
-  return b;
+void carve_sort_bufs(Carver& c, long long N, SortBufs* b) {
+  const int ntiles = scan_tiles(N > 0 ? N : 1);
+  b->k_alt = c.take<uint32_t>(N > 0 ? N : 1);
+  b->v_alt = c.take<int32_t>(N > 0 ? N : 1);
+  b->counts = c.take<int>((long long)kMaxBuckets * ntiles + 1);
+  b->bsum = c.take<int>(scan_tiles((long long)kMaxBuckets * ntiles) + 1);
 }
 
 // Sorts (keys, vals) by key, stable; keys < 2^bits.  Result in keys/vals.
@@ -226,6 +226,8 @@ hef_status radix_sort(uint32_t* keys, int32_t* vals, long long N, int bits, Sort
   }
   return HEF_OK;
 }
+
+namespace {
 
 // ----------------------------------------------------------------- build kernels
 

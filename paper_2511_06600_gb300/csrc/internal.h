@@ -160,6 +160,32 @@ inline size_t carve_tape(void* base, long long n, long long m, int k, int S, siz
   return c.bytes();
 }
 
+// Device-wide scan and sort (incidence.cu), shared by the build and the
+// downstream calls.
+int scan_tiles(long long N);
+// out[0..N] = exclusive scan of in[0..N); out[N] = total.  bsum needs
+// scan_tiles(N) + 1 ints; counter is zero on entry (and on exit); in and out
+// may alias.
+hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, unsigned int* counter,
+                          cudaStream_t st);
+struct SortBufs {
+  uint32_t* k_alt;
+  int32_t* v_alt;
+  unsigned int* counter;  // of the scans (zero between calls)
+  int* counts;            // buckets x tiles + 1
+  int* bsum;
+};
+// Buffers of radix_sort for up to N items (the counter is the caller's).
+void carve_sort_bufs(Carver& c, long long N, SortBufs* b);
+inline int bits_for(long long maxkey) {
+  int b = 1;
+  while (b < 32 && (1ll << b) <= maxkey) ++b;
+  return b;
+}
+// Sorts (keys, vals) by key, stable (LSD radix); keys < 2^bits.
+hef_status radix_sort(uint32_t* keys, int32_t* vals, long long N, int bits, SortBufs b,
+                      cudaStream_t st);
+
 // Whether hef_krylov_basis(_tape) calls from this thread may run all Krylov
 // steps as one persistent launch (default on).  The persistent grid needs
 // every CTA resident at once, so callers that overlap other work on the GPU
