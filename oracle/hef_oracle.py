@@ -196,28 +196,37 @@ def krylov_chain(M, d, trivial, x0, k):
     return X
 
 
-def krylov_basis(H_n, eptr, pins, w, x0_c, x0_b, k, clique="hyperedge"):
+def krylov_basis(H_n, eptr, pins, w, x0_c, x0_b, k, clique="hyperedge", ops="both"):
     """The n x K matrix V (K = 2 k S) of Algorithm 1 step 3.
 
     Column c = (j-1)*2S + op*S + s holds the vertex entries of the j-th chain
     vector of start s of expansion op (0 = clique, 1 = star), with its mean
     removed (vectors are taken modulo the all-ones vector: scores only see
-    differences).  Star-node entries are dropped (Section III-A.3)."""
+    differences).  Star-node entries are dropped (Section III-A.3).
+
+    ops="star" (or "clique") keeps the pool of one expansion only (K = k S,
+    column (j-1)*S + s): the star-only pool is the earlier HyperEF method
+    that Section III-A.3 contrasts with the mixed pool."""
     n = H_n
     S = x0_c.shape[1]
+    chosen = {"both": (CLIQUE, STAR), "clique": (CLIQUE,), "star": (STAR,)}[ops]
     Mc, dc = random_walk(clique_expansion(n, eptr, pins, w, clique))
     Mb, db = random_walk(star_expansion(n, eptr, pins, w))
     tc = trivial_vectors(CLIQUE, n, dc)
     tb = trivial_vectors(STAR, n, db)
-    K = 2 * k * S
+    nop = len(chosen)
+    K = nop * k * S
     V = np.zeros((n, K))
     for s in range(S):
-        Xc = krylov_chain(Mc, dc, tc, x0_c[:, s], k)
-        Xb = krylov_chain(Mb, db, tb, x0_b[:, s], k)
+        chains = {}
+        if CLIQUE in chosen:
+            chains[CLIQUE] = krylov_chain(Mc, dc, tc, x0_c[:, s], k)
+        if STAR in chosen:
+            chains[STAR] = krylov_chain(Mb, db, tb, x0_b[:, s], k)
         for j in range(k):
-            for op, X in ((CLIQUE, Xc), (STAR, Xb)):
-                col = X[:n, j]
-                V[:, j * 2 * S + op * S + s] = col - col.mean()
+            for slot, op in enumerate(chosen):
+                col = chains[op][:n, j]
+                V[:, j * nop * S + slot * S + s] = col - col.mean()
     return V
 
 
@@ -358,19 +367,85 @@ def edge_resistance(Q, eptr, pins, w, reduce="max", kept=None):
     return dict(R=R, QH=QH, r=r, argvec=argvec, pmax=pmax, pmin=pmin, use=use)
 
 
+def embed_pairs(Q, eptr, pins):
+    """Reading A7's alternative for "p and q are the most distant nodes in the
+    embedding space" (Eq. ratios): per hyperedge, the pair of pins farthest
+    apart in the K-dimensional embedding, by squared Euclidean distance
+    summed over the columns in ascending order (FP64); ties go to the first
+    pair in (position of p, position of q) order, p before q in pin order.
+    Returns (p, q) per hyperedge (-1 for hyperedges with < 2 pins)."""
+    m = len(eptr) - 1
+    K = Q.shape[1]
+    pp = np.full(m, -1, dtype=np.int64)
+    qq = np.full(m, -1, dtype=np.int64)
+    for e in range(m):
+        a, b = int(eptr[e]), int(eptr[e + 1])
+        k = b - a
+        if k < 2:
+            continue
+        ia, ib = np.triu_indices(k, 1)   # pairs in (a, b) lexicographic order
+        X = Q[np.asarray(pins[a:b], dtype=np.int64), :].astype(np.float64)
+        d = np.zeros(ia.size)
+        for i in range(K):               # ascending columns, one rounding per step
+            diff = X[ia, i] - X[ib, i]
+            d = d + diff * diff
+        t = int(np.argmax(d))            # first maximum
+        pp[e] = pins[a + ia[t]]
+        qq[e] = pins[a + ib[t]]
+    return pp, qq
+
+
+def edge_resistance_embed(Q, eptr, pins, w, kept=None):
+    """Eq. ratios with p, q the embedding-farthest pair of ``embed_pairs``:
+    r_e(chi^(i)) = (chi_p^(i) - chi_q^(i))^2 / Q_H(chi^(i)) with Q_H of Eq.
+    non-linerQ (unchanged), R_e = max_i (Eq. R), argvec the lowest maximising
+    column, pmax / pmin the pair ordered by their values in that column (p
+    first when equal)."""
+    w = np.asarray(w, dtype=np.float64)
+    spread, _, _ = spreads(Q, eptr, pins)
+    QH = quadratic_form(spread, w)
+    use = QH > QH_TINY
+    if kept is not None:
+        use &= kept
+    pp, qq = embed_pairs(Q, eptr, pins)
+    m = len(eptr) - 1
+    R = np.zeros(m)
+    argvec = np.full(m, -1, dtype=np.int64)
+    pmax = np.full(m, -1, dtype=np.int64)
+    pmin = np.full(m, -1, dtype=np.int64)
+    for e in range(m):
+        if pp[e] < 0 or not use.any():
+            continue
+        best, bi = -1.0, -1
+        for i in np.flatnonzero(use):
+            diff = float(Q[pp[e], i]) - float(Q[qq[e], i])
+            r = (diff * diff) / QH[i]
+            if r > best:
+                best, bi = r, int(i)
+        R[e], argvec[e] = best, bi
+        hi = Q[pp[e], bi] >= Q[qq[e], bi]
+        pmax[e], pmin[e] = (pp[e], qq[e]) if hi else (qq[e], pp[e])
+    return dict(R=R, QH=QH, argvec=argvec, pmax=pmax, pmin=pmin, use=use, p=pp, q=qq)
+
+
 # ----------------------------------------------------------------------------
 # Algorithm 1 end to end
 
 
 def hyperedge_resistance(n, eptr, pins, w, x0_c, x0_b, k, clique="hyperedge",
-                         reduce="max"):
+                         reduce="max", ops="both"):
     """Algorithm 1: expansions, Krylov basis, Gram-Schmidt, ratios, max.
+    ``ops`` selects the Krylov pool (see krylov_basis); reduce="embed" scores
+    with the embedding-farthest pair (edge_resistance_embed).
     Returns the dict of ``edge_resistance`` plus V, Q, Rfac, kept."""
     eptr = np.asarray(eptr, dtype=np.int64)
     pins = np.asarray(pins, dtype=np.int64)
     w = np.asarray(w, dtype=np.float64)
-    V = krylov_basis(n, eptr, pins, w, x0_c, x0_b, k, clique)
+    V = krylov_basis(n, eptr, pins, w, x0_c, x0_b, k, clique, ops)
     Q, Rf, kept = gram_schmidt(V)
-    out = edge_resistance(Q, eptr, pins, w, reduce, kept)
+    if reduce == "embed":
+        out = edge_resistance_embed(Q, eptr, pins, w, kept)
+    else:
+        out = edge_resistance(Q, eptr, pins, w, reduce, kept)
     out.update(V=V, Q=Q, Rfac=Rf, kept=kept)
     return out
