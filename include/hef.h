@@ -64,6 +64,14 @@ typedef int32_t hef_status;
 #define HEF_REDUCE_MAX 0 /* Eq. R: R_e = max_i r_e(chi_i) */
 #define HEF_REDUCE_SUM 1 /* sum_i r_e(chi_i); with Laplacian eigenvectors of a
                             2-pin graph as the basis this is Eq. eff_resist0 */
+#define HEF_REDUCE_EMBED 2 /* Eq. R with p, q of Eq. ratios the pins farthest
+                              apart in the whole K-dimensional embedding (one
+                              pair per hyperedge; see hef_edge_resistance) */
+
+/* Krylov pools (hef_krylov_basis_ops). */
+#define HEF_OPS_CLIQUE 1 /* clique expansion only */
+#define HEF_OPS_STAR 2   /* star expansion only: the earlier HyperEF pool */
+#define HEF_OPS_BOTH 3   /* both (the mixed pool of Section III-A.3) */
 
 /* Clique-expansion pair weight (Section III-A.3). */
 #define HEF_CLIQUE_HYPEREDGE 0 /* w(e)/(|e|-1): clique degree = hypergraph degree */
@@ -211,6 +219,23 @@ hef_status hef_krylov_basis_tape(const hef_incidence* inc, int32_t k,
                                  void* tape, size_t tape_bytes,
                                  void* workspace, size_t workspace_bytes,
                                  void* stream);
+/* Krylov pool of one expansion, or both (ops = HEF_OPS_*).  HEF_OPS_STAR is
+ * the star-only pool of the earlier HyperEF method, which Section III-A.3
+ * contrasts with the mixed pool; HEF_OPS_BOTH is hef_krylov_basis.  With a
+ * single expansion V gets K = k S columns, column (j-1) S + s holding the
+ * j-th chain vector of start s, exactly the columns of that expansion in
+ * hef_krylov_basis (k S <= 256 for a single expansion; ldv >= k S).  The
+ * chains of both expansions are computed (the kernels fuse them) and the
+ * other expansion's columns are discarded.  Workspace:
+ * hef_krylov_ops_workspace_bytes. */
+size_t hef_krylov_ops_workspace_bytes(const hef_incidence* inc, int32_t k,
+                                      int32_t S, int32_t dtype, int32_t ops);
+hef_status hef_krylov_basis_ops(const hef_incidence* inc, int32_t k,
+                                int32_t S, int32_t dtype, int32_t ops,
+                                const double* x0_clique,
+                                const double* x0_star, void* V, int64_t ldv,
+                                void* workspace, size_t workspace_bytes,
+                                void* stream);
 /* ------------------------------------------------------------------------
  * Orthonormalisation (Algorithm 1 step 4): in place, V (n x K, ldv, dtype)
  * becomes Q with orthonormal, mean-free columns spanning the mean-free parts
@@ -239,6 +264,13 @@ hef_status hef_orthonormalize(int64_t n, int32_t K, int32_t dtype, void* V,
  * Q_H[i] = sum_e w_e spread_{e,i}^2 (FP64, fixed summation order);
  * r_{e,i} = spread_{e,i}^2 / Q_H[i] for columns with Q_H[i] > 1e-300;
  * R_e = max_i r_{e,i} (HEF_REDUCE_MAX) or sum_i r_{e,i} (HEF_REDUCE_SUM).
+ * HEF_REDUCE_EMBED (a reading of "p and q are the most distant nodes in the
+ * embedding space"): per hyperedge the pin pair (p, q) with the largest
+ * squared Euclidean distance over all K columns (summed in ascending column
+ * order in FP64; ties to the first pair in pin-position order), then
+ * r_{e,i} = (Q[p,i] - Q[q,i])^2 / Q_H[i] in FP64, R_e = max_i (lowest i on
+ * ties), pmax / pmin = p, q ordered by their values in column argvec (p
+ * first when equal); Q_H is unchanged.  Work grows as |e|^2 K per hyperedge.
  * Precision: spreads in the basis dtype; the arg-max column is chosen on the
  * ratios in that dtype; R_e is formed in FP64 as spread^2 times the FP64
  * 1/Q_H (within an ulp or two of the quotient).  The workspace call and the

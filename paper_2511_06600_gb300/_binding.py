@@ -17,7 +17,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhef.so")
 
 HEF_F64, HEF_F32 = 0, 1
-HEF_REDUCE_MAX, HEF_REDUCE_SUM = 0, 1
+HEF_REDUCE_MAX, HEF_REDUCE_SUM, HEF_REDUCE_EMBED = 0, 1, 2
+HEF_OPS_CLIQUE, HEF_OPS_STAR, HEF_OPS_BOTH = 1, 2, 3
 HEF_CLIQUE_HYPEREDGE, HEF_CLIQUE_PAPER = 0, 1
 HEF_ERR_INVALID_INPUT = -7
 
@@ -45,6 +46,9 @@ _SIGS = {
     "hef_free_incidence": (None, [c_p]),
     "hef_krylov_workspace_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32]),
     "hef_krylov_basis": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p, c_sz, c_p]),
+    "hef_krylov_ops_workspace_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32, c_i32]),
+    "hef_krylov_basis_ops": (c_i32, [c_p, c_i32, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p,
+                                     c_sz, c_p]),
     "hef_orthonormalize_workspace_bytes": (c_sz, [c_i64, c_i32, c_i32]),
     "hef_orthonormalize": (c_i32, [c_i64, c_i32, c_i32, c_p, c_i64, c_p, c_p, c_p, c_sz, c_p]),
     "hef_edge_resistance_workspace_bytes": (c_sz, [c_p, c_i32]),
@@ -217,15 +221,26 @@ def build_incidence(n, eptr, pins, w, clique_mode=HEF_CLIQUE_HYPEREDGE, stream=N
 
 
 def krylov_basis(inc, x0_clique, x0_star, k, dtype=torch.float64, V=None, workspace=None,
-                 stream=None):
+                 stream=None, ops=HEF_OPS_BOTH):
     """V (n x ldv, dtype): vertex rows of the k Krylov vectors of every chain
-    (hef_krylov_basis).  Returns V; its first K = 2kS columns are the basis."""
+    (hef_krylov_basis; hef_krylov_basis_ops for one expansion).  Returns V;
+    its first K = 2kS (one expansion: kS) columns are the basis."""
     L = lib()
     code = _dtype_code(dtype)
     S = int(x0_clique.shape[1])
-    K = 2 * k * S
+    K = (2 if ops == HEF_OPS_BOTH else 1) * k * S
     if V is None:
         V = torch.empty(inc.n, padded_ld(K, code), dtype=_DTYPES[code], device=inc.device)
+    if ops != HEF_OPS_BOTH:
+        ws = L.hef_krylov_ops_workspace_bytes(inc.handle, k, S, code, int(ops))
+        if ws == 0:
+            raise HefError("hef_krylov_ops_workspace_bytes", -6, "unsupported k/S/dtype/ops")
+        workspace = _workspace(ws, inc.device) if workspace is None else workspace
+        _check("hef_krylov_basis_ops",
+               L.hef_krylov_basis_ops(inc.handle, k, S, code, int(ops), _ptr(x0_clique),
+                                      _ptr(x0_star), _ptr(V), V.stride(0), _ptr(workspace),
+                                      workspace.numel(), _stream(stream)))
+        return V
     ws = L.hef_krylov_workspace_bytes(inc.handle, k, S, code)
     if ws == 0:
         raise HefError("hef_krylov_workspace_bytes", -6, "unsupported k/S/dtype")
@@ -378,13 +393,14 @@ def edge_resistance_noalloc(inc, Q, K, reduce=HEF_REDUCE_MAX, out=None, stream=N
 
 
 def hyperedge_resistance(n, eptr, pins, w, x0_clique, x0_star, k, dtype=torch.float64,
-                         clique_mode=HEF_CLIQUE_HYPEREDGE, reduce=HEF_REDUCE_MAX, check=True):
+                         clique_mode=HEF_CLIQUE_HYPEREDGE, reduce=HEF_REDUCE_MAX, check=True,
+                         ops=HEF_OPS_BOTH):
     """Algorithm 1 end to end on the GPU: incidence, Krylov basis, CholQR2,
     scores.  All inputs are CUDA tensors."""
     inc = build_incidence(n, eptr, pins, w, clique_mode)
     S = int(x0_clique.shape[1])
-    K = 2 * k * S
-    V = krylov_basis(inc, x0_clique, x0_star, k, dtype)
+    K = (2 if ops == HEF_OPS_BOTH else 1) * k * S
+    V = krylov_basis(inc, x0_clique, x0_star, k, dtype, ops=ops)
     Q, _, rank = orthonormalize(V, K)
     out = edge_resistance(inc, Q, K, reduce)
     if check:

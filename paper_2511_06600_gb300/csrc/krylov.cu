@@ -1174,6 +1174,24 @@ hef_status run_krylov(const hef_incidence* inc, int k, int S, const double* x0c,
   return HEF_OK;
 }
 
+// Columns of one expansion from the mixed basis W (n x ldw): V[v, (j-1) S +
+// s] = W[v, (j-1) 2S + op S + s].
+template <typename T>
+__global__ void k_select_op(long long n, int k, int S, int op, const T* __restrict__ W,
+                            long long ldw, T* __restrict__ V, long long ldv) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long KS = (long long)k * S;
+  if (t >= n * KS) return;
+  const long long v = t / KS;
+  const int c = (int)(t % KS), j = c / S, s = c % S;
+  V[v * ldv + c] = W[v * ldw + (long long)j * 2 * S + op * S + s];
+}
+
+inline long long mixed_ld(int k, int S, size_t esz) {
+  const long long K = 2ll * k * S, per = 16 / (long long)esz;
+  return (K + per - 1) / per * per;
+}
+
 hef_status check_krylov_args(const hef_incidence* inc, int k, int S, int dtype, const char* fn) {
   if (!inc) return set_error(HEF_ERR_INVALID_ARG, "%s: NULL incidence", fn);
   if (dtype != HEF_F64 && dtype != HEF_F32)
@@ -1264,4 +1282,58 @@ extern "C" hef_status hef_krylov_basis_tape(const hef_incidence* inc, int32_t k,
   if (dtype == HEF_F64)
     return run_krylov<double>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st, tape);
   return run_krylov<float>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st, tape);
+}
+
+extern "C" size_t hef_krylov_ops_workspace_bytes(const hef_incidence* inc, int32_t k, int32_t S,
+                                                 int32_t dtype, int32_t ops) {
+  const size_t base = hef_krylov_workspace_bytes(inc, k, S, dtype);
+  if (!base || (ops != HEF_OPS_CLIQUE && ops != HEF_OPS_STAR && ops != HEF_OPS_BOTH)) return 0;
+  if (ops == HEF_OPS_BOTH) return base;
+  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  return (base + 255) / 256 * 256 + (size_t)inc->n * mixed_ld(k, S, esz) * esz + 256;
+}
+
+extern "C" hef_status hef_krylov_basis_ops(const hef_incidence* inc, int32_t k, int32_t S,
+                                           int32_t dtype, int32_t ops, const double* x0_clique,
+                                           const double* x0_star, void* V, int64_t ldv,
+                                           void* workspace, size_t workspace_bytes,
+                                           void* stream) {
+  if (ops == HEF_OPS_BOTH)
+    return hef_krylov_basis(inc, k, S, dtype, x0_clique, x0_star, V, ldv, workspace,
+                            workspace_bytes, stream);
+  if (ops != HEF_OPS_CLIQUE && ops != HEF_OPS_STAR)
+    return set_error(HEF_ERR_INVALID_ARG, "hef_krylov_basis_ops: unknown ops %d", ops);
+  hef_status s = check_krylov_args(inc, k, S, dtype, "hef_krylov_basis_ops");
+  if (s) return s;
+  if (!x0_clique || !x0_star || !V) return set_error(HEF_ERR_INVALID_ARG, "hef_krylov_basis_ops: NULL array");
+  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  if (ldv < (long long)k * S || (ldv * esz) % 16 || (reinterpret_cast<uintptr_t>(V) & 15))
+    return set_error(HEF_ERR_INVALID_ARG,
+                     "hef_krylov_basis_ops: ldv must be >= k S with 16-byte aligned rows");
+  const size_t base = hef_krylov_workspace_bytes(inc, k, S, dtype);
+  const size_t need = hef_krylov_ops_workspace_bytes(inc, k, S, dtype, ops);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
+    return set_error(HEF_ERR_WORKSPACE, "hef_krylov_basis_ops: workspace needs %zu bytes", need);
+  // the kernels fuse both expansions: run them into a mixed basis in the
+  // workspace, then keep the chosen expansion's columns
+  char* W = static_cast<char*>(workspace) + (base + 255) / 256 * 256;
+  const long long ldw = mixed_ld(k, S, esz);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  s = dtype == HEF_F64 ? run_krylov<double>(inc, k, S, x0_clique, x0_star, W, ldw, workspace, st)
+                       : run_krylov<float>(inc, k, S, x0_clique, x0_star, W, ldw, workspace, st);
+  if (s) return s;
+  const long long total = inc->n * (long long)k * S;
+  if (total == 0) return HEF_OK;
+  const int op = ops == HEF_OPS_CLIQUE ? 0 : 1;
+  const int grid = (int)((total + kThreads - 1) / kThreads);
+  if (dtype == HEF_F64)
+    HEF_LAUNCH("k_select_op", st, k_select_op<double><<<grid, kThreads, 0, st>>>(
+                                      inc->n, k, S, op, reinterpret_cast<const double*>(W), ldw,
+                                      static_cast<double*>(V), ldv));
+  else
+    HEF_LAUNCH("k_select_op", st, k_select_op<float><<<grid, kThreads, 0, st>>>(
+                                      inc->n, k, S, op, reinterpret_cast<const float*>(W), ldw,
+                                      static_cast<float*>(V), ldv));
+  HEF_CHECK_LAUNCH();
+  return HEF_OK;
 }

@@ -837,6 +837,96 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
   return fn;
 }
 
+// Scores with the embedding-farthest pair (HEF_REDUCE_EMBED; reading A7's
+// alternative for "p and q are the most distant nodes in the embedding
+// space", Eq. ratios).  One warp per hyperedge: lanes take the pin pairs
+// (a < b, positions in the hyperedge) in row-major order, strided by 32;
+// each squared distance is summed over the columns in ascending order with
+// round-to-nearest FP64 operations; the largest wins, ties to the first
+// pair.  Then lanes take the columns: r_i = (Q[p,i] - Q[q,i])^2 / Q_H[i] over
+// the usable columns, the largest wins, ties to the lowest i.
+template <typename T>
+__global__ void __launch_bounds__(256) k_score_embed(IncView g, const T* __restrict__ Q,
+                                                     long long ldq, int K,
+                                                     const double* __restrict__ QH,
+                                                     double* __restrict__ R_out,
+                                                     int32_t* __restrict__ argvec,
+                                                     int32_t* __restrict__ pmax,
+                                                     int32_t* __restrict__ pmin) {
+  const int lane = threadIdx.x & 31;
+  const long long wg = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (wg >= g.m) return;
+  const int i = (int)wg;
+  if (g.status[0]) return;
+  const int e = g.perm[i];
+  const int a0 = g.ceptr[i], k = g.ceptr[i + 1] - a0;
+  double R = 0.0;
+  int av = -1, px = -1, pn = -1;
+  if (k >= 2) {
+    // pairs (a, b), a < b, in row-major order; this lane starts at pair `lane`
+    int a = 0, b = 1 + lane;
+    while (a < k - 1 && b >= k) {
+      const int over = b - k;
+      ++a;
+      b = a + 1 + over;
+    }
+    double bd = -1.0;
+    long long bt = -1;
+    int ba = 0, bb = 1;
+    while (a < k - 1) {
+      const long long ra = (long long)g.cpins[a0 + a] * ldq, rb = (long long)g.cpins[a0 + b] * ldq;
+      double d = 0.0;
+      for (int c = 0; c < K; ++c) {
+        const double diff = __dsub_rn((double)Q[ra + c], (double)Q[rb + c]);
+        d = __dadd_rn(d, __dmul_rn(diff, diff));
+      }
+      const long long t = (long long)a * k + b;  // increases with the pair order
+      if (d > bd) bd = d, bt = t, ba = a, bb = b;
+      b += 32;
+      while (a < k - 1 && b >= k) {
+        const int over = b - k;
+        ++a;
+        b = a + 1 + over;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+      const long long ot = __shfl_xor_sync(0xffffffffu, bt, o);
+      const int oa = __shfl_xor_sync(0xffffffffu, ba, o), ob = __shfl_xor_sync(0xffffffffu, bb, o);
+      if (od > bd || (od == bd && ot >= 0 && (bt < 0 || ot < bt))) bd = od, bt = ot, ba = oa, bb = ob;
+    }
+    const int p = g.cpins[a0 + ba], q = g.cpins[a0 + bb];
+    double br = -1.0;
+    int bi = -1;
+    for (int c = lane; c < K; c += 32) {
+      const double qh = QH[c];
+      if (!(qh > 1e-300)) continue;
+      const double diff = __dsub_rn((double)Q[(long long)p * ldq + c], (double)Q[(long long)q * ldq + c]);
+      const double r = __ddiv_rn(__dmul_rn(diff, diff), qh);
+      if (r > br) br = r, bi = c;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double orr = __shfl_xor_sync(0xffffffffu, br, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi >= 0 && (bi < 0 || orr > br || (orr == br && oi < bi))) br = orr, bi = oi;
+    }
+    if (bi >= 0) {
+      R = br, av = bi;
+      const bool hi = Q[(long long)p * ldq + bi] >= Q[(long long)q * ldq + bi];
+      px = hi ? p : q;
+      pn = hi ? q : p;
+    }
+  }
+  if (lane == 0) {
+    R_out[e] = R;
+    if (argvec) argvec[e] = av;
+    if (pmax) pmax[e] = px;
+    if (pmin) pmin[e] = pn;
+  }
+}
+
 // Tensor map of the row-major n x ldq matrix Q with a box of one row of bw
 // elements (for tile::gather4); false when it cannot be encoded.
 template <typename T>
@@ -920,6 +1010,13 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
     HEF_LAUNCH("k_score_pass1", st, k_score_pass1<T, NC><<<g1, kThreads, 0, st>>>(
                                         g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out,
                                         w.counter + kWorkSlot, spread, ldsp));
+  }
+  if (reduce == HEF_REDUCE_EMBED) {
+    const int ge = (int)(((long long)(inc->m > 0 ? inc->m : 1) * 32 + kThreads - 1) / kThreads);
+    HEF_LAUNCH("k_score_embed", st, k_score_embed<T><<<ge, kThreads, 0, st>>>(
+                                        g, Q, ldq, K, w.QH, R_out, argvec, pmax, pmin));
+    HEF_CHECK_LAUNCH();
+    return HEF_OK;
   }
   if (spread) {
     const int g3 = stride_grid(inc->m > 0 ? inc->m : 1, 8);
@@ -1035,7 +1132,7 @@ extern "C" hef_status hef_edge_resistance_noalloc(const hef_incidence* inc, cons
                      K, kNoallocScratchBytes);
   if (dtype != HEF_F64 && dtype != HEF_F32)
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: dtype must be HEF_F64 or HEF_F32");
-  if (reduce != HEF_REDUCE_MAX && reduce != HEF_REDUCE_SUM)
+  if (reduce != HEF_REDUCE_MAX && reduce != HEF_REDUCE_SUM && reduce != HEF_REDUCE_EMBED)
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: unknown reduce %d", reduce);
   if (!Q || ldq < K || (inc->m > 0 && !R_out))
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: Q or R_out NULL, or ldq < K");
@@ -1071,7 +1168,7 @@ extern "C" hef_status hef_edge_resistance(const hef_incidence* inc, const void* 
   if (K < 1 || K > 512) return set_error(HEF_ERR_UNSUPPORTED, "hef_edge_resistance: need 1 <= K <= 512");
   if (dtype != HEF_F64 && dtype != HEF_F32)
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance: dtype must be HEF_F64 or HEF_F32");
-  if (reduce != HEF_REDUCE_MAX && reduce != HEF_REDUCE_SUM)
+  if (reduce != HEF_REDUCE_MAX && reduce != HEF_REDUCE_SUM && reduce != HEF_REDUCE_EMBED)
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance: unknown reduce %d", reduce);
   if (!Q || ldq < K || (inc->m > 0 && !R_out))
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance: Q or R_out NULL, or ldq < K");
