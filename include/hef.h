@@ -320,6 +320,18 @@ hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q,
  * partial sums and weight-gradient sums; the Q_H adjoint is summed with FP64
  * atomics, so two runs agree to rounding, not bit for bit.
  * ---------------------------------------------------------------------- */
+/* Memory policy of the backward (no counterpart in the paper): whether the
+ * forward should keep the Krylov tape for the backward (*use_tape = 1:
+ * hef_krylov_basis_tape) or the backward should recompute the chains
+ * (*use_tape = 0: hef_krylov_basis, then the backward with tape = NULL,
+ * whose workspace holds the chains only while it runs).  The tape
+ * (*tape_bytes, nullable; hef_krylov_tape_bytes) is kept when it fits
+ * budget_bytes, or with budget_bytes = 0 half of the device memory that
+ * cudaMemGetInfo reports free on the current device.  Synchronous query of
+ * the device's memory; no device work. */
+hef_status hef_backward_plan(const hef_incidence* inc, int32_t k, int32_t S,
+                             int32_t dtype, uint64_t budget_bytes,
+                             int32_t* use_tape, uint64_t* tape_bytes);
 size_t hef_edge_resistance_backward_workspace_bytes(const hef_incidence* inc,
                                                     int32_t k, int32_t S,
                                                     int32_t dtype,

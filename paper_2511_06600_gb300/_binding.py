@@ -71,6 +71,8 @@ _SIGS = {
     "hef_coarsen_level": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_i32, c_i32, c_p,
                                   ctypes.c_double, ctypes.c_double, c_p, c_p, c_sz, c_p]),
     "hef_edge_resistance_backward_workspace_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32, c_i32]),
+    "hef_backward_plan": (c_i32, [c_p, c_i32, c_i32, c_i32, ctypes.c_uint64,
+                                  ctypes.POINTER(c_i32), ctypes.POINTER(ctypes.c_uint64)]),
     "hef_edge_resistance_backward": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_sz, c_p,
                                              c_i64, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_p,
                                              c_sz, c_p]),
@@ -298,21 +300,39 @@ def edge_resistance_backward(inc, k, x0_clique, x0_star, Q, R_fac, scores, dR, t
     return dw, dxc, dxb
 
 
+def backward_plan(inc, k, S, dtype, budget_bytes=0):
+    """hef_backward_plan: (keep the tape?, tape bytes) for a budget (0: half
+    of the free device memory)."""
+    use = c_i32(0)
+    tb = ctypes.c_uint64(0)
+    _check("hef_backward_plan",
+           lib().hef_backward_plan(inc.handle, int(k), int(S), _dtype_code(dtype),
+                                   int(budget_bytes), ctypes.byref(use), ctypes.byref(tb)))
+    return bool(use.value), int(tb.value)
+
+
 class HefResistance(torch.autograd.Function):
     """R = HyperEF resistance scores (Algorithm 1, HEF_REDUCE_MAX) as a
     differentiable function of the hyperedge weights w and the random starts
     (x0_clique, x0_star); the structure (n, eptr, pins) and k are fixed.
-    Forward keeps the Krylov tape; backward calls hef_edge_resistance_backward."""
+    Forward keeps the Krylov tape when hef_backward_plan says it fits
+    `tape_budget` bytes (0: half of the free device memory), else the
+    backward recomputes the chains; backward calls
+    hef_edge_resistance_backward."""
 
     @staticmethod
-    def forward(ctx, w, x0_clique, x0_star, n, eptr, pins, k, dtype, clique_mode):
+    def forward(ctx, w, x0_clique, x0_star, n, eptr, pins, k, dtype, clique_mode, tape_budget=0):
         w64 = w.detach().to(torch.float64).contiguous()
         xc = x0_clique.detach().to(torch.float64).contiguous()
         xb = x0_star.detach().to(torch.float64).contiguous()
         inc = build_incidence(n, eptr, pins, w64, clique_mode)
         S = int(xc.shape[1])
         K = 2 * k * S
-        V, tape = krylov_basis_tape(inc, xc, xb, k, dtype)
+        keep, _ = backward_plan(inc, k, S, dtype, tape_budget)
+        if keep:
+            V, tape = krylov_basis_tape(inc, xc, xb, k, dtype)
+        else:
+            V, tape = krylov_basis(inc, xc, xb, k, dtype), None
         Q, Rf, rank = orthonormalize(V, K, want_R=True)
         scores = edge_resistance(inc, Q, K)
         ctx.state = (inc, k, xc, xb, Q, Rf, scores, tape, w.dtype)
@@ -323,13 +343,14 @@ class HefResistance(torch.autograd.Function):
         inc, k, xc, xb, Q, Rf, scores, tape, wdt = ctx.state
         dw, dxc, dxb = edge_resistance_backward(inc, k, xc, xb, Q, Rf, scores, gR, tape=tape)
         ctx.state = None
-        return dw.to(wdt), dxc, dxb, None, None, None, None, None, None
+        return dw.to(wdt), dxc, dxb, None, None, None, None, None, None, None
 
 
 def resistance(w, x0_clique, x0_star, n, eptr, pins, k, dtype=torch.float64,
-               clique_mode=HEF_CLIQUE_HYPEREDGE):
+               clique_mode=HEF_CLIQUE_HYPEREDGE, tape_budget=0):
     """Differentiable scores: HefResistance.apply with keyword defaults."""
-    return HefResistance.apply(w, x0_clique, x0_star, n, eptr, pins, k, dtype, clique_mode)
+    return HefResistance.apply(w, x0_clique, x0_star, n, eptr, pins, k, dtype, clique_mode,
+                               tape_budget)
 
 
 def orthonormalize(V, K, want_R=False, workspace=None, stream=None):

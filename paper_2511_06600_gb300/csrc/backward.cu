@@ -839,3 +839,22 @@ extern "C" hef_status hef_edge_resistance_backward(
   return run_bwd<float>(inc, k, S, x0_clique, x0_star, tape, static_cast<const float*>(Q), ldq,
                         R_fac, QH, argvec, R, dR, dw, dx0_clique, dx0_star, w, st);
 }
+
+extern "C" hef_status hef_backward_plan(const hef_incidence* inc, int32_t k, int32_t S,
+                                        int32_t dtype, uint64_t budget_bytes, int32_t* use_tape,
+                                        uint64_t* tape_bytes) {
+  static const char* fn = "hef_backward_plan";
+  hef_status s = check_bwd_args(inc, k, S, dtype, fn);
+  if (s) return s;
+  if (!use_tape) return set_error(HEF_ERR_INVALID_ARG, "%s: NULL use_tape", fn);
+  const uint64_t tb = hef_krylov_tape_bytes(inc, k, S, dtype);
+  uint64_t budget = budget_bytes;
+  if (budget == 0) {
+    size_t free_b = 0, total_b = 0;
+    HEF_CHECK_CUDA(cudaMemGetInfo(&free_b, &total_b));
+    budget = free_b / 2;
+  }
+  *use_tape = tb <= budget ? 1 : 0;
+  if (tape_bytes) *tape_bytes = tb;
+  return HEF_OK;
+}
