@@ -626,27 +626,26 @@ def main():
            "normwise": float(np.abs(R32 - R64).max() / R64.max())}
     del pipe64
 
-    # ---- end to end through the public API: pinned host inputs in, scores out
+    # ---- end to end through the C ABI's host-array call (hef_resistance_host):
+    # pinned host inputs in, the whole path, the scores back in host memory
     e2e = None
     if not args.no_e2e:
         host = {key: t.cpu().pin_memory() for key, t in t_in.items()}
         R_host = torch.empty(H.m, dtype=torch.float64).pin_memory()
         h2d = sum(t.numel() * t.element_size() for t in host.values())
         d2h = R_host.numel() * R_host.element_size()
+        ws_host = hef.resistance_host_workspace(H.n, H.m, H.P, k, S, dtype, device=dev)
 
         def e2e_step():
-            # host -> device copies into the graph's input buffers, the path,
-            # and the scores back to pinned host memory
-            for key in host:
-                t_in[key].copy_(host[key], non_blocking=True)
-            o = step()
-            R_host.copy_(o["R"], non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+            hef.resistance_host(H.n, host["eptr"], host["pins"], host["w"], host["x0c"],
+                                host["x0b"], k, dtype, R_out=R_host, workspace=ws_host)
 
         ms_e, _, _, _ = timed(e2e_step, args.steps, 1)
         te = max_ranks(sum(ms_e) / len(ms_e))
+        assert np.allclose(R_host.numpy(), R32, rtol=1e-4, atol=0), "host-array call disagrees"
         e2e = {"value": P_all / (te * 1e-3), "unit": "pins/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "ms_per_step": te}
+               "d2h_bytes_per_step": d2h, "ms_per_step": te,
+               "call": "hef_resistance_host (host arrays in, R out, one synchronisation)"}
 
     # ---- differentiation form: forward + backward of a score-based loss
     bwd = None

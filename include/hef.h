@@ -294,6 +294,29 @@ hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q,
                                void* stream);
 
 /* ------------------------------------------------------------------------
+ * Algorithm 1 end to end from HOST arrays (a service of the library for C
+ * callers that hold the hypergraph in host memory): copies eptr[m+1],
+ * pins[P], w[m], x0_clique[n x S], x0_star[(n+m) x S] (host; pinned memory
+ * makes the copies asynchronous) into `workspace` (DEVICE, 256-byte aligned,
+ * hef_resistance_host_workspace_bytes), runs hef_build_incidence,
+ * hef_krylov_basis, hef_orthonormalize and hef_edge_resistance
+ * (HEF_REDUCE_MAX) on `stream`, copies R (m doubles) to the host array
+ * R_out and synchronises `stream`.  Returns the first error of those calls,
+ * HEF_ERR_INVALID_INPUT when the device-side validation failed, or
+ * HEF_ERR_TIMEOUT when a bounded device wait expired.
+ * ---------------------------------------------------------------------- */
+size_t hef_resistance_host_workspace_bytes(int64_t n, int64_t m, int64_t P,
+                                           int32_t k, int32_t S,
+                                           int32_t dtype);
+hef_status hef_resistance_host(int64_t n, int64_t m, int64_t P,
+                               const int64_t* eptr, const int32_t* pins,
+                               const double* w, const double* x0_clique,
+                               const double* x0_star, int32_t k, int32_t S,
+                               int32_t dtype, int32_t clique_mode,
+                               double* R_out, void* workspace,
+                               size_t workspace_bytes, void* stream);
+
+/* ------------------------------------------------------------------------
  * Backward of the whole path (Algorithm 1 steps 3-7).  The paper defines
  * only the forward; this is its derivative: given g = dL/dR (R as returned
  * by hef_edge_resistance with HEF_REDUCE_MAX), it writes

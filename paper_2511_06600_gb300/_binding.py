@@ -66,6 +66,9 @@ _SIGS = {
     "hef_set_krylov_persistent": (c_i32, [c_i32]),
     "hef_krylov_basis_tape": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p, c_sz,
                                       c_p, c_sz, c_p]),
+    "hef_resistance_host_workspace_bytes": (c_sz, [c_i64, c_i64, c_i64, c_i32, c_i32, c_i32]),
+    "hef_resistance_host": (c_i32, [c_i64, c_i64, c_i64, c_p, c_p, c_p, c_p, c_p, c_i32, c_i32,
+                                    c_i32, c_i32, c_p, c_p, c_sz, c_p]),
     "hef_level_workspace_bytes": (c_sz, [c_i64, c_i64, c_i32]),
     "hef_sort_resistance": (c_i32, [c_i64, c_p, c_p, c_p, c_sz, c_p]),
     "hef_coarsen_level": (c_i32, [c_p, c_p, c_p, c_p, c_p, c_p, c_p, c_i64, c_i32, c_i32, c_p,
@@ -733,3 +736,33 @@ def multilevel(n, eptr, pins, w, starts, k, levels, dtype=torch.float32, quantil
         eta = lo["eta_out"][:nf].clone()
         cur = (nf, lo["ceptr"][:mc + 1].clone(), lo["cpins"][:pc].clone(), lo["cw"][:mc].clone())
     return out, of_orig
+
+
+def resistance_host_workspace(n, m, P, k, S, dtype=torch.float32, device=None):
+    """Device workspace of hef_resistance_host."""
+    nb = lib().hef_resistance_host_workspace_bytes(int(n), int(m), int(P), int(k), int(S),
+                                                   _dtype_code(dtype))
+    if nb == 0:
+        raise HefError("hef_resistance_host_workspace_bytes", -1, "bad sizes")
+    return _workspace(nb, device or torch.device("cuda", torch.cuda.current_device()))
+
+
+def resistance_host(n, eptr, pins, w, x0_clique, x0_star, k, dtype=torch.float32, R_out=None,
+                    workspace=None, clique_mode=HEF_CLIQUE_HYPEREDGE, stream=None):
+    """hef_resistance_host: Algorithm 1 from HOST (CPU) tensors; returns R as
+    a host tensor (synchronises the stream)."""
+    m = int(eptr.numel() - 1)
+    P = int(pins.numel())
+    S = int(x0_clique.shape[1])
+    for t in (eptr, pins, w, x0_clique, x0_star):
+        assert not t.is_cuda and t.is_contiguous()
+    if R_out is None:
+        R_out = torch.empty(m, dtype=torch.float64)
+    if workspace is None:
+        workspace = resistance_host_workspace(n, m, P, k, S, dtype)
+    _check("hef_resistance_host",
+           lib().hef_resistance_host(int(n), m, P, _ptr(eptr), _ptr(pins), _ptr(w),
+                                     _ptr(x0_clique), _ptr(x0_star), int(k), S,
+                                     _dtype_code(dtype), int(clique_mode), _ptr(R_out),
+                                     _ptr(workspace), workspace.numel(), _stream(stream)))
+    return R_out

@@ -812,6 +812,7 @@ extern "C" hef_status hef_edge_resistance_backward(
     const double* R_fac, const double* QH, const int32_t* argvec, const double* R,
     const double* dR, double* dw, double* dx0_clique, double* dx0_star, void* workspace,
     size_t workspace_bytes, void* stream) {
+  HEF_NVTX("hef_edge_resistance_backward");
   static const char* fn = "hef_edge_resistance_backward";
   hef_status s = check_bwd_args(inc, k, S, dtype, fn);
   if (s) return s;

@@ -217,6 +217,7 @@ extern "C" hef_status hef_resistance_batched(const hef_batch_item* items, int32_
                                              int32_t S, int32_t dtype, int32_t clique_mode,
                                              const int32_t* schedule, int32_t nstreams,
                                              void* workspace, size_t workspace_bytes, void* stream) {
+  HEF_NVTX("hef_resistance_batched");
   static const char* fn = "hef_resistance_batched";
   if (hef_status s = check_items(items, G, k, S, dtype, fn)) return s;
   if (nstreams < 1 || nstreams > kMaxStreams)

@@ -8,6 +8,8 @@
 #include <mutex>
 #include <unordered_map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/hef.h"
 
 namespace hef {
@@ -51,6 +53,16 @@ struct LaunchTrace {
     ::hef::LaunchTrace hef_lt_((name), (st));     \
     __VA_ARGS__;                                  \
   } while (0)
+
+// NVTX range around a C-ABI call, named for the step of the method it runs
+// (header-only NVTX: a no-op unless a profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+#define HEF_NVTX(name) ::hef::NvtxRange hef_nvtx_(name)
 
 constexpr int kThreads = 256;
 

@@ -501,6 +501,7 @@ extern "C" size_t hef_level_workspace_bytes(int64_t n, int64_t m, int32_t K) {
 
 extern "C" hef_status hef_sort_resistance(int64_t m, const double* R, int32_t* order,
                                           void* workspace, size_t workspace_bytes, void* stream) {
+  HEF_NVTX("hef_sort_resistance (Algorithm 1 step 6)");
   if (m < 0 || m > 0x7fffffffll) return set_error(HEF_ERR_INVALID_ARG, "hef_sort_resistance: bad m");
   if (m > 0 && (!R || !order)) return set_error(HEF_ERR_INVALID_ARG, "hef_sort_resistance: NULL array");
   LevelWs w;
@@ -523,6 +524,7 @@ extern "C" hef_status hef_coarsen_level(const hef_incidence* inc, const int64_t*
                                         int32_t dtype, const double* QH, double delta,
                                         double quantile, const hef_level_out* out,
                                         void* workspace, size_t workspace_bytes, void* stream) {
+  HEF_NVTX("hef_coarsen_level (Algorithm 2 steps 4-10)");
   if (!inc || !out) return set_error(HEF_ERR_INVALID_ARG, "hef_coarsen_level: NULL incidence or out");
   const long long n = inc->n, m = inc->m;
   if (m > 0 && (!eptr || !pins || !w || !R))

@@ -1,0 +1,120 @@
+// Algorithm 1 end to end from host arrays (hef_resistance_host): the copies
+// in, the four calls of the path, the scores back, one synchronisation.  A C
+// caller that holds its hypergraph in host memory needs nothing else but a
+// device workspace.
+#include "internal.h"
+
+namespace hef {
+namespace {
+
+struct HostWs {
+  int64_t* eptr;
+  int32_t* pins;
+  double* w;
+  double* x0c;
+  double* x0b;
+  double* R;
+  int32_t* rank;
+  void* inc;
+  size_t inc_b;
+  void* V;
+  long long ldv;
+  void* kry;
+  size_t kry_b;
+  void* ortho;
+  size_t ortho_b;
+  void* score;
+  size_t score_b;
+};
+
+size_t carve_host(void* base, long long n, long long m, long long P, int k, int S, int dtype,
+                  HostWs* h) {
+  hef_incidence shape;  // the size queries read only n, m, P
+  shape.n = n, shape.m = m, shape.P = P;
+  const int K = 2 * k * S;
+  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  Carver c(base);
+  h->eptr = c.take<int64_t>(m + 1);
+  h->pins = c.take<int32_t>(P > 0 ? P : 1);
+  h->w = c.take<double>(m > 0 ? m : 1);
+  h->x0c = c.take<double>((size_t)(n > 0 ? n : 1) * S);
+  h->x0b = c.take<double>((size_t)(n + m > 0 ? n + m : 1) * S);
+  h->R = c.take<double>(m > 0 ? m : 1);
+  h->rank = c.take<int32_t>(1);
+  h->inc_b = hef_incidence_workspace_bytes(n, m, P);
+  h->inc = c.take<char>(h->inc_b);
+  h->ldv = (long long)(((size_t)K * esz + 15) / 16 * 16 / esz);
+  h->V = c.take<char>((size_t)(n > 0 ? n : 1) * h->ldv * esz);
+  h->kry_b = hef_krylov_workspace_bytes(&shape, k, S, dtype);
+  h->kry = c.take<char>(h->kry_b);
+  h->ortho_b = hef_orthonormalize_workspace_bytes(n > 0 ? n : 1, K, dtype);
+  h->ortho = c.take<char>(h->ortho_b);
+  h->score_b = hef_edge_resistance_workspace_bytes(&shape, K);
+  h->score = c.take<char>(h->score_b);
+  return c.bytes();
+}
+
+}  // namespace
+}  // namespace hef
+
+using namespace hef;
+
+extern "C" size_t hef_resistance_host_workspace_bytes(int64_t n, int64_t m, int64_t P, int32_t k,
+                                                      int32_t S, int32_t dtype) {
+  if (n < 1 || m < 0 || P < 0 || k < 1 || S < 1 || (dtype != HEF_F64 && dtype != HEF_F32))
+    return 0;
+  HostWs h;
+  return carve_host(nullptr, n, m, P, k, S, dtype, &h);
+}
+
+extern "C" hef_status hef_resistance_host(int64_t n, int64_t m, int64_t P, const int64_t* eptr,
+                                          const int32_t* pins, const double* w,
+                                          const double* x0_clique, const double* x0_star,
+                                          int32_t k, int32_t S, int32_t dtype,
+                                          int32_t clique_mode, double* R_out, void* workspace,
+                                          size_t workspace_bytes, void* stream) {
+  HEF_NVTX("hef_resistance_host (Algorithm 1 from host arrays)");
+  static const char* fn = "hef_resistance_host";
+  const size_t need = hef_resistance_host_workspace_bytes(n, m, P, k, S, dtype);
+  if (!need) return set_error(HEF_ERR_INVALID_ARG, "%s: bad sizes, k, S or dtype", fn);
+  if (!eptr || (P > 0 && !pins) || (m > 0 && (!w || !R_out)) || !x0_clique || !x0_star)
+    return set_error(HEF_ERR_INVALID_ARG, "%s: NULL host array", fn);
+  if (!workspace || (reinterpret_cast<uintptr_t>(workspace) & 255) || workspace_bytes < need)
+    return set_error(HEF_ERR_WORKSPACE, "%s: workspace needs %zu bytes (256-aligned)", fn, need);
+  HostWs h;
+  carve_host(workspace, n, m, P, k, S, dtype, &h);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int K = 2 * k * S;
+  HEF_CHECK_CUDA(cudaMemcpyAsync(h.eptr, eptr, (m + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st));
+  if (P > 0)
+    HEF_CHECK_CUDA(cudaMemcpyAsync(h.pins, pins, P * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+  if (m > 0) HEF_CHECK_CUDA(cudaMemcpyAsync(h.w, w, m * sizeof(double), cudaMemcpyHostToDevice, st));
+  HEF_CHECK_CUDA(cudaMemcpyAsync(h.x0c, x0_clique, (size_t)n * S * sizeof(double),
+                                 cudaMemcpyHostToDevice, st));
+  HEF_CHECK_CUDA(cudaMemcpyAsync(h.x0b, x0_star, (size_t)(n + m) * S * sizeof(double),
+                                 cudaMemcpyHostToDevice, st));
+  hef_incidence* inc = nullptr;
+  hef_status s = hef_build_incidence(n, m, P, h.eptr, h.pins, h.w, clique_mode, h.inc, h.inc_b,
+                                     stream, &inc);
+  if (s) return s;
+  s = hef_krylov_basis(inc, k, S, dtype, h.x0c, h.x0b, h.V, h.ldv, h.kry, h.kry_b, stream);
+  if (!s)
+    s = hef_orthonormalize(n, K, dtype, h.V, h.ldv, nullptr, h.rank, h.ortho, h.ortho_b, stream);
+  if (!s)
+    s = hef_edge_resistance(inc, h.V, h.ldv, K, dtype, HEF_REDUCE_MAX, h.R, nullptr, nullptr,
+                            nullptr, nullptr, h.score, h.score_b, stream);
+  if (!s && m > 0) {
+    const cudaError_t e = cudaMemcpyAsync(R_out, h.R, m * sizeof(double), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = set_error(HEF_ERR_CUDA, "%s: copy of R failed: %s", fn, cudaGetErrorString(e));
+  }
+  int32_t rank = 0;
+  if (!s) {
+    const cudaError_t e = cudaMemcpyAsync(&rank, h.rank, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) s = set_error(HEF_ERR_CUDA, "%s: copy of the rank failed: %s", fn, cudaGetErrorString(e));
+  }
+  // synchronises the stream; device-side validation and waits are reported here
+  if (!s) s = hef_incidence_check(inc, stream, nullptr, nullptr);
+  if (!s && rank < 0) s = set_error(HEF_ERR_TIMEOUT, "%s: a tensor-core wait timed out", fn);
+  hef_free_incidence(inc);
+  return s;
+}

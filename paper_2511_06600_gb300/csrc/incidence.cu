@@ -604,6 +604,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
                                           int32_t clique_mode, void* workspace,
                                           size_t workspace_bytes, void* stream,
                                           hef_incidence** out) {
+  HEF_NVTX("hef_build_incidence (Algorithm 1 steps 1-2)");
   if (!out) return set_error(HEF_ERR_INVALID_ARG, "hef_build_incidence: out is NULL");
   *out = nullptr;
   if (n < 1 || m < 0 || P < 0)

@@ -1227,6 +1227,7 @@ extern "C" hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int3
                                        int32_t dtype, const double* x0_clique,
                                        const double* x0_star, void* V, int64_t ldv,
                                        void* workspace, size_t workspace_bytes, void* stream) {
+  HEF_NVTX("hef_krylov_basis (Algorithm 1 step 3)");
   hef_status s = check_krylov_args(inc, k, S, dtype, "hef_krylov_basis");
   if (s) return s;
   const long long K = 2ll * k * S;
@@ -1263,6 +1264,7 @@ extern "C" hef_status hef_krylov_basis_tape(const hef_incidence* inc, int32_t k,
                                             const double* x0_star, void* V, int64_t ldv,
                                             void* tape, size_t tape_bytes, void* workspace,
                                             size_t workspace_bytes, void* stream) {
+  HEF_NVTX("hef_krylov_basis_tape (Algorithm 1 step 3, taped)");
   hef_status s = check_krylov_args(inc, k, S, dtype, "hef_krylov_basis_tape");
   if (s) return s;
   const long long K = 2ll * k * S;
@@ -1298,6 +1300,7 @@ extern "C" hef_status hef_krylov_basis_ops(const hef_incidence* inc, int32_t k, 
                                            const double* x0_star, void* V, int64_t ldv,
                                            void* workspace, size_t workspace_bytes,
                                            void* stream) {
+  HEF_NVTX("hef_krylov_basis_ops (Algorithm 1 step 3, one expansion)");
   if (ops == HEF_OPS_BOTH)
     return hef_krylov_basis(inc, k, S, dtype, x0_clique, x0_star, V, ldv, workspace,
                             workspace_bytes, stream);

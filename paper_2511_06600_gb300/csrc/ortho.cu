@@ -713,6 +713,7 @@ extern "C" size_t hef_orthonormalize_workspace_bytes(int64_t n, int32_t K, int32
 extern "C" hef_status hef_orthonormalize(int64_t n, int32_t K, int32_t dtype, void* V, int64_t ldv,
                                          double* R_out, int32_t* rank_out, void* workspace,
                                          size_t workspace_bytes, void* stream) {
+  HEF_NVTX("hef_orthonormalize (Algorithm 1 step 4)");
   if (n < 1 || K < 1) return set_error(HEF_ERR_INVALID_ARG, "hef_orthonormalize: need n, K >= 1");
   if (K > 512) return set_error(HEF_ERR_UNSUPPORTED, "hef_orthonormalize: K must be <= 512");
   if (n >= (1ll << 31) - 1)

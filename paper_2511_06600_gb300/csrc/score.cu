@@ -1164,6 +1164,7 @@ extern "C" hef_status hef_edge_resistance(const hef_incidence* inc, const void* 
                                           double* QH_out, int32_t* argvec, int32_t* pmax,
                                           int32_t* pmin, void* workspace, size_t workspace_bytes,
                                           void* stream) {
+  HEF_NVTX("hef_edge_resistance (Algorithm 1 steps 5, 7)");
   if (!inc) return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance: NULL incidence");
   if (K < 1 || K > 512) return set_error(HEF_ERR_UNSUPPORTED, "hef_edge_resistance: need 1 <= K <= 512");
   if (dtype != HEF_F64 && dtype != HEF_F32)
