@@ -29,7 +29,8 @@
  *  - Matrices are row-major: row r of an n x K matrix starts at r * ld
  *    elements; ld >= K.  Rows must start 16-byte aligned (ld * element size
  *    a multiple of 16 bytes).
- *  - Element types: HEF_F64 (double), HEF_F32 (float).
+ *  - Element types: HEF_F64 (double), HEF_F32 (float), HEF_BF16 (the basis
+ *    V / Q stored as bfloat16, arithmetic in FP32 / FP64 as stated per call).
  *  - Return value: HEF_OK or a negative hef_status; hef_last_error() gives a
  *    thread-local message for the last failing call.  Errors found by device
  *    code (malformed incidence, non-positive weights) are recorded in the
@@ -59,6 +60,8 @@ typedef int32_t hef_status;
 
 #define HEF_F64 0
 #define HEF_F32 1
+#define HEF_BF16 2 /* basis stored in BF16 (Krylov chains, Gram and spreads in
+                      FP32; Cholesky and Q_H in FP64); K <= 511; no backward */
 
 /* Reductions over basis vectors in hef_edge_resistance. */
 #define HEF_REDUCE_MAX 0 /* Eq. R: R_e = max_i r_e(chi_i) */

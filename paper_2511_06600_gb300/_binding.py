@@ -16,14 +16,15 @@ import torch
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libhef.so")
 
-HEF_F64, HEF_F32 = 0, 1
+HEF_F64, HEF_F32, HEF_BF16 = 0, 1, 2
 HEF_REDUCE_MAX, HEF_REDUCE_SUM, HEF_REDUCE_EMBED = 0, 1, 2
 HEF_OPS_CLIQUE, HEF_OPS_STAR, HEF_OPS_BOTH = 1, 2, 3
 HEF_CLIQUE_HYPEREDGE, HEF_CLIQUE_PAPER = 0, 1
 HEF_ERR_INVALID_INPUT = -7
 
-_DTYPES = {HEF_F64: torch.float64, HEF_F32: torch.float32}
-_CODES = {torch.float64: HEF_F64, torch.float32: HEF_F32, "f64": HEF_F64, "f32": HEF_F32}
+_DTYPES = {HEF_F64: torch.float64, HEF_F32: torch.float32, HEF_BF16: torch.bfloat16}
+_CODES = {torch.float64: HEF_F64, torch.float32: HEF_F32, torch.bfloat16: HEF_BF16,
+          "f64": HEF_F64, "f32": HEF_F32, "bf16": HEF_BF16}
 
 c_i32, c_i64, c_sz, c_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t, ctypes.c_void_p
 

@@ -22,8 +22,11 @@
 // only, FP64 sums in the stated orders with explicit round-to-nearest
 // operations (no contraction into fused multiply-adds), so the results equal
 // a sequential CPU statement of the same rules bit for bit.
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -231,7 +234,8 @@ __global__ void k_clusters(int n, const int32_t* __restrict__ owner, const int32
 
 template <typename T>
 __device__ __forceinline__ double qval(const T* Q, long long ldq, long long row, int i) {
-  return (double)Q[row * ldq + i];
+  if constexpr (std::is_same<T, __nv_bfloat16>::value) return (double)__bfloat162float(Q[row * ldq + i]);
+  else return (double)Q[row * ldq + i];
 }
 
 // Centroid rows of the contracted supernodes: one warp per supernode, lanes
@@ -536,8 +540,9 @@ extern "C" hef_status hef_coarsen_level(const hef_incidence* inc, const int64_t*
   if (Q) {
     if (K < 1 || K > 512 || ldq < K || !QH)
       return set_error(HEF_ERR_INVALID_ARG, "hef_coarsen_level: need 1 <= K <= 512, ldq >= K and QH");
-    if (dtype != HEF_F64 && dtype != HEF_F32)
-      return set_error(HEF_ERR_INVALID_ARG, "hef_coarsen_level: dtype must be HEF_F64 or HEF_F32");
+    if (dtype != HEF_F64 && dtype != HEF_F32 && dtype != HEF_BF16)
+      return set_error(HEF_ERR_INVALID_ARG,
+                       "hef_coarsen_level: dtype must be HEF_F64, HEF_F32 or HEF_BF16");
   }
   if (!(delta >= 0.0) && !(quantile >= 0.0 && quantile <= 1.0))
     return set_error(HEF_ERR_INVALID_ARG,
@@ -619,25 +624,21 @@ extern "C" hef_status hef_coarsen_level(const hef_incidence* inc, const int64_t*
     HEF_PASS(exclusive_scan(ws.cflag, ws.cflag, n, ws.bsum, ws.counter, st));
     const IncView g = view(inc);
     const int wgrid = (int)((n * 32 + kThreads - 1) / kThreads);
-    if (dtype == HEF_F64) {
-      HEF_LAUNCH("k_centroids", st, k_centroids<double><<<wgrid, kThreads, 0, st>>>(
+    auto run = [&](auto tag) -> hef_status {
+      using QT = decltype(tag);
+      HEF_LAUNCH("k_centroids", st, k_centroids<QT><<<wgrid, kThreads, 0, st>>>(
                                         nn, ws.formed_by, ws.cflag, eptr, pins,
-                                        static_cast<const double*>(Q), ldq, K, ws.mu));
-      HEF_LAUNCH("k_seeds", st, k_seeds<double><<<wgrid, kThreads, 0, st>>>(
+                                        static_cast<const QT*>(Q), ldq, K, ws.mu));
+      HEF_LAUNCH("k_seeds", st, k_seeds<QT><<<wgrid, kThreads, 0, st>>>(
                                     nn, out->owner, g.vptr, g.vedge, g.perm, eptr, pins,
                                     out->cluster, ws.formed_by, ws.cflag, ws.mu,
-                                    static_cast<const double*>(Q), ldq, K, QH, out->target,
+                                    static_cast<const QT*>(Q), ldq, K, QH, out->target,
                                     out->dist));
-    } else {
-      HEF_LAUNCH("k_centroids", st, k_centroids<float><<<wgrid, kThreads, 0, st>>>(
-                                        nn, ws.formed_by, ws.cflag, eptr, pins,
-                                        static_cast<const float*>(Q), ldq, K, ws.mu));
-      HEF_LAUNCH("k_seeds", st, k_seeds<float><<<wgrid, kThreads, 0, st>>>(
-                                    nn, out->owner, g.vptr, g.vedge, g.perm, eptr, pins,
-                                    out->cluster, ws.formed_by, ws.cflag, ws.mu,
-                                    static_cast<const float*>(Q), ldq, K, QH, out->target,
-                                    out->dist));
-    }
+      return HEF_OK;
+    };
+    if (dtype == HEF_F64) HEF_PASS(run(double{}));
+    else if (dtype == HEF_BF16) HEF_PASS(run(__nv_bfloat16{}));
+    else HEF_PASS(run(float{}));
     HEF_CHECK_LAUNCH();
     HEF_LAUNCH("k_merge_keys", st, k_merge_keys<<<grid_of(n), kThreads, 0, st>>>(
                                        nn, out->target, ws.keys, ws.vals));

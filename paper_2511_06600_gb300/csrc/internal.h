@@ -197,12 +197,12 @@ void krylov_force_oversized(bool on);
 // (ortho_tc.cu): G = V^T V (K x K), c = V^T 1; part is per-CTA scratch.
 int gram_tc_supported(int K);
 size_t gram_tc_part_doubles(long long n, int K);
-hef_status gram_tc(const float* V, long long ldv, long long n, int K, double* part, double* G,
-                   double* c, int* err, cudaStream_t st);
+hef_status gram_tc(const void* V, bool bf16, long long ldv, long long n, int K, double* part,
+                   double* G, double* c, int* err, cudaStream_t st);
 // Tensor-core in-place apply Q = (V - 1 mu^T) Rinv of an FP32 basis, K <= 256.
 int apply_tc_supported(int K);
 size_t apply_tc_scratch_floats(int K);
-hef_status apply_tc(float* V, long long ldv, long long n, int K, const float* Rinv, int Kp,
-                    const float* mu, float* scratch, int* err, cudaStream_t st);
+hef_status apply_tc(void* V, bool bf16, long long ldv, long long n, int K, const float* Rinv,
+                    int Kp, const float* mu, float* scratch, int* err, cudaStream_t st);
 
 }  // namespace hef

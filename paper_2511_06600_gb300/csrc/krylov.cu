@@ -29,7 +29,10 @@
 // step) and reduces the Lanczos dots, and an update pass (thread per vertex
 // record or star hyperedge row) forming x_j and its D-norm.  Every reduction
 // is a per-CTA partial followed by a two-level fixed-order sum (grid_reduce).
+#include <cuda_bf16.h>
+
 #include <algorithm>
+#include <type_traits>
 
 #include "internal.h"
 
@@ -173,6 +176,30 @@ __device__ __forceinline__ void strow_cs(T* __restrict__ p, const T (&v)[N]) {
   } else {
 #pragma unroll
     for (int s = 0; s < N; ++s) __stcs(p + s, v[s]);
+  }
+}
+
+// Archive store of a record into a basis of storage type TV (the working
+// type, or BF16 rounded to nearest).
+template <typename T, int N, typename TV>
+__device__ __forceinline__ void store_basis(TV* __restrict__ p, const T (&v)[N]) {
+  if constexpr (std::is_same<T, TV>::value) {
+    strow_cs<T, N>(p, v);
+  } else if constexpr (N % 8 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 8; ++i) {
+      __nv_bfloat162 h[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn((float)v[8 * i + 2 * q], (float)v[8 * i + 2 * q + 1]);
+      __stcs(reinterpret_cast<uint4*>(p) + i, *reinterpret_cast<const uint4*>(h));
+    }
+  } else if constexpr (N % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < N / 2; ++i)
+      reinterpret_cast<__nv_bfloat162*>(p)[i] = __floats2bfloat162_rn((float)v[2 * i], (float)v[2 * i + 1]);
+  } else {
+#pragma unroll
+    for (int i = 0; i < N; ++i) p[i] = __float2bfloat16_rn((float)v[i]);
   }
 }
 
@@ -469,10 +496,10 @@ __device__ __forceinline__ void edge_final(const KView<T>& kv, int S, const doub
 // of the Lanczos coefficients, added to acc.
 // ofs(v) gives the offset of vertex v's incidences and edge(t) the hyperedge
 // of incidence t; CG as in edge_item.
-template <typename T, int S, bool CG, typename Ofs, typename Edge>
+template <typename T, int S, bool CG, typename TV, typename Ofs, typename Edge>
 __device__ __forceinline__ void node_item(const IncView& g, const ScalView<T>& sv,
                                           const KView<T>& kv, const T* nuT, int j, int v,
-                                          T (&acc)[6][S], T* __restrict__ V, long long ldv,
+                                          T (&acc)[6][S], TV* __restrict__ V, long long ldv,
                                           Ofs ofs, Edge edge) {
   const T* __restrict__ curv = pick2(kv.Bv, (j - 1) & 1);
   const T* __restrict__ prvv = j >= 3 ? pick2(kv.Bv, j & 1) : nullptr;
@@ -515,7 +542,7 @@ __device__ __forceinline__ void node_item(const IncView& g, const ScalView<T>& s
     }
     strow<T, 2 * S>(kv.Yv + (long long)v * 2 * S, y);
     if (j >= 2)  // x_{j-1} is basis vector j-1 -> column block j-2
-      strow_cs<T, 2 * S>(V + (long long)v * ldv + (long long)(j - 2) * 2 * S, xo);
+      store_basis<T, 2 * S, TV>(V + (long long)v * ldv + (long long)(j - 2) * 2 * S, xo);
   }
 }
 
@@ -663,9 +690,9 @@ __device__ __forceinline__ void update_final(const KView<T>& kv, int S, int j, c
 }
 
 // Archive of the last chain vector x_k of vertex v into V.
-template <typename T, int S, bool CG = false>
+template <typename T, int S, bool CG, typename TV>
 __device__ __forceinline__ void archive_item(const IncView& g, const KView<T>& kv, const T* nuT,
-                                             int k, int v, T* __restrict__ V, long long ldv) {
+                                             int k, int v, TV* __restrict__ V, long long ldv) {
   if (v >= g.n) return;
   T x[2 * S];
   ldrow<T, 2 * S, CG>(pick2(kv.Bv, k & 1) + (long long)v * 2 * S, x);
@@ -674,7 +701,7 @@ __device__ __forceinline__ void archive_item(const IncView& g, const KView<T>& k
     x[s] *= nuT[(size_t)k * 2 * S + s];
     x[S + s] *= nuT[(size_t)k * 2 * S + S + s];
   }
-  strow_cs<T, 2 * S>(V + (long long)v * ldv + (long long)(k - 1) * 2 * S, x);
+  store_basis<T, 2 * S, TV>(V + (long long)v * ldv + (long long)(k - 1) * 2 * S, x);
 }
 
 template <int NQ, int S, typename T>
@@ -704,16 +731,16 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(6))
 
 // Vertex pass of step j (thread per vertex); the final CTA forms the
 // Lanczos coefficients.
-template <typename T, int S>
+template <typename T, int S, typename TV>
 __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
-    k_node_pass(IncView g, ScalView<T> sv, KView<T> kv, int j, T* __restrict__ V, long long ldv) {
+    k_node_pass(IncView g, ScalView<T> sv, KView<T> kv, int j, TV* __restrict__ V, long long ldv) {
   pdl_wait();
   pdl_trigger();
   if (g.status[0]) return;
   T acc[6][S];
   zero_acc(acc);
-  node_item<T, S, false>(g, sv, kv, kv.nuT, j, blockIdx.x * blockDim.x + threadIdx.x, acc, V,
-                         ldv,
+  node_item<T, S, false, TV>(g, sv, kv, kv.nuT, j, blockIdx.x * blockDim.x + threadIdx.x, acc, V,
+                             ldv,
                          [&](int v) { return g.vptr[v]; },
                          [&](int t) { return __ldg(g.vedge + t); });
   block_partials_qs<6, S, T>(acc, kv.red.part);
@@ -739,12 +766,12 @@ __global__ void __launch_bounds__(kThreads, kMinBlocks<T, S>(4))
 }
 
 // Archive of the last chain vectors x_k into V (thread per vertex).
-template <typename T, int S>
+template <typename T, int S, typename TV>
 __global__ void __launch_bounds__(kThreads) k_archive_last(IncView g, KView<T> kv, int k,
-                                                           T* __restrict__ V, long long ldv) {
+                                                           TV* __restrict__ V, long long ldv) {
   pdl_wait();
   if (g.status[0]) return;
-  archive_item<T, S>(g, kv, kv.nuT, k, blockIdx.x * blockDim.x + threadIdx.x, V, ldv);
+  archive_item<T, S, false, TV>(g, kv, kv.nuT, k, blockIdx.x * blockDim.x + threadIdx.x, V, ldv);
 }
 
 // ---------------------------------------------------------------- persistent form
@@ -911,9 +938,9 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
   return true;
 }
 
-template <typename T, int S>
+template <typename T, int S, typename TV>
 __global__ void __launch_bounds__(pers_threads<T, S>(), 1)
-    k_krylov_steps(IncView g, ScalView<T> sv, KView<T> kv, int k, T* __restrict__ V,
+    k_krylov_steps(IncView g, ScalView<T> sv, KView<T> kv, int k, TV* __restrict__ V,
                    long long ldv, double* part, unsigned int* cnt, unsigned int* status) {
   constexpr int NT = pers_threads<T, S>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -982,7 +1009,7 @@ __global__ void __launch_bounds__(pers_threads<T, S>(), 1)
       zero_acc(acc);
       for (int base = v0 + wid * 32; base < v1; base += NT) {
         const int v = base + lane;
-        node_item<T, S, true>(g, sv, kv, s_nuT, j, v < v1 ? v : g.n, acc, V, ldv, vofs, vedg);
+        node_item<T, S, true, TV>(g, sv, kv, s_nuT, j, v < v1 ? v : g.n, acc, V, ldv, vofs, vedg);
       }
       if (!pbarrier<6, S, NT>(acc, part, pub, ph++, cnt, status, s_red)) return;
       for (int c = tid; c < 2 * S; c += NT) {
@@ -1031,7 +1058,7 @@ __global__ void __launch_bounds__(pers_threads<T, S>(), 1)
       __syncthreads();
     }
   }
-  for (int v = v0 + tid; v < v1; v += NT) archive_item<T, S, true>(g, kv, s_nuT, k, v, V, ldv);
+  for (int v = v0 + tid; v < v1; v += NT) archive_item<T, S, true, TV>(g, kv, s_nuT, k, v, V, ldv);
 }
 
 inline int blocks_for(long long rows) { return (int)((rows + kThreads - 1) / kThreads); }
@@ -1072,9 +1099,9 @@ thread_local bool t_persistent = true;
 // resident grid, so that its first barrier cannot complete.
 thread_local bool t_force_oversized = false;
 
-template <typename T, int S>
+template <typename T, int S, typename TV>
 hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, const double* x0b,
-                        T* V, long long ldv, KView<T>& kv, bool persistent, cudaStream_t st) {
+                        TV* V, long long ldv, KView<T>& kv, bool persistent, cudaStream_t st) {
   IncView g = view(inc);
   const ScalView<T> sv = scal_view<T>(inc);
   const long long n = inc->n, m = inc->m;
@@ -1097,10 +1124,10 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
     constexpr int NT = pers_threads<T, S>();
     const size_t smem = pers_smem<T>(k, S);
     constexpr size_t kSmemLimit = 227 * 1024;  // per-CTA opt-in limit of the sm_100 family
-    if (smem <= kSmemLimit) HEF_ENSURE_SMEM((k_krylov_steps<T, S>), smem);
+    if (smem <= kSmemLimit) HEF_ENSURE_SMEM((k_krylov_steps<T, S, TV>), smem);
     int occ = 0;
     if (smem <= kSmemLimit &&
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_krylov_steps<T, S>, NT, smem) ==
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_krylov_steps<T, S, TV>, NT, smem) ==
             cudaSuccess &&
         occ >= 1) {
       HEF_CHECK_CUDA(cudaMemsetAsync(kv.pcount, 0, 2 * sizeof(unsigned int), st));
@@ -1110,12 +1137,12 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
       cudaError_t e = cudaSuccess;
       if (t_force_oversized) {
         HEF_LAUNCH("k_krylov_steps", st,
-                   k_krylov_steps<T, S><<<grid, NT, smem, st>>>(g, sv, kv, k, V, ldv, kv.ppart,
+                   k_krylov_steps<T, S, TV><<<grid, NT, smem, st>>>(g, sv, kv, k, V, ldv, kv.ppart,
                                                                kv.pcount, inc->status));
         e = cudaGetLastError();
       } else {
         HEF_LAUNCH("k_krylov_steps", st,
-                   e = launch_cooperative_smem(k_krylov_steps<T, S>, grid, NT, smem, st, g, sv,
+                   e = launch_cooperative_smem(k_krylov_steps<T, S, TV>, grid, NT, smem, st, g, sv,
                                                kv, k, V, ldv, kv.ppart, kv.pcount, inc->status));
       }
       if (e == cudaSuccess) return HEF_OK;
@@ -1130,20 +1157,20 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
     HEF_LAUNCH("k_edge_pass", st,
                HEF_CHECK_CUDA(launch_dependent(k_edge_pass<T, S>, grid_e, kThreads, st, g, sv, kv, j)));
     HEF_LAUNCH("k_node_pass", st,
-               HEF_CHECK_CUDA(launch_dependent(k_node_pass<T, S>, grid_n, kThreads, st, g, sv, kv,
+               HEF_CHECK_CUDA(launch_dependent(k_node_pass<T, S, TV>, grid_n, kThreads, st, g, sv, kv,
                                                j, V, ldv)));
     HEF_LAUNCH("k_update", st,
                HEF_CHECK_CUDA(launch_dependent(k_update<T, S>, grid_upd, kThreads, st, g, sv, kv, j)));
     HEF_CHECK_LAUNCH();
   }
   HEF_LAUNCH("k_archive_last", st,
-             HEF_CHECK_CUDA(launch_dependent(k_archive_last<T, S>, grid_n, kThreads, st, g, kv, k,
+             HEF_CHECK_CUDA(launch_dependent(k_archive_last<T, S, TV>, grid_n, kThreads, st, g, kv, k,
                                              V, ldv)));
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
 
-template <typename T>
+template <typename T, typename TV = T>
 hef_status run_krylov(const hef_incidence* inc, int k, int S, const double* x0c, const double* x0b,
                       void* Vv, long long ldv, void* ws, cudaStream_t st, void* tape = nullptr) {
   KView<T> kv;
@@ -1156,14 +1183,14 @@ hef_status run_krylov(const hef_incidence* inc, int k, int S, const double* x0c,
   const int ngr = red_groups(blocks_for(2 * inc->n + inc->m));
   HEF_CHECK_CUDA(cudaMemsetAsync(kv.red.gcnt, 0, (ngr + 1) * sizeof(unsigned int), st));
   HEF_CHECK_CUDA(cudaMemsetAsync(kv.red.tcnt, 0, sizeof(unsigned int), st));
-  T* V = static_cast<T*>(Vv);
+  TV* V = static_cast<TV*>(Vv);
   hef_status s;
   switch (S) {
-    case 1: s = run_krylov_s<T, 1>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
-    case 2: s = run_krylov_s<T, 2>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
-    case 4: s = run_krylov_s<T, 4>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
-    case 8: s = run_krylov_s<T, 8>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
-    case 16: s = run_krylov_s<T, 16>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 1: s = run_krylov_s<T, 1, TV>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 2: s = run_krylov_s<T, 2, TV>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 4: s = run_krylov_s<T, 4, TV>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 8: s = run_krylov_s<T, 8, TV>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
+    case 16: s = run_krylov_s<T, 16, TV>(inc, k, x0c, x0b, V, ldv, kv, t_persistent, st); break;
     default: return set_error(HEF_ERR_UNSUPPORTED, "hef_krylov_basis: S must be 1, 2, 4, 8 or 16");
   }
   if (s || !tape) return s;
@@ -1192,10 +1219,14 @@ inline long long mixed_ld(int k, int S, size_t esz) {
   return (K + per - 1) / per * per;
 }
 
+// Bytes of a basis element of `dtype` (FP64, FP32, or BF16: FP32 chains
+// archived in BF16).
+inline size_t basis_esz(int dtype) { return dtype == HEF_F64 ? 8 : (dtype == HEF_BF16 ? 2 : 4); }
+
 hef_status check_krylov_args(const hef_incidence* inc, int k, int S, int dtype, const char* fn) {
   if (!inc) return set_error(HEF_ERR_INVALID_ARG, "%s: NULL incidence", fn);
-  if (dtype != HEF_F64 && dtype != HEF_F32)
-    return set_error(HEF_ERR_INVALID_ARG, "%s: dtype must be HEF_F64 or HEF_F32", fn);
+  if (dtype != HEF_F64 && dtype != HEF_F32 && dtype != HEF_BF16)
+    return set_error(HEF_ERR_INVALID_ARG, "%s: dtype must be HEF_F64, HEF_F32 or HEF_BF16", fn);
   if (k < 1) return set_error(HEF_ERR_INVALID_ARG, "%s: k must be >= 1", fn);
   if (S < 1 || S > kMaxS || (S & (S - 1)))
     return set_error(HEF_ERR_UNSUPPORTED, "%s: S must be 1, 2, 4, 8 or 16", fn);
@@ -1233,7 +1264,7 @@ extern "C" hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int3
   const long long K = 2ll * k * S;
   if (!x0_clique || !x0_star || !V)
     return set_error(HEF_ERR_INVALID_ARG, "hef_krylov_basis: NULL array");
-  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  const size_t esz = basis_esz(dtype);
   if (ldv < K || (ldv * esz) % 16 || (reinterpret_cast<uintptr_t>(V) & 15))
     return set_error(HEF_ERR_INVALID_ARG,
                      "hef_krylov_basis: ldv must be >= K = %lld with 16-byte aligned rows", K);
@@ -1243,6 +1274,8 @@ extern "C" hef_status hef_krylov_basis(const hef_incidence* inc, int32_t k, int3
                      need);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (dtype == HEF_F64) return run_krylov<double>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st);
+  if (dtype == HEF_BF16)
+    return run_krylov<float, __nv_bfloat16>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st);
   return run_krylov<float>(inc, k, S, x0_clique, x0_star, V, ldv, workspace, st);
 }
 
@@ -1254,7 +1287,7 @@ extern "C" hef_status hef_set_krylov_persistent(int32_t on) {
 }
 
 extern "C" size_t hef_krylov_tape_bytes(const hef_incidence* inc, int32_t k, int32_t S, int32_t dtype) {
-  if (check_krylov_args(inc, k, S, dtype, "hef_krylov_tape_bytes")) return 0;
+  if (check_krylov_args(inc, k, S, dtype, "hef_krylov_tape_bytes") || dtype == HEF_BF16) return 0;
   TapeLayout tl;
   return carve_tape(nullptr, inc->n, inc->m, k, S, dtype == HEF_F64 ? 8 : 4, &tl);
 }
@@ -1267,6 +1300,8 @@ extern "C" hef_status hef_krylov_basis_tape(const hef_incidence* inc, int32_t k,
   HEF_NVTX("hef_krylov_basis_tape (Algorithm 1 step 3, taped)");
   hef_status s = check_krylov_args(inc, k, S, dtype, "hef_krylov_basis_tape");
   if (s) return s;
+  if (dtype == HEF_BF16)
+    return set_error(HEF_ERR_UNSUPPORTED, "hef_krylov_basis_tape: the backward has no BF16 form");
   const long long K = 2ll * k * S;
   if (!x0_clique || !x0_star || !V || !tape)
     return set_error(HEF_ERR_INVALID_ARG, "hef_krylov_basis_tape: NULL array");
@@ -1291,7 +1326,7 @@ extern "C" size_t hef_krylov_ops_workspace_bytes(const hef_incidence* inc, int32
   const size_t base = hef_krylov_workspace_bytes(inc, k, S, dtype);
   if (!base || (ops != HEF_OPS_CLIQUE && ops != HEF_OPS_STAR && ops != HEF_OPS_BOTH)) return 0;
   if (ops == HEF_OPS_BOTH) return base;
-  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  const size_t esz = basis_esz(dtype);
   return (base + 255) / 256 * 256 + (size_t)inc->n * mixed_ld(k, S, esz) * esz + 256;
 }
 
@@ -1309,7 +1344,7 @@ extern "C" hef_status hef_krylov_basis_ops(const hef_incidence* inc, int32_t k, 
   hef_status s = check_krylov_args(inc, k, S, dtype, "hef_krylov_basis_ops");
   if (s) return s;
   if (!x0_clique || !x0_star || !V) return set_error(HEF_ERR_INVALID_ARG, "hef_krylov_basis_ops: NULL array");
-  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  const size_t esz = basis_esz(dtype);
   if (ldv < (long long)k * S || (ldv * esz) % 16 || (reinterpret_cast<uintptr_t>(V) & 15))
     return set_error(HEF_ERR_INVALID_ARG,
                      "hef_krylov_basis_ops: ldv must be >= k S with 16-byte aligned rows");
@@ -1322,8 +1357,10 @@ extern "C" hef_status hef_krylov_basis_ops(const hef_incidence* inc, int32_t k, 
   char* W = static_cast<char*>(workspace) + (base + 255) / 256 * 256;
   const long long ldw = mixed_ld(k, S, esz);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  s = dtype == HEF_F64 ? run_krylov<double>(inc, k, S, x0_clique, x0_star, W, ldw, workspace, st)
-                       : run_krylov<float>(inc, k, S, x0_clique, x0_star, W, ldw, workspace, st);
+  s = dtype == HEF_F64    ? run_krylov<double>(inc, k, S, x0_clique, x0_star, W, ldw, workspace, st)
+      : dtype == HEF_BF16 ? run_krylov<float, __nv_bfloat16>(inc, k, S, x0_clique, x0_star, W,
+                                                             ldw, workspace, st)
+                          : run_krylov<float>(inc, k, S, x0_clique, x0_star, W, ldw, workspace, st);
   if (s) return s;
   const long long total = inc->n * (long long)k * S;
   if (total == 0) return HEF_OK;
@@ -1333,6 +1370,10 @@ extern "C" hef_status hef_krylov_basis_ops(const hef_incidence* inc, int32_t k, 
     HEF_LAUNCH("k_select_op", st, k_select_op<double><<<grid, kThreads, 0, st>>>(
                                       inc->n, k, S, op, reinterpret_cast<const double*>(W), ldw,
                                       static_cast<double*>(V), ldv));
+  else if (dtype == HEF_BF16)
+    HEF_LAUNCH("k_select_op", st, k_select_op<__nv_bfloat16><<<grid, kThreads, 0, st>>>(
+                                      inc->n, k, S, op, reinterpret_cast<const __nv_bfloat16*>(W),
+                                      ldw, static_cast<__nv_bfloat16*>(V), ldv));
   else
     HEF_LAUNCH("k_select_op", st, k_select_op<float><<<grid, kThreads, 0, st>>>(
                                       inc->n, k, S, op, reinterpret_cast<const float*>(W), ldw,

@@ -564,9 +564,9 @@ size_t carve_ortho(void* base, long long n, int K, int dtype, OrthoWs* w) {
   w->nchunk = nchunk;
   w->rows_per_chunk = (int)(((n + nchunk - 1) / nchunk + kPR - 1) / kPR * kPR);
   const size_t KK = (size_t)K * K;
-  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  const size_t esz = dtype == HEF_F64 ? 8 : 4;  // of R^-1 and mu (FP32 for the BF16 basis)
   size_t npart = (size_t)nchunk * npairs * kGB * kGB;
-  if (dtype == HEF_F32 && gram_tc_supported(K)) {
+  if (dtype != HEF_F64 && gram_tc_supported(K)) {
     const size_t tc = gram_tc_part_doubles(n, K);
     if (tc > npart) npart = tc;
   }
@@ -584,13 +584,15 @@ size_t carve_ortho(void* base, long long n, int K, int dtype, OrthoWs* w) {
   w->kept = cv.take<int>(K);
   w->rank = cv.take<int>(4);
   w->flag = cv.take<int>(4);
-  w->tcs = cv.take<float>(dtype == HEF_F32 && apply_tc_supported(K) ? apply_tc_scratch_floats(K) : 1);
+  w->tcs = cv.take<float>(dtype != HEF_F64 && apply_tc_supported(K) ? apply_tc_scratch_floats(K) : 1);
   return cv.bytes();
 }
 
+// bf16: V holds the basis as BF16 (T = float is then the type of R^-1 and
+// the elimination; the Gram and the apply run on the tensor cores).
 template <typename T>
 hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int* rank_out,
-                     const OrthoWs& w, cudaStream_t st) {
+                     const OrthoWs& w, cudaStream_t st, bool bf16 = false) {
   const int Kp = round8(K);
   const size_t gram_smem = (size_t)kPR * Kp * sizeof(T);
   HEF_ENSURE_SMEM(k_gram<T>, (int)gram_smem);
@@ -633,8 +635,7 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
   for (int pass = 0; pass < 2; ++pass) {
     CholOut o{w.Rinv, w.mu, Rs[pass], w.kept, w.rank, w.flag};
     if (use_tc) {
-      hef_status s = gram_tc(reinterpret_cast<const float*>(V), ldv, n, K, w.part, w.G, w.c,
-                             w.flag + 1, st);
+      hef_status s = gram_tc(V, bf16, ldv, n, K, w.part, w.G, w.c, w.flag + 1, st);
       if (s) return s;
     } else {
       HEF_LAUNCH("k_gram", st, k_gram<T><<<ggrid, kPairs, gram_smem, st>>>(
@@ -677,8 +678,7 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
     }
     HEF_CHECK_LAUNCH();
     if (sizeof(T) == 4 && apply_tc_supported(K)) {
-      hef_status s = apply_tc(reinterpret_cast<float*>(V), ldv, n, K,
-                              static_cast<const float*>(w.Rinv), Kp,
+      hef_status s = apply_tc(V, bf16, ldv, n, K, static_cast<const float*>(w.Rinv), Kp,
                               static_cast<const float*>(w.mu), w.tcs, w.flag + 1, st);
       if (s) return s;
     } else {
@@ -705,7 +705,9 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
 using namespace hef;
 
 extern "C" size_t hef_orthonormalize_workspace_bytes(int64_t n, int32_t K, int32_t dtype) {
-  if (n < 1 || K < 1 || K > 512 || (dtype != HEF_F64 && dtype != HEF_F32)) return 0;
+  if (n < 1 || K < 1 || K > 512 || (dtype != HEF_F64 && dtype != HEF_F32 && dtype != HEF_BF16))
+    return 0;
+  if (dtype == HEF_BF16 && !(gram_tc_supported(K) && apply_tc_supported(K))) return 0;
   OrthoWs w;
   return carve_ortho(nullptr, n, K, dtype, &w);
 }
@@ -718,9 +720,12 @@ extern "C" hef_status hef_orthonormalize(int64_t n, int32_t K, int32_t dtype, vo
   if (K > 512) return set_error(HEF_ERR_UNSUPPORTED, "hef_orthonormalize: K must be <= 512");
   if (n >= (1ll << 31) - 1)
     return set_error(HEF_ERR_UNSUPPORTED, "hef_orthonormalize: n must be < 2^31 - 1");
-  if (dtype != HEF_F64 && dtype != HEF_F32)
-    return set_error(HEF_ERR_INVALID_ARG, "hef_orthonormalize: dtype must be HEF_F64 or HEF_F32");
-  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  if (dtype != HEF_F64 && dtype != HEF_F32 && dtype != HEF_BF16)
+    return set_error(HEF_ERR_INVALID_ARG,
+                     "hef_orthonormalize: dtype must be HEF_F64, HEF_F32 or HEF_BF16");
+  if (dtype == HEF_BF16 && !(gram_tc_supported(K) && apply_tc_supported(K)))
+    return set_error(HEF_ERR_UNSUPPORTED, "hef_orthonormalize: the BF16 basis needs K <= 511");
+  const size_t esz = dtype == HEF_F64 ? 8 : (dtype == HEF_BF16 ? 2 : 4);
   if (!V || ldv < K || (ldv * esz) % 16 || (reinterpret_cast<uintptr_t>(V) & 15))
     return set_error(HEF_ERR_INVALID_ARG,
                      "hef_orthonormalize: V NULL, ldv < K or rows not 16-byte aligned");
@@ -732,5 +737,6 @@ extern "C" hef_status hef_orthonormalize(int64_t n, int32_t K, int32_t dtype, vo
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   if (dtype == HEF_F64)
     return run_ortho<double>(n, K, static_cast<double*>(V), ldv, R_out, rank_out, w, st);
-  return run_ortho<float>(n, K, static_cast<float*>(V), ldv, R_out, rank_out, w, st);
+  return run_ortho<float>(n, K, static_cast<float*>(V), ldv, R_out, rank_out, w, st,
+                          dtype == HEF_BF16);
 }

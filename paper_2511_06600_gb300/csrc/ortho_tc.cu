@@ -12,6 +12,15 @@
 // on an mbarrier per stage; every wait is bounded and a timeout sets *err.
 // The epilogue moves the FP32 accumulators from TMEM to per-CTA FP32 partials
 // (no FP64 work on the SM); k_gram_tc_reduce widens them and sums in FP64.
+//
+// A basis stored in BF16 (BF = true) enters the same MMAs: a BF16 value is
+// exact in TF32 (8 significant bits within TF32's 11), so its lo part is
+// zero and one product hi hi' gives the exact products of the stored
+// values, accumulated in FP32 — what a BF16-input MMA with FP32 accumulation
+// computes.  The apply likewise needs hi(V) hi(R^-1) + hi(V) lo(R^-1), and
+// rounds Q to BF16 on the store.
+#include <cuda_bf16.h>
+
 #include "internal.h"
 #include "umma.cuh"
 
@@ -28,6 +37,7 @@ constexpr uint32_t kWaitIters = 1u << 20;    // bounded mbarrier waits
 
 struct GramTcArgs {
   const float* V;
+  const __nv_bfloat16* Vb;  // BF16 basis (the BF form of the kernels)
   long long ldv;
   int n, K, Kq, nb;
   int rows_per_cta;
@@ -39,7 +49,13 @@ struct GramTcArgs {
 // Slab loader: thread tid owns the float4 slots f = tid + 256 k of a slab
 // (slab row f % 32, basis columns 4 (f / 32) .. + 3); values past K are the
 // ones column (index K) or zero, rows past the chunk are zero.
-template <int PER>
+template <bool BF>
+__device__ __forceinline__ float gram_elem(const GramTcArgs& a, long long row, int c) {
+  if constexpr (BF) return __bfloat162float(a.Vb[row * a.ldv + c]);
+  else return a.V[row * a.ldv + c];
+}
+
+template <int PER, bool BF>
 __device__ __forceinline__ void gram_load_slab(const GramTcArgs& a, long long rowbase, long long r1,
                                                float4 (&buf)[PER]) {
 #pragma unroll
@@ -50,13 +66,21 @@ __device__ __forceinline__ void gram_load_slab(const GramTcArgs& a, long long ro
     const long long row = rowbase + r;
     const bool valid = row < r1;
     if (valid && c0 + 3 < a.K) {
-      buf[k] = __ldg(reinterpret_cast<const float4*>(a.V + row * a.ldv + c0));
+      if constexpr (BF) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(a.Vb + row * a.ldv + c0));
+        const __nv_bfloat162 h0 = *reinterpret_cast<const __nv_bfloat162*>(&u.x);
+        const __nv_bfloat162 h1 = *reinterpret_cast<const __nv_bfloat162*>(&u.y);
+        const float2 f0 = __bfloat1622float2(h0), f1 = __bfloat1622float2(h1);
+        buf[k] = make_float4(f0.x, f0.y, f1.x, f1.y);
+      } else {
+        buf[k] = __ldg(reinterpret_cast<const float4*>(a.V + row * a.ldv + c0));
+      }
     } else {
       float x[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         const int c = c0 + u;
-        x[u] = !valid ? 0.f : (c < a.K ? a.V[row * a.ldv + c] : (c == a.K ? 1.f : 0.f));
+        x[u] = !valid ? 0.f : (c < a.K ? gram_elem<BF>(a, row, c) : (c == a.K ? 1.f : 0.f));
       }
       buf[k] = make_float4(x[0], x[1], x[2], x[3]);
     }
@@ -68,7 +92,7 @@ __device__ __forceinline__ void gram_load_slab(const GramTcArgs& a, long long ro
 // as MMAs of N <= 256); its accumulator occupies TMEM columns from the sum of
 // the earlier blocks' N in the group.  NB blocks of 128 rows pad the
 // transposed slab; STAGES shared-memory stages (2, or 1 when two do not fit).
-template <int NB, int STAGES>
+template <int NB, int STAGES, bool BF>
 __global__ void __launch_bounds__(kGrThreads, 1) k_gram_tc(GramTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -114,12 +138,12 @@ __global__ void __launch_bounds__(kGrThreads, 1) k_gram_tc(GramTcArgs a) {
   bool ok = true;
   int committed = 0;  // slabs whose MMAs were issued
   float4 cur[PER], nxt[PER];
-  if (nslab > 0) gram_load_slab<PER>(a, r0, r1, cur);
+  if (nslab > 0) gram_load_slab<PER, BF>(a, r0, r1, cur);
 
   for (int t = 0; t < nslab; ++t) {
     const int s = t % STAGES;
     // next slab's loads are in flight while this one is converted and issued
-    if (t + 1 < nslab) gram_load_slab<PER>(a, r0 + (long long)(t + 1) * kSlab, r1, nxt);
+    if (t + 1 < nslab) gram_load_slab<PER, BF>(a, r0 + (long long)(t + 1) * kSlab, r1, nxt);
     if (t >= STAGES) ok = ok && mbar_wait(&bars[s], ((t - STAGES) / STAGES) & 1, kWaitIters);
     if (!__syncthreads_and(ok)) {
       ok = false;
@@ -136,10 +160,14 @@ __global__ void __launch_bounds__(kGrThreads, 1) k_gram_tc(GramTcArgs a) {
       const float x[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const float h = tf32_round(x[u]);
         const uint32_t off = sw128_offset(c0 + u, r);
-        *reinterpret_cast<float*>(hi + off) = h;
-        *reinterpret_cast<float*>(lo + off) = x[u] - h;
+        if constexpr (BF) {
+          *reinterpret_cast<float*>(hi + off) = x[u];  // exact in TF32; lo = 0
+        } else {
+          const float h = tf32_round(x[u]);
+          *reinterpret_cast<float*>(hi + off) = h;
+          *reinterpret_cast<float*>(lo + off) = x[u] - h;
+        }
       }
     }
 #pragma unroll
@@ -163,8 +191,10 @@ __global__ void __launch_bounds__(kGrThreads, 1) k_gram_tc(GramTcArgs a) {
             const uint32_t d = tmem + (uint32_t)(toff[b] + h0);
             const uint32_t id = idesc_tf32(128, Nh);
             mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(shi + boff), id, acc);
-            mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(slo + boff), id, 1u);
-            mma_tf32(d, desc_k_sw128(slo + aoff), desc_k_sw128(shi + boff), id, 1u);
+            if constexpr (!BF) {
+              mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(slo + boff), id, 1u);
+              mma_tf32(d, desc_k_sw128(slo + aoff), desc_k_sw128(shi + boff), id, 1u);
+            }
           }
         }
       }
@@ -297,6 +327,7 @@ __global__ void k_rinv_split(const float* __restrict__ Rinv, const float* __rest
 
 struct ApplyTcArgs {
   float* V;
+  __nv_bfloat16* Vb;  // BF16 basis (the BF form), Q rounded to BF16
   long long ldv;
   int n, K, Kq, Kd;
   const float* RtH;
@@ -311,7 +342,7 @@ struct ApplyTcArgs {
 // Rinv^T (Rinv is upper triangular, so block ka feeds output columns
 // j >= 32 ka only).  RESB: every B tile stays resident in shared memory
 // (staged once per CTA); otherwise B is staged with A for every block.
-template <bool RESB, int STAGES>
+template <bool RESB, int STAGES, bool BF>
 __global__ void __launch_bounds__(kApThreads, 1) k_apply_tc(ApplyTcArgs a) {
   extern __shared__ unsigned char smem_raw[];
   unsigned char* base = reinterpret_cast<unsigned char*>(
@@ -376,12 +407,22 @@ __global__ void __launch_bounds__(kApThreads, 1) k_apply_tc(ApplyTcArgs a) {
       const long long row = (long long)tile * 128 + r;
       const int col = ka * 32 + 4 * q;
       if (tile < ntiles && row < a.n && col + 3 < a.K) {
-        buf[k] = __ldg(reinterpret_cast<const float4*>(a.V + row * a.ldv + col));
+        if constexpr (BF) {
+          const uint2 u = __ldg(reinterpret_cast<const uint2*>(a.Vb + row * a.ldv + col));
+          const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.x));
+          const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u.y));
+          buf[k] = make_float4(f0.x, f0.y, f1.x, f1.y);
+        } else {
+          buf[k] = __ldg(reinterpret_cast<const float4*>(a.V + row * a.ldv + col));
+        }
       } else {
         float x[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
-          x[u] = (tile < ntiles && row < a.n && col + u < a.K) ? a.V[row * a.ldv + col + u] : 0.f;
+        for (int u = 0; u < 4; ++u) {
+          const bool in = tile < ntiles && row < a.n && col + u < a.K;
+          if constexpr (BF) x[u] = in ? __bfloat162float(a.Vb[row * a.ldv + col + u]) : 0.f;
+          else x[u] = in ? a.V[row * a.ldv + col + u] : 0.f;
+        }
         buf[k] = make_float4(x[0], x[1], x[2], x[3]);
       }
     }
@@ -417,12 +458,16 @@ __global__ void __launch_bounds__(kApThreads, 1) k_apply_tc(ApplyTcArgs a) {
         const int f = tid + kApThreads * k;
         const int r = f >> 3, q = f & 7;
         const float x[4] = {cur[k].x, cur[k].y, cur[k].z, cur[k].w};
-        float h[4], l[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) h[u] = tf32_round(x[u]), l[u] = x[u] - h[u];
         const uint32_t off = sw128_offset(r, 4 * q);
-        *reinterpret_cast<float4*>(ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
-        *reinterpret_cast<float4*>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
+        if constexpr (BF) {  // exact in TF32: no lo part
+          *reinterpret_cast<float4*>(ahi + off) = make_float4(x[0], x[1], x[2], x[3]);
+        } else {
+          float h[4], l[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) h[u] = tf32_round(x[u]), l[u] = x[u] - h[u];
+          *reinterpret_cast<float4*>(ahi + off) = make_float4(h[0], h[1], h[2], h[3]);
+          *reinterpret_cast<float4*>(alo + off) = make_float4(l[0], l[1], l[2], l[3]);
+        }
       }
 #pragma unroll
       for (int k = 0; k < kAPer; ++k) cur[k] = nxt[k];
@@ -447,7 +492,7 @@ __global__ void __launch_bounds__(kApThreads, 1) k_apply_tc(ApplyTcArgs a) {
             const uint32_t acc = (ka > 0 || ks > 0) ? 1u : 0u;
             mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbh + bo), id, acc);
             mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbl + bo), id, 1u);
-            mma_tf32(d, desc_k_sw128(sal + ko), desc_k_sw128(sbh + bo), id, 1u);
+            if constexpr (!BF) mma_tf32(d, desc_k_sw128(sal + ko), desc_k_sw128(sbh + bo), id, 1u);
           }
         }
         mma_commit(&bars[s]);
@@ -476,7 +521,22 @@ __global__ void __launch_bounds__(kApThreads, 1) k_apply_tc(ApplyTcArgs a) {
       tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)c8 * 8u, v);
       tmem_wait_ld();
       const int j0 = c8 * 8;
-      if (row < a.n) {
+      if (BF && row < a.n) {
+        if (j0 + 7 < a.K) {
+          const float4 m0 = __ldg(reinterpret_cast<const float4*>(a.muR + j0));
+          const float4 m1 = __ldg(reinterpret_cast<const float4*>(a.muR + j0 + 4));
+          __nv_bfloat162 h[4];
+          h[0] = __floats2bfloat162_rn(v[0] - m0.x, v[1] - m0.y);
+          h[1] = __floats2bfloat162_rn(v[2] - m0.z, v[3] - m0.w);
+          h[2] = __floats2bfloat162_rn(v[4] - m1.x, v[5] - m1.y);
+          h[3] = __floats2bfloat162_rn(v[6] - m1.z, v[7] - m1.w);
+          *reinterpret_cast<uint4*>(a.Vb + row * a.ldv + j0) = *reinterpret_cast<const uint4*>(h);
+        } else {
+#pragma unroll
+          for (int u = 0; u < 8; ++u)
+            if (j0 + u < a.K) a.Vb[row * a.ldv + j0 + u] = __float2bfloat16_rn(v[u] - a.muR[j0 + u]);
+        }
+      } else if (row < a.n) {
         if (j0 + 7 < a.K) {
           float* dst = a.V + row * a.ldv + j0;
           const float4 m0 = __ldg(reinterpret_cast<const float4*>(a.muR + j0));
@@ -515,7 +575,7 @@ size_t apply_tc_scratch_floats(int K) {
   return 2 * (size_t)Kq * Kd + Kq + 64;
 }
 
-hef_status apply_tc(float* V, long long ldv, long long n, int K, const float* Rinv, int Kp,
+hef_status apply_tc(void* V, bool bf16, long long ldv, long long n, int K, const float* Rinv, int Kp,
                     const float* mu, float* scratch, int* err, cudaStream_t st) {
   const int Kq = (K + 15) & ~15, Kd = (K + 31) & ~31;
   float* RtH = scratch;
@@ -524,7 +584,8 @@ hef_status apply_tc(float* V, long long ldv, long long n, int K, const float* Ri
   HEF_LAUNCH("k_rinv_split", st, k_rinv_split<<<stride_grid((long long)Kq * Kd, 2), kThreads, 0, st>>>(
                                      Rinv, mu, K, Kp, Kq, Kd, RtH, RtL, muR));
   ApplyTcArgs a;
-  a.V = V;
+  a.V = bf16 ? nullptr : static_cast<float*>(V);
+  a.Vb = bf16 ? static_cast<__nv_bfloat16*>(V) : nullptr;
   a.ldv = ldv;
   a.n = (int)n;
   a.K = K;
@@ -541,16 +602,19 @@ hef_status apply_tc(float* V, long long ldv, long long n, int K, const float* Ri
   const size_t smem_res = 1024 + bres + 2 * (2 * 128 * 128) + 64;
   const size_t stage = 2 * 128 * 128 + 2 * (size_t)Kq * 128;  // A and B of one K block
   const size_t smem2 = 1024 + 2 * stage + 64, smem1 = 1024 + stage + 64;
-  if (smem_res <= 220 * 1024) {
-    HEF_ENSURE_SMEM((k_apply_tc<true, 2>), (int)smem_res);
-    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<true, 2><<<ctas, kApThreads, smem_res, st>>>(a)));
-  } else if (smem2 <= 220 * 1024) {
-    HEF_ENSURE_SMEM((k_apply_tc<false, 2>), (int)smem2);
-    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<false, 2><<<ctas, kApThreads, smem2, st>>>(a)));
-  } else {
-    HEF_ENSURE_SMEM((k_apply_tc<false, 1>), (int)smem1);
-    HEF_LAUNCH("k_apply_tc", st, (k_apply_tc<false, 1><<<ctas, kApThreads, smem1, st>>>(a)));
-  }
+  auto launch = [&](auto kern, size_t smem) -> hef_status {
+    HEF_ENSURE_SMEM(kern, (int)smem);
+    HEF_LAUNCH("k_apply_tc", st, (kern<<<ctas, kApThreads, smem, st>>>(a)));
+    return HEF_OK;
+  };
+  hef_status s;
+  if (smem_res <= 220 * 1024)
+    s = bf16 ? launch(k_apply_tc<true, 2, true>, smem_res) : launch(k_apply_tc<true, 2, false>, smem_res);
+  else if (smem2 <= 220 * 1024)
+    s = bf16 ? launch(k_apply_tc<false, 2, true>, smem2) : launch(k_apply_tc<false, 2, false>, smem2);
+  else
+    s = bf16 ? launch(k_apply_tc<false, 1, true>, smem1) : launch(k_apply_tc<false, 1, false>, smem1);
+  if (s) return s;
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
@@ -587,18 +651,24 @@ static int gram_groups(int Kq, int nb, int (&gmask)[4]) {
 template <int NB, int STAGES>
 static hef_status launch_gram_tc(const GramTcArgs& a, int ctas, int ng, cudaStream_t st) {
   const size_t smem = 1024 + 2 * (size_t)STAGES * NB * 128 * 128 + 64;
-  HEF_ENSURE_SMEM((k_gram_tc<NB, STAGES>), (int)smem);
-  HEF_LAUNCH("k_gram_tc", st, (k_gram_tc<NB, STAGES><<<dim3(ctas, ng), kGrThreads, smem, st>>>(a)));
+  if (a.Vb) {
+    HEF_ENSURE_SMEM((k_gram_tc<NB, STAGES, true>), (int)smem);
+    HEF_LAUNCH("k_gram_tc", st, (k_gram_tc<NB, STAGES, true><<<dim3(ctas, ng), kGrThreads, smem, st>>>(a)));
+  } else {
+    HEF_ENSURE_SMEM((k_gram_tc<NB, STAGES, false>), (int)smem);
+    HEF_LAUNCH("k_gram_tc", st, (k_gram_tc<NB, STAGES, false><<<dim3(ctas, ng), kGrThreads, smem, st>>>(a)));
+  }
   return HEF_OK;
 }
 
-hef_status gram_tc(const float* V, long long ldv, long long n, int K, double* part, double* G,
-                   double* c, int* err, cudaStream_t st) {
+hef_status gram_tc(const void* V, bool bf16, long long ldv, long long n, int K, double* part,
+                   double* G, double* c, int* err, cudaStream_t st) {
   const int Kq = (K + 1 + 15) & ~15;
   const int nb = (Kq + 127) / 128;
   const int ctas = gram_tc_ctas(n);
   GramTcArgs a;
-  a.V = V;
+  a.V = bf16 ? nullptr : static_cast<const float*>(V);
+  a.Vb = bf16 ? static_cast<const __nv_bfloat16*>(V) : nullptr;
   a.ldv = ldv;
   a.n = (int)n;
   a.K = K;

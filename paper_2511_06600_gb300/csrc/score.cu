@@ -12,11 +12,13 @@
 // across warps and CTAs in a fixed order); pass 2 recomputes the spreads and
 // takes the max with its arg-max column and the pins that realise it.
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <cfloat>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 
 #include "internal.h"
 #include "umma.cuh"
@@ -44,6 +46,13 @@ __device__ __forceinline__ float lowest<float>() {
   return -FLT_MAX;
 }
 
+// An element of Q in the working type T (a BF16 basis widens exactly).
+template <typename T, typename QT>
+__device__ __forceinline__ T qw(QT x) {
+  if constexpr (std::is_same<QT, __nv_bfloat16>::value) return (T)__bfloat162float(x);
+  else return (T)x;
+}
+
 // Next group of 32 hyperedges for the calling warp (dynamic distribution:
 // one atomic per group on a counter that starts each call at zero).
 __device__ __forceinline__ long long next_group(unsigned int* work) {
@@ -54,8 +63,8 @@ __device__ __forceinline__ long long next_group(unsigned int* work) {
 
 // Extrema of two hyperedges at once (pins [a0, b0) and [a1, b1), warp-uniform):
 // four clamped pin rows of each are in flight together.
-template <typename T, int NC, typename PinAt>
-__device__ __forceinline__ void two_edge_extrema(const T* __restrict__ Q, long long ldq, int K,
+template <typename T, int NC, typename PinAt, typename QT>
+__device__ __forceinline__ void two_edge_extrema(const QT* __restrict__ Q, long long ldq, int K,
                                                  PinAt cpins, int a0, int b0,
                                                  int a1, int b1, int lane, T (&mx0)[NC],
                                                  T (&mn0)[NC], T (&mx1)[NC], T (&mn1)[NC]) {
@@ -68,7 +77,7 @@ __device__ __forceinline__ void two_edge_extrema(const T* __restrict__ Q, long l
   while (t0 < b0 || t1 < b1) {
     const bool u0 = t0 < b0, u1 = t1 < b1;
     const int l0 = b0 - 1, l1 = b1 - 1;
-    const T* r[8];
+    const QT* r[8];
     r[0] = Q + (long long)(u0 ? cpins(t0) : 0) * ldq;
     r[1] = Q + (long long)(u0 ? cpins(min(t0 + 1, l0)) : 0) * ldq;
     r[2] = Q + (long long)(u0 ? cpins(min(t0 + 2, l0)) : 0) * ldq;
@@ -83,7 +92,7 @@ __device__ __forceinline__ void two_edge_extrema(const T* __restrict__ Q, long l
       if (col < K) {
         T v[8];
 #pragma unroll
-        for (int q = 0; q < 8; ++q) v[q] = r[q][col];
+        for (int q = 0; q < 8; ++q) v[q] = qw<T>(r[q][col]);
         if (u0) {
           mx0[c] = fmax(fmax(mx0[c], fmax(v[0], v[1])), fmax(v[2], v[3]));
           mn0[c] = fmin(fmin(mn0[c], fmin(v[0], v[1])), fmin(v[2], v[3]));
@@ -103,8 +112,8 @@ __device__ __forceinline__ void two_edge_extrema(const T* __restrict__ Q, long l
 // batches w, w + 8, ...; partial extrema meet in shared memory (smx/smn,
 // [warp][32 NC]).  On return every thread's columns (lane + 32 c) hold the
 // hyperedge's extrema in mx/mn.
-template <typename T, int NC>
-__device__ __forceinline__ void cta_edge_extrema(const T* __restrict__ Q, long long ldq, int K,
+template <typename T, int NC, typename QT>
+__device__ __forceinline__ void cta_edge_extrema(const QT* __restrict__ Q, long long ldq, int K,
                                                  const int32_t* __restrict__ cpins, int a, int b,
                                                  T* smx, T* smn, T (&mx)[NC], T (&mn)[NC]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -112,15 +121,15 @@ __device__ __forceinline__ void cta_edge_extrema(const T* __restrict__ Q, long l
   for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
   for (int t = a + 4 * wid; t < b; t += 4 * nw) {
     const int last = b - 1;
-    const T* r0 = Q + (long long)cpins[t] * ldq;
-    const T* r1 = Q + (long long)cpins[min(t + 1, last)] * ldq;
-    const T* r2 = Q + (long long)cpins[min(t + 2, last)] * ldq;
-    const T* r3 = Q + (long long)cpins[min(t + 3, last)] * ldq;
+    const QT* r0 = Q + (long long)cpins[t] * ldq;
+    const QT* r1 = Q + (long long)cpins[min(t + 1, last)] * ldq;
+    const QT* r2 = Q + (long long)cpins[min(t + 2, last)] * ldq;
+    const QT* r3 = Q + (long long)cpins[min(t + 3, last)] * ldq;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int col = lane + 32 * c;
       if (col < K) {
-        const T v0 = r0[col], v1 = r1[col], v2 = r2[col], v3 = r3[col];
+        const T v0 = qw<T>(r0[col]), v1 = qw<T>(r1[col]), v2 = qw<T>(r2[col]), v3 = qw<T>(r3[col]);
         mx[c] = fmax(fmax(mx[c], fmax(v0, v1)), fmax(v2, v3));
         mn[c] = fmin(fmin(mn[c], fmin(v0, v1)), fmin(v2, v3));
       }
@@ -146,8 +155,8 @@ __device__ __forceinline__ void cta_edge_extrema(const T* __restrict__ Q, long l
 
 // Pass 1, large hyperedges: CTA b handles list entries b, b + grid, ...; its
 // sum of w_e spread^2 per column goes to bpart[b][col] (FP64).
-template <typename T, int NC>
-__global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restrict__ Q, long long ldq,
+template <typename T, int NC, typename QT = T>
+__global__ void __launch_bounds__(256) k_score_big1(IncView g, const QT* __restrict__ Q, long long ldq,
                                                     int K, double* bpart, T* spread, int ldsp) {
   // the staged pass 1 may start beside this one: it reads bpart only after
   // its dependency wait
@@ -162,7 +171,7 @@ __global__ void __launch_bounds__(256) k_score_big1(IncView g, const T* __restri
   for (int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
     const int e = g.big_idx[bi];
     T mx[NC], mn[NC];
-    cta_edge_extrema<T, NC>(Q, ldq, K, g.cpins, g.ceptr[e], g.ceptr[e + 1], smx, smn, mx, mn);
+    cta_edge_extrema<T, NC, QT>(Q, ldq, K, g.cpins, g.ceptr[e], g.ceptr[e + 1], smx, smn, mx, mn);
     const double we = g.ew[e];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -205,8 +214,8 @@ __device__ __forceinline__ void finish_qh(const GridRed& red, int K, const doubl
 // spreads stored row-major (spread[e K + i]) when `spread` is given; Q_H[i] =
 // sum of per-CTA partials, then the large hyperedges' partials bpart, in a
 // fixed order.
-template <typename T, int NC>
-__global__ void __launch_bounds__(256) k_score_pass1(IncView g, const T* __restrict__ Q, long long ldq,
+template <typename T, int NC, typename QT = T>
+__global__ void __launch_bounds__(256) k_score_pass1(IncView g, const QT* __restrict__ Q, long long ldq,
                                                      int K, GridRed red, const double* __restrict__ bpart,
                                                      int nbpart, double* QH, double* invQH,
                                                      double* QH_out, unsigned int* work,
@@ -554,8 +563,8 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
 
 // Pass 2 for one hyperedge whose extrema a warp holds (lanes over columns):
 // arg-max column (lowest on ties), its pins (lowest position on ties), R_e.
-template <typename T, int NC>
-__device__ __forceinline__ void score_edge_out(IncView g, const T* __restrict__ Q, long long ldq,
+template <typename T, int NC, typename QT>
+__device__ __forceinline__ void score_edge_out(IncView g, const QT* __restrict__ Q, long long ldq,
                                                int K, int reduce, const double* __restrict__ invQH,
                                                const T (&iq)[NC], const bool (&use)[NC], int e,
                                                int a, int b, const T (&mx)[NC], const T (&mn)[NC],
@@ -600,7 +609,7 @@ __device__ __forceinline__ void score_edge_out(IncView g, const T* __restrict__ 
   int tmax = 0x7fffffff, tmin = 0x7fffffff;
   if (any) {
     for (int t = a + lane; t < b; t += 32) {
-      const T v = Q[(long long)g.cpins[t] * ldq + bcol];
+      const T v = qw<T>(Q[(long long)g.cpins[t] * ldq + bcol]);
       if (v == vmax && t < tmax) tmax = t;
       if (v == vmin && t < tmin) tmin = t;
     }
@@ -638,8 +647,8 @@ __device__ __forceinline__ void load_use(const double* __restrict__ QH, const do
 }
 
 // Pass 2, large hyperedges (one CTA each; warp 0 writes the outputs).
-template <typename T, int NC>
-__global__ void __launch_bounds__(256) k_score_big2(IncView g, const T* __restrict__ Q, long long ldq,
+template <typename T, int NC, typename QT = T>
+__global__ void __launch_bounds__(256) k_score_big2(IncView g, const QT* __restrict__ Q, long long ldq,
                                                     int K, int reduce, const double* __restrict__ QH,
                                                     const double* __restrict__ invQH, double* R_out,
                                                     int32_t* argvec, int32_t* pmax, int32_t* pmin) {
@@ -653,17 +662,17 @@ __global__ void __launch_bounds__(256) k_score_big2(IncView g, const T* __restri
     const int e = g.big_idx[bi];
     const int a = g.ceptr[e], b = g.ceptr[e + 1];
     T mx[NC], mn[NC];
-    cta_edge_extrema<T, NC>(Q, ldq, K, g.cpins, a, b, smx, smn, mx, mn);
+    cta_edge_extrema<T, NC, QT>(Q, ldq, K, g.cpins, a, b, smx, smn, mx, mn);
     if ((threadIdx.x >> 5) == 0)
-      score_edge_out<T, NC>(g, Q, ldq, K, reduce, invQH, iq, use, e, a, b, mx, mn, R_out, argvec, pmax,
-                            pmin);
+      score_edge_out<T, NC, QT>(g, Q, ldq, K, reduce, invQH, iq, use, e, a, b, mx, mn, R_out, argvec,
+                                pmax, pmin);
   }
 }
 
 // Pass 2, the other hyperedges: warp per group of 32, two at a time; those
 // with < 2 pins get 0 / -1.
-template <typename T, int NC>
-__global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restrict__ Q, long long ldq,
+template <typename T, int NC, typename QT = T>
+__global__ void __launch_bounds__(256) k_score_pass2(IncView g, const QT* __restrict__ Q, long long ldq,
                                                      int K, int reduce, const double* __restrict__ QH,
                                                      const double* __restrict__ invQH, double* R_out,
                                                      int32_t* argvec, int32_t* pmax, int32_t* pmin,
@@ -696,11 +705,11 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const T* __restr
       two_edge_extrema<T, NC>(Q, ldq, K, [&](int t) { return g.cpins[t]; }, a0, b0, a1, b1, lane,
                               mx0, mn0, mx1, mn1);
       if (b0 > a0)
-        score_edge_out<T, NC>(g, Q, ldq, K, reduce, invQH, iq, use, (int)(grp * 32 + i), a0, b0, mx0, mn0,
-                              R_out, argvec, pmax, pmin);
+        score_edge_out<T, NC, QT>(g, Q, ldq, K, reduce, invQH, iq, use, (int)(grp * 32 + i), a0, b0,
+                                  mx0, mn0, R_out, argvec, pmax, pmin);
       if (b1 > a1)
-        score_edge_out<T, NC>(g, Q, ldq, K, reduce, invQH, iq, use, (int)(grp * 32 + i + 1), a1, b1, mx1,
-                              mn1, R_out, argvec, pmax, pmin);
+        score_edge_out<T, NC, QT>(g, Q, ldq, K, reduce, invQH, iq, use, (int)(grp * 32 + i + 1), a1,
+                                  b1, mx1, mn1, R_out, argvec, pmax, pmin);
     }
   }
 }
@@ -770,7 +779,7 @@ __global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restr
       // extrema of column bcol over the pins, lowest position on ties
       T vmax = Q[(long long)g.cpins[a] * ldq + bcol], vmin = vmax;
       for (int t = a + 1; t < b; ++t) {
-        const T v = Q[(long long)g.cpins[t] * ldq + bcol];
+        const T v = qw<T>(Q[(long long)g.cpins[t] * ldq + bcol]);
         if (v > vmax) vmax = v, tmax = t;
         if (v < vmin) vmin = v, tmin = t;
       }
@@ -845,8 +854,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
 // round-to-nearest FP64 operations; the largest wins, ties to the first
 // pair.  Then lanes take the columns: r_i = (Q[p,i] - Q[q,i])^2 / Q_H[i] over
 // the usable columns, the largest wins, ties to the lowest i.
-template <typename T>
-__global__ void __launch_bounds__(256) k_score_embed(IncView g, const T* __restrict__ Q,
+template <typename T, typename QT = T>
+__global__ void __launch_bounds__(256) k_score_embed(IncView g, const QT* __restrict__ Q,
                                                      long long ldq, int K,
                                                      const double* __restrict__ QH,
                                                      double* __restrict__ R_out,
@@ -877,7 +886,7 @@ __global__ void __launch_bounds__(256) k_score_embed(IncView g, const T* __restr
       const long long ra = (long long)g.cpins[a0 + a] * ldq, rb = (long long)g.cpins[a0 + b] * ldq;
       double d = 0.0;
       for (int c = 0; c < K; ++c) {
-        const double diff = __dsub_rn((double)Q[ra + c], (double)Q[rb + c]);
+        const double diff = __dsub_rn(qw<double>(Q[ra + c]), qw<double>(Q[rb + c]));
         d = __dadd_rn(d, __dmul_rn(diff, diff));
       }
       const long long t = (long long)a * k + b;  // increases with the pair order
@@ -902,7 +911,8 @@ __global__ void __launch_bounds__(256) k_score_embed(IncView g, const T* __restr
     for (int c = lane; c < K; c += 32) {
       const double qh = QH[c];
       if (!(qh > 1e-300)) continue;
-      const double diff = __dsub_rn((double)Q[(long long)p * ldq + c], (double)Q[(long long)q * ldq + c]);
+      const double diff =
+          __dsub_rn(qw<double>(Q[(long long)p * ldq + c]), qw<double>(Q[(long long)q * ldq + c]));
       const double r = __ddiv_rn(__dmul_rn(diff, diff), qh);
       if (r > br) br = r, bi = c;
     }
@@ -914,7 +924,7 @@ __global__ void __launch_bounds__(256) k_score_embed(IncView g, const T* __restr
     }
     if (bi >= 0) {
       R = br, av = bi;
-      const bool hi = Q[(long long)p * ldq + bi] >= Q[(long long)q * ldq + bi];
+      const bool hi = qw<double>(Q[(long long)p * ldq + bi]) >= qw<double>(Q[(long long)q * ldq + bi]);
       px = hi ? p : q;
       pn = hi ? q : p;
     }
@@ -1035,6 +1045,60 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
   return HEF_OK;
 }
 
+// BF16 basis: spreads, Q_H partials and ratios in FP32 from BF16 loads;
+// pass 1 gathers the rows (the staged form copies FP32 / FP64 rows) and pass
+// 2 gathers them again (no stored spreads).
+template <int NC>
+hef_status launch_score_bf16(const hef_incidence* inc, const __nv_bfloat16* Q, long long ldq, int K,
+                             int reduce, double* R_out, double* QH_out, int32_t* argvec,
+                             int32_t* pmax, int32_t* pmin, const ScoreWs& w, cudaStream_t st) {
+  using QT = __nv_bfloat16;
+  IncView g = view(inc);
+  GridRed red;
+  red.part = w.part;
+  red.gpart = w.gpart;
+  red.gcnt = w.counter;
+  red.tcnt = w.counter + 63;
+  HEF_LAUNCH("k_score_big1", st, (k_score_big1<float, NC, QT><<<w.bgrid, kThreads, 0, st>>>(
+                                     g, Q, ldq, K, w.bpart, nullptr, 0)));
+  const int g1 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass1<float, NC, QT>, kThreads));
+  HEF_LAUNCH("k_score_pass1", st, (k_score_pass1<float, NC, QT><<<g1, kThreads, 0, st>>>(
+                                      g, Q, ldq, K, red, w.bpart, w.bgrid, w.QH, w.invQH, QH_out,
+                                      w.counter + kWorkSlot, nullptr, 0)));
+  if (reduce == HEF_REDUCE_EMBED) {
+    const int ge = (int)(((long long)(inc->m > 0 ? inc->m : 1) * 32 + kThreads - 1) / kThreads);
+    HEF_LAUNCH("k_score_embed", st, (k_score_embed<float, QT><<<ge, kThreads, 0, st>>>(
+                                        g, Q, ldq, K, w.QH, R_out, argvec, pmax, pmin)));
+    HEF_CHECK_LAUNCH();
+    return HEF_OK;
+  }
+  const int g2 = std::min(w.grid, num_sms() * resident_ctas(k_score_pass2<float, NC, QT>, kThreads));
+  HEF_LAUNCH("k_score_big2", st, (k_score_big2<float, NC, QT><<<w.bgrid, kThreads, 0, st>>>(
+                                     g, Q, ldq, K, reduce, w.QH, w.invQH, R_out, argvec, pmax, pmin)));
+  HEF_LAUNCH("k_score_pass2", st, (k_score_pass2<float, NC, QT><<<g2, kThreads, 0, st>>>(
+                                      g, Q, ldq, K, reduce, w.QH, w.invQH, R_out, argvec, pmax, pmin,
+                                      w.counter + kWorkSlot + 1)));
+  HEF_CHECK_LAUNCH();
+  return HEF_OK;
+}
+
+hef_status dispatch_score_bf16(const hef_incidence* inc, const __nv_bfloat16* Q, long long ldq,
+                               int K, int reduce, double* R_out, double* QH_out, int32_t* argvec,
+                               int32_t* pmax, int32_t* pmin, const ScoreWs& w, cudaStream_t st) {
+  const int nc = (K + 31) / 32;
+#define HEF_SCORE_CASE(N) \
+  if (nc <= N) return launch_score_bf16<N>(inc, Q, ldq, K, reduce, R_out, QH_out, argvec, pmax, pmin, w, st)
+  HEF_SCORE_CASE(1);
+  HEF_SCORE_CASE(2);
+  HEF_SCORE_CASE(4);
+  HEF_SCORE_CASE(5);
+  HEF_SCORE_CASE(8);
+  HEF_SCORE_CASE(12);
+  HEF_SCORE_CASE(16);
+#undef HEF_SCORE_CASE
+  return set_error(HEF_ERR_UNSUPPORTED, "hef_edge_resistance: K must be <= 512");
+}
+
 template <typename T>
 hef_status dispatch_score(const hef_incidence* inc, const T* Q, long long ldq, int K, int reduce,
                           double* R_out, double* QH_out, int32_t* argvec, int32_t* pmax,
@@ -1130,8 +1194,9 @@ extern "C" hef_status hef_edge_resistance_noalloc(const hef_incidence* inc, cons
                      "hef_edge_resistance_noalloc: K = %d outside 1..512 (the fixed %zu-byte "
                      "scratch is sized for K <= 512)",
                      K, kNoallocScratchBytes);
-  if (dtype != HEF_F64 && dtype != HEF_F32)
-    return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: dtype must be HEF_F64 or HEF_F32");
+  if (dtype != HEF_F64 && dtype != HEF_F32 && dtype != HEF_BF16)
+    return set_error(HEF_ERR_INVALID_ARG,
+                     "hef_edge_resistance_noalloc: dtype must be HEF_F64, HEF_F32 or HEF_BF16");
   if (reduce != HEF_REDUCE_MAX && reduce != HEF_REDUCE_SUM && reduce != HEF_REDUCE_EMBED)
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance_noalloc: unknown reduce %d", reduce);
   if (!Q || ldq < K || (inc->m > 0 && !R_out))
@@ -1149,6 +1214,9 @@ extern "C" hef_status hef_edge_resistance_noalloc(const hef_incidence* inc, cons
   if (dtype == HEF_F64)
     return dispatch_score<double>(inc, static_cast<const double*>(Q), ldq, K, reduce, R_out, QH_out,
                                   argvec, pmax, pmin, w, st);
+  if (dtype == HEF_BF16)
+    return dispatch_score_bf16(inc, static_cast<const __nv_bfloat16*>(Q), ldq, K, reduce, R_out,
+                               QH_out, argvec, pmax, pmin, w, st);
   return dispatch_score<float>(inc, static_cast<const float*>(Q), ldq, K, reduce, R_out, QH_out,
                                argvec, pmax, pmin, w, st);
 }
@@ -1167,8 +1235,9 @@ extern "C" hef_status hef_edge_resistance(const hef_incidence* inc, const void* 
   HEF_NVTX("hef_edge_resistance (Algorithm 1 steps 5, 7)");
   if (!inc) return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance: NULL incidence");
   if (K < 1 || K > 512) return set_error(HEF_ERR_UNSUPPORTED, "hef_edge_resistance: need 1 <= K <= 512");
-  if (dtype != HEF_F64 && dtype != HEF_F32)
-    return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance: dtype must be HEF_F64 or HEF_F32");
+  if (dtype != HEF_F64 && dtype != HEF_F32 && dtype != HEF_BF16)
+    return set_error(HEF_ERR_INVALID_ARG,
+                     "hef_edge_resistance: dtype must be HEF_F64, HEF_F32 or HEF_BF16");
   if (reduce != HEF_REDUCE_MAX && reduce != HEF_REDUCE_SUM && reduce != HEF_REDUCE_EMBED)
     return set_error(HEF_ERR_INVALID_ARG, "hef_edge_resistance: unknown reduce %d", reduce);
   if (!Q || ldq < K || (inc->m > 0 && !R_out))
@@ -1182,6 +1251,9 @@ extern "C" hef_status hef_edge_resistance(const hef_incidence* inc, const void* 
   if (dtype == HEF_F64)
     return dispatch_score<double>(inc, static_cast<const double*>(Q), ldq, K, reduce, R_out, QH_out,
                                   argvec, pmax, pmin, w, st);
+  if (dtype == HEF_BF16)
+    return dispatch_score_bf16(inc, static_cast<const __nv_bfloat16*>(Q), ldq, K, reduce, R_out,
+                               QH_out, argvec, pmax, pmin, w, st);
   return dispatch_score<float>(inc, static_cast<const float*>(Q), ldq, K, reduce, R_out, QH_out,
                                argvec, pmax, pmin, w, st);
 }
