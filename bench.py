@@ -408,13 +408,36 @@ def batched_leg(hef, args, dev, rank, timed, max_ranks, world):
     b32.run()
     torch.cuda.synchronize()
     b32.check()
+    # each Krylov form at 16 streams (graph replays), then the autotuner's pick
+    forms = {}
+    for form in (1, 0):
+        hef.set_batch_krylov_form(form)
+        bf = hef.Batch(graphs, k, S, torch.float32, nstreams=16)
+        bf.run()
+        bf.capture()
+        msf, _, _, _ = timed(bf.replay, max(2, args.steps // 4), 1)
+        forms["one_launch" if form else "per_step"] = round(statistics.median(msf), 3)
+        del bf
+    hef.set_batch_krylov_form(1)
     ns, _, tune_ms = b32.autotune()
+    form = hef.batch_krylov_form()
+    # launches and the top kernels of one eager run with the chosen settings
+    hef.trace_read()
+    hef.trace_kernels("k_")
+    l0 = hef.launch_count()
+    b32.run()
+    torch.cuda.synchronize()
+    launches = hef.launch_count() - l0
+    hef.trace_kernels(None)
+    top = {k_: round(v[1], 3) for k_, v in
+           sorted(hef.trace_read().items(), key=lambda kv: -kv[1][1])[:8]}
     b32.capture()
     ms, _, _, _ = timed(b32.replay, args.steps, args.warmup)
     t32 = max_ranks(sum(ms) / len(ms))
     R32 = [o["R"].double().cpu().numpy() for o in b32.out]
     del b32
-    b64 = hef.Batch(graphs, k, S, torch.float64, nstreams=1)
+    # the FP64 form on the same schedule (streams and Krylov form)
+    b64 = hef.Batch(graphs, k, S, torch.float64, nstreams=ns)
     b64.run()
     torch.cuda.synchronize()
     b64.capture()
@@ -427,10 +450,16 @@ def batched_leg(hef, args, dev, rank, timed, max_ranks, world):
     big = r >= 1e-3 * r.max()
     rel = np.abs(a - r) / np.maximum(r, 1e-300)
     norm = max(float(np.abs(x - y).max() / y.max()) for x, y in zip(R32, R64))
+    hef.set_batch_krylov_form(1)
     return {"graphs": len(graphs), "n_total": n_tot, "P_total": P, "k": k, "S": S,
-            "dtype": "f32", "nstreams": ns, "autotune_ms": tune_ms, "ms_per_batch": t32,
+            "dtype": "f32", "nstreams": ns,
+            "krylov_form": "one cooperative launch for all netlists" if form else
+                           "per-step launches per netlist",
+            "ms_per_batch_by_form_16_streams": forms, "launches_per_batch": launches,
+            "top_kernels_ms_eager_batch": top,
+            "autotune_ms": tune_ms, "ms_per_batch": t32,
             "pins_per_s": world * P / (t32 * 1e-3),
-            "fp64_one_stream": {"ms_per_batch": t64, "pins_per_s": world * P / (t64 * 1e-3)},
+            "fp64_same_schedule": {"ms_per_batch": t64, "pins_per_s": world * P / (t64 * 1e-3)},
             "speedup_vs_fp64": t64 / t32,
             "error_vs_fp64": {"max_rel": float(rel[big].max()),
                               "p99_rel": float(np.percentile(rel[r > 0], 99)),

@@ -382,24 +382,32 @@ hef_status hef_edge_resistance_backward(
  * hyperedge (hef_incidence_check's detail and where), so a caller can check
  * every item after the stream has run.
  *
- * Each item runs the whole path (HEF_REDUCE_MAX) as one chain of launches on
- * one stream of a per-device pool of 16 streams; chains of different items
- * overlap.  The call forks from `stream` with an event and joins back, so it
+ * Each item runs the whole path (HEF_REDUCE_MAX) on one stream of a
+ * per-device pool of 16 streams; chains of different items overlap.  The
+ * Krylov stage (hef_set_batch_krylov_form): form 1 (default) runs the k
+ * steps of every item in one cooperative launch (up to 64 items per
+ * launch), each item on a share of the CTAs in proportion to its work
+ * (at least one), with its own grid barriers and partial sums — between the
+ * items' incidence builds and Krylov starts (on their streams) and their
+ * CholQR2 and scoring (on their streams again); form 0 runs each item's
+ * Krylov steps as per-step launches on its stream.  The call forks from `stream` with an event and joins back, so it
  * can be captured in a CUDA graph; the pool is created by the first call on
  * a device, which must happen outside stream capture.  schedule[g] (HOST,
  * nullable) is the pool stream of item g in [0, nstreams); NULL assigns items
- * longest first to the least loaded stream (hef_batch_schedule).  Results are
- * identical, bit for bit, to one hef_build_incidence / hef_krylov_basis /
- * hef_orthonormalize / hef_edge_resistance sequence per item made with the
- * per-step Krylov form (hef_set_krylov_persistent(0)).
+ * longest first to the least loaded stream (hef_batch_schedule).  With form 0
+ * the results are identical, bit for bit, to one hef_build_incidence /
+ * hef_krylov_basis / hef_orthonormalize / hef_edge_resistance sequence per
+ * item made with the per-step Krylov form (hef_set_krylov_persistent(0));
+ * with form 1 they equal them up to the order of floating-point sums.
  * The pool and its fork/join events are shared by every batched call on a
  * device: make batched calls from one host thread at a time.
- * hef_batch_autotune waits for `stream`, then for nstreams = 1, 2, 4, 8, 16
- * (each with its longest-first schedule) captures the batch as a CUDA graph
- * on a private stream and times three replays; it returns the fastest:
- * nstreams_out, schedule_out[G] (HOST), ms_out (nullable, ms per batch).  It
- * writes the items' outputs while timing and must not be called inside a
- * stream capture.
+ * hef_batch_autotune waits for `stream`, then for both Krylov forms and
+ * nstreams = 1, 2, 4, 8, 16 (each with its longest-first schedule) captures
+ * the batch as a CUDA graph on a private stream and times three replays; it
+ * returns the fastest: nstreams_out, schedule_out[G] (HOST), ms_out
+ * (nullable, ms per batch), and leaves the calling thread set to the faster
+ * Krylov form (hef_batch_krylov_form reads it).  It writes the items'
+ * outputs while timing and must not be called inside a stream capture.
  * ---------------------------------------------------------------------- */
 typedef struct hef_batch_item {
   int64_t n, m, P;
@@ -425,6 +433,10 @@ hef_status hef_resistance_batched(const hef_batch_item* items, int32_t G,
                                   int32_t clique_mode, const int32_t* schedule,
                                   int32_t nstreams, void* workspace,
                                   size_t workspace_bytes, void* stream);
+/* Krylov stage of hef_resistance_batched for calls from this thread: 1 = one
+ * cooperative launch for all items (default), 0 = per-step launches per item. */
+hef_status hef_set_batch_krylov_form(int32_t form);
+int32_t hef_batch_krylov_form(void);
 hef_status hef_batch_autotune(const hef_batch_item* items, int32_t G,
                               int32_t k, int32_t S, int32_t dtype,
                               int32_t clique_mode, void* workspace,

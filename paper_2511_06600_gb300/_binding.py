@@ -63,6 +63,8 @@ _SIGS = {
                                        c_sz, c_p]),
     "hef_batch_autotune": (c_i32, [c_p, c_i32, c_i32, c_i32, c_i32, c_i32, c_p, c_sz, c_p, c_p,
                                    c_p, c_p]),
+    "hef_set_batch_krylov_form": (c_i32, [c_i32]),
+    "hef_batch_krylov_form": (c_i32, []),
     "hef_krylov_tape_bytes": (c_sz, [c_p, c_i32, c_i32, c_i32]),
     "hef_set_krylov_persistent": (c_i32, [c_i32]),
     "hef_krylov_basis_tape": (c_i32, [c_p, c_i32, c_i32, c_i32, c_p, c_p, c_p, c_i64, c_p, c_sz,
@@ -767,3 +769,13 @@ def resistance_host(n, eptr, pins, w, x0_clique, x0_star, k, dtype=torch.float32
                                      _dtype_code(dtype), int(clique_mode), _ptr(R_out),
                                      _ptr(workspace), workspace.numel(), _stream(stream)))
     return R_out
+
+
+def set_batch_krylov_form(form):
+    """hef_set_batch_krylov_form for batched calls from this thread: 1 = one
+    cooperative Krylov launch for all items, 0 = per-step launches per item."""
+    _check("hef_set_batch_krylov_form", lib().hef_set_batch_krylov_form(int(form)))
+
+
+def batch_krylov_form():
+    return int(lib().hef_batch_krylov_form())

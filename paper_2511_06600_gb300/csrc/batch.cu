@@ -65,7 +65,7 @@ void item_sizes(const hef_batch_item& it, int k, int S, int dtype, ItemSizes* z)
   hef_incidence shape;  // only n, m, P are read by the size queries
   shape.n = it.n, shape.m = it.m, shape.P = it.P;
   const int K = 2 * k * S;
-  const size_t esz = dtype == HEF_F64 ? 8 : 4;
+  const size_t esz = dtype == HEF_F64 ? 8 : (dtype == HEF_BF16 ? 2 : 4);
   z->ldv = (long long)(((size_t)K * esz + 15) / 16 * 16 / esz);
   z->inc = align256(hef_incidence_workspace_bytes(it.n, it.m, it.P));
   z->kry = align256(hef_krylov_workspace_bytes(&shape, k, S, dtype));
@@ -102,8 +102,8 @@ void lpt_schedule(const hef_batch_item* items, int G, int k, int S, int ns, int3
 
 hef_status check_items(const hef_batch_item* items, int G, int k, int S, int dtype, const char* fn) {
   if (!items || G < 1) return set_error(HEF_ERR_INVALID_ARG, "%s: need G >= 1 items", fn);
-  if (dtype != HEF_F64 && dtype != HEF_F32)
-    return set_error(HEF_ERR_INVALID_ARG, "%s: dtype must be HEF_F64 or HEF_F32", fn);
+  if (dtype != HEF_F64 && dtype != HEF_F32 && dtype != HEF_BF16)
+    return set_error(HEF_ERR_INVALID_ARG, "%s: dtype must be HEF_F64, HEF_F32 or HEF_BF16", fn);
   if (k < 1 || S < 1 || S > 16 || (S & (S - 1)) || 2ll * k * S > 512)
     return set_error(HEF_ERR_UNSUPPORTED, "%s: need k >= 1, S in {1,2,4,8,16}, 2kS <= 512", fn);
   for (int g = 0; g < G; ++g) {
@@ -147,6 +147,75 @@ hef_status run_item(const hef_batch_item& it, int k, int S, int dtype, int cliqu
   return s;
 }
 
+// Krylov stage of the batched form (a per-thread setting, see
+// hef_set_batch_krylov_form): 1 = all hypergraphs' steps in one cooperative
+// launch, 0 = per-step launches of each hypergraph on its stream.
+thread_local int t_batch_form = 1;
+
+// The batched path with the one-launch Krylov stage: per item on its stream,
+// the incidence and the Krylov starts; join; all Krylov steps in one
+// cooperative launch on `stream`; fork; per item, CholQR2 and scoring.
+hef_status run_batch_one_launch(const hef_batch_item* items, int G, int k, int S, int dtype,
+                                int clique_mode, const int32_t* sched, int ns, char* base,
+                                const std::vector<size_t>& off, const std::vector<ItemSizes>& zs,
+                                const std::vector<int>& order, const std::vector<double>& cost,
+                                StreamPool* pool, cudaStream_t stream) {
+  const int K = 2 * k * S;
+  std::vector<hef_incidence*> incs(G, nullptr);
+  hef_status first = HEF_OK;
+  auto join = [&]() -> hef_status {
+    for (int i = 0; i < ns; ++i) {
+      HEF_CHECK_CUDA(cudaEventRecord(pool->join[i], pool->s[i]));
+      HEF_CHECK_CUDA(cudaStreamWaitEvent(stream, pool->join[i], 0));
+    }
+    return HEF_OK;
+  };
+  for (int g : order) {
+    const ItemSizes& z = zs[g];
+    char* p = base + off[g];
+    const hef_batch_item& it = items[g];
+    cudaStream_t st = pool->s[sched[g]];
+    hef_status r = hef_build_incidence(it.n, it.m, it.P, it.eptr, it.pins, it.w, clique_mode, p,
+                                       z.inc, st, &incs[g]);
+    if (!r) r = krylov_batch_start(incs[g], k, S, dtype, it.x0_clique, it.x0_star, p + z.inc, st);
+    if (r && !first) first = r;
+  }
+  if (hef_status r = join()) first = first ? first : r;
+  if (!first) {
+    std::vector<KrylovBatchArg> args(G);
+    for (int g = 0; g < G; ++g)
+      args[g] = KrylovBatchArg{incs[g], base + off[g] + zs[g].inc + zs[g].kry, zs[g].ldv,
+                               base + off[g] + zs[g].inc, cost[g]};
+    first = krylov_batch_steps(args.data(), G, k, S, dtype, stream);
+  }
+  cudaError_t fe = cudaEventRecord(pool->fork, stream);
+  for (int i = 0; i < ns && fe == cudaSuccess; ++i) fe = cudaStreamWaitEvent(pool->s[i], pool->fork, 0);
+  if (fe != cudaSuccess && !first) first = set_error(HEF_ERR_CUDA, "batched call: fork failed");
+  for (int g : order) {
+    const ItemSizes& z = zs[g];
+    char* p = base + off[g];
+    const hef_batch_item& it = items[g];
+    cudaStream_t st = pool->s[sched[g]];
+    if (!first && incs[g]) {
+      void* V = p + z.inc + z.kry;
+      hef_status r = hef_orthonormalize(it.n, K, dtype, V, z.ldv, nullptr, nullptr,
+                                        p + z.inc + z.kry + z.V, z.ortho, st);
+      if (!r)
+        r = hef_edge_resistance(incs[g], V, z.ldv, K, dtype, HEF_REDUCE_MAX, it.R_out, it.QH_out,
+                                it.argvec, it.pmax, it.pmin, p + z.inc + z.kry + z.V + z.ortho,
+                                z.score, st);
+      if (!r && it.status_out &&
+          cudaMemcpyAsync(it.status_out, incs[g]->status, 2 * sizeof(uint32_t),
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        r = set_error(HEF_ERR_CUDA, "batched call: status copy failed");
+      if (r && !first) first = r;
+    }
+    if (incs[g]) hef_free_incidence(incs[g]);
+  }
+  if (hef_status r = join()) first = first ? first : r;
+  return first;
+}
+
 hef_status run_batch(const hef_batch_item* items, int G, int k, int S, int dtype, int clique_mode,
                      const int32_t* sched, int ns, void* workspace, cudaStream_t stream) {
   StreamPool* pool = nullptr;
@@ -168,6 +237,9 @@ hef_status run_batch(const hef_batch_item* items, int G, int k, int S, int dtype
     off[g + 1] = off[g] + item_bytes(zs[g]);
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+  if (t_batch_form == 1)
+    return run_batch_one_launch(items, G, k, S, dtype, clique_mode, sched, ns, base, off, zs, order,
+                                cost, pool, stream);
   // items overlap on the GPU: one-launch Krylov grids could not all be resident
   krylov_allow_persistent(false);
   for (int g : order) {
@@ -263,9 +335,12 @@ extern "C" hef_status hef_batch_autotune(const hef_batch_item* items, int32_t G,
     status = set_error(HEF_ERR_CUDA, "%s: event creation failed", fn);
   std::vector<int32_t> sched(G), best_sched(G);
   float best = -1.0f;
-  int best_ns = 1;
-  for (int ns = 1; ns <= kMaxStreams && status == HEF_OK; ns *= 2) {
-    if (ns > 1 && ns > G) break;
+  int best_ns = 1, best_form = t_batch_form;
+  const int form0 = t_batch_form;
+  for (int cand = 0; cand < 2 * 5 && status == HEF_OK; ++cand) {
+    const int form = cand < 5 ? 1 : 0, ns = 1 << (cand % 5);
+    if (ns > 1 && ns > G) continue;
+    t_batch_form = form;
     lpt_schedule(items, G, k, S, ns, sched.data());
     status = run_batch(items, G, k, S, dtype, clique_mode, sched.data(), ns, workspace, ts);
     if (status) break;
@@ -293,8 +368,9 @@ extern "C" hef_status hef_batch_autotune(const hef_batch_item* items, int32_t G,
     cudaGraphDestroy(graph);
     if (status) break;
     ms /= 3.0f;
-    if (best < 0.0f || ms < best) best = ms, best_ns = ns, best_sched = sched;
+    if (best < 0.0f || ms < best) best = ms, best_ns = ns, best_sched = sched, best_form = form;
   }
+  t_batch_form = status ? form0 : best_form;  // the caller's thread keeps the faster form
   if (e0) cudaEventDestroy(e0);
   if (e1) cudaEventDestroy(e1);
   cudaStreamSynchronize(ts);
@@ -305,3 +381,12 @@ extern "C" hef_status hef_batch_autotune(const hef_batch_item* items, int32_t G,
   if (ms_out) *ms_out = best;
   return HEF_OK;
 }
+
+extern "C" hef_status hef_set_batch_krylov_form(int32_t form) {
+  if (form != 0 && form != 1)
+    return set_error(HEF_ERR_INVALID_ARG, "hef_set_batch_krylov_form: form must be 0 or 1");
+  t_batch_form = form;
+  return HEF_OK;
+}
+
+extern "C" int32_t hef_batch_krylov_form(void) { return t_batch_form; }

@@ -191,6 +191,23 @@ hef_status radix_sort(uint32_t* keys, int32_t* vals, long long N, int bits, Sort
 // every CTA resident at once, so callers that overlap other work on the GPU
 // turn it off.
 void krylov_allow_persistent(bool on);
+
+// The batched form's Krylov stage: per hypergraph, the starts on its own
+// stream (krylov_batch_start, workspace as for hef_krylov_basis); then all
+// k steps of every hypergraph in cooperative launches of up to 64
+// hypergraphs, each on a share of the CTAs in proportion to `cost`
+// (krylov_batch_steps; V, ldv as for hef_krylov_basis).
+struct KrylovBatchArg {
+  const hef_incidence* inc;
+  void* V;
+  long long ldv;
+  void* ws;
+  double cost;
+};
+hef_status krylov_batch_start(const hef_incidence* inc, int k, int S, int dtype, const double* x0c,
+                              const double* x0b, void* ws, cudaStream_t st);
+hef_status krylov_batch_steps(const KrylovBatchArg* items, int G, int k, int S, int dtype,
+                              cudaStream_t st);
 void krylov_force_oversized(bool on);
 
 // Tensor-core (tcgen05, 3xTF32) Gram matrix of an FP32 basis with K + 1 <= 256

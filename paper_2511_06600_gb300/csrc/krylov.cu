@@ -32,7 +32,10 @@
 #include <cuda_bf16.h>
 
 #include <algorithm>
+#include <memory>
 #include <type_traits>
+#include <utility>
+#include <vector>
 
 #include "internal.h"
 
@@ -218,8 +221,9 @@ __device__ __forceinline__ void split2(const T (&r)[2 * S], T (&lo)[S], T (&hi)[
 // working type; only the CTA's sums are widened to FP64 (conversions and
 // FP64 adds run at 1/64 rate on GB300).
 // PMAX caps the butterfly width (values held at once) for register-tight callers.
+// row: the partial's row in part (default: the CTA's index).
 template <int NQ, int S, typename A, int NT = kThreads, int PMAX = 32>
-__device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* part) {
+__device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* part, int row = -1) {
   constexpr int N = NQ * S;
   constexpr int P0 = N > 16 ? 32 : (N > 8 ? 16 : (N > 4 ? 8 : (N > 2 ? 4 : (N > 1 ? 2 : 1))));
   constexpr int P = P0 < PMAX ? P0 : PMAX;
@@ -253,7 +257,7 @@ __device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* p
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     A acc = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][t];
-    part[(size_t)blockIdx.x * N + t] = (double)acc;
+    part[(size_t)(row < 0 ? (int)blockIdx.x : row) * N + t] = (double)acc;
   }
 }
 
@@ -890,22 +894,23 @@ __device__ __forceinline__ bool stopped(const unsigned int* status) {
 // the launch must stop.
 template <int NQ, int S, int NT, typename T>
 __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, double* pub, int ph,
-                                         unsigned int* cnt, unsigned int* status, double* out) {
+                                         unsigned int* cnt, unsigned int* status, double* out,
+                                         int b, int G) {
   constexpr int N = NQ * S;
-  double* buf = part + (size_t)(ph & 1) * gridDim.x * 6 * S;
+  double* buf = part + (size_t)(ph & 1) * G * 6 * S;
   double* res = pub + (size_t)(ph & 1) * 6 * S;
-  block_partials_qs<NQ, S, T, NT, 8>(acc, buf);
+  block_partials_qs<NQ, S, T, NT, 8>(acc, buf, b);
   __shared__ int role;
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const unsigned int old = atomicAdd(cnt, 1u);
-    role = old == (unsigned int)(ph + 1) * gridDim.x - 1u;
+    role = old == (unsigned int)(ph + 1) * G - 1u;
     if (role) __threadfence();
   }
   __syncthreads();
   if (role) {
-    reduce_slots_wide<NT>(buf, gridDim.x, N, out);
+    reduce_slots_wide<NT>(buf, G, N, out);
     for (int t = threadIdx.x; t < N; t += NT) res[t] = out[t];
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -938,10 +943,13 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
   return true;
 }
 
+// The persistent form's work for one hypergraph on CTAs b = 0..G-1 of a
+// launch (G of them meet at its barriers).
 template <typename T, int S, typename TV>
-__global__ void __launch_bounds__(pers_threads<T, S>(), 1)
-    k_krylov_steps(IncView g, ScalView<T> sv, KView<T> kv, int k, TV* __restrict__ V,
-                   long long ldv, double* part, unsigned int* cnt, unsigned int* status) {
+__device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>& sv,
+                                            const KView<T>& kv, int k, TV* __restrict__ V,
+                                            long long ldv, double* part, unsigned int* cnt,
+                                            unsigned int* status, const int b, const int G) {
   constexpr int NT = pers_threads<T, S>();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = (k + 1) * 2 * S;
@@ -956,11 +964,10 @@ __global__ void __launch_bounds__(pers_threads<T, S>(), 1)
   T* s_cfT = reinterpret_cast<T*>(s_itot + 4);
   T* s_nuT = s_cfT + (size_t)nc * 4;
   __shared__ int rng[4];
-  double* pub = part + (size_t)2 * gridDim.x * 6 * S;
+  double* pub = part + (size_t)2 * G * 6 * S;
 
   if (stopped(status)) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int G = gridDim.x, b = blockIdx.x;
   // this CTA's ranges: boundaries at b/G of the weights (incidences + items)
   if (wid < 4) {
     const bool vtx = wid < 2;
@@ -1000,7 +1007,7 @@ __global__ void __launch_bounds__(pers_threads<T, S>(), 1)
         const int e = base + lane;
         edge_item<T, S, true>(g, sv, kv, s_nuT, j, e < e1 ? e : g.m, acc, eofs, epin);
       }
-      if (!pbarrier<3, S, NT>(acc, part, pub, ph++, cnt, status, s_red)) return;
+      if (!pbarrier<3, S, NT>(acc, part, pub, ph++, cnt, status, s_red, b, G)) return;
       for (int t = tid; t < 3 * S; t += NT) s_te[t] = s_red[t];
       __syncthreads();
     }
@@ -1011,7 +1018,7 @@ __global__ void __launch_bounds__(pers_threads<T, S>(), 1)
         const int v = base + lane;
         node_item<T, S, true, TV>(g, sv, kv, s_nuT, j, v < v1 ? v : g.n, acc, V, ldv, vofs, vedg);
       }
-      if (!pbarrier<6, S, NT>(acc, part, pub, ph++, cnt, status, s_red)) return;
+      if (!pbarrier<6, S, NT>(acc, part, pub, ph++, cnt, status, s_red, b, G)) return;
       for (int c = tid; c < 2 * S; c += NT) {
         const int op = c / S, q = c % S;
         double cf[4];
@@ -1046,7 +1053,7 @@ __global__ void __launch_bounds__(pers_threads<T, S>(), 1)
       zero_acc(acc);
       for (int v = v0 + tid; v < v1; v += NT) update_vertex<T, S, true>(g, sv, kv, j, v, cf, acc);
       for (int e = e0 + tid; e < e1; e += NT) update_edge<T, S, true>(g, sv, kv, j, e, cf, acc);
-      if (!pbarrier<2, S, NT>(acc, part, pub, ph++, cnt, status, s_red)) return;
+      if (!pbarrier<2, S, NT>(acc, part, pub, ph++, cnt, status, s_red, b, G)) return;
       for (int c = tid; c < 2 * S; c += NT) {
         const double nu2 = s_red[c];
         const bool alive = s_inv_nu[(size_t)(j - 1) * 2 * S + c] > 0.0 && nu2 > kv.tol * kv.tol;
@@ -1059,6 +1066,43 @@ __global__ void __launch_bounds__(pers_threads<T, S>(), 1)
     }
   }
   for (int v = v0 + tid; v < v1; v += NT) archive_item<T, S, true, TV>(g, kv, s_nuT, k, v, V, ldv);
+}
+
+template <typename T, int S, typename TV>
+__global__ void __launch_bounds__(pers_threads<T, S>(), 1)
+    k_krylov_steps(IncView g, ScalView<T> sv, KView<T> kv, int k, TV* __restrict__ V,
+                   long long ldv, double* part, unsigned int* cnt, unsigned int* status) {
+  krylov_body<T, S, TV>(g, sv, kv, k, V, ldv, part, cnt, status, (int)blockIdx.x, (int)gridDim.x);
+}
+
+// Many hypergraphs in one cooperative launch (the batched form): hypergraph
+// i owns CTAs [cta0[i], cta0[i+1]) and runs the persistent form on them with
+// its own barriers and partials; the table travels as the kernel parameter.
+constexpr int kBatchItems = 64;  // hypergraphs per launch (parameter space)
+template <typename T, typename TV>
+struct KBatchItem {
+  IncView g;
+  ScalView<T> sv;
+  KView<T> kv;
+  TV* V;
+  long long ldv;
+  unsigned int* status;
+};
+template <typename T, typename TV>
+struct KBatch {
+  int nitems, k;
+  int cta0[kBatchItems + 1];
+  KBatchItem<T, TV> it[kBatchItems];
+};
+
+template <typename T, int S, typename TV>
+__global__ void __launch_bounds__(pers_threads<T, S>(), 1)
+    k_krylov_batched(const __grid_constant__ KBatch<T, TV> bt) {
+  int i = 0;
+  while (i + 1 < bt.nitems && (int)blockIdx.x >= bt.cta0[i + 1]) ++i;
+  const KBatchItem<T, TV>& it = bt.it[i];
+  krylov_body<T, S, TV>(it.g, it.sv, it.kv, bt.k, it.V, it.ldv, it.kv.ppart, it.kv.pcount,
+                        it.status, (int)blockIdx.x - bt.cta0[i], bt.cta0[i + 1] - bt.cta0[i]);
 }
 
 inline int blocks_for(long long rows) { return (int)((rows + kThreads - 1) / kThreads); }
@@ -1099,22 +1143,32 @@ thread_local bool t_persistent = true;
 // resident grid, so that its first barrier cannot complete.
 thread_local bool t_force_oversized = false;
 
-template <typename T, int S, typename TV>
-hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, const double* x0b,
-                        TV* V, long long ldv, KView<T>& kv, bool persistent, cudaStream_t st) {
+// The deflated starts x_0 and their norms (the first two launches of every form).
+template <typename T, int S>
+hef_status krylov_start_s(const hef_incidence* inc, const double* x0c, const double* x0b,
+                          const KView<T>& kv, cudaStream_t st) {
   IncView g = view(inc);
   const ScalView<T> sv = scal_view<T>(inc);
-  const long long n = inc->n, m = inc->m;
-  const int grid_all = blocks_for(n + m);
-  const int grid_e = blocks_for(m > 0 ? m : 1);
-  const int grid_n = blocks_for(n);
-  const int grid_upd = blocks_for((n + m + upd_rows<T, S>() - 1) / upd_rows<T, S>());
+  const int grid_all = blocks_for(inc->n + inc->m);
   HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
   // the launches after the first are programmatically dependent on their
   // predecessor (each kernel waits for it before touching shared buffers)
   HEF_LAUNCH("k_start_write", st,
              HEF_CHECK_CUDA(launch_dependent(k_start_write<T, S>, grid_all, kThreads, st, g, sv, kv)));
   HEF_CHECK_LAUNCH();
+  return HEF_OK;
+}
+
+template <typename T, int S, typename TV>
+hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, const double* x0b,
+                        TV* V, long long ldv, KView<T>& kv, bool persistent, cudaStream_t st) {
+  IncView g = view(inc);
+  const ScalView<T> sv = scal_view<T>(inc);
+  const long long n = inc->n, m = inc->m;
+  const int grid_e = blocks_for(m > 0 ? m : 1);
+  const int grid_n = blocks_for(n);
+  const int grid_upd = blocks_for((n + m + upd_rows<T, S>() - 1) / upd_rows<T, S>());
+  if (hef_status s0 = krylov_start_s<T, S>(inc, x0c, x0b, kv, st)) return s0;
   // all steps as one cooperative launch of one CTA per SM (see
   // k_krylov_steps) unless this thread's calls share the GPU with other work
   // (the batched form); if the runtime refuses the grid, three launches per
@@ -1170,19 +1224,27 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   return HEF_OK;
 }
 
+// The Krylov workspace's view (no tape) with its reduction counters zeroed.
+template <typename T>
+hef_status krylov_view(const hef_incidence* inc, int k, int S, void* ws, void* tape, KView<T>* kv,
+                       TapeLayout* tl, cudaStream_t st) {
+  carve_krylov<T>(ws, inc->n, inc->m, k, S, kv);
+  carve_tape(tape, inc->n, inc->m, k, S, sizeof(T), tl);
+  kv->tape_c = static_cast<T*>(tl->uc);
+  kv->tape_b = static_cast<T*>(tl->ub);
+  kv->tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
+  const int ngr = red_groups(blocks_for(2 * inc->n + inc->m));
+  HEF_CHECK_CUDA(cudaMemsetAsync(kv->red.gcnt, 0, (ngr + 1) * sizeof(unsigned int), st));
+  HEF_CHECK_CUDA(cudaMemsetAsync(kv->red.tcnt, 0, sizeof(unsigned int), st));
+  return HEF_OK;
+}
+
 template <typename T, typename TV = T>
 hef_status run_krylov(const hef_incidence* inc, int k, int S, const double* x0c, const double* x0b,
                       void* Vv, long long ldv, void* ws, cudaStream_t st, void* tape = nullptr) {
   KView<T> kv;
-  carve_krylov<T>(ws, inc->n, inc->m, k, S, &kv);
   TapeLayout tl;
-  carve_tape(tape, inc->n, inc->m, k, S, sizeof(T), &tl);
-  kv.tape_c = static_cast<T*>(tl.uc);
-  kv.tape_b = static_cast<T*>(tl.ub);
-  kv.tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
-  const int ngr = red_groups(blocks_for(2 * inc->n + inc->m));
-  HEF_CHECK_CUDA(cudaMemsetAsync(kv.red.gcnt, 0, (ngr + 1) * sizeof(unsigned int), st));
-  HEF_CHECK_CUDA(cudaMemsetAsync(kv.red.tcnt, 0, sizeof(unsigned int), st));
+  if (hef_status s0 = krylov_view<T>(inc, k, S, ws, tape, &kv, &tl, st)) return s0;
   TV* V = static_cast<TV*>(Vv);
   hef_status s;
   switch (S) {
@@ -1234,7 +1296,115 @@ hef_status check_krylov_args(const hef_incidence* inc, int k, int S, int dtype, 
   return HEF_OK;
 }
 
+// Starts of one hypergraph of a batch (the Krylov call up to its steps).
+template <typename T>
+hef_status batch_start(const hef_incidence* inc, int k, int S, const double* x0c,
+                       const double* x0b, void* ws, cudaStream_t st) {
+  KView<T> kv;
+  TapeLayout tl;
+  if (hef_status s0 = krylov_view<T>(inc, k, S, ws, nullptr, &kv, &tl, st)) return s0;
+  switch (S) {
+    case 1: return krylov_start_s<T, 1>(inc, x0c, x0b, kv, st);
+    case 2: return krylov_start_s<T, 2>(inc, x0c, x0b, kv, st);
+    case 4: return krylov_start_s<T, 4>(inc, x0c, x0b, kv, st);
+    case 8: return krylov_start_s<T, 8>(inc, x0c, x0b, kv, st);
+    case 16: return krylov_start_s<T, 16>(inc, x0c, x0b, kv, st);
+    default: return set_error(HEF_ERR_UNSUPPORTED, "batched Krylov: S must be 1, 2, 4, 8 or 16");
+  }
+}
+
+// CTA shares of a launch: at least one per hypergraph, the rest in proportion
+// to the cost (largest remainders first); the shares sum to `total`.
+void cta_shares(const double* cost, int n, int total, int* share) {
+  double sum = 0.0;
+  for (int i = 0; i < n; ++i) sum += cost[i] > 0 ? cost[i] : 0.0;
+  const int spare = total - n;
+  std::vector<std::pair<double, int>> rem;
+  int used = 0;
+  for (int i = 0; i < n; ++i) {
+    const double want = sum > 0 ? spare * (cost[i] > 0 ? cost[i] : 0.0) / sum : 0.0;
+    share[i] = 1 + (int)want;
+    used += share[i];
+    rem.push_back({want - (int)want, i});
+  }
+  std::stable_sort(rem.begin(), rem.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  for (size_t q = 0; q < rem.size() && used < total; ++q, ++used) ++share[rem[q].second];
+}
+
+template <typename T, int S, typename TV>
+hef_status batch_steps_s(const KrylovBatchArg* items, int G, int k, cudaStream_t st) {
+  constexpr int NT = pers_threads<T, S>();
+  const size_t smem = pers_smem<T>(k, S);
+  constexpr size_t kSmemLimit = 227 * 1024;
+  if (smem > kSmemLimit) return set_error(HEF_ERR_UNSUPPORTED, "batched Krylov: k too large");
+  HEF_ENSURE_SMEM((k_krylov_batched<T, S, TV>), smem);
+  int occ = 0;
+  HEF_CHECK_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_krylov_batched<T, S, TV>, NT,
+                                                               smem));
+  // one CTA per SM at most (the partial-sum buffers hold up to num_sms rows)
+  const int total = num_sms() * std::min(std::max(occ, 1), 1);
+  static_assert(sizeof(KBatch<T, TV>) < 32000, "kernel parameter space");
+  auto bt = std::make_unique<KBatch<T, TV>>();
+  for (int g0 = 0; g0 < G; g0 += kBatchItems) {
+    const int nb = std::min(kBatchItems, G - g0);
+    if (nb > total) return set_error(HEF_ERR_UNSUPPORTED, "batched Krylov: more items than CTAs");
+    std::vector<double> cost(nb);
+    std::vector<int> share(nb);
+    for (int i = 0; i < nb; ++i) cost[i] = items[g0 + i].cost;
+    cta_shares(cost.data(), nb, total, share.data());
+    bt->nitems = nb;
+    bt->k = k;
+    bt->cta0[0] = 0;
+    for (int i = 0; i < nb; ++i) {
+      const KrylovBatchArg& a = items[g0 + i];
+      KBatchItem<T, TV>& it = bt->it[i];
+      it.g = view(a.inc);
+      it.sv = scal_view<T>(a.inc);
+      carve_krylov<T>(a.ws, a.inc->n, a.inc->m, k, S, &it.kv);
+      it.kv.tape_c = it.kv.tape_b = nullptr;
+      it.kv.tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
+      it.V = static_cast<TV*>(a.V);
+      it.ldv = a.ldv;
+      it.status = a.inc->status;
+      bt->cta0[i + 1] = bt->cta0[i] + share[i];
+      HEF_CHECK_CUDA(cudaMemsetAsync(it.kv.pcount, 0, 2 * sizeof(unsigned int), st));
+    }
+    const KBatch<T, TV>& arg = *bt;
+    cudaError_t e = cudaSuccess;
+    HEF_LAUNCH("k_krylov_batched", st,
+               e = launch_cooperative_smem(k_krylov_batched<T, S, TV>, bt->cta0[nb], NT, smem, st,
+                                           arg));
+    if (e != cudaSuccess) return set_error(HEF_ERR_CUDA, "k_krylov_batched: %s", cudaGetErrorString(e));
+  }
+  return HEF_OK;
+}
+
+template <typename T, typename TV>
+hef_status batch_steps(const KrylovBatchArg* items, int G, int k, int S, cudaStream_t st) {
+  switch (S) {
+    case 1: return batch_steps_s<T, 1, TV>(items, G, k, st);
+    case 2: return batch_steps_s<T, 2, TV>(items, G, k, st);
+    case 4: return batch_steps_s<T, 4, TV>(items, G, k, st);
+    case 8: return batch_steps_s<T, 8, TV>(items, G, k, st);
+    case 16: return batch_steps_s<T, 16, TV>(items, G, k, st);
+    default: return set_error(HEF_ERR_UNSUPPORTED, "batched Krylov: S must be 1, 2, 4, 8 or 16");
+  }
+}
+
 }  // namespace
+
+hef_status krylov_batch_start(const hef_incidence* inc, int k, int S, int dtype, const double* x0c,
+                              const double* x0b, void* ws, cudaStream_t st) {
+  if (dtype == HEF_F64) return batch_start<double>(inc, k, S, x0c, x0b, ws, st);
+  return batch_start<float>(inc, k, S, x0c, x0b, ws, st);
+}
+
+hef_status krylov_batch_steps(const KrylovBatchArg* items, int G, int k, int S, int dtype,
+                              cudaStream_t st) {
+  if (dtype == HEF_F64) return batch_steps<double, double>(items, G, k, S, st);
+  if (dtype == HEF_BF16) return batch_steps<float, __nv_bfloat16>(items, G, k, S, st);
+  return batch_steps<float, float>(items, G, k, S, st);
+}
 
 void krylov_allow_persistent(bool on) { t_persistent = on; }
 void krylov_force_oversized(bool on) { t_force_oversized = on; }

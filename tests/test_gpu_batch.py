@@ -1,7 +1,9 @@
-"""Batched form (hef_resistance_batched through the C ABI): every item's
-outputs equal, bit for bit, those of the one-hypergraph path on the same
-inputs; the FP64 items match the oracle; graph replay and the autotuner
-leave the results unchanged; a malformed item is flagged alone."""
+"""Batched form (hef_resistance_batched through the C ABI): with per-step
+Krylov launches every item's outputs equal, bit for bit, those of the
+one-hypergraph path on the same inputs; with the one-launch Krylov stage
+(all items' steps in one cooperative launch) they equal them up to the
+order of floating-point sums; the FP64 items match the oracle; graph replay
+after the autotuner reproduces a run; a malformed item is flagged alone."""
 import numpy as np
 import pytest
 import torch
@@ -47,10 +49,14 @@ def test_batched_equals_single_path_bitwise(dtype, nstreams):
     Hs = uneven_netlists()
     graphs, host = batch_inputs(Hs, S)
     b = hef().Batch(graphs, k, S, dtype, nstreams=nstreams)
-    out = b.run()
-    torch.cuda.synchronize()
+    hef().set_batch_krylov_form(0)
+    try:
+        out = b.run()
+        torch.cuda.synchronize()
+    finally:
+        hef().set_batch_krylov_form(1)
     b.check()
-    # the batched form runs the per-step Krylov form; so does the reference
+    # per-step Krylov launches in the batch, and in the reference
     hef().set_krylov_persistent(0)
     try:
         refs = [run_pipeline(H, x0c, x0b, k, dtype) for H, x0c, x0b in host]
@@ -62,6 +68,25 @@ def test_batched_equals_single_path_bitwise(dtype, nstreams):
         for key in ("argvec", "pmax", "pmin"):
             assert np.array_equal(got[key], ref[key]), (g, key)
         assert np.array_equal(got["QH"], ref["QH"]), g
+
+
+@pytest.mark.parametrize("dtype,tol", [(torch.float64, 1e-12), (torch.float32, 1e-5)])
+def test_batched_one_launch_krylov_matches_single_path(dtype, tol):
+    k, S = 5, 2
+    Hs = uneven_netlists()
+    graphs, host = batch_inputs(Hs, S)
+    assert hef().batch_krylov_form() == 1
+    b = hef().Batch(graphs, k, S, dtype, nstreams=4)
+    out = b.run()
+    torch.cuda.synchronize()
+    b.check()
+    again = [o["R"].clone() for o in b.run()]
+    torch.cuda.synchronize()
+    for g, (H, x0c, x0b) in enumerate(host):
+        ref = run_pipeline(H, x0c, x0b, k, dtype)
+        R = out[g]["R"].cpu().numpy()
+        assert rel_errors(R, ref["R"])["normwise"] <= tol, g
+        assert torch.equal(again[g], out[g]["R"]), g  # repeatable bit for bit
 
 
 def test_batched_fp64_matches_oracle():
@@ -82,16 +107,20 @@ def test_batched_graph_replay_and_autotune():
     Hs = uneven_netlists()
     graphs, _ = batch_inputs(Hs, S)
     b = hef().Batch(graphs, k, S, torch.float32, nstreams=2)
-    first = [o["R"].clone() for o in b.run()]
-    ns, sched, ms = b.autotune()
-    assert ns in (1, 2, 4, 8, 16) and len(sched) == len(Hs) and ms > 0
-    assert all(0 <= s < ns for s in sched)
-    for o in b.out:
-        o["R"].zero_()
-    b.capture()
-    for _ in range(2):
-        out = b.replay()
-    torch.cuda.synchronize()
+    try:
+        ns, sched, ms = b.autotune()
+        assert ns in (1, 2, 4, 8, 16) and len(sched) == len(Hs) and ms > 0
+        assert all(0 <= s < ns for s in sched)
+        assert hef().batch_krylov_form() in (0, 1)
+        first = [o["R"].clone() for o in b.run()]
+        for o in b.out:
+            o["R"].zero_()
+        b.capture()
+        for _ in range(2):
+            out = b.replay()
+        torch.cuda.synchronize()
+    finally:
+        hef().set_batch_krylov_form(1)
     for g in range(len(Hs)):
         assert torch.equal(out[g]["R"], first[g]), g
 
