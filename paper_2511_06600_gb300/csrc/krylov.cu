@@ -86,7 +86,7 @@ struct KView {
   double tol;      // breakdown threshold on the D-norm of a new vector
   double* ppart;   // persistent launch: partial sums (2 x grid x 6S; the timeout
                    // test's grid is 2 num_sms), then the published sums (2 x 6S)
-  unsigned int* pcount;  // persistent launch: barrier arrivals, barriers released
+  unsigned int* pcount;  // persistent launch: arrival flags of the CTAs, then the release flag
 };
 
 // ---------------------------------------------------------------- row I/O
@@ -301,11 +301,21 @@ __device__ __forceinline__ void seg_gather(bool valid, int a, int b, Idx idx, Ro
     T part[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) part[i] = 0;
-    for (int t = ba + lane; t < bb; t += 32) {
-      T r0[N];
-      ldrow<T, N, CG>(row(idx(t)), r0);
+    // kSeg records per lane in flight: a 400-pin hyperedge takes 4 dependent
+    // rounds instead of 13 (each lane still adds in entry order)
+    for (int t0 = ba + lane; t0 < bb; t0 += 32 * kSeg) {
+      T r[kSeg][N];
 #pragma unroll
-      for (int i = 0; i < N; ++i) part[i] += r0[i];
+      for (int q = 0; q < kSeg; ++q) {
+        const int t = min(t0 + 32 * q, bb - 1);
+        ldrow<T, N, CG>(row(idx(t)), r[q]);
+      }
+#pragma unroll
+      for (int q = 0; q < kSeg; ++q) {
+        const bool in = t0 + 32 * q < bb;
+#pragma unroll
+        for (int i = 0; i < N; ++i) part[i] += in ? r[q][i] : (T)0;
+      }
     }
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -883,46 +893,62 @@ __device__ __forceinline__ bool stopped(const unsigned int* status) {
   return *reinterpret_cast<const volatile unsigned int*>(status) != 0u;
 }
 
+__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Grid barrier number `ph` with its phase's reduction.  Every CTA writes its
-// partial sums to part[ph & 1] and arrives on cnt[0]; the last CTA to arrive
-// sums all partials in a fixed order (reduce_slots), publishes the N results
-// in pub[ph & 1] and releases the others through cnt[1]; each CTA then copies
-// the results to `out` (shared memory).  Double buffers suffice: a buffer is
-// written again only at barrier ph + 2, which no CTA reaches before every
-// CTA has finished reading barrier ph's results.  Every wait is bounded; on
-// expiry HEF_WAIT_TIMEOUT is set in the status word.  Returns false when
-// the launch must stop.
+// partial sums to part[ph & 1] and then, with a release store, its own
+// arrival flag flags[b] = ph + 1.  CTA 0 reduces: its threads poll the G
+// flags in parallel (acquire loads), it sums all partials in a fixed order
+// (reduce_slots_wide), publishes the N results in pub[ph & 1] and releases
+// the others through flags[G] = ph + 1; each CTA then copies the results to
+// `out` (shared memory).  Double buffers suffice: a buffer is written again
+// only at barrier ph + 2, which no CTA reaches before every CTA has read
+// barrier ph's results (CTA 0 waits for all arrivals of ph + 1 first).  The
+// flags rise monotonically within a launch (zeroed before it).  Every wait is
+// bounded; on expiry HEF_WAIT_TIMEOUT is set in the status word.  Returns
+// false when the launch must stop.
 template <int NQ, int S, int NT, typename T>
 __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, double* pub, int ph,
-                                         unsigned int* cnt, unsigned int* status, double* out,
+                                         unsigned int* flags, unsigned int* status, double* out,
                                          int b, int G) {
   constexpr int N = NQ * S;
   double* buf = part + (size_t)(ph & 1) * G * 6 * S;
   double* res = pub + (size_t)(ph & 1) * 6 * S;
+  const unsigned int want = (unsigned int)ph + 1u;
   block_partials_qs<NQ, S, T, NT, 8>(acc, buf, b);
-  __shared__ int role;
+  __shared__ int go;
   __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned int old = atomicAdd(cnt, 1u);
-    role = old == (unsigned int)(ph + 1) * G - 1u;
-    if (role) __threadfence();
-  }
-  __syncthreads();
-  if (role) {
+  if (threadIdx.x == 0) st_release(flags + b, want);
+  if (b == 0) {
+    // arrivals: thread t watches CTAs t, t + NT, ...
+    int ok = 1;
+    for (int c = threadIdx.x; c < G && ok; c += NT) {
+      unsigned int it = 0;
+      while (ld_acquire(flags + c) < want) {
+        if (++it > kBarIters) {
+          atomicOr(status, HEF_WAIT_TIMEOUT);
+          ok = 0;
+          break;
+        }
+        if ((it & 255u) == 0u && stopped(status)) {
+          ok = 0;
+          break;
+        }
+      }
+    }
+    if (!__syncthreads_and(ok)) return false;
     reduce_slots_wide<NT>(buf, G, N, out);
     for (int t = threadIdx.x; t < N; t += NT) res[t] = out[t];
     __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      atomicExch(cnt + 1, (unsigned int)(ph + 1));
-    }
+    if (threadIdx.x == 0) st_release(flags + G, want);
     return true;
   }
   if (threadIdx.x == 0) {
     unsigned int it = 0;
     int ok = 1;
-    while (ld_acquire(cnt + 1) < (unsigned int)(ph + 1)) {
+    while (ld_acquire(flags + G) < want) {
       if (++it > kBarIters) {
         atomicOr(status, HEF_WAIT_TIMEOUT);
         ok = 0;
@@ -933,18 +959,15 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
         break;
       }
     }
-    __threadfence();
-    role = ok ? 2 : 0;
+    go = ok;
   }
   __syncthreads();
-  if (role != 2) return false;
+  if (!go) return false;
   for (int t = threadIdx.x; t < N; t += NT) out[t] = __ldcg(res + t);
   __syncthreads();
   return true;
 }
 
-// The persistent form's work for one hypergraph on CTAs b = 0..G-1 of a
-// launch (G of them meet at its barriers).
 template <typename T, int S, typename TV>
 __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>& sv,
                                             const KView<T>& kv, int k, TV* __restrict__ V,
@@ -1132,7 +1155,7 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->red.gcnt = c.take<unsigned int>(red_groups((int)maxblk) + 1);
   kv->red.tcnt = c.take<unsigned int>(1);
   kv->ppart = c.take<double>((size_t)2 * num_sms() * 2 * 6 * S + 2 * 6 * S);
-  kv->pcount = c.take<unsigned int>(2);
+  kv->pcount = c.take<unsigned int>((size_t)2 * num_sms() + 1);
   return c.bytes();
 }
 
@@ -1184,7 +1207,7 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_krylov_steps<T, S, TV>, NT, smem) ==
             cudaSuccess &&
         occ >= 1) {
-      HEF_CHECK_CUDA(cudaMemsetAsync(kv.pcount, 0, 2 * sizeof(unsigned int), st));
+      HEF_CHECK_CUDA(cudaMemsetAsync(kv.pcount, 0, (2 * num_sms() + 1) * sizeof(unsigned int), st));
       // the timeout test launches twice the resident grid as a plain launch,
       // so that the first barrier cannot complete and its bounded wait runs out
       const int grid = num_sms() * (t_force_oversized ? 2 : 1);
@@ -1367,7 +1390,7 @@ hef_status batch_steps_s(const KrylovBatchArg* items, int G, int k, cudaStream_t
       it.ldv = a.ldv;
       it.status = a.inc->status;
       bt->cta0[i + 1] = bt->cta0[i] + share[i];
-      HEF_CHECK_CUDA(cudaMemsetAsync(it.kv.pcount, 0, 2 * sizeof(unsigned int), st));
+      HEF_CHECK_CUDA(cudaMemsetAsync(it.kv.pcount, 0, (2 * num_sms() + 1) * sizeof(unsigned int), st));
     }
     const KBatch<T, TV>& arg = *bt;
     cudaError_t e = cudaSuccess;
