@@ -1,6 +1,9 @@
 // Internal host-side declarations shared by the hef translation units.
 #pragma once
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "common.cuh"
 
 // Host handle of a built incidence.  Every pointer is device memory inside
@@ -107,6 +110,21 @@ inline IncView view(const hef_incidence* h) {
 }
 
 hef_status check_stream_ptrs(const void* p, const char* what);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); null when unavailable.
+inline PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+            cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
 
 // The expansion scalars in the arithmetic type of a form (FP64 arrays for
 // double, their FP32 copies for float).

@@ -199,14 +199,7 @@ __device__ __forceinline__ double pivot_rsqrt<double>(double d) {
 // C: arithmetic type; W: the K x 2K work matrix (shared or global memory).
 // fast = 1: report (flag) any kept pivot <= 1e-4 G_jj instead of trusting
 // it.  fast = 0: exact path; runs only when `flag` is set unless `always`.
-// REGP (FP32, K <= kRegK, 512 threads): each panel is eliminated by warp 0 in
-// registers (lane l holds columns j0 + l + 32 q of the panel's rows; the
-// pivot rows' entries travel by shuffles), so a panel costs two CTA barriers
-// instead of two named barriers per pivot.
-constexpr int kRegK = 176;   // columns j0 .. j0 + K + 15 fit 6 per lane
-constexpr int kRegQ = 6;
-
-template <typename C, typename T, int THREADS = 1024, bool REGP = false>
+template <typename C, typename T, int THREADS = 1024>
 __global__ void __launch_bounds__(THREADS) k_chol_aug(const double* __restrict__ G,
                                                    const double* __restrict__ c,
                                                    const C* __restrict__ Aproj, int K, int Kp,
@@ -242,49 +235,7 @@ __global__ void __launch_bounds__(THREADS) k_chol_aug(const double* __restrict__
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j0 = 0; j0 < K; j0 += kPB) {
     const int jend = min(K, j0 + kPB);
-    if (REGP) {
-      if (wid == 0) {
-        float rw[kPB][kRegQ];
-#pragma unroll
-        for (int p = 0; p < kPB; ++p)
-#pragma unroll
-          for (int q = 0; q < kRegQ; ++q) {
-            const int col = j0 + lane + 32 * q;
-            rw[p][q] = (j0 + p < K && col < W2) ? (float)W[(size_t)(j0 + p) * W2 + col] : 0.0f;
-          }
-#pragma unroll
-        for (int p = 0; p < kPB; ++p) {
-          const int j = j0 + p;
-          if (j < K) {  // warp-uniform
-            const float d = __shfl_sync(0xffffffffu, rw[p][0], p);  // (j, j): lane p
-            const int kj = (ref[j] > (C)0 && d > (float)thr_keep[j]) ? 1 : 0;
-            const float pinv = kj ? pivot_rsqrt<float>(d) : 0.0f;
-            if (lane == 0) {
-              if (fast && kj && d <= (float)thr_near[j]) near_def = 1;
-              o.kept[j] = kj;
-              pk[p] = kj;
-            }
-#pragma unroll
-            for (int q = 0; q < kRegQ; ++q) rw[p][q] *= pinv;  // dropped rows become zero
-            if (kj) {
-#pragma unroll
-              for (int i = p + 1; i < kPB; ++i) {
-                const float r = __shfl_sync(0xffffffffu, rw[p][0], i);  // scaled (j, j0 + i)
-#pragma unroll
-                for (int q = 0; q < kRegQ; ++q) rw[i][q] -= r * rw[p][q];
-              }
-            }
-          }
-        }
-#pragma unroll
-        for (int p = 0; p < kPB; ++p)
-#pragma unroll
-          for (int q = 0; q < kRegQ; ++q) {
-            const int col = j0 + lane + 32 * q;
-            if (j0 + p < K && col < W2) W[(size_t)(j0 + p) * W2 + col] = (C)rw[p][q];
-          }
-      }
-    } else if (wid < kPB) {
+    if (wid < kPB) {
       const int i = j0 + wid;
       C* rowi = W + (size_t)i * W2;
       for (int j = j0; j < jend; ++j) {
@@ -396,6 +347,246 @@ __global__ void __launch_bounds__(THREADS) k_chol_aug(const double* __restrict__
     for (int j = 0; j < K; ++j) r += o.kept[j];
     *o.rank = r;
     if (fast) o.flag[0] = near_def;
+  }
+}
+
+// The FP32 form's first-pass factorisation when [A | I] fits in shared memory
+// (Kq = K rounded up to 4, Kq <= kPanelMaxK; the padded pivots are dropped):
+// the same elimination, outputs and pivot rules as k_chol_aug with fast = 1,
+// organised so that one CTA keeps all its warps busy.  Per panel of kCP
+// pivots:
+//  (a) warp 0 eliminates [D | I] in registers, D the panel's diagonal block
+//      (lane c < 16 holds column c of D, lane 16 + c column c of I): R11 and
+//      the lower triangular T with T D = R11, i.e. the panel's row operations;
+//  (b) all threads apply T to the panel rows' other live columns
+//      [jend, Kq + j0) (the right half's block at Kq + j0 becomes T itself);
+//  (c) rows i >= jend take the rank-kCP update on their live columns
+//      [jend, Kq + jend) in 4 x 4 tiles (multipliers R[p][i] read as float4).
+// R^-1 leaves transposed through the left half of W (skewed 32 x 32 blocks,
+// no bank conflicts on either side) so that its global stores coalesce.
+constexpr int kCP = 16;
+constexpr int kPanelThreads = 512;
+constexpr int kPanelMaxK = 160;
+
+inline size_t panel_smem(int K) {
+  const size_t Kq = (size_t)((K + 3) & ~3);
+  return Kq * 2 * Kq * sizeof(float);
+}
+inline bool panel_supported(int K) { return ((K + 3) & ~3) <= kPanelMaxK; }
+
+template <typename T>  // float: R^-1 and mu of the FP32 and BF16 forms
+__global__ void __launch_bounds__(kPanelThreads, 1) k_chol_panels(const double* __restrict__ G,
+                                                              const double* __restrict__ c,
+                                                              const float* __restrict__ Aproj, int K,
+                                                              int Kp, double n, double tol, CholOut o) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  __shared__ float ref[kPanelMaxK], thr_keep[kPanelMaxK], thr_near[kPanelMaxK];
+  __shared__ float Ts[kCP][kCP];
+  __shared__ int keptS[kPanelMaxK];
+  __shared__ int near_def;
+  float* W = reinterpret_cast<float*>(sm_raw);
+  const int Kq = (K + 3) & ~3, W2 = 2 * Kq;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  // [A | I]: every load of A issued before the first store (A is L2-resident)
+  {
+    constexpr int kIt = (kPanelMaxK * kPanelMaxK / 4 + kPanelThreads - 1) / kPanelThreads;
+    const int nq = Kq / 4;
+    if ((K & 3) == 0) {  // rows of A are whole float4s
+      float4 buf[kIt];
+#pragma unroll
+      for (int t = 0; t < kIt; ++t) {
+        const int idx = tid + t * kPanelThreads;
+        buf[t] = idx < K * nq ? reinterpret_cast<const float4*>(Aproj)[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int t = 0; t < kIt; ++t) {
+        const int idx = tid + t * kPanelThreads;
+        if (idx < K * nq) reinterpret_cast<float4*>(W + (size_t)(idx / nq) * W2)[idx % nq] = buf[t];
+      }
+    } else {
+      for (int idx = tid; idx < Kq * Kq; idx += kPanelThreads) {
+        const int i = idx / Kq, j = idx % Kq;
+        W[(size_t)i * W2 + j] = (i < K && j < K) ? Aproj[(size_t)i * K + j] : 0.0f;
+      }
+    }
+    // right half: the identity on rows < K
+    for (int idx = tid; idx < Kq * nq; idx += kPanelThreads) {
+      const int i = idx / nq, q = idx % nq, d = i - 4 * q;
+      const float one = i < K ? 1.0f : 0.0f;
+      reinterpret_cast<float4*>(W + (size_t)i * W2 + Kq)[q] =
+          make_float4(d == 0 ? one : 0.f, d == 1 ? one : 0.f, d == 2 ? one : 0.f, d == 3 ? one : 0.f);
+    }
+    for (int i = tid; i < Kq; i += kPanelThreads) {
+      const double gi = i < K ? G[(size_t)i * K + i] : 0.0;
+      ref[i] = (float)gi;
+      thr_keep[i] = (float)(tol * gi);
+      thr_near[i] = (float)(1e-4 * gi);
+    }
+    if (tid == 0) near_def = 0;
+  }
+  __syncthreads();
+  for (int j0 = 0; j0 < Kq; j0 += kCP) {
+    const int np = min(kCP, Kq - j0), jend = j0 + np;  // np is a multiple of 4
+    // (a)
+    if (wid == 0) {
+      const int col = lane & 15;
+      const bool left = lane < 16;
+      float v[kCP];
+#pragma unroll
+      for (int r = 0; r < kCP; ++r)
+        v[r] = left ? ((r < np && col < np) ? W[(size_t)(j0 + r) * W2 + j0 + col] : 0.0f)
+                    : (r == col ? 1.0f : 0.0f);
+      const int jl = j0 + col;
+      const float my_ref = jl < Kq ? ref[jl] : 0.0f;
+      const float my_keep = jl < Kq ? thr_keep[jl] : 0.0f;
+      const float my_near = jl < Kq ? thr_near[jl] : 0.0f;
+      unsigned kept_mask = 0;
+      int near = 0;
+#pragma unroll
+      for (int p = 0; p < kCP; ++p) {
+        if (p < np) {  // warp-uniform
+          const float d = __shfl_sync(0xffffffffu, v[p], p);
+          const float rf = __shfl_sync(0xffffffffu, my_ref, p);
+          const float tk = __shfl_sync(0xffffffffu, my_keep, p);
+          const float tn = __shfl_sync(0xffffffffu, my_near, p);
+          const int kj = (j0 + p < K && rf > 0.0f && d > tk) ? 1 : 0;
+          near |= (kj && d <= tn) ? 1 : 0;
+          kept_mask |= (unsigned)kj << p;
+          v[p] *= kj ? rsqrtf(d) : 0.0f;  // R refined by the second CholQR pass
+          if (kj) {
+#pragma unroll
+            for (int i = p + 1; i < kCP; ++i) {
+              const float r = __shfl_sync(0xffffffffu, v[p], i);  // scaled (j0 + p, j0 + i)
+              v[i] -= r * v[p];
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < kCP; ++r) {
+        if (left) {
+          if (r < np && col < np) W[(size_t)(j0 + r) * W2 + j0 + col] = r <= col ? v[r] : 0.0f;
+        } else {
+          Ts[r][col] = v[r];
+          if (r < np && col < np) W[(size_t)(j0 + r) * W2 + Kq + j0 + col] = v[r];
+        }
+      }
+      if (lane < np && j0 + lane < K) {
+        const int kj = (int)((kept_mask >> lane) & 1u);
+        keptS[j0 + lane] = kj;
+        o.kept[j0 + lane] = kj;
+      }
+      if (lane == 0 && near) near_def = 1;
+    }
+    __syncthreads();
+    // (b) two items (row r, 4 columns) per thread at most: np (Kq - np) / 4 <= 2 x 512
+    {
+      const int ncg = (Kq - np) / 4;
+      const int nit = np * ncg;
+      float4 res[2];
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const int it = tid + sl * kPanelThreads;
+        res[sl] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (it < nit) {
+          const int r = it / ncg, cg = it % ncg;
+          const float* base = W + (size_t)j0 * W2 + jend + 4 * cg;
+          for (int p = 0; p <= r; ++p) {
+            const float t = Ts[r][p];
+            const float4 x = *reinterpret_cast<const float4*>(base + (size_t)p * W2);
+            res[sl].x += t * x.x, res[sl].y += t * x.y, res[sl].z += t * x.z, res[sl].w += t * x.w;
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int sl = 0; sl < 2; ++sl) {
+        const int it = tid + sl * kPanelThreads;
+        if (it < nit) {
+          const int r = it / ncg, cg = it % ncg;
+          *reinterpret_cast<float4*>(W + (size_t)(j0 + r) * W2 + jend + 4 * cg) = res[sl];
+        }
+      }
+    }
+    __syncthreads();
+    // (c)
+    {
+      const int ncg = Kq / 4;
+      const int nit = (Kq - jend) / 4 * ncg;
+      for (int it = tid; it < nit; it += kPanelThreads) {
+        const int i0 = jend + 4 * (it / ncg), c0 = jend + 4 * (it % ncg);
+        float4 acc[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[r] = *reinterpret_cast<const float4*>(W + (size_t)(i0 + r) * W2 + c0);
+#pragma unroll
+        for (int p = 0; p < kCP; ++p) {
+          if (p < np) {
+            const float* rowp = W + (size_t)(j0 + p) * W2;
+            const float4 a = *reinterpret_cast<const float4*>(rowp + i0);
+            const float4 b = *reinterpret_cast<const float4*>(rowp + c0);
+            const float am[4] = {a.x, a.y, a.z, a.w};
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+              acc[r].x -= am[r] * b.x, acc[r].y -= am[r] * b.y;
+              acc[r].z -= am[r] * b.z, acc[r].w -= am[r] * b.w;
+            }
+          }
+        }
+#pragma unroll
+        for (int r = 0; r < 4; ++r) *reinterpret_cast<float4*>(W + (size_t)(i0 + r) * W2 + c0) = acc[r];
+      }
+    }
+    __syncthreads();
+  }
+  // outputs: R (FP64, row j: columns i >= j), then R^-1 = (R^-T)^T by way of
+  // the left half, mu, rank, flag
+  if (o.R)
+    for (int idx = tid; idx < K * K; idx += kPanelThreads) {
+      const int j = idx / K, i = idx % K;
+      o.R[idx] = j <= i ? (double)W[(size_t)j * W2 + i] : 0.0;
+    }
+  __syncthreads();
+  {
+    // block (bi, bj), bi <= bj; lane l moves (i, j) = (32 bi + (l + t) % 32,
+    // 32 bj + l): bank (W2 + 1) l + const on the read, W2 ((l + t) % 32) + l
+    // on the write, distinct over the warp (W2 even)
+    const int nb = (Kq + 31) / 32;
+    const int npair = nb * (nb + 1) / 2;
+    for (int pr = wid; pr < npair; pr += kPanelThreads / 32) {
+      int bi = 0, rem = pr;
+      while (rem >= nb - bi) rem -= nb - bi, ++bi;
+      const int bj = bi + rem;
+      const int j = 32 * bj + lane;
+      for (int t = 0; t < 32; ++t) {
+        const int i = 32 * bi + ((lane + t) & 31);
+        if (i < Kq && j < Kq && i <= j) W[(size_t)i * W2 + j] = W[(size_t)j * W2 + Kq + i];
+      }
+    }
+  }
+  __syncthreads();
+  T* Rinv = static_cast<T*>(o.Rinv);
+  T* mu = static_cast<T*>(o.mu);
+  // Kp is a multiple of 8: four columns of R^-1 per store
+  const int kp4 = Kp / 4;
+  for (int idx = tid; idx < Kp * kp4; idx += kPanelThreads) {
+    const int i = idx / kp4, j0 = 4 * (idx % kp4);
+    float x[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int j = j0 + u;
+      x[u] = (i < K && j < K && i <= j) ? W[(size_t)i * W2 + j] : 0.0f;
+    }
+    reinterpret_cast<float4*>(Rinv)[idx] = make_float4(x[0], x[1], x[2], x[3]);
+  }
+  for (int i = tid; i < Kp; i += kPanelThreads) mu[i] = i < K ? (T)(c[i] / n) : (T)0;
+  if (wid == 0) {
+    int r = 0;
+    for (int j = lane; j < K; j += 32) r += keptS[j];
+    r = __reduce_add_sync(0xffffffffu, r);
+    if (lane == 0) {
+      *o.rank = r;
+      o.flag[0] = near_def;
+    }
   }
 }
 
@@ -621,10 +812,9 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
   const size_t fast_smem = (size_t)K * 2 * K * sizeof(float);
   const bool fast_ok = sizeof(T) == 4;
   const bool fast_in_smem = fast_ok && fast_smem <= 200 * 1024;
-  if (fast_in_smem) {
-    HEF_ENSURE_SMEM((k_chol_aug<float, T>), fast_smem);
-    HEF_ENSURE_SMEM((k_chol_aug<float, T, 512, true>), fast_smem);
-  }
+  const bool panels = fast_ok && panel_supported(K);
+  if (fast_in_smem) HEF_ENSURE_SMEM((k_chol_aug<float, T>), fast_smem);
+  if (panels) HEF_ENSURE_SMEM(k_chol_panels<T>, panel_smem(K));
   const double tol = sizeof(T) == 8 ? 1e-12 : 1e-5;
   // second pass: the first-order factor of the near-identity Gram is exact to
   // O(|E|^2); a BF16 basis leaves |E| near its rounding (~4e-3), where the
@@ -652,10 +842,9 @@ hef_status run_ortho(long long n, int K, T* V, long long ldv, double* R_out, int
       HEF_LAUNCH("k_gram_project", st, k_gram_project<<<stride_grid((long long)K * K, 2), kThreads, 0,
                                                          st>>>(w.G, w.c, K, (double)n, w.A64, w.A32));
       if (fast_ok) {
-        if (fast_in_smem && K <= kRegK) {
-          HEF_LAUNCH("k_chol_aug", st, (k_chol_aug<float, T, 512, true><<<1, 512, fast_smem, st>>>(
-                                           w.G, w.c, w.A32, K, Kp, (double)n, tol, nullptr, 1, 1, 0,
-                                           o)));
+        if (panels) {
+          HEF_LAUNCH("k_chol_panels", st, k_chol_panels<T><<<1, kPanelThreads, panel_smem(K), st>>>(
+                                              w.G, w.c, w.A32, K, Kp, (double)n, tol, o));
         } else {
           HEF_LAUNCH("k_chol_aug", st, k_chol_aug<float, T><<<1, 1024, fast_in_smem ? fast_smem : 0, st>>>(
                                            w.G, w.c, w.A32, K, Kp, (double)n, tol,

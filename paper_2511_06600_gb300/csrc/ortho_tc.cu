@@ -21,6 +21,8 @@
 // rounds Q to BF16 on the store.
 #include <cuda_bf16.h>
 
+#include <cstring>
+
 #include "internal.h"
 #include "umma.cuh"
 
@@ -566,7 +568,415 @@ __global__ void __launch_bounds__(kApThreads, 1) k_apply_tc(ApplyTcArgs a) {
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
+// ---------------------------------------------------------------- TMA pipelines
+//
+// The FP32 basis with a 16-byte aligned row pitch: tensor-map loads feed a
+// warp-specialised pipeline, so that no warp waits for its own global loads.
+//   warp 0            one thread issues the TMA loads into a ring of stages
+//   warp 1            one thread issues the MMAs (tcgen05) and commits
+//   converter warps   hi/lo TF32 split of each landed stage
+//   epilogue warps    TMEM -> registers -> global memory (apply)
+// Hand-offs are mbarriers; every wait is bounded (a timeout sets *err, and
+// each role still waits for the copies and MMAs it issued before the CTA
+// leaves).
+
+constexpr int kTmThreads = 512;
+constexpr int kTmConvFirst = 2;  // apply: warps 2..7 split, warps 8..15 drain
+constexpr int kTmConvWarps = 6;
+constexpr int kTmEpiFirst = 8;
+constexpr int kTmEpiWarps = 8;
+constexpr uint32_t kATile = 128u * 128u;  // one apply A tile: 128 rows x 32 values
+
+struct ApplyTmaArgs {
+  float* V;
+  long long ldv;
+  int n, K, Kq, Kd;
+  const float* RtH;
+  const float* RtL;
+  const float* muR;
+  int* err;
+};
+
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
+  return __all_sync(0xffffffffu, mbar_wait(bar, parity, kWaitIters));
+}
+
+// Q = (V - 1 mu^T) Rinv in place, 128-row tiles (as k_apply_tc, RESB): the
+// A tile of K block ka is the box (32 values from 32 ka) x (128 rows) of V,
+// loaded K-major with the 128-byte swizzle, i.e. already in the MMA's
+// layout; the converters round it to its hi part in place and write the lo
+// part beside it.  Two TMEM accumulators: tile t drains while tile t + 1
+// accumulates.  NS stages of A.
+template <int NS>
+__global__ void __launch_bounds__(kTmThreads, 1)
+    k_apply_tma(ApplyTmaArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int nka = a.Kd / 32;
+  auto brows = [&](int ka) { return a.Kq - 32 * ka; };
+  auto boff = [&](int ka) { return (uint32_t)(ka * a.Kq - 16 * ka * (ka - 1)) * 256u; };
+  unsigned char* abase = base + boff(nka);  // stage s: hi at 2 s kATile, lo after it
+  uint64_t* full = reinterpret_cast<uint64_t*>(abase + 2u * NS * kATile);  // NS: landed
+  uint64_t* conv = full + NS;     // NS: split
+  uint64_t* empty = conv + NS;    // NS: MMAs done with the stage
+  uint64_t* tfull = empty + NS;   // 2: accumulator complete
+  uint64_t* tempty = tfull + 2;   // 2: accumulator drained
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  uint32_t ncols = 32;
+  while (ncols < 2u * (uint32_t)a.Kq) ncols <<= 1;
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&conv[q], kTmConvWarps);
+      mbar_init(&empty[q], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], kTmEpiWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // resident B tiles: tile ka holds rows 32 ka .. Kq - 1 of Rinv^T, basis
+  // values [32 ka, 32 ka + 32)
+  for (int ka = 0; ka < nka; ++ka) {
+    unsigned char* bhi = base + boff(ka);
+    unsigned char* blo = bhi + (uint32_t)brows(ka) * 128u;
+    const int c0 = ka * 32;
+    for (int f = tid; f < brows(ka) * 8; f += kTmThreads) {
+      const int jr = f >> 3, q = f & 7;
+      const size_t src = (size_t)(c0 + jr) * a.Kd + c0 + 4 * q;
+      const uint32_t off = sw128_offset(jr, 4 * q);
+      *reinterpret_cast<float4*>(bhi + off) = __ldg(reinterpret_cast<const float4*>(a.RtH + src));
+      *reinterpret_cast<float4*>(blo + off) = __ldg(reinterpret_cast<const float4*>(a.RtL + src));
+    }
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const int ntiles = (a.n + 127) / 128;
+  bool ok = true;
+  if (warp == 0) {
+    if (lane == 0) {
+      int g = 0;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+        for (int ka = 0; ka < nka; ++ka) {
+          const int s = g % NS;
+          if (g >= NS && !(ok = mbar_wait(&empty[s], (uint32_t)((g / NS) - 1) & 1u, kWaitIters))) break;
+          mbar_arrive_expect_tx(&full[s], kATile);
+          tma_load_2d(abase + 2u * s * kATile, &tmap, 32 * ka, tile * 128, &full[s]);
+          ++g;
+        }
+      // copies still landing finish before the CTA may leave
+      for (int q = g - NS > 0 ? g - NS : 0; q < g; ++q)
+        mbar_wait(&full[q % NS], (uint32_t)(q / NS) & 1u, kWaitIters);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      int g = 0, lt = 0;
+      for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+        const int b = lt & 1;
+        if (lt >= 2 && !(ok = mbar_wait(&tempty[b], (uint32_t)((lt >> 1) - 1) & 1u, kWaitIters))) break;
+        tc_fence_after();
+        const uint32_t dbase = tmem + (uint32_t)(b * a.Kq);
+        for (int ka = 0; ka < nka; ++ka, ++g) {
+          const int s = g % NS;
+          if (!(ok = mbar_wait(&conv[s], (uint32_t)(g / NS) & 1u, kWaitIters))) break;
+          tc_fence_after();
+          const int c0 = ka * 32, nr = brows(ka);
+          const uint32_t sah = smem_u32(abase + 2u * s * kATile), sal = sah + kATile;
+          const uint32_t sbh = smem_u32(base + boff(ka)), sbl = sbh + (uint32_t)nr * 128u;
+          const uint32_t id = idesc_tf32(128, nr);
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks) {
+            const uint32_t ko = (uint32_t)ks * 32u;
+            const uint32_t d = dbase + (uint32_t)c0;
+            const uint32_t acc = (ka > 0 || ks > 0) ? 1u : 0u;  // block 0 starts every column
+            mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbh + ko), id, acc);
+            mma_tf32(d, desc_k_sw128(sah + ko), desc_k_sw128(sbl + ko), id, 1u);
+            mma_tf32(d, desc_k_sw128(sal + ko), desc_k_sw128(sbh + ko), id, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!ok) break;
+        mma_commit(&tfull[b]);
+      }
+      // MMAs in flight finish before TMEM may be released
+      if (g > 0) mbar_wait(&empty[(g - 1) % NS], (uint32_t)((g - 1) / NS) & 1u, kWaitIters);
+    }
+  } else if (warp < kTmEpiFirst) {
+    const int ctid = tid - kTmConvFirst * 32;
+    int g = 0;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x)
+      for (int ka = 0; ka < nka; ++ka, ++g) {
+        const int s = g % NS;
+        if (!(ok = warp_wait(&full[s], (uint32_t)(g / NS) & 1u))) break;
+        float4* hi = reinterpret_cast<float4*>(abase + 2u * s * kATile);
+        float4* lo = reinterpret_cast<float4*>(abase + (2u * s + 1u) * kATile);
+        for (int f = ctid; f < (int)(kATile / 16); f += kTmConvWarps * 32) {
+          const float4 x = hi[f];
+          const float4 h = make_float4(tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w));
+          hi[f] = h;
+          lo[f] = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+        }
+        fence_async_smem();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&conv[s]);
+      }
+  } else {
+    // warp w drains TMEM lanes 32 (w mod 4) ..; the two warps of a lane
+    // quarter take alternate groups of 8 columns
+    const int q4 = warp & 3, half = (warp - kTmEpiFirst) >> 2;
+    int lt = 0;
+    for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++lt) {
+      const int b = lt & 1;
+      if (!(ok = warp_wait(&tfull[b], (uint32_t)(lt >> 1) & 1u))) break;
+      tc_fence_after();
+      const long long row = (long long)tile * 128 + q4 * 32 + lane;
+      for (int c8 = half; c8 < a.Kq / 8; c8 += 2) {
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(q4 * 32) << 16) + (uint32_t)(b * a.Kq + c8 * 8), v);
+        tmem_wait_ld();
+        const int j0 = c8 * 8;
+        if (row < a.n) {
+          float* dst = a.V + row * a.ldv + j0;
+          if (j0 + 7 < a.K) {
+            const float4 m0 = __ldg(reinterpret_cast<const float4*>(a.muR + j0));
+            const float4 m1 = __ldg(reinterpret_cast<const float4*>(a.muR + j0 + 4));
+            reinterpret_cast<float4*>(dst)[0] = make_float4(v[0] - m0.x, v[1] - m0.y, v[2] - m0.z, v[3] - m0.w);
+            reinterpret_cast<float4*>(dst)[1] = make_float4(v[4] - m1.x, v[5] - m1.y, v[6] - m1.z, v[7] - m1.w);
+          } else {
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+              if (j0 + u < a.K) dst[u] = v[u] - a.muR[j0 + u];
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tempty[b]);
+    }
+  }
+  if (!ok) atomicExch(a.err, 1);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
+struct GramTmaArgs {
+  int n, K, Kq, ncb;
+  int rows_per_cta;
+  int gmask[4];
+  float* part;
+  int* err;
+};
+
+// G_aug = [V 1]^T [V 1] (as k_gram_tc, NB <= 2 blocks of 128 basis rows).  A
+// 32-row slab of V lands as ncb boxes of 32 values x 32 rows (128-byte
+// swizzle) in a ring of NR raw stages; the converter warps (2..15) transpose
+// it into the hi/lo K-major tiles of one of two tile stages (lanes run along
+// the slab rows: conflict-free on both sides), adding the ones column.
+template <int NB, int NR>
+__global__ void __launch_bounds__(kTmThreads, 1)
+    k_gram_tma(GramTmaArgs a, const __grid_constant__ CUtensorMap tmap) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* base = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  constexpr int Mpad = NB * 128;
+  constexpr uint32_t tile_bytes = (uint32_t)Mpad * 128u;
+  constexpr int kConv = kTmThreads / 32 - kTmConvFirst;  // converter warps
+  const uint32_t raw_bytes = (uint32_t)a.ncb * 4096u;
+  unsigned char* tiles = base;                            // stage u: hi, lo
+  unsigned char* raw = base + 4u * tile_bytes;            // NR stages
+  uint64_t* rfull = reinterpret_cast<uint64_t*>(raw + (size_t)NR * raw_bytes);
+  uint64_t* rempty = rfull + NR;   // NR: converted out of
+  uint64_t* tfull = rempty + NR;   // 2: tile stage written
+  uint64_t* tempty = tfull + 2;    // 2: MMAs done with the tile stage
+  uint64_t* done = tempty + 2;     // 1: every MMA complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(done + 1);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int gmask = a.gmask[blockIdx.y];
+  int toff[NB];
+  int used = 0;
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    toff[b] = used;
+    if ((gmask >> b) & 1) used += a.Kq - 128 * b;
+  }
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)used) ncols <<= 1;
+  if (warp == 0) tmem_alloc(tmem_slot, ncols);
+  if (tid == 0) {
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+      mbar_init(&rfull[q], 1);
+      mbar_init(&rempty[q], kConv);
+    }
+    for (int u = 0; u < 2; ++u) {
+      mbar_init(&tfull[u], kConv);
+      mbar_init(&tempty[u], 1);
+    }
+    mbar_init(done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // basis rows [Kq, Mpad) of the tiles stay zero
+  for (int q = 0; q < 4; ++q) {
+    unsigned char* tile = tiles + (size_t)q * tile_bytes;
+    for (int e = tid; e < (Mpad - a.Kq) * 32; e += kTmThreads)
+      *reinterpret_cast<float*>(tile + sw128_offset(a.Kq + e / 32, e % 32)) = 0.f;
+  }
+  fence_async_smem();
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const long long r0 = (long long)blockIdx.x * a.rows_per_cta;
+  const long long r1 = min((long long)a.n, r0 + a.rows_per_cta);
+  const int nslab = r1 > r0 ? (int)((r1 - r0 + kSlab - 1) / kSlab) : 0;
+  bool ok = true;
+  if (warp == 0) {
+    if (lane == 0) {
+      int t = 0;
+      for (; t < nslab; ++t) {
+        const int s = t % NR;
+        if (t >= NR && !(ok = mbar_wait(&rempty[s], (uint32_t)((t / NR) - 1) & 1u, kWaitIters))) break;
+        mbar_arrive_expect_tx(&rfull[s], raw_bytes);
+        for (int cb = 0; cb < a.ncb; ++cb)
+          tma_load_2d(raw + (size_t)s * raw_bytes + cb * 4096u, &tmap, 32 * cb, (int)(r0 + (long long)t * kSlab),
+                      &rfull[s]);
+      }
+      for (int q = t - NR > 0 ? t - NR : 0; q < t; ++q)
+        mbar_wait(&rfull[q % NR], (uint32_t)(q / NR) & 1u, kWaitIters);
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int t = 0; t < nslab; ++t) {
+        const int u = t & 1;
+        if (!(ok = mbar_wait(&tfull[u], (uint32_t)(t >> 1) & 1u, kWaitIters))) break;
+        tc_fence_after();
+        const uint32_t shi = smem_u32(tiles + 2u * u * tile_bytes), slo = shi + tile_bytes;
+#pragma unroll
+        for (int ks = 0; ks < kSlab / 8; ++ks) {
+#pragma unroll
+          for (int b = 0; b < NB; ++b) {
+            if (!((gmask >> b) & 1)) continue;
+            const int Nb = a.Kq - 128 * b;  // <= 256
+            // block b: basis rows [128 b, 128 b + 128) against columns [128 b, Kq)
+            const uint32_t aoff = (uint32_t)b * 128u * 128u + (uint32_t)ks * 32u;
+            const uint32_t acc = (t > 0 || ks > 0) ? 1u : 0u;
+            const uint32_t d = tmem + (uint32_t)toff[b];
+            const uint32_t id = idesc_tf32(128, Nb);
+            mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(shi + aoff), id, acc);
+            mma_tf32(d, desc_k_sw128(shi + aoff), desc_k_sw128(slo + aoff), id, 1u);
+            mma_tf32(d, desc_k_sw128(slo + aoff), desc_k_sw128(shi + aoff), id, 1u);
+          }
+        }
+        mma_commit(&tempty[u]);
+      }
+      mma_commit(done);
+      if (!mbar_wait(done, 0u, kWaitIters)) ok = false;
+    }
+  } else {
+    const int ctid = tid - kTmConvFirst * 32;
+    const int nq = a.Kq / 4;  // groups of four basis values
+    for (int t = 0; t < nslab; ++t) {
+      const int s = t % NR, u = t & 1;
+      if (!(ok = warp_wait(&rfull[s], (uint32_t)(t / NR) & 1u))) break;
+      if (t >= 2 && !(ok = warp_wait(&tempty[u], (uint32_t)((t >> 1) - 1) & 1u))) break;
+      const unsigned char* rs = raw + (size_t)s * raw_bytes;
+      unsigned char* hi = tiles + 2u * u * tile_bytes;
+      unsigned char* lo = hi + tile_bytes;
+      const long long rowbase = r0 + (long long)t * kSlab;
+      for (int f = ctid; f < nq * kSlab; f += kConv * 32) {
+        const int r = f & (kSlab - 1), cq = f >> 5;
+        float x[4] = {0.f, 0.f, 0.f, 0.f};
+        if (cq < a.ncb * 8) {
+          const int c4 = cq & 7;
+          const float4 v = *reinterpret_cast<const float4*>(rs + (cq >> 3) * 4096 + r * 128 + ((c4 ^ (r & 7)) << 4));
+          x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
+        }
+        const float one = rowbase + r < a.n ? 1.f : 0.f;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+          const int c = 4 * cq + w;
+          const float val = c < a.K ? x[w] : (c == a.K ? one : 0.f);
+          const float h = tf32_round(val);
+          const uint32_t off = sw128_offset(c, r);
+          *reinterpret_cast<float*>(hi + off) = h;
+          *reinterpret_cast<float*>(lo + off) = val - h;
+        }
+      }
+      fence_async_smem();
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&rempty[s]);
+        mbar_arrive(&tfull[u]);
+      }
+    }
+  }
+  // every MMA complete (the MMA thread's final commit) before TMEM is read
+  if (warp != 1) ok = warp_wait(done, 0u) && ok;
+  ok = __syncthreads_and(ok);
+  tc_fence_after();
+  float* P = a.part + (size_t)blockIdx.x * a.Kq * a.Kq;
+  if (ok && nslab > 0) {
+    const int q = warp & 3, part = warp >> 2;
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      if (!((gmask >> b) & 1)) continue;
+      const int ncol = a.Kq - 128 * b;
+      const int i = b * 128 + q * 32 + lane;
+      for (int c8 = part; c8 < ncol / 8; c8 += kTmThreads / 128) {
+        float v[8];
+        tmem_ld8(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)toff[b] + (uint32_t)c8 * 8u, v);
+        tmem_wait_ld();
+        const int j0 = b * 128 + c8 * 8;
+        if (i < a.Kq && j0 + 7 >= i) {
+#pragma unroll
+          for (int w = 0; w < 8; ++w) P[(size_t)i * a.Kq + j0 + w] = v[w];
+        }
+      }
+    }
+  } else {
+    for (int e = tid; e < a.Kq * a.Kq; e += kTmThreads)
+      if ((gmask >> ((e / a.Kq) / 128)) & 1) P[e] = 0.f;
+    if (!ok && tid == 0) atomicExch(a.err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, ncols);
+}
+
 }  // namespace
+
+// Rows of a 4-byte basis that a tensor map can address: 16-byte aligned base
+// and row pitch.
+static bool tma_rows_ok(const void* V, long long ldv) {
+  return (reinterpret_cast<uintptr_t>(V) & 15) == 0 && ((size_t)ldv * 4) % 16 == 0 && ldv <= (1ll << 36);
+}
+
+// Tensor map of the FP32 matrix V (n rows of K values, pitch ldv) with a box
+// of bw values x bh rows in the 128-byte swizzle (bw * 4 = 128 bytes); values
+// past K and rows past n read as zero.
+static bool encode_box_map(CUtensorMap* tm, const float* V, long long ldv, int K, long long n, int bw,
+                           int bh) {
+  const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
+  if (!fn || n < 1 || n > 0x7fffffffll || K < 1) return false;
+  memset(tm, 0, sizeof(*tm));
+  const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)n};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldv * sizeof(float)};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t estr[2] = {1u, 1u};
+  return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(V), dims, strides, box, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
 
 int apply_tc_supported(int K) { return K >= 1 && K <= 511; }
 
@@ -598,6 +1008,36 @@ hef_status apply_tc(void* V, bool bf16, long long ldv, long long n, int K, const
   const long long ntiles = (n + 127) / 128;
   const int ctas = (int)(ntiles < num_sms() ? ntiles : num_sms());
   const int nka = Kd / 32;
+  {
+    // TMA pipeline: FP32 basis, 16-byte aligned rows, two accumulators of
+    // Kq columns in TMEM, resident B and at least two A stages in shared memory
+    const size_t bres_t = (size_t)(nka * Kq - 16 * nka * (nka - 1)) * 256;
+    auto smem_tma = [&](int ns) { return 1024 + bres_t + 2 * (size_t)ns * 128 * 128 + (3 * ns + 4) * 8 + 16; };
+    CUtensorMap tm;
+    if (!bf16 && Kq <= 256 && smem_tma(2) <= 227 * 1024 && tma_rows_ok(V, ldv) &&
+        encode_box_map(&tm, static_cast<const float*>(V), ldv, K, n, 32, 128)) {
+      ApplyTmaArgs t;
+      t.V = static_cast<float*>(V);
+      t.ldv = ldv;
+      t.n = (int)n;
+      t.K = K;
+      t.Kq = Kq;
+      t.Kd = Kd;
+      t.RtH = RtH;
+      t.RtL = RtL;
+      t.muR = muR;
+      t.err = err;
+      if (smem_tma(3) <= 227 * 1024) {
+        HEF_ENSURE_SMEM(k_apply_tma<3>, (int)smem_tma(3));
+        HEF_LAUNCH("k_apply_tc", st, (k_apply_tma<3><<<ctas, kTmThreads, smem_tma(3), st>>>(t, tm)));
+      } else {
+        HEF_ENSURE_SMEM(k_apply_tma<2>, (int)smem_tma(2));
+        HEF_LAUNCH("k_apply_tc", st, (k_apply_tma<2><<<ctas, kTmThreads, smem_tma(2), st>>>(t, tm)));
+      }
+      HEF_CHECK_LAUNCH();
+      return HEF_OK;
+    }
+  }
   const size_t bres = (size_t)(nka * Kq - 16 * nka * (nka - 1)) * 256;  // resident B, hi + lo
   const size_t smem_res = 1024 + bres + 2 * (2 * 128 * 128) + 64;
   const size_t stage = 2 * 128 * 128 + 2 * (size_t)Kq * 128;  // A and B of one K block
@@ -680,11 +1120,51 @@ hef_status gram_tc(const void* V, bool bf16, long long ldv, long long n, int K, 
   for (int g = 0; g < 4; ++g) a.gmask[g] = 0;
   const int ng = gram_groups(Kq, nb, a.gmask);
   hef_status s;
-  switch (nb) {
+  CUtensorMap tm;
+  const int ncb = (K + 31) / 32;
+  // TMA pipeline: FP32 basis, 16-byte aligned rows, at most two blocks of
+  // 128 basis rows, two tile stages and at least two raw stages in shared memory
+  auto smem_tma = [&](int nr) {
+    return 1024 + 4 * (size_t)nb * 128 * 128 + (size_t)nr * ncb * 4096 + (2 * nr + 5) * 8 + 16;
+  };
+  if (!bf16 && nb <= 2 && smem_tma(2) <= 227 * 1024 && tma_rows_ok(V, ldv) &&
+      encode_box_map(&tm, static_cast<const float*>(V), ldv, K, n, 32, kSlab)) {
+    GramTmaArgs t;
+    t.n = (int)n;
+    t.K = K;
+    t.Kq = Kq;
+    t.ncb = ncb;
+    t.rows_per_cta = a.rows_per_cta;
+    for (int g = 0; g < 4; ++g) t.gmask[g] = a.gmask[g];
+    t.part = a.part;
+    t.err = err;
+    int nr = 4;
+    while (nr > 2 && smem_tma(nr) > 227 * 1024) --nr;
+    const dim3 grid(ctas, ng);
+#define HEF_GRAM_TMA(NBv, NRv)                                                                  \
+  do {                                                                                          \
+    HEF_ENSURE_SMEM((k_gram_tma<NBv, NRv>), (int)smem_tma(NRv));                                \
+    HEF_LAUNCH("k_gram_tc", st,                                                                 \
+               (k_gram_tma<NBv, NRv><<<grid, kTmThreads, smem_tma(NRv), st>>>(t, tm)));         \
+  } while (0)
+    if (nb == 1) {
+      if (nr == 4) HEF_GRAM_TMA(1, 4);
+      else if (nr == 3) HEF_GRAM_TMA(1, 3);
+      else HEF_GRAM_TMA(1, 2);
+    } else {
+      if (nr == 4) HEF_GRAM_TMA(2, 4);
+      else if (nr == 3) HEF_GRAM_TMA(2, 3);
+      else HEF_GRAM_TMA(2, 2);
+    }
+#undef HEF_GRAM_TMA
+    s = HEF_OK;
+  } else {
+    switch (nb) {
     case 1: s = launch_gram_tc<1, 2>(a, ctas, ng, st); break;
     case 2: s = launch_gram_tc<2, 2>(a, ctas, ng, st); break;
     case 3: s = launch_gram_tc<3, 2>(a, ctas, ng, st); break;
     default: s = launch_gram_tc<4, 1>(a, ctas, ng, st); break;
+    }
   }
   if (s) return s;
   HEF_LAUNCH("k_gram_tc_reduce", st,

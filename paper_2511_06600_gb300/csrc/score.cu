@@ -831,21 +831,6 @@ size_t carve_score(void* base, int K, long long m, ScoreWs* w) {
   return c.bytes();
 }
 
-// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
-// against the driver library); null when unavailable.
-PFN_cuTensorMapEncodeTiled_v12000 encode_tiled() {
-  static const PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
-    void* p = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-            cudaSuccess ||
-        q != cudaDriverEntryPointSuccess)
-      return nullptr;
-    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }();
-  return fn;
-}
-
 // Scores with the embedding-farthest pair (HEF_REDUCE_EMBED; reading A7's
 // alternative for "p and q are the most distant nodes in the embedding
 // space", Eq. ratios).  One warp per hyperedge: lanes take the pin pairs

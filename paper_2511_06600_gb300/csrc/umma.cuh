@@ -80,6 +80,19 @@ __device__ __forceinline__ void gather4_g2s(void* dst, const void* tmap, int y0,
       : "memory");
 }
 
+// 2D tensor-map tile load (the box the map encodes) into this CTA's shared
+// memory at `dst` (1024-byte aligned for the 128-byte swizzle) from
+// coordinates x (innermost, elements; x * element size a multiple of 16
+// bytes) and y; out-of-range elements read as zero; completion counts the
+// box bytes against the phase of `bar`.
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // ---------------------------------------------------------------- fences
 
 // generic-proxy shared-memory writes -> visible to the tensor core (async proxy)
