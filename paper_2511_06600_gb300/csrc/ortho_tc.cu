@@ -605,8 +605,8 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity) {
 // A tile of K block ka is the box (32 values from 32 ka) x (128 rows) of V,
 // loaded K-major with the 128-byte swizzle, i.e. already in the MMA's
 // layout; the converters round it to its hi part in place and write the lo
-// part beside it.  Two TMEM accumulators: tile t drains while tile t + 1
-// accumulates.  NS stages of A.
+// part into one of two lo buffers (so that a stage holds 16 KB).  Two TMEM
+// accumulators: tile t drains while tile t + 1 accumulates.  NS stages of A.
 template <int NS>
 __global__ void __launch_bounds__(kTmThreads, 1)
     k_apply_tma(ApplyTmaArgs a, const __grid_constant__ CUtensorMap tmap) {
@@ -616,13 +616,15 @@ __global__ void __launch_bounds__(kTmThreads, 1)
   const int nka = a.Kd / 32;
   auto brows = [&](int ka) { return a.Kq - 32 * ka; };
   auto boff = [&](int ka) { return (uint32_t)(ka * a.Kq - 16 * ka * (ka - 1)) * 256u; };
-  unsigned char* abase = base + boff(nka);  // stage s: hi at 2 s kATile, lo after it
-  uint64_t* full = reinterpret_cast<uint64_t*>(abase + 2u * NS * kATile);  // NS: landed
+  unsigned char* abase = base + boff(nka);          // stage s at s kATile
+  unsigned char* lbase = abase + (uint32_t)NS * kATile;  // lo buffer b at b kATile
+  uint64_t* full = reinterpret_cast<uint64_t*>(lbase + 2u * kATile);  // NS: landed
   uint64_t* conv = full + NS;     // NS: split
   uint64_t* empty = conv + NS;    // NS: MMAs done with the stage
   uint64_t* tfull = empty + NS;   // 2: accumulator complete
   uint64_t* tempty = tfull + 2;   // 2: accumulator drained
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tempty + 2);
+  uint64_t* lfree = tempty + 2;   // 2: MMAs done with the lo buffer
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(lfree + 2);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   uint32_t ncols = 32;
   while (ncols < 2u * (uint32_t)a.Kq) ncols <<= 1;
@@ -637,6 +639,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
     for (int b = 0; b < 2; ++b) {
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], kTmEpiWarps);
+      mbar_init(&lfree[b], 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -669,7 +672,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
           const int s = g % NS;
           if (g >= NS && !(ok = mbar_wait(&empty[s], (uint32_t)((g / NS) - 1) & 1u, kWaitIters))) break;
           mbar_arrive_expect_tx(&full[s], kATile);
-          tma_load_2d(abase + 2u * s * kATile, &tmap, 32 * ka, tile * 128, &full[s]);
+          tma_load_2d(abase + (uint32_t)s * kATile, &tmap, 32 * ka, tile * 128, &full[s]);
           ++g;
         }
       // copies still landing finish before the CTA may leave
@@ -689,7 +692,8 @@ __global__ void __launch_bounds__(kTmThreads, 1)
           if (!(ok = mbar_wait(&conv[s], (uint32_t)(g / NS) & 1u, kWaitIters))) break;
           tc_fence_after();
           const int c0 = ka * 32, nr = brows(ka);
-          const uint32_t sah = smem_u32(abase + 2u * s * kATile), sal = sah + kATile;
+          const uint32_t sah = smem_u32(abase + (uint32_t)s * kATile);
+          const uint32_t sal = smem_u32(lbase + (uint32_t)(g & 1) * kATile);
           const uint32_t sbh = smem_u32(base + boff(ka)), sbl = sbh + (uint32_t)nr * 128u;
           const uint32_t id = idesc_tf32(128, nr);
 #pragma unroll
@@ -702,6 +706,7 @@ __global__ void __launch_bounds__(kTmThreads, 1)
             mma_tf32(d, desc_k_sw128(sal + ko), desc_k_sw128(sbh + ko), id, 1u);
           }
           mma_commit(&empty[s]);
+          mma_commit(&lfree[g & 1]);
         }
         if (!ok) break;
         mma_commit(&tfull[b]);
@@ -716,8 +721,9 @@ __global__ void __launch_bounds__(kTmThreads, 1)
       for (int ka = 0; ka < nka; ++ka, ++g) {
         const int s = g % NS;
         if (!(ok = warp_wait(&full[s], (uint32_t)(g / NS) & 1u))) break;
-        float4* hi = reinterpret_cast<float4*>(abase + 2u * s * kATile);
-        float4* lo = reinterpret_cast<float4*>(abase + (2u * s + 1u) * kATile);
+        if (g >= 2 && !(ok = warp_wait(&lfree[g & 1], (uint32_t)((g >> 1) - 1) & 1u))) break;
+        float4* hi = reinterpret_cast<float4*>(abase + (uint32_t)s * kATile);
+        float4* lo = reinterpret_cast<float4*>(lbase + (uint32_t)(g & 1) * kATile);
         for (int f = ctid; f < (int)(kATile / 16); f += kTmConvWarps * 32) {
           const float4 x = hi[f];
           const float4 h = make_float4(tf32_round(x.x), tf32_round(x.y), tf32_round(x.z), tf32_round(x.w));
@@ -778,10 +784,10 @@ struct GramTmaArgs {
 };
 
 // G_aug = [V 1]^T [V 1] (as k_gram_tc, NB <= 2 blocks of 128 basis rows).  A
-// 32-row slab of V lands as ncb boxes of 32 values x 32 rows (128-byte
-// swizzle) in a ring of NR raw stages; the converter warps (2..15) transpose
-// it into the hi/lo K-major tiles of one of two tile stages (lanes run along
-// the slab rows: conflict-free on both sides), adding the ones column.
+// 32-row slab of V lands as ncb unswizzled boxes of 32 values x 32 rows in a
+// ring of NR raw stages (only the converters read them); the converter warps
+// (2..15) transpose it into the hi/lo K-major tiles of one of two tile
+// stages, adding the ones column.
 template <int NB, int NR>
 __global__ void __launch_bounds__(kTmThreads, 1)
     k_gram_tma(GramTmaArgs a, const __grid_constant__ CUtensorMap tmap) {
@@ -883,8 +889,16 @@ __global__ void __launch_bounds__(kTmThreads, 1)
       if (!mbar_wait(done, 0u, kWaitIters)) ok = false;
     }
   } else {
-    const int ctid = tid - kTmConvFirst * 32;
-    const int nq = a.Kq / 4;  // groups of four basis values
+    // warp item (column block cbw of 32 basis values, row half h): lane
+    // (q = lane / 8, l = lane % 8) transposes the 4 x 4 block of slab rows
+    // 4 rho .. 4 rho + 3, rho = ((l / 2 + q) mod 4) + 4 h, and basis values
+    // 4 cq .. 4 cq + 3, cq = 8 cbw + l: four 16-byte loads of the unswizzled
+    // raw rows (a quarter warp reads eight distinct 16-byte bank groups) and
+    // eight 16-byte stores into the swizzled tiles (group rho ^ (c mod 8),
+    // again distinct over a quarter warp)
+    const int cw = warp - kTmConvFirst;
+    const int q = lane >> 3, l = lane & 7;
+    const int nwi = 2 * ((a.Kq + 31) / 32);
     for (int t = 0; t < nslab; ++t) {
       const int s = t % NR, u = t & 1;
       if (!(ok = warp_wait(&rfull[s], (uint32_t)(t / NR) & 1u))) break;
@@ -893,23 +907,35 @@ __global__ void __launch_bounds__(kTmThreads, 1)
       unsigned char* hi = tiles + 2u * u * tile_bytes;
       unsigned char* lo = hi + tile_bytes;
       const long long rowbase = r0 + (long long)t * kSlab;
-      for (int f = ctid; f < nq * kSlab; f += kConv * 32) {
-        const int r = f & (kSlab - 1), cq = f >> 5;
-        float x[4] = {0.f, 0.f, 0.f, 0.f};
-        if (cq < a.ncb * 8) {
-          const int c4 = cq & 7;
-          const float4 v = *reinterpret_cast<const float4*>(rs + (cq >> 3) * 4096 + r * 128 + ((c4 ^ (r & 7)) << 4));
-          x[0] = v.x, x[1] = v.y, x[2] = v.z, x[3] = v.w;
-        }
-        const float one = rowbase + r < a.n ? 1.f : 0.f;
+      for (int wi = cw; wi < nwi; wi += kConv) {
+        const int cbw = wi >> 1, h = wi & 1;
+        const int cq = 8 * cbw + l;
+        if (4 * cq >= a.Kq) continue;
+        const int rb = 4 * ((((l >> 1) + q) & 3) + 4 * h);
+        float4 x[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          x[k] = cbw < a.ncb ? *reinterpret_cast<const float4*>(rs + cbw * 4096 + (rb + k) * 128 + l * 16)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        float one[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) one[k] = rowbase + rb + k < a.n ? 1.f : 0.f;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
           const int c = 4 * cq + w;
-          const float val = c < a.K ? x[w] : (c == a.K ? one : 0.f);
-          const float h = tf32_round(val);
-          const uint32_t off = sw128_offset(c, r);
-          *reinterpret_cast<float*>(hi + off) = h;
-          *reinterpret_cast<float*>(lo + off) = val - h;
+          float v[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            const float xv = w == 0 ? x[k].x : w == 1 ? x[k].y : w == 2 ? x[k].z : x[k].w;
+            v[k] = c < a.K ? xv : (c == a.K ? one[k] : 0.f);
+          }
+          float hv[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) hv[k] = tf32_round(v[k]);
+          const uint32_t off = sw128_offset(c, rb);
+          *reinterpret_cast<float4*>(hi + off) = make_float4(hv[0], hv[1], hv[2], hv[3]);
+          *reinterpret_cast<float4*>(lo + off) =
+              make_float4(v[0] - hv[0], v[1] - hv[1], v[2] - hv[2], v[3] - hv[3]);
         }
       }
       fence_async_smem();
@@ -962,10 +988,10 @@ static bool tma_rows_ok(const void* V, long long ldv) {
 }
 
 // Tensor map of the FP32 matrix V (n rows of K values, pitch ldv) with a box
-// of bw values x bh rows in the 128-byte swizzle (bw * 4 = 128 bytes); values
-// past K and rows past n read as zero.
+// of bw values x bh rows (bw * 4 = 128 bytes), in the 128-byte swizzle or
+// unswizzled; values past K and rows past n read as zero.
 static bool encode_box_map(CUtensorMap* tm, const float* V, long long ldv, int K, long long n, int bw,
-                           int bh) {
+                           int bh, bool swizzle) {
   const PFN_cuTensorMapEncodeTiled_v12000 fn = encode_tiled();
   if (!fn || n < 1 || n > 0x7fffffffll || K < 1) return false;
   memset(tm, 0, sizeof(*tm));
@@ -974,7 +1000,8 @@ static bool encode_box_map(CUtensorMap* tm, const float* V, long long ldv, int K
   const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
   const cuuint32_t estr[2] = {1u, 1u};
   return fn(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(V), dims, strides, box, estr,
-            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -1012,10 +1039,10 @@ hef_status apply_tc(void* V, bool bf16, long long ldv, long long n, int K, const
     // TMA pipeline: FP32 basis, 16-byte aligned rows, two accumulators of
     // Kq columns in TMEM, resident B and at least two A stages in shared memory
     const size_t bres_t = (size_t)(nka * Kq - 16 * nka * (nka - 1)) * 256;
-    auto smem_tma = [&](int ns) { return 1024 + bres_t + 2 * (size_t)ns * 128 * 128 + (3 * ns + 4) * 8 + 16; };
+    auto smem_tma = [&](int ns) { return 1024 + bres_t + (size_t)(ns + 2) * 128 * 128 + (3 * ns + 6) * 8 + 16; };
     CUtensorMap tm;
     if (!bf16 && Kq <= 256 && smem_tma(2) <= 227 * 1024 && tma_rows_ok(V, ldv) &&
-        encode_box_map(&tm, static_cast<const float*>(V), ldv, K, n, 32, 128)) {
+        encode_box_map(&tm, static_cast<const float*>(V), ldv, K, n, 32, 128, true)) {
       ApplyTmaArgs t;
       t.V = static_cast<float*>(V);
       t.ldv = ldv;
@@ -1027,7 +1054,10 @@ hef_status apply_tc(void* V, bool bf16, long long ldv, long long n, int K, const
       t.RtL = RtL;
       t.muR = muR;
       t.err = err;
-      if (smem_tma(3) <= 227 * 1024) {
+      if (smem_tma(4) <= 227 * 1024) {
+        HEF_ENSURE_SMEM(k_apply_tma<4>, (int)smem_tma(4));
+        HEF_LAUNCH("k_apply_tc", st, (k_apply_tma<4><<<ctas, kTmThreads, smem_tma(4), st>>>(t, tm)));
+      } else if (smem_tma(3) <= 227 * 1024) {
         HEF_ENSURE_SMEM(k_apply_tma<3>, (int)smem_tma(3));
         HEF_LAUNCH("k_apply_tc", st, (k_apply_tma<3><<<ctas, kTmThreads, smem_tma(3), st>>>(t, tm)));
       } else {
@@ -1128,7 +1158,7 @@ hef_status gram_tc(const void* V, bool bf16, long long ldv, long long n, int K, 
     return 1024 + 4 * (size_t)nb * 128 * 128 + (size_t)nr * ncb * 4096 + (2 * nr + 5) * 8 + 16;
   };
   if (!bf16 && nb <= 2 && smem_tma(2) <= 227 * 1024 && tma_rows_ok(V, ldv) &&
-      encode_box_map(&tm, static_cast<const float*>(V), ldv, K, n, 32, kSlab)) {
+      encode_box_map(&tm, static_cast<const float*>(V), ldv, K, n, 32, kSlab, false)) {
     GramTmaArgs t;
     t.n = (int)n;
     t.K = K;
