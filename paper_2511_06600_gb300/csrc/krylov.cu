@@ -221,9 +221,12 @@ __device__ __forceinline__ void split2(const T (&r)[2 * S], T (&lo)[S], T (&hi)[
 // working type; only the CTA's sums are widened to FP64 (conversions and
 // FP64 adds run at 1/64 rate on GB300).
 // PMAX caps the butterfly width (values held at once) for register-tight callers.
-// row: the partial's row in part (default: the CTA's index).
-template <int NQ, int S, typename A, int NT = kThreads, int PMAX = 32>
-__device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* part, int row = -1) {
+// row: the partial's row in part (default: the CTA's index); with
+// col_stride > 0 the partials are stored slot-major instead, value t at
+// part[t * col_stride + row].
+template <int NQ, int S, typename A, int NT = kThreads, int PMAX = 32, typename PT = double>
+__device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], PT* part, int row = -1,
+                                                  int col_stride = 0) {
   constexpr int N = NQ * S;
   constexpr int P0 = N > 16 ? 32 : (N > 8 ? 16 : (N > 4 ? 8 : (N > 2 ? 4 : (N > 1 ? 2 : 1))));
   constexpr int P = P0 < PMAX ? P0 : PMAX;
@@ -257,7 +260,8 @@ __device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], double* p
   for (int t = threadIdx.x; t < N; t += blockDim.x) {
     A acc = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) acc += red[w][t];
-    part[(size_t)(row < 0 ? (int)blockIdx.x : row) * N + t] = (double)acc;
+    const size_t r = (size_t)(row < 0 ? (int)blockIdx.x : row);
+    part[col_stride > 0 ? (size_t)t * col_stride + r : r * N + t] = (PT)acc;
   }
 }
 
@@ -814,36 +818,77 @@ __host__ __device__ constexpr int pers_threads() {
   return 2 * S * sizeof(T) <= 32 ? 512 : 256;
 }
 
-// In one CTA of NT threads: out[slot] = sum over b < nb of part[b * N + slot]
-// for slot < N, with every load of a thread issued before its adds (one
-// round trip to L2 for up to 8 partials a thread), then the per-thread sums
-// of a slot added in thread order: a fixed order for given nb, N and NT.
+// Double-float addition (Knuth's two-sum of the high parts, the low parts
+// added and renormalised): about 44 significant bits from FP32 operations.
+struct DFloat {
+  float hi, lo;
+};
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v)),
+                            __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
+// In one CTA of NT threads: out[slot] = sum over b < nb of part[slot * nb + b]
+// (slot-major partials) for slot < N.  Warp w takes slots w, w + NT / 32,
+// ... (up to four at a time): lane l loads partials l, l + 32, ... of each
+// (every load issued before the adds: one round trip to L2 for up to 256
+// partials and 4 NT / 32 slots), adds its eight in a fixed pairwise tree,
+// then the lanes combine by a butterfly and lane 0's sum is kept: a fixed
+// order for given nb.  DF (FP32 partials, P = float): the sums run in
+// double-float arithmetic, since FP64 operations and conversions are slow on
+// this part (a warp-wide FP64 add costs tens of issue cycles); otherwise in
+// FP64 (P = double).
 // Ends with __syncthreads (out may be shared memory).
-template <int NT>
-__device__ __forceinline__ void reduce_slots_wide(const double* part, int nb, int N,
-                                                  double* out) {
-  __shared__ double tmp[NT];
-  const int per = NT / N;  // threads per slot (N <= 6 * 16 <= NT)
-  const int t = threadIdx.x, slot = t % N, r = t / N;
-  double acc = 0.0;
-  if (r < per) {
-    for (int b0 = r; b0 < nb; b0 += 8 * per) {
-      double x[8];
+template <int NT, bool DF, typename P>
+__device__ __forceinline__ void reduce_slots_wide(const P* part, int nb, int N, double* out) {
+  constexpr int kW = NT / 32;
+  constexpr int kI = DF ? 4 : 1;  // slots of a warp per round
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int s0 = w; s0 < N; s0 += kI * kW) {
+    P x[kI][8];
+    DFloat da[kI];
+    double acc[kI];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int b = b0 + q * per;
-        x[q] = b < nb ? __ldcg(part + (size_t)b * N + slot) : 0.0;
+    for (int i = 0; i < kI; ++i) da[i] = {0.f, 0.f}, acc[i] = 0.0;
+    for (int b0 = 0; b0 < nb; b0 += 256) {
+#pragma unroll
+      for (int i = 0; i < kI; ++i)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int bb = b0 + lane + 32 * q, slot = s0 + i * kW;
+          x[i][q] = bb < nb && slot < N ? __ldcg(part + (size_t)slot * nb + bb) : (P)0;
+        }
+#pragma unroll
+      for (int i = 0; i < kI; ++i) {
+        if (DF) {
+          DFloat y[8];
+#pragma unroll
+          for (int q = 0; q < 8; ++q) y[q] = {(float)x[i][q], 0.f};  // exact: P is float
+          da[i] = df_add(da[i], df_add(df_add(df_add(y[0], y[1]), df_add(y[2], y[3])),
+                                       df_add(df_add(y[4], y[5]), df_add(y[6], y[7]))));
+        } else {
+          acc[i] += ((x[i][0] + x[i][1]) + (x[i][2] + x[i][3])) + ((x[i][4] + x[i][5]) + (x[i][6] + x[i][7]));
+        }
+      }
+    }
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1)
+#pragma unroll
+      for (int i = 0; i < kI; ++i) {
+        if (DF) {
+          const DFloat p{__shfl_xor_sync(0xffffffffu, da[i].hi, o), __shfl_xor_sync(0xffffffffu, da[i].lo, o)};
+          da[i] = df_add(da[i], p);
+        } else {
+          acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], o);
+        }
       }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) acc += x[q];
-    }
-  }
-  tmp[t] = acc;
-  __syncthreads();
-  if (t < N) {
-    double sacc = 0.0;
-    for (int q = 0; q < per; ++q) sacc += tmp[q * N + t];
-    out[t] = sacc;
+    for (int i = 0; i < kI; ++i)
+      if (lane == 0 && s0 + i * kW < N) out[s0 + i * kW] = DF ? (double)da[i].hi + (double)da[i].lo : acc[i];
   }
   __syncthreads();
 }
@@ -898,7 +943,7 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
 }
 
 // Grid barrier number `ph` with its phase's reduction.  Every CTA writes its
-// partial sums to part[ph & 1] and then, with a release store, its own
+// partial sums to part[ph & 1] (slot-major) and then, with a release store, its own
 // arrival flag flags[b] = ph + 1.  CTA 0 reduces: its threads poll the G
 // flags in parallel (acquire loads), it sums all partials in a fixed order
 // (reduce_slots_wide), publishes the N results in pub[ph & 1] and releases
@@ -917,7 +962,11 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
   double* buf = part + (size_t)(ph & 1) * G * 6 * S;
   double* res = pub + (size_t)(ph & 1) * 6 * S;
   const unsigned int want = (unsigned int)ph + 1u;
-  block_partials_qs<NQ, S, T, NT, 8>(acc, buf, b);
+  // FP32 forms: FP32 partials (their values are FP32 sums), reduced in
+  // double-float arithmetic
+  using P = T;
+  P* pbuf = reinterpret_cast<P*>(buf);
+  block_partials_qs<NQ, S, T, NT, 8, P>(acc, pbuf, b, G);
   __shared__ int go;
   __syncthreads();
   if (threadIdx.x == 0) st_release(flags + b, want);
@@ -939,7 +988,7 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
       }
     }
     if (!__syncthreads_and(ok)) return false;
-    reduce_slots_wide<NT>(buf, G, N, out);
+    reduce_slots_wide<NT, sizeof(T) == 4, P>(pbuf, G, N, out);
     for (int t = threadIdx.x; t < N; t += NT) res[t] = out[t];
     __syncthreads();
     if (threadIdx.x == 0) st_release(flags + G, want);
