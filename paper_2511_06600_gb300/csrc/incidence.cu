@@ -239,13 +239,16 @@ __device__ __forceinline__ void flag(unsigned int* status, unsigned bits, int e)
 // Offsets, weight, pin range and duplicate pins of every hyperedge, and its
 // locality key (smallest pin; 0 for an empty hyperedge) with val = caller id:
 // one thread per hyperedge, the pins of a hyperedge with at most kRegPins
-// loaded at once into registers; its warp together for hyperedges with more
-// than 32 pins.
+// loaded at once into registers; its warp together for longer hyperedges,
+// duplicates then found by a hash table in shared memory (quadratic scan
+// beyond kHashSlots / 2 pins).
 constexpr int kRegPins = 8;
+constexpr int kHashSlots = 1024;  // per warp: duplicate checks of up to 512 pins in O(k)
 
 __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict__ eptr,
                            const int32_t* __restrict__ pins, const double* __restrict__ w,
                            unsigned int* status, uint32_t* keys, int32_t* vals) {
+  __shared__ int htab[kThreads / 32][kHashSlots];
   const int lane = threadIdx.x & 31;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (eptr[0] != 0 || eptr[m] != P) flag(status, HEF_BAD_EPTR, 0);
@@ -266,9 +269,9 @@ __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict_
       if (!(we > 0.0 && we <= 1.7976931348623157e308)) flag(status, HEF_BAD_WEIGHT, (int)e);
       const int k = (int)(b - a);
       bool bad_pin = false, dup = false;
-      if (k > 32) {
+      if (k > kRegPins) {
         big = true;
-      } else if (k > 0 && k <= kRegPins) {
+      } else if (k > 0) {
         int q[kRegPins];
 #pragma unroll
         for (int i = 0; i < kRegPins; ++i) q[i] = pins[a + min(i, k - 1)];
@@ -280,14 +283,6 @@ __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict_
 #pragma unroll
             for (int j = i + 1; j < kRegPins; ++j) dup |= j < k && q[j] == q[i];
           }
-        }
-      } else {
-        for (int i = 0; i < k; ++i) {
-          const int p = pins[a + i];
-          bad_pin |= p < 0 || p >= n;
-          mn = min(mn, p);
-          for (int j = i + 1; j < k; ++j)
-            if (pins[a + j] == p) dup = true;
         }
       }
       if (bad_pin) flag(status, HEF_BAD_PIN, (int)e);
@@ -301,12 +296,42 @@ __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict_
       const int k = (int)(bb - ba);
       bool bad_pin = false, dup = false;
       int wmn = 0x7fffffff;
-      for (int i = lane; i < k; i += 32) {
-        const int p = pins[ba + i];
-        if (p < 0 || p >= n) bad_pin = true;
-        wmn = min(wmn, p);
-        for (int j = i + 1; j < k; ++j)
-          if (pins[ba + j] == p) dup = true;
+      if (k <= kHashSlots / 2) {
+        // duplicates by insertion into an open-addressing table of at least
+        // 2k slots in shared memory (linear probing, multiplicative hash)
+        int bits = 1;
+        while ((1 << bits) < 2 * k) ++bits;
+        const unsigned hmask = (1u << bits) - 1u;
+        int* tab = htab[threadIdx.x >> 5];
+        for (int i = lane; i <= (int)hmask; i += 32) tab[i] = -1;
+        __syncwarp();
+        for (int i = lane; i < k; i += 32) {
+          const int p = pins[ba + i];
+          wmn = min(wmn, p);
+          if (p < 0 || p >= n) {
+            bad_pin = true;
+            continue;
+          }
+          unsigned h = ((unsigned)p * 2654435761u) >> (32 - bits);
+          while (true) {
+            const int old = atomicCAS(&tab[h], -1, p);
+            if (old == -1) break;
+            if (old == p) {
+              dup = true;
+              break;
+            }
+            h = (h + 1u) & hmask;
+          }
+        }
+        __syncwarp();
+      } else {
+        for (int i = lane; i < k; i += 32) {
+          const int p = pins[ba + i];
+          if (p < 0 || p >= n) bad_pin = true;
+          wmn = min(wmn, p);
+          for (int j = i + 1; j < k; ++j)
+            if (pins[ba + j] == p) dup = true;
+        }
       }
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) wmn = min(wmn, __shfl_xor_sync(0xffffffffu, wmn, o));

@@ -86,6 +86,35 @@ def test_invalid_hypergraph_is_rejected(bad, bit):
     del out
 
 
+@pytest.mark.parametrize("size,bad", [(20, None), (20, "dup"), (300, None), (300, "dup"),
+                                      (300, "pin"), (700, None), (700, "dup")])
+def test_long_hyperedge_validation(size, bad):
+    """Pins of long hyperedges: duplicates found by the shared-memory hash
+    (up to 512 pins) or the quadratic scan beyond, bad pins flagged, and a
+    clean hypergraph accepted."""
+    rng = np.random.default_rng(size)
+    n = 1000
+    sizes = [2, 3, size, 4, 2]
+    edges = [rng.choice(n, k, replace=False).astype(np.int32) for k in sizes]
+    if bad == "dup":
+        edges[2][size - 1] = edges[2][size // 3]
+    elif bad == "pin":
+        edges[2][size // 2] = n + 7
+    pins = np.concatenate(edges)
+    eptr = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    w = np.ones(len(sizes))
+    h = hef()
+    t = {"eptr": torch.from_numpy(eptr).to(DEV), "pins": torch.from_numpy(pins).to(DEV),
+         "w": torch.from_numpy(w).to(DEV)}
+    inc = h.build_incidence(n, t["eptr"], t["pins"], t["w"])
+    if bad is None:
+        inc.check()
+    else:
+        with pytest.raises(h.HefError) as ei:
+            inc.check()
+        assert ei.value.status == -7 and ei.value.detail & (4 if bad == "dup" else 2)
+
+
 def test_host_argument_errors():
     h = hef()
     H = random_hypergraph(30, 20, 4, 1)
