@@ -237,7 +237,8 @@ __device__ __forceinline__ void flag(unsigned int* status, unsigned bits, int e)
 }
 
 // Offsets, weight, pin range and duplicate pins of every hyperedge, and its
-// locality key (smallest pin; 0 for an empty hyperedge) with val = caller id:
+// locality key (smallest pin; 0 for an empty hyperedge) with val = caller id
+// and the key's count in cnt:
 // one thread per hyperedge, the pins of a hyperedge with at most kRegPins
 // loaded at once into registers; its warp together for longer hyperedges,
 // duplicates then found by a hash table in shared memory (quadratic scan
@@ -247,7 +248,7 @@ constexpr int kHashSlots = 1024;  // per warp: duplicate checks of up to 512 pin
 
 __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict__ eptr,
                            const int32_t* __restrict__ pins, const double* __restrict__ w,
-                           unsigned int* status, uint32_t* keys, int32_t* vals) {
+                           unsigned int* status, uint32_t* keys, int32_t* vals, int* cnt) {
   __shared__ int htab[kThreads / 32][kHashSlots];
   const int lane = threadIdx.x & 31;
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -341,8 +342,10 @@ __global__ void k_validate(int n, int m, long long P, const int64_t* __restrict_
       if (__any_sync(0xffffffffu, dup) && lane == 0) flag(status, HEF_DUP_PIN, (int)ee);
     }
     if (e < m) {
-      keys[e] = b > a ? (uint32_t)mn : 0u;
+      const uint32_t key = b > a ? (uint32_t)mn : 0u;
+      keys[e] = key;
       vals[e] = (int32_t)e;
+      if (key < (uint32_t)n) atomicAdd(&cnt[key], 1);  // bucket sizes of the locality sort
     }
   }
 }
@@ -470,22 +473,72 @@ __global__ void k_big_scatter(int m, const int32_t* __restrict__ ceptr,
     if ((ceptr[i + 1] - ceptr[i]) > kBigEdge) idx[pos[i]] = (int32_t)i;
 }
 
-__global__ void k_csr_edges(long long P, const int32_t* __restrict__ vslot,
-                            const int32_t* __restrict__ slot_edge, const unsigned int* status,
-                            int32_t* vedge) {
+// Stable counting sort of the indices i < N by keys[i] < nb (the locality
+// schedule of hyperedges, the vertex-major transpose of the CSC slots): the
+// bucket sizes come from atomics and an exclusive scan gives the offsets
+// off[0..nb]; k_place drops each index into its bucket behind an atomic
+// cursor (any order), and k_bucket_order sorts each bucket by index, which
+// is the order a stable sort leaves: the result does not depend on
+// scheduling.
+__global__ void k_place(long long N, const int32_t* __restrict__ keys, const int32_t* __restrict__ off,
+                        int* cur, const unsigned int* status, int32_t* placed) {
   if (status[0]) return;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < P;
-       i += (long long)gridDim.x * blockDim.x)
-    vedge[i] = slot_edge[vslot[i]];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = keys[i];
+    placed[off[k] + atomicAdd(&cur[k], 1)] = (int32_t)i;
+  }
 }
 
-__global__ void k_slot_keys(long long P, const int32_t* __restrict__ cpins, const unsigned int* status,
-                            uint32_t* keys, int32_t* vals) {
+constexpr int kSmallBucket = 8;  // buckets up to this size: one thread, a sorting network
+
+// out[off[b] ..] = the indices of bucket b ascending (and out2[t] =
+// map[out[t]] when map is given): one thread per bucket of at most
+// kSmallBucket entries (an insertion network in registers), the bucket's warp
+// for larger ones (each entry's rank is the count of smaller entries; the
+// indices are distinct).
+__global__ void k_bucket_order(long long nb, const int32_t* __restrict__ off,
+                               const int32_t* __restrict__ placed, const int32_t* __restrict__ map,
+                               const unsigned int* status, int32_t* out, int32_t* out2) {
   if (status[0]) return;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < P;
-       t += (long long)gridDim.x * blockDim.x) {
-    keys[t] = (uint32_t)cpins[t];
-    vals[t] = (int32_t)t;
+  const int lane = threadIdx.x & 31;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < nb;
+       base += (long long)gridDim.x * blockDim.x) {
+    const long long b = base + threadIdx.x;
+    int a0 = 0, d = 0;
+    if (b < nb) a0 = off[b], d = off[b + 1] - a0;
+    const bool big = d > kSmallBucket;
+    if (d > 0 && !big) {
+      int x[kSmallBucket];
+#pragma unroll
+      for (int q = 0; q < kSmallBucket; ++q) x[q] = q < d ? placed[a0 + q] : 0x7fffffff;
+#pragma unroll
+      for (int i = 1; i < kSmallBucket; ++i)
+#pragma unroll
+        for (int j = i; j > 0; --j) {
+          const int lo = min(x[j - 1], x[j]), hi = max(x[j - 1], x[j]);
+          x[j - 1] = lo, x[j] = hi;
+        }
+#pragma unroll
+      for (int q = 0; q < kSmallBucket; ++q)
+        if (q < d) {
+          out[a0 + q] = x[q];
+          if (map) out2[a0 + q] = map[x[q]];
+        }
+    }
+    unsigned mask = __ballot_sync(0xffffffffu, big);
+    while (mask) {
+      const int src = __ffs(mask) - 1;
+      mask &= mask - 1;
+      const int s0 = __shfl_sync(0xffffffffu, a0, src), sd = __shfl_sync(0xffffffffu, d, src);
+      for (int i = lane; i < sd; i += 32) {
+        const int v = placed[s0 + i];
+        int r = 0;
+        for (int j = 0; j < sd; ++j) r += placed[s0 + j] < v ? 1 : 0;
+        out[s0 + r] = v;
+        if (map) out2[s0 + r] = map[v];
+      }
+    }
   }
 }
 
@@ -561,6 +614,8 @@ struct IncLayout {
   int32_t* vals;
   SortBufs sb;
   int* tmp;       // max(m, n) + 1 ints (sizes / degree counts, scanned in place)
+  int* cur;       // max(m, n) + 1 ints: cursors of the counting sorts
+  int32_t* place; // max(m, P): indices as placed in their buckets
   int* scan_bsum;
   double* part;
 };
@@ -569,7 +624,6 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   Carver c(base);
   const long long NS = (m > P ? m : P);
   const long long NT = (m > n ? m : n) + 1;
-  const int ntiles = scan_tiles(NS > 0 ? NS : 1);
   L->h.status = c.take<unsigned int>(64);
   L->h.counter = L->h.status + 32;
   L->sb.counter = L->h.status + 34;  // zeroed with the status word at the start of a build
@@ -602,11 +656,9 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   L->h.totals = c.take<double>(8);
   L->keys = c.take<uint32_t>(NS > 0 ? NS : 1);
   L->vals = c.take<int32_t>(NS > 0 ? NS : 1);
-  L->sb.k_alt = c.take<uint32_t>(NS > 0 ? NS : 1);
-  L->sb.v_alt = c.take<int32_t>(NS > 0 ? NS : 1);
-  L->sb.counts = c.take<int>((long long)kMaxBuckets * ntiles + 1);
-  L->sb.bsum = c.take<int>(scan_tiles((long long)kMaxBuckets * ntiles) + 1);
+  L->place = c.take<int32_t>(NS > 0 ? NS : 1);
   L->tmp = c.take<int>(NT);
+  L->cur = c.take<int>(NT);
   L->scan_bsum = c.take<int>(scan_tiles(NT) + 1);
   L->part = c.take<double>(2ll * 8 * 1024);
   return c.bytes();
@@ -680,13 +732,21 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
   {
     int grid = stride_grid(m > 0 ? m : 1, 8);
     HEF_LAUNCH("k_validate", st, k_validate<<<grid, kThreads, 0, st>>>((int)n, (int)m, P, eptr, pins, w,
-                                                                       h->status, L.keys, L.vals));
+                                                                       h->status, L.keys, L.vals, L.tmp));
     HEF_TRY_CUDA(cudaGetLastError());
   }
-  // 2. locality schedule of hyperedges: stable sort by smallest pin
+  // 2. locality schedule of hyperedges: stable counting sort by smallest pin
+  // (bucket offsets in vptr, which the transpose fills later)
   if (m > 0) {
     int grid = stride_grid(m);
-    HEF_TRY(radix_sort(L.keys, L.vals, m, bits_for(n), L.sb, st));
+    HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, L.sb.counter, st));
+    HEF_TRY_CUDA(cudaMemsetAsync(L.cur, 0, sizeof(int) * (n + 1), st));
+    HEF_LAUNCH("k_place", st, k_place<<<grid, kThreads, 0, st>>>(m, reinterpret_cast<const int32_t*>(L.keys),
+                                                                h->vptr, L.cur, h->status, L.place));
+    HEF_TRY_CUDA(cudaGetLastError());
+    HEF_LAUNCH("k_bucket_order", st, k_bucket_order<<<stride_grid(n), kThreads, 0, st>>>(
+                                         n, h->vptr, L.place, nullptr, h->status, L.vals, nullptr));
+    HEF_TRY_CUDA(cudaGetLastError());
     // internal CSC offsets
     HEF_LAUNCH("k_edge_sizes", st, k_edge_sizes<<<grid, kThreads, 0, st>>>((int)m, eptr, L.vals, h->status, L.tmp));
     HEF_TRY_CUDA(cudaGetLastError());
@@ -714,14 +774,17 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     HEF_TRY_CUDA(cudaMemsetAsync(h->win_edge, 0, sizeof(int32_t) * (num_windows(P) + 1), st));
     HEF_TRY_CUDA(cudaMemsetAsync(h->totals, 0, 8 * sizeof(double), st));
   }
-  // 3. vertex-major transpose: stable sort of CSC slots by vertex
+  // 3. vertex-major transpose: stable counting sort of the CSC slots by
+  // vertex (the degree counts of k_edge_fill, scanned, are the offsets)
   HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, L.sb.counter, st));
   if (P > 0) {
     int grid = stride_grid(P);
-    HEF_LAUNCH("k_slot_keys", st, k_slot_keys<<<grid, kThreads, 0, st>>>(P, h->cpins, h->status, L.keys, h->vslot));
+    HEF_TRY_CUDA(cudaMemsetAsync(L.cur, 0, sizeof(int) * (n + 1), st));
+    HEF_LAUNCH("k_place", st, k_place<<<grid, kThreads, 0, st>>>(P, h->cpins, h->vptr, L.cur, h->status,
+                                                                L.place));
     HEF_TRY_CUDA(cudaGetLastError());
-    HEF_TRY(radix_sort(L.keys, h->vslot, P, bits_for(n), L.sb, st));
-    HEF_LAUNCH("k_csr_edges", st, k_csr_edges<<<grid, kThreads, 0, st>>>(P, h->vslot, h->slot_edge, h->status, h->vedge));
+    HEF_LAUNCH("k_bucket_order", st, k_bucket_order<<<stride_grid(n), kThreads, 0, st>>>(
+                                         n, h->vptr, L.place, h->slot_edge, h->status, h->vslot, h->vedge));
     HEF_TRY_CUDA(cudaGetLastError());
   }
   // 4. vertex degrees of both expansions and their totals
