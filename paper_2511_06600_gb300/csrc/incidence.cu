@@ -1,8 +1,10 @@
 // Incidence build: Algorithm 1 steps 1-2 (star and clique expansions of
 // Section III-A.3, kept implicit).  Validates H on the device, orders the
 // hyperedges for locality (ascending smallest pin, stable), builds the
-// vertex-major transpose with a stable radix sort (so every later sum runs in
-// a fixed order) and the per-edge / per-vertex scalars of both expansions.
+// vertex-major transpose with a stable counting sort (so every later sum runs
+// in a fixed order) and the per-edge / per-vertex scalars of both expansions.
+// The device-wide scan and the LSD radix sort here serve the downstream
+// level (sort of R).
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -119,7 +121,7 @@ hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, unsig
 
 namespace {
 
-// ----------------------------------------------------------------- stable LSD radix sort
+// ----------------------------------------------------------------- stable LSD radix sort (downstream sort of R)
 
 // Digits of up to kMaxDigitBits bits: keys of b bits take ceil(b / 10)
 // passes of equal width (an 18-bit vertex id: two passes of 9 bits).
