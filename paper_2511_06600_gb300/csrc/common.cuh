@@ -331,6 +331,20 @@ __device__ __forceinline__ bool grid_reduce(const GridRed& r, int nslot, double*
   return true;
 }
 
+// Double-float addition (Knuth's two-sum of the high parts, the low parts
+// added and renormalised): about 44 significant bits from FP32 operations.
+struct DFloat {
+  float hi, lo;
+};
+__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float v = __fsub_rn(s, a.hi);
+  const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v)),
+                            __fadd_rn(a.lo, b.lo));
+  const float h = __fadd_rn(s, e);
+  return {h, __fsub_rn(e, __fsub_rn(h, s))};
+}
+
 inline int red_groups(int nblk) { return (nblk + kRedGroup - 1) / kRedGroup; }
 
 // In one CTA: out[slot] = sum over b < nblk of part[b * nslot + slot], for

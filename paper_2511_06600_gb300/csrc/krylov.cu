@@ -344,29 +344,31 @@ __global__ void __launch_bounds__(kThreads) k_start_dots(IncView g, ScalView<T> 
                                                          const double* __restrict__ x0c,
                                                          const double* __restrict__ x0b) {
   if (g.status[0]) return;
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   T acc[3][S];
 #pragma unroll
   for (int q = 0; q < 3; ++q)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
-  if (r < g.n) {
-    const T dc = sv.dc[r], db = sv.db[r];
-    T u[2 * S];
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < (long long)g.n + g.m;
+       r += (long long)gridDim.x * blockDim.x) {
+    if (r < g.n) {
+      const T dc = sv.dc[r], db = sv.db[r];
+      T u[2 * S];
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      u[s] = (T)x0c[r * S + s], acc[0][s] = dc * u[s];
-      u[S + s] = (T)x0b[r * S + s], acc[1][s] = db * u[S + s];
+      for (int s = 0; s < S; ++s) {
+        u[s] = (T)x0c[r * S + s], acc[0][s] += dc * u[s];
+        u[S + s] = (T)x0b[r * S + s], acc[1][s] += db * u[S + s];
+      }
+      strow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
+    } else {
+      const int i = (int)(r - g.n);
+      const T d = sv.ew[i];
+      const long long src = (long long)(g.n + g.perm[i]) * S;
+      T u[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) u[s] = (T)x0b[src + s], acc[2][s] += d * u[s];
+      strow<T, S>(kv.Be[0] + (long long)i * S, u);
     }
-    strow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
-  } else if (r < (long long)g.n + g.m) {
-    const int i = (int)(r - g.n);
-    const T d = sv.ew[i];
-    const long long src = (long long)(g.n + g.perm[i]) * S;
-    T u[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) u[s] = (T)x0b[src + s], acc[2][s] = d * u[s];
-    strow<T, S>(kv.Be[0] + (long long)i * S, u);
   }
   block_partials_qs<3, S, T>(acc, kv.red.part);
   __shared__ double tot[3 * kMaxS];
@@ -394,42 +396,44 @@ __global__ void __launch_bounds__(kThreads) k_start_write(IncView g, ScalView<T>
   pdl_wait();
   pdl_trigger();
   if (g.status[0]) return;
-  const long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   T acc[2][S];
 #pragma unroll
   for (int q = 0; q < 2; ++q)
 #pragma unroll
     for (int s = 0; s < S; ++s) acc[q][s] = 0;
-  if (r < g.n) {
-    const T dc = sv.dc[r], db = sv.db[r];
-    T u[2 * S];
-    ldrow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
+  for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < (long long)g.n + g.m;
+       r += (long long)gridDim.x * blockDim.x) {
+    if (r < g.n) {
+      const T dc = sv.dc[r], db = sv.db[r];
+      T u[2 * S];
+      ldrow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      u[s] -= (dc > 0 ? kv.cfT[(size_t)s * 4] : (T)0);
-      acc[0][s] = dc * u[s] * u[s];
-      u[S + s] -= (db > 0 ? kv.cfT[(size_t)(S + s) * 4] : (T)0);
-      acc[1][s] = db * u[S + s] * u[S + s];
-    }
-    strow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
-    if (kv.tape_c) {
-      T uc[S], ub[S];
-      split2<T, S>(u, uc, ub);
-      strow<T, S>(kv.tape_c + r * S, uc);
-      strow<T, S>(kv.tape_b + r * S, ub);
-    }
-  } else if (r < (long long)g.n + g.m) {
-    const long long i = r - g.n;  // star hyperedge row
-    const T d = sv.ew[i];
-    T u[S];
-    ldrow<T, S>(kv.Be[0] + i * S, u);
+      for (int s = 0; s < S; ++s) {
+        u[s] -= (dc > 0 ? kv.cfT[(size_t)s * 4] : (T)0);
+        acc[0][s] += dc * u[s] * u[s];
+        u[S + s] -= (db > 0 ? kv.cfT[(size_t)(S + s) * 4] : (T)0);
+        acc[1][s] += db * u[S + s] * u[S + s];
+      }
+      strow<T, 2 * S>(kv.Bv[0] + r * 2 * S, u);
+      if (kv.tape_c) {
+        T uc[S], ub[S];
+        split2<T, S>(u, uc, ub);
+        strow<T, S>(kv.tape_c + r * S, uc);
+        strow<T, S>(kv.tape_b + r * S, ub);
+      }
+    } else {
+      const long long i = r - g.n;  // star hyperedge row
+      const T d = sv.ew[i];
+      T u[S];
+      ldrow<T, S>(kv.Be[0] + i * S, u);
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      u[s] -= (d > 0 ? kv.cfT[(size_t)(S + s) * 4 + 1] : (T)0);
-      acc[1][s] = d * u[s] * u[s];
+      for (int s = 0; s < S; ++s) {
+        u[s] -= (d > 0 ? kv.cfT[(size_t)(S + s) * 4 + 1] : (T)0);
+        acc[1][s] += d * u[s] * u[s];
+      }
+      strow<T, S>(kv.Be[0] + i * S, u);
+      if (kv.tape_b) strow<T, S>(kv.tape_b + (g.n + i) * S, u);
     }
-    strow<T, S>(kv.Be[0] + i * S, u);
-    if (kv.tape_b) strow<T, S>(kv.tape_b + (g.n + i) * S, u);
   }
   block_partials_qs<2, S, T>(acc, kv.red.part);
   __shared__ double tot[2 * kMaxS];
@@ -816,20 +820,6 @@ constexpr int kCapList = 12288;               // incidences / pins cached per CT
 template <typename T, int S>
 __host__ __device__ constexpr int pers_threads() {
   return 2 * S * sizeof(T) <= 32 ? 512 : 256;
-}
-
-// Double-float addition (Knuth's two-sum of the high parts, the low parts
-// added and renormalised): about 44 significant bits from FP32 operations.
-struct DFloat {
-  float hi, lo;
-};
-__device__ __forceinline__ DFloat df_add(DFloat a, DFloat b) {
-  const float s = __fadd_rn(a.hi, b.hi);
-  const float v = __fsub_rn(s, a.hi);
-  const float e = __fadd_rn(__fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, v)), __fsub_rn(b.hi, v)),
-                            __fadd_rn(a.lo, b.lo));
-  const float h = __fadd_rn(s, e);
-  return {h, __fsub_rn(e, __fsub_rn(h, s))};
 }
 
 // In one CTA of NT threads: out[slot] = sum over b < nb of part[slot * nb + b]
@@ -1221,7 +1211,8 @@ hef_status krylov_start_s(const hef_incidence* inc, const double* x0c, const dou
                           const KView<T>& kv, cudaStream_t st) {
   IncView g = view(inc);
   const ScalView<T> sv = scal_view<T>(inc);
-  const int grid_all = blocks_for(inc->n + inc->m);
+  // grid-stride rows: few CTAs, so few partials and grid-reduction arrivals
+  const int grid_all = std::min(blocks_for(inc->n + inc->m), 4 * num_sms());
   HEF_LAUNCH("k_start_dots", st, k_start_dots<T, S><<<grid_all, kThreads, 0, st>>>(g, sv, kv, x0c, x0b));
   // the launches after the first are programmatically dependent on their
   // predecessor (each kernel waits for it before touching shared buffers)

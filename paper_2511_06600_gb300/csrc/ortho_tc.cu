@@ -248,53 +248,51 @@ __global__ void __launch_bounds__(kGrThreads, 1) k_gram_tc(GramTcArgs a) {
   if (warp == 0) tmem_dealloc(tmem, ncols);
 }
 
-// G (K x K, FP64) and c (K): fixed-order FP64 sums of the per-CTA FP32
-// partials of G_aug (column K holds the column sums).  Eight lanes per entry:
-// lane l of the eight sums partials l, l + 8, ... in order, then a fixed
-// shuffle tree; a warp takes four consecutive entries per round.
-__global__ void k_gram_tc_reduce(const float* __restrict__ part, int K, int Kq, int nchunk,
-                                 double* G, double* c) {
-  const long long KK = (long long)K * K, total = KK + K;
-  const int lane = threadIdx.x & 31, sub = lane & 7, grp = lane >> 3;
-  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+// G (K x K, FP64) and c (K): fixed-order sums of the per-CTA FP32 partials of
+// G_aug (column K holds the column sums), in double-float arithmetic (FP64
+// operations are slow on this part; about 44 significant bits), rounded to
+// FP64 at the end.  A block takes 32 consecutive entries (i, j), j in [i, K],
+// of the row-major (K + 1)-wide upper part: warp w sums the partials w, w + 8,
+// ... of its entries (each load a contiguous 128 bytes), then warp 0 adds the
+// eight warp sums in warp order.
+__global__ void __launch_bounds__(256) k_gram_tc_reduce(const float* __restrict__ part, int K, int Kq,
+                                                        int nchunk, double* G, double* c) {
+  __shared__ DFloat red[8][32];
+  const int e = threadIdx.x & 31, sub = threadIdx.x >> 5;
+  const long long total = (long long)K * (K + 1);
   const size_t stride = (size_t)Kq * Kq;
-  for (long long wb = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * 4; wb < total;
-       wb += nwarps * 4) {
-    const long long idx = wb + grp;
-    int i = 0, j = 0;
-    bool act = idx < total;
-    if (act) {
-      if (idx < KK) {
-        i = (int)(idx / K), j = (int)(idx % K);
-        act = i <= j;
-      } else {
-        i = (int)(idx - KK), j = K;
-      }
-    }
-    double s = 0.0;
+  for (long long base = (long long)blockIdx.x * 32; base < total; base += (long long)gridDim.x * 32) {
+    const long long idx = base + e;
+    const int i = (int)(idx / (K + 1)), j = (int)(idx % (K + 1));
+    const bool act = idx < total && i <= j;
+    DFloat s{0.f, 0.f};
     if (act) {
       const float* p = part + (size_t)i * Kq + j;
       int q = sub;
-      for (; q + 24 < nchunk; q += 32) {
-        float v[4];
+      for (; q + 56 < nchunk; q += 64) {
+        float v[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = __ldcg(p + (size_t)(q + 8 * u) * stride);
+        for (int u = 0; u < 8; ++u) v[u] = __ldcg(p + (size_t)(q + 8 * u) * stride);
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s += (double)v[u];
+        for (int u = 0; u < 8; ++u) s = df_add(s, DFloat{v[u], 0.f});
       }
-      for (; q < nchunk; q += 8) s += (double)__ldcg(p + (size_t)q * stride);
+      for (; q < nchunk; q += 8) s = df_add(s, DFloat{__ldcg(p + (size_t)q * stride), 0.f});
     }
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    s += __shfl_xor_sync(0xffffffffu, s, 4);
-    if (act && sub == 0) {
+    red[sub][e] = s;
+    __syncthreads();
+    if (sub == 0 && act) {
+      DFloat t = red[0][e];
+#pragma unroll
+      for (int u = 1; u < 8; ++u) t = df_add(t, red[u][e]);
+      const double sd = (double)t.hi + (double)t.lo;
       if (j < K) {
-        G[(size_t)i * K + j] = s;
-        G[(size_t)j * K + i] = s;
+        G[(size_t)i * K + j] = sd;
+        G[(size_t)j * K + i] = sd;
       } else {
-        c[i] = s;
+        c[i] = sd;
       }
     }
+    __syncthreads();
   }
 }
 
@@ -312,18 +310,16 @@ __global__ void k_rinv_split(const float* __restrict__ Rinv, const float* __rest
     RtH[idx] = h;
     RtL[idx] = x - h;
   }
-  for (long long j = (long long)blockIdx.x * blockDim.x + threadIdx.x; j < Kq;
-       j += (long long)gridDim.x * blockDim.x) {
-    float s0 = 0.f, s1 = 0.f;
-    if (j < K) {
-      int i = 0;
-      for (; i + 1 <= (int)j; i += 2) {
-        s0 += mu[i] * Rinv[(size_t)i * Kp + j];
-        s1 += mu[i + 1] * Rinv[(size_t)(i + 1) * Kp + j];
-      }
-      if (i <= (int)j) s0 += mu[i] * Rinv[(size_t)i * Kp + j];
-    }
-    muR[j] = s0 + s1;
+  // muR[j] by a warp per column: lanes stride over i <= j, then a shuffle tree
+  const int lane = threadIdx.x & 31;
+  for (long long j = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; j < Kq;
+       j += ((long long)gridDim.x * blockDim.x) >> 5) {
+    float s = 0.f;
+    if (j < K)
+      for (int i = lane; i <= (int)j; i += 32) s += mu[i] * Rinv[(size_t)i * Kp + j];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) muR[j] = s;
   }
 }
 
@@ -1198,7 +1194,7 @@ hef_status gram_tc(const void* V, bool bf16, long long ldv, long long n, int K, 
   }
   if (s) return s;
   HEF_LAUNCH("k_gram_tc_reduce", st,
-             k_gram_tc_reduce<<<stride_grid(((long long)K * K + K) * 8, 8), kThreads, 0, st>>>(
+             k_gram_tc_reduce<<<(int)std::min<long long>(((long long)K * (K + 1) + 31) / 32, 8ll * num_sms()), 256, 0, st>>>(
                  reinterpret_cast<const float*>(part), K, Kq, ctas, G, c));
   HEF_CHECK_LAUNCH();
   return HEF_OK;
