@@ -28,7 +28,7 @@ def entries():
 
 def test_record_lines_are_well_formed():
     es = entries()
-    assert {"k_node_pass", "k_edge_pass", "k_update"} <= {e[0] for e in es}
+    assert "k_krylov_steps" in {e[0] for e in es}  # the dominant kernel of the step
     for name, nbytes, digest, files in es:
         assert nbytes > 0 and len(digest) == 64, name
         for f in files:
