@@ -304,7 +304,11 @@ hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q,
  * hef_resistance_host_workspace_bytes), runs hef_build_incidence,
  * hef_krylov_basis, hef_orthonormalize and hef_edge_resistance
  * (HEF_REDUCE_MAX) on `stream`, copies R (m doubles) to the host array
- * R_out and synchronises `stream`.  Returns the first error of those calls,
+ * R_out and synchronises `stream`.  The start vectors are copied on a side
+ * stream of the library (one per calling thread and device, created on the
+ * first call) that waits for the work already queued on `stream` and joins
+ * it before the Krylov stage, so that their copy overlaps the incidence
+ * build.  Returns the first error of those calls,
  * HEF_ERR_INVALID_INPUT when the device-side validation failed, or
  * HEF_ERR_TIMEOUT when a bounded device wait expired.
  * ---------------------------------------------------------------------- */

@@ -1,11 +1,43 @@
 // Algorithm 1 end to end from host arrays (hef_resistance_host): the copies
-// in, the four calls of the path, the scores back, one synchronisation.  A C
+// in (the start vectors on a side stream, overlapping the incidence build),
+// the four calls of the path, the scores back, one synchronisation.  A C
 // caller that holds its hypergraph in host memory needs nothing else but a
 // device workspace.
 #include "internal.h"
 
 namespace hef {
 namespace {
+
+// A side stream and two events per calling thread (created on first use):
+// the start vectors, which only the Krylov stage reads, are copied on the
+// side stream while the incidence is built on the caller's stream.
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t fork = nullptr, join = nullptr;
+  int device = -1;
+};
+thread_local SideStream t_side;
+
+cudaError_t side_stream(SideStream** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  SideStream& s = t_side;
+  if (s.device != dev) {
+    if (s.s) {  // created for another device: made again for this one
+      cudaStreamDestroy(s.s);
+      cudaEventDestroy(s.fork);
+      cudaEventDestroy(s.join);
+      s = SideStream{};
+    }
+    if ((e = cudaStreamCreateWithFlags(&s.s, cudaStreamNonBlocking)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&s.fork, cudaEventDisableTiming)) != cudaSuccess) return e;
+    if ((e = cudaEventCreateWithFlags(&s.join, cudaEventDisableTiming)) != cudaSuccess) return e;
+    s.device = dev;
+  }
+  *out = &s;
+  return cudaSuccess;
+}
 
 struct HostWs {
   int64_t* eptr;
@@ -89,14 +121,26 @@ extern "C" hef_status hef_resistance_host(int64_t n, int64_t m, int64_t P, const
   if (P > 0)
     HEF_CHECK_CUDA(cudaMemcpyAsync(h.pins, pins, P * sizeof(int32_t), cudaMemcpyHostToDevice, st));
   if (m > 0) HEF_CHECK_CUDA(cudaMemcpyAsync(h.w, w, m * sizeof(double), cudaMemcpyHostToDevice, st));
+  // the starts on the side stream, after everything already queued on st
+  // (the workspace may still be in use by earlier work), joined before the
+  // Krylov stage
+  SideStream* side = nullptr;
+  HEF_CHECK_CUDA(side_stream(&side));
+  HEF_CHECK_CUDA(cudaEventRecord(side->fork, st));
+  HEF_CHECK_CUDA(cudaStreamWaitEvent(side->s, side->fork, 0));
   HEF_CHECK_CUDA(cudaMemcpyAsync(h.x0c, x0_clique, (size_t)n * S * sizeof(double),
-                                 cudaMemcpyHostToDevice, st));
+                                 cudaMemcpyHostToDevice, side->s));
   HEF_CHECK_CUDA(cudaMemcpyAsync(h.x0b, x0_star, (size_t)(n + m) * S * sizeof(double),
-                                 cudaMemcpyHostToDevice, st));
+                                 cudaMemcpyHostToDevice, side->s));
+  HEF_CHECK_CUDA(cudaEventRecord(side->join, side->s));
   hef_incidence* inc = nullptr;
   hef_status s = hef_build_incidence(n, m, P, h.eptr, h.pins, h.w, clique_mode, h.inc, h.inc_b,
                                      stream, &inc);
-  if (s) return s;
+  if (s) {
+    cudaStreamWaitEvent(st, side->join, 0);  // the copies finish before the caller reuses buffers
+    return s;
+  }
+  HEF_CHECK_CUDA(cudaStreamWaitEvent(st, side->join, 0));
   s = hef_krylov_basis(inc, k, S, dtype, h.x0c, h.x0b, h.V, h.ldv, h.kry, h.kry_b, stream);
   if (!s)
     s = hef_orthonormalize(n, K, dtype, h.V, h.ldv, nullptr, h.rank, h.ortho, h.ortho_b, stream);
