@@ -85,8 +85,10 @@ struct KView {
   T* tape_b;       // nullable: u_j of the star chains, (k+1) x (n+m) x S
   double tol;      // breakdown threshold on the D-norm of a new vector
   double* ppart;   // persistent launch: partial sums (2 x grid x 6S; the timeout
-                   // test's grid is 2 num_sms), then the published sums (2 x 6S)
-  unsigned int* pcount;  // persistent launch: arrival flags of the CTAs, then the release flag
+                   // test's grid is 2 num_sms), then kRelCopies copies (4 KB
+                   // apart) of the published sums (2 x 6S)
+  unsigned int* pcount;  // persistent launch: arrival flags of the CTAs (one per 128
+                         // bytes), then kRelCopies release flags (4 KB apart)
 };
 
 // ---------------------------------------------------------------- row I/O
@@ -932,12 +934,29 @@ __device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
   asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Barrier scratch layout.  The time of a grid barrier depended on where its
+// few hot lines landed (about 2 us per barrier between two placements 4 KB
+// apart), so they are spread: each CTA's arrival flag has a 128-byte line of
+// its own, and the release flag and the published sums exist in kRelCopies
+// copies 4 KB apart (CTA c polls and reads copy c mod kRelCopies).
+constexpr int kFlagStride = 32;   // uint32 words between arrival flags (128 bytes)
+constexpr int kRelCopies = 4;
+constexpr int kRelStride = 1024;  // uint32 words between release copies (4 KB)
+constexpr int kPubStride = 512;   // doubles between copies of the published sums (4 KB)
+__host__ __device__ inline size_t rel_base(int Gmax) {  // first release copy (word index)
+  return ((size_t)Gmax * kFlagStride + kRelStride - 1) / kRelStride * kRelStride;
+}
+__host__ __device__ inline size_t flag_words(int Gmax) {
+  return rel_base(Gmax) + (size_t)kRelCopies * kRelStride;
+}
+
 // Grid barrier number `ph` with its phase's reduction.  Every CTA writes its
 // partial sums to part[ph & 1] (slot-major) and then, with a release store, its own
 // arrival flag flags[b] = ph + 1.  CTA 0 reduces: its threads poll the G
 // flags in parallel (acquire loads), it sums all partials in a fixed order
-// (reduce_slots_wide), publishes the N results in pub[ph & 1] and releases
-// the others through flags[G] = ph + 1; each CTA then copies the results to
+// (reduce_slots_wide), publishes the N results in every copy of pub[ph & 1]
+// and releases the others through every copy of the release flag; each CTA
+// reads its own copy and then copies the results to
 // `out` (shared memory).  Double buffers suffice: a buffer is written again
 // only at barrier ph + 2, which no CTA reaches before every CTA has read
 // barrier ph's results (CTA 0 waits for all arrivals of ph + 1 first).  The
@@ -950,7 +969,8 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
                                          int b, int G) {
   constexpr int N = NQ * S;
   double* buf = part + (size_t)(ph & 1) * G * 6 * S;
-  double* res = pub + (size_t)(ph & 1) * 6 * S;
+  const int cp = b % kRelCopies;  // this CTA's copy of the release flag and the sums
+  unsigned int* rel = flags + rel_base(G);
   const unsigned int want = (unsigned int)ph + 1u;
   // FP32 forms: FP32 partials (their values are FP32 sums), reduced in
   // double-float arithmetic
@@ -959,13 +979,13 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
   block_partials_qs<NQ, S, T, NT, 8, P>(acc, pbuf, b, G);
   __shared__ int go;
   __syncthreads();
-  if (threadIdx.x == 0) st_release(flags + b, want);
+  if (threadIdx.x == 0) st_release(flags + (size_t)b * kFlagStride, want);
   if (b == 0) {
     // arrivals: thread t watches CTAs t, t + NT, ...
     int ok = 1;
     for (int c = threadIdx.x; c < G && ok; c += NT) {
       unsigned int it = 0;
-      while (ld_acquire(flags + c) < want) {
+      while (ld_acquire(flags + (size_t)c * kFlagStride) < want) {
         if (++it > kBarIters) {
           atomicOr(status, HEF_WAIT_TIMEOUT);
           ok = 0;
@@ -979,15 +999,16 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
     }
     if (!__syncthreads_and(ok)) return false;
     reduce_slots_wide<NT, sizeof(T) == 4, P>(pbuf, G, N, out);
-    for (int t = threadIdx.x; t < N; t += NT) res[t] = out[t];
+    for (int t = threadIdx.x; t < kRelCopies * N; t += NT)
+      pub[(size_t)(t / N) * kPubStride + (size_t)(ph & 1) * 6 * S + t % N] = out[t % N];
     __syncthreads();
-    if (threadIdx.x == 0) st_release(flags + G, want);
+    if (threadIdx.x < kRelCopies) st_release(rel + (size_t)threadIdx.x * kRelStride, want);
     return true;
   }
   if (threadIdx.x == 0) {
     unsigned int it = 0;
     int ok = 1;
-    while (ld_acquire(flags + G) < want) {
+    while (ld_acquire(rel + (size_t)cp * kRelStride) < want) {
       if (++it > kBarIters) {
         atomicOr(status, HEF_WAIT_TIMEOUT);
         ok = 0;
@@ -1002,6 +1023,7 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
   }
   __syncthreads();
   if (!go) return false;
+  const double* res = pub + (size_t)cp * kPubStride + (size_t)(ph & 1) * 6 * S;
   for (int t = threadIdx.x; t < N; t += NT) out[t] = __ldcg(res + t);
   __syncthreads();
   return true;
@@ -1193,8 +1215,8 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->red.gpart = c.take<double>((size_t)red_groups((int)maxblk) * 6 * S);
   kv->red.gcnt = c.take<unsigned int>(red_groups((int)maxblk) + 1);
   kv->red.tcnt = c.take<unsigned int>(1);
-  kv->ppart = c.take<double>((size_t)2 * num_sms() * 2 * 6 * S + 2 * 6 * S);
-  kv->pcount = c.take<unsigned int>((size_t)2 * num_sms() + 1);
+  kv->ppart = c.take<double>((size_t)2 * num_sms() * 2 * 6 * S + (size_t)kRelCopies * kPubStride);
+  kv->pcount = c.take<unsigned int>(flag_words(2 * num_sms()));
   return c.bytes();
 }
 
@@ -1247,7 +1269,7 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_krylov_steps<T, S, TV>, NT, smem) ==
             cudaSuccess &&
         occ >= 1) {
-      HEF_CHECK_CUDA(cudaMemsetAsync(kv.pcount, 0, (2 * num_sms() + 1) * sizeof(unsigned int), st));
+      HEF_CHECK_CUDA(cudaMemsetAsync(kv.pcount, 0, flag_words(2 * num_sms()) * sizeof(unsigned int), st));
       // the timeout test launches twice the resident grid as a plain launch,
       // so that the first barrier cannot complete and its bounded wait runs out
       const int grid = num_sms() * (t_force_oversized ? 2 : 1);
@@ -1430,7 +1452,7 @@ hef_status batch_steps_s(const KrylovBatchArg* items, int G, int k, cudaStream_t
       it.ldv = a.ldv;
       it.status = a.inc->status;
       bt->cta0[i + 1] = bt->cta0[i] + share[i];
-      HEF_CHECK_CUDA(cudaMemsetAsync(it.kv.pcount, 0, (2 * num_sms() + 1) * sizeof(unsigned int), st));
+      HEF_CHECK_CUDA(cudaMemsetAsync(it.kv.pcount, 0, flag_words(2 * num_sms()) * sizeof(unsigned int), st));
     }
     const KBatch<T, TV>& arg = *bt;
     cudaError_t e = cudaSuccess;
