@@ -369,8 +369,8 @@ __global__ void k_edge_fill(int m, int clique_mode, const int64_t* __restrict__ 
                             const int32_t* __restrict__ sched, const int32_t* __restrict__ ceptr,
                             unsigned int* status, unsigned int* counter, int32_t* perm,
                             int32_t* cpins, int32_t* slot_edge, double* ew, double* ewh, double* ez,
-                            float* f_ew, float* f_ewh, float* f_ez, int* deg, double* part,
-                            double* totals) {
+                            float* f_ew, float* f_ewh, float* f_ez, double* ec, int* deg,
+                            double* part, double* totals) {
   if (status[0]) return;
   double wsum = 0.0;
   const int lane = threadIdx.x & 31;
@@ -431,6 +431,7 @@ __global__ void k_edge_fill(int m, int clique_mode, const int64_t* __restrict__ 
       wsum += we;
     }
     ew[i] = wa, ewh[i] = bh, ez[i] = z;
+    ec[i] = k >= 2 ? bh * (double)(k - 1) : 0.0;  // clique degree contribution, added per incidence
     f_ew[i] = (float)wa, f_ewh[i] = (float)bh, f_ez[i] = (float)z;
   }
   double v[1] = {wsum};
@@ -547,7 +548,7 @@ __global__ void k_bucket_order(long long nb, const int32_t* __restrict__ off,
 // Vertex degrees of both expansions, in CSR (ascending hyperedge) order:
 // d_c(v) = sum_e ewh_e (|e|-1), d_b(v) = sum_e w_e/|e|.
 __global__ void k_node_scalars(int n, const int32_t* __restrict__ vptr, const int32_t* __restrict__ vedge,
-                               const int32_t* __restrict__ ceptr, const double* __restrict__ ewh,
+                               const double* __restrict__ ec, const double* __restrict__ ewh,
                                const double* __restrict__ ez, unsigned int* status,
                                unsigned int* counter, double* dc, double* db, double* inv_dc,
                                double* inv_db, double* wsc, float* f_dc, float* f_db,
@@ -559,24 +560,24 @@ __global__ void k_node_scalars(int n, const int32_t* __restrict__ vptr, const in
        v += (long long)gridDim.x * blockDim.x) {
     double c = 0.0, b = 0.0, ws = 0.0;
     const int t0 = vptr[v], t1 = vptr[v + 1];
-    // four incidences per round: their hyperedge ids, then their offsets and
-    // weights, each set of loads in flight together (sums in incidence order)
+    // four incidences per round: their hyperedge ids, then their three
+    // per-edge terms, each set of loads in flight together (sums in incidence
+    // order; the clique term ewh_e (|e|-1) comes precomputed per hyperedge)
     for (int t = t0; t < t1; t += 4) {
       int e[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) e[u] = vedge[min(t + u, t1 - 1)];
-      int k[4];
-      double wh[4], wz[4];
+      double wc[4], wh[4], wz[4];
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        k[u] = ceptr[e[u] + 1] - ceptr[e[u]];
+        wc[u] = ec[e[u]];
         wh[u] = ewh[e[u]];
         wz[u] = ez[e[u]];
       }
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
         if (t + u < t1) {
-          c += wh[u] * (double)(k[u] - 1);
+          c += wc[u];
           b += wz[u];
           ws += wh[u];
         }
@@ -618,6 +619,7 @@ struct IncLayout {
   int* tmp;       // max(m, n) + 1 ints (sizes / degree counts, scanned in place)
   int* cur;       // max(m, n) + 1 ints: cursors of the counting sorts
   int32_t* place; // max(m, P): indices as placed in their buckets
+  double* ec;     // m: ewh_e (|e| - 1), the clique-degree term of each hyperedge
   int* scan_bsum;
   double* part;
 };
@@ -659,6 +661,7 @@ size_t carve_incidence(void* base, long long n, long long m, long long P, IncLay
   L->keys = c.take<uint32_t>(NS > 0 ? NS : 1);
   L->vals = c.take<int32_t>(NS > 0 ? NS : 1);
   L->place = c.take<int32_t>(NS > 0 ? NS : 1);
+  L->ec = c.take<double>(m > 0 ? m : 1);
   L->tmp = c.take<int>(NT);
   L->cur = c.take<int>(NT);
   L->scan_bsum = c.take<int>(scan_tiles(NT) + 1);
@@ -756,7 +759,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     HEF_TRY_CUDA(cudaMemsetAsync(L.tmp, 0, sizeof(int) * (n + 1), st));
     HEF_LAUNCH("k_edge_fill", st, k_edge_fill<<<grid, kThreads, 0, st>>>((int)m, clique_mode, eptr, pins, w, L.vals, h->ceptr,
                                            h->status, h->counter, h->perm, h->cpins, h->slot_edge,
-                                           h->ew, h->ewh, h->ez, h->f_ew, h->f_ewh, h->f_ez, L.tmp,
+                                           h->ew, h->ewh, h->ez, h->f_ew, h->f_ewh, h->f_ez, L.ec, L.tmp,
                                            L.part, h->totals));
     HEF_TRY_CUDA(cudaGetLastError());
     // list of large hyperedges (scored by whole CTAs)
@@ -792,7 +795,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
   // 4. vertex degrees of both expansions and their totals
   {
     int grid = stride_grid(n);
-    HEF_LAUNCH("k_node_scalars", st, k_node_scalars<<<grid, kThreads, 0, st>>>((int)n, h->vptr, h->vedge, h->ceptr, h->ewh, h->ez,
+    HEF_LAUNCH("k_node_scalars", st, k_node_scalars<<<grid, kThreads, 0, st>>>((int)n, h->vptr, h->vedge, L.ec, h->ewh, h->ez,
                                               h->status, h->counter, h->dc, h->db, h->inv_dc,
                                               h->inv_db, h->wsc, h->f_dc, h->f_db, h->f_inv_dc,
                                               h->f_inv_db, h->f_wsc, L.part, h->totals));
