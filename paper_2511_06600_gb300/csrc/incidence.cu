@@ -20,101 +20,130 @@ constexpr int kTile = kThreads * kItems;        // 2048 items per tile
 
 // ----------------------------------------------------------------- scan
 
-__device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
-  __shared__ int wsum[kThreads / 32];
+// Single-pass scan (decoupled look-back): tiles of kScanTile items, each CTA
+// takes the next tile id from an atomic counter (so a tile waits only on
+// tiles that running CTAs have claimed), publishes its aggregate, then warp 0
+// looks back over up to 32 predecessors at a time (aggregates summed until
+// the nearest published prefix) and publishes its inclusive prefix.  Status
+// word of tile t: high half 0 empty, 1 aggregate, 2 prefix; low half the
+// value.  Bounded waits set HEF_WAIT_TIMEOUT in *err (when given).
+constexpr int kScanThreads = 1024;
+constexpr int kScanTile = kScanThreads * kItems;  // 8192
+constexpr unsigned int kScanWaitIters = 1u << 22;
+
+__device__ __forceinline__ int block_exclusive_scan_1024(int v, int* total) {
+  __shared__ int wsum[32];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   int x = v;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    int y = __shfl_up_sync(0xffffffffu, x, o);
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) wsum[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    int s = lane < kThreads / 32 ? wsum[lane] : 0;
+    int q = wsum[lane];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      int y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
+      const int y = __shfl_up_sync(0xffffffffu, q, o);
+      if (lane >= o) q += y;
     }
-    if (lane < kThreads / 32) wsum[lane] = s;
+    wsum[lane] = q;
   }
   __syncthreads();
-  int incl = x + (wid ? wsum[wid - 1] : 0);
-  *total = wsum[kThreads / 32 - 1];
+  const int incl = x + (wid ? wsum[wid - 1] : 0);
+  *total = wsum[31];
   __syncthreads();
   return incl - v;
 }
 
-// Tile sums bsum[b] of in; the last CTA to finish (counter, zero on entry and
-// on exit) then scans them in place (exclusive) and writes the grand total to
-// bsum[nb].
-__global__ void k_scan_tiles(const int* __restrict__ in, int N, int* __restrict__ bsum,
-                             unsigned int* counter) {
-  const long long base = (long long)blockIdx.x * kTile;
-  int s = 0;
-  for (int j = 0; j < kItems; ++j) {
-    long long i = base + (long long)threadIdx.x * kItems + j;
-    if (i < N) s += in[i];
-  }
-  int total;
-  block_exclusive_scan(s, &total);
-  if (threadIdx.x == 0) bsum[blockIdx.x] = total;
-  if (!last_block_done(counter)) return;
-  const int nb = gridDim.x;
-  const int per = (nb + kThreads - 1) / kThreads;
-  const int b0 = threadIdx.x * per;
-  int t = 0;
-  for (int i = 0; i < per; ++i)
-    if (b0 + i < nb) t += __ldcg(bsum + b0 + i);
-  int grand;
-  int run = block_exclusive_scan(t, &grand);
-  for (int i = 0; i < per; ++i)
-    if (b0 + i < nb) {
-      const int v = __ldcg(bsum + b0 + i);
-      bsum[b0 + i] = run;
-      run += v;
-    }
-  if (threadIdx.x == 0) bsum[nb] = grand;
-}
-
-__global__ void k_scan_apply(const int* __restrict__ in, int N, const int* __restrict__ bsum,
-                             int* __restrict__ out) {
-  const long long base = (long long)blockIdx.x * kTile + (long long)threadIdx.x * kItems;
+__global__ void __launch_bounds__(kScanThreads) k_scan1(const int* in, int* out, int N, int ntiles,
+                                                        unsigned int* tctr,
+                                                        unsigned long long* stat,
+                                                        unsigned int* err) {
+  __shared__ int s_tile, s_excl;
+  if (threadIdx.x == 0) s_tile = (int)atomicAdd(tctr, 1u);
+  __syncthreads();
+  const int t = s_tile;
+  const long long base = (long long)t * kScanTile + (long long)threadIdx.x * kItems;
   int v[kItems];
-  int s = 0;
+  int sum = 0;
+#pragma unroll
   for (int j = 0; j < kItems; ++j) {
-    long long i = base + j;
-    v[j] = i < N ? in[i] : 0;
-    s += v[j];
+    v[j] = base + j < N ? in[base + j] : 0;
+    sum += v[j];
   }
   int total;
-  int run = block_exclusive_scan(s, &total) + bsum[blockIdx.x];
+  const int local = block_exclusive_scan_1024(sum, &total);
+  if (ntiles > 1 && threadIdx.x < 32) {  // one tile: nothing to publish or look back on
+    const int lane = threadIdx.x;
+    if (lane == 0) {
+      const unsigned long long w = ((t == 0 ? 2ull : 1ull) << 32) | (unsigned int)total;
+      asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(stat + t), "l"(w) : "memory");
+    }
+    int excl = 0;
+    for (int p = t - 1; p >= 0;) {
+      const int q = p - lane;
+      unsigned long long w = 2ull << 32;  // before tile 0: a zero prefix
+      if (q >= 0) {
+        unsigned int it = 0;
+        do {
+          asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(w) : "l"(stat + q) : "memory");
+        } while ((w >> 32) == 0ull && ++it < kScanWaitIters);
+        if ((w >> 32) == 0ull && err) atomicOr(err, HEF_WAIT_TIMEOUT);
+      }
+      const unsigned pm = __ballot_sync(0xffffffffu, (w >> 32) == 2ull);
+      const int lp = pm ? __ffs(pm) - 1 : 32;  // nearest published prefix
+      int val = (lane <= lp && q >= 0) ? (int)(unsigned int)(w & 0xffffffffull) : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) val += __shfl_xor_sync(0xffffffffu, val, o);
+      excl += val;
+      if (lp < 32) break;
+      p -= 32;
+    }
+    if (lane == 0) {
+      if (t > 0) {
+        const unsigned long long w = (2ull << 32) | (unsigned int)(excl + total);
+        asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(stat + t), "l"(w) : "memory");
+      }
+      s_excl = excl;
+    }
+  } else if (threadIdx.x == 0) {
+    s_excl = 0;
+  }
+  __syncthreads();
+  int run = s_excl + local;
+#pragma unroll
   for (int j = 0; j < kItems; ++j) {
-    long long i = base + j;
-    if (i < N) out[i] = run;
+    if (base + j < N) out[base + j] = run;
     run += v[j];
   }
-  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[N] = bsum[gridDim.x];
+  if (t == ntiles - 1 && threadIdx.x == 0) out[N] = s_excl + total;
 }
 
 }  // namespace
 
 int scan_tiles(long long N) { return (int)((N + kTile - 1) / kTile); }
 
-// out[0..N] = exclusive scan of in[0..N); out[N] = total.  bsum needs
-// scan_tiles(N) + 1 ints; counter is zero on entry (and on exit).  `in` and
-// `out` may alias.
+// out[0..N] = exclusive scan of in[0..N); out[N] = total (k_scan1).  bsum
+// needs scan_tiles(N) + 1 ints; counter is zero on entry (and on exit).  `in`
+// and `out` may alias.
 hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, unsigned int* counter,
-                          cudaStream_t st) {
-  int nb = scan_tiles(N);
-  if (nb == 0) {
+                          cudaStream_t st, unsigned int* err) {
+  (void)counter;  // the single-pass scan keeps its tile counter in bsum
+  if (N == 0) {
     HEF_CHECK_CUDA(cudaMemsetAsync(out, 0, sizeof(int), st));
     return HEF_OK;
   }
-  HEF_LAUNCH("k_scan_tiles", st, k_scan_tiles<<<nb, kThreads, 0, st>>>(in, (int)N, bsum, counter));
-  HEF_LAUNCH("k_scan_apply", st, k_scan_apply<<<nb, kThreads, 0, st>>>(in, (int)N, bsum, out));
+  // bsum (scan_tiles(N) + 1 ints, 8-byte aligned) holds the tile counter and,
+  // for more than one tile, a 64-bit status word per kScanTile tile:
+  // 2 + 2 ceil(N / 8192) ints, which then never exceeds it
+  const int nt = (int)((N + kScanTile - 1) / kScanTile);
+  HEF_CHECK_CUDA(cudaMemsetAsync(bsum, 0, (size_t)(nt == 1 ? 1 : 2 + 2 * nt) * sizeof(int), st));
+  HEF_LAUNCH("k_scan1", st, k_scan1<<<nt, kScanThreads, 0, st>>>(
+                                in, out, (int)N, nt, reinterpret_cast<unsigned int*>(bsum),
+                                reinterpret_cast<unsigned long long*>(bsum + 2), err));
   HEF_CHECK_LAUNCH();
   return HEF_OK;
 }
@@ -744,7 +773,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
   // (bucket offsets in vptr, which the transpose fills later)
   if (m > 0) {
     int grid = stride_grid(m);
-    HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, L.sb.counter, st));
+    HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, L.sb.counter, st, h->status));
     HEF_TRY_CUDA(cudaMemsetAsync(L.cur, 0, sizeof(int) * (n + 1), st));
     HEF_LAUNCH("k_place", st, k_place<<<grid, kThreads, 0, st>>>(m, reinterpret_cast<const int32_t*>(L.keys),
                                                                 h->vptr, L.cur, h->status, L.place));
@@ -755,7 +784,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     // internal CSC offsets
     HEF_LAUNCH("k_edge_sizes", st, k_edge_sizes<<<grid, kThreads, 0, st>>>((int)m, eptr, L.vals, h->status, L.tmp));
     HEF_TRY_CUDA(cudaGetLastError());
-    HEF_TRY(exclusive_scan(L.tmp, h->ceptr, m, L.scan_bsum, L.sb.counter, st));
+    HEF_TRY(exclusive_scan(L.tmp, h->ceptr, m, L.scan_bsum, L.sb.counter, st, h->status));
     HEF_TRY_CUDA(cudaMemsetAsync(L.tmp, 0, sizeof(int) * (n + 1), st));
     HEF_LAUNCH("k_edge_fill", st, k_edge_fill<<<grid, kThreads, 0, st>>>((int)m, clique_mode, eptr, pins, w, L.vals, h->ceptr,
                                            h->status, h->counter, h->perm, h->cpins, h->slot_edge,
@@ -766,7 +795,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
     HEF_LAUNCH("k_big_flags", st, k_big_flags<<<grid, kThreads, 0, st>>>((int)m, h->ceptr, h->status,
                                                                         h->big_pos));
     HEF_TRY_CUDA(cudaGetLastError());
-    HEF_TRY(exclusive_scan(h->big_pos, h->big_pos, m, L.scan_bsum, L.sb.counter, st));
+    HEF_TRY(exclusive_scan(h->big_pos, h->big_pos, m, L.scan_bsum, L.sb.counter, st, h->status));
     HEF_LAUNCH("k_windows", st, k_windows<<<stride_grid(m + 1), kThreads, 0, st>>>(
                                     (int)m, P, h->ceptr, h->status, h->win_edge));
     HEF_TRY_CUDA(cudaGetLastError());
@@ -781,7 +810,7 @@ extern "C" hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P, const
   }
   // 3. vertex-major transpose: stable counting sort of the CSC slots by
   // vertex (the degree counts of k_edge_fill, scanned, are the offsets)
-  HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, L.sb.counter, st));
+  HEF_TRY(exclusive_scan(L.tmp, h->vptr, n, L.scan_bsum, L.sb.counter, st, h->status));
   if (P > 0) {
     int grid = stride_grid(P);
     HEF_TRY_CUDA(cudaMemsetAsync(L.cur, 0, sizeof(int) * (n + 1), st));

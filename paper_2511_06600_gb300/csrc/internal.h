@@ -182,10 +182,11 @@ inline size_t carve_tape(void* base, long long n, long long m, int k, int S, siz
 // downstream calls.
 int scan_tiles(long long N);
 // out[0..N] = exclusive scan of in[0..N); out[N] = total.  bsum needs
-// scan_tiles(N) + 1 ints; counter is zero on entry (and on exit); in and out
-// may alias.
+// scan_tiles(N) + 1 ints (8-byte aligned); counter is zero on entry (and on
+// exit); in and out may alias; a bounded wait that expires sets
+// HEF_WAIT_TIMEOUT in *err when err is given.
 hef_status exclusive_scan(const int* in, int* out, long long N, int* bsum, unsigned int* counter,
-                          cudaStream_t st);
+                          cudaStream_t st, unsigned int* err = nullptr);
 struct SortBufs {
   uint32_t* k_alt;
   int32_t* v_alt;
