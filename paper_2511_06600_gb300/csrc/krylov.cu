@@ -84,11 +84,12 @@ struct KView {
   T* tape_c;       // nullable: u_j of the clique chains, (k+1) x n x S
   T* tape_b;       // nullable: u_j of the star chains, (k+1) x (n+m) x S
   double tol;      // breakdown threshold on the D-norm of a new vector
-  double* ppart;   // persistent launch: partial sums (2 x grid x 6S; the timeout
-                   // test's grid is 2 num_sms), then kRelCopies copies (4 KB
-                   // apart) of the published sums (2 x 6S)
-  unsigned int* pcount;  // persistent launch: arrival flags of the CTAs (one per 128
-                         // bytes), then kRelCopies release flags (4 KB apart)
+  double* ppart;   // persistent launch: partial sums (2 x grid x 9S; the timeout
+                   // test's grid is 2 num_sms)
+  unsigned int* pcount;  // persistent launch: kRelCopies arrival counters (4 KB apart)
+  int capi, capl;  // persistent launch: vertices / hyperedges (capi) and incidences /
+                   // pins (capl) whose offsets and index lists a CTA keeps in shared
+                   // memory
 };
 
 // ---------------------------------------------------------------- row I/O
@@ -109,11 +110,69 @@ __device__ __forceinline__ V ld1(const V* p) {
   else return __ldg(p);
 }
 
-// N contiguous values with the widest vector access the row size allows
-// (rows and records start at multiples of their own size).
+// One 32-byte access (the 256-bit loads and stores of sm_100 and later): a
+// record that fills an L2 sector costs one request instead of two 16-byte
+// ones.  p is 32-byte aligned.  The coherent (CG) loads and the stores are
+// ordered with the grid barriers' memory operations like the plain accesses
+// they replace.
+template <bool CG>
+__device__ __forceinline__ void ld32B(const float* p, float* v) {
+  if constexpr (CG)
+    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]),
+                   "=f"(v[6]), "=f"(v[7])
+                 : "l"(p)
+                 : "memory");
+  else
+    asm("ld.global.nc.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+        : "=f"(v[0]), "=f"(v[1]), "=f"(v[2]), "=f"(v[3]), "=f"(v[4]), "=f"(v[5]), "=f"(v[6]),
+          "=f"(v[7])
+        : "l"(p));
+}
+template <bool CG>
+__device__ __forceinline__ void ld32B(const double* p, double* v) {
+  if constexpr (CG)
+    asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
+                 : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+                 : "l"(p)
+                 : "memory");
+  else
+    asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];"
+        : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+        : "l"(p));
+}
+__device__ __forceinline__ void st32B(float* p, const float* v) {
+  asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]), "f"(v[1]),
+               "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void st32B(double* p, const double* v) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]),
+               "d"(v[3])
+               : "memory");
+}
+
+__device__ __forceinline__ void st32B_cs(float* p, const float* v) {
+  asm volatile("st.global.cs.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"l"(p), "f"(v[0]),
+               "f"(v[1]), "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+               : "memory");
+}
+__device__ __forceinline__ void st32B_cs(double* p, const double* v) {
+  asm volatile("st.global.cs.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]),
+               "d"(v[2]), "d"(v[3])
+               : "memory");
+}
+
+// N contiguous values with the widest vector access the row size allows.
+// Rows and records start at multiples of their own size from 256-byte aligned
+// buffers, so a row of a multiple of 32 bytes is 32-byte aligned.
 template <typename T, int N, bool CG = false>
 __device__ __forceinline__ void ldrow(const T* __restrict__ p, T (&v)[N]) {
-  if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+  if constexpr ((N * sizeof(T)) % 32 == 0) {
+    constexpr int E = 32 / sizeof(T);
+#pragma unroll
+    for (int i = 0; i < N / E; ++i) ld32B<CG>(p + E * i, v + E * i);
+  } else if constexpr (sizeof(T) == 4 && N % 4 == 0) {
     const float4* q = reinterpret_cast<const float4*>(p);
 #pragma unroll
     for (int i = 0; i < N / 4; ++i) {
@@ -142,7 +201,11 @@ __device__ __forceinline__ void ldrow(const T* __restrict__ p, T (&v)[N]) {
 
 template <typename T, int N>
 __device__ __forceinline__ void strow(T* __restrict__ p, const T (&v)[N]) {
-  if constexpr (sizeof(T) == 4 && N % 4 == 0) {
+  if constexpr ((N * sizeof(T)) % 32 == 0) {
+    constexpr int E = 32 / sizeof(T);
+#pragma unroll
+    for (int i = 0; i < N / E; ++i) st32B(p + E * i, v + E * i);
+  } else if constexpr (sizeof(T) == 4 && N % 4 == 0) {
     float4* q = reinterpret_cast<float4*>(p);
 #pragma unroll
     for (int i = 0; i < N / 4; ++i) q[i] = make_float4(v[4 * i], v[4 * i + 1], v[4 * i + 2], v[4 * i + 3]);
@@ -188,7 +251,17 @@ __device__ __forceinline__ void strow_cs(T* __restrict__ p, const T (&v)[N]) {
 // type, or BF16 rounded to nearest).
 template <typename T, int N, typename TV>
 __device__ __forceinline__ void store_basis(TV* __restrict__ p, const T (&v)[N]) {
-  if constexpr (std::is_same<T, TV>::value) {
+  if constexpr (std::is_same<T, TV>::value && (N * sizeof(T)) % 32 == 0) {
+    // the caller's basis rows need only 16-byte alignment: 32-byte stores
+    // where the record happens to be 32-byte aligned
+    if ((reinterpret_cast<uintptr_t>(p) & 31) == 0) {
+      constexpr int E = 32 / sizeof(T);
+#pragma unroll
+      for (int i = 0; i < N / E; ++i) st32B_cs(p + E * i, v + E * i);
+    } else {
+      strow_cs<T, N>(p, v);
+    }
+  } else if constexpr (std::is_same<T, TV>::value) {
     strow_cs<T, N>(p, v);
   } else if constexpr (N % 8 == 0) {
 #pragma unroll
@@ -816,6 +889,7 @@ constexpr unsigned int kBarIters = 1u << 21;  // bounded barrier wait (polls of 
 constexpr int kCapItems = 4096;               // vertices / hyperedges cached per CTA
 constexpr long long kPersistentMinRows = 32768;  // n + m from which the persistent form runs
 constexpr int kCapList = 12288;               // incidences / pins cached per CTA
+constexpr int kPartSlots = 9;                 // reduction slots per start (see part_buffer)
 
 // Threads of the persistent CTA: 128 registers a thread (the fused phases
 // spill at 64) for records of up to 32 bytes, 255 for wider records.
@@ -886,16 +960,19 @@ __device__ __forceinline__ void reduce_slots_wide(const P* part, int nb, int N, 
 }
 
 // Dynamic shared memory of the persistent kernel.
-// Layout: the vertex and edge lists at fixed offsets (so that their addresses
-// take no registers), then inv_nu, te, the reduction results, itot (FP64),
-// cfT and nuT (working type).
-constexpr size_t kListBytes = (size_t)2 * (kCapItems + 1 + kCapList) * sizeof(int);
+// Layout: the vertex and edge lists (capi + 1 offsets and capl entries each),
+// then inv_nu, the reduction results, itot (FP64), cfT and nuT (working
+// type).  The lists take what the balanced ranges need (the rest of the SM's
+// storage stays L1); entries past their capacity are read from global memory.
+__host__ __device__ inline size_t list_bytes(int capi, int capl) {
+  return ((size_t)2 * (capi + 1 + capl) * sizeof(int) + 15) / 16 * 16;
+}
 template <typename T>
-__host__ __device__ inline size_t pers_smem(int k, int S) {
+__host__ __device__ inline size_t pers_smem(int k, int S, int capi, int capl) {
   const size_t nc = (size_t)(k + 1) * 2 * S;
-  size_t b = kListBytes;
+  size_t b = list_bytes(capi, capl);
   b += nc * sizeof(double);                                            // inv_nu
-  b += (size_t)(3 + 6 + 1) * S * sizeof(double) + 4 * sizeof(double);  // te, red, spare, itot
+  b += (size_t)(kPartSlots + 1) * S * sizeof(double) + 4 * sizeof(double);  // red, spare, itot
   b += nc * 4 * sizeof(T) + nc * sizeof(T);                            // cfT, nuT
   return (b + 15) / 16 * 16;
 }
@@ -920,95 +997,49 @@ __device__ __forceinline__ int warp_lower_bound(int hi, long long t, Key key) {
   return lo + __ffs(mask) - 1;
 }
 
-__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
-  unsigned int v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
 __device__ __forceinline__ bool stopped(const unsigned int* status) {
   return *reinterpret_cast<const volatile unsigned int*>(status) != 0u;
 }
 
-__device__ __forceinline__ void st_release(unsigned int* p, unsigned int v) {
-  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Barrier scratch layout.  The time of a grid barrier depended on where its
 // few hot lines landed (about 2 us per barrier between two placements 4 KB
-// apart), so they are spread: each CTA's arrival flag has a 128-byte line of
-// its own, and the release flag and the published sums exist in kRelCopies
-// copies 4 KB apart (CTA c polls and reads copy c mod kRelCopies).
-constexpr int kFlagStride = 32;   // uint32 words between arrival flags (128 bytes)
+// apart), so the arrival counter exists in kRelCopies copies 4 KB apart:
+// every CTA adds to all of them and CTA c polls copy c mod kRelCopies.
 constexpr int kRelCopies = 4;
-constexpr int kRelStride = 1024;  // uint32 words between release copies (4 KB)
-constexpr int kPubStride = 512;   // doubles between copies of the published sums (4 KB)
-__host__ __device__ inline size_t rel_base(int Gmax) {  // first release copy (word index)
-  return ((size_t)Gmax * kFlagStride + kRelStride - 1) / kRelStride * kRelStride;
-}
-__host__ __device__ inline size_t flag_words(int Gmax) {
-  return rel_base(Gmax) + (size_t)kRelCopies * kRelStride;
+constexpr int kRelStride = 1024;  // uint32 words between copies (4 KB)
+__host__ __device__ inline size_t flag_words(int /*Gmax*/) { return (size_t)kRelCopies * kRelStride; }
+
+// Grid barrier number `ph`.  Every CTA, after its partial sums are written,
+// adds 1 with release semantics to each of the kRelCopies arrival counters
+// (4 KB apart); thread 0 of CTA b polls copy b mod kRelCopies with relaxed
+// loads until all G CTAs of barrier ph have arrived (G (ph + 1) arrivals),
+// then an acquire fence orders the partials' reads after the arrivals.  The
+// counters rise monotonically within a launch (zeroed before it), and a copy
+// first reaches G (ph + 1) only when every CTA has arrived at barrier ph (no
+// CTA adds for ph + 1 before it has passed ph).  Every wait is bounded; on
+// expiry HEF_WAIT_TIMEOUT is set in the status word.  Returns false when the
+// launch must stop.
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Grid barrier number `ph` with its phase's reduction.  Every CTA writes its
-// partial sums to part[ph & 1] (slot-major) and then, with a release store, its own
-// arrival flag flags[b] = ph + 1.  CTA 0 reduces: its threads poll the G
-// flags in parallel (acquire loads), it sums all partials in a fixed order
-// (reduce_slots_wide), publishes the N results in every copy of pub[ph & 1]
-// and releases the others through every copy of the release flag; each CTA
-// reads its own copy and then copies the results to
-// `out` (shared memory).  Double buffers suffice: a buffer is written again
-// only at barrier ph + 2, which no CTA reaches before every CTA has read
-// barrier ph's results (CTA 0 waits for all arrivals of ph + 1 first).  The
-// flags rise monotonically within a launch (zeroed before it).  Every wait is
-// bounded; on expiry HEF_WAIT_TIMEOUT is set in the status word.  Returns
-// false when the launch must stop.
-template <int NQ, int S, int NT, typename T>
-__device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, double* pub, int ph,
-                                         unsigned int* flags, unsigned int* status, double* out,
-                                         int b, int G) {
-  constexpr int N = NQ * S;
-  double* buf = part + (size_t)(ph & 1) * G * 6 * S;
-  const int cp = b % kRelCopies;  // this CTA's copy of the release flag and the sums
-  unsigned int* rel = flags + rel_base(G);
-  const unsigned int want = (unsigned int)ph + 1u;
-  // FP32 forms: FP32 partials (their values are FP32 sums), reduced in
-  // double-float arithmetic
-  using P = T;
-  P* pbuf = reinterpret_cast<P*>(buf);
-  block_partials_qs<NQ, S, T, NT, 8, P>(acc, pbuf, b, G);
+__device__ __forceinline__ unsigned int ld_relaxed(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool grid_arrive_wait(int ph, unsigned int* flags, unsigned int* status,
+                                                 int b, int G) {
   __shared__ int go;
   __syncthreads();
-  if (threadIdx.x == 0) st_release(flags + (size_t)b * kFlagStride, want);
-  if (b == 0) {
-    // arrivals: thread t watches CTAs t, t + NT, ...
-    int ok = 1;
-    for (int c = threadIdx.x; c < G && ok; c += NT) {
-      unsigned int it = 0;
-      while (ld_acquire(flags + (size_t)c * kFlagStride) < want) {
-        if (++it > kBarIters) {
-          atomicOr(status, HEF_WAIT_TIMEOUT);
-          ok = 0;
-          break;
-        }
-        if ((it & 255u) == 0u && stopped(status)) {
-          ok = 0;
-          break;
-        }
-      }
-    }
-    if (!__syncthreads_and(ok)) return false;
-    reduce_slots_wide<NT, sizeof(T) == 4, P>(pbuf, G, N, out);
-    for (int t = threadIdx.x; t < kRelCopies * N; t += NT)
-      pub[(size_t)(t / N) * kPubStride + (size_t)(ph & 1) * 6 * S + t % N] = out[t % N];
-    __syncthreads();
-    if (threadIdx.x < kRelCopies) st_release(rel + (size_t)threadIdx.x * kRelStride, want);
-    return true;
-  }
+  const unsigned int want = (unsigned int)G * (unsigned int)(ph + 1);
+  if (threadIdx.x < kRelCopies) red_release_add(flags + (size_t)threadIdx.x * kRelStride, 1u);
   if (threadIdx.x == 0) {
+    const unsigned int* mine = flags + (size_t)(b % kRelCopies) * kRelStride;
     unsigned int it = 0;
     int ok = 1;
-    while (ld_acquire(rel + (size_t)cp * kRelStride) < want) {
+    while (ld_relaxed(mine) < want) {
       if (++it > kBarIters) {
         atomicOr(status, HEF_WAIT_TIMEOUT);
         ok = 0;
@@ -1019,13 +1050,44 @@ __device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, do
         break;
       }
     }
+    asm volatile("fence.acq_rel.gpu;" ::: "memory");
     go = ok;
   }
   __syncthreads();
-  if (!go) return false;
-  const double* res = pub + (size_t)cp * kPubStride + (size_t)(ph & 1) * 6 * S;
-  for (int t = threadIdx.x; t < N; t += NT) out[t] = __ldcg(res + t);
-  __syncthreads();
+  return go != 0;
+}
+
+// Partial-sum buffers of the persistent kernel: two buffers (barriers
+// alternate) of kPartSlots S slots by G CTAs, slot-major.  The vertex
+// barrier's buffer holds the vertex dots in slots [0, 6S) and the edge
+// pass's star-row dots in [6S, 9S): the edge barrier only synchronises, and
+// the vertex barrier reduces both (kPartSlots is defined with the
+// persistent kernel's shared-memory layout).
+template <typename T>
+__device__ __forceinline__ T* part_buffer(double* part, int ph, int G, int S) {
+  return reinterpret_cast<T*>(part + (size_t)(ph & 1) * G * kPartSlots * S);
+}
+
+// Grid barrier `ph` carrying a reduction: the CTA's partial sums of acc go to
+// slots [0, NQ S) of barrier ph's buffer, and after the barrier every CTA
+// sums slots [0, nred) of all CTAs in the same fixed order
+// (reduce_slots_wide) into `out` (shared memory): every CTA obtains the same
+// bits, and no CTA publishes results for the others (one L2 round trip fewer
+// on the critical path).  Two buffers suffice: a buffer's slots are written
+// again only for barrier ph + 2, and no CTA writes them before every CTA has
+// arrived at barrier ph + 1, that is, has finished reading barrier ph's
+// partials (the edge pass's early writes to slots [6S, 9S) of barrier ph + 2's
+// buffer do not overlap the slots [0, 2S) that the update barrier ph reads).
+template <int NQ, int S, int NT, typename T>
+__device__ __forceinline__ bool pbarrier(const T (&acc)[NQ][S], double* part, int ph, int nred,
+                                         unsigned int* flags, unsigned int* status, double* out,
+                                         int b, int G) {
+  // FP32 forms: FP32 partials (their values are FP32 sums), reduced in
+  // double-float arithmetic
+  T* pbuf = part_buffer<T>(part, ph, G, S);
+  block_partials_qs<NQ, S, T, NT, 8, T>(acc, pbuf, b, G);
+  if (!grid_arrive_wait(ph, flags, status, b, G)) return false;
+  reduce_slots_wide<NT, sizeof(T) == 4, T>(pbuf, G, nred, out);
   return true;
 }
 
@@ -1038,17 +1100,17 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int nc = (k + 1) * 2 * S;
   int* lv_ofs = reinterpret_cast<int*>(smem_raw);
-  int* lv_edge = lv_ofs + kCapItems + 1;
-  int* le_ofs = lv_edge + kCapList;
-  int* le_pin = le_ofs + kCapItems + 1;
-  double* s_inv_nu = reinterpret_cast<double*>(smem_raw + kListBytes);
-  double* s_te = s_inv_nu + nc;
-  double* s_red = s_te + 3 * S;
-  double* s_itot = s_red + 7 * S;
+  const int capi = kv.capi, capl = kv.capl;
+  int* lv_edge = lv_ofs + capi + 1;
+  int* le_ofs = lv_edge + capl;
+  int* le_pin = le_ofs + capi + 1;
+  double* s_inv_nu = reinterpret_cast<double*>(smem_raw + list_bytes(capi, capl));
+  double* s_red = s_inv_nu + nc;    // reduction results (kPartSlots S)
+  double* s_te = s_red + 6 * S;     // the star hyperedge-row dots of the step
+  double* s_itot = s_red + (kPartSlots + 1) * S;
   T* s_cfT = reinterpret_cast<T*>(s_itot + 4);
   T* s_nuT = s_cfT + (size_t)nc * 4;
   __shared__ int rng[4];
-  double* pub = part + (size_t)2 * G * 6 * S;
 
   if (stopped(status)) return;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -1070,8 +1132,8 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
   __syncthreads();
   const int v0 = rng[0], v1 = rng[1], e0 = rng[2], e1 = rng[3];
   const int i0 = g.vptr[v0], p0 = g.ceptr[e0];
-  const int nv = min(v1 - v0, kCapItems), ne = min(e1 - e0, kCapItems);
-  const int ni = min(g.vptr[v1] - i0, kCapList), np = min(g.ceptr[e1] - p0, kCapList);
+  const int nv = min(v1 - v0, capi), ne = min(e1 - e0, capi);
+  const int ni = min(g.vptr[v1] - i0, capl), np = min(g.ceptr[e1] - p0, capl);
   for (int i = tid; i <= nv; i += NT) lv_ofs[i] = __ldg(g.vptr + v0 + i);
   for (int i = tid; i < ni; i += NT) lv_edge[i] = __ldg(g.vedge + i0 + i);
   for (int i = tid; i <= ne; i += NT) le_ofs[i] = __ldg(g.ceptr + e0 + i);
@@ -1084,16 +1146,16 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
 
   int ph = 0;
   for (int j = 1; j <= k; ++j) {
-    {  // edge phase
+    {  // edge phase; its star-row dots are reduced at the vertex barrier
       T acc[3][S];
       zero_acc(acc);
       for (int base = e0 + wid * 32; base < e1; base += NT) {
         const int e = base + lane;
         edge_item<T, S, true>(g, sv, kv, s_nuT, j, e < e1 ? e : g.m, acc, eofs, epin);
       }
-      if (!pbarrier<3, S, NT>(acc, part, pub, ph++, cnt, status, s_red, b, G)) return;
-      for (int t = tid; t < 3 * S; t += NT) s_te[t] = s_red[t];
-      __syncthreads();
+      block_partials_qs<3, S, T, NT, 8, T>(acc, part_buffer<T>(part, ph + 1, G, S) + (size_t)6 * S * G,
+                                           b, G);
+      if (!grid_arrive_wait(ph++, cnt, status, b, G)) return;
     }
     {  // vertex phase; then the Lanczos coefficients of step j
       T acc[6][S];
@@ -1102,7 +1164,7 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
         const int v = base + lane;
         node_item<T, S, true, TV>(g, sv, kv, s_nuT, j, v < v1 ? v : g.n, acc, V, ldv, vofs, vedg);
       }
-      if (!pbarrier<6, S, NT>(acc, part, pub, ph++, cnt, status, s_red, b, G)) return;
+      if (!pbarrier<6, S, NT>(acc, part, ph++, kPartSlots * S, cnt, status, s_red, b, G)) return;
       for (int c = tid; c < 2 * S; c += NT) {
         const int op = c / S, q = c % S;
         double cf[4];
@@ -1137,7 +1199,7 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
       zero_acc(acc);
       for (int v = v0 + tid; v < v1; v += NT) update_vertex<T, S, true>(g, sv, kv, j, v, cf, acc);
       for (int e = e0 + tid; e < e1; e += NT) update_edge<T, S, true>(g, sv, kv, j, e, cf, acc);
-      if (!pbarrier<2, S, NT>(acc, part, pub, ph++, cnt, status, s_red, b, G)) return;
+      if (!pbarrier<2, S, NT>(acc, part, ph++, 2 * S, cnt, status, s_red, b, G)) return;
       for (int c = tid; c < 2 * S; c += NT) {
         const double nu2 = s_red[c];
         const bool alive = s_inv_nu[(size_t)(j - 1) * 2 * S + c] > 0.0 && nu2 > kv.tol * kv.tol;
@@ -1215,8 +1277,10 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->red.gpart = c.take<double>((size_t)red_groups((int)maxblk) * 6 * S);
   kv->red.gcnt = c.take<unsigned int>(red_groups((int)maxblk) + 1);
   kv->red.tcnt = c.take<unsigned int>(1);
-  kv->ppart = c.take<double>((size_t)2 * num_sms() * 2 * 6 * S + (size_t)kRelCopies * kPubStride);
+  kv->ppart = c.take<double>((size_t)2 * num_sms() * 2 * kPartSlots * S);
   kv->pcount = c.take<unsigned int>(flag_words(2 * num_sms()));
+  kv->capi = kCapItems;
+  kv->capl = kCapList;
   return c.bytes();
 }
 
@@ -1261,8 +1325,13 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
   // (small hypergraphs: the per-step launches are as fast as the barriers)
   if (persistent && (n + m >= kPersistentMinRows || t_force_oversized)) {
     constexpr int NT = pers_threads<T, S>();
-    const size_t smem = pers_smem<T>(k, S);
     constexpr size_t kSmemLimit = 227 * 1024;  // per-CTA opt-in limit of the sm_100 family
+    // list capacities: 1.25 times the average range (the balanced ranges
+    // stay within a few per cent of it), at most kCapItems / kCapList
+    const double G = (double)num_sms();
+    kv.capi = (int)std::min<double>(kCapItems, 1.25 * (double)std::max(n, m) / G + 64.0);
+    kv.capl = (int)std::min<double>(kCapList, 1.25 * (double)inc->P / G + 256.0);
+    const size_t smem = pers_smem<T>(k, S, kv.capi, kv.capl);
     if (smem <= kSmemLimit) HEF_ENSURE_SMEM((k_krylov_steps<T, S, TV>), smem);
     int occ = 0;
     if (smem <= kSmemLimit &&
@@ -1419,7 +1488,7 @@ void cta_shares(const double* cost, int n, int total, int* share) {
 template <typename T, int S, typename TV>
 hef_status batch_steps_s(const KrylovBatchArg* items, int G, int k, cudaStream_t st) {
   constexpr int NT = pers_threads<T, S>();
-  const size_t smem = pers_smem<T>(k, S);
+  const size_t smem = pers_smem<T>(k, S, kCapItems, kCapList);
   constexpr size_t kSmemLimit = 227 * 1024;
   if (smem > kSmemLimit) return set_error(HEF_ERR_UNSUPPORTED, "batched Krylov: k too large");
   HEF_ENSURE_SMEM((k_krylov_batched<T, S, TV>), smem);

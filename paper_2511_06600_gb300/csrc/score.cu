@@ -16,6 +16,7 @@
 #include <cudaTypedefs.h>
 
 #include <cfloat>
+#include <climits>
 #include <cstring>
 #include <mutex>
 #include <type_traits>
@@ -797,6 +798,106 @@ __global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restr
   }
 }
 
+// Pass 2 from the stored spreads for the max reduction (Eq. R), eight lanes
+// per hyperedge: lane l of a group reads 16-byte chunks l, l + 8, ... of the
+// row, so each load instruction of a warp covers four rows in full 128-byte
+// lines instead of 32 rows in 16-byte pieces.  Each lane keeps the largest
+// ratio of its columns (lowest column on ties, scanning upwards) and the
+// group combines by value, then column, which selects the same column as a
+// scan of the whole row.  The routing pins: the lanes split the hyperedge's
+// pins the same way and combine the extrema of the arg-max column by value,
+// then position.  R_e, the arg-max column and the routing pins are therefore
+// bit-identical to k_score_ratio's.
+constexpr int kRatioLanes = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_score_ratio8(IncView g, const T* __restrict__ Q, long long ldq,
+                                                      int K, const double* __restrict__ QH,
+                                                      const double* __restrict__ invQH,
+                                                      const T* __restrict__ spread, int ldsp,
+                                                      double* R_out, int32_t* argvec, int32_t* pmax,
+                                                      int32_t* pmin) {
+  if (g.status[0]) return;
+  constexpr int V = 16 / sizeof(T);  // elements per 16-byte chunk
+  constexpr int U = 4;               // chunks of a lane in flight
+  extern __shared__ unsigned char iq_raw[];
+  T* iq = reinterpret_cast<T*>(iq_raw);  // K: 1 / Q_H in the working type, 0 when unused
+  for (int i = threadIdx.x; i < K; i += blockDim.x) iq[i] = QH[i] > kQhTiny ? (T)invQH[i] : (T)0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, sub = lane & (kRatioLanes - 1);
+  const int nchunk = (K + V - 1) / V;
+  const long long groups_per_warp = 32 / kRatioLanes;
+  const long long wglob = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long wstride = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long eb = wglob * groups_per_warp; eb < g.m; eb += wstride * groups_per_warp) {
+    const long long e = eb + (lane >> 3);
+    const bool valid = e < g.m;
+    int a = 0, b = 0;
+    if (valid) a = g.ceptr[e], b = g.ceptr[e + 1];
+    const bool scored = valid && b - a >= 2;
+    T best = (T)-1, spb = 0;
+    int bcol = -1;
+    if (scored) {
+      const uint4* row = reinterpret_cast<const uint4*>(spread + e * ldsp);
+      for (int c0 = sub; c0 < nchunk; c0 += U * kRatioLanes) {
+        T sp[U][V];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          uint4 v = make_uint4(0u, 0u, 0u, 0u);
+          if (c0 + u * kRatioLanes < nchunk) v = __ldg(row + c0 + u * kRatioLanes);
+          memcpy(&sp[u][0], &v, 16);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+#pragma unroll
+          for (int q = 0; q < V; ++q) {
+            const int i = (c0 + u * kRatioLanes) * V + q;
+            if (i >= K || iq[i] == (T)0) continue;
+            const T r = sp[u][q] * sp[u][q] * iq[i];
+            if (r > best) best = r, bcol = i, spb = sp[u][q];
+          }
+      }
+    }
+    // combine the group's candidates: larger ratio, then lower column
+#pragma unroll
+    for (int o = kRatioLanes / 2; o > 0; o >>= 1) {
+      const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const T os = __shfl_xor_sync(0xffffffffu, spb, o);
+      const int oc = __shfl_xor_sync(0xffffffffu, bcol, o);
+      if (oc >= 0 && (bcol < 0 || ob > best || (ob == best && oc < bcol))) best = ob, bcol = oc, spb = os;
+    }
+    const bool any = scored && bcol >= 0;
+    T vmax = lowest<T>(), vmin = -lowest<T>();
+    int tmax = INT_MAX, tmin = INT_MAX;
+    if (any && (pmax || pmin)) {
+      for (int t = a + sub; t < b; t += kRatioLanes) {
+        const T v = qw<T>(Q[(long long)g.cpins[t] * ldq + bcol]);
+        if (tmax == INT_MAX || v > vmax) vmax = v, tmax = t;
+        if (tmin == INT_MAX || v < vmin) vmin = v, tmin = t;
+      }
+    }
+#pragma unroll
+    for (int o = kRatioLanes / 2; o > 0; o >>= 1) {
+      const T ovx = __shfl_xor_sync(0xffffffffu, vmax, o), ovn = __shfl_xor_sync(0xffffffffu, vmin, o);
+      const int otx = __shfl_xor_sync(0xffffffffu, tmax, o), otn = __shfl_xor_sync(0xffffffffu, tmin, o);
+      if (otx != INT_MAX && (tmax == INT_MAX || ovx > vmax || (ovx == vmax && otx < tmax))) vmax = ovx, tmax = otx;
+      if (otn != INT_MAX && (tmin == INT_MAX || ovn < vmin || (ovn == vmin && otn < tmin))) vmin = ovn, tmin = otn;
+    }
+    if (valid && sub == 0) {
+      const int oe = g.perm[e];
+      double Re = 0.0;
+      if (any) {  // times the FP64 1/Q_H, as k_score_ratio
+        const double spw = (double)spb;
+        Re = spw * spw * invQH[bcol];
+      }
+      R_out[oe] = Re;
+      if (argvec) argvec[oe] = any ? bcol : -1;
+      if (pmax) pmax[oe] = any ? g.cpins[tmax] : -1;
+      if (pmin) pmin[oe] = any ? g.cpins[tmin] : -1;
+    }
+  }
+}
+
 struct ScoreWs {
   double* part;
   double* QH;
@@ -1013,7 +1114,15 @@ hef_status launch_score(const hef_incidence* inc, const T* Q, long long ldq, int
     HEF_CHECK_LAUNCH();
     return HEF_OK;
   }
-  if (spread) {
+  if (spread && reduce == HEF_REDUCE_MAX) {
+    const int g3 = stride_grid((long long)(inc->m > 0 ? inc->m : 1) * kRatioLanes, 8);
+    HEF_LAUNCH("k_score_ratio", st, k_score_ratio8<T><<<g3, kThreads, K * sizeof(T), st>>>(
+                                        g, Q, ldq, K, w.QH, w.invQH, spread, ldsp, R_out, argvec,
+                                        pmax, pmin));
+    HEF_CHECK_LAUNCH();
+    return HEF_OK;
+  }
+  if (spread) {  // the sum reduction adds a row's terms in column order
     const int g3 = stride_grid(inc->m > 0 ? inc->m : 1, 8);
     HEF_LAUNCH("k_score_ratio", st, k_score_ratio<T><<<g3, kThreads, K * sizeof(T), st>>>(
                                         g, Q, ldq, K, reduce, w.QH, w.invQH, spread, ldsp, R_out,
