@@ -90,6 +90,8 @@ struct KView {
   int capi, capl;  // persistent launch: vertices / hyperedges (capi) and incidences /
                    // pins (capl) whose offsets and index lists a CTA keeps in shared
                    // memory
+  int capv;        // persistent launch: own vertices whose chain records (two steps)
+                   // and Y rows a CTA keeps in shared memory (0: none)
 };
 
 // ---------------------------------------------------------------- row I/O
@@ -408,6 +410,52 @@ __device__ __forceinline__ void seg_gather(bool valid, int a, int b, Idx idx, Ro
   }
 }
 
+// Records of the persistent kernel's own vertices in shared memory: the
+// chain records u_{j-1}, u_{j-2} (x[0], x[1], alternating like Bv) and the Y
+// rows of vertices [0, cap) of a CTA's range, so that the vertex and update
+// passes read and write them without going through L2 (only u_j still goes
+// to Bv, for the gathers).  Each record of N values is stored as 16-byte
+// planes (plane p of record i at p * cap + i), so a warp's access to 32
+// consecutive records of one plane reads 512 contiguous bytes.
+template <typename T, int N>
+struct OwnRows {
+  T* x[2];
+  T* y;
+  int cap;
+  static constexpr int kPlaneBytes = (N * sizeof(T)) % 16 == 0 ? 16 : (int)(N * sizeof(T));
+  static constexpr int E = kPlaneBytes / (int)sizeof(T);  // values per plane
+  __device__ __forceinline__ void ld(const T* base, int i, T (&v)[N]) const {
+#pragma unroll
+    for (int p = 0; p < N / E; ++p) {
+      const T* q = base + ((size_t)p * cap + i) * E;
+      if constexpr (kPlaneBytes == 16 && sizeof(T) == 4) {
+        const float4 f = *reinterpret_cast<const float4*>(q);
+        v[E * p] = f.x, v[E * p + 1] = f.y, v[E * p + 2] = f.z, v[E * p + 3] = f.w;
+      } else if constexpr (kPlaneBytes == 16) {
+        const double2 f = *reinterpret_cast<const double2*>(q);
+        v[E * p] = f.x, v[E * p + 1] = f.y;
+      } else {
+#pragma unroll
+        for (int t = 0; t < E; ++t) v[E * p + t] = q[t];
+      }
+    }
+  }
+  __device__ __forceinline__ void st(T* base, int i, const T (&v)[N]) const {
+#pragma unroll
+    for (int p = 0; p < N / E; ++p) {
+      T* q = base + ((size_t)p * cap + i) * E;
+      if constexpr (kPlaneBytes == 16 && sizeof(T) == 4) {
+        *reinterpret_cast<float4*>(q) = make_float4(v[E * p], v[E * p + 1], v[E * p + 2], v[E * p + 3]);
+      } else if constexpr (kPlaneBytes == 16) {
+        *reinterpret_cast<double2*>(q) = make_double2(v[E * p], v[E * p + 1]);
+      } else {
+#pragma unroll
+        for (int t = 0; t < E; ++t) q[t] = v[E * p + t];
+      }
+    }
+  }
+};
+
 // ---------------------------------------------------------------- start vectors
 
 // D-weighted dots of the raw starts with the trivial vectors -> coef[0]; the
@@ -597,7 +645,8 @@ template <typename T, int S, bool CG, typename TV, typename Ofs, typename Edge>
 __device__ __forceinline__ void node_item(const IncView& g, const ScalView<T>& sv,
                                           const KView<T>& kv, const T* nuT, int j, int v,
                                           T (&acc)[6][S], TV* __restrict__ V, long long ldv,
-                                          Ofs ofs, Edge edge) {
+                                          Ofs ofs, Edge edge,
+                                          OwnRows<T, 2 * S> own = {}, int si = -1) {
   const T* __restrict__ curv = pick2(kv.Bv, (j - 1) & 1);
   const T* __restrict__ prvv = j >= 3 ? pick2(kv.Bv, j & 1) : nullptr;
   const bool valid = v < g.n;
@@ -608,8 +657,13 @@ __device__ __forceinline__ void node_item(const IncView& g, const ScalView<T>& s
   T xr[2 * S], pr[2 * S];
   T wsum = 0, idc = 0, idb = 0, dcv = 0, dbv = 0;
   if (valid) {
-    ldrow<T, 2 * S, CG>(curv + (long long)v * 2 * S, xr);
-    if (prvv) ldrow<T, 2 * S, CG>(prvv + (long long)v * 2 * S, pr);
+    if (si >= 0) {
+      own.ld(pick2(own.x, (j - 1) & 1), si, xr);
+      if (prvv) own.ld(pick2(own.x, j & 1), si, pr);
+    } else {
+      ldrow<T, 2 * S, CG>(curv + (long long)v * 2 * S, xr);
+      if (prvv) ldrow<T, 2 * S, CG>(prvv + (long long)v * 2 * S, pr);
+    }
     wsum = sv.wsc[v], idc = sv.inv_dc[v], idb = sv.inv_db[v], dcv = sv.dc[v], dbv = sv.db[v];
   }
   T sum[2 * S];
@@ -637,7 +691,8 @@ __device__ __forceinline__ void node_item(const IncView& g, const ScalView<T>& s
       y[s] = yc, y[S + s] = yb;
       xo[s] = xv, xo[S + s] = xb;
     }
-    strow<T, 2 * S>(kv.Yv + (long long)v * 2 * S, y);
+    if (si >= 0) own.st(own.y, si, y);
+    else strow<T, 2 * S>(kv.Yv + (long long)v * 2 * S, y);
     if (j >= 2)  // x_{j-1} is basis vector j-1 -> column block j-2
       store_basis<T, 2 * S, TV>(V + (long long)v * ldv + (long long)(j - 2) * 2 * S, xo);
   }
@@ -679,15 +734,22 @@ __device__ __forceinline__ void node_final(const IncView& g, const KView<T>& kv,
 template <typename T, int S, bool CG, typename CF>
 __device__ __forceinline__ void update_vertex(const IncView& g, const ScalView<T>& sv,
                                               const KView<T>& kv, int j, long long r,
-                                              const CF& cf, T (&acc)[2][S]) {
+                                              const CF& cf, T (&acc)[2][S],
+                                              OwnRows<T, 2 * S> own = {}, int si = -1) {
   const bool has_prv = j >= 3;
   const T* cur = pick2(kv.Bv, (j - 1) & 1) + r * 2 * S;
   T* nw = pick2(kv.Bv, j & 1) + r * 2 * S;
   const T dc = sv.dc[r], db = sv.db[r];
   T y[2 * S], xc[2 * S], xp[2 * S], u[2 * S];
-  ldrow<T, 2 * S, CG>(kv.Yv + r * 2 * S, y);
-  ldrow<T, 2 * S, CG>(cur, xc);
-  if (has_prv) ldrow<T, 2 * S, CG>(nw, xp);
+  if (si >= 0) {
+    own.ld(own.y, si, y);
+    own.ld(pick2(own.x, (j - 1) & 1), si, xc);
+    if (has_prv) own.ld(pick2(own.x, j & 1), si, xp);
+  } else {
+    ldrow<T, 2 * S, CG>(kv.Yv + r * 2 * S, y);
+    ldrow<T, 2 * S, CG>(cur, xc);
+    if (has_prv) ldrow<T, 2 * S, CG>(nw, xp);
+  }
 #pragma unroll
   for (int s = 0; s < S; ++s) {
     const T tc = dc > 0 ? cf[0][s][0] : (T)0;
@@ -699,6 +761,7 @@ __device__ __forceinline__ void update_vertex(const IncView& g, const ScalView<T
     acc[1][s] += db * u[S + s] * u[S + s];
   }
   strow<T, 2 * S>(nw, u);
+  if (si >= 0) own.st(pick2(own.x, j & 1), si, u);
   if (kv.tape_c) {
     T uc[S], ub[S];
     split2<T, S>(u, uc, ub);
@@ -1138,6 +1201,19 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
   for (int i = tid; i < ni; i += NT) lv_edge[i] = __ldg(g.vedge + i0 + i);
   for (int i = tid; i <= ne; i += NT) le_ofs[i] = __ldg(g.ceptr + e0 + i);
   for (int i = tid; i < np; i += NT) le_pin[i] = __ldg(g.cpins + p0 + i);
+  // own vertices [v0, v0 + nown): chain records and Y rows in shared memory,
+  // starting from x_0 (written by the start kernels)
+  OwnRows<T, 2 * S> own;
+  own.cap = kv.capv;
+  own.x[0] = reinterpret_cast<T*>(smem_raw + pers_smem<T>(k, S, capi, capl));
+  own.x[1] = own.x[0] + (size_t)own.cap * 2 * S;
+  own.y = own.x[1] + (size_t)own.cap * 2 * S;
+  const int nown = min(v1 - v0, own.cap);
+  for (int i = tid; i < nown; i += NT) {
+    T r[2 * S];
+    ldrow<T, 2 * S, true>(kv.Bv[0] + (long long)(v0 + i) * 2 * S, r);
+    own.st(own.x[0], i, r);
+  }
   __syncthreads();
   auto vofs = [&](int v) { const int i = v - v0; return i <= nv ? lv_ofs[i] : __ldg(g.vptr + v); };
   auto vedg = [&](int t) { const int i = t - i0; return i < ni ? lv_edge[i] : __ldg(g.vedge + t); };
@@ -1162,7 +1238,8 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
       zero_acc(acc);
       for (int base = v0 + wid * 32; base < v1; base += NT) {
         const int v = base + lane;
-        node_item<T, S, true, TV>(g, sv, kv, s_nuT, j, v < v1 ? v : g.n, acc, V, ldv, vofs, vedg);
+        node_item<T, S, true, TV>(g, sv, kv, s_nuT, j, v < v1 ? v : g.n, acc, V, ldv, vofs, vedg,
+                                  own, v < v1 && v - v0 < nown ? v - v0 : -1);
       }
       if (!pbarrier<6, S, NT>(acc, part, ph++, kPartSlots * S, cnt, status, s_red, b, G)) return;
       for (int c = tid; c < 2 * S; c += NT) {
@@ -1197,7 +1274,8 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
       const CoefView<T, S> cf{s_cfT + (size_t)j * 2 * S * 4};
       T acc[2][S];
       zero_acc(acc);
-      for (int v = v0 + tid; v < v1; v += NT) update_vertex<T, S, true>(g, sv, kv, j, v, cf, acc);
+      for (int v = v0 + tid; v < v1; v += NT)
+        update_vertex<T, S, true>(g, sv, kv, j, v, cf, acc, own, v - v0 < nown ? v - v0 : -1);
       for (int e = e0 + tid; e < e1; e += NT) update_edge<T, S, true>(g, sv, kv, j, e, cf, acc);
       if (!pbarrier<2, S, NT>(acc, part, ph++, 2 * S, cnt, status, s_red, b, G)) return;
       for (int c = tid; c < 2 * S; c += NT) {
@@ -1281,6 +1359,7 @@ size_t carve_krylov(void* base, long long n, long long m, int k, int S, KView<T>
   kv->pcount = c.take<unsigned int>(flag_words(2 * num_sms()));
   kv->capi = kCapItems;
   kv->capl = kCapList;
+  kv->capv = 0;
   return c.bytes();
 }
 
@@ -1331,8 +1410,24 @@ hef_status run_krylov_s(const hef_incidence* inc, int k, const double* x0c, cons
     const double G = (double)num_sms();
     kv.capi = (int)std::min<double>(kCapItems, 1.25 * (double)std::max(n, m) / G + 64.0);
     kv.capl = (int)std::min<double>(kCapList, 1.25 * (double)inc->P / G + 256.0);
-    const size_t smem = pers_smem<T>(k, S, kv.capi, kv.capl);
-    if (smem <= kSmemLimit) HEF_ENSURE_SMEM((k_krylov_steps<T, S, TV>), smem);
+    size_t smem = pers_smem<T>(k, S, kv.capi, kv.capl);
+    kv.capv = 0;
+    if (smem <= kSmemLimit) {
+      // own vertices' chain records (two steps) and Y rows in shared memory:
+      // room for 1.1 times the average vertex range, within the limit
+      static thread_local int stat = -1;  // static shared bytes of this instantiation
+      if (stat < 0) {
+        cudaFuncAttributes fa;
+        HEF_CHECK_CUDA(cudaFuncGetAttributes(&fa, k_krylov_steps<T, S, TV>));
+        stat = (int)fa.sharedSizeBytes;
+      }
+      const size_t used = smem + (size_t)stat + 1024;
+      const size_t per_v = (size_t)3 * 2 * S * sizeof(T);
+      const size_t fit = used < kSmemLimit ? (kSmemLimit - used) / per_v : 0;
+      kv.capv = (int)std::min<double>((double)fit, 1.1 * (double)n / G + 64.0) & ~1;
+      smem += (size_t)kv.capv * per_v;
+      HEF_ENSURE_SMEM((k_krylov_steps<T, S, TV>), smem);
+    }
     int occ = 0;
     if (smem <= kSmemLimit &&
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_krylov_steps<T, S, TV>, NT, smem) ==
