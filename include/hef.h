@@ -57,6 +57,8 @@ typedef int32_t hef_status;
 #define HEF_ERR_TIMEOUT (-5)       /* a bounded device wait expired */
 #define HEF_ERR_UNSUPPORTED (-6)   /* valid request outside supported sizes */
 #define HEF_ERR_INVALID_INPUT (-7) /* device-side check of the hypergraph failed */
+#define HEF_ERR_BOUNDS (-8)        /* HEF_DEBUG build: an index read from the
+                                      incidence lay outside its array */
 
 #define HEF_F64 0
 #define HEF_F32 1
@@ -88,8 +90,14 @@ typedef int32_t hef_status;
 #define HEF_WAIT_TIMEOUT 16u /* a bounded grid-wide wait of the one-launch
                                 Krylov form expired (hef_incidence_check then
                                 returns HEF_ERR_TIMEOUT) */
+#define HEF_BOUNDS 32u       /* HEF_DEBUG build: a kernel read a vertex or
+                                hyperedge index outside [0, n) or [0, m) from
+                                the incidence; the access was redirected to
+                                index 0 and hef_incidence_check returns
+                                HEF_ERR_BOUNDS */
 
 const char* hef_last_error(void);
+
 const char* hef_status_string(hef_status s);
 int32_t hef_abi_version(void);
 
@@ -142,9 +150,33 @@ hef_status hef_build_incidence(int64_t n, int64_t m, int64_t P,
  * bits in *detail, the first offending hyperedge in *where; either may be
  * NULL) if the device-side validation failed, HEF_ERR_TIMEOUT if a bounded
  * device wait of a later call on this incidence expired (HEF_WAIT_TIMEOUT),
- * else HEF_OK. */
+ * HEF_ERR_BOUNDS if a kernel of the bounds-checked build met an index
+ * outside its array (HEF_BOUNDS), else HEF_OK. */
 hef_status hef_incidence_check(const hef_incidence* inc, void* stream,
                                uint32_t* detail, int64_t* where);
+
+/* ------------------------------------------------------------------------
+ * Bounds-checked build (no counterpart in the paper; a debugging aid).
+ *
+ * The library built with -DHEF_DEBUG=1 (libhef_debug.so: `python -m
+ * paper_2511_06600_gb300.build --debug`) checks every vertex or hyperedge
+ * index that a gather of the Krylov, scoring and backward kernels reads from
+ * the incidence (pins, incidence lists) against its array before using it.
+ * An index outside the array sets HEF_BOUNDS in the incidence's status word
+ * and the access goes to index 0 instead, so the kernel never reads outside
+ * its buffers; hef_incidence_check then returns HEF_ERR_BOUNDS.  The regular
+ * build has no checks (the incidence build validates every pin).
+ *
+ * hef_debug_checks: 1 for the bounds-checked build, 0 otherwise.
+ * hef_debug_set_pin: bounds-checked build only: overwrites pin slot `slot`
+ *   (internal CSC order, 0 <= slot < P) of a built incidence with `value`
+ *   (a copy on `stream`, which it synchronises), so that a test can plant an
+ *   index that the checks must catch.  The regular build returns HEF_ERR_UNSUPPORTED and
+ *   touches nothing; bad arguments give HEF_ERR_INVALID_ARG.
+ * ---------------------------------------------------------------------- */
+int32_t hef_debug_checks(void);
+hef_status hef_debug_set_pin(const hef_incidence* inc, int64_t slot, int32_t value,
+                             void* stream);
 
 hef_status hef_incidence_sizes(const hef_incidence* inc, int64_t* n,
                                int64_t* m, int64_t* P);

@@ -14,7 +14,9 @@ import os
 import torch
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libhef.so")
+# HEF_LIBRARY selects another build of the same ABI (the bounds-checked
+# libhef_debug.so, see build.py --debug); the default is libhef.so.
+LIB_PATH = os.environ.get("HEF_LIBRARY") or os.path.join(HERE, "libhef.so")
 
 HEF_F64, HEF_F32, HEF_BF16 = 0, 1, 2
 HEF_REDUCE_MAX, HEF_REDUCE_SUM, HEF_REDUCE_EMBED = 0, 1, 2
@@ -32,6 +34,8 @@ _SIGS = {
     "hef_last_error": (ctypes.c_char_p, []),
     "hef_status_string": (ctypes.c_char_p, [c_i32]),
     "hef_abi_version": (c_i32, []),
+    "hef_debug_checks": (c_i32, []),
+    "hef_debug_set_pin": (c_i32, [c_p, c_i64, c_i32, c_p]),
     "hef_launch_count": (ctypes.c_uint64, []),
     "hef_trace_kernels": (c_i32, [ctypes.c_char_p]),
     "hef_trace_read": (c_i32, [c_i32, ctypes.c_char_p, ctypes.POINTER(c_i64),
@@ -203,6 +207,12 @@ class Incidence:
             err.detail = detail.value
             err.where = where.value
             raise err
+
+    def debug_set_pin(self, slot, value, stream=None):
+        """Bounds-checked build only: overwrite pin slot `slot` (internal CSC
+        order) with `value`, to plant an index that the checks must catch."""
+        _check("hef_debug_set_pin",
+               lib().hef_debug_set_pin(self.handle, int(slot), int(value), _stream(stream)))
 
     def export(self, stream=None):
         dev = self.device

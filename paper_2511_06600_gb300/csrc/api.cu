@@ -155,8 +155,11 @@ extern "C" const char* hef_status_string(hef_status s) {
     case HEF_ERR_TIMEOUT: return "HEF_ERR_TIMEOUT";
     case HEF_ERR_UNSUPPORTED: return "HEF_ERR_UNSUPPORTED";
     case HEF_ERR_INVALID_INPUT: return "HEF_ERR_INVALID_INPUT";
+    case HEF_ERR_BOUNDS: return "HEF_ERR_BOUNDS";
     default: return "HEF_ERR_UNKNOWN";
   }
 }
 
 extern "C" int32_t hef_abi_version(void) { return 1; }
+
+extern "C" int32_t hef_debug_checks(void) { return HEF_DEBUG ? 1 : 0; }

@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(256) k_bwd_scores(IncView g, const T* __restri
 #pragma unroll
     for (int c = 0; c < NC; ++c) mx[c] = lowest_v<T>(), mn[c] = -lowest_v<T>(), imx[c] = a, imn[c] = a;
     for (int t = a; t < b; ++t) {
-      const T* row = Q + (long long)g.cpins[t] * ldq;
+      const T* row = Q + (long long)dbg_index(g.cpins[t], g.n, g.status) * ldq;
 #pragma unroll
       for (int c = 0; c < NC; ++c) {
         const int col = lane + 32 * c;
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256) k_bwd_qbar(IncView g, int K, const double
       const int col = c0 + lane;
       double acc = 0.0;
       for (int t = t0; t < t1; ++t) {
-        const int e = g.vedge[t];
+        const int e = dbg_index(g.vedge[t], g.m, g.status);
         const int a = g.ceptr[e];
         if (g.ceptr[e + 1] - a < 2 || col >= K) continue;
         const int pos = g.vslot[t] - a;
@@ -373,7 +373,7 @@ __global__ void k_bwd_edge1(IncView g, ChainBwd<T> c) {
     const T nu = (T)c.inv_nu[(size_t)(j - 1) * 2 * S + s];
     T sx = 0, sz = 0, szb = 0;
     for (int t = a; t < b; ++t) {
-      const long long p = g.cpins[t];
+      const long long p = dbg_index(g.cpins[t], g.n, g.status);
       sx += uc[p * S + s];
       sz += c.zc[p * S + s];
       szb += c.zb[p * S + s];
@@ -403,7 +403,7 @@ __global__ void k_bwd_node(IncView g, ChainBwd<T> c) {
     const T zv = c.zc[idx];
     T fc = 0, fb = 0, tc = 0, tb = 0;
     for (int t = g.vptr[v]; t < g.vptr[v + 1]; ++t) {
-      const int e = g.vedge[t];
+      const int e = dbg_index(g.vedge[t], g.m, g.status);
       const T wh = c.sv.ewh[e], z = c.sv.ez[e];
       fc += wh * c.sc[(long long)e * S + s];
       fb += z * ub[(long long)(c.n + e) * S + s];
@@ -443,7 +443,7 @@ __global__ void k_bwd_edge2(IncView g, ChainBwd<T> c) {
       const T xe = ub[(c.n + e) * S + s] * nb;
       T t1 = 0, t2 = 0, t3 = 0, t4 = 0;
       for (int t = a; t < b; ++t) {
-        const long long p = g.cpins[t];
+        const long long p = dbg_index(g.cpins[t], g.n, g.status);
         const T zc = c.zc[p * S + s];
         const T zb = c.zb[p * S + s];
         t1 += zc * (se - uc[p * S + s] * nc);
@@ -561,7 +561,7 @@ __global__ void k_bwd_defl_w(IncView g, const double* __restrict__ dbar, double*
     const double be = g.ewh[e] / g.ew[e] * (double)(k - 1);
     double sc = 0.0, sb = 0.0;
     for (int t = a; t < b; ++t) {
-      const int p = g.cpins[t];
+      const int p = dbg_index(g.cpins[t], g.n, g.status);
       sc += dbar[p];
       sb += dbar[(long long)g.n + p];
     }

@@ -64,6 +64,26 @@ struct NvtxRange {
 };
 #define HEF_NVTX(name) ::hef::NvtxRange hef_nvtx_(name)
 
+// Bounds checks of the debugging build (-DHEF_DEBUG=1): dbg_index(i, lim,
+// status) returns i when 0 <= i < lim; otherwise it sets HEF_BOUNDS in the
+// incidence's status word and returns 0, so the access stays inside its
+// array.  In the regular build it returns i unchecked.
+#ifndef HEF_DEBUG
+#define HEF_DEBUG 0
+#endif
+__device__ __forceinline__ int dbg_index(int i, int lim, const unsigned int* status) {
+#if HEF_DEBUG
+  if ((unsigned int)i >= (unsigned int)lim) {
+    atomicOr(const_cast<unsigned int*>(status), HEF_BOUNDS);
+    return 0;
+  }
+#else
+  (void)lim;
+  (void)status;
+#endif
+  return i;
+}
+
 constexpr int kThreads = 256;
 
 // Programmatic dependent launch (sm_90 and later).  A kernel launched by

@@ -847,10 +847,28 @@ extern "C" hef_status hef_incidence_check(const hef_incidence* inc, void* stream
   if (where) *where = st_host[0] ? (int64_t)st_host[1] : -1;
   if (st_host[0] & HEF_WAIT_TIMEOUT)
     return set_error(HEF_ERR_TIMEOUT, "a bounded grid-wide wait of the Krylov launch expired");
+  if (st_host[0] & HEF_BOUNDS)
+    return set_error(HEF_ERR_BOUNDS, "a kernel read an incidence index outside its array (bits 0x%x)",
+                     st_host[0]);
   if (st_host[0])
     return set_error(HEF_ERR_INVALID_INPUT,
                      "hypergraph rejected by device validation (bits 0x%x, hyperedge %u)",
                      st_host[0], st_host[1]);
+  return HEF_OK;
+}
+
+extern "C" hef_status hef_debug_set_pin(const hef_incidence* inc, int64_t slot, int32_t value,
+                                        void* stream) {
+  if (!HEF_DEBUG)
+    return set_error(HEF_ERR_UNSUPPORTED, "hef_debug_set_pin: only in the bounds-checked build");
+  if (!inc || slot < 0 || slot >= inc->P)
+    return set_error(HEF_ERR_INVALID_ARG, "hef_debug_set_pin: NULL handle or slot outside [0, P)");
+  // a pinned staging word per call would outlive the asynchronous copy only
+  // with a synchronisation; the copy is small, so it is made synchronous
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  HEF_CHECK_CUDA(cudaMemcpyAsync(const_cast<int32_t*>(inc->cpins) + slot, &value, sizeof(int32_t),
+                                 cudaMemcpyHostToDevice, st));
+  HEF_CHECK_CUDA(cudaStreamSynchronize(st));
   return HEF_OK;
 }
 

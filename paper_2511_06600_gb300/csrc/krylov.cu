@@ -350,9 +350,11 @@ __device__ __forceinline__ void block_partials_qs(const A (&v)[NQ][S], PT* part,
 // in flight (entries past the end repeat the last one and are not added).
 // Each thread adds in entry order, so the sum does not depend on scheduling.
 // Result in acc (the owner thread).
+// idx values lie in [0, lim) (checked in the bounds-checked build, which
+// reports a violation in `status`).
 template <typename T, int N, bool CG, typename Idx, typename Row>
 __device__ __forceinline__ void seg_gather(bool valid, int a, int b, Idx idx, Row row,
-                                           T (&acc)[N]) {
+                                           T (&acc)[N], int lim, const unsigned int* status) {
   const int lane = threadIdx.x & 31;
   constexpr int kSeg = gather_round<T, N>();
 #pragma unroll
@@ -362,7 +364,7 @@ __device__ __forceinline__ void seg_gather(bool valid, int a, int b, Idx idx, Ro
     for (int t = a; t < b; t += kSeg) {
       int ii[kSeg];
 #pragma unroll
-      for (int q = 0; q < kSeg; ++q) ii[q] = idx(min(t + q, b - 1));
+      for (int q = 0; q < kSeg; ++q) ii[q] = dbg_index(idx(min(t + q, b - 1)), lim, status);
       T r[kSeg][N];
 #pragma unroll
       for (int q = 0; q < kSeg; ++q) ldrow<T, N, CG>(row(ii[q]), r[q]);
@@ -389,7 +391,7 @@ __device__ __forceinline__ void seg_gather(bool valid, int a, int b, Idx idx, Ro
 #pragma unroll
       for (int q = 0; q < kSeg; ++q) {
         const int t = min(t0 + 32 * q, bb - 1);
-        ldrow<T, N, CG>(row(idx(t)), r[q]);
+        ldrow<T, N, CG>(row(dbg_index(idx(t), lim, status)), r[q]);
       }
 #pragma unroll
       for (int q = 0; q < kSeg; ++q) {
@@ -605,7 +607,7 @@ __device__ __forceinline__ void edge_item(const IncView& g, const ScalView<T>& s
   }
   T sum[2 * S];
   seg_gather<T, 2 * S, CG>(valid, a, b, pin,
-                           [&](int p) { return curv + (long long)p * 2 * S; }, sum);
+                           [&](int p) { return curv + (long long)p * 2 * S; }, sum, g.n, g.status);
   if (valid) {
     const int k = b - a;
     const T invk = k >= 2 ? (T)1 / (T)k : (T)0;
@@ -668,7 +670,7 @@ __device__ __forceinline__ void node_item(const IncView& g, const ScalView<T>& s
   }
   T sum[2 * S];
   seg_gather<T, 2 * S, CG>(valid, a, b, edge,
-                           [&](int e) { return er + (long long)e * 2 * S; }, sum);
+                           [&](int e) { return er + (long long)e * 2 * S; }, sum, g.m, g.status);
   if (valid) {
     // inverse norms of x_{j-1} and x_{j-2} (both expansions)
     const T* __restrict__ n1 = nuT + (size_t)(j - 1) * 2 * S;

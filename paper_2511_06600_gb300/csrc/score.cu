@@ -115,17 +115,18 @@ __device__ __forceinline__ void two_edge_extrema(const QT* __restrict__ Q, long 
 // hyperedge's extrema in mx/mn.
 template <typename T, int NC, typename QT>
 __device__ __forceinline__ void cta_edge_extrema(const QT* __restrict__ Q, long long ldq, int K,
-                                                 const int32_t* __restrict__ cpins, int a, int b,
+                                                 const int32_t* __restrict__ cpins, int nv,
+                                                 const unsigned int* status, int a, int b,
                                                  T* smx, T* smn, T (&mx)[NC], T (&mn)[NC]) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
 #pragma unroll
   for (int c = 0; c < NC; ++c) mx[c] = lowest<T>(), mn[c] = -lowest<T>();
   for (int t = a + 4 * wid; t < b; t += 4 * nw) {
     const int last = b - 1;
-    const QT* r0 = Q + (long long)cpins[t] * ldq;
-    const QT* r1 = Q + (long long)cpins[min(t + 1, last)] * ldq;
-    const QT* r2 = Q + (long long)cpins[min(t + 2, last)] * ldq;
-    const QT* r3 = Q + (long long)cpins[min(t + 3, last)] * ldq;
+    const QT* r0 = Q + (long long)dbg_index(cpins[t], nv, status) * ldq;
+    const QT* r1 = Q + (long long)dbg_index(cpins[min(t + 1, last)], nv, status) * ldq;
+    const QT* r2 = Q + (long long)dbg_index(cpins[min(t + 2, last)], nv, status) * ldq;
+    const QT* r3 = Q + (long long)dbg_index(cpins[min(t + 3, last)], nv, status) * ldq;
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
       const int col = lane + 32 * c;
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(256) k_score_big1(IncView g, const QT* __restr
   for (int bi = blockIdx.x; bi < nbig; bi += gridDim.x) {
     const int e = g.big_idx[bi];
     T mx[NC], mn[NC];
-    cta_edge_extrema<T, NC, QT>(Q, ldq, K, g.cpins, g.ceptr[e], g.ceptr[e + 1], smx, smn, mx, mn);
+    cta_edge_extrema<T, NC, QT>(Q, ldq, K, g.cpins, g.n, g.status, g.ceptr[e], g.ceptr[e + 1], smx,
+                                smn, mx, mn);
     const double we = g.ew[e];
 #pragma unroll
     for (int c = 0; c < NC; ++c) {
@@ -247,7 +249,9 @@ __global__ void __launch_bounds__(256) k_score_pass1(IncView g, const QT* __rest
     __syncwarp();  // the previous group's reads of spins are done
     for (int q = lane; q < npin; q += 32) spins[wid][q] = g.cpins[gp0 + q];
     __syncwarp();
-    auto pin_at = [&](int t) { return t - gp0 < npin ? spins[wid][t - gp0] : g.cpins[t]; };
+    auto pin_at = [&](int t) {
+      return dbg_index(t - gp0 < npin ? spins[wid][t - gp0] : g.cpins[t], g.n, g.status);
+    };
     if (b - a < 2 || b - a > kBigEdge) b = a;  // not scored here
     const T wl = (lane < kGroup1 && e < g.m) ? (T)g.ew[e] : (T)0;
     T* sprow = spread ? spread + grp * kGroup1 * ldsp : nullptr;  // row-major spreads of the group
@@ -382,6 +386,13 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
           const long long t = jw * kWinSlots + 4 * (lane & 15);
           pp4[h] = (jw < wc && t < g.P) ? *reinterpret_cast<const int4*>(g.cpins + t)
                                         : make_int4(0, 0, 0, 0);
+          if (HEF_DEBUG) {
+            // slots past P read as pin 0 of the padded array: only real slots are checked
+            pp4[h].x = t < g.P ? dbg_index(pp4[h].x, g.n, g.status) : pp4[h].x;
+            pp4[h].y = t + 1 < g.P ? dbg_index(pp4[h].y, g.n, g.status) : pp4[h].y;
+            pp4[h].z = t + 2 < g.P ? dbg_index(pp4[h].z, g.n, g.status) : pp4[h].z;
+            pp4[h].w = t + 3 < g.P ? dbg_index(pp4[h].w, g.n, g.status) : pp4[h].w;
+          }
         }
       } else {
 #pragma unroll
@@ -389,7 +400,9 @@ __global__ void __launch_bounds__(kBulkThreads, 1)
 #pragma unroll
           for (int u = 0; u < kRegs; ++u) {
             const long long t = (g0 + d) * kWinSlots + lane + 32 * u;
-            pp[d][u] = (g0 + d < wc && lane + 32 * u < kWinSlots && t < g.P) ? g.cpins[t] : 0;
+            pp[d][u] = (g0 + d < wc && lane + 32 * u < kWinSlots && t < g.P)
+                           ? dbg_index(g.cpins[t], g.n, g.status)
+                           : 0;
           }
       }
       wl = (lane <= kGroupWin && g0 + lane <= nwin) ? g.win_edge[g0 + lane] : 0;
@@ -610,7 +623,7 @@ __device__ __forceinline__ void score_edge_out(IncView g, const QT* __restrict__
   int tmax = 0x7fffffff, tmin = 0x7fffffff;
   if (any) {
     for (int t = a + lane; t < b; t += 32) {
-      const T v = qw<T>(Q[(long long)g.cpins[t] * ldq + bcol]);
+      const T v = qw<T>(Q[(long long)dbg_index(g.cpins[t], g.n, g.status) * ldq + bcol]);
       if (v == vmax && t < tmax) tmax = t;
       if (v == vmin && t < tmin) tmin = t;
     }
@@ -663,7 +676,7 @@ __global__ void __launch_bounds__(256) k_score_big2(IncView g, const QT* __restr
     const int e = g.big_idx[bi];
     const int a = g.ceptr[e], b = g.ceptr[e + 1];
     T mx[NC], mn[NC];
-    cta_edge_extrema<T, NC, QT>(Q, ldq, K, g.cpins, a, b, smx, smn, mx, mn);
+    cta_edge_extrema<T, NC, QT>(Q, ldq, K, g.cpins, g.n, g.status, a, b, smx, smn, mx, mn);
     if ((threadIdx.x >> 5) == 0)
       score_edge_out<T, NC, QT>(g, Q, ldq, K, reduce, invQH, iq, use, e, a, b, mx, mn, R_out, argvec,
                                 pmax, pmin);
@@ -703,7 +716,8 @@ __global__ void __launch_bounds__(256) k_score_pass2(IncView g, const QT* __rest
       const int a1 = __shfl_sync(0xffffffffu, a, i + 1), b1 = __shfl_sync(0xffffffffu, b, i + 1);
       if (a0 == b0 && a1 == b1) continue;
       T mx0[NC], mn0[NC], mx1[NC], mn1[NC];
-      two_edge_extrema<T, NC>(Q, ldq, K, [&](int t) { return g.cpins[t]; }, a0, b0, a1, b1, lane,
+      two_edge_extrema<T, NC>(Q, ldq, K, [&](int t) { return dbg_index(g.cpins[t], g.n, g.status); },
+                              a0, b0, a1, b1, lane,
                               mx0, mn0, mx1, mn1);
       if (b0 > a0)
         score_edge_out<T, NC, QT>(g, Q, ldq, K, reduce, invQH, iq, use, (int)(grp * 32 + i), a0, b0,
@@ -778,9 +792,9 @@ __global__ void __launch_bounds__(256) k_score_ratio(IncView g, const T* __restr
     int tmax = a, tmin = a;
     if (any && (pmax || pmin)) {
       // extrema of column bcol over the pins, lowest position on ties
-      T vmax = Q[(long long)g.cpins[a] * ldq + bcol], vmin = vmax;
+      T vmax = Q[(long long)dbg_index(g.cpins[a], g.n, g.status) * ldq + bcol], vmin = vmax;
       for (int t = a + 1; t < b; ++t) {
-        const T v = qw<T>(Q[(long long)g.cpins[t] * ldq + bcol]);
+        const T v = qw<T>(Q[(long long)dbg_index(g.cpins[t], g.n, g.status) * ldq + bcol]);
         if (v > vmax) vmax = v, tmax = t;
         if (v < vmin) vmin = v, tmin = t;
       }
@@ -871,7 +885,7 @@ __global__ void __launch_bounds__(256) k_score_ratio8(IncView g, const T* __rest
     int tmax = INT_MAX, tmin = INT_MAX;
     if (any && (pmax || pmin)) {
       for (int t = a + sub; t < b; t += kRatioLanes) {
-        const T v = qw<T>(Q[(long long)g.cpins[t] * ldq + bcol]);
+        const T v = qw<T>(Q[(long long)dbg_index(g.cpins[t], g.n, g.status) * ldq + bcol]);
         if (tmax == INT_MAX || v > vmax) vmax = v, tmax = t;
         if (tmin == INT_MAX || v < vmin) vmin = v, tmin = t;
       }
@@ -969,7 +983,8 @@ __global__ void __launch_bounds__(256) k_score_embed(IncView g, const QT* __rest
     long long bt = -1;
     int ba = 0, bb = 1;
     while (a < k - 1) {
-      const long long ra = (long long)g.cpins[a0 + a] * ldq, rb = (long long)g.cpins[a0 + b] * ldq;
+      const long long ra = (long long)dbg_index(g.cpins[a0 + a], g.n, g.status) * ldq;
+      const long long rb = (long long)dbg_index(g.cpins[a0 + b], g.n, g.status) * ldq;
       double d = 0.0;
       for (int c = 0; c < K; ++c) {
         const double diff = __dsub_rn(qw<double>(Q[ra + c]), qw<double>(Q[rb + c]));
@@ -991,7 +1006,8 @@ __global__ void __launch_bounds__(256) k_score_embed(IncView g, const QT* __rest
       const int oa = __shfl_xor_sync(0xffffffffu, ba, o), ob = __shfl_xor_sync(0xffffffffu, bb, o);
       if (od > bd || (od == bd && ot >= 0 && (bt < 0 || ot < bt))) bd = od, bt = ot, ba = oa, bb = ob;
     }
-    const int p = g.cpins[a0 + ba], q = g.cpins[a0 + bb];
+    const int p = dbg_index(g.cpins[a0 + ba], g.n, g.status);
+    const int q = dbg_index(g.cpins[a0 + bb], g.n, g.status);
     double br = -1.0;
     int bi = -1;
     for (int c = lane; c < K; c += 32) {

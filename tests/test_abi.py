@@ -39,3 +39,24 @@ def test_workspace_queries_reject_bad_sizes():
     assert L.hef_incidence_workspace_bytes(10, 3, 4) > 0
     assert L.hef_orthonormalize_workspace_bytes(100, 513, 0) == 0
     assert L.hef_orthonormalize_workspace_bytes(100, 20, 1) > 0
+
+
+def test_regular_build_has_no_bounds_checks():
+    import paper_2511_06600_gb300 as hef
+    L = hef.lib()
+    assert L.hef_debug_checks() == 0
+    # the test hook refuses (HEF_ERR_UNSUPPORTED) before touching its arguments
+    assert L.hef_debug_set_pin(None, 0, 0, None) == -6
+    assert L.hef_status_string(-8).decode() == "HEF_ERR_BOUNDS"
+
+
+def test_bounds_checked_build_exports_the_same_abi():
+    from paper_2511_06600_gb300 import build
+    path = build.build(debug=True)
+    lib = ctypes.CDLL(path)
+    missing = [nm for nm in declared_functions() if not hasattr(lib, nm)]
+    assert not missing, missing
+    lib.hef_debug_set_pin.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                      ctypes.c_void_p]
+    assert lib.hef_debug_checks() == 1
+    assert lib.hef_debug_set_pin(None, 0, 0, None) == -1  # NULL handle
