@@ -343,6 +343,18 @@ hef_status hef_edge_resistance(const hef_incidence* inc, const void* Q,
  * build.  Returns the first error of those calls,
  * HEF_ERR_INVALID_INPUT when the device-side validation failed, or
  * HEF_ERR_TIMEOUT when a bounded device wait expired.
+ *
+ * Repeated calls: when a thread calls again with the same host arrays,
+ * workspace, sizes, form and stream as its previous call, and every host
+ * array is page-locked, the second such call captures its device work (the
+ * copies, the four calls, the copy of R) into a CUDA graph on a private
+ * stream of the library, and later calls launch that graph on `stream`
+ * instead of some forty separate launches.  The graph copies the host
+ * arrays when it runs, so new contents in the same buffers are scored; it
+ * keeps the Krylov launch form chosen when it was captured
+ * (hef_set_krylov_persistent), and its launches do not pass through the
+ * library's launch accounting (hef_launch_count, hef_trace_kernels).  A call
+ * with anything different, or with pageable host arrays, runs as above.
  * ---------------------------------------------------------------------- */
 size_t hef_resistance_host_workspace_bytes(int64_t n, int64_t m, int64_t P,
                                            int32_t k, int32_t S,
