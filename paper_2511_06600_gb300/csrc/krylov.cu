@@ -974,12 +974,18 @@ __host__ __device__ constexpr int pers_threads() {
 // this part (a warp-wide FP64 add costs tens of issue cycles); otherwise in
 // FP64 (P = double).
 // Ends with __syncthreads (out may be shared memory).
+// reduce_slot_range: the same sums for slots [s_begin, s_end) by the nw warps
+// from warp w_first (the others return at once); each slot's result depends
+// only on its partials, not on which warp sums it.  No barrier at the end.
 template <int NT, bool DF, typename P>
-__device__ __forceinline__ void reduce_slots_wide(const P* part, int nb, int N, double* out) {
-  constexpr int kW = NT / 32;
+__device__ __forceinline__ void reduce_slot_range(const P* part, int nb, int s_begin, int s_end,
+                                                  double* out, int w_first, int nw) {
   constexpr int kI = DF ? 4 : 1;  // slots of a warp per round
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int s0 = w; s0 < N; s0 += kI * kW) {
+  const int lane = threadIdx.x & 31, w = (int)(threadIdx.x >> 5) - w_first;
+  if (w < 0 || w >= nw) return;
+  const int kW = nw;
+  const int N = s_end;
+  for (int s0 = s_begin + w; s0 < N; s0 += kI * kW) {
     P x[kI][8];
     DFloat da[kI];
     double acc[kI];
@@ -1021,6 +1027,10 @@ __device__ __forceinline__ void reduce_slots_wide(const P* part, int nb, int N, 
     for (int i = 0; i < kI; ++i)
       if (lane == 0 && s0 + i * kW < N) out[s0 + i * kW] = DF ? (double)da[i].hi + (double)da[i].lo : acc[i];
   }
+}
+template <int NT, bool DF, typename P>
+__device__ __forceinline__ void reduce_slots_wide(const P* part, int nb, int N, double* out) {
+  reduce_slot_range<NT, DF, P>(part, nb, 0, N, out, 0, NT / 32);
   __syncthreads();
 }
 
@@ -1094,8 +1104,11 @@ __device__ __forceinline__ unsigned int ld_relaxed(const unsigned int* p) {
   return v;
 }
 
+// `work` runs in warps 1.. while thread 0 waits (work that needs no result of
+// this barrier).
+template <typename Work>
 __device__ __forceinline__ bool grid_arrive_wait(int ph, unsigned int* flags, unsigned int* status,
-                                                 int b, int G) {
+                                                 int b, int G, Work work) {
   __shared__ int go;
   __syncthreads();
   const unsigned int want = (unsigned int)G * (unsigned int)(ph + 1);
@@ -1117,9 +1130,15 @@ __device__ __forceinline__ bool grid_arrive_wait(int ph, unsigned int* flags, un
     }
     asm volatile("fence.acq_rel.gpu;" ::: "memory");
     go = ok;
+  } else if (threadIdx.x >= 32) {
+    work();
   }
   __syncthreads();
   return go != 0;
+}
+__device__ __forceinline__ bool grid_arrive_wait(int ph, unsigned int* flags, unsigned int* status,
+                                                 int b, int G) {
+  return grid_arrive_wait(ph, flags, status, b, G, [] {});
 }
 
 // Partial-sum buffers of the persistent kernel: two buffers (barriers
@@ -1243,7 +1262,17 @@ __device__ __forceinline__ void krylov_body(const IncView& g, const ScalView<T>&
         node_item<T, S, true, TV>(g, sv, kv, s_nuT, j, v < v1 ? v : g.n, acc, V, ldv, vofs, vedg,
                                   own, v < v1 && v - v0 < nown ? v - v0 : -1);
       }
-      if (!pbarrier<6, S, NT>(acc, part, ph++, kPartSlots * S, cnt, status, s_red, b, G)) return;
+      // the vertex barrier: while thread 0 waits, warps 1.. sum the edge
+      // pass's slots [6S, 9S) (complete since the edge barrier); then all
+      // warps sum the vertex slots [0, 6S)
+      T* pbuf = part_buffer<T>(part, ph, G, S);
+      block_partials_qs<6, S, T, NT, 8, T>(acc, pbuf, b, G);
+      if (!grid_arrive_wait(ph++, cnt, status, b, G, [&] {
+            reduce_slot_range<NT, sizeof(T) == 4, T>(pbuf, G, 6 * S, kPartSlots * S, s_red, 1,
+                                                    NT / 32 - 1);
+          }))
+        return;
+      reduce_slots_wide<NT, sizeof(T) == 4, T>(pbuf, G, 6 * S, s_red);
       for (int c = tid; c < 2 * S; c += NT) {
         const int op = c / S, q = c % S;
         double cf[4];
