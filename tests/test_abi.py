@@ -60,3 +60,19 @@ def test_bounds_checked_build_exports_the_same_abi():
                                       ctypes.c_void_p]
     assert lib.hef_debug_checks() == 1
     assert lib.hef_debug_set_pin(None, 0, 0, None) == -1  # NULL handle
+
+
+def test_missing_library_fails_loudly_and_HEF_LIBRARY_selects_the_build():
+    """The binding has no other implementation: a library that is not there
+    raises at the first call; HEF_LIBRARY picks which build is loaded."""
+    import subprocess
+    import sys
+    code = ("import os, sys; sys.path.insert(0, %r); "
+            "os.environ['HEF_LIBRARY'] = '/nonexistent/libhef_missing.so'; "
+            "import paper_2511_06600_gb300._binding as B; "
+            "assert B.LIB_PATH == '/nonexistent/libhef_missing.so'; "
+            "\ntry:\n    B.lib()\nexcept RuntimeError as e:\n    print('raised', 'no fallback' in str(e))\n"
+            "else:\n    print('loaded')") % ROOT
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().splitlines()[-1] == "raised True"
